@@ -1,0 +1,239 @@
+/*
+ * sparrow_gb.h -- C ABI of the GB300 vectorized Sparrow environment step
+ * (paper arxiv 2305.04180, "Color": Sec. 3.2 Sparrow simulator, Sec. 3.1
+ * Actor-Sharer-Learner).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Return value: SG_OK (0) or a negative SG_E_* code.  No C++ exception
+ *   crosses this boundary.  sg_strerror() names a code.
+ * - "_dev" pointers are device pointers (cudaMalloc / torch tensors on the
+ *   library's device), owned by the caller, contiguous, 16-byte aligned
+ *   unless stated otherwise; the library never frees them.  Host pointers are
+ *   plain host memory.  Handles (sg_sim_t, sg_qnet_t, sg_replay_t) own their
+ *   device memory and release it in the matching _destroy call.
+ * - Every call that takes an sg_stream_t enqueues its work on that stream
+ *   (NULL = the legacy default stream) and returns without waiting; results
+ *   are valid once the stream reaches that point.  Calls without a stream are
+ *   synchronous.  Work on one handle must not run concurrently on two streams.
+ * - Errors found on the device (a bad action index, a wait that ran out) are
+ *   latched into a status word per handle; read it with sg_sim_status().
+ * - Layouts: an observation row has obs_dim = n_beams + 5 floats:
+ *   [0, n_beams)   LiDAR ranges / range_max (beams beyond an env's own beam
+ *                  count read 1.0),
+ *   n_beams + 0/1  goal vector in the robot frame (forward, left) / D,
+ *   n_beams + 2    heading-to-goal angle alpha / pi,
+ *   n_beams + 3/4  linear / angular velocity over their nominal maxima.
+ *   Matrices are row-major [rows][cols].
+ */
+#ifndef SPARROW_GB_H
+#define SPARROW_GB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* sg_stream_t; /* same type as cudaStream_t */
+typedef struct sg_sim* sg_sim_t;
+typedef struct sg_qnet* sg_qnet_t;
+typedef struct sg_replay* sg_replay_t;
+
+enum {
+  SG_OK = 0,
+  SG_E_INVAL = -1,   /* a NULL handle/pointer, a size or enum out of range */
+  SG_E_ALIGN = -2,   /* a device pointer without the documented alignment */
+  SG_E_OOM = -3,     /* a device or host allocation failed */
+  SG_E_CUDA = -4,    /* a CUDA runtime call failed */
+  SG_E_DEVICE = -5,  /* the device status word holds an error */
+  SG_E_TIMEOUT = -6  /* a bounded device-side wait ran out */
+};
+
+/* Device status bits (sg_sim_status). */
+#define SG_DEV_BAD_ACTION 0x1u /* an action index >= n_actions was stepped */
+#define SG_DEV_TIMEOUT 0x2u    /* a bounded spin-wait gave up */
+
+/* Rollout action sources (sg_sim_rollout). */
+#define SG_POLICY_RANDOM 0 /* uniform over the action table, counter RNG */
+#define SG_POLICY_EPS_Q 1  /* VEM: eps_i-greedy over the Q-network */
+
+/*
+ * Simulation parameters (Sec. 3.2; nominal values in the paper's
+ * simulation-parameter table).  Lengths are in cells (1 cell = 1 cm),
+ * angles in radians, times in seconds.  Each *_lo/*_hi pair is the uniform
+ * range that "vectorized diversity" (Sec. 3.2.4) re-draws per env at the start
+ * of every episode; lo == hi fixes the value.
+ */
+typedef struct sg_sim_config {
+  int32_t n_envs;      /* N >= 1 */
+  int32_t n_beams;     /* B_max in [2, 64]; obs_dim = n_beams + 5 */
+  int32_t n_actions;   /* in [1, 8] */
+  int32_t t_max;       /* episode truncation length (steps), >= 1 */
+  int32_t delay_lo;    /* control delay in steps, 0 <= lo <= hi <= 2 */
+  int32_t delay_hi;
+  float fov;           /* LiDAR fan, radians; beam j at phi - fov/2 + j fov/(nb-1) */
+  float range_max;     /* R_max, cells, > 0 */
+  float march_step;    /* ray-march sample spacing, cells, > 0; R_max/step <= 4096 */
+  float robot_radius;  /* collision disc radius, cells */
+  float goal_radius;   /* arrival disc radius around the goal, cells */
+  float near_dist;     /* reward term r_d = -1 when an obstacle is closer */
+  float start_offset;  /* S = (off, off), G = (W - off, H - off) per map */
+  float start_jitter;  /* start position jitter, uniform in +-jitter per axis */
+  float dt_lo, dt_hi;        /* control interval */
+  float k_lo, k_hi;          /* inertia factor K of Eq. 5 */
+  float cap_lo, cap_hi;      /* velocity-range factor on the action table */
+  float sigma_lo, sigma_hi;  /* LiDAR noise standard deviation, cells */
+  float v_nom, w_nom;        /* nominal max linear / angular velocity */
+  float action_v[8];         /* target linear velocity of each action */
+  float action_w[8];         /* target angular velocity of each action */
+  uint64_t seed;             /* counter-RNG key of every random draw */
+} sg_sim_config;
+
+/* Read-only facts about a simulator (sg_sim_info). */
+typedef struct sg_sim_info {
+  int32_t n_envs;
+  int32_t n_beams;
+  int32_t obs_dim;
+  int32_t n_maps;
+  int64_t atlas_words;   /* 32-bit words of the bit-packed map atlas */
+  int64_t state_bytes;   /* size of the sg_sim_get_state / set_state blob */
+  int32_t device;        /* CUDA device ordinal the simulator lives on */
+  int32_t pad0;
+} sg_sim_info;
+
+/* ---------------------------------------------------------------------- */
+/* Simulator                                                               */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * Create N vectorized environments on the current CUDA device.
+ * Sec. 3.2 (world matrix [x, y, phi, v_l, v_a, dt, K, O_xy], Sec. 3.2.3) and
+ * Sec. 3.2 "Map customization": maps are binary occupancy grids.
+ *   cfg        parameters (copied).
+ *   n_maps     number of maps, >= 1.
+ *   maps_host  n_maps host pointers; map m is a row-major uint8 grid of
+ *              map_h[m] rows x map_w[m] columns, nonzero = occupied.  The
+ *              library packs them into a device bit atlas (1 bit per cell,
+ *              rows padded to 16 bytes) and does not keep the host pointers.
+ *   map_w/h    map sides, each in [1, 16384].
+ *   env_map    n_envs host ints: the map of each env, in [0, n_maps).
+ *   env_beams  NULL (every env uses cfg->n_beams) or n_envs host ints in
+ *              [2, cfg->n_beams]: per-env beam counts (uneven batching).
+ *   out        receives the handle.
+ * Synchronous.  Errors: SG_E_INVAL, SG_E_OOM, SG_E_CUDA.
+ */
+int sg_sim_create(const sg_sim_config* cfg, int32_t n_maps, const uint8_t* const* maps_host,
+                  const int32_t* map_w, const int32_t* map_h, const int32_t* env_map,
+                  const int32_t* env_beams, sg_sim_t* out);
+
+/* Release every device buffer of the simulator.  Synchronous. */
+int sg_sim_destroy(sg_sim_t sim);
+
+/* Static facts (sizes) of a simulator. */
+int sg_sim_info_get(sg_sim_t sim, sg_sim_info* info);
+
+/*
+ * Start episode 0 of every env (Sec. 3.2.4: every randomised parameter is
+ * drawn per env; the robot starts near S with a random heading) and write the
+ * first observation.
+ *   seed     replaces cfg->seed for this and every later draw.
+ *   obs_dev  N x obs_dim floats (may be NULL: no observation written).
+ */
+int sg_sim_reset(sg_sim_t sim, uint64_t seed, float* obs_dev, sg_stream_t stream);
+
+/*
+ * One vectorized step of every env (Sec. 3.2: Eq. 5 and Eq. 6 kinematics with
+ * control delay, LiDAR ray casting with sensor noise, collision, arrival,
+ * reward Eq. 11 of Sec. 4.3.1, and AutoReset of done envs, Sec. 3.2.5).
+ *   act_dev       N uint8 action indices; an index >= n_actions counts as
+ *                 "no command" (zero target velocity) and sets
+ *                 SG_DEV_BAD_ACTION in the status word.
+ *   obs_dev       N x obs_dim floats: observation after the step (after the
+ *                 reset for done envs).
+ *   rew_dev       N floats.
+ *   done_dev      N uint8: bit0 collided, bit1 arrived, bit2 truncated.
+ *   term_obs_dev  N x obs_dim floats or NULL: for done envs the observation
+ *                 before the reset (rows of other envs are not written).
+ * No alignment beyond 4 bytes is required of these buffers.
+ */
+int sg_sim_step(sg_sim_t sim, const uint8_t* act_dev, float* obs_dev, float* rew_dev, uint8_t* done_dev,
+                float* term_obs_dev, sg_stream_t stream);
+
+/*
+ * K vectorized steps in one persistent launch (Alg. 1 steps 2-5 of the
+ * paper's Actor, the "vectorized data collection").  Each step picks the
+ * actions on the device:
+ *   SG_POLICY_RANDOM  uniform over the action table from the counter RNG;
+ *   SG_POLICY_EPS_Q   VEM (Sec. 3.1.1): with probability eps_dev[i] the random
+ *                     action, otherwise argmax_a Q(s, a) of `qnet` (lowest
+ *                     index on ties), Q evaluated in BF16 with FP32
+ *                     accumulation inside the same kernel.
+ *   qnet          required for SG_POLICY_EPS_Q, ignored otherwise.
+ *   eps_dev       N floats (required for SG_POLICY_EPS_Q).
+ *   replay        NULL or a ring that receives one transition per env-step
+ *                 (s, a, r, s', terminal), Alg. 1 step 5.
+ *   obs_dev       NULL or N x obs_dim floats: observation after the last step.
+ *   obs_seq_dev   NULL or K x N x obs_dim floats: observation after each step
+ *                 (after the reset for envs that were done).
+ *   act_seq_dev   NULL or K x N uint8: action taken at each step.
+ *   rew_seq_dev   NULL or K x N floats.
+ *   done_seq_dev  NULL or K x N uint8 (flags as in sg_sim_step).
+ * K in [1, 1 << 20].
+ */
+int sg_sim_rollout(sg_sim_t sim, int32_t K, int32_t policy, sg_qnet_t qnet, const float* eps_dev,
+                   sg_replay_t replay, float* obs_dev, float* obs_seq_dev, uint8_t* act_seq_dev,
+                   float* rew_seq_dev, uint8_t* done_seq_dev, sg_stream_t stream);
+
+/*
+ * Copy the complete env state to / from host memory (checkpoint / resume;
+ * every random draw is keyed by state, so a restored run continues
+ * bit-identically).  Blob layout, N = n_envs:
+ *   float    [9][N]  x, y, phi, v_l, v_a, dt, K, cap, sigma
+ *   uint32_t [3][N]  ep_step, ep_id, t (steps since reset)
+ *   uint32_t [1][N]  fifo: last action | previous action << 8 | delay << 16
+ *                    (255 = no action yet)
+ * *bytes: in = size of host_buf, out = bytes used (info.state_bytes).
+ * Synchronous.
+ */
+int sg_sim_get_state(sg_sim_t sim, void* host_buf, size_t* bytes);
+int sg_sim_set_state(sg_sim_t sim, const void* host_buf, size_t bytes);
+
+/*
+ * Copy the bit-packed map atlas to the host: for map m, row cy starts at
+ * word offs_host[m] + cy * row_words_host[m]; bit (cx & 31) of word
+ * (cx >> 5) of that row is cell cx.  Any of the three outputs may be NULL.
+ * *words: in = capacity of atlas_host in words, out = atlas words.
+ * Synchronous.
+ */
+int sg_sim_get_atlas(sg_sim_t sim, uint32_t* atlas_host, size_t* words, int64_t* offs_host,
+                     int32_t* row_words_host);
+
+/*
+ * Copy the clearance maps to the host (an acceleration structure of the ray
+ * march, not part of the paper's step): for map m, byte offs_host[m] +
+ * cy * W + cx is min(255, Chebyshev distance in cells from cell (cx, cy) to
+ * the nearest occupied cell), cells outside the map counting as occupied; 0
+ * on occupied cells.  *bytes: in = capacity of host, out = total bytes.
+ * host and offs_host may be NULL.  Synchronous.
+ */
+int sg_sim_get_clearance(sg_sim_t sim, uint8_t* host, size_t* bytes, int64_t* offs_host);
+
+/*
+ * Read (synchronously) and clear the device status word: SG_DEV_* bits.
+ * Returns SG_E_DEVICE if any bit was set, SG_OK otherwise.
+ */
+int sg_sim_status(sg_sim_t sim, uint32_t* device_status);
+
+/* Human-readable name of an SG_* return code. */
+const char* sg_strerror(int code);
+
+/* Text of the last CUDA error seen by this thread inside the library. */
+const char* sg_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPARROW_GB_H */

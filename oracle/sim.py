@@ -94,10 +94,15 @@ def lib(prec: str = "f32"):
             L.orc_reset_env.argtypes = [vp, vp, vp, C.c_int32, C.c_uint32, vp]
             L.orc_reset.argtypes = [vp, vp, vp, vp]
             L.orc_step.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
+            L.orc_step_one.argtypes = [vp, vp, vp, C.c_int32, C.c_uint8, vp, vp, vp, vp, vp]
             L.orc_random_action.restype = C.c_uint8
             L.orc_random_action.argtypes = [vp, C.c_int32, C.c_uint64]
             L.orc_explore_uniform.restype = R
             L.orc_explore_uniform.argtypes = [vp, C.c_int32, C.c_uint64]
+            L.orc_march_samples.restype = C.c_uint64
+            L.orc_march_samples.argtypes = []
+            L.orc_reset_march_samples.argtypes = []
+            L.orc_rollout_random_range.argtypes = [vp, vp, vp, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, vp]
             L.orc_rollout_random.argtypes = [vp, vp, vp, C.c_int32, C.c_uint64, vp, vp, vp, vp, vp, vp]
             _LIBS[prec] = L
         return _LIBS[prec]
@@ -207,6 +212,20 @@ class OracleSim:
                         self.status.ctypes.data)
         return obs, rew, done, term
 
+    def step_one(self, i: int, a: int):
+        """Step env i alone; returns (obs row, reward, done, term row)."""
+        obs = np.zeros(self.obs_dim, self.dtype)
+        term = np.zeros(self.obs_dim, self.dtype)
+        rew = np.zeros(1, self.dtype)
+        done = np.zeros(1, np.uint8)
+        self.L.orc_step_one(C.byref(self.cfg), C.byref(self.cmaps), C.byref(self.cenvs), int(i), int(a),
+                            obs.ctypes.data, rew.ctypes.data, done.ctypes.data, term.ctypes.data,
+                            self.status.ctypes.data)
+        return obs, rew[0], int(done[0]), term
+
+    def random_action(self, i: int, t: int) -> int:
+        return int(self.L.orc_random_action(C.byref(self.cfg), int(i), int(t)))
+
     def random_actions(self, t: int) -> np.ndarray:
         return np.array([self.L.orc_random_action(C.byref(self.cfg), i, int(t)) for i in range(self.n)],
                         np.uint8)
@@ -225,6 +244,11 @@ class OracleSim:
                                   int(t0), obs.ctypes.data, term.ctypes.data, act.ctypes.data,
                                   rew.ctypes.data, done.ctypes.data, self.status.ctypes.data)
         return obs, act, rew, done
+
+    def rollout_random_range(self, i0: int, i1: int, K: int, t0: int = 0):
+        """Step envs [i0, i1) alone for K random-action steps (timing)."""
+        self.L.orc_rollout_random_range(C.byref(self.cfg), C.byref(self.cmaps), C.byref(self.cenvs), int(i0),
+                                        int(i1), int(K), int(t0), self.status.ctypes.data)
 
     # -- single-query helpers for the pins ---------------------------------
     def lidar(self, map_id: int, x: float, y: float, phi: float, nb: int | None = None):

@@ -258,8 +258,13 @@ void orc_pack_map(const uint8_t* grid, int32_t w, int32_t h, int32_t row_words, 
  * p_k = (fma(kD, ux, x), fma(kD, uy, y)) for k = 1..kmax; the first sample
  * whose cell floor(p) is occupied or outside the map is the hit.  Returns the
  * hit index, or kmax + 1 when no sample hits. */
+static uint64_t g_samples = 0; /* march samples evaluated (instrumentation) */
+uint64_t orc_march_samples(void) { return g_samples; }
+void orc_reset_march_samples(void) { g_samples = 0; }
+
 static int32_t march(const orc_maps* m, int32_t map, R x, R y, R ux, R uy, R delta, int32_t kmax) {
   for (int32_t k = 1; k <= kmax; ++k) {
+    ++g_samples;
     R t = (R)k * delta;
     R px = FMA(t, ux, x);
     R py = FMA(t, uy, y);
@@ -549,6 +554,13 @@ void orc_step(const orc_config* c, const orc_maps* m, orc_envs* e, const uint8_t
     step_env(c, m, e, i, act[i], obs + i * stride, rew + i, done + i, term_obs + i * stride, status);
 }
 
+/* Step env i alone (the other envs are untouched); obs/term_obs are its
+ * rows. */
+void orc_step_one(const orc_config* c, const orc_maps* m, orc_envs* e, int32_t i, uint8_t a, R* obs, R* rew,
+                  uint8_t* done, R* term_obs, uint32_t* status) {
+  step_env(c, m, e, i, a, obs, rew, done, term_obs, status);
+}
+
 /* Network-free action source: uniform over the action table from the
  * counter RNG keyed by (seed, env, global step). */
 uint8_t orc_random_action(const orc_config* c, int32_t i, uint64_t t) {
@@ -560,6 +572,17 @@ uint8_t orc_random_action(const orc_config* c, int32_t i, uint64_t t) {
  * explores when it is below its exploration noise eps_i (Sec. 3.1.1). */
 R orc_explore_uniform(const orc_config* c, int32_t i, uint64_t t) {
   return u24(orc_rng(c->seed, STREAM_ACTION, (uint64_t)i, t, 1u));
+}
+
+/* K steps of envs [i0, i1) alone with random actions from global step t0;
+ * rewards and done flags are not kept (used to time the oracle). */
+void orc_rollout_random_range(const orc_config* c, const orc_maps* m, orc_envs* e, int32_t i0, int32_t i1,
+                              int32_t K, uint64_t t0, uint32_t* status) {
+  R obs[69], term[69], rew;
+  uint8_t done;
+  for (int32_t i = i0; i < i1; ++i)
+    for (int32_t k = 0; k < K; ++k)
+      step_env(c, m, e, i, orc_random_action(c, i, t0 + (uint64_t)k), obs, &rew, &done, term, status);
 }
 
 /* K steps with random actions starting at global step t0.  Per step k it

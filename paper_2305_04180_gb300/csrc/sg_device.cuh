@@ -1,0 +1,542 @@
+// sg_device.cuh -- device-side building blocks of the vectorized Sparrow step
+// (paper arxiv 2305.04180, Sec. 3.2).  One warp simulates one environment:
+// the scalar part of the step (kinematics, reward, reset draws) runs
+// redundantly in every lane, so that no shuffle is needed to share it, while
+// the LiDAR beams, the collision disc rows and the observation stores are
+// spread over the lanes.
+//
+// Floating point: this file is compiled with -fmad=false, so every a*b+c is a
+// rounded multiply followed by a rounded add; fmaf() appears exactly where the
+// step definition fuses.  Divisions and square roots are IEEE (no fast math).
+// Under these rules the step is a fixed float32 expression tree, and its
+// discrete decisions (hit index, collision, arrival, reset) are reproducible
+// bit for bit by any IEEE float32 evaluation of the same tree.
+#pragma once
+
+#include <cstdint>
+
+namespace sg {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr uint32_t kStreamReset = 1;
+constexpr uint32_t kStreamNoise = 2;
+constexpr uint32_t kStreamAction = 3;
+constexpr uint32_t kNoAction = 255;
+constexpr float kPi = 3.14159265358979323846f;
+constexpr float kTwoPow24Inv = 5.9604644775390625e-08f;
+
+// Atlas entry of one map.  Bits: row cy starts at word_off + cy * row_words.
+// Clearance: byte clr_off + cy * w + cx holds min(255, Chebyshev distance in
+// cells from (cx, cy) to the nearest occupied cell, cells outside the map
+// counting as occupied); 0 exactly on occupied cells.
+struct MapDesc {
+  long long word_off;
+  long long clr_off;
+  int w, h;
+  int row_words;
+  int pad;
+};
+
+// Launch-time copy of the configuration (float32 values).
+struct DevCfg {
+  int n_envs, B, obs_dim, n_actions, t_max, kmax, delay_lo, delay_span;
+  int skip_ok;      // march_step <= 1: clearance skipping is exact
+  int clr_collide;  // clearance at which the collision disc cannot touch a wall
+  float fov, half_fov, range_max, delta, robot_r, goal_r, near_dist, start_offset, jitter;
+  float dt_lo, dt_hi, k_lo, k_hi, cap_lo, cap_hi, sig_lo, sig_hi;
+  float v_nom, w_nom;
+  float av[8], aw[8];
+  unsigned long long seed;
+};
+
+// Device buffers of a simulator (structure of arrays, stride n).
+struct SimPtrs {
+  float* f;               // [9][n]: x y phi vl va dt K cap sigma
+  uint32_t* u;            // [4][n]: ep_step ep_id t fifo
+  const uint32_t* atlas;  // bit-packed maps
+  const uint8_t* clr;     // clearance maps
+  const MapDesc* maps;
+  const int* env_map;
+  const int* env_beams;   // nullptr: every env uses B beams
+  uint32_t* status;       // SG_DEV_* bits
+  int n;
+  int pad;
+};
+
+// Registers of one environment.
+struct Env {
+  float x, y, phi, vl, va, dt, K, cap, sigma;
+  uint32_t ep_step, ep_id, t, fifo;  // fifo: q0 | q1 << 8 | delay << 16
+};
+
+// ------------------------------------------------------------- RNG
+// SplitMix64 (Steele, Lea & Flood 2014): value of the generator seeded with s
+// after c+1 steps; nesting it hashes several counters.
+__device__ __forceinline__ uint64_t sm_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ uint64_t sm_at(uint64_t s, uint64_t c) {
+  return sm_mix(s + (c + 1ull) * 0x9E3779B97F4A7C15ull);
+}
+__device__ __forceinline__ float u24_hi(uint64_t h) {
+  return (float)(uint32_t)(h >> 40) * kTwoPow24Inv;
+}
+__device__ __forceinline__ float u24_mid(uint64_t h) {
+  return (float)(uint32_t)((h >> 16) & 0xFFFFFFu) * kTwoPow24Inv;
+}
+
+// ------------------------------------------------- float32 functions
+// sin and cos together: Cody-Waite reduction by the nearest multiple of
+// pi/2 (two-word pi/2 through fma), Taylor polynomials of sin (degree 11)
+// and cos (degree 12) in Horner form, quadrant from q mod 4.
+__device__ __forceinline__ void f_sincos(float a, float& s, float& c) {
+  const float q = rintf(a * 0.636619772f);
+  const int qi = (int)q;
+  float r = fmaf(-q, 1.57079637050628662109375f, a);
+  r = fmaf(-q, -4.371139000186243e-08f, r);
+  const float z = r * r;
+  float ps = fmaf(z, -2.505210838544172e-08f, 2.7557319223985893e-06f);
+  ps = fmaf(z, ps, -1.984126984126984e-04f);
+  ps = fmaf(z, ps, 8.333333333333333e-03f);
+  ps = fmaf(z, ps, -1.6666666666666666e-01f);
+  const float sr = fmaf(r * z, ps, r);
+  float pc = fmaf(z, 2.08767569878681e-09f, -2.755731922398589e-07f);
+  pc = fmaf(z, pc, 2.48015873015873e-05f);
+  pc = fmaf(z, pc, -1.388888888888889e-03f);
+  pc = fmaf(z, pc, 4.1666666666666664e-02f);
+  pc = fmaf(z, pc, -0.5f);
+  const float cr = fmaf(z, pc, 1.0f);
+  switch (qi & 3) {
+    case 0: s = sr; c = cr; break;
+    case 1: s = cr; c = -sr; break;
+    case 2: s = -sr; c = -cr; break;
+    default: s = -cr; c = sr; break;
+  }
+}
+
+// atan2 by octant reduction, the identity atan t = pi/4 + atan((t-1)/(t+1))
+// above tan(pi/8), and the alternating series of atan to degree 21.
+// Coefficients are the floats nearest 1/n.
+__device__ __forceinline__ float f_atan2(float y, float x) {
+  const float ax = fabsf(x), ay = fabsf(y);
+  if (ax == 0.0f && ay == 0.0f) return 0.0f;
+  const bool swap = ay > ax;
+  const float num = swap ? ax : ay;
+  const float den = swap ? ay : ax;
+  float t = num / den;
+  float base = 0.0f;
+  if (t > 0.414213562373095f) {
+    t = (t - 1.0f) / (t + 1.0f);
+    base = 0.785398163397448f;
+  }
+  const float w = t * t;
+  float p = fmaf(w, 0.04761905f, -0.05263158f);
+  p = fmaf(w, p, 0.05882353f);
+  p = fmaf(w, p, -0.06666667f);
+  p = fmaf(w, p, 0.07692308f);
+  p = fmaf(w, p, -0.09090909f);
+  p = fmaf(w, p, 0.11111111f);
+  p = fmaf(w, p, -0.14285715f);
+  p = fmaf(w, p, 0.2f);
+  p = fmaf(w, p, -0.33333334f);
+  p = fmaf(w, p, 1.0f);
+  float a = base + t * p;
+  if (swap) a = 1.57079632679490f - a;
+  if (x < 0.0f) a = 3.14159265358979f - a;
+  if (y < 0.0f) a = -a;
+  return a;
+}
+
+// Natural log of a positive normal float: x = m 2^e with m in
+// (sqrt(1/2), sqrt(2)], ln m = 2 atanh((m-1)/(m+1)) by its odd series to
+// degree 13, plus e ln 2 split in two words.
+__device__ __forceinline__ float f_log(float x) {
+  const uint32_t bits = __float_as_uint(x);
+  int e = (int)((bits >> 23) & 0xFFu) - 127;
+  float m = __uint_as_float((bits & 0x7FFFFFu) | 0x3F800000u);
+  if (m > 1.41421356237310f) {
+    m = m * 0.5f;
+    e = e + 1;
+  }
+  const float z = (m - 1.0f) / (m + 1.0f);
+  const float w = z * z;
+  float p = fmaf(w, 0.07692308f, 0.09090909f);
+  p = fmaf(w, p, 0.11111111f);
+  p = fmaf(w, p, 0.14285715f);
+  p = fmaf(w, p, 0.2f);
+  p = fmaf(w, p, 0.33333334f);
+  p = fmaf(w, p, 1.0f);
+  const float t = z * p;
+  const float lnm = t + t;
+  const float ef = (float)e;
+  const float lo = fmaf(ef, 1.4286068203094172e-06f, lnm);
+  return fmaf(ef, 0.693145751953125f, lo);
+}
+
+// ------------------------------------------------------- state I/O
+__device__ __forceinline__ Env load_env(const SimPtrs& p, int i) {
+  Env s;
+  const int n = p.n;
+  s.x = p.f[0 * n + i];
+  s.y = p.f[1 * n + i];
+  s.phi = p.f[2 * n + i];
+  s.vl = p.f[3 * n + i];
+  s.va = p.f[4 * n + i];
+  s.dt = p.f[5 * n + i];
+  s.K = p.f[6 * n + i];
+  s.cap = p.f[7 * n + i];
+  s.sigma = p.f[8 * n + i];
+  s.ep_step = p.u[0 * n + i];
+  s.ep_id = p.u[1 * n + i];
+  s.t = p.u[2 * n + i];
+  s.fifo = p.u[3 * n + i];
+  return s;
+}
+
+__device__ __forceinline__ void store_env(const SimPtrs& p, int i, const Env& s) {
+  const int n = p.n;
+  p.f[0 * n + i] = s.x;
+  p.f[1 * n + i] = s.y;
+  p.f[2 * n + i] = s.phi;
+  p.f[3 * n + i] = s.vl;
+  p.f[4 * n + i] = s.va;
+  p.f[5 * n + i] = s.dt;
+  p.f[6 * n + i] = s.K;
+  p.f[7 * n + i] = s.cap;
+  p.f[8 * n + i] = s.sigma;
+  p.u[0 * n + i] = s.ep_step;
+  p.u[1 * n + i] = s.ep_id;
+  p.u[2 * n + i] = s.t;
+  p.u[3 * n + i] = s.fifo;
+}
+
+// -------------------------------------------------------- geometry
+struct Layout {
+  float sx, sy, gx, gy, D;
+};
+
+// Start S (lower left), goal G (upper right) and planning distance D = |G-S|.
+__device__ __forceinline__ Layout layout_of(const DevCfg& c, const MapDesc& m) {
+  Layout L;
+  L.sx = c.start_offset;
+  L.sy = c.start_offset;
+  L.gx = (float)m.w - c.start_offset;
+  L.gy = (float)m.h - c.start_offset;
+  const float ex = L.gx - L.sx, ey = L.gy - L.sy;
+  L.D = sqrtf(fmaf(ex, ex, ey * ey));
+  return L;
+}
+
+// Fixed-step ray march: sample k = 1..kmax at (fma(k d, ux, x), fma(k d, uy, y));
+// the first sample whose cell is occupied or outside the map is the hit.
+//
+// The march reads the clearance map instead of the bits: clearance 0 is an
+// occupied cell, and clearance c >= 1 says every cell within Chebyshev
+// distance c - 1 is free and inside the map.  With march_step <= 1 and
+// |ux|, |uy| <= 1 the sample cell moves by at most j + 1 cells per axis over
+// j samples (j cells of travel plus one for the rounding of the two fma
+// results, which is below 2^-9 cells for maps up to 16384 cells), so the
+// samples k+1 .. k+c-2 all lie in free cells and the next sample that can hit
+// is k + max(1, c - 1).  The hit index is therefore the same as testing every
+// sample.
+__device__ __forceinline__ int march(const uint8_t* __restrict__ clr, int W, int H, float x, float y, float ux,
+                                     float uy, float delta, int kmax, int skip_ok) {
+  int k = 1;
+  while (k <= kmax) {
+    const float t = (float)k * delta;
+    const float px = fmaf(t, ux, x);
+    const float py = fmaf(t, uy, y);
+    const int ix = __float2int_rd(px), iy = __float2int_rd(py);
+    if ((unsigned)ix >= (unsigned)W || (unsigned)iy >= (unsigned)H) return k;
+    const int c = __ldg(clr + iy * W + ix);
+    if (c == 0) return k;
+    k += skip_ok ? max(1, c - 1) : 1;
+  }
+  return kmax + 1;
+}
+
+// Robot disc against the occupied cells: the centre leaving the map, or an
+// occupied cell centre within robot_r (fma(dx,dx,dy*dy) <= r*r).  Lanes take
+// rows of the candidate box; only set bits reach the distance test.
+__device__ __forceinline__ bool collide_warp(const DevCfg& c, const MapDesc& m, const uint32_t* __restrict__ rows,
+                                             const uint8_t* __restrict__ clr, float x, float y, int lane) {
+  if (x < 0.0f || y < 0.0f || x >= (float)m.w || y >= (float)m.h) return true;
+  // every occupied cell centre is at least clearance - 0.5 cells away from a
+  // point of this cell: far enough means no cell can be within robot_r
+  const int own = __ldg(clr + __float2int_rd(y) * m.w + __float2int_rd(x));
+  if (own >= c.clr_collide) return false;
+  const float r = c.robot_r;
+  const float r2 = r * r;
+  int cx0 = (int)floorf(x - r) - 1, cx1 = (int)floorf(x + r) + 1;
+  int cy0 = (int)floorf(y - r) - 1, cy1 = (int)floorf(y + r) + 1;
+  cx0 = max(cx0, 0);
+  cy0 = max(cy0, 0);
+  cx1 = min(cx1, m.w - 1);
+  cy1 = min(cy1, m.h - 1);
+  bool hit = false;
+  for (int cy = cy0 + lane; cy <= cy1; cy += 32) {
+    const uint32_t* row = rows + (long long)cy * m.row_words;
+    for (int wd = cx0 >> 5; wd <= (cx1 >> 5); ++wd) {
+      const int lo = max(cx0 - wd * 32, 0), hi = min(cx1 - wd * 32, 31);
+      const uint32_t mask = (0xFFFFFFFFu >> (31 - hi)) & (0xFFFFFFFFu << lo);
+      uint32_t bits = __ldg(row + wd) & mask;
+      while (bits) {
+        const int b = __ffs(bits) - 1;
+        bits &= bits - 1;
+        const float dx = ((float)(wd * 32 + b) + 0.5f) - x;
+        const float dy = ((float)cy + 0.5f) - y;
+        if (fmaf(dx, dx, dy * dy) <= r2) hit = true;
+      }
+    }
+  }
+  return __any_sync(kFull, hit);
+}
+
+// ------------------------------------------------- per-env constants
+// Quantities that do not change between the steps of one launch.
+struct EnvConst {
+  MapDesc m;
+  const uint32_t* rows;  // this env's bit rows
+  const uint8_t* clr;    // this env's clearance map
+  Layout L;
+  int env, nb;
+  float off0, off1;      // heading offsets of this lane's beams (lane, lane + 32)
+  uint64_t nkey;         // counter-RNG prefix of the sensor noise
+  uint64_t rkey;         // counter-RNG prefix of the episode draws
+};
+
+__device__ __forceinline__ EnvConst env_const(const DevCfg& c, const SimPtrs& p, int env, int lane) {
+  EnvConst k;
+  k.env = env;
+  k.m = p.maps[p.env_map[env]];
+  k.rows = p.atlas + k.m.word_off;
+  k.clr = p.clr + k.m.clr_off;
+  k.L = layout_of(c, k.m);
+  k.nb = p.env_beams ? p.env_beams[env] : c.B;
+  // beam j points at phi + j * (fov / (nb - 1)) - fov / 2
+  const float stepb = c.fov / (float)(k.nb - 1);
+  k.off0 = (float)lane * stepb - c.half_fov;
+  k.off1 = (float)(lane + 32) * stepb - c.half_fov;
+  k.nkey = sm_at(sm_at(c.seed, kStreamNoise), (uint64_t)k.env);
+  k.rkey = sm_at(sm_at(c.seed, kStreamReset), (uint64_t)k.env);
+  return k;
+}
+
+// ---------------------------------------------------- observation
+// This lane's share of an observation row: beams lane and lane + 32, and
+// entry n_beams + lane for lanes 0..4.
+struct ObsRegs {
+  float b0, b1, ex;
+};
+struct Aux {
+  float min_range, alpha, ddx, ddy;
+};
+// Standard normal samples of this lane's beams for one (episode, step).
+struct Noise {
+  float n0, n1;
+};
+
+// Box-Muller on one 64-bit draw: u1 in (0, 1] from the top 24 bits, u2 in
+// [0, 1) from bits 16..39; n = sqrt(-2 ln u1) cos(2 pi u2).
+__device__ __forceinline__ float box_muller(uint64_t hs) {
+  const float u1 = (float)((uint32_t)(hs >> 40) + 1u) * kTwoPow24Inv;
+  const float u2 = u24_mid(hs);
+  const float l = f_log(u1);
+  const float rad = sqrtf(-2.0f * l);
+  const float ang = u2 * (2.0f * kPi);
+  float sn, cs;
+  f_sincos(ang, sn, cs);
+  return rad * cs;
+}
+
+// Noise of the observation taken at step ep_step of episode ep_id.  It does
+// not depend on the scan, so it is drawn ahead, off the scan's critical path.
+__device__ __forceinline__ Noise noise_for(const EnvConst& k, float sigma, uint32_t ep_id, uint32_t ep_step,
+                                           int lane) {
+  Noise z;
+  z.n0 = 0.0f;
+  z.n1 = 0.0f;
+  if (sigma > 0.0f) {
+    const uint64_t pre = sm_at(k.nkey, ((uint64_t)ep_id << 32) | ep_step);
+    z.n0 = box_muller(sm_at(pre, (uint64_t)lane));
+    if (k.nb > 32) z.n1 = box_muller(sm_at(pre, (uint64_t)(lane + 32)));
+  }
+  return z;
+}
+
+__device__ __forceinline__ float beam_range(const DevCfg& c, const EnvConst& k, const Env& s, float off, float nz,
+                                            float& mn) {
+  const float beta = s.phi + off;
+  float sn, cs;
+  f_sincos(beta, sn, cs);
+  const int h = march(k.clr, k.m.w, k.m.h, s.x, s.y, -cs, -sn, c.delta, c.kmax, c.skip_ok);
+  float r = fminf((float)h * c.delta, c.range_max);
+  mn = fminf(mn, r);
+  if (s.sigma > 0.0f) {
+    // additive Gaussian sensor noise on the reported range, clamped
+    r = r + s.sigma * nz;
+    r = fminf(fmaxf(r, 0.0f), c.range_max);
+  }
+  return r / c.range_max;
+}
+
+__device__ __forceinline__ void observe(const DevCfg& c, const EnvConst& k, const Env& s, const Noise& z, int lane,
+                                        ObsRegs& o, Aux& aux) {
+  // goal in the robot frame (forward (-cos phi, -sin phi), left = forward
+  // turned by +90 degrees) and the heading-to-goal angle; independent of the
+  // scan, so issued first
+  float sn, cs;
+  f_sincos(s.phi, sn, cs);
+  const float ddx = k.L.gx - s.x, ddy = k.L.gy - s.y;
+  const float fwd = -(ddx * cs + ddy * sn);
+  const float left = sn * ddx - cs * ddy;
+  const float alpha = f_atan2(left, fwd);
+  // lanes 0..4 hold fwd/D, left/D, alpha/pi, vl/v_nom, va/w_nom: one division
+  const float num = lane == 0 ? fwd : lane == 1 ? left : lane == 2 ? alpha : lane == 3 ? s.vl : s.va;
+  const float den = lane < 2 ? k.L.D : lane == 2 ? kPi : lane == 3 ? c.v_nom : c.w_nom;
+  o.ex = num / den;
+  float mn = c.range_max;
+  o.b0 = lane < k.nb ? beam_range(c, k, s, k.off0, z.n0, mn) : 1.0f;
+  o.b1 = lane + 32 < k.nb ? beam_range(c, k, s, k.off1, z.n1, mn) : 1.0f;
+  // ranges are >= 0, so their bit patterns order like the values
+  aux.min_range = __uint_as_float(__reduce_min_sync(kFull, __float_as_uint(mn)));
+  aux.alpha = alpha;
+  aux.ddx = ddx;
+  aux.ddy = ddy;
+}
+
+__device__ __forceinline__ void write_obs(float* row, const ObsRegs& o, int B, int lane) {
+  if (lane < B) row[lane] = o.b0;
+  if (lane + 32 < B) row[lane + 32] = o.b1;
+  if (lane < 5) row[B + lane] = o.ex;
+}
+
+// ------------------------------------------------------------ reset
+__device__ __forceinline__ uint64_t shfl_u64(uint64_t v, int src) {
+  const uint32_t hi = __shfl_sync(kFull, (uint32_t)(v >> 32), src);
+  const uint32_t lo = __shfl_sync(kFull, (uint32_t)v, src);
+  return ((uint64_t)hi << 32) | lo;
+}
+
+// New episode ep_id (Sec. 3.2.4): every randomised parameter re-drawn from
+// the counter RNG keyed by (seed, env, ep_id); start near S.  Lanes 0..7
+// draw one slot each.
+__device__ __forceinline__ void reset_env(const DevCfg& c, const EnvConst& k, Env& s, uint32_t ep_id, int lane) {
+  const uint64_t pre = sm_at(k.rkey, (uint64_t)ep_id);
+  const uint64_t mine = sm_at(pre, (uint64_t)(lane & 7));
+  const uint64_t h0 = shfl_u64(mine, 0), h1 = shfl_u64(mine, 1), h2 = shfl_u64(mine, 2);
+  const uint64_t h3 = shfl_u64(mine, 3), h4 = shfl_u64(mine, 4), h5 = shfl_u64(mine, 5);
+  const uint64_t h6 = shfl_u64(mine, 6), h7 = shfl_u64(mine, 7);
+  s.dt = c.dt_lo + u24_hi(h0) * (c.dt_hi - c.dt_lo);
+  const uint32_t d = (uint32_t)c.delay_lo + (uint32_t)(h1 >> 32) % (uint32_t)c.delay_span;
+  s.K = c.k_lo + u24_hi(h2) * (c.k_hi - c.k_lo);
+  s.cap = c.cap_lo + u24_hi(h3) * (c.cap_hi - c.cap_lo);
+  s.sigma = c.sig_lo + u24_hi(h4) * (c.sig_hi - c.sig_lo);
+  const float J = c.jitter;
+  const float jx = -J + u24_hi(h5) * (J - (-J));
+  const float jy = -J + u24_hi(h6) * (J - (-J));
+  s.x = k.L.sx + jx;
+  s.y = k.L.sy + jy;
+  s.phi = -kPi + u24_hi(h7) * (kPi - (-kPi));
+  s.vl = 0.0f;
+  s.va = 0.0f;
+  s.ep_step = 0;
+  s.ep_id = ep_id;
+  s.fifo = kNoAction | (kNoAction << 8) | (d << 16);
+}
+
+// ------------------------------------------------------------- step
+// Control delay, target velocity, Eq. 5, Eq. 6 (new velocity, old heading),
+// heading wrap into [-pi, pi).
+__device__ __forceinline__ bool kinematics(const DevCfg& c, Env& s, uint32_t a) {
+  const uint32_t q0 = s.fifo & 0xFFu, q1 = (s.fifo >> 8) & 0xFFu, d = (s.fifo >> 16) & 0xFFu;
+  const uint32_t ahat = d == 0 ? a : (d == 1 ? q0 : q1);
+  s.fifo = (a & 0xFFu) | (q0 << 8) | (d << 16);
+  float vhl = 0.0f, vha = 0.0f;
+  if (ahat < (uint32_t)c.n_actions) {
+    vhl = c.av[ahat] * s.cap;
+    vha = c.aw[ahat] * s.cap;
+  }
+  const float omk = 1.0f - s.K;
+  s.vl = s.K * s.vl + omk * vhl;
+  s.va = s.K * s.va + omk * vha;
+  float sn, cs;
+  f_sincos(s.phi, sn, cs);
+  s.x = s.x - s.dt * (s.vl * cs);
+  s.y = s.y - s.dt * (s.vl * sn);
+  float phi = s.phi + s.dt * s.va;
+  if (phi >= kPi)
+    phi = phi - 2.0f * kPi;
+  else if (phi < -kPi)
+    phi = phi + 2.0f * kPi;
+  s.phi = phi;
+  s.ep_step += 1u;
+  s.t += 1u;
+  return a >= (uint32_t)c.n_actions;
+}
+
+struct StepOut {
+  float rew;
+  uint32_t done;
+};
+
+// One full step of one env by its warp.  `term_row` (may be null) receives
+// the pre-reset observation of a done env; `o` returns this lane's share of
+// the observation after the step (after the reset when done).
+__device__ __forceinline__ StepOut env_step(const DevCfg& c, const SimPtrs& p, const EnvConst& k, Env& s,
+                                            uint32_t a, int lane, ObsRegs& o, float* term_row) {
+  // noise of the observation this step produces, drawn before the scan
+  const Noise z = noise_for(k, s.sigma, s.ep_id, s.ep_step + 1u, lane);
+  const bool bad = kinematics(c, s, a);
+  if (bad && lane == 0) atomicOr(p.status, 1u);
+  const bool col = collide_warp(c, k.m, k.rows, k.clr, s.x, s.y, lane);
+  Aux aux;
+  observe(c, k, s, z, lane, o, aux);
+  const float d1sq = fmaf(aux.ddx, aux.ddx, aux.ddy * aux.ddy);
+  const bool arrive = d1sq <= c.goal_r * c.goal_r;
+  const bool trunc = s.ep_step >= (uint32_t)c.t_max;
+  // Eq. 11: 0.3 r_d1 + 0.1 r_d2 + 0.3 r_v + 0.3 r_alpha + 0.1 r_d
+  const Layout& L = k.L;
+  const float d1 = sqrtf(d1sq);
+  const float rd1 = 1.0f - d1 / L.D;
+  const float ex = L.gx - L.sx, ey = L.gy - L.sy;
+  const float px = s.x - L.sx, py = s.y - L.sy;
+  const float cr = ex * py - ey * px;
+  const float t2 = fabsf(cr) / L.D / L.D;
+  const float rd2 = 1.0f - (t2 + t2);
+  const float vmax = c.v_nom * s.cap;
+  const float rv = s.vl > 0.5f * vmax ? 1.0f : 0.0f;
+  const float ra = 1.0f - fabsf(aux.alpha) / kPi;
+  const float rdn = aux.min_range < c.near_dist ? -1.0f : 0.0f;
+  float r = 0.3f * rd1;
+  r = r + 0.1f * rd2;
+  r = r + 0.3f * rv;
+  r = r + 0.3f * ra;
+  r = r + 0.1f * rdn;
+  if (col)
+    r = -10.0f;
+  else if (arrive)
+    r = 75.0f;
+  StepOut out;
+  out.rew = r;
+  out.done = (col ? 1u : 0u) | (arrive ? 2u : 0u) | (trunc ? 4u : 0u);
+  if (out.done) {
+    // AutoReset (Sec. 3.2.5): keep s' for the caller, then a new episode
+    if (term_row) write_obs(term_row, o, c.B, lane);
+    reset_env(c, k, s, s.ep_id + 1u, lane);
+    const Noise z0 = noise_for(k, s.sigma, s.ep_id, 0u, lane);
+    observe(c, k, s, z0, lane, o, aux);
+  }
+  return out;
+}
+
+// Random action of step t for env (uniform over the action table): lane l
+// draws the action of step t0 + l, so that one batch of hashes serves 32 steps.
+__device__ __forceinline__ uint32_t random_action_for(const DevCfg& c, uint64_t akey, uint32_t t) {
+  const uint64_t ha = sm_at(sm_at(akey, (uint64_t)t), 0ull);
+  return (uint32_t)(ha >> 32) % (uint32_t)c.n_actions;
+}
+
+}  // namespace sg

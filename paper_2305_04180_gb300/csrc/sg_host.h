@@ -1,0 +1,31 @@
+// sg_host.h -- host-side objects behind the C handles (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "sg_device.cuh"
+#include "sparrow_gb.h"
+
+struct sg_sim {
+  sg_sim_config cfg;
+  sg::DevCfg dc;
+  int n_maps = 0;
+  int device = 0;
+  long long atlas_words = 0;
+  long long clr_bytes = 0;
+  std::vector<sg::MapDesc> maps_host;
+  uint32_t* atlas = nullptr;
+  uint8_t* clr = nullptr;
+  sg::MapDesc* maps_dev = nullptr;
+  int* env_map_dev = nullptr;
+  int* env_beams_dev = nullptr;
+  float* fstate = nullptr;     // [9][n]
+  uint32_t* ustate = nullptr;  // [4][n]
+  uint32_t* status_dev = nullptr;
+};
+
+sg::SimPtrs sg_sim_ptrs(sg_sim* s);
+long long sg_state_bytes(const sg_sim* s);
+int sg_set_cuda_error(cudaError_t e, const char* what);

@@ -1,0 +1,489 @@
+// sg_sim.cu -- kernels and C entry points of the vectorized Sparrow simulator
+// (paper arxiv 2305.04180, Sec. 3.2).  See include/sparrow_gb.h for the
+// contract of every extern "C" function.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "sg_device.cuh"
+#include "sg_host.h"
+#include "sparrow_gb.h"
+
+using namespace sg;
+
+// ------------------------------------------------------------------ kernels
+
+// Pack one map: warp w of the grid turns 32 cells of a row into one word with
+// a ballot (bit b = cell 32*word + b).  Rows are padded to row_words words.
+__global__ void k_pack_map(const uint8_t* __restrict__ grid, int w, int h, int row_words, uint32_t* __restrict__ out) {
+  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const long long total = (long long)h * row_words;
+  if (gw >= total) return;  // whole warps exit together (gw is warp-uniform)
+  const int cy = (int)(gw / row_words);
+  const int wd = (int)(gw % row_words);
+  const int cx = wd * 32 + lane;
+  const bool occ = cx < w && grid[(long long)cy * w + cx] != 0;
+  const uint32_t word = __ballot_sync(kFull, occ);
+  if (lane == 0) out[gw] = word;
+}
+
+// Clearance map, pass 1: per row, the distance to the nearest occupied cell
+// of the same row (outside counts as occupied), capped at 255.  One thread
+// per row, two sweeps.
+__global__ void k_clr_rows(const uint8_t* __restrict__ grid, int w, int h, uint8_t* __restrict__ g) {
+  const int cy = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cy >= h) return;
+  const uint8_t* row = grid + (long long)cy * w;
+  uint8_t* out = g + (long long)cy * w;
+  int d = 0;  // distance to the last occupied cell on the left (x = -1 is outside)
+  for (int cx = 0; cx < w; ++cx) {
+    d = row[cx] ? 0 : d + 1;
+    out[cx] = (uint8_t)min(d, 255);
+  }
+  d = 0;
+  for (int cx = w - 1; cx >= 0; --cx) {
+    d = row[cx] ? 0 : d + 1;
+    out[cx] = (uint8_t)min((int)out[cx], min(d, 255));
+  }
+}
+
+// Pass 2: Chebyshev distance d(x, y) = min over rows y' of max(g(x, y'), |y - y'|),
+// with the rows above and below the map (outside) at g = 0; capped at 255.
+__global__ void k_clr_cols(const uint8_t* __restrict__ g, int w, int h, uint8_t* __restrict__ clr) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)w * h) return;
+  const int cx = (int)(i % w), cy = (int)(i / w);
+  int best = min(min(cy + 1, h - cy), 255);
+  for (int dd = 0; dd < best; ++dd) {
+    if (cy - dd >= 0) best = min(best, max((int)g[(long long)(cy - dd) * w + cx], dd));
+    if (cy + dd < h) best = min(best, max((int)g[(long long)(cy + dd) * w + cx], dd));
+  }
+  clr[i] = (uint8_t)best;
+}
+
+// Episode 0 of every env; one warp per env.
+__global__ void __launch_bounds__(128) k_reset(const __grid_constant__ DevCfg c, SimPtrs p, float* __restrict__ obs) {
+  const int env = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (env >= c.n_envs) return;
+  const EnvConst k = env_const(c, p, env, lane);
+  Env s;
+  s.t = 0;
+  reset_env(c, k, s, 0u, lane);
+  const Noise z = noise_for(k, s.sigma, s.ep_id, 0u, lane);
+  ObsRegs o;
+  Aux aux;
+  observe(c, k, s, z, lane, o, aux);
+  if (obs) write_obs(obs + (long long)env * c.obs_dim, o, c.B, lane);
+  if (lane == 0) store_env(p, env, s);
+}
+
+// One vectorized step; one warp per env.
+__global__ void __launch_bounds__(128) k_step(const __grid_constant__ DevCfg c, SimPtrs p, const uint8_t* __restrict__ act,
+                                              float* __restrict__ obs, float* __restrict__ rew,
+                                              uint8_t* __restrict__ done, float* __restrict__ term) {
+  const int env = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (env >= c.n_envs) return;
+  const EnvConst k = env_const(c, p, env, lane);
+  Env s = load_env(p, env);
+  ObsRegs o;
+  const StepOut r = env_step(c, p, k, s, (uint32_t)act[env], lane, o,
+                             term ? term + (long long)env * c.obs_dim : nullptr);
+  write_obs(obs + (long long)env * c.obs_dim, o, c.B, lane);
+  if (lane == 0) {
+    rew[env] = r.rew;
+    done[env] = (uint8_t)r.done;
+    store_env(p, env, s);
+  }
+}
+
+// K steps with uniformly random actions drawn on the device; the env stays
+// in registers between steps.  One warp per env.  Per-step outputs are
+// optional: obs_seq [K][n][obs_dim], act/rew/done_seq [K][n].
+__global__ void __launch_bounds__(128) k_rollout_random(const __grid_constant__ DevCfg c, SimPtrs p, int K,
+                                                        float* __restrict__ obs, float* __restrict__ obs_seq,
+                                                        uint8_t* __restrict__ act_seq, float* __restrict__ rew_seq,
+                                                        uint8_t* __restrict__ done_seq) {
+  const int env = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (env >= c.n_envs) return;
+  const EnvConst k = env_const(c, p, env, lane);
+  Env s = load_env(p, env);
+  const uint64_t akey = sm_at(sm_at(c.seed, kStreamAction), (uint64_t)env);
+  ObsRegs o;
+  o.b0 = o.b1 = o.ex = 0.0f;
+  const long long n = c.n_envs;
+  uint32_t abatch = 0;
+  for (int i = 0; i < K; ++i) {
+    if ((i & 31) == 0) abatch = random_action_for(c, akey, s.t + (uint32_t)lane);
+    const uint32_t a = __shfl_sync(kFull, abatch, i & 31);
+    const StepOut r = env_step(c, p, k, s, a, lane, o, nullptr);
+    if (obs_seq) write_obs(obs_seq + ((long long)i * n + env) * c.obs_dim, o, c.B, lane);
+    if (lane == 0) {
+      if (act_seq) act_seq[i * n + env] = (uint8_t)a;
+      if (rew_seq) rew_seq[i * n + env] = r.rew;
+      if (done_seq) done_seq[i * n + env] = (uint8_t)r.done;
+    }
+  }
+  if (obs) write_obs(obs + (long long)env * c.obs_dim, o, c.B, lane);
+  if (lane == 0) store_env(p, env, s);
+}
+
+// ------------------------------------------------------------- host side
+
+namespace {
+thread_local char g_cuda_err[256] = "";
+
+int cuda_fail(cudaError_t e, const char* what) {
+  std::snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", what, cudaGetErrorString(e));
+  return SG_E_CUDA;
+}
+#define SG_CUDA(call)                                           \
+  do {                                                          \
+    cudaError_t e_ = (call);                                    \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);         \
+  } while (0)
+
+constexpr int kWarpsPerBlock = 4;
+
+int grid_for(int n_envs) { return (n_envs + kWarpsPerBlock - 1) / kWarpsPerBlock; }
+
+bool finite_nonneg(float v) { return std::isfinite(v) && v >= 0.0f; }
+}  // namespace
+
+const char* sg_cuda_err_text() { return g_cuda_err; }
+int sg_set_cuda_error(cudaError_t e, const char* what) { return cuda_fail(e, what); }
+
+// Validates the configuration; fills the launch-time copy.
+static int make_devcfg(const sg_sim_config* cfg, DevCfg* dc) {
+  if (cfg->n_envs < 1 || cfg->n_envs > (1 << 24)) return SG_E_INVAL;
+  if (cfg->n_beams < 2 || cfg->n_beams > 64) return SG_E_INVAL;
+  if (cfg->n_actions < 1 || cfg->n_actions > 8) return SG_E_INVAL;
+  if (cfg->t_max < 1) return SG_E_INVAL;
+  if (cfg->delay_lo < 0 || cfg->delay_hi > 2 || cfg->delay_lo > cfg->delay_hi) return SG_E_INVAL;
+  if (!(cfg->range_max > 0.0f) || !(cfg->march_step > 0.0f) || !std::isfinite(cfg->range_max)) return SG_E_INVAL;
+  const float kmaxf = std::floor(cfg->range_max / cfg->march_step);
+  if (!(kmaxf >= 1.0f) || kmaxf > 4096.0f) return SG_E_INVAL;
+  if (!finite_nonneg(cfg->fov) || !finite_nonneg(cfg->robot_radius) || !finite_nonneg(cfg->goal_radius))
+    return SG_E_INVAL;
+  if (!std::isfinite(cfg->near_dist) || !std::isfinite(cfg->start_offset) || !finite_nonneg(cfg->start_jitter))
+    return SG_E_INVAL;
+  const float pairs[][2] = {{cfg->dt_lo, cfg->dt_hi}, {cfg->k_lo, cfg->k_hi}, {cfg->cap_lo, cfg->cap_hi},
+                            {cfg->sigma_lo, cfg->sigma_hi}};
+  for (const auto& pr : pairs)
+    if (!std::isfinite(pr[0]) || !std::isfinite(pr[1]) || pr[0] > pr[1]) return SG_E_INVAL;
+  if (cfg->sigma_lo < 0.0f) return SG_E_INVAL;
+  if (!(cfg->v_nom > 0.0f) || !(cfg->w_nom > 0.0f)) return SG_E_INVAL;
+  std::memset(dc, 0, sizeof(*dc));
+  dc->n_envs = cfg->n_envs;
+  dc->B = cfg->n_beams;
+  dc->obs_dim = cfg->n_beams + 5;
+  dc->n_actions = cfg->n_actions;
+  dc->t_max = cfg->t_max;
+  dc->kmax = (int)kmaxf;
+  dc->delay_lo = cfg->delay_lo;
+  dc->delay_span = cfg->delay_hi - cfg->delay_lo + 1;
+  dc->skip_ok = cfg->march_step <= 1.0f ? 1 : 0;
+  // a point of a cell with clearance c is at least c - 0.5 cells from every
+  // occupied cell centre; keep a margin of one cell above the radius so that
+  // the rounded disc test could not have fired either
+  dc->clr_collide = (int)std::ceil(cfg->robot_radius) + 2;
+  dc->fov = cfg->fov;
+  dc->half_fov = cfg->fov * 0.5f;
+  dc->range_max = cfg->range_max;
+  dc->delta = cfg->march_step;
+  dc->robot_r = cfg->robot_radius;
+  dc->goal_r = cfg->goal_radius;
+  dc->near_dist = cfg->near_dist;
+  dc->start_offset = cfg->start_offset;
+  dc->jitter = cfg->start_jitter;
+  dc->dt_lo = cfg->dt_lo;
+  dc->dt_hi = cfg->dt_hi;
+  dc->k_lo = cfg->k_lo;
+  dc->k_hi = cfg->k_hi;
+  dc->cap_lo = cfg->cap_lo;
+  dc->cap_hi = cfg->cap_hi;
+  dc->sig_lo = cfg->sigma_lo;
+  dc->sig_hi = cfg->sigma_hi;
+  dc->v_nom = cfg->v_nom;
+  dc->w_nom = cfg->w_nom;
+  for (int i = 0; i < 8; ++i) {
+    dc->av[i] = cfg->action_v[i];
+    dc->aw[i] = cfg->action_w[i];
+  }
+  dc->seed = cfg->seed;
+  return SG_OK;
+}
+
+SimPtrs sg_sim_ptrs(sg_sim* s) {
+  SimPtrs p;
+  p.f = s->fstate;
+  p.u = s->ustate;
+  p.atlas = s->atlas;
+  p.clr = s->clr;
+  p.maps = s->maps_dev;
+  p.env_map = s->env_map_dev;
+  p.env_beams = s->env_beams_dev;
+  p.status = s->status_dev;
+  p.n = s->dc.n_envs;
+  p.pad = 0;
+  return p;
+}
+
+static void free_sim(sg_sim* s) {
+  if (!s) return;
+  cudaFree(s->atlas);
+  cudaFree(s->clr);
+  cudaFree(s->maps_dev);
+  cudaFree(s->env_map_dev);
+  cudaFree(s->env_beams_dev);
+  cudaFree(s->fstate);
+  cudaFree(s->ustate);
+  cudaFree(s->status_dev);
+  delete s;
+}
+
+extern "C" int sg_sim_create(const sg_sim_config* cfg, int32_t n_maps, const uint8_t* const* maps_host,
+                             const int32_t* map_w, const int32_t* map_h, const int32_t* env_map,
+                             const int32_t* env_beams, sg_sim_t* out) {
+  if (!cfg || !maps_host || !map_w || !map_h || !env_map || !out) return SG_E_INVAL;
+  if (n_maps < 1) return SG_E_INVAL;
+  *out = nullptr;
+  DevCfg dc;
+  int rc = make_devcfg(cfg, &dc);
+  if (rc) return rc;
+  const int n = cfg->n_envs;
+  std::vector<MapDesc> md((size_t)n_maps);
+  long long words = 0;
+  long long clr_bytes = 0;
+  size_t max_cells = 0;
+  for (int m = 0; m < n_maps; ++m) {
+    if (!maps_host[m] || map_w[m] < 1 || map_h[m] < 1 || map_w[m] > 16384 || map_h[m] > 16384) return SG_E_INVAL;
+    md[m].word_off = words;
+    md[m].w = map_w[m];
+    md[m].h = map_h[m];
+    md[m].row_words = ((map_w[m] + 127) / 128) * 4;  // rows padded to 16 bytes
+    md[m].pad = 0;
+    md[m].clr_off = clr_bytes;
+    words += (long long)md[m].row_words * map_h[m];
+    clr_bytes += (long long)map_w[m] * map_h[m];
+    max_cells = std::max(max_cells, (size_t)map_w[m] * (size_t)map_h[m]);
+  }
+  for (int i = 0; i < n; ++i) {
+    if (env_map[i] < 0 || env_map[i] >= n_maps) return SG_E_INVAL;
+    if (env_beams && (env_beams[i] < 2 || env_beams[i] > cfg->n_beams)) return SG_E_INVAL;
+  }
+  sg_sim* s = new (std::nothrow) sg_sim();
+  if (!s) return SG_E_OOM;
+  s->cfg = *cfg;
+  s->dc = dc;
+  s->n_maps = n_maps;
+  s->maps_host = md;
+  s->atlas_words = words;
+  s->clr_bytes = clr_bytes;
+  cudaGetDevice(&s->device);
+  uint8_t* staging = nullptr;
+  cudaError_t e = cudaSuccess;
+  auto alloc = [&](void** ptr, size_t bytes) {
+    if (e != cudaSuccess) return;
+    e = cudaMalloc(ptr, bytes);
+  };
+  alloc((void**)&s->atlas, (size_t)words * 4);
+  alloc((void**)&s->clr, (size_t)clr_bytes);
+  alloc((void**)&s->maps_dev, sizeof(MapDesc) * n_maps);
+  alloc((void**)&s->env_map_dev, sizeof(int) * n);
+  if (env_beams) alloc((void**)&s->env_beams_dev, sizeof(int) * n);
+  alloc((void**)&s->fstate, sizeof(float) * 9 * (size_t)n);
+  alloc((void**)&s->ustate, sizeof(uint32_t) * 4 * (size_t)n);
+  alloc((void**)&s->status_dev, sizeof(uint32_t));
+  alloc((void**)&staging, max_cells * 2);
+  if (e != cudaSuccess) {
+    cudaFree(staging);
+    free_sim(s);
+    cuda_fail(e, "cudaMalloc");
+    return SG_E_OOM;
+  }
+  // pack every map on the device (synchronous, default stream)
+  for (int m = 0; m < n_maps && e == cudaSuccess; ++m) {
+    const size_t cells = (size_t)map_w[m] * map_h[m];
+    e = cudaMemcpy(staging, maps_host[m], cells, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) break;
+    const long long total_words = (long long)md[m].row_words * map_h[m];
+    const long long threads = total_words * 32;
+    const int blocks = (int)((threads + 255) / 256);
+    k_pack_map<<<blocks, 256>>>(staging, map_w[m], map_h[m], md[m].row_words, s->atlas + md[m].word_off);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) break;
+    k_clr_rows<<<(map_h[m] + 127) / 128, 128>>>(staging, map_w[m], map_h[m], staging + max_cells);
+    k_clr_cols<<<(int)((cells + 255) / 256), 256>>>(staging + max_cells, map_w[m], map_h[m], s->clr + md[m].clr_off);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(s->maps_dev, md.data(), sizeof(MapDesc) * n_maps, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(s->env_map_dev, env_map, sizeof(int) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && env_beams)
+    e = cudaMemcpy(s->env_beams_dev, env_beams, sizeof(int) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(s->fstate, 0, sizeof(float) * 9 * (size_t)n);
+  if (e == cudaSuccess) e = cudaMemset(s->ustate, 0, sizeof(uint32_t) * 4 * (size_t)n);
+  if (e == cudaSuccess) e = cudaMemset(s->status_dev, 0, sizeof(uint32_t));
+  cudaFree(staging);
+  if (e != cudaSuccess) {
+    free_sim(s);
+    return cuda_fail(e, "sg_sim_create");
+  }
+  *out = s;
+  return SG_OK;
+}
+
+extern "C" int sg_sim_destroy(sg_sim_t sim) {
+  if (!sim) return SG_E_INVAL;
+  cudaDeviceSynchronize();
+  free_sim(sim);
+  return SG_OK;
+}
+
+extern "C" int sg_sim_info_get(sg_sim_t sim, sg_sim_info* info) {
+  if (!sim || !info) return SG_E_INVAL;
+  std::memset(info, 0, sizeof(*info));
+  info->n_envs = sim->dc.n_envs;
+  info->n_beams = sim->dc.B;
+  info->obs_dim = sim->dc.obs_dim;
+  info->n_maps = sim->n_maps;
+  info->atlas_words = sim->atlas_words;
+  info->state_bytes = sg_state_bytes(sim);
+  info->device = sim->device;
+  return SG_OK;
+}
+
+long long sg_state_bytes(const sg_sim* s) { return (long long)s->dc.n_envs * (9 * 4 + 4 * 4); }
+
+extern "C" int sg_sim_reset(sg_sim_t sim, uint64_t seed, float* obs_dev, sg_stream_t stream) {
+  if (!sim) return SG_E_INVAL;
+  sim->dc.seed = seed;
+  sim->cfg.seed = seed;
+  k_reset<<<grid_for(sim->dc.n_envs), 32 * kWarpsPerBlock, 0, stream>>>(sim->dc, sg_sim_ptrs(sim), obs_dev);
+  SG_CUDA(cudaGetLastError());
+  return SG_OK;
+}
+
+extern "C" int sg_sim_step(sg_sim_t sim, const uint8_t* act_dev, float* obs_dev, float* rew_dev,
+                           uint8_t* done_dev, float* term_obs_dev, sg_stream_t stream) {
+  if (!sim || !act_dev || !obs_dev || !rew_dev || !done_dev) return SG_E_INVAL;
+  if (((uintptr_t)obs_dev & 3) || ((uintptr_t)rew_dev & 3) || ((uintptr_t)term_obs_dev & 3)) return SG_E_ALIGN;
+  k_step<<<grid_for(sim->dc.n_envs), 32 * kWarpsPerBlock, 0, stream>>>(sim->dc, sg_sim_ptrs(sim), act_dev, obs_dev,
+                                                                        rew_dev, done_dev, term_obs_dev);
+  SG_CUDA(cudaGetLastError());
+  return SG_OK;
+}
+
+// Q-network rollouts live with the network (sg_qnet.cu).
+int sg_rollout_eps_q(sg_sim* sim, int K, sg_qnet* q, const float* eps, sg_replay* rp, float* obs, float* obs_seq,
+                     uint8_t* act_seq, float* rew_seq, uint8_t* done_seq, cudaStream_t stream);
+
+extern "C" int sg_sim_rollout(sg_sim_t sim, int32_t K, int32_t policy, sg_qnet_t qnet, const float* eps_dev,
+                              sg_replay_t replay, float* obs_dev, float* obs_seq_dev, uint8_t* act_seq_dev,
+                              float* rew_seq_dev, uint8_t* done_seq_dev, sg_stream_t stream) {
+  if (!sim || K < 1 || K > (1 << 20)) return SG_E_INVAL;
+  if (((uintptr_t)obs_dev & 3) || ((uintptr_t)obs_seq_dev & 3) || ((uintptr_t)rew_seq_dev & 3)) return SG_E_ALIGN;
+  if (policy == SG_POLICY_RANDOM) {
+    if (replay) return SG_E_INVAL;  // transitions are recorded by the Q-policy rollout
+    k_rollout_random<<<grid_for(sim->dc.n_envs), 32 * kWarpsPerBlock, 0, stream>>>(
+        sim->dc, sg_sim_ptrs(sim), K, obs_dev, obs_seq_dev, act_seq_dev, rew_seq_dev, done_seq_dev);
+    SG_CUDA(cudaGetLastError());
+    return SG_OK;
+  }
+  if (policy == SG_POLICY_EPS_Q) {
+    if (!qnet || !eps_dev) return SG_E_INVAL;
+    return sg_rollout_eps_q(sim, K, qnet, eps_dev, replay, obs_dev, obs_seq_dev, act_seq_dev, rew_seq_dev,
+                            done_seq_dev, stream);
+  }
+  return SG_E_INVAL;
+}
+
+extern "C" int sg_sim_get_state(sg_sim_t sim, void* host_buf, size_t* bytes) {
+  if (!sim || !bytes) return SG_E_INVAL;
+  const size_t need = (size_t)sg_state_bytes(sim);
+  if (!host_buf) {
+    *bytes = need;
+    return SG_OK;
+  }
+  if (*bytes < need) return SG_E_INVAL;
+  const size_t n = (size_t)sim->dc.n_envs;
+  SG_CUDA(cudaDeviceSynchronize());
+  SG_CUDA(cudaMemcpy(host_buf, sim->fstate, 9 * 4 * n, cudaMemcpyDeviceToHost));
+  SG_CUDA(cudaMemcpy((char*)host_buf + 9 * 4 * n, sim->ustate, 4 * 4 * n, cudaMemcpyDeviceToHost));
+  *bytes = need;
+  return SG_OK;
+}
+
+extern "C" int sg_sim_set_state(sg_sim_t sim, const void* host_buf, size_t bytes) {
+  if (!sim || !host_buf) return SG_E_INVAL;
+  const size_t need = (size_t)sg_state_bytes(sim);
+  if (bytes != need) return SG_E_INVAL;
+  const size_t n = (size_t)sim->dc.n_envs;
+  SG_CUDA(cudaDeviceSynchronize());
+  SG_CUDA(cudaMemcpy(sim->fstate, host_buf, 9 * 4 * n, cudaMemcpyHostToDevice));
+  SG_CUDA(cudaMemcpy(sim->ustate, (const char*)host_buf + 9 * 4 * n, 4 * 4 * n, cudaMemcpyHostToDevice));
+  return SG_OK;
+}
+
+extern "C" int sg_sim_get_atlas(sg_sim_t sim, uint32_t* atlas_host, size_t* words, int64_t* offs_host,
+                                int32_t* row_words_host) {
+  if (!sim) return SG_E_INVAL;
+  if (atlas_host) {
+    if (!words || *words < (size_t)sim->atlas_words) return SG_E_INVAL;
+    SG_CUDA(cudaDeviceSynchronize());
+    SG_CUDA(cudaMemcpy(atlas_host, sim->atlas, (size_t)sim->atlas_words * 4, cudaMemcpyDeviceToHost));
+  }
+  if (words) *words = (size_t)sim->atlas_words;
+  for (int m = 0; m < sim->n_maps; ++m) {
+    if (offs_host) offs_host[m] = sim->maps_host[m].word_off;
+    if (row_words_host) row_words_host[m] = sim->maps_host[m].row_words;
+  }
+  return SG_OK;
+}
+
+extern "C" int sg_sim_get_clearance(sg_sim_t sim, uint8_t* host, size_t* bytes, int64_t* offs_host) {
+  if (!sim || !bytes) return SG_E_INVAL;
+  if (host) {
+    if (*bytes < (size_t)sim->clr_bytes) return SG_E_INVAL;
+    SG_CUDA(cudaDeviceSynchronize());
+    SG_CUDA(cudaMemcpy(host, sim->clr, (size_t)sim->clr_bytes, cudaMemcpyDeviceToHost));
+  }
+  *bytes = (size_t)sim->clr_bytes;
+  if (offs_host)
+    for (int m = 0; m < sim->n_maps; ++m) offs_host[m] = sim->maps_host[m].clr_off;
+  return SG_OK;
+}
+
+extern "C" int sg_sim_status(sg_sim_t sim, uint32_t* device_status) {
+  if (!sim || !device_status) return SG_E_INVAL;
+  uint32_t v = 0;
+  SG_CUDA(cudaDeviceSynchronize());
+  SG_CUDA(cudaMemcpy(&v, sim->status_dev, 4, cudaMemcpyDeviceToHost));
+  SG_CUDA(cudaMemset(sim->status_dev, 0, 4));
+  *device_status = v;
+  return v ? SG_E_DEVICE : SG_OK;
+}
+
+extern "C" const char* sg_strerror(int code) {
+  switch (code) {
+    case SG_OK: return "ok";
+    case SG_E_INVAL: return "invalid argument";
+    case SG_E_ALIGN: return "misaligned pointer";
+    case SG_E_OOM: return "out of memory";
+    case SG_E_CUDA: return "CUDA runtime error";
+    case SG_E_DEVICE: return "device reported an error";
+    case SG_E_TIMEOUT: return "device wait timed out";
+    default: return "unknown error";
+  }
+}
+
+extern "C" const char* sg_last_cuda_error(void) { return g_cuda_err; }

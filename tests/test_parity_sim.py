@@ -1,0 +1,278 @@
+"""GPU parity of the simulator against the CPU oracle (through the C ABI).
+
+Bar: against the strict-float32 oracle everything is bit-exact (state, obs,
+rewards, done flags, term obs, atlas).  Against the float64 oracle pose and
+velocity agree within 1e-5 relative and noise-free ranges are equal in
+>= 99.99% of beams, otherwise within one march step.
+"""
+
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle.sim import OracleSim, pack_map
+from tests._helpers import bits, gpu_state_to_oracle, oracle_state_to_gpu
+from workloads import workload
+from workloads.configs import base_params
+from workloads.maps import empty_map, make_map, random_tiny_map
+
+pytestmark = pytest.mark.gpu
+
+
+def _sim(params, maps, env_map, env_beams=None):
+    from paper_2305_04180_gb300 import Sim
+
+    return Sim(params, maps, env_map, env_beams)
+
+
+def _pair(w_or_params, maps=None, env_map=None, env_beams=None):
+    if maps is None:
+        w = w_or_params
+        maps = w.maps()
+        params, env_map, env_beams = w.params, w.env_map, w.env_beams
+    else:
+        params = w_or_params
+    g = _sim(params, maps, env_map, env_beams)
+    o = OracleSim(params, maps, env_map, env_beams, prec="f32")
+    return g, o, maps
+
+
+def _assert_state_equal(g, o, t):
+    f, u = g.get_state()
+    of, ou, ob = o.state()
+    gf, gu = oracle_state_to_gpu(of, ou, ob, t)
+    assert np.array_equal(bits(f), bits(gf)), np.argwhere(bits(f) != bits(gf))[:5]
+    assert np.array_equal(u, gu), np.argwhere(u != gu)[:5]
+
+
+def test_atlas_bit_exact():
+    maps = [make_map(1), make_map(2, 128), make_map(3, 200, 77), random_tiny_map(4, 33, 5, 0.5),
+            random_tiny_map(5, 1, 1, 1.0), make_map(6, 1024)]
+    g = _sim(base_params(), maps, np.arange(6, dtype=np.int32) % 6)
+    atlas, offs, rw = g.atlas()
+    for m, grid in enumerate(maps):
+        h = grid.shape[0]
+        ref = pack_map(grid, int(rw[m]))
+        got = atlas[offs[m]: offs[m] + h * rw[m]].reshape(h, rw[m])
+        assert np.array_equal(got, ref)
+        assert rw[m] % 4 == 0  # rows are 16-byte aligned
+
+
+@pytest.mark.parametrize("name,n", [("plain16", 16), ("dr1024", 1024), ("dr1024", 37)])
+def test_reset_bit_exact(name, n):
+    g, o, _ = _pair(workload(name, n_envs=n))
+    obs = g.reset().cpu().numpy()
+    oobs = o.reset()
+    assert np.array_equal(bits(obs), bits(oobs))
+    _assert_state_equal(g, o, 0)
+
+
+def _teacher_forced(g, o, steps, seed=0, act_fn=None):
+    """Every step both sides start from the same state bits and take the same
+    actions; every output must match bit for bit."""
+    n = g.n
+    obs = g.reset()
+    o.reset()
+    term = torch.full((n, g.obs_dim), float("nan"), device="cuda")
+    rng = np.random.default_rng(seed)
+    checked = 0
+    for t in range(steps):
+        a = rng.integers(0, 5, size=n).astype(np.uint8) if act_fn is None else act_fn(t)
+        f, u = g.get_state()
+        o.set_state(*gpu_state_to_oracle(f, u))
+        at = torch.from_numpy(a).cuda()
+        obs, rew, done = g.step(at, term_obs=term)
+        oobs, orew, odone, oterm = o.step(a)
+        d = done.cpu().numpy()
+        assert np.array_equal(d, odone), (t, np.argwhere(d != odone)[:5])
+        assert np.array_equal(bits(rew.cpu().numpy()), bits(orew)), t
+        assert np.array_equal(bits(obs.cpu().numpy()), bits(oobs)), t
+        if d.any():
+            tg = term.cpu().numpy()[d != 0]
+            assert np.array_equal(bits(tg), bits(oterm[d != 0])), t
+        _assert_state_equal(g, o, t + 1)
+        checked += n
+    return checked
+
+
+def test_step_teacher_forced_plain16():
+    g, o, _ = _pair(workload("plain16"))
+    assert _teacher_forced(g, o, 400) == 6400
+
+
+def test_step_teacher_forced_domain_randomised():
+    """1024 envs over 32 maps with every randomisation on (delay, K, cap,
+    noise, control interval): 200 steps = 204,800 env-steps."""
+    g, o, _ = _pair(workload("dr1024"))
+    assert _teacher_forced(g, o, 200, seed=1) == 204800
+
+
+def test_step_uneven_beams_and_ragged_batch():
+    """Per-env beam counts 2..64 on mixed map sizes, N not a multiple of the
+    envs per block."""
+    p = base_params(n_beams=64, **{k: v for k, v in workload("dr1024").params.items() if k.endswith(("_lo", "_hi"))})
+    maps = [make_map(11, 128), make_map(12, 366), make_map(13, 512), make_map(14, 256, 300)]
+    n = 29
+    rng = np.random.default_rng(2)
+    env_map = rng.integers(0, 4, n).astype(np.int32)
+    beams = rng.choice([2, 3, 16, 31, 32, 33, 64], n).astype(np.int32)
+    g, o, _ = _pair(p, maps, env_map, beams)
+    _teacher_forced(g, o, 150, seed=3)
+
+
+def test_step_degenerate_cases():
+    """N = 1; a map smaller than the start offset (the robot starts outside
+    and collides every step); a 1x1 map; a map with no obstacle and no
+    border; the out-of-range action index sets the device status bit."""
+    p = base_params()
+    for maps in ([random_tiny_map(7, 20, 20, 0.1)], [np.ones((1, 1), np.uint8)], [empty_map(400)]):
+        g, o, _ = _pair(p, maps, np.zeros(1, np.int32))
+        _teacher_forced(g, o, 30, seed=4)
+        assert g.status() == 0
+    g, o, _ = _pair(p, [make_map(1)], np.zeros(3, np.int32))
+    bad = np.array([0, 7, 255], np.uint8)
+    _teacher_forced(g, o, 5, act_fn=lambda t: bad)
+    assert g.status() == 1
+    assert g.status() == 0  # reading clears it
+
+
+def test_rollout_random_free_running_bit_exact():
+    """1000 free-running steps with on-device random actions: every step's
+    action, reward, done flags and observation, and the final state, equal
+    the oracle's."""
+    w = workload("plain16")
+    g, o, _ = _pair(w)
+    g.reset()
+    o.reset()
+    K = 1000
+    n = g.n
+    obs = g.new_obs()
+    obs_seq = torch.empty((K, n, g.obs_dim), dtype=torch.float32, device="cuda")
+    act = torch.empty((K, n), dtype=torch.uint8, device="cuda")
+    rew = torch.empty((K, n), dtype=torch.float32, device="cuda")
+    done = torch.empty((K, n), dtype=torch.uint8, device="cuda")
+    g.rollout(K, obs=obs, obs_seq=obs_seq, act_seq=act, rew_seq=rew, done_seq=done)
+    act, rew, done, obs_seq = act.cpu().numpy(), rew.cpu().numpy(), done.cpu().numpy(), obs_seq.cpu().numpy()
+    ndone = 0
+    for k in range(K):
+        a = o.random_actions(k)
+        assert np.array_equal(act[k], a), k
+        oobs, orew, odone, _ = o.step(a)
+        assert np.array_equal(done[k], odone), k
+        assert np.array_equal(bits(rew[k]), bits(orew)), k
+        assert np.array_equal(bits(obs_seq[k]), bits(oobs)), k
+        ndone += int((odone != 0).sum())
+    assert np.array_equal(bits(obs.cpu().numpy()), bits(oobs))
+    _assert_state_equal(g, o, K)
+    assert ndone > 100  # episodes did end and reset
+
+
+def test_rollout_continues_across_calls_and_matches_steps():
+    """Two rollouts of K/2 equal one of K; state and RNG counters persist."""
+    w = workload("dr1024", n_envs=64)
+    maps = w.maps()
+    a = _sim(w.params, maps, w.env_map)
+    b = _sim(w.params, maps, w.env_map)
+    a.reset()
+    b.reset()
+    ra = torch.empty((100, 64), device="cuda")
+    rb = torch.empty((100, 64), device="cuda")
+    a.rollout(100, rew_seq=ra)
+    b.rollout(50, rew_seq=rb[:50])
+    b.rollout(50, rew_seq=rb[50:])
+    assert torch.equal(ra, rb)
+    fa, ua = a.get_state()
+    fb, ub = b.get_state()
+    assert np.array_equal(bits(fa), bits(fb)) and np.array_equal(ua, ub)
+
+
+def test_rollout_full_size_sampled_against_oracle():
+    """The 1024-env, 32-map domain-randomised workload in the launch
+    configuration the benchmark times: 300 steps on the GPU, then a sample of
+    envs replayed one by one on the oracle from the same start."""
+    w = workload("dr1024")
+    maps = w.maps()
+    g = _sim(w.params, maps, w.env_map)
+    g.reset()
+    K = 300
+    rew = torch.empty((K, g.n), device="cuda")
+    done = torch.empty((K, g.n), dtype=torch.uint8, device="cuda")
+    g.rollout(K, rew_seq=rew, done_seq=done)
+    rew = rew.cpu().numpy()
+    done = done.cpu().numpy()
+    f, u = g.get_state()
+    o = OracleSim(w.params, maps, w.env_map, prec="f32")
+    for i in [0, 1, 31, 32, 500, 777, 1023]:
+        o.reset_env(i, 0)
+        for k in range(K):
+            _, orew, odone, _ = o.step_one(i, o.random_action(i, k))
+            assert odone == done[k, i] and bits(np.float32(orew)) == bits(rew[k, i]), (i, k)
+        assert np.array_equal(bits(o.f[:, i]), bits(f[:, i]))
+        assert np.array_equal(o.u[:, i], u[:2, i])
+
+
+def test_against_float64_oracle_tolerances():
+    """Teacher forced against the float64 oracle (noise off so that ranges
+    are comparable): pose/velocity within 1e-5 relative; ranges equal in
+    >= 99.99% of beams and otherwise one march step apart; discrete flags
+    equal wherever they are not decided within float rounding."""
+    p = dict(workload("dr1024").params, sigma_lo=0.0, sigma_hi=0.0)
+    maps = [make_map(s) for s in range(1, 33)]
+    env_map = (np.arange(1024) % 32).astype(np.int32)
+    g = _sim(p, maps, env_map)
+    o = OracleSim(p, maps, env_map, prec="f64")
+    g.reset()
+    rng = np.random.default_rng(8)
+    tot = diff = 0
+    for t in range(60):
+        f, u = g.get_state()
+        of, ou, ob = gpu_state_to_oracle(f, u)
+        o.set_state(of.astype(np.float64), ou, ob)
+        a = rng.integers(0, 5, size=1024).astype(np.uint8)
+        obs, rew, done = g.step(torch.from_numpy(a).cuda())
+        oobs, orew, odone, _ = o.step(a)
+        d = done.cpu().numpy()
+        live = (d == 0) & (odone == 0)
+        f2, _ = g.get_state()
+        rel = np.abs(f2[:5, live] - o.f[:5, live]) / np.maximum(1.0, np.abs(o.f[:5, live]))
+        assert rel.max() <= 1e-5
+        gr = np.rint(obs.cpu().numpy()[live, :32] * 100.0)
+        orr = np.rint(oobs[live, :32] * 100.0)
+        dd = np.abs(gr - orr)
+        assert dd.max() <= 1.0
+        tot += dd.size
+        diff += int((dd > 0).sum())
+        assert (d != odone).mean() <= 1e-3
+    assert diff / tot <= 1e-4, (diff, tot)
+
+
+def test_clearance_matches_chessboard_distance_transform():
+    """The march's clearance map equals scipy's chessboard distance transform
+    of the free cells, with the outside of the map counted as occupied and
+    values capped at 255."""
+    ndimage = pytest.importorskip("scipy.ndimage")
+    maps = [make_map(1), make_map(2, 128), make_map(3, 200, 77), random_tiny_map(4, 33, 5, 0.5),
+            np.ones((1, 1), np.uint8), empty_map(700), empty_map(9, 600)]
+    g = _sim(base_params(), maps, np.arange(len(maps), dtype=np.int32))
+    clr, offs = g.clearance()
+    for m, grid in enumerate(maps):
+        h, w = grid.shape
+        pad = np.ones((h + 2, w + 2), np.uint8)
+        pad[1:-1, 1:-1] = grid != 0
+        ref = ndimage.distance_transform_cdt(pad == 0, metric="chessboard")[1:-1, 1:-1]
+        ref = np.minimum(ref, 255).astype(np.uint8)
+        got = clr[offs[m]: offs[m] + h * w].reshape(h, w)
+        assert np.array_equal(got, ref), m
+
+
+@pytest.mark.parametrize("delta,rmax", [(0.5, 60.0), (1.5, 120.0), (1.0, 250.0)])
+def test_step_other_march_steps(delta, rmax):
+    """Sample spacing below one cell (clearance skipping on), above one cell
+    (skipping off), and a range beyond the clearance cap."""
+    p = dict(workload("dr1024").params, march_step=delta, range_max=rmax)
+    maps = [make_map(s) for s in range(1, 5)] + [empty_map(600)]
+    env_map = (np.arange(40) % 5).astype(np.int32)
+    g, o, _ = _pair(p, maps, env_map)
+    _teacher_forced(g, o, 60, seed=5)
