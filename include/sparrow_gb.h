@@ -226,6 +226,79 @@ int sg_sim_get_clearance(sg_sim_t sim, uint8_t* host, size_t* bytes, int64_t* of
  */
 int sg_sim_status(sg_sim_t sim, uint32_t* device_status);
 
+/* ---------------------------------------------------------------------- */
+/* Learned part: dueling Q-network, replay ring, TD learner                */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * Dueling Q-network in -> 256 -> 256 -> (1 value + 5 advantages), ReLU,
+ * Q = V + A - mean(A) (the dueling architecture the paper cites in Sec. 2;
+ * 5 discrete actions of Sec. 4.3.1).  Inference and learning run on the
+ * tensor cores with BF16 weights/activations and FP32 accumulation; FP32
+ * master weights, a target copy and Adam moments stay on the device.
+ *   n_in       input width = the simulator's obs_dim, in [1, 69].
+ *   max_batch  largest sg_td_train_step batch, in [1, 65536] (sizes the
+ *              learner's scratch buffers).
+ *   seed       parameters start uniform in +-1/sqrt(fan_in), drawn from the
+ *              counter RNG with this seed; the target copy equals them.
+ * Flat parameter order (set/get): W1[256][n_in], b1[256], W2[256][256],
+ * b2[256], W3[6][256], b3[6]; row 0 of W3/b3 is the value head.
+ * Synchronous.
+ */
+int sg_qnet_create(int32_t n_in, int32_t max_batch, uint64_t seed, sg_qnet_t* out);
+int sg_qnet_destroy(sg_qnet_t q);
+/* Number of parameters (77,062 for n_in = 37). */
+int sg_qnet_num_params(sg_qnet_t q, int64_t* n);
+/* Copy parameters from / to host floats; which: 0 online, 1 target, 2 both
+ * (set only).  Setting rebuilds the BF16 copies.  Synchronous. */
+int sg_qnet_set_params(sg_qnet_t q, const float* host, int64_t n, int32_t which);
+int sg_qnet_get_params(sg_qnet_t q, float* host, int64_t n, int32_t which);
+/* Adam first / second moments (either pointer may be NULL) and the number of
+ * optimiser steps taken.  Synchronous. */
+int sg_qnet_get_optimizer(sg_qnet_t q, float* m_host, float* v_host, int64_t n, uint64_t* steps);
+
+/*
+ * Batched inference: q_dev[M][5] = Q(obs_dev[M][n_in]) with the online
+ * network (the same tensor-core path the fused rollout uses).
+ */
+int sg_qnet_forward(sg_qnet_t q, const float* obs_dev, int32_t M, float* q_dev, sg_stream_t stream);
+
+/*
+ * Device replay ring (Alg. 1 step 5 adds one batch of N transitions per
+ * vectorized step; Alg. 2 step 1 samples a mini-batch).  Entry
+ * e = slot * n_envs + env, slot = (step index) mod slots_per_env; capacity =
+ * slots_per_env * n_envs transitions of (s, a, r, s', terminal) with s, s'
+ * float[obs_dim], terminal = collided or arrived.  Synchronous.
+ */
+int sg_replay_create(int32_t slots_per_env, int32_t n_envs, int32_t obs_dim, sg_replay_t* out);
+int sg_replay_destroy(sg_replay_t r);
+/* Capacity, vectorized steps recorded so far (synchronous read) and the
+ * device arrays (s, s2: [cap][obs_dim] float; a, term: [cap] uint8;
+ * r: [cap] float).  Any output may be NULL. */
+int sg_replay_info(sg_replay_t r, int64_t* capacity, uint64_t* steps_recorded, void** s_dev, void** s2_dev,
+                   void** a_dev, void** r_dev, void** term_dev);
+
+/* Copy ring entries [first, first + count) to host arrays (any may be NULL).
+ * Synchronous. */
+int sg_replay_read(sg_replay_t r, int64_t first, int64_t count, float* s_host, float* s2_host, uint8_t* a_host,
+                   float* r_host, uint8_t* term_host);
+
+/*
+ * One optimisation step of the learner (Alg. 2 steps 1-2 with DDQN): sample
+ * `batch` ring entries uniformly from those written (counter RNG keyed by
+ * seed and the optimiser step count), y = r + gamma (1 - terminal)
+ * Q_target(s', argmax_a Q_online(s', a)), loss = mean Huber(Q(s, a) - y)
+ * (delta 1), gradient by backpropagation, Adam (beta 0.9 / 0.999, eps 1e-8)
+ * with learning rate lr; when the step count reaches a multiple of
+ * target_every (> 0) the target network takes the online weights.
+ *   lr = 0      computes loss and gradient only (no update, step count kept).
+ *   loss_dev    NULL or 1 float: the batch loss.
+ *   grad_dev    NULL or num_params floats: the summed gradient.
+ * The replay's obs_dim must equal n_in; batch in [1, max_batch].
+ */
+int sg_td_train_step(sg_qnet_t q, sg_replay_t replay, int32_t batch, float gamma, float lr, int32_t target_every,
+                     uint64_t seed, float* loss_dev, float* grad_dev, sg_stream_t stream);
+
 /* Human-readable name of an SG_* return code. */
 const char* sg_strerror(int code);
 

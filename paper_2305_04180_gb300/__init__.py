@@ -6,6 +6,7 @@ This package is its Python binding: it marshals arguments, uses PyTorch only
 for device memory and streams, and has no CPU fallback.
 """
 
+from .qnet import QNet, Replay
 from .sim import Sim, make_config
 
-__all__ = ["Sim", "make_config"]
+__all__ = ["Sim", "make_config", "QNet", "Replay"]

@@ -1,9 +1,958 @@
-// sg_qnet.cu -- dueling Q-network, fused eps-greedy rollout, replay ring.
+// sg_qnet.cu -- the learned part: dueling Q-network (Sec. 2 "Dueling DQN",
+// Sec. 4.3.1 discrete actions), the VEM eps-greedy rollout with the network
+// fused into the simulator loop (Sec. 3.1.1, Alg. 1), the device replay ring
+// (Alg. 1 step 5, Alg. 2 step 1) and the double-DQN learner with Adam
+// (Alg. 2 step 2; appendix hyperparameter table).
+//
+// Network: in -> 256 -> 256 -> 6 (value + 5 advantages), ReLU,
+// Q = V + A - mean(A).  Weights are BF16 on the tensor cores with FP32
+// accumulation; FP32 master weights, Adam moments and a target copy live on
+// the device.  Flat parameter order (sg_qnet_set/get_params):
+// W1[256][in] b1[256] W2[256][256] b2[256] W3[6][256] b3[6].
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "sg_device.cuh"
 #include "sg_host.h"
+#include "sg_mma.cuh"
+#include "sparrow_gb.h"
+
+using namespace sg;
+
+namespace {
+
+constexpr int kHid = 256;
+constexpr int kLdh = kHid + 8;  // padded row of a 256-wide BF16 matrix
+constexpr int kOut = 6;
+constexpr int kOutPad = 8;
+constexpr int kTile = 16;       // envs / samples per CTA = warps per CTA
+constexpr int kThreads = kTile * 32;
+constexpr uint32_t kStreamSample = 4;
+constexpr uint32_t kStreamInit = 5;
+
+// Byte layout of the BF16 weight image (identical in global and shared memory).
+struct ImgLayout {
+  int n_in, k1, ld1;   // input width, padded to 16, row stride
+  int w1, w2, w3, b1, b2, b3, bytes;
+};
+
+ImgLayout img_layout(int n_in) {
+  ImgLayout L;
+  L.n_in = n_in;
+  L.k1 = (n_in + 15) / 16 * 16;
+  L.ld1 = L.k1 + 8;
+  L.w1 = 0;
+  L.w2 = L.w1 + kHid * L.ld1 * 2;
+  L.w3 = L.w2 + kHid * kLdh * 2;
+  L.b1 = L.w3 + kOutPad * kLdh * 2;
+  L.b2 = L.b1 + kHid * 4;
+  L.b3 = L.b2 + kHid * 4;
+  L.bytes = (L.b3 + kOutPad * 4 + 15) / 16 * 16;
+  return L;
+}
+
+// Offsets of the flat FP32 parameter vector.
+struct ParamLayout {
+  int w1, b1, w2, b2, w3, b3, total;
+};
+ParamLayout param_layout(int n_in) {
+  ParamLayout P;
+  P.w1 = 0;
+  P.b1 = P.w1 + kHid * n_in;
+  P.w2 = P.b1 + kHid;
+  P.b2 = P.w2 + kHid * kHid;
+  P.w3 = P.b2 + kHid;
+  P.b3 = P.w3 + kOut * kHid;
+  P.total = P.b3 + kOut;
+  return P;
+}
+
+}  // namespace
+
+// Device view of a replay ring: slot-major SoA, entry e = slot * n_envs + env.
+struct ReplayDev {
+  float* s;              // [cap][obs_dim]
+  float* s2;             // [cap][obs_dim]
+  uint8_t* a;            // [cap]
+  float* r;              // [cap]
+  uint8_t* term;         // [cap] collided or arrived
+  unsigned long long* steps;  // vectorized steps recorded so far
+  int slots, n_envs, obs_dim, pad;
+};
+
+struct sg_replay {
+  ReplayDev d;
+  long long cap = 0;
+  int device = 0;
+};
+
+struct sg_qnet {
+  int n_in = 0;
+  int device = 0;
+  ImgLayout IL;
+  ParamLayout PL;
+  float* master = nullptr;  // [P]
+  float* target = nullptr;  // [P]
+  float* adam_m = nullptr;
+  float* adam_v = nullptr;
+  uint8_t* img = nullptr;    // online BF16 image
+  uint8_t* img_t = nullptr;  // target BF16 image
+  unsigned long long* step = nullptr;  // optimiser steps taken (device)
+  // learner scratch, sized for max_batch
+  int max_batch = 0;
+  float* partial = nullptr;  // [max_batch / kTile][P + 1] (last entry: loss)
+  float* y = nullptr;        // [max_batch] TD targets
+  int* idx = nullptr;        // [max_batch] sampled ring entries
+};
+
+// --------------------------------------------------------------- kernels
+
+// Image entries from the FP32 parameters: W1/W2/W3 rounded to BF16 into the
+// padded layout (pad entries zero), biases copied.
+__global__ void k_build_image(const float* __restrict__ th, uint8_t* __restrict__ img, ImgLayout L, ParamLayout P) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  bf16* W1 = reinterpret_cast<bf16*>(img + L.w1);
+  bf16* W2 = reinterpret_cast<bf16*>(img + L.w2);
+  bf16* W3 = reinterpret_cast<bf16*>(img + L.w3);
+  float* b1 = reinterpret_cast<float*>(img + L.b1);
+  float* b2 = reinterpret_cast<float*>(img + L.b2);
+  float* b3 = reinterpret_cast<float*>(img + L.b3);
+  const int n1 = kHid * L.ld1, n2 = kHid * kLdh, n3 = kOutPad * kLdh;
+  if (i < n1) {
+    const int r = i / L.ld1, k = i % L.ld1;
+    W1[i] = __float2bfloat16_rn(k < L.n_in ? th[P.w1 + r * L.n_in + k] : 0.0f);
+  } else if (i < n1 + n2) {
+    const int j = i - n1, r = j / kLdh, k = j % kLdh;
+    W2[j] = __float2bfloat16_rn(k < kHid ? th[P.w2 + r * kHid + k] : 0.0f);
+  } else if (i < n1 + n2 + n3) {
+    const int j = i - n1 - n2, r = j / kLdh, k = j % kLdh;
+    W3[j] = __float2bfloat16_rn(r < kOut && k < kHid ? th[P.w3 + r * kHid + k] : 0.0f);
+  } else if (i < n1 + n2 + n3 + kHid) {
+    const int j = i - n1 - n2 - n3;
+    b1[j] = th[P.b1 + j];
+  } else if (i < n1 + n2 + n3 + 2 * kHid) {
+    const int j = i - n1 - n2 - n3 - kHid;
+    b2[j] = th[P.b2 + j];
+  } else if (i < n1 + n2 + n3 + 2 * kHid + kOutPad) {
+    const int j = i - n1 - n2 - n3 - 2 * kHid;
+    b3[j] = j < kOut ? th[P.b3 + j] : 0.0f;
+  }
+}
+
+static int image_elems(const ImgLayout& L) { return kHid * L.ld1 + kHid * kLdh + kOutPad * kLdh + 2 * kHid + kOutPad; }
+
+// Seeded uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) initialisation.
+__global__ void k_init_params(float* __restrict__ th, ParamLayout P, int n_in, unsigned long long seed) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P.total) return;
+  const float fan = i < P.w2 ? (float)n_in : (float)kHid;
+  const float bound = 1.0f / sqrtf(fan);
+  const float u = u24_hi(sm_at(sm_at(sm_at(seed, kStreamInit), 0ull), (uint64_t)i));
+  th[i] = -bound + u * (bound + bound);
+}
+
+// Copy the image into shared memory (16-byte vectors).
+__device__ __forceinline__ void stage_image(uint8_t* dst, const uint8_t* __restrict__ src, int bytes) {
+  const int4* s = reinterpret_cast<const int4*>(src);
+  int4* d = reinterpret_cast<int4*>(dst);
+  for (int i = threadIdx.x; i < bytes / 16; i += blockDim.x) d[i] = __ldg(s + i);
+}
+
+// Pointers into a shared-memory copy of the image.
+struct QW {
+  const bf16* W1;
+  const bf16* W2;
+  const bf16* W3;
+  const float* b1;
+  const float* b2;
+  const float* b3;
+  int k1, ld1;
+};
+__device__ __forceinline__ QW qw_at(const uint8_t* base, const ImgLayout& L) {
+  QW w;
+  w.W1 = reinterpret_cast<const bf16*>(base + L.w1);
+  w.W2 = reinterpret_cast<const bf16*>(base + L.w2);
+  w.W3 = reinterpret_cast<const bf16*>(base + L.w3);
+  w.b1 = reinterpret_cast<const float*>(base + L.b1);
+  w.b2 = reinterpret_cast<const float*>(base + L.b2);
+  w.b3 = reinterpret_cast<const float*>(base + L.b3);
+  w.k1 = L.k1;
+  w.ld1 = L.ld1;
+  return w;
+}
+
+// One hidden layer for 16 rows: Hout[16][256] = bf16(ReLU(Xin * W^T + b)).
+// Warp w computes output columns [8w, 8w+8) and [8w+128, 8w+136).
+__device__ __forceinline__ void hidden_layer(const bf16* Xin, int ldx, int kdim, const bf16* W, int ldw,
+                                             const float* b, bf16* Hout, int warp, int lane, float* zout) {
+  const int g = lane >> 2, q = lane & 3;
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    const int n0 = 8 * warp + 128 * half;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int k0 = 0; k0 < kdim; k0 += 16) {
+      uint32_t a[4], b0, b1;
+      load_a_row(a, Xin, ldx, 0, k0, lane);
+      load_b_col(b0, b1, W, ldw, k0, n0, lane);
+      mma_bf16(acc, a, b0, b1);
+    }
+    const int n = n0 + 2 * q;
+    const float z0 = acc[0] + b[n], z1 = acc[1] + b[n + 1];
+    const float z2 = acc[2] + b[n], z3 = acc[3] + b[n + 1];
+    if (zout) {  // pre-activation signs for the backward pass (kept as values)
+      zout[g * kHid + n] = z0;
+      zout[g * kHid + n + 1] = z1;
+      zout[(g + 8) * kHid + n] = z2;
+      zout[(g + 8) * kHid + n + 1] = z3;
+    }
+    *reinterpret_cast<uint32_t*>(Hout + g * kLdh + n) = pack_bf16x2(fmaxf(z0, 0.f), fmaxf(z1, 0.f));
+    *reinterpret_cast<uint32_t*>(Hout + (g + 8) * kLdh + n) = pack_bf16x2(fmaxf(z2, 0.f), fmaxf(z3, 0.f));
+  }
+}
+
+// Head for 16 rows by warp 0: O[16][8] = H2 * W3^T + b3 (FP32), two
+// accumulator chains (even / odd k-steps) summed in a fixed order.
+__device__ __forceinline__ void head_layer(const bf16* H2, const QW& w, float* O, int lane) {
+  const int g = lane >> 2, q = lane & 3;
+  float acc0[4] = {0.f, 0.f, 0.f, 0.f}, acc1[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int k0 = 0; k0 < kHid; k0 += 32) {
+    uint32_t a[4], b0, b1;
+    load_a_row(a, H2, kLdh, 0, k0, lane);
+    load_b_col(b0, b1, w.W3, kLdh, k0, 0, lane);
+    mma_bf16(acc0, a, b0, b1);
+    load_a_row(a, H2, kLdh, 0, k0 + 16, lane);
+    load_b_col(b0, b1, w.W3, kLdh, k0 + 16, 0, lane);
+    mma_bf16(acc1, a, b0, b1);
+  }
+  const int n = 2 * q;
+  O[g * kOutPad + n] = (acc0[0] + acc1[0]) + w.b3[n];
+  O[g * kOutPad + n + 1] = (acc0[1] + acc1[1]) + w.b3[n + 1];
+  O[(g + 8) * kOutPad + n] = (acc0[2] + acc1[2]) + w.b3[n];
+  O[(g + 8) * kOutPad + n + 1] = (acc0[3] + acc1[3]) + w.b3[n + 1];
+}
+
+// Full forward of a 16-row tile (all 16 warps; contains block barriers).
+__device__ __forceinline__ void mlp_tile(const QW& w, const bf16* X, bf16* H1, bf16* H2, float* O, int warp,
+                                         int lane, float* z1 = nullptr, float* z2 = nullptr) {
+  hidden_layer(X, w.ld1, w.k1, w.W1, w.ld1, w.b1, H1, warp, lane, z1);
+  __syncthreads();
+  hidden_layer(H1, kLdh, kHid, w.W2, kLdh, w.b2, H2, warp, lane, z2);
+  __syncthreads();
+  if (warp == 0) head_layer(H2, w, O, lane);
+  __syncthreads();
+}
+
+// Dueling combine and greedy action of one row of head outputs:
+// Q_a = (V + A_a) - mean(A), argmax with the lowest index on ties.
+__device__ __forceinline__ uint32_t greedy_action(const float* o, float* qv = nullptr) {
+  const float V = o[0];
+  const float meanA = ((((o[1] + o[2]) + o[3]) + o[4]) + o[5]) / 5.0f;
+  uint32_t best = 0;
+  float bq = (V + o[1]) - meanA;
+  if (qv) qv[0] = bq;
+#pragma unroll
+  for (int a = 1; a < kOut - 1; ++a) {
+    const float qa = (V + o[1 + a]) - meanA;
+    if (qv) qv[a] = qa;
+    if (qa > bq) {
+      bq = qa;
+      best = (uint32_t)a;
+    }
+  }
+  return best;
+}
+
+// This warp's observation row (lane share `o`) into a BF16 tile row.
+__device__ __forceinline__ void obs_to_tile(bf16* row, const ObsRegs& o, int B, int lane) {
+  if (lane < B) row[lane] = __float2bfloat16_rn(o.b0);
+  if (lane + 32 < B) row[lane + 32] = __float2bfloat16_rn(o.b1);
+  if (lane < 5) row[B + lane] = __float2bfloat16_rn(o.ex);
+}
+
+// Standalone batched inference: Q[M][5] of obs[M][n_in].  16 rows per CTA.
+__global__ void __launch_bounds__(kThreads, 1) k_qnet_forward(const uint8_t* __restrict__ img, ImgLayout L,
+                                                              const float* __restrict__ obs, int M,
+                                                              float* __restrict__ qout) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  uint8_t* sw = smem;
+  bf16* X = reinterpret_cast<bf16*>(smem + L.bytes);
+  bf16* H1 = X + kTile * L.ld1;
+  bf16* H2 = H1 + kTile * kLdh;
+  float* O = reinterpret_cast<float*>(H2 + kTile * kLdh);
+  stage_image(sw, img, L.bytes);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * kTile + warp;
+  for (int k = lane; k < L.ld1; k += 32) {
+    const float v = (row < M && k < L.n_in) ? obs[(long long)row * L.n_in + k] : 0.0f;
+    X[warp * L.ld1 + k] = __float2bfloat16_rn(v);
+  }
+  __syncthreads();
+  const QW w = qw_at(sw, L);
+  mlp_tile(w, X, H1, H2, O, warp, lane);
+  if (row < M && lane == 0) {
+    float qv[5];
+    greedy_action(O + warp * kOutPad, qv);
+    for (int a = 0; a < 5; ++a) qout[(long long)row * 5 + a] = qv[a];
+  }
+}
+
+// VEM eps-greedy rollout with the network fused in: per step, the 16 envs of
+// a CTA write their observations to a BF16 tile, the tile goes through the
+// network on the tensor cores, every env takes argmax Q or (with probability
+// eps_i) the random action, then steps; the transition is appended to the
+// replay ring.  One warp per env, 16 envs per CTA.
+__global__ void __launch_bounds__(kThreads, 1)
+    k_rollout_q(const __grid_constant__ DevCfg c, SimPtrs p, const uint8_t* __restrict__ img, ImgLayout L, int K,
+                const float* __restrict__ eps, ReplayDev rp, int use_replay, float* __restrict__ obs_out,
+                float* __restrict__ obs_seq, uint8_t* __restrict__ act_seq, float* __restrict__ rew_seq,
+                uint8_t* __restrict__ done_seq) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  uint8_t* sw = smem;
+  bf16* X = reinterpret_cast<bf16*>(smem + L.bytes);
+  bf16* H1 = X + kTile * L.ld1;
+  bf16* H2 = H1 + kTile * kLdh;
+  float* O = reinterpret_cast<float*>(H2 + kTile * kLdh);
+  stage_image(sw, img, L.bytes);
+  for (int i = threadIdx.x; i < kTile * L.ld1; i += blockDim.x) X[i] = __float2bfloat16_rn(0.0f);
+  const QW w = qw_at(sw, L);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int env = blockIdx.x * kTile + warp;
+  const bool live = env < c.n_envs;
+  const long long n = c.n_envs;
+  EnvConst k;
+  Env s;
+  ObsRegs o;
+  o.b0 = o.b1 = o.ex = 0.0f;
+  float eps_i = 0.0f;
+  uint64_t akey = 0;
+  if (live) {
+    k = env_const(c, p, env, lane);
+    s = load_env(p, env);
+    const Noise z = noise_for(k, s.sigma, s.ep_id, s.ep_step, lane);
+    Aux aux;
+    observe(c, k, s, z, lane, o, aux);  // the current observation, from the state
+    eps_i = eps[env];
+    akey = sm_at(sm_at(c.seed, kStreamAction), (uint64_t)env);
+  }
+  const unsigned long long rbase = use_replay ? *rp.steps : 0ull;
+  uint32_t ra_batch = 0, ex_batch = 0;
+  __syncthreads();
+  for (int i = 0; i < K; ++i) {
+    if (live) obs_to_tile(X + warp * L.ld1, o, c.B, lane);
+    __syncthreads();
+    mlp_tile(w, X, H1, H2, O, warp, lane);
+    if (!live) continue;
+    if ((i & 31) == 0) {
+      // lane l draws the random action and the exploration uniform of step t + l
+      const uint64_t h = sm_at(akey, (uint64_t)(s.t + (uint32_t)lane));
+      ra_batch = (uint32_t)(sm_at(h, 0ull) >> 32) % (uint32_t)c.n_actions;
+      ex_batch = __ballot_sync(kFull, u24_hi(sm_at(h, 1ull)) < eps_i);
+    }
+    const uint32_t ra = __shfl_sync(kFull, ra_batch, i & 31);
+    const bool explore = (ex_batch >> (i & 31)) & 1u;
+    const uint32_t greedy = greedy_action(O + warp * kOutPad);
+    const uint32_t a = explore ? ra : greedy;
+    long long e = 0;
+    float* srow = nullptr;
+    float* s2row = nullptr;
+    if (use_replay) {
+      e = (long long)((rbase + (unsigned long long)i) % (unsigned long long)rp.slots) * rp.n_envs + env;
+      srow = rp.s + e * rp.obs_dim;
+      s2row = rp.s2 + e * rp.obs_dim;
+      write_obs(srow, o, c.B, lane);
+    }
+    const StepOut r = env_step(c, p, k, s, a, lane, o, s2row);
+    if (use_replay) {
+      if (!r.done) write_obs(s2row, o, c.B, lane);
+      if (lane == 0) {
+        rp.a[e] = (uint8_t)a;
+        rp.r[e] = r.rew;
+        rp.term[e] = (r.done & 3u) ? 1 : 0;
+      }
+    }
+    if (obs_seq) write_obs(obs_seq + ((long long)i * n + env) * c.obs_dim, o, c.B, lane);
+    if (lane == 0) {
+      if (act_seq) act_seq[i * n + env] = (uint8_t)a;
+      if (rew_seq) rew_seq[i * n + env] = r.rew;
+      if (done_seq) done_seq[i * n + env] = (uint8_t)r.done;
+    }
+  }
+  if (live) {
+    if (obs_out) write_obs(obs_out + (long long)env * c.obs_dim, o, c.B, lane);
+    if (lane == 0) store_env(p, env, s);
+  }
+}
+
+__global__ void k_replay_advance(unsigned long long* steps, int K) { *steps += (unsigned long long)K; }
+
+// ------------------------------------------------------------ learner
+// Ring entry of sample i of optimiser step `tstep`: uniform over the entries
+// written so far (a prefix of the ring: min(steps, slots) slots x n_envs).
+__device__ __forceinline__ long long sample_entry(unsigned long long seed, unsigned long long tstep, int i,
+                                                  const ReplayDev& rp) {
+  const unsigned long long st = *rp.steps;
+  const unsigned long long valid = (st < (unsigned long long)rp.slots ? st : (unsigned long long)rp.slots) *
+                                   (unsigned long long)rp.n_envs;
+  if (valid == 0) return -1;
+  const uint64_t h = sm_at(sm_at(sm_at(sm_at(seed, kStreamSample), tstep), (uint64_t)i), 0ull);
+  return (long long)(h % valid);
+}
+
+// Gather 16 rows of a ring array into a BF16 tile (zero padded).
+__device__ __forceinline__ void gather_tile(bf16* X, int ld1, const float* __restrict__ src, const int* rows,
+                                            int obs_dim, int warp, int lane) {
+  const int e = rows[warp];
+  for (int k = lane; k < ld1; k += 32) {
+    const float v = (e >= 0 && k < obs_dim) ? src[(long long)e * obs_dim + k] : 0.0f;
+    X[warp * ld1 + k] = __float2bfloat16_rn(v);
+  }
+}
+
+// Double-DQN targets of 16 samples per CTA: a* = argmax_a Q_online(s', a),
+// y = r + gamma (1 - term) Q_target(s', a*).  Also records the sampled entries.
+__global__ void __launch_bounds__(kThreads, 1)
+    k_td_target(const uint8_t* __restrict__ img, const uint8_t* __restrict__ img_t, ImgLayout L, ReplayDev rp,
+                unsigned long long seed, const unsigned long long* __restrict__ step, int batch, float gamma,
+                float* __restrict__ y, int* __restrict__ idx) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  uint8_t* sw = smem;
+  bf16* X = reinterpret_cast<bf16*>(smem + L.bytes);
+  bf16* H1 = X + kTile * L.ld1;
+  bf16* H2 = H1 + kTile * kLdh;
+  float* O = reinterpret_cast<float*>(H2 + kTile * kLdh);
+  __shared__ int rows[kTile];
+  __shared__ int astar[kTile];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * kTile + warp;
+  if (lane == 0) {
+    rows[warp] = i < batch ? (int)sample_entry(seed, *step, i, rp) : -1;
+    if (i < batch) idx[i] = rows[warp];
+  }
+  stage_image(sw, img, L.bytes);
+  __syncthreads();
+  gather_tile(X, L.ld1, rp.s2, rows, rp.obs_dim, warp, lane);
+  __syncthreads();
+  mlp_tile(qw_at(sw, L), X, H1, H2, O, warp, lane);
+  if (lane == 0) astar[warp] = (int)greedy_action(O + warp * kOutPad);
+  __syncthreads();
+  stage_image(sw, img_t, L.bytes);
+  __syncthreads();
+  mlp_tile(qw_at(sw, L), X, H1, H2, O, warp, lane);
+  if (lane == 0 && i < batch) {
+    float qv[5];
+    greedy_action(O + warp * kOutPad, qv);
+    const int e = rows[warp];
+    const float r = e >= 0 ? rp.r[e] : 0.0f;
+    const float nt = (e >= 0 && rp.term[e]) ? 0.0f : 1.0f;
+    y[i] = r + gamma * nt * qv[astar[warp]];
+  }
+}
+
+// Loss and gradient of 16 samples per CTA.  Forward of Q_online(s) keeping
+// the activations, delta = Q(s, a) - y, dL/dQ(s,a) = clip(delta, -1, 1) / B,
+// back through the dueling combine, W3, ReLU, W2, ReLU, W1.  The CTA's
+// parameter gradient (and Huber sum) goes to its own row of `partial`, so
+// that the reduction order is fixed.
+__global__ void __launch_bounds__(kThreads, 1)
+    k_td_grad(const uint8_t* __restrict__ img, ImgLayout L, ParamLayout P, ReplayDev rp,
+              const int* __restrict__ idx, const float* __restrict__ y, int batch, float* __restrict__ partial) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  uint8_t* sw = smem;
+  bf16* S = reinterpret_cast<bf16*>(smem + L.bytes);
+  bf16* H1 = S + kTile * L.ld1;
+  bf16* H2 = H1 + kTile * kLdh;  // becomes dZ2 after the head gradient
+  bf16* D1 = H2 + kTile * kLdh;  // dZ1
+  float* O = reinterpret_cast<float*>(D1 + kTile * kLdh);
+  float* DO = O + kTile * kOutPad;  // dL/d(head outputs) [16][8]
+  __shared__ int rows[kTile];
+  __shared__ float hub[kTile];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, q = lane & 3;
+  const int i = blockIdx.x * kTile + warp;
+  if (lane == 0) rows[warp] = i < batch ? idx[i] : -1;
+  stage_image(sw, img, L.bytes);
+  __syncthreads();
+  gather_tile(S, L.ld1, rp.s, rows, rp.obs_dim, warp, lane);
+  __syncthreads();
+  const QW w = qw_at(sw, L);
+  mlp_tile(w, S, H1, H2, O, warp, lane);
+  // dL/dQ and back through Q_a = V + A_a - mean(A)
+  if (lane == 0) {
+    float qv[5];
+    greedy_action(O + warp * kOutPad, qv);
+    const int e = rows[warp];
+    float gq = 0.0f, hl = 0.0f;
+    if (e >= 0) {
+      const int a = rp.a[e];
+      const float d = qv[a] - y[i];
+      const float ad = fabsf(d);
+      hl = ad <= 1.0f ? 0.5f * d * d : ad - 0.5f;
+      gq = fminf(fmaxf(d, -1.0f), 1.0f) / (float)batch;
+      DO[warp * kOutPad + 0] = gq;
+      for (int k = 0; k < 5; ++k) DO[warp * kOutPad + 1 + k] = (k == a ? gq : 0.0f) - gq / 5.0f;
+    } else {
+      for (int k = 0; k < 6; ++k) DO[warp * kOutPad + k] = 0.0f;
+    }
+    DO[warp * kOutPad + 6] = 0.0f;
+    DO[warp * kOutPad + 7] = 0.0f;
+    hub[warp] = hl;
+  }
+  __syncthreads();
+  float* pg = partial + (long long)blockIdx.x * (P.total + 1);
+  // head gradient on the CUDA cores: dW3[o][j] = sum_s DO[s][o] H2[s][j],
+  // db3[o] = sum_s DO[s][o]; dH2 = DO W3 (BF16 W3 as in the forward), masked
+  // by the ReLU into dZ2 (written over H2 after a barrier)
+  const int tid = threadIdx.x;
+  float dz2v[kTile];
+  if (tid < kHid) {
+    const int j = tid;
+    float acc[kOut];
+    for (int o = 0; o < kOut; ++o) acc[o] = 0.0f;
+    for (int s = 0; s < kTile; ++s) {
+      const float h = __bfloat162float(H2[s * kLdh + j]);
+      for (int o = 0; o < kOut; ++o) acc[o] += DO[s * kOutPad + o] * h;
+    }
+    for (int o = 0; o < kOut; ++o) pg[P.w3 + o * kHid + j] = acc[o];
+    float db2 = 0.0f;
+    for (int s = 0; s < kTile; ++s) {
+      float dh = 0.0f;
+      for (int o = 0; o < kOut; ++o) dh += DO[s * kOutPad + o] * __bfloat162float(w.W3[o * kLdh + j]);
+      const float v = __bfloat162float(H2[s * kLdh + j]) > 0.0f ? dh : 0.0f;
+      dz2v[s] = v;
+      db2 += v;
+    }
+    pg[P.b2 + j] = db2;
+  }
+  if (tid < kOut) {
+    float acc = 0.0f;
+    for (int s = 0; s < kTile; ++s) acc += DO[s * kOutPad + tid];
+    pg[P.b3 + tid] = acc;
+  }
+  if (tid == 0) {
+    float acc = 0.0f;
+    for (int s = 0; s < kTile; ++s) acc += hub[s];
+    pg[P.total] = acc;
+  }
+  __syncthreads();
+  if (tid < kHid)
+    for (int s = 0; s < kTile; ++s) H2[s * kLdh + tid] = __float2bfloat16_rn(dz2v[s]);
+  __syncthreads();
+  bf16* DZ2 = H2;
+  // dW2[m][n] = sum_s dZ2[s][m] H1[s][n]: M = N = 256, K = 16 -> 512 tiles,
+  // 32 per warp (A = dZ2^T, B = H1, both stored sample-major)
+  for (int t = warp; t < 16 * 32; t += kTile) {
+    const int m0 = (t >> 5) * 16, n0 = (t & 31) * 8;
+    uint32_t a[4], b0, b1;
+    load_a_col(a, DZ2, kLdh, m0, 0, lane);
+    load_b_row(b0, b1, H1, kLdh, 0, n0, lane);
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    mma_bf16(acc, a, b0, b1);
+    float* dst = pg + P.w2;
+    dst[(m0 + g) * kHid + n0 + 2 * q] = acc[0];
+    dst[(m0 + g) * kHid + n0 + 2 * q + 1] = acc[1];
+    dst[(m0 + g + 8) * kHid + n0 + 2 * q] = acc[2];
+    dst[(m0 + g + 8) * kHid + n0 + 2 * q + 1] = acc[3];
+  }
+  // dH1 = dZ2 W2 (B = W2 stored [out][in] -> "row" layout), masked -> dZ1
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    const int n0 = 8 * warp + 128 * half;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int k0 = 0; k0 < kHid; k0 += 16) {
+      uint32_t a[4], b0, b1;
+      load_a_row(a, DZ2, kLdh, 0, k0, lane);
+      load_b_row(b0, b1, w.W2, kLdh, k0, n0, lane);
+      mma_bf16(acc, a, b0, b1);
+    }
+    const int n = n0 + 2 * q;
+    const bool m00 = __bfloat162float(H1[g * kLdh + n]) > 0.f, m01 = __bfloat162float(H1[g * kLdh + n + 1]) > 0.f;
+    const bool m10 = __bfloat162float(H1[(g + 8) * kLdh + n]) > 0.f;
+    const bool m11 = __bfloat162float(H1[(g + 8) * kLdh + n + 1]) > 0.f;
+    *reinterpret_cast<uint32_t*>(D1 + g * kLdh + n) = pack_bf16x2(m00 ? acc[0] : 0.f, m01 ? acc[1] : 0.f);
+    *reinterpret_cast<uint32_t*>(D1 + (g + 8) * kLdh + n) = pack_bf16x2(m10 ? acc[2] : 0.f, m11 ? acc[3] : 0.f);
+    // db1 needs the FP32 values: reduce the 16 rows of this fragment column
+    float c0 = (m00 ? acc[0] : 0.f) + (m10 ? acc[2] : 0.f);
+    float c1 = (m01 ? acc[1] : 0.f) + (m11 ? acc[3] : 0.f);
+    for (int off = 4; off < 32; off <<= 1) {
+      c0 += __shfl_xor_sync(kFull, c0, off);
+      c1 += __shfl_xor_sync(kFull, c1, off);
+    }
+    if (g == 0) {
+      pg[P.b1 + n] = c0;
+      pg[P.b1 + n + 1] = c1;
+    }
+  }
+  __syncthreads();
+  // dW1[m][k] = sum_s dZ1[s][m] S[s][k]: M = 256, N = k1, K = 16
+  const int nt1 = L.k1 / 8;
+  for (int t = warp; t < 16 * nt1; t += kTile) {
+    const int m0 = (t / nt1) * 16, n0 = (t % nt1) * 8;
+    uint32_t a[4], b0, b1;
+    load_a_col(a, D1, kLdh, m0, 0, lane);
+    load_b_row(b0, b1, S, L.ld1, 0, n0, lane);
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    mma_bf16(acc, a, b0, b1);
+    float* dst = pg + P.w1;
+    const int c0 = n0 + 2 * q, c1 = c0 + 1;
+    if (c0 < L.n_in) {
+      dst[(m0 + g) * L.n_in + c0] = acc[0];
+      dst[(m0 + g + 8) * L.n_in + c0] = acc[2];
+    }
+    if (c1 < L.n_in) {
+      dst[(m0 + g) * L.n_in + c1] = acc[1];
+      dst[(m0 + g + 8) * L.n_in + c1] = acc[3];
+    }
+  }
+}
+
+// Sum the per-CTA partials in CTA order, Adam (Kingma & Ba) on the FP32
+// master, and the BF16 image entry of each parameter.  The step counter is
+// read here and advanced by k_step_advance afterwards.
+__global__ void k_adam(float* __restrict__ th, float* __restrict__ m, float* __restrict__ v,
+                       const float* __restrict__ partial, int nblk, ParamLayout P, ImgLayout L, uint8_t* __restrict__ img,
+                       const unsigned long long* __restrict__ step, float lr, float b1, float b2, float eps,
+                       float* __restrict__ loss, float* __restrict__ grad_out, int batch) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0 && loss) {
+    float acc = 0.0f;
+    for (int b = 0; b < nblk; ++b) acc += partial[(long long)b * (P.total + 1) + P.total];
+    *loss = acc / (float)batch;
+  }
+  if (i >= P.total) return;
+  float gsum = 0.0f;
+  for (int b = 0; b < nblk; ++b) gsum += partial[(long long)b * (P.total + 1) + i];
+  if (grad_out) grad_out[i] = gsum;
+  if (lr == 0.0f) return;
+  const float t = (float)(*step + 1ull);
+  const float mi = b1 * m[i] + (1.0f - b1) * gsum;
+  const float vi = b2 * v[i] + (1.0f - b2) * gsum * gsum;
+  m[i] = mi;
+  v[i] = vi;
+  const float mh = mi / (1.0f - powf(b1, t));
+  const float vh = vi / (1.0f - powf(b2, t));
+  const float nth = th[i] - lr * mh / (sqrtf(vh) + eps);
+  th[i] = nth;
+  // image entry
+  const bf16 hv = __float2bfloat16_rn(nth);
+  if (i < P.b1) {
+    const int r = i / L.n_in, k = i % L.n_in;
+    reinterpret_cast<bf16*>(img + L.w1)[r * L.ld1 + k] = hv;
+  } else if (i < P.w2) {
+    reinterpret_cast<float*>(img + L.b1)[i - P.b1] = nth;
+  } else if (i < P.b2) {
+    const int j = i - P.w2;
+    reinterpret_cast<bf16*>(img + L.w2)[(j / kHid) * kLdh + j % kHid] = hv;
+  } else if (i < P.w3) {
+    reinterpret_cast<float*>(img + L.b2)[i - P.b2] = nth;
+  } else if (i < P.b3) {
+    const int j = i - P.w3;
+    reinterpret_cast<bf16*>(img + L.w3)[(j / kHid) * kLdh + j % kHid] = hv;
+  } else {
+    reinterpret_cast<float*>(img + L.b3)[i - P.b3] = nth;
+  }
+}
+
+__global__ void k_step_advance(unsigned long long* step) { *step += 1ull; }
+
+// Target network <- online network when the optimiser step count is a
+// multiple of `every` (checked on the device, so the call can be replayed
+// from a CUDA graph).
+__global__ void k_target_sync(const unsigned long long* __restrict__ step, int every, const float* __restrict__ th,
+                              float* __restrict__ tgt, const uint8_t* __restrict__ img, uint8_t* __restrict__ img_t,
+                              int P, int img_words) {
+  if (every <= 0 || (*step % (unsigned long long)every) != 0ull) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < P) tgt[i] = th[i];
+  if (i < img_words) reinterpret_cast<uint32_t*>(img_t)[i] = reinterpret_cast<const uint32_t*>(img)[i];
+}
+
+// ------------------------------------------------------------- host side
+
+namespace {
+#define SG_CUDA(call)                                        \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return sg_set_cuda_error(e_, #call); \
+  } while (0)
+
+size_t fwd_smem(const ImgLayout& L) {
+  return (size_t)L.bytes + (size_t)kTile * L.ld1 * 2 + 2ull * kTile * kLdh * 2 + kTile * kOutPad * 4;
+}
+size_t grad_smem(const ImgLayout& L) {
+  return (size_t)L.bytes + (size_t)kTile * L.ld1 * 2 + 3ull * kTile * kLdh * 2 + 2ull * kTile * kOutPad * 4;
+}
+
+int set_smem_attr(const void* fn, size_t bytes) {
+  SG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  return SG_OK;
+}
+
+int rebuild_image(sg_qnet* q, const float* th, uint8_t* img, cudaStream_t st) {
+  const int n = image_elems(q->IL);
+  k_build_image<<<(n + 255) / 256, 256, 0, st>>>(th, img, q->IL, q->PL);
+  SG_CUDA(cudaGetLastError());
+  return SG_OK;
+}
+
+void free_qnet(sg_qnet* q) {
+  if (!q) return;
+  cudaFree(q->master);
+  cudaFree(q->target);
+  cudaFree(q->adam_m);
+  cudaFree(q->adam_v);
+  cudaFree(q->img);
+  cudaFree(q->img_t);
+  cudaFree(q->step);
+  cudaFree(q->partial);
+  cudaFree(q->y);
+  cudaFree(q->idx);
+  delete q;
+}
+}  // namespace
+
+extern "C" int sg_qnet_create(int32_t n_in, int32_t max_batch, uint64_t seed, sg_qnet_t* out) {
+  if (!out || n_in < 1 || n_in > 69 || max_batch < 1 || max_batch > (1 << 16)) return SG_E_INVAL;
+  *out = nullptr;
+  sg_qnet* q = new (std::nothrow) sg_qnet();
+  if (!q) return SG_E_OOM;
+  q->n_in = n_in;
+  q->IL = img_layout(n_in);
+  q->PL = param_layout(n_in);
+  q->max_batch = (max_batch + kTile - 1) / kTile * kTile;
+  cudaGetDevice(&q->device);
+  const size_t P = (size_t)q->PL.total;
+  const size_t nblk = (size_t)q->max_batch / kTile;
+  cudaError_t e = cudaSuccess;
+  auto alloc = [&](void** p, size_t b) {
+    if (e == cudaSuccess) e = cudaMalloc(p, b);
+  };
+  alloc((void**)&q->master, P * 4);
+  alloc((void**)&q->target, P * 4);
+  alloc((void**)&q->adam_m, P * 4);
+  alloc((void**)&q->adam_v, P * 4);
+  alloc((void**)&q->img, (size_t)q->IL.bytes);
+  alloc((void**)&q->img_t, (size_t)q->IL.bytes);
+  alloc((void**)&q->step, 8);
+  alloc((void**)&q->partial, nblk * (P + 1) * 4);
+  alloc((void**)&q->y, (size_t)q->max_batch * 4);
+  alloc((void**)&q->idx, (size_t)q->max_batch * 4);
+  if (e != cudaSuccess) {
+    free_qnet(q);
+    sg_set_cuda_error(e, "cudaMalloc");
+    return SG_E_OOM;
+  }
+  int rc = SG_OK;
+  if (e == cudaSuccess) e = cudaMemset(q->adam_m, 0, P * 4);
+  if (e == cudaSuccess) e = cudaMemset(q->adam_v, 0, P * 4);
+  if (e == cudaSuccess) e = cudaMemset(q->step, 0, 8);
+  if (e == cudaSuccess) e = cudaMemset(q->img, 0, (size_t)q->IL.bytes);
+  if (e == cudaSuccess) e = cudaMemset(q->img_t, 0, (size_t)q->IL.bytes);
+  if (e == cudaSuccess) {
+    k_init_params<<<((int)P + 255) / 256, 256>>>(q->master, q->PL, n_in, seed);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) rc = rebuild_image(q, q->master, q->img, 0);
+  if (e == cudaSuccess && rc == SG_OK) e = cudaMemcpy(q->target, q->master, P * 4, cudaMemcpyDeviceToDevice);
+  if (e == cudaSuccess && rc == SG_OK) e = cudaMemcpy(q->img_t, q->img, (size_t)q->IL.bytes, cudaMemcpyDeviceToDevice);
+  if (e == cudaSuccess && rc == SG_OK) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess || rc != SG_OK) {
+    free_qnet(q);
+    return e != cudaSuccess ? sg_set_cuda_error(e, "sg_qnet_create") : rc;
+  }
+  if ((rc = set_smem_attr((const void*)k_qnet_forward, fwd_smem(q->IL))) ||
+      (rc = set_smem_attr((const void*)k_rollout_q, fwd_smem(q->IL))) ||
+      (rc = set_smem_attr((const void*)k_td_target, fwd_smem(q->IL))) ||
+      (rc = set_smem_attr((const void*)k_td_grad, grad_smem(q->IL)))) {
+    free_qnet(q);
+    return rc;
+  }
+  *out = q;
+  return SG_OK;
+}
+
+extern "C" int sg_qnet_destroy(sg_qnet_t q) {
+  if (!q) return SG_E_INVAL;
+  cudaDeviceSynchronize();
+  free_qnet(q);
+  return SG_OK;
+}
+
+extern "C" int sg_qnet_num_params(sg_qnet_t q, int64_t* n) {
+  if (!q || !n) return SG_E_INVAL;
+  *n = q->PL.total;
+  return SG_OK;
+}
+
+extern "C" int sg_qnet_set_params(sg_qnet_t q, const float* host, int64_t n, int32_t which) {
+  if (!q || !host || n != q->PL.total || which < 0 || which > 2) return SG_E_INVAL;
+  SG_CUDA(cudaDeviceSynchronize());
+  if (which == 0 || which == 2) {
+    SG_CUDA(cudaMemcpy(q->master, host, (size_t)n * 4, cudaMemcpyHostToDevice));
+    int rc = rebuild_image(q, q->master, q->img, 0);
+    if (rc) return rc;
+  }
+  if (which == 1 || which == 2) {
+    SG_CUDA(cudaMemcpy(q->target, host, (size_t)n * 4, cudaMemcpyHostToDevice));
+    int rc = rebuild_image(q, q->target, q->img_t, 0);
+    if (rc) return rc;
+  }
+  SG_CUDA(cudaDeviceSynchronize());
+  return SG_OK;
+}
+
+extern "C" int sg_qnet_get_params(sg_qnet_t q, float* host, int64_t n, int32_t which) {
+  if (!q || !host || n != q->PL.total || which < 0 || which > 1) return SG_E_INVAL;
+  SG_CUDA(cudaDeviceSynchronize());
+  SG_CUDA(cudaMemcpy(host, which == 0 ? q->master : q->target, (size_t)n * 4, cudaMemcpyDeviceToHost));
+  return SG_OK;
+}
+
+extern "C" int sg_qnet_get_optimizer(sg_qnet_t q, float* m_host, float* v_host, int64_t n, uint64_t* steps) {
+  if (!q || n != q->PL.total) return SG_E_INVAL;
+  SG_CUDA(cudaDeviceSynchronize());
+  if (m_host) SG_CUDA(cudaMemcpy(m_host, q->adam_m, (size_t)n * 4, cudaMemcpyDeviceToHost));
+  if (v_host) SG_CUDA(cudaMemcpy(v_host, q->adam_v, (size_t)n * 4, cudaMemcpyDeviceToHost));
+  if (steps) SG_CUDA(cudaMemcpy(steps, q->step, 8, cudaMemcpyDeviceToHost));
+  return SG_OK;
+}
+
+extern "C" int sg_qnet_forward(sg_qnet_t q, const float* obs_dev, int32_t M, float* q_dev, sg_stream_t stream) {
+  if (!q || !obs_dev || !q_dev || M < 1) return SG_E_INVAL;
+  k_qnet_forward<<<(M + kTile - 1) / kTile, kThreads, fwd_smem(q->IL), stream>>>(q->img, q->IL, obs_dev, M, q_dev);
+  SG_CUDA(cudaGetLastError());
+  return SG_OK;
+}
+
+extern "C" int sg_replay_create(int32_t slots_per_env, int32_t n_envs, int32_t obs_dim, sg_replay_t* out) {
+  if (!out || slots_per_env < 1 || n_envs < 1 || obs_dim < 1) return SG_E_INVAL;
+  const long long cap = (long long)slots_per_env * n_envs;
+  if (cap > (1ll << 31)) return SG_E_INVAL;
+  *out = nullptr;
+  sg_replay* r = new (std::nothrow) sg_replay();
+  if (!r) return SG_E_OOM;
+  r->cap = cap;
+  cudaGetDevice(&r->device);
+  r->d.slots = slots_per_env;
+  r->d.n_envs = n_envs;
+  r->d.obs_dim = obs_dim;
+  r->d.pad = 0;
+  cudaError_t e = cudaSuccess;
+  auto alloc = [&](void** p, size_t b) {
+    if (e == cudaSuccess) e = cudaMalloc(p, b);
+  };
+  alloc((void**)&r->d.s, (size_t)cap * obs_dim * 4);
+  alloc((void**)&r->d.s2, (size_t)cap * obs_dim * 4);
+  alloc((void**)&r->d.a, (size_t)cap);
+  alloc((void**)&r->d.r, (size_t)cap * 4);
+  alloc((void**)&r->d.term, (size_t)cap);
+  alloc((void**)&r->d.steps, 8);
+  if (e == cudaSuccess) e = cudaMemset(r->d.steps, 0, 8);
+  if (e != cudaSuccess) {
+    cudaFree(r->d.s);
+    cudaFree(r->d.s2);
+    cudaFree(r->d.a);
+    cudaFree(r->d.r);
+    cudaFree(r->d.term);
+    cudaFree(r->d.steps);
+    delete r;
+    sg_set_cuda_error(e, "cudaMalloc");
+    return SG_E_OOM;
+  }
+  *out = r;
+  return SG_OK;
+}
+
+extern "C" int sg_replay_destroy(sg_replay_t r) {
+  if (!r) return SG_E_INVAL;
+  cudaDeviceSynchronize();
+  cudaFree(r->d.s);
+  cudaFree(r->d.s2);
+  cudaFree(r->d.a);
+  cudaFree(r->d.r);
+  cudaFree(r->d.term);
+  cudaFree(r->d.steps);
+  delete r;
+  return SG_OK;
+}
+
+extern "C" int sg_replay_info(sg_replay_t r, int64_t* capacity, uint64_t* steps_recorded, void** s_dev, void** s2_dev,
+                              void** a_dev, void** r_dev, void** term_dev) {
+  if (!r) return SG_E_INVAL;
+  if (capacity) *capacity = r->cap;
+  if (steps_recorded) {
+    SG_CUDA(cudaDeviceSynchronize());
+    SG_CUDA(cudaMemcpy(steps_recorded, r->d.steps, 8, cudaMemcpyDeviceToHost));
+  }
+  if (s_dev) *s_dev = r->d.s;
+  if (s2_dev) *s2_dev = r->d.s2;
+  if (a_dev) *a_dev = r->d.a;
+  if (r_dev) *r_dev = r->d.r;
+  if (term_dev) *term_dev = r->d.term;
+  return SG_OK;
+}
+
+extern "C" int sg_replay_read(sg_replay_t r, int64_t first, int64_t count, float* s_host, float* s2_host,
+                              uint8_t* a_host, float* r_host, uint8_t* term_host) {
+  if (!r || first < 0 || count < 0 || first + count > r->cap) return SG_E_INVAL;
+  SG_CUDA(cudaDeviceSynchronize());
+  const size_t od = (size_t)r->d.obs_dim;
+  if (s_host) SG_CUDA(cudaMemcpy(s_host, r->d.s + first * od, count * od * 4, cudaMemcpyDeviceToHost));
+  if (s2_host) SG_CUDA(cudaMemcpy(s2_host, r->d.s2 + first * od, count * od * 4, cudaMemcpyDeviceToHost));
+  if (a_host) SG_CUDA(cudaMemcpy(a_host, r->d.a + first, count, cudaMemcpyDeviceToHost));
+  if (r_host) SG_CUDA(cudaMemcpy(r_host, r->d.r + first, count * 4, cudaMemcpyDeviceToHost));
+  if (term_host) SG_CUDA(cudaMemcpy(term_host, r->d.term + first, count, cudaMemcpyDeviceToHost));
+  return SG_OK;
+}
 
 int sg_rollout_eps_q(sg_sim* sim, int K, sg_qnet* q, const float* eps, sg_replay* rp, float* obs, float* obs_seq,
                      uint8_t* act_seq, float* rew_seq, uint8_t* done_seq, cudaStream_t stream) {
-  (void)sim; (void)K; (void)q; (void)eps; (void)rp; (void)obs; (void)obs_seq; (void)act_seq; (void)rew_seq; (void)done_seq;
-  (void)stream;
-  return SG_E_INVAL;
+  if (q->n_in != sim->dc.obs_dim) return SG_E_INVAL;
+  ReplayDev rd;
+  std::memset(&rd, 0, sizeof(rd));
+  if (rp) {
+    if (rp->d.n_envs != sim->dc.n_envs || rp->d.obs_dim != sim->dc.obs_dim) return SG_E_INVAL;
+    rd = rp->d;
+  }
+  const int grid = (sim->dc.n_envs + kTile - 1) / kTile;
+  k_rollout_q<<<grid, kThreads, fwd_smem(q->IL), stream>>>(sim->dc, sg_sim_ptrs(sim), q->img, q->IL, K, eps, rd,
+                                                           rp ? 1 : 0, obs, obs_seq, act_seq, rew_seq, done_seq);
+  SG_CUDA(cudaGetLastError());
+  if (rp) {
+    k_replay_advance<<<1, 1, 0, stream>>>(rp->d.steps, K);
+    SG_CUDA(cudaGetLastError());
+  }
+  return SG_OK;
+}
+
+extern "C" int sg_td_train_step(sg_qnet_t q, sg_replay_t rp, int32_t batch, float gamma, float lr,
+                                int32_t target_every, uint64_t seed, float* loss_dev, float* grad_dev,
+                                sg_stream_t stream) {
+  if (!q || !rp || batch < 1 || batch > q->max_batch || rp->d.obs_dim != q->n_in) return SG_E_INVAL;
+  if (!(gamma >= 0.0f && gamma <= 1.0f) || !(lr >= 0.0f)) return SG_E_INVAL;
+  const int nblk = (batch + kTile - 1) / kTile;
+  k_td_target<<<nblk, kThreads, fwd_smem(q->IL), stream>>>(q->img, q->img_t, q->IL, rp->d, seed, q->step, batch,
+                                                            gamma, q->y, q->idx);
+  SG_CUDA(cudaGetLastError());
+  k_td_grad<<<nblk, kThreads, grad_smem(q->IL), stream>>>(q->img, q->IL, q->PL, rp->d, q->idx, q->y, batch,
+                                                          q->partial);
+  SG_CUDA(cudaGetLastError());
+  const int P = q->PL.total;
+  k_adam<<<(P + 255) / 256, 256, 0, stream>>>(q->master, q->adam_m, q->adam_v, q->partial, nblk, q->PL, q->IL, q->img,
+                                               q->step, lr, 0.9f, 0.999f, 1e-8f, loss_dev, grad_dev, batch);
+  SG_CUDA(cudaGetLastError());
+  if (lr > 0.0f) {
+    k_step_advance<<<1, 1, 0, stream>>>(q->step);
+    SG_CUDA(cudaGetLastError());
+    const int words = q->IL.bytes / 4;
+    const int n = P > words ? P : words;
+    k_target_sync<<<(n + 255) / 256, 256, 0, stream>>>(q->step, target_every, q->master, q->target, q->img, q->img_t,
+                                                        P, words);
+    SG_CUDA(cudaGetLastError());
+  }
+  return SG_OK;
 }

@@ -1,0 +1,253 @@
+"""GPU parity of the learned part against the float64 oracle (through the C ABI).
+
+* Forward: the tensor-core Q-values against the oracle's bf16 recipe (same
+  roundings, float64 sums) and against exact float64; the max relative Q
+  error is printed and bounded.
+* Fused eps-greedy rollout: exploration decisions and random actions exact;
+  greedy actions equal the oracle's argmax wherever its top-2 margin exceeds
+  the Q error bound (otherwise either near-tied action is valid); the
+  simulator part of every step bit-exact given the chosen actions; replay
+  contents exact.
+* TD learner: targets, loss and gradient against the oracle's bf16 recipe;
+  Adam update against the oracle's Adam on the same gradient; target sync.
+"""
+
+import ctypes as C
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import qnet as OQ
+from oracle.sim import OracleSim, lib as olib
+from tests._helpers import bits, gpu_state_to_oracle
+from workloads import workload
+
+pytestmark = pytest.mark.gpu
+
+Q_REL_TOL = 4e-3  # max |Q_gpu - Q_bf16_recipe| / max|Q| (float32 vs float64 sums, bf16 re-rounding)
+
+
+def _theta(seed, n_in=37, scale=1.0):
+    p = OQ.init_params(seed, n_in)
+    for k in p:
+        p[k] = p[k] * scale
+    return OQ.flatten(p).astype(np.float32)
+
+
+def _qnet(n_in=37, max_batch=256, seed=0):
+    from paper_2305_04180_gb300 import QNet
+
+    return QNet(n_in, max_batch, seed)
+
+
+def test_params_roundtrip_and_count():
+    q = _qnet()
+    assert q.n_params == 77062
+    th = _theta(1)
+    q.set_params(th)
+    assert np.array_equal(q.get_params("online"), th) and np.array_equal(q.get_params("target"), th)
+    th2 = _theta(2)
+    q.set_params(th2, "target")
+    assert np.array_equal(q.get_params("online"), th) and np.array_equal(q.get_params("target"), th2)
+
+
+@pytest.mark.parametrize("n_in,M", [(37, 1), (37, 53), (37, 4096), (69, 300), (21, 17)])
+def test_forward_against_oracle(n_in, M):
+    rng = np.random.default_rng(n_in + M)
+    q = _qnet(n_in)
+    th = _theta(3, n_in, scale=2.0)
+    q.set_params(th)
+    obs = rng.uniform(-1, 1, size=(M, n_in)).astype(np.float32)
+    got = q.forward(torch.from_numpy(obs).cuda()).cpu().numpy().astype(np.float64)
+    p = OQ.unflatten(th.astype(np.float64), n_in)
+    ref_bf = OQ.forward(p, obs, bf16=True)
+    ref_64 = OQ.forward(p, obs)
+    scale = np.abs(ref_64).max()
+    err_bf = np.abs(got - ref_bf).max() / scale
+    err_64 = np.abs(got - ref_64).max() / scale
+    print(f"max relative Q error: vs bf16 recipe {err_bf:.2e}, vs exact float64 {err_64:.2e}")
+    assert err_bf <= Q_REL_TOL
+    assert err_64 <= 5e-2
+
+
+def _margin_ok(q_ref, act, tol):
+    """Greedy action equals the argmax, or the argmax is within tol of it."""
+    best = q_ref.max(axis=1)
+    chosen = q_ref[np.arange(len(act)), act]
+    return best - chosen <= tol
+
+
+def test_fused_rollout_teacher_forced():
+    """Step by step (K = 1 rollouts) from the GPU's own state: every decision
+    checked, every simulator output bit-exact, the replay ring exact."""
+    from paper_2305_04180_gb300 import Replay, Sim
+
+    w = workload("qnet4096", n_envs=64)
+    maps = w.maps()
+    g = Sim(w.params, maps, w.env_map)
+    o = OracleSim(w.params, maps, w.env_map, prec="f32")
+    q = _qnet(g.obs_dim)
+    th = _theta(5, g.obs_dim, scale=3.0)
+    q.set_params(th)
+    p = OQ.unflatten(th.astype(np.float64), g.obs_dim)
+    n = g.n
+    rp = Replay(8, n, g.obs_dim)
+    eps = torch.from_numpy(w.eps).cuda()
+    obs = g.reset()
+    o.reset()
+    obs_prev = obs.cpu().numpy()
+    act = torch.empty((1, n), dtype=torch.uint8, device="cuda")
+    rew = torch.empty((1, n), dtype=torch.float32, device="cuda")
+    done = torch.empty((1, n), dtype=torch.uint8, device="cuda")
+    n_greedy = n_explore = 0
+    for t in range(40):
+        f, u = g.get_state()
+        o.set_state(*gpu_state_to_oracle(f, u))
+        g.rollout(1, policy="eps_q", qnet=q, eps=eps, replay=rp, obs=obs, act_seq=act, rew_seq=rew, done_seq=done)
+        a = act.cpu().numpy()[0]
+        # exploration draws and random actions are exact
+        explore = o.explore_uniform(t) < w.eps
+        rand_a = o.random_actions(t)
+        assert np.array_equal(a[explore], rand_a[explore]), t
+        # greedy actions: argmax of the oracle's bf16-recipe Q of the previous obs
+        qref = OQ.forward(p, obs_prev, bf16=True)
+        tol = Q_REL_TOL * np.abs(qref).max()
+        ok = _margin_ok(qref, a, 2 * tol)
+        assert np.all(ok[~explore]), (t, np.argwhere(~ok & ~explore))
+        n_greedy += int((~explore).sum())
+        n_explore += int(explore.sum())
+        # the simulator part with the chosen actions is bit-exact
+        oobs, orew, odone, oterm = o.step(a)
+        d = done.cpu().numpy()[0]
+        assert np.array_equal(d, odone), t
+        assert np.array_equal(bits(rew.cpu().numpy()[0]), bits(orew)), t
+        assert np.array_equal(bits(obs.cpu().numpy()), bits(oobs)), t
+        # the transition in the ring: slot t mod 8
+        s, s2, ra, rr, rt = rp.read((t % 8) * n, n)
+        assert np.array_equal(bits(s), bits(obs_prev)), t
+        expect_s2 = np.where((odone != 0)[:, None], oterm, oobs)
+        assert np.array_equal(bits(s2), bits(expect_s2)), t
+        assert np.array_equal(ra, a) and np.array_equal(bits(rr), bits(orew))
+        assert np.array_equal(rt, ((odone & 3) != 0).astype(np.uint8))
+        obs_prev = oobs
+    assert rp.steps_recorded() == 40
+    assert n_greedy > 1000 and n_explore > 50
+
+
+def test_fused_rollout_free_running_matches_stepwise():
+    """A K-step fused rollout equals K single-step rollouts from the same start."""
+    from paper_2305_04180_gb300 import Sim
+
+    w = workload("qnet4096", n_envs=48)
+    maps = w.maps()
+    a = Sim(w.params, maps, w.env_map)
+    b = Sim(w.params, maps, w.env_map)
+    q = _qnet(a.obs_dim)
+    q.set_params(_theta(6, a.obs_dim, scale=3.0))
+    eps = torch.from_numpy(w.eps).cuda()
+    a.reset()
+    b.reset()
+    K = 70
+    ra = torch.empty((K, a.n), device="cuda")
+    rb = torch.empty((K, b.n), device="cuda")
+    aa = torch.empty((K, a.n), dtype=torch.uint8, device="cuda")
+    ab = torch.empty((K, b.n), dtype=torch.uint8, device="cuda")
+    a.rollout(K, policy="eps_q", qnet=q, eps=eps, rew_seq=ra, act_seq=aa)
+    for k in range(K):
+        b.rollout(1, policy="eps_q", qnet=q, eps=eps, rew_seq=rb[k:k + 1], act_seq=ab[k:k + 1])
+    assert torch.equal(aa, ab) and torch.equal(ra, rb)
+
+
+def _fill_replay(n_envs=64, steps=40, seed_theta=7):
+    from paper_2305_04180_gb300 import Replay, Sim
+
+    w = workload("qnet4096", n_envs=n_envs)
+    g = Sim(w.params, w.maps(), w.env_map)
+    q = _qnet(g.obs_dim)
+    q.set_params(_theta(seed_theta, g.obs_dim, scale=2.0))
+    rp = Replay(32, g.n, g.obs_dim)
+    g.reset()
+    g.rollout(steps, policy="eps_q", qnet=q, eps=torch.from_numpy(w.eps).cuda(), replay=rp)
+    torch.cuda.synchronize()
+    return g, q, rp
+
+
+def _oracle_batch(rp, seed, tstep, batch):
+    steps = rp.steps_recorded()
+    valid = min(steps, rp.slots) * rp.n_envs
+    idx = np.array([olib("f32").orc_rng(seed, 4, tstep, i, 0) % valid for i in range(batch)])
+    s, s2, a, r, t = rp.read(0, valid)
+    return idx, dict(s=s[idx].astype(np.float64), a=a[idx].astype(np.int64), r=r[idx].astype(np.float64),
+                     s2=s2[idx].astype(np.float64), term=t[idx].astype(np.float64))
+
+
+@pytest.mark.parametrize("batch", [256, 100])
+def test_td_loss_and_gradient_against_oracle(batch):
+    g, q, rp = _fill_replay()
+    th_on = _theta(8, g.obs_dim, scale=2.0)
+    th_tg = _theta(9, g.obs_dim, scale=2.0)
+    q.set_params(th_on, "online")
+    q.set_params(th_tg, "target")
+    seed = 1234
+    loss = torch.zeros(1, device="cuda")
+    grad = torch.zeros(q.n_params, device="cuda")
+    q.train_step(rp, batch, gamma=0.98, lr=0.0, seed=seed, loss=loss, grad=grad)
+    _, bt = _oracle_batch(rp, seed, 0, batch)
+    pon = OQ.unflatten(th_on.astype(np.float64), g.obs_dim)
+    ptg = OQ.unflatten(th_tg.astype(np.float64), g.obs_dim)
+    ref_loss, ref_g = OQ.td_loss_grad(pon, ptg, bt, 0.98, bf16=True)
+    _, ref_g64 = OQ.td_loss_grad(pon, ptg, bt, 0.98, bf16=False)
+    gl = float(loss.item())
+    gg = grad.cpu().numpy().astype(np.float64)
+    rflat = OQ.flatten(ref_g)
+    r64 = OQ.flatten(ref_g64)
+    rel_loss = abs(gl - ref_loss) / max(1e-6, abs(ref_loss))
+    rel_g = np.linalg.norm(gg - rflat) / np.linalg.norm(rflat)
+    rel_g64 = np.linalg.norm(gg - r64) / np.linalg.norm(r64)
+    print(f"TD loss rel err {rel_loss:.2e}; grad rel err vs bf16 recipe {rel_g:.2e}, vs float64 {rel_g64:.2e}")
+    assert rel_loss <= 1e-2
+    assert rel_g <= 3e-2
+    assert rel_g64 <= 1e-1
+    # every block of the gradient, not just the norm
+    for name, sl in _blocks(g.obs_dim):
+        nb = np.linalg.norm(rflat[sl])
+        if nb > 0:
+            assert np.linalg.norm(gg[sl] - rflat[sl]) / nb <= 6e-2, name
+
+
+def _blocks(n_in):
+    o = 0
+    out = []
+    for name, shp in OQ.param_shapes(n_in):
+        k = int(np.prod(shp))
+        out.append((name, slice(o, o + k)))
+        o += k
+    return out
+
+
+def test_adam_step_and_target_sync():
+    g, q, rp = _fill_replay()
+    th = _theta(10, g.obs_dim, scale=1.0)
+    q.set_params(th)
+    grad = torch.zeros(q.n_params, device="cuda")
+    q.train_step(rp, 64, lr=0.0, seed=7, grad=grad)  # gradient at step 0
+    g0 = grad.cpu().numpy().astype(np.float64)
+    q.train_step(rp, 64, lr=1e-3, target_every=3, seed=7)  # the same batch (step 0), now updating
+    th1 = q.get_params("online").astype(np.float64)
+    ref, m, v = OQ.adam_step(th.astype(np.float64), g0, np.zeros_like(g0), np.zeros_like(g0), 1, lr=1e-3)
+    assert np.max(np.abs(th1 - ref)) <= 2e-6
+    mg, vg, steps = q.optimizer_state()
+    assert steps == 1
+    assert np.allclose(mg, m, rtol=1e-5, atol=1e-12) and np.allclose(vg, v, rtol=1e-4, atol=1e-15)
+    # target copy unchanged until the step count reaches 3
+    assert np.array_equal(q.get_params("target"), th.astype(np.float32))
+    q.train_step(rp, 64, lr=1e-3, target_every=3, seed=7)
+    assert np.array_equal(q.get_params("target"), th.astype(np.float32))
+    q.train_step(rp, 64, lr=1e-3, target_every=3, seed=7)
+    assert np.array_equal(q.get_params("target"), q.get_params("online"))
+    # the inference copy follows the master weights: forward equals a fresh net with those weights
+    obs = torch.rand((40, g.obs_dim), device="cuda")
+    q2 = _qnet(g.obs_dim)
+    q2.set_params(q.get_params("online"))
+    assert torch.equal(q.forward(obs), q2.forward(obs))
