@@ -764,10 +764,14 @@ extern "C" int sg_qnet_create(int32_t n_in, int32_t max_batch, uint64_t seed, sg
     free_qnet(q);
     return e != cudaSuccess ? sg_set_cuda_error(e, "sg_qnet_create") : rc;
   }
-  if ((rc = set_smem_attr((const void*)k_qnet_forward, fwd_smem(q->IL))) ||
-      (rc = set_smem_attr((const void*)k_rollout_q, fwd_smem(q->IL))) ||
-      (rc = set_smem_attr((const void*)k_td_target, fwd_smem(q->IL))) ||
-      (rc = set_smem_attr((const void*)k_td_grad, grad_smem(q->IL)))) {
+  // The limit is a property of the kernel, shared by every handle: set it for
+  // the widest supported input so that a narrower network created later
+  // cannot lower it below what a wider one launches with.
+  const ImgLayout widest = img_layout(69);
+  if ((rc = set_smem_attr((const void*)k_qnet_forward, fwd_smem(widest))) ||
+      (rc = set_smem_attr((const void*)k_rollout_q, fwd_smem(widest))) ||
+      (rc = set_smem_attr((const void*)k_td_target, fwd_smem(widest))) ||
+      (rc = set_smem_attr((const void*)k_td_grad, grad_smem(widest)))) {
     free_qnet(q);
     return rc;
   }
