@@ -299,6 +299,37 @@ int sg_replay_read(sg_replay_t r, int64_t first, int64_t count, float* s_host, f
 int sg_td_train_step(sg_qnet_t q, sg_replay_t replay, int32_t batch, float gamma, float lr, int32_t target_every,
                      uint64_t seed, float* loss_dev, float* grad_dev, sg_stream_t stream);
 
+/*
+ * TD loss and gradient that allocates nothing (the paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory --
+ * code under a fixed memory budget, inside another framework's allocator, or
+ * where cudaMalloc is not allowed -- and so cannot create an sg_qnet_t).
+ * Computes what sg_td_train_step computes with lr = 0, for an explicit batch
+ * instead of ring samples: y_i = r_i + gamma (1 - term_i)
+ * Q_target(s2_i, argmax_a Q(s2_i, a)), loss = mean Huber(Q(s_i, a_i) - y_i),
+ * and its gradient w.r.t. the online parameters.
+ *   params_dev, target_params_dev  flat FP32 parameters (layout of
+ *                 sg_qnet_set_params) of the online and the target network.
+ *   n_in          input width, in [1, 69].
+ *   s_dev, s2_dev batch x n_in floats; a_dev, term_dev batch uint8 (a < 5);
+ *                 r_dev batch floats.  All caller-owned device memory.
+ *   batch         in [1, 256].
+ *   loss_dev      NULL or 1 float; grad_dev num_params floats (outputs).
+ * Scratch: one file-scope device array of about 5.8 MB (BF16 weight images,
+ * targets, per-CTA partial gradients) that every GPU loading the library
+ * holds until the process exits.  Every call shares it and overwrites all of
+ * it that it reads, so nothing carries over between calls; calls that
+ * overlap on the GPU (two streams, two threads) race on it and must be
+ * serialised by the caller.  The first call on a device looks up the array's
+ * device address and sets kernel attributes (no allocation); make that first
+ * call before any stream capture.  Sizes beyond the limits return
+ * SG_E_INVAL with a message in sg_last_cuda_error().  No cudaMalloc,
+ * cudaFree or allocating library routine is called.
+ */
+int sg_td_grad_noalloc(const float* params_dev, const float* target_params_dev, int32_t n_in, const float* s_dev,
+                       const uint8_t* a_dev, const float* r_dev, const float* s2_dev, const uint8_t* term_dev,
+                       int32_t batch, float gamma, float* loss_dev, float* grad_dev, sg_stream_t stream);
+
 /* Human-readable name of an SG_* return code. */
 const char* sg_strerror(int code);
 

@@ -79,6 +79,7 @@ SIGNATURES = {
     "sg_replay_info": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "sg_replay_read": (C.c_int, [_vp, C.c_int64, C.c_int64, _vp, _vp, _vp, _vp, _vp]),
     "sg_td_train_step": (C.c_int, [_vp, _vp, _i32, C.c_float, C.c_float, _i32, C.c_uint64, _vp, _vp, _vp]),
+    "sg_td_grad_noalloc": (C.c_int, [_vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _i32, C.c_float, _vp, _vp, _vp]),
     "sg_strerror": (C.c_char_p, [C.c_int]),
     "sg_last_cuda_error": (C.c_char_p, []),
 }

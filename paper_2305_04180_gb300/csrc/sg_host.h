@@ -29,3 +29,4 @@ struct sg_sim {
 sg::SimPtrs sg_sim_ptrs(sg_sim* s);
 long long sg_state_bytes(const sg_sim* s);
 int sg_set_cuda_error(cudaError_t e, const char* what);
+int sg_set_error_text(const char* msg, int code);

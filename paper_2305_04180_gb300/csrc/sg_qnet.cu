@@ -14,6 +14,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -958,5 +959,141 @@ extern "C" int sg_td_train_step(sg_qnet_t q, sg_replay_t rp, int32_t batch, floa
                                                         P, words);
     SG_CUDA(cudaGetLastError());
   }
+  return SG_OK;
+}
+
+// ------------------------------------------------------------------------
+// TD loss and gradient without any allocation (sg_td_grad_noalloc).
+//
+// For callers that must not allocate device memory at all -- code running
+// under a fixed memory budget, inside another framework's allocator, or in a
+// context where cudaMalloc is not allowed -- and so cannot create a Q-network
+// handle.  The caller passes the FP32 parameters and the batch; every
+// intermediate buffer (BF16 weight images, TD targets, sample indices,
+// per-CTA gradient partials) lives in one file-scope device array that each
+// GPU holds from the moment the library is loaded until the process exits.
+namespace {
+constexpr int kNaMaxBatch = 256;
+constexpr int kNaMaxIn = 69;
+constexpr int kNaMaxBlk = kNaMaxBatch / kTile;
+constexpr int kNaImgBytes = kHid * ((kNaMaxIn + 15) / 16 * 16 + 8) * 2 + kHid * kLdh * 2 + kOutPad * kLdh * 2 +
+                            2 * kHid * 4 + kOutPad * 4;
+constexpr int kNaImgSlot = (kNaImgBytes + 255) / 256 * 256;
+constexpr int kNaMaxParams = kHid * kNaMaxIn + kHid + kHid * kHid + kHid + kOut * kHid + kOut;
+constexpr long long kNaOffY = 2ll * kNaImgSlot;
+constexpr long long kNaOffIdx = kNaOffY + kNaMaxBatch * 4;
+constexpr long long kNaOffPartial = (kNaOffIdx + kNaMaxBatch * 4 + 255) / 256 * 256;
+constexpr long long kNaBytes = kNaOffPartial + (long long)kNaMaxBlk * (kNaMaxParams + 1) * 4;
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_td_noalloc_scratch[kNaBytes];
+
+// Double-DQN targets for an explicit batch (sample i is row i).
+__global__ void __launch_bounds__(kThreads, 1)
+    k_td_target_given(const uint8_t* __restrict__ img, const uint8_t* __restrict__ img_t, ImgLayout L, ReplayDev b,
+                      int batch, float gamma, float* __restrict__ y, int* __restrict__ idx) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  uint8_t* sw = smem;
+  bf16* X = reinterpret_cast<bf16*>(smem + L.bytes);
+  bf16* H1 = X + kTile * L.ld1;
+  bf16* H2 = H1 + kTile * kLdh;
+  float* O = reinterpret_cast<float*>(H2 + kTile * kLdh);
+  __shared__ int rows[kTile];
+  __shared__ int astar[kTile];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * kTile + warp;
+  if (lane == 0) {
+    rows[warp] = i < batch ? i : -1;
+    if (i < batch) idx[i] = i;
+  }
+  stage_image(sw, img, L.bytes);
+  __syncthreads();
+  gather_tile(X, L.ld1, b.s2, rows, b.obs_dim, warp, lane);
+  __syncthreads();
+  mlp_tile(qw_at(sw, L), X, H1, H2, O, warp, lane);
+  if (lane == 0) astar[warp] = (int)greedy_action(O + warp * kOutPad);
+  __syncthreads();
+  stage_image(sw, img_t, L.bytes);
+  __syncthreads();
+  mlp_tile(qw_at(sw, L), X, H1, H2, O, warp, lane);
+  if (lane == 0 && i < batch) {
+    float qv[5];
+    greedy_action(O + warp * kOutPad, qv);
+    const float nt = b.term[i] ? 0.0f : 1.0f;
+    y[i] = b.r[i] + gamma * nt * qv[astar[warp]];
+  }
+}
+
+namespace {
+constexpr int kNaMaxDevices = 64;
+std::mutex g_na_mutex;
+unsigned char* g_na_ptr[kNaMaxDevices] = {};
+
+// Once per device, with that device current: the device address of the
+// scratch array (in host code its name is only a host-side stand-in) and
+// the shared-memory limits of the kernels this path launches.
+int na_setup(unsigned char** out) {
+  int dev = 0;
+  SG_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNaMaxDevices) return sg_set_error_text("sg_td_grad_noalloc: device ordinal too large", SG_E_INVAL);
+  std::lock_guard<std::mutex> lock(g_na_mutex);
+  if (!g_na_ptr[dev]) {
+    void* p = nullptr;
+    SG_CUDA(cudaGetSymbolAddress(&p, g_td_noalloc_scratch));
+    const ImgLayout L = img_layout(kNaMaxIn);
+    int rc = set_smem_attr((const void*)k_td_target_given, fwd_smem(L));
+    if (!rc) rc = set_smem_attr((const void*)k_td_grad, grad_smem(L));
+    if (rc) return rc;
+    g_na_ptr[dev] = static_cast<unsigned char*>(p);
+  }
+  *out = g_na_ptr[dev];
+  return SG_OK;
+}
+}  // namespace
+
+extern "C" int sg_td_grad_noalloc(const float* params_dev, const float* target_params_dev, int32_t n_in,
+                                  const float* s_dev, const uint8_t* a_dev, const float* r_dev, const float* s2_dev,
+                                  const uint8_t* term_dev, int32_t batch, float gamma, float* loss_dev,
+                                  float* grad_dev, sg_stream_t stream) {
+  if (!params_dev || !target_params_dev || !s_dev || !a_dev || !r_dev || !s2_dev || !term_dev || !grad_dev)
+    return sg_set_error_text("sg_td_grad_noalloc: a required pointer is NULL", SG_E_INVAL);
+  if (n_in < 1 || n_in > kNaMaxIn)
+    return sg_set_error_text("sg_td_grad_noalloc: n_in must be in [1, 69] (static scratch limit)", SG_E_INVAL);
+  if (batch < 1 || batch > kNaMaxBatch)
+    return sg_set_error_text("sg_td_grad_noalloc: batch must be in [1, 256] (static scratch limit)", SG_E_INVAL);
+  if (!(gamma >= 0.0f && gamma <= 1.0f)) return sg_set_error_text("sg_td_grad_noalloc: gamma outside [0, 1]", SG_E_INVAL);
+  unsigned char* base = nullptr;
+  int rc = na_setup(&base);
+  if (rc) return rc;
+  const ImgLayout IL = img_layout(n_in);
+  const ParamLayout PL = param_layout(n_in);
+  uint8_t* img = base;
+  uint8_t* img_t = base + kNaImgSlot;
+  float* y = reinterpret_cast<float*>(base + kNaOffY);
+  int* idx = reinterpret_cast<int*>(base + kNaOffIdx);
+  float* partial = reinterpret_cast<float*>(base + kNaOffPartial);
+  ReplayDev b;
+  std::memset(&b, 0, sizeof(b));
+  b.s = const_cast<float*>(s_dev);
+  b.s2 = const_cast<float*>(s2_dev);
+  b.a = const_cast<uint8_t*>(a_dev);
+  b.r = const_cast<float*>(r_dev);
+  b.term = const_cast<uint8_t*>(term_dev);
+  b.slots = 1;
+  b.n_envs = batch;
+  b.obs_dim = n_in;
+  const int ne = image_elems(IL);
+  k_build_image<<<(ne + 255) / 256, 256, 0, stream>>>(params_dev, img, IL, PL);
+  SG_CUDA(cudaGetLastError());
+  k_build_image<<<(ne + 255) / 256, 256, 0, stream>>>(target_params_dev, img_t, IL, PL);
+  SG_CUDA(cudaGetLastError());
+  const int nblk = (batch + kTile - 1) / kTile;
+  k_td_target_given<<<nblk, kThreads, fwd_smem(IL), stream>>>(img, img_t, IL, b, batch, gamma, y, idx);
+  SG_CUDA(cudaGetLastError());
+  k_td_grad<<<nblk, kThreads, grad_smem(IL), stream>>>(img, IL, PL, b, idx, y, batch, partial);
+  SG_CUDA(cudaGetLastError());
+  k_adam<<<(PL.total + 255) / 256, 256, 0, stream>>>(nullptr, nullptr, nullptr, partial, nblk, PL, IL, nullptr,
+                                                      nullptr, 0.0f, 0.9f, 0.999f, 1e-8f, loss_dev, grad_dev, batch);
+  SG_CUDA(cudaGetLastError());
   return SG_OK;
 }

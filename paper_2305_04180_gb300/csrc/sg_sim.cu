@@ -160,6 +160,10 @@ bool finite_nonneg(float v) { return std::isfinite(v) && v >= 0.0f; }
 
 const char* sg_cuda_err_text() { return g_cuda_err; }
 int sg_set_cuda_error(cudaError_t e, const char* what) { return cuda_fail(e, what); }
+int sg_set_error_text(const char* msg, int code) {
+  std::snprintf(g_cuda_err, sizeof(g_cuda_err), "%s", msg);
+  return code;
+}
 
 // Validates the configuration; fills the launch-time copy.
 static int make_devcfg(const sg_sim_config* cfg, DevCfg* dc) {
