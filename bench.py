@@ -230,6 +230,9 @@ def run_ours(a):
     h2d = int(f0.nbytes + u0.nbytes)
     d2h = int(rew_h.numel() * 4 + done_h.numel())
 
+    extras = None
+    if not a.no_extras and rank == 0:
+        extras = run_extras(flush)
     out = None
     if rank == 0:
         out = {
@@ -264,7 +267,185 @@ def run_ours(a):
             "device_status": st,
             "step_ms": ms,
         }
+        if extras is not None:
+            out["extras"] = extras
     return out, pool, (w, n, K, ms_per_step, clk)
+
+
+def _time_cuda(fn, reps, flush=None):
+    """Mean device time (ms) of fn() over reps launches, CUDA events on the
+    current stream, L2 flushed before each (outside the events)."""
+    import torch
+
+    st = torch.cuda.current_stream()
+    tot = 0.0
+    for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    return tot / reps
+
+
+def run_extras(flush):
+    """Secondary measurements on the same GPU: the fused Q-net rollout
+    against the network-free rollout on the 4,096-env workload, the learner
+    step, the Q-value accuracy, and the single-step kernel at 65,536 envs."""
+    import numpy as np
+    import torch
+
+    from paper_2305_04180_gb300 import QNet, Replay, Sim
+    from workloads import workload
+
+    out = {}
+    # fused eps-greedy Q-net rollout vs plain random rollout (4,096 envs, 32 maps)
+    w = workload("qnet4096")
+    sim = Sim(w.params, w.maps(), w.env_map)
+    sim.reset()
+    q = QNet(sim.obs_dim, w.extra["batch"], seed=1)
+    slots = w.extra["ring"] // sim.n
+    rp = Replay(slots, sim.n, sim.obs_dim)
+    eps = torch.from_numpy(w.eps).cuda()
+    Kq = w.steps
+    rew = torch.empty((Kq, sim.n), device="cuda")
+    done = torch.empty((Kq, sim.n), dtype=torch.uint8, device="cuda")
+    fq = lambda: sim.rollout(Kq, policy="eps_q", qnet=q, eps=eps, replay=rp, rew_seq=rew, done_seq=done)  # noqa: E731
+    fr = lambda: sim.rollout(Kq, policy="random", rew_seq=rew, done_seq=done)  # noqa: E731
+    for _ in range(3):
+        fq()
+        fr()
+    ms_q = _time_cuda(fq, 5, flush)
+    ms_r = _time_cuda(fr, 5, flush)
+    out["qnet_rollout"] = {
+        "workload": w.name, "n_envs": sim.n, "steps_per_call": Kq,
+        "value": sim.n * Kq / (ms_q / 1e3), "unit": UNIT,
+        "plain_rollout_same_workload": sim.n * Kq / (ms_r / 1e3),
+        "fused_over_plain": ms_r / ms_q,
+        "replay": f"{rp.capacity} transitions, 302 B each, appended every step",
+        "gpu_launches_per_call": 2,
+    }
+    # Q-value accuracy of the tensor-core forward against a float64 torch CPU forward
+    th = q.get_params()
+    obs = torch.rand((1024, sim.obs_dim), device="cuda") * 2 - 1
+    qg = q.forward(obs).double().cpu()
+    n_in = sim.obs_dim
+    t = torch.from_numpy(th.astype(np.float64))
+    o = 0
+    mats = []
+    for shp in ((256, n_in), (256,), (256, 256), (256,), (6, 256), (6,)):
+        k = int(np.prod(shp))
+        mats.append(t[o:o + k].reshape(shp))
+        o += k
+    W1, b1, W2, b2, W3, b3 = mats
+    x = obs.double().cpu()
+    h = torch.relu(torch.relu(x @ W1.T + b1) @ W2.T + b2) @ W3.T + b3
+    qref = h[:, :1] + h[:, 1:] - h[:, 1:].mean(dim=1, keepdim=True)
+    out["qnet_rollout"]["max_rel_q_error_vs_fp64"] = float((qg - qref).abs().max() / qref.abs().max())
+    # learner: one TD step at batch 256 from the ring filled above
+    loss = torch.zeros(1, device="cuda")
+    ft = lambda: q.train_step(rp, w.extra["batch"], gamma=w.extra["gamma"], lr=w.extra["lr"],  # noqa: E731
+                              target_every=w.extra["target_every"], seed=3, loss=loss)
+    for _ in range(3):
+        ft()
+    ms_t = _time_cuda(ft, 20, flush)
+    out["td_train_step"] = {"batch": w.extra["batch"], "ms": ms_t, "samples_per_s": w.extra["batch"] / (ms_t / 1e3),
+                            "gpu_launches_per_call": 5, "loss": float(loss.item())}
+    del sim, q, rp
+    # single-step kernel with state in HBM, 65,536 envs over the 32 randomised maps
+    w2 = workload("dr1024", n_envs=65536)
+    sim2 = Sim(w2.params, w2.maps(), w2.env_map)
+    obs2 = sim2.reset()
+    act = torch.randint(0, 5, (sim2.n,), dtype=torch.uint8, device="cuda")
+    rew2 = torch.empty(sim2.n, device="cuda")
+    done2 = torch.empty(sim2.n, dtype=torch.uint8, device="cuda")
+    fs = lambda: sim2.step(act, obs=obs2, rew=rew2, done=done2)  # noqa: E731
+    for _ in range(3):
+        fs()
+    ms_s = _time_cuda(fs, 20, flush)
+    # state read 52 B + action 1 B; obs 148 B + reward 4 B + done 1 B + state 52 B written
+    soa_bytes = 52 + 1 + 148 + 4 + 1 + 52
+    out["sim_step"] = {"n_envs": sim2.n, "us_per_launch": ms_s * 1e3, "value": sim2.n / (ms_s / 1e3),
+                       "unit": UNIT, "soa_bytes_per_env_step": soa_bytes,
+                       "soa_gbs": sim2.n * soa_bytes / (ms_s / 1e3) / 1e9}
+    del sim2, obs2
+    out["uneven_batching"] = run_uneven(flush)
+    out["full_learned_loop"] = run_full_loop(flush)
+    return out
+
+
+def run_uneven(flush):
+    """8,192 envs, one seeded map each (sides 128..1024), beams 16/32/64:
+    autotuned launch configuration, 64-step rollouts replayed as a graph."""
+    import torch
+
+    from paper_2305_04180_gb300 import Sim
+    from paper_2305_04180_gb300.autotune import autotune_rollout
+    from paper_2305_04180_gb300.graph import Graph
+    from workloads import workload
+
+    w = workload("uneven8192")
+    t0 = time.perf_counter()
+    sim = Sim(w.params, w.maps(), w.env_map, w.env_beams)
+    build_s = time.perf_counter() - t0
+    sim.reset()
+    K = w.steps
+    tune = autotune_rollout(sim, K=16, reps=2, cache_path=None)
+    rew = torch.empty((K, sim.n), device="cuda")
+    done = torch.empty((K, sim.n), dtype=torch.uint8, device="cuda")
+    st = torch.cuda.Stream()
+    g = Graph()
+    with g.capture(st):
+        sim.rollout(K, rew_seq=rew, done_seq=done, stream=st)
+    for _ in range(2):
+        g.launch(st)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(st):
+        ms = _time_cuda(lambda: g.launch(st), 5, flush)
+    return {"workload": w.name, "n_envs": sim.n, "maps": sim.n_maps, "steps_per_graph": K,
+            "value": sim.n * K / (ms / 1e3), "unit": UNIT, "ms_per_graph": ms,
+            "autotuned": tune["config"], "autotune_table_ms": {f"{r['warps_per_block']}w-{'pq' if r['persistent'] else 'grid'}-{r['order']}": round(r["ms"], 4) for r in tune["table"]},
+            "atlas_build_s": build_s}
+
+
+def run_full_loop(flush):
+    """65,536 envs over 1,024 maps (sides 256..1024), beams 16..64, every
+    randomisation on; fused Q-net rollouts of 32 steps with the learner
+    (batch 4,096, target network, Huber) on a second stream, overlapping, as
+    one graph per iteration; 4 iterations = 128 steps."""
+    import torch
+
+    from paper_2305_04180_gb300 import Sim
+    from paper_2305_04180_gb300.trainer import ColorTrainer
+    from workloads import workload
+
+    w = workload("full65536")
+    sim = Sim(w.params, w.maps(), w.env_map, w.env_beams)
+    sim.reset()
+    slots = w.extra["ring"] // sim.n
+    tr = ColorTrainer(sim, batch=w.extra["batch"], slots=slots, gamma=w.extra["gamma"], lr=w.extra["lr"],
+                      target_every=w.extra["target_every"], learn_start=0, two_streams=True, max_rollout_k=32,
+                      eps=torch.from_numpy(w.eps).cuda(), seed=5)
+    # fill the ring once, then capture: 32 rollout steps || 8 learner steps, upload
+    for _ in range(slots // 32):
+        sim.rollout(32, policy="eps_q", qnet=tr.actor, eps=tr.eps, replay=tr.replay)
+    torch.cuda.synchronize()
+    td = 8
+    g = tr.capture_iteration(32, td, concurrent=True)
+    for _ in range(2):
+        g.launch(tr.s_actor)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(tr.s_actor):
+        ms = _time_cuda(lambda: [g.launch(tr.s_actor) for _ in range(4)], 3, flush)
+    return {"workload": w.name, "n_envs": sim.n, "maps": sim.n_maps, "steps_timed": 128,
+            "value": sim.n * 128 / (ms / 1e3), "unit": UNIT, "ms_per_128_steps": ms,
+            "learner": {"batch": tr.batch, "td_steps_per_128_env_steps": 4 * td,
+                        "td_steps_per_s": 4 * td / (ms / 1e3), "loss": float(tr.loss.item())},
+            "ring": f"{tr.replay.capacity} transitions (reserve 32 slots)", "graph_nodes": g.num_nodes()}
 
 
 def roofline_alu(samples_per_env_step, n, K, ms_per_step, clk):

@@ -40,6 +40,7 @@ typedef struct CUstream_st* sg_stream_t; /* same type as cudaStream_t */
 typedef struct sg_sim* sg_sim_t;
 typedef struct sg_qnet* sg_qnet_t;
 typedef struct sg_replay* sg_replay_t;
+typedef struct sg_graph* sg_graph_t;
 
 enum {
   SG_OK = 0,
@@ -187,6 +188,21 @@ int sg_sim_rollout(sg_sim_t sim, int32_t K, int32_t policy, sg_qnet_t qnet, cons
                    float* rew_seq_dev, uint8_t* done_seq_dev, sg_stream_t stream);
 
 /*
+ * Launch configuration of the network-free rollout (uneven batching and the
+ * autotuner; results do not depend on it):
+ *   warps_per_block  1, 2, 4 (default), 8 or 16 envs per CTA (one warp each).
+ *   persistent       0: one warp per env; 1: a fixed grid of warps pulls envs
+ *                    from a work list through a device counter.
+ *   blocks_per_sm    CTAs per SM of the persistent grid (0 = the occupancy
+ *                    limit).
+ *   order_mode       0: envs in index order; 1: work list sorted by cost
+ *                    (beams x map size), longest first.
+ * Synchronous (computes and uploads the work list on first use).
+ */
+int sg_sim_set_launch(sg_sim_t sim, int32_t warps_per_block, int32_t persistent, int32_t blocks_per_sm,
+                      int32_t order_mode);
+
+/*
  * Copy the complete env state to / from host memory (checkpoint / resume;
  * every random draw is keyed by state, so a restored run continues
  * bit-identically).  Blob layout, N = n_envs:
@@ -258,6 +274,13 @@ int sg_qnet_get_params(sg_qnet_t q, float* host, int64_t n, int32_t which);
 int sg_qnet_get_optimizer(sg_qnet_t q, float* m_host, float* v_host, int64_t n, uint64_t* steps);
 
 /*
+ * Model upload (Alg. 2 step 3 / Alg. 1 step 1: the actor takes the learner's
+ * latest parameters every U optimisation steps): dst's online network takes
+ * src's online parameters and BF16 copy, stream-ordered.  Same n_in.
+ */
+int sg_qnet_copy_params(sg_qnet_t dst, sg_qnet_t src, sg_stream_t stream);
+
+/*
  * Batched inference: q_dev[M][5] = Q(obs_dev[M][n_in]) with the online
  * network (the same tensor-core path the fused rollout uses).
  */
@@ -268,9 +291,15 @@ int sg_qnet_forward(sg_qnet_t q, const float* obs_dev, int32_t M, float* q_dev, 
  * vectorized step; Alg. 2 step 1 samples a mini-batch).  Entry
  * e = slot * n_envs + env, slot = (step index) mod slots_per_env; capacity =
  * slots_per_env * n_envs transitions of (s, a, r, s', terminal) with s, s'
- * float[obs_dim], terminal = collided or arrived.  Synchronous.
+ * float[obs_dim], terminal = collided or arrived.  The learner samples only
+ * the min(steps, slots_per_env - reserve_slots) most recently completed
+ * slots: with reserve_slots >= the longest rollout that may run concurrently
+ * with a training step (on another stream), no sample can be a slot that
+ * rollout is still writing.  0 <= reserve_slots < slots_per_env.
+ * Synchronous.
  */
-int sg_replay_create(int32_t slots_per_env, int32_t n_envs, int32_t obs_dim, sg_replay_t* out);
+int sg_replay_create(int32_t slots_per_env, int32_t n_envs, int32_t obs_dim, int32_t reserve_slots,
+                     sg_replay_t* out);
 int sg_replay_destroy(sg_replay_t r);
 /* Capacity, vectorized steps recorded so far (synchronous read) and the
  * device arrays (s, s2: [cap][obs_dim] float; a, term: [cap] uint8;
@@ -285,8 +314,8 @@ int sg_replay_read(sg_replay_t r, int64_t first, int64_t count, float* s_host, f
 
 /*
  * One optimisation step of the learner (Alg. 2 steps 1-2 with DDQN): sample
- * `batch` ring entries uniformly from those written (counter RNG keyed by
- * seed and the optimiser step count), y = r + gamma (1 - terminal)
+ * `batch` ring entries uniformly from the completed slots (see
+ * sg_replay_create; counter RNG keyed by seed and the optimiser step count), y = r + gamma (1 - terminal)
  * Q_target(s', argmax_a Q_online(s', a)), loss = mean Huber(Q(s, a) - y)
  * (delta 1), gradient by backpropagation, Adam (beta 0.9 / 0.999, eps 1e-8)
  * with learning rate lr; when the step count reaches a multiple of
@@ -329,6 +358,27 @@ int sg_td_train_step(sg_qnet_t q, sg_replay_t replay, int32_t batch, float gamma
 int sg_td_grad_noalloc(const float* params_dev, const float* target_params_dev, int32_t n_in, const float* s_dev,
                        const uint8_t* a_dev, const float* r_dev, const float* s2_dev, const uint8_t* term_dev,
                        int32_t batch, float gamma, float* loss_dev, float* grad_dev, sg_stream_t stream);
+
+/* ---------------------------------------------------------------------- */
+/* CUDA graphs of rollouts and learner steps                                */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * Capture the library calls enqueued on `stream` between sg_graph_begin and
+ * sg_graph_end (thread-local capture mode) into an executable graph; replay
+ * it with sg_graph_launch.  Every counter the kernels use (per-env step
+ * counts, the ring position, the optimiser step) lives on the device, so a
+ * replay continues from where the previous one stopped: capturing K-step
+ * rollouts once and replaying them equals calling them again.  Buffers
+ * passed to the captured calls must stay valid while the graph exists.
+ * Other streams may join the capture through events recorded on `stream`
+ * and must rejoin it before sg_graph_end.  `stream` must not be NULL.
+ */
+int sg_graph_begin(sg_stream_t stream);
+int sg_graph_end(sg_stream_t stream, sg_graph_t* out);
+int sg_graph_launch(sg_graph_t g, sg_stream_t stream);
+int sg_graph_num_nodes(sg_graph_t g, int64_t* n);
+int sg_graph_destroy(sg_graph_t g);
 
 /* Human-readable name of an SG_* return code. */
 const char* sg_strerror(int code);

@@ -62,6 +62,7 @@ SIGNATURES = {
     "sg_sim_reset": (C.c_int, [_vp, C.c_uint64, _vp, _vp]),
     "sg_sim_step": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "sg_sim_rollout": (C.c_int, [_vp, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "sg_sim_set_launch": (C.c_int, [_vp, _i32, _i32, _i32, _i32]),
     "sg_sim_get_state": (C.c_int, [_vp, _vp, _vp]),
     "sg_sim_set_state": (C.c_int, [_vp, _vp, C.c_size_t]),
     "sg_sim_get_atlas": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
@@ -73,13 +74,19 @@ SIGNATURES = {
     "sg_qnet_set_params": (C.c_int, [_vp, _vp, C.c_int64, _i32]),
     "sg_qnet_get_params": (C.c_int, [_vp, _vp, C.c_int64, _i32]),
     "sg_qnet_get_optimizer": (C.c_int, [_vp, _vp, _vp, C.c_int64, _vp]),
+    "sg_qnet_copy_params": (C.c_int, [_vp, _vp, _vp]),
     "sg_qnet_forward": (C.c_int, [_vp, _vp, _i32, _vp, _vp]),
-    "sg_replay_create": (C.c_int, [_i32, _i32, _i32, _vp]),
+    "sg_replay_create": (C.c_int, [_i32, _i32, _i32, _i32, _vp]),
     "sg_replay_destroy": (C.c_int, [_vp]),
     "sg_replay_info": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "sg_replay_read": (C.c_int, [_vp, C.c_int64, C.c_int64, _vp, _vp, _vp, _vp, _vp]),
     "sg_td_train_step": (C.c_int, [_vp, _vp, _i32, C.c_float, C.c_float, _i32, C.c_uint64, _vp, _vp, _vp]),
     "sg_td_grad_noalloc": (C.c_int, [_vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _i32, C.c_float, _vp, _vp, _vp]),
+    "sg_graph_begin": (C.c_int, [_vp]),
+    "sg_graph_end": (C.c_int, [_vp, _vp]),
+    "sg_graph_launch": (C.c_int, [_vp, _vp]),
+    "sg_graph_num_nodes": (C.c_int, [_vp, _vp]),
+    "sg_graph_destroy": (C.c_int, [_vp]),
     "sg_strerror": (C.c_char_p, [C.c_int]),
     "sg_last_cuda_error": (C.c_char_p, []),
 }

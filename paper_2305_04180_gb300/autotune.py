@@ -1,0 +1,102 @@
+"""Autotuner of the network-free rollout's launch configuration.
+
+For a given simulator it times every candidate (envs per CTA, one warp per
+env vs a persistent work-list grid, index vs cost-sorted work list) on short
+rollouts, restoring the env state after each trial, and applies the fastest.
+Results are cached as JSON per (device, workload signature, rollout length),
+so later runs of the same workload reuse them without timing.  The choice
+never changes the results, only their speed.
+"""
+
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+
+import numpy as np
+import torch
+
+CANDIDATES = [dict(warps_per_block=w, persistent=p, order=o)
+              for w in (2, 4, 8, 16) for p in (False, True) for o in ("index", "cost")
+              if not (o == "cost" and not p)]
+DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
+
+
+def _device_name(sim) -> str:
+    try:
+        return torch.cuda.get_device_name(sim.device)
+    except Exception:
+        return "unknown"
+
+
+def signature(sim, K: int) -> str:
+    """Cache key: device name, env count, per-env beams, map sizes, env->map, K."""
+    h = hashlib.sha1()
+    h.update(_device_name(sim).encode())
+    h.update(str((sim.n, sim.obs_dim, sim.n_maps, int(K))).encode())
+    h.update(np.asarray(sim.env_beams if sim.env_beams is not None else [], np.int32).tobytes())
+    h.update(np.asarray(sim.map_shapes, np.int32).tobytes())
+    h.update(np.asarray(sim.env_map_host, np.int32).tobytes())
+    return h.hexdigest()
+
+
+def load_cache(path: str) -> dict:
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def save_cache(path: str, cache: dict) -> None:
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = f"{path}.{os.getpid()}.tmp"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def _time_config(sim, cfg, K, reps, state):
+    sim.set_launch(cfg["warps_per_block"], cfg["persistent"], 0, cfg["order"])
+    times = []
+    for _ in range(reps + 1):
+        sim.set_state(*state)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sim.rollout(K)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return float(np.median(times[1:]))
+
+
+def autotune_rollout(sim, K: int = 32, reps: int = 3, cache_path: str | None = DEFAULT_CACHE,
+                     candidates=None, timer=None) -> dict:
+    """Pick and apply the fastest launch configuration for sim.rollout(K).
+
+    Returns {"config": ..., "ms": ..., "table": [...], "cached": bool}.
+    `timer(sim, cfg, K, reps, state) -> ms` may replace the CUDA-event timer.
+    """
+    candidates = list(candidates or CANDIDATES)
+    key = signature(sim, K)
+    cache = load_cache(cache_path) if cache_path else {}
+    if key in cache:
+        cfg = cache[key]["config"]
+        sim.set_launch(cfg["warps_per_block"], cfg["persistent"], 0, cfg["order"])
+        return dict(cache[key], cached=True)
+    state = sim.get_state()
+    timer = timer or _time_config
+    table = []
+    for cfg in candidates:
+        ms = timer(sim, cfg, K, reps, state)
+        table.append(dict(cfg, ms=ms))
+    sim.set_state(*state)
+    best = min(table, key=lambda r: r["ms"])
+    cfg = {k: best[k] for k in ("warps_per_block", "persistent", "order")}
+    sim.set_launch(cfg["warps_per_block"], cfg["persistent"], 0, cfg["order"])
+    result = {"config": cfg, "ms": best["ms"], "table": table}
+    if cache_path:
+        cache[key] = result
+        save_cache(cache_path, cache)
+    return dict(result, cached=False)

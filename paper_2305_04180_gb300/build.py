@@ -29,6 +29,7 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE
 UNITS = {
     "sg_sim.cu": ["-fmad=false"],
     "sg_qnet.cu": ["-fmad=false"],
+    "sg_graph.cu": [],
 }
 
 

@@ -24,6 +24,13 @@ struct sg_sim {
   float* fstate = nullptr;     // [9][n]
   uint32_t* ustate = nullptr;  // [4][n]
   uint32_t* status_dev = nullptr;
+  // launch configuration of the random rollout (sg_sim_set_launch)
+  int warps_per_block = 4;
+  int persistent = 0;
+  int persistent_blocks = 0;
+  int order_mode = 0;
+  int* order_dev = nullptr;      // work list (cost-sorted env indices) or null
+  unsigned* queue_dev = nullptr; // work-list cursor of the persistent kernel
 };
 
 sg::SimPtrs sg_sim_ptrs(sg_sim* s);

@@ -83,7 +83,8 @@ struct ReplayDev {
   float* r;              // [cap]
   uint8_t* term;         // [cap] collided or arrived
   unsigned long long* steps;  // vectorized steps recorded so far
-  int slots, n_envs, obs_dim, pad;
+  int slots, n_envs, obs_dim;
+  int reserve;           // newest slots the learner never samples (an actor may be writing them)
 };
 
 struct sg_replay {
@@ -392,16 +393,22 @@ __global__ void __launch_bounds__(kThreads, 1)
 __global__ void k_replay_advance(unsigned long long* steps, int K) { *steps += (unsigned long long)K; }
 
 // ------------------------------------------------------------ learner
-// Ring entry of sample i of optimiser step `tstep`: uniform over the entries
-// written so far (a prefix of the ring: min(steps, slots) slots x n_envs).
+// Ring entry of sample i of optimiser step `tstep`: uniform over the
+// V = min(steps, slots - reserve) most recently completed slots, so that a
+// rollout running concurrently (which writes the next slots) is never read.
+// With j = h mod (V n_envs): slot = (steps - 1 - j / n_envs) mod slots,
+// env = j mod n_envs.
 __device__ __forceinline__ long long sample_entry(unsigned long long seed, unsigned long long tstep, int i,
                                                   const ReplayDev& rp) {
   const unsigned long long st = *rp.steps;
-  const unsigned long long valid = (st < (unsigned long long)rp.slots ? st : (unsigned long long)rp.slots) *
-                                   (unsigned long long)rp.n_envs;
-  if (valid == 0) return -1;
+  const unsigned long long usable = (unsigned long long)(rp.slots - rp.reserve);
+  const unsigned long long V = st < usable ? st : usable;
+  if (V == 0) return -1;
   const uint64_t h = sm_at(sm_at(sm_at(sm_at(seed, kStreamSample), tstep), (uint64_t)i), 0ull);
-  return (long long)(h % valid);
+  const unsigned long long j = h % (V * (unsigned long long)rp.n_envs);
+  const unsigned long long back = j / (unsigned long long)rp.n_envs;
+  const unsigned long long slot = (st - 1ull - back) % (unsigned long long)rp.slots;
+  return (long long)(slot * (unsigned long long)rp.n_envs + j % (unsigned long long)rp.n_envs);
 }
 
 // Gather 16 rows of a ring array into a BF16 tile (zero padded).
@@ -826,6 +833,14 @@ extern "C" int sg_qnet_get_optimizer(sg_qnet_t q, float* m_host, float* v_host, 
   return SG_OK;
 }
 
+extern "C" int sg_qnet_copy_params(sg_qnet_t dst, sg_qnet_t src, sg_stream_t stream) {
+  if (!dst || !src || dst->n_in != src->n_in) return SG_E_INVAL;
+  const size_t P = (size_t)src->PL.total;
+  SG_CUDA(cudaMemcpyAsync(dst->master, src->master, P * 4, cudaMemcpyDeviceToDevice, stream));
+  SG_CUDA(cudaMemcpyAsync(dst->img, src->img, (size_t)src->IL.bytes, cudaMemcpyDeviceToDevice, stream));
+  return SG_OK;
+}
+
 extern "C" int sg_qnet_forward(sg_qnet_t q, const float* obs_dev, int32_t M, float* q_dev, sg_stream_t stream) {
   if (!q || !obs_dev || !q_dev || M < 1) return SG_E_INVAL;
   k_qnet_forward<<<(M + kTile - 1) / kTile, kThreads, fwd_smem(q->IL), stream>>>(q->img, q->IL, obs_dev, M, q_dev);
@@ -833,8 +848,10 @@ extern "C" int sg_qnet_forward(sg_qnet_t q, const float* obs_dev, int32_t M, flo
   return SG_OK;
 }
 
-extern "C" int sg_replay_create(int32_t slots_per_env, int32_t n_envs, int32_t obs_dim, sg_replay_t* out) {
+extern "C" int sg_replay_create(int32_t slots_per_env, int32_t n_envs, int32_t obs_dim, int32_t reserve_slots,
+                                sg_replay_t* out) {
   if (!out || slots_per_env < 1 || n_envs < 1 || obs_dim < 1) return SG_E_INVAL;
+  if (reserve_slots < 0 || reserve_slots >= slots_per_env) return SG_E_INVAL;
   const long long cap = (long long)slots_per_env * n_envs;
   if (cap > (1ll << 31)) return SG_E_INVAL;
   *out = nullptr;
@@ -845,7 +862,7 @@ extern "C" int sg_replay_create(int32_t slots_per_env, int32_t n_envs, int32_t o
   r->d.slots = slots_per_env;
   r->d.n_envs = n_envs;
   r->d.obs_dim = obs_dim;
-  r->d.pad = 0;
+  r->d.reserve = reserve_slots;
   cudaError_t e = cudaSuccess;
   auto alloc = [&](void** p, size_t b) {
     if (e == cudaSuccess) e = cudaMalloc(p, b);

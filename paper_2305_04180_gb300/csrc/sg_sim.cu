@@ -104,16 +104,13 @@ __global__ void __launch_bounds__(128) k_step(const __grid_constant__ DevCfg c, 
   }
 }
 
-// K steps with uniformly random actions drawn on the device; the env stays
-// in registers between steps.  One warp per env.  Per-step outputs are
-// optional: obs_seq [K][n][obs_dim], act/rew/done_seq [K][n].
-__global__ void __launch_bounds__(128) k_rollout_random(const __grid_constant__ DevCfg c, SimPtrs p, int K,
-                                                        float* __restrict__ obs, float* __restrict__ obs_seq,
-                                                        uint8_t* __restrict__ act_seq, float* __restrict__ rew_seq,
-                                                        uint8_t* __restrict__ done_seq) {
-  const int env = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (env >= c.n_envs) return;
+// K steps of one env with uniformly random actions drawn on the device; the
+// env stays in registers between steps.  Per-step outputs are optional:
+// obs_seq [K][n][obs_dim], act/rew/done_seq [K][n].
+__device__ __forceinline__ void rollout_env(const DevCfg& c, const SimPtrs& p, int env, int lane, int K,
+                                            float* __restrict__ obs, float* __restrict__ obs_seq,
+                                            uint8_t* __restrict__ act_seq, float* __restrict__ rew_seq,
+                                            uint8_t* __restrict__ done_seq) {
   const EnvConst k = env_const(c, p, env, lane);
   Env s = load_env(p, env);
   const uint64_t akey = sm_at(sm_at(c.seed, kStreamAction), (uint64_t)env);
@@ -136,6 +133,38 @@ __global__ void __launch_bounds__(128) k_rollout_random(const __grid_constant__ 
   if (lane == 0) store_env(p, env, s);
 }
 
+// One warp per env, envs in index order.
+__global__ void __launch_bounds__(512) k_rollout_random(const __grid_constant__ DevCfg c, SimPtrs p, int K,
+                                                        float* __restrict__ obs, float* __restrict__ obs_seq,
+                                                        uint8_t* __restrict__ act_seq, float* __restrict__ rew_seq,
+                                                        uint8_t* __restrict__ done_seq) {
+  const int env = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (env >= c.n_envs) return;
+  rollout_env(c, p, env, lane, K, obs, obs_seq, act_seq, rew_seq, done_seq);
+}
+
+// Persistent variant for uneven batches: a fixed grid of warps pulls envs
+// from a work list (typically sorted by cost, longest first) through a
+// device counter, so that envs with many beams or large maps start first and
+// short ones fill the tail.
+__global__ void __launch_bounds__(512) k_rollout_random_queue(const __grid_constant__ DevCfg c, SimPtrs p, int K,
+                                                              const int* __restrict__ order,
+                                                              unsigned* __restrict__ next, float* __restrict__ obs,
+                                                              float* __restrict__ obs_seq, uint8_t* __restrict__ act_seq,
+                                                              float* __restrict__ rew_seq,
+                                                              uint8_t* __restrict__ done_seq) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    unsigned w = 0;
+    if (lane == 0) w = atomicAdd(next, 1u);
+    w = __shfl_sync(kFull, w, 0);
+    if (w >= (unsigned)c.n_envs) break;
+    const int env = order ? order[w] : (int)w;
+    rollout_env(c, p, env, lane, K, obs, obs_seq, act_seq, rew_seq, done_seq);
+  }
+}
+
 // ------------------------------------------------------------- host side
 
 namespace {
@@ -154,6 +183,11 @@ int cuda_fail(cudaError_t e, const char* what) {
 constexpr int kWarpsPerBlock = 4;
 
 int grid_for(int n_envs) { return (n_envs + kWarpsPerBlock - 1) / kWarpsPerBlock; }
+
+// Host-side cost of an env for the work list: beams x the march work one
+// beam of its map can take (clearance-skipped march: about proportional to
+// the number of beams; larger maps are less cache friendly).
+double env_cost(int beams, int w, int h) { return (double)beams * (1.0 + 1e-6 * (double)w * (double)h); }
 
 bool finite_nonneg(float v) { return std::isfinite(v) && v >= 0.0f; }
 }  // namespace
@@ -251,6 +285,8 @@ static void free_sim(sg_sim* s) {
   cudaFree(s->fstate);
   cudaFree(s->ustate);
   cudaFree(s->status_dev);
+  cudaFree(s->order_dev);
+  cudaFree(s->queue_dev);
   delete s;
 }
 
@@ -398,8 +434,16 @@ extern "C" int sg_sim_rollout(sg_sim_t sim, int32_t K, int32_t policy, sg_qnet_t
   if (((uintptr_t)obs_dev & 3) || ((uintptr_t)obs_seq_dev & 3) || ((uintptr_t)rew_seq_dev & 3)) return SG_E_ALIGN;
   if (policy == SG_POLICY_RANDOM) {
     if (replay) return SG_E_INVAL;  // transitions are recorded by the Q-policy rollout
-    k_rollout_random<<<grid_for(sim->dc.n_envs), 32 * kWarpsPerBlock, 0, stream>>>(
-        sim->dc, sg_sim_ptrs(sim), K, obs_dev, obs_seq_dev, act_seq_dev, rew_seq_dev, done_seq_dev);
+    const int wpb = sim->warps_per_block;
+    if (sim->persistent) {
+      SG_CUDA(cudaMemsetAsync(sim->queue_dev, 0, sizeof(unsigned), stream));
+      k_rollout_random_queue<<<sim->persistent_blocks, 32 * wpb, 0, stream>>>(
+          sim->dc, sg_sim_ptrs(sim), K, sim->order_dev, sim->queue_dev, obs_dev, obs_seq_dev, act_seq_dev,
+          rew_seq_dev, done_seq_dev);
+    } else {
+      k_rollout_random<<<(sim->dc.n_envs + wpb - 1) / wpb, 32 * wpb, 0, stream>>>(
+          sim->dc, sg_sim_ptrs(sim), K, obs_dev, obs_seq_dev, act_seq_dev, rew_seq_dev, done_seq_dev);
+    }
     SG_CUDA(cudaGetLastError());
     return SG_OK;
   }
@@ -409,6 +453,51 @@ extern "C" int sg_sim_rollout(sg_sim_t sim, int32_t K, int32_t policy, sg_qnet_t
                             done_seq_dev, stream);
   }
   return SG_E_INVAL;
+}
+
+extern "C" int sg_sim_set_launch(sg_sim_t sim, int32_t warps_per_block, int32_t persistent, int32_t blocks_per_sm,
+                                 int32_t order_mode) {
+  if (!sim) return SG_E_INVAL;
+  if (warps_per_block != 1 && warps_per_block != 2 && warps_per_block != 4 && warps_per_block != 8 &&
+      warps_per_block != 16)
+    return SG_E_INVAL;
+  if (persistent < 0 || persistent > 1 || blocks_per_sm < 0 || blocks_per_sm > 64 || order_mode < 0 ||
+      order_mode > 1)
+    return SG_E_INVAL;
+  int sms = 0;
+  SG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, sim->device));
+  int bps = blocks_per_sm;
+  if (persistent && bps == 0) {
+    SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_rollout_random_queue, 32 * warps_per_block, 0));
+    if (bps < 1) bps = 1;
+  }
+  if (order_mode == 1 && !sim->order_dev) {
+    // longest first: beams x map size, ties by env index
+    const int n = sim->dc.n_envs;
+    std::vector<int> beams((size_t)n, sim->dc.B), emap((size_t)n);
+    SG_CUDA(cudaMemcpy(emap.data(), sim->env_map_dev, sizeof(int) * n, cudaMemcpyDeviceToHost));
+    if (sim->env_beams_dev) SG_CUDA(cudaMemcpy(beams.data(), sim->env_beams_dev, sizeof(int) * n, cudaMemcpyDeviceToHost));
+    std::vector<int> order((size_t)n);
+    std::vector<double> cost((size_t)n);
+    for (int i = 0; i < n; ++i) {
+      order[i] = i;
+      const sg::MapDesc& m = sim->maps_host[emap[i]];
+      cost[i] = env_cost(beams[i], m.w, m.h);
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    SG_CUDA(cudaMalloc(&sim->order_dev, sizeof(int) * n));
+    SG_CUDA(cudaMemcpy(sim->order_dev, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+  }
+  if (persistent && !sim->queue_dev) SG_CUDA(cudaMalloc(&sim->queue_dev, sizeof(unsigned)));
+  sim->warps_per_block = warps_per_block;
+  sim->persistent = persistent;
+  sim->persistent_blocks = persistent ? bps * sms : 0;
+  sim->order_mode = order_mode;
+  if (order_mode == 0 && sim->order_dev) {
+    SG_CUDA(cudaFree(sim->order_dev));
+    sim->order_dev = nullptr;
+  }
+  return SG_OK;
 }
 
 extern "C" int sg_sim_get_state(sg_sim_t sim, void* host_buf, size_t* bytes) {

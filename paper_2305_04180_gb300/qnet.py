@@ -65,6 +65,10 @@ class QNet:
                                            C.byref(steps)), "sg_qnet_get_optimizer")
         return m, v, int(steps.value)
 
+    def copy_from(self, src: "QNet", stream=None):
+        """This network's online weights <- src's (model upload), stream-ordered."""
+        check(self.L.sg_qnet_copy_params(self.handle, src.handle, _stream(stream)), "sg_qnet_copy_params")
+
     def forward(self, obs: torch.Tensor, out=None, stream=None) -> torch.Tensor:
         assert obs.is_cuda and obs.dtype == torch.float32 and obs.shape[1] == self.n_in
         obs = obs.contiguous()
@@ -82,13 +86,16 @@ class QNet:
 
 
 class Replay:
-    """Device replay ring (``sg_replay_t``) of slots_per_env x n_envs entries."""
+    """Device replay ring (``sg_replay_t``) of slots_per_env x n_envs entries;
+    the learner never samples the ``reserve`` newest slots' successors (see
+    sg_replay_create)."""
 
-    def __init__(self, slots_per_env: int, n_envs: int, obs_dim: int):
+    def __init__(self, slots_per_env: int, n_envs: int, obs_dim: int, reserve: int = 0):
         self.L = _lib.load()
         self.slots, self.n_envs, self.obs_dim = int(slots_per_env), int(n_envs), int(obs_dim)
+        self.reserve = int(reserve)
         self.handle = C.c_void_p()
-        check(self.L.sg_replay_create(self.slots, self.n_envs, self.obs_dim, C.byref(self.handle)),
+        check(self.L.sg_replay_create(self.slots, self.n_envs, self.obs_dim, self.reserve, C.byref(self.handle)),
               "sg_replay_create")
         self.capacity = self.slots * self.n_envs
 

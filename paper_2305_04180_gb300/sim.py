@@ -64,6 +64,9 @@ class Sim:
         w = np.array([g.shape[1] for g in grids], np.int32)
         h = np.array([g.shape[0] for g in grids], np.int32)
         eb = None if env_beams is None else np.ascontiguousarray(env_beams, dtype=np.int32)
+        self.env_beams = eb
+        self.env_map_host = env_map
+        self.map_shapes = [tuple(g.shape) for g in grids]
         self.handle = C.c_void_p()
         with torch.cuda.device(dev):
             check(self.L.sg_sim_create(C.byref(self.cfg), len(grids), ptrs, w.ctypes.data, h.ctypes.data,
@@ -114,6 +117,11 @@ class Sim:
                                     _ptr(act_seq), _ptr(rew_seq), _ptr(done_seq), _stream(stream)),
               "sg_sim_rollout")
         return obs
+
+    def set_launch(self, warps_per_block=4, persistent=False, blocks_per_sm=0, order="index"):
+        """Launch configuration of the network-free rollout (sg_sim_set_launch)."""
+        check(self.L.sg_sim_set_launch(self.handle, int(warps_per_block), int(bool(persistent)), int(blocks_per_sm),
+                                       {"index": 0, "cost": 1}[order]), "sg_sim_set_launch")
 
     def get_state(self):
         """(f [9, N] float32, u [4, N] uint32) host copies of the env state."""

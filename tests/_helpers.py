@@ -26,3 +26,18 @@ def bits(a):
     distinguish -0.0 and NaN payloads)."""
     a = np.ascontiguousarray(a, np.float32)
     return a.view(np.uint32)
+
+
+def ring_sample_entries(seed, tstep, batch, steps, slots, n_envs, reserve=0):
+    """Ring entries the learner samples at optimiser step tstep: uniform over
+    the min(steps, slots - reserve) most recent slots (counter RNG from the
+    oracle), newest slot first."""
+    from oracle.sim import lib as olib
+
+    V = min(steps, slots - reserve)
+    out = []
+    for i in range(batch):
+        j = olib("f32").orc_rng(seed, 4, tstep, i, 0) % (V * n_envs)
+        slot = (steps - 1 - j // n_envs) % slots
+        out.append(slot * n_envs + j % n_envs)
+    return np.array(out)

@@ -1,0 +1,156 @@
+"""Uneven batching (per-env maps, beams and dynamics; persistent work-list
+kernel), CUDA-graph replay of rollouts and of actor-learner iterations, and
+the autotuner.  Launch configuration and graphs must never change results."""
+
+import numpy as np
+import pytest
+import torch
+
+from oracle.sim import OracleSim
+from tests._helpers import bits
+from workloads.configs import DR_RANGES, base_params
+from workloads.maps import make_map
+
+pytestmark = pytest.mark.gpu
+
+
+def _uneven(n=96, seed=0):
+    rng = np.random.default_rng(seed)
+    sides = [128, 256, 366, 512]
+    maps = [make_map(300 + m, sides[m % 4]) for m in range(12)]
+    env_map = rng.integers(0, 12, n).astype(np.int32)
+    beams = rng.choice([16, 32, 64], n).astype(np.int32)
+    return base_params(n_beams=64, **DR_RANGES), maps, env_map, beams
+
+
+def _run(sim, K):
+    n = sim.n
+    out = dict(obs_seq=torch.empty((K, n, sim.obs_dim), device="cuda"),
+               rew=torch.empty((K, n), device="cuda"),
+               done=torch.empty((K, n), dtype=torch.uint8, device="cuda"))
+    sim.rollout(K, obs_seq=out["obs_seq"], rew_seq=out["rew"], done_seq=out["done"])
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def test_uneven_launch_configurations_agree_and_match_oracle():
+    from paper_2305_04180_gb300 import Sim
+
+    p, maps, env_map, beams = _uneven()
+    K = 50
+    results = []
+    for cfg in (None, (8, True, "cost"), (2, False, "index"), (16, True, "index")):
+        s = Sim(p, maps, env_map, beams)
+        if cfg:
+            s.set_launch(cfg[0], cfg[1], 0, cfg[2])
+        s.reset()
+        results.append((_run(s, K), s.get_state()))
+    ref, (f0, u0) = results[0]
+    for r, (f, u) in results[1:]:
+        for k in ref:
+            assert np.array_equal(bits(r[k]) if r[k].dtype == np.float32 else r[k],
+                                  bits(ref[k]) if ref[k].dtype == np.float32 else ref[k]), k
+        assert np.array_equal(bits(f), bits(f0)) and np.array_equal(u, u0)
+    # sampled envs replayed on the oracle
+    o = OracleSim(p, maps, env_map, beams, prec="f32")
+    for i in (0, 5, 17, 42, 95):
+        o.reset_env(i, 0)
+        for k in range(K):
+            obs, rew, done, _ = o.step_one(i, o.random_action(i, k))
+            assert done == ref["done"][k, i] and bits(np.float32(rew)) == bits(ref["rew"][k, i])
+            assert np.array_equal(bits(obs), bits(ref["obs_seq"][k, i]))
+
+
+def test_graph_replay_equals_direct_calls():
+    from paper_2305_04180_gb300 import Sim
+    from paper_2305_04180_gb300.graph import Graph
+
+    p, maps, env_map, beams = _uneven(64, seed=1)
+    a = Sim(p, maps, env_map, beams)
+    b = Sim(p, maps, env_map, beams)
+    a.reset()
+    b.reset()
+    st = torch.cuda.Stream()
+    rew_g = torch.empty((4, 16, a.n), device="cuda")
+    g = Graph()
+    with g.capture(st):
+        for c in range(4):
+            a.rollout(16, rew_seq=rew_g[c], stream=st)
+    assert g.num_nodes() >= 4
+    rew_d = torch.empty((4, 16, b.n), device="cuda")
+    for rep in range(3):
+        g.launch(st)
+        st.synchronize()
+        for c in range(4):
+            b.rollout(16, rew_seq=rew_d[c])
+        torch.cuda.synchronize()
+        assert torch.equal(rew_g, rew_d), rep
+    fa, ua = a.get_state()
+    fb, ub = b.get_state()
+    assert np.array_equal(bits(fa), bits(fb)) and np.array_equal(ua, ub)
+    assert ua[2, 0] == 3 * 64  # 3 replays x 4 rollouts x 16 steps
+
+
+def _trainer(sim_seed=3):
+    from paper_2305_04180_gb300 import Sim
+    from paper_2305_04180_gb300.trainer import ColorTrainer
+
+    p = base_params(**DR_RANGES)
+    maps = [make_map(s) for s in range(1, 5)]
+    sim = Sim(dict(p, seed=sim_seed), maps, (np.arange(64) % 4).astype(np.int32))
+    sim.reset()
+    return ColorTrainer(sim, batch=128, slots=32, lr=5e-4, learn_start=0, two_streams=True, seed=2)
+
+
+def test_graph_actor_learner_iteration_sequential_is_deterministic():
+    """The captured (sequential) iteration equals the same calls made directly."""
+    ta = _trainer()
+    tb = _trainer()
+    ta.sim.rollout(8, policy="eps_q", qnet=ta.actor, eps=ta.eps, replay=ta.replay)
+    tb.sim.rollout(8, policy="eps_q", qnet=tb.actor, eps=tb.eps, replay=tb.replay)
+    g = ta.capture_iteration(8, 4, concurrent=False)
+    for _ in range(5):
+        g.launch(ta.s_actor)
+        tb.sim.rollout(8, policy="eps_q", qnet=tb.actor, eps=tb.eps, replay=tb.replay)
+        for _ in range(4):
+            tb.learner.train_step(tb.replay, tb.batch, lr=tb.lr, target_every=tb.target_every, seed=tb.seed)
+        tb.actor.copy_from(tb.learner)
+    torch.cuda.synchronize()
+    assert np.array_equal(ta.learner.get_params(), tb.learner.get_params())
+    assert np.array_equal(ta.actor.get_params(), tb.learner.get_params())
+    assert ta.replay.steps_recorded() == tb.replay.steps_recorded() == 48
+    assert ta.learner.optimizer_state()[2] == 20
+
+
+def test_graph_actor_learner_iteration_concurrent_runs():
+    """Concurrent branches: counters advance, upload happens, values stay finite."""
+    t = _trainer(sim_seed=4)
+    t.sim.rollout(8, policy="eps_q", qnet=t.actor, eps=t.eps, replay=t.replay)
+    g = t.capture_iteration(8, 4, concurrent=True)
+    for _ in range(6):
+        g.launch(t.s_actor)
+    torch.cuda.synchronize()
+    assert t.replay.steps_recorded() == 8 + 6 * 8
+    assert t.learner.optimizer_state()[2] == 24
+    th = t.learner.get_params()
+    assert np.isfinite(th).all() and np.array_equal(t.actor.get_params(), th)
+    assert np.isfinite(t.loss.item())
+
+
+def test_autotune_applies_a_candidate_and_results_do_not_change(tmp_path):
+    from paper_2305_04180_gb300 import Sim
+    from paper_2305_04180_gb300.autotune import CANDIDATES, autotune_rollout
+
+    p, maps, env_map, beams = _uneven(80, seed=2)
+    a = Sim(p, maps, env_map, beams)
+    b = Sim(p, maps, env_map, beams)
+    a.reset()
+    b.reset()
+    cache = str(tmp_path / "tune.json")
+    res = autotune_rollout(a, K=8, reps=1, cache_path=cache)
+    assert not res["cached"] and len(res["table"]) == len(CANDIDATES)
+    assert {k: res["config"][k] for k in ("warps_per_block", "persistent", "order")} in \
+        [{k: c[k] for k in ("warps_per_block", "persistent", "order")} for c in CANDIDATES]
+    assert np.array_equal(bits(_run(a, 20)["rew"]), bits(_run(b, 20)["rew"]))
+    again = autotune_rollout(a, K=8, reps=1, cache_path=cache)
+    assert again["cached"] and again["config"] == res["config"]

@@ -20,7 +20,7 @@ import torch
 
 from oracle import qnet as OQ
 from oracle.sim import OracleSim, lib as olib
-from tests._helpers import bits, gpu_state_to_oracle
+from tests._helpers import bits, gpu_state_to_oracle, ring_sample_entries
 from workloads import workload
 
 pytestmark = pytest.mark.gpu
@@ -175,9 +175,8 @@ def _fill_replay(n_envs=64, steps=40, seed_theta=7):
 
 def _oracle_batch(rp, seed, tstep, batch):
     steps = rp.steps_recorded()
-    valid = min(steps, rp.slots) * rp.n_envs
-    idx = np.array([olib("f32").orc_rng(seed, 4, tstep, i, 0) % valid for i in range(batch)])
-    s, s2, a, r, t = rp.read(0, valid)
+    idx = ring_sample_entries(seed, tstep, batch, steps, rp.slots, rp.n_envs, rp.reserve)
+    s, s2, a, r, t = rp.read(0, rp.capacity)
     return idx, dict(s=s[idx].astype(np.float64), a=a[idx].astype(np.int64), r=r[idx].astype(np.float64),
                      s2=s2[idx].astype(np.float64), term=t[idx].astype(np.float64))
 

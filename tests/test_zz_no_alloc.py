@@ -16,7 +16,7 @@ import pytest
 import torch
 
 from oracle import qnet as OQ
-from oracle.sim import lib as olib
+from tests._helpers import ring_sample_entries
 from workloads import workload
 
 pytestmark = pytest.mark.gpu
@@ -50,9 +50,8 @@ def _regular(q, rp, th_on, th_tg, batch, seed):
     grad = torch.zeros(q.n_params, device="cuda")
     q.train_step(rp, batch, gamma=0.98, lr=0.0, seed=seed, loss=loss, grad=grad)
     torch.cuda.synchronize()
-    valid = min(rp.steps_recorded(), rp.slots) * rp.n_envs
-    idx = np.array([olib("f32").orc_rng(seed, 4, 0, i, 0) % valid for i in range(batch)])
-    s, s2, a, r, t = rp.read(0, valid)
+    idx = ring_sample_entries(seed, 0, batch, rp.steps_recorded(), rp.slots, rp.n_envs, rp.reserve)
+    s, s2, a, r, t = rp.read(0, rp.capacity)
     return float(loss.item()), grad.cpu().numpy(), (s[idx], a[idx], r[idx], s2[idx], t[idx])
 
 
