@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--rollout-steps", type=int, default=None, help="vectorized steps per bench step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--extras", default="qnet,td,step,uneven,full",
+                    help="comma list of secondary measurements: qnet, td, step, uneven, full")
+    ap.add_argument("--launch", default=None,
+                    help="fixed rollout launch 'warps_per_block,persistent,order,warps_per_env' (skips the autotuner)")
     return ap.parse_args()
 
 
@@ -162,6 +166,15 @@ def run_ours(a):
     sim = Sim(w.params, maps, w.env_map, w.env_beams)
     n = sim.n
     sim.reset(seed=w.params["seed"] + 7919 * rank)
+    from paper_2305_04180_gb300.autotune import autotune_rollout
+
+    if a.launch:
+        wpb, pers, order, wpe = a.launch.split(",")
+        tune = {"config": dict(warps_per_block=int(wpb), persistent=bool(int(pers)), order=order,
+                               warps_per_env=int(wpe))}
+        sim.set_launch(int(wpb), bool(int(pers)), 0, order, int(wpe))
+    else:
+        tune = autotune_rollout(sim, K=64, reps=2, cache_path=None)  # untimed; restores the env state
     obs = sim.new_obs()
     obs_seq = torch.empty((K, n, sim.obs_dim), dtype=torch.float32, device="cuda")
     rew_seq = torch.empty((K, n), dtype=torch.float32, device="cuda")
@@ -232,7 +245,7 @@ def run_ours(a):
 
     extras = None
     if not a.no_extras and rank == 0:
-        extras = run_extras(flush)
+        extras = run_extras(flush, set(a.extras.split(",")))
     out = None
     if rank == 0:
         out = {
@@ -255,7 +268,9 @@ def run_ours(a):
                 "rollout_steps_per_bench_step": K,
                 "env_steps_per_bench_step": n * K,
                 "policy": "random (on-device counter RNG)",
+                "launch": tune["config"],
                 "outputs_per_env_step": "observation (obs_dim floats), reward, done flags",
+                "obs_dim": sim.obs_dim,
                 "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                 "parallelism": "replicas" if world > 1 else "single GPU",
             },
@@ -292,7 +307,7 @@ def _time_cuda(fn, reps, flush=None):
     return tot / reps
 
 
-def run_extras(flush):
+def run_extras(flush, which):
     """Secondary measurements on the same GPU: the fused Q-net rollout
     against the network-free rollout on the 4,096-env workload, the learner
     step, the Q-value accuracy, and the single-step kernel at 65,536 envs."""
@@ -303,6 +318,8 @@ def run_extras(flush):
     from workloads import workload
 
     out = {}
+    if not which & {"qnet", "td"}:
+        return _run_extras_tail(out, flush, which)
     # fused eps-greedy Q-net rollout vs plain random rollout (4,096 envs, 32 maps)
     w = workload("qnet4096")
     sim = Sim(w.params, w.maps(), w.env_map)
@@ -356,6 +373,21 @@ def run_extras(flush):
     out["td_train_step"] = {"batch": w.extra["batch"], "ms": ms_t, "samples_per_s": w.extra["batch"] / (ms_t / 1e3),
                             "gpu_launches_per_call": 5, "loss": float(loss.item())}
     del sim, q, rp
+    return _run_extras_tail(out, flush, which)
+
+
+def _run_extras_tail(out, flush, which):
+    import torch
+
+    from paper_2305_04180_gb300 import Sim
+    from workloads import workload
+
+    if "step" not in which:
+        if "uneven" in which:
+            out["uneven_batching"] = run_uneven(flush)
+        if "full" in which:
+            out["full_learned_loop"] = run_full_loop(flush)
+        return out
     # single-step kernel with state in HBM, 65,536 envs over the 32 randomised maps
     w2 = workload("dr1024", n_envs=65536)
     sim2 = Sim(w2.params, w2.maps(), w2.env_map)
@@ -373,8 +405,10 @@ def run_extras(flush):
                        "unit": UNIT, "soa_bytes_per_env_step": soa_bytes,
                        "soa_gbs": sim2.n * soa_bytes / (ms_s / 1e3) / 1e9}
     del sim2, obs2
-    out["uneven_batching"] = run_uneven(flush)
-    out["full_learned_loop"] = run_full_loop(flush)
+    if "uneven" in which:
+        out["uneven_batching"] = run_uneven(flush)
+    if "full" in which:
+        out["full_learned_loop"] = run_full_loop(flush)
     return out
 
 
@@ -448,6 +482,15 @@ def run_full_loop(flush):
             "ring": f"{tr.replay.capacity} transitions (reserve 32 slots)", "graph_nodes": g.num_nodes()}
 
 
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]), "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+
+
 def roofline_alu(samples_per_env_step, n, K, ms_per_step, clk):
     """March samples of the step definition per second against the lane-issue
     bound of the SMs (see DESIGN: 152 SMs x 128 lanes x SM clock / 8 lane
@@ -481,6 +524,19 @@ def main():
         samples_per_env_step = 1500.0
     out["roofline"] = roofline_alu(samples_per_env_step, n, K, ms_per_step, clk)
     out["roofline"]["samples_per_env_step"] = samples_per_env_step
+    # the streaming view: bytes a step must see if the map window and the SoA
+    # state were streamed from HBM every step (the rollout keeps them on chip)
+    peaks = _measured_peaks()
+    env_steps_s = out["value"] / max(1, out["n_gpus"])
+    win = 201 * 201 / 8.0  # bits of the square around the 100-cell scan disc
+    soa = 65 + 185
+    outb = 4 * (int(out["config"].get("obs_dim", 37))) + 4 + 1
+    out["l2_hbm"] = {"algorithmic_bytes_per_env_step": round(win + soa),
+                     "basis": "201x201-cell map window of the 100-cell scan + SoA state/params/outputs",
+                     "achieved_gbs": env_steps_s * (win + soa) / 1e9, "peak_gbs": peaks.get("hbm_gbs"),
+                     "frac": env_steps_s * (win + soa) / 1e9 / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
+                     "output_bytes_per_env_step": outb, "output_gbs": env_steps_s * outb / 1e9,
+                     "peak_source": peaks.get("source")}
     print(json.dumps(out))
 
 

@@ -197,10 +197,16 @@ int sg_sim_rollout(sg_sim_t sim, int32_t K, int32_t policy, sg_qnet_t qnet, cons
  *                    limit).
  *   order_mode       0: envs in index order; 1: work list sorted by cost
  *                    (beams x map size), longest first.
+ *   warps_per_env    1..16 (not with persistent): W warps share one env.  With
+ *                    random actions the pose chain (motion, collision,
+ *                    arrival, AutoReset draws) never depends on the LiDAR, so
+ *                    every warp replays it and warp w computes the scans,
+ *                    observations and rewards of the steps i = w (mod W).  A
+ *                    CTA then holds max(1, warps_per_block / W) envs.
  * Synchronous (computes and uploads the work list on first use).
  */
 int sg_sim_set_launch(sg_sim_t sim, int32_t warps_per_block, int32_t persistent, int32_t blocks_per_sm,
-                      int32_t order_mode);
+                      int32_t order_mode, int32_t warps_per_env);
 
 /*
  * Copy the complete env state to / from host memory (checkpoint / resume;
@@ -272,6 +278,14 @@ int sg_qnet_get_params(sg_qnet_t q, float* host, int64_t n, int32_t which);
 /* Adam first / second moments (either pointer may be NULL) and the number of
  * optimiser steps taken.  Synchronous. */
 int sg_qnet_get_optimizer(sg_qnet_t q, float* m_host, float* v_host, int64_t n, uint64_t* steps);
+
+/*
+ * Envs per CTA of the fused rollout: 16 or 32 (one warp each; the network's
+ * BF16 weights take most of an SM's shared memory, so one CTA runs per SM),
+ * or 0 (default) to take 32 when that needs fewer waves over the SMs.  The
+ * results do not depend on it.
+ */
+int sg_qnet_set_rollout_rows(sg_qnet_t q, int32_t rows);
 
 /*
  * Model upload (Alg. 2 step 3 / Alg. 1 step 1: the actor takes the learner's

@@ -62,7 +62,7 @@ SIGNATURES = {
     "sg_sim_reset": (C.c_int, [_vp, C.c_uint64, _vp, _vp]),
     "sg_sim_step": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "sg_sim_rollout": (C.c_int, [_vp, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
-    "sg_sim_set_launch": (C.c_int, [_vp, _i32, _i32, _i32, _i32]),
+    "sg_sim_set_launch": (C.c_int, [_vp, _i32, _i32, _i32, _i32, _i32]),
     "sg_sim_get_state": (C.c_int, [_vp, _vp, _vp]),
     "sg_sim_set_state": (C.c_int, [_vp, _vp, C.c_size_t]),
     "sg_sim_get_atlas": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
@@ -74,6 +74,7 @@ SIGNATURES = {
     "sg_qnet_set_params": (C.c_int, [_vp, _vp, C.c_int64, _i32]),
     "sg_qnet_get_params": (C.c_int, [_vp, _vp, C.c_int64, _i32]),
     "sg_qnet_get_optimizer": (C.c_int, [_vp, _vp, _vp, C.c_int64, _vp]),
+    "sg_qnet_set_rollout_rows": (C.c_int, [_vp, _i32]),
     "sg_qnet_copy_params": (C.c_int, [_vp, _vp, _vp]),
     "sg_qnet_forward": (C.c_int, [_vp, _vp, _i32, _vp, _vp]),
     "sg_replay_create": (C.c_int, [_i32, _i32, _i32, _i32, _vp]),

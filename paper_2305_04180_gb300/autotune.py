@@ -1,8 +1,8 @@
 """Autotuner of the network-free rollout's launch configuration.
 
-For a given simulator it times every candidate (envs per CTA, one warp per
-env vs a persistent work-list grid, index vs cost-sorted work list) on short
-rollouts, restoring the env state after each trial, and applies the fastest.
+For a given simulator it times every candidate (envs per CTA, warps per
+env, one warp per env vs a persistent work-list grid, index vs cost-sorted
+work list) on short rollouts, restoring the env state after each trial, and applies the fastest.
 Results are cached as JSON per (device, workload signature, rollout length),
 so later runs of the same workload reuse them without timing.  The choice
 never changes the results, only their speed.
@@ -17,9 +17,12 @@ import os
 import numpy as np
 import torch
 
-CANDIDATES = [dict(warps_per_block=w, persistent=p, order=o)
-              for w in (2, 4, 8, 16) for p in (False, True) for o in ("index", "cost")
-              if not (o == "cost" and not p)]
+CANDIDATES = ([dict(warps_per_block=w, persistent=p, order=o, warps_per_env=1)
+               for w in (2, 4, 8, 16) for p in (False, True) for o in ("index", "cost")
+               if not (o == "cost" and not p)]
+              + [dict(warps_per_block=8, persistent=False, order="index", warps_per_env=W)
+                 for W in (2, 3, 4, 6, 8)])
+KEYS = ("warps_per_block", "persistent", "order", "warps_per_env")
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
 
@@ -57,8 +60,12 @@ def save_cache(path: str, cache: dict) -> None:
     os.replace(tmp, path)
 
 
+def _apply(sim, cfg):
+    sim.set_launch(cfg["warps_per_block"], cfg["persistent"], 0, cfg["order"], cfg.get("warps_per_env", 1))
+
+
 def _time_config(sim, cfg, K, reps, state):
-    sim.set_launch(cfg["warps_per_block"], cfg["persistent"], 0, cfg["order"])
+    _apply(sim, cfg)
     times = []
     for _ in range(reps + 1):
         sim.set_state(*state)
@@ -83,7 +90,7 @@ def autotune_rollout(sim, K: int = 32, reps: int = 3, cache_path: str | None = D
     cache = load_cache(cache_path) if cache_path else {}
     if key in cache:
         cfg = cache[key]["config"]
-        sim.set_launch(cfg["warps_per_block"], cfg["persistent"], 0, cfg["order"])
+        _apply(sim, cfg)
         return dict(cache[key], cached=True)
     state = sim.get_state()
     timer = timer or _time_config
@@ -93,8 +100,8 @@ def autotune_rollout(sim, K: int = 32, reps: int = 3, cache_path: str | None = D
         table.append(dict(cfg, ms=ms))
     sim.set_state(*state)
     best = min(table, key=lambda r: r["ms"])
-    cfg = {k: best[k] for k in ("warps_per_block", "persistent", "order")}
-    sim.set_launch(cfg["warps_per_block"], cfg["persistent"], 0, cfg["order"])
+    cfg = {k: best[k] for k in KEYS}
+    _apply(sim, cfg)
     result = {"config": cfg, "ms": best["ms"], "table": table}
     if cache_path:
         cache[key] = result

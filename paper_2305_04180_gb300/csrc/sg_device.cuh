@@ -482,23 +482,11 @@ struct StepOut {
   uint32_t done;
 };
 
-// One full step of one env by its warp.  `term_row` (may be null) receives
-// the pre-reset observation of a done env; `o` returns this lane's share of
-// the observation after the step (after the reset when done).
-__device__ __forceinline__ StepOut env_step(const DevCfg& c, const SimPtrs& p, const EnvConst& k, Env& s,
-                                            uint32_t a, int lane, ObsRegs& o, float* term_row) {
-  // noise of the observation this step produces, drawn before the scan
-  const Noise z = noise_for(k, s.sigma, s.ep_id, s.ep_step + 1u, lane);
-  const bool bad = kinematics(c, s, a);
-  if (bad && lane == 0) atomicOr(p.status, 1u);
-  const bool col = collide_warp(c, k.m, k.rows, k.clr, s.x, s.y, lane);
-  Aux aux;
-  observe(c, k, s, z, lane, o, aux);
-  const float d1sq = fmaf(aux.ddx, aux.ddx, aux.ddy * aux.ddy);
-  const bool arrive = d1sq <= c.goal_r * c.goal_r;
-  const bool trunc = s.ep_step >= (uint32_t)c.t_max;
-  // Eq. 11: 0.3 r_d1 + 0.1 r_d2 + 0.3 r_v + 0.3 r_alpha + 0.1 r_d
+// Eq. 11 for a live (not collided, not arrived) step: 0.3 r_d1 + 0.1 r_d2 +
+// 0.3 r_v + 0.3 r_alpha + 0.1 r_d at the state `s` whose scan gave `aux`.
+__device__ __forceinline__ float shaped_reward(const DevCfg& c, const EnvConst& k, const Env& s, const Aux& aux) {
   const Layout& L = k.L;
+  const float d1sq = fmaf(aux.ddx, aux.ddx, aux.ddy * aux.ddy);
   const float d1 = sqrtf(d1sq);
   const float rd1 = 1.0f - d1 / L.D;
   const float ex = L.gx - L.sx, ey = L.gy - L.sy;
@@ -515,6 +503,25 @@ __device__ __forceinline__ StepOut env_step(const DevCfg& c, const SimPtrs& p, c
   r = r + 0.3f * rv;
   r = r + 0.3f * ra;
   r = r + 0.1f * rdn;
+  return r;
+}
+
+// One full step of one env by its warp.  `term_row` (may be null) receives
+// the pre-reset observation of a done env; `o` returns this lane's share of
+// the observation after the step (after the reset when done).
+__device__ __forceinline__ StepOut env_step(const DevCfg& c, const SimPtrs& p, const EnvConst& k, Env& s,
+                                            uint32_t a, int lane, ObsRegs& o, float* term_row) {
+  // noise of the observation this step produces, drawn before the scan
+  const Noise z = noise_for(k, s.sigma, s.ep_id, s.ep_step + 1u, lane);
+  const bool bad = kinematics(c, s, a);
+  if (bad && lane == 0) atomicOr(p.status, 1u);
+  const bool col = collide_warp(c, k.m, k.rows, k.clr, s.x, s.y, lane);
+  Aux aux;
+  observe(c, k, s, z, lane, o, aux);
+  const float d1sq = fmaf(aux.ddx, aux.ddx, aux.ddy * aux.ddy);
+  const bool arrive = d1sq <= c.goal_r * c.goal_r;
+  const bool trunc = s.ep_step >= (uint32_t)c.t_max;
+  float r = shaped_reward(c, k, s, aux);
   if (col)
     r = -10.0f;
   else if (arrive)
@@ -530,6 +537,47 @@ __device__ __forceinline__ StepOut env_step(const DevCfg& c, const SimPtrs& p, c
     observe(c, k, s, z0, lane, o, aux);
   }
   return out;
+}
+
+// The part of a step that the next step depends on: delay, Eq. 5, Eq. 6,
+// collision, arrival, truncation and, when done, the AutoReset draws.  It
+// never needs the LiDAR.  `pre` receives the state after the motion and
+// before the reset.  Returns the done flags.
+__device__ __forceinline__ uint32_t pose_step(const DevCfg& c, const SimPtrs& p, const EnvConst& k, Env& s, Env& pre,
+                                              uint32_t a, int lane, bool report) {
+  const bool bad = kinematics(c, s, a);
+  if (bad && report && lane == 0) atomicOr(p.status, 1u);
+  const bool col = collide_warp(c, k.m, k.rows, k.clr, s.x, s.y, lane);
+  const float ddx = k.L.gx - s.x, ddy = k.L.gy - s.y;
+  const float d1sq = fmaf(ddx, ddx, ddy * ddy);
+  const bool arrive = d1sq <= c.goal_r * c.goal_r;
+  const bool trunc = s.ep_step >= (uint32_t)c.t_max;
+  const uint32_t done = (col ? 1u : 0u) | (arrive ? 2u : 0u) | (trunc ? 4u : 0u);
+  pre = s;
+  if (done) reset_env(c, k, s, s.ep_id + 1u, lane);
+  return done;
+}
+
+// The rest of a step, given pose_step's result: the observation (after the
+// reset when done) and the reward (from the pre-reset scan when the episode
+// was only truncated; the terminal constants otherwise).
+__device__ __forceinline__ float obs_step(const DevCfg& c, const EnvConst& k, const Env& s, const Env& pre,
+                                          uint32_t done, int lane, ObsRegs& o) {
+  Aux aux;
+  float r;
+  if (done & 1u) {
+    r = -10.0f;
+  } else if (done & 2u) {
+    r = 75.0f;
+  } else if (done) {
+    const Noise zp = noise_for(k, pre.sigma, pre.ep_id, pre.ep_step, lane);
+    observe(c, k, pre, zp, lane, o, aux);
+    r = shaped_reward(c, k, pre, aux);
+  }
+  const Noise z = noise_for(k, s.sigma, s.ep_id, s.ep_step, lane);
+  observe(c, k, s, z, lane, o, aux);
+  if (!done) r = shaped_reward(c, k, s, aux);
+  return r;
 }
 
 // Random action of step t for env (uniform over the action table): lane l

@@ -29,6 +29,7 @@ struct sg_sim {
   int persistent = 0;
   int persistent_blocks = 0;
   int order_mode = 0;
+  int warps_per_env = 1;
   int* order_dev = nullptr;      // work list (cost-sorted env indices) or null
   unsigned* queue_dev = nullptr; // work-list cursor of the persistent kernel
 };

@@ -110,6 +110,7 @@ struct sg_qnet {
   float* partial = nullptr;  // [max_batch / kTile][P + 1] (last entry: loss)
   float* y = nullptr;        // [max_batch] TD targets
   int* idx = nullptr;        // [max_batch] sampled ring entries
+  int rollout_mt = 0;        // m-tiles per CTA of the fused rollout (0 = choose by waves)
 };
 
 // --------------------------------------------------------------- kernels
@@ -188,64 +189,77 @@ __device__ __forceinline__ QW qw_at(const uint8_t* base, const ImgLayout& L) {
   return w;
 }
 
-// One hidden layer for 16 rows: Hout[16][256] = bf16(ReLU(Xin * W^T + b)).
-// Warp w computes output columns [8w, 8w+8) and [8w+128, 8w+136).
+// One hidden layer for R = 16 * MT rows and R warps: Hout[R][256] =
+// bf16(ReLU(Xin * W^T + b)).  The 32 output n-tiles of 8 columns are spread
+// over the warps (32 / R per warp), each warp covering all MT m-tiles so
+// that one B fragment serves MT MMAs.
+template <int MT>
 __device__ __forceinline__ void hidden_layer(const bf16* Xin, int ldx, int kdim, const bf16* W, int ldw,
-                                             const float* b, bf16* Hout, int warp, int lane, float* zout) {
+                                             const float* b, bf16* Hout, int warp, int lane) {
+  constexpr int kWarps = 16 * MT;
+  constexpr int kNt = 32 / kWarps;
   const int g = lane >> 2, q = lane & 3;
 #pragma unroll
-  for (int half = 0; half < 2; ++half) {
-    const int n0 = 8 * warp + 128 * half;
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int t = 0; t < kNt; ++t) {
+    const int n0 = 8 * (warp + kWarps * t);
+    float acc[MT][4];
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt) acc[mt][0] = acc[mt][1] = acc[mt][2] = acc[mt][3] = 0.f;
     for (int k0 = 0; k0 < kdim; k0 += 16) {
-      uint32_t a[4], b0, b1;
-      load_a_row(a, Xin, ldx, 0, k0, lane);
+      uint32_t b0, b1;
       load_b_col(b0, b1, W, ldw, k0, n0, lane);
-      mma_bf16(acc, a, b0, b1);
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt) {
+        uint32_t a[4];
+        load_a_row(a, Xin, ldx, 16 * mt, k0, lane);
+        mma_bf16(acc[mt], a, b0, b1);
+      }
     }
     const int n = n0 + 2 * q;
-    const float z0 = acc[0] + b[n], z1 = acc[1] + b[n + 1];
-    const float z2 = acc[2] + b[n], z3 = acc[3] + b[n + 1];
-    if (zout) {  // pre-activation signs for the backward pass (kept as values)
-      zout[g * kHid + n] = z0;
-      zout[g * kHid + n + 1] = z1;
-      zout[(g + 8) * kHid + n] = z2;
-      zout[(g + 8) * kHid + n + 1] = z3;
+    const float bn = b[n], bn1 = b[n + 1];
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt) {
+      const int r0 = 16 * mt + g;
+      *reinterpret_cast<uint32_t*>(Hout + r0 * kLdh + n) =
+          pack_bf16x2(fmaxf(acc[mt][0] + bn, 0.f), fmaxf(acc[mt][1] + bn1, 0.f));
+      *reinterpret_cast<uint32_t*>(Hout + (r0 + 8) * kLdh + n) =
+          pack_bf16x2(fmaxf(acc[mt][2] + bn, 0.f), fmaxf(acc[mt][3] + bn1, 0.f));
     }
-    *reinterpret_cast<uint32_t*>(Hout + g * kLdh + n) = pack_bf16x2(fmaxf(z0, 0.f), fmaxf(z1, 0.f));
-    *reinterpret_cast<uint32_t*>(Hout + (g + 8) * kLdh + n) = pack_bf16x2(fmaxf(z2, 0.f), fmaxf(z3, 0.f));
   }
 }
 
-// Head for 16 rows by warp 0: O[16][8] = H2 * W3^T + b3 (FP32), two
-// accumulator chains (even / odd k-steps) summed in a fixed order.
-__device__ __forceinline__ void head_layer(const bf16* H2, const QW& w, float* O, int lane) {
+// Head for the 16 rows of m-tile mt (one warp): O[16][8] = H2 * W3^T + b3
+// (FP32), two accumulator chains (even / odd k-steps) summed in a fixed order.
+__device__ __forceinline__ void head_layer(const bf16* H2, const QW& w, float* O, int mt, int lane) {
   const int g = lane >> 2, q = lane & 3;
   float acc0[4] = {0.f, 0.f, 0.f, 0.f}, acc1[4] = {0.f, 0.f, 0.f, 0.f};
   for (int k0 = 0; k0 < kHid; k0 += 32) {
     uint32_t a[4], b0, b1;
-    load_a_row(a, H2, kLdh, 0, k0, lane);
+    load_a_row(a, H2, kLdh, 16 * mt, k0, lane);
     load_b_col(b0, b1, w.W3, kLdh, k0, 0, lane);
     mma_bf16(acc0, a, b0, b1);
-    load_a_row(a, H2, kLdh, 0, k0 + 16, lane);
+    load_a_row(a, H2, kLdh, 16 * mt, k0 + 16, lane);
     load_b_col(b0, b1, w.W3, kLdh, k0 + 16, 0, lane);
     mma_bf16(acc1, a, b0, b1);
   }
   const int n = 2 * q;
-  O[g * kOutPad + n] = (acc0[0] + acc1[0]) + w.b3[n];
-  O[g * kOutPad + n + 1] = (acc0[1] + acc1[1]) + w.b3[n + 1];
-  O[(g + 8) * kOutPad + n] = (acc0[2] + acc1[2]) + w.b3[n];
-  O[(g + 8) * kOutPad + n + 1] = (acc0[3] + acc1[3]) + w.b3[n + 1];
+  const int r0 = 16 * mt + g;
+  O[r0 * kOutPad + n] = (acc0[0] + acc1[0]) + w.b3[n];
+  O[r0 * kOutPad + n + 1] = (acc0[1] + acc1[1]) + w.b3[n + 1];
+  O[(r0 + 8) * kOutPad + n] = (acc0[2] + acc1[2]) + w.b3[n];
+  O[(r0 + 8) * kOutPad + n + 1] = (acc0[3] + acc1[3]) + w.b3[n + 1];
 }
 
-// Full forward of a 16-row tile (all 16 warps; contains block barriers).
+// Full forward of a tile of 16 * MT rows by 16 * MT warps (contains block
+// barriers; every thread of the block must call it).
+template <int MT = 1>
 __device__ __forceinline__ void mlp_tile(const QW& w, const bf16* X, bf16* H1, bf16* H2, float* O, int warp,
-                                         int lane, float* z1 = nullptr, float* z2 = nullptr) {
-  hidden_layer(X, w.ld1, w.k1, w.W1, w.ld1, w.b1, H1, warp, lane, z1);
+                                         int lane) {
+  hidden_layer<MT>(X, w.ld1, w.k1, w.W1, w.ld1, w.b1, H1, warp, lane);
   __syncthreads();
-  hidden_layer(H1, kLdh, kHid, w.W2, kLdh, w.b2, H2, warp, lane, z2);
+  hidden_layer<MT>(H1, kLdh, kHid, w.W2, kLdh, w.b2, H2, warp, lane);
   __syncthreads();
-  if (warp == 0) head_layer(H2, w, O, lane);
+  if (warp < MT) head_layer(H2, w, O, warp, lane);
   __syncthreads();
 }
 
@@ -308,7 +322,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_qnet_forward(const uint8_t* __r
 // network on the tensor cores, every env takes argmax Q or (with probability
 // eps_i) the random action, then steps; the transition is appended to the
 // replay ring.  One warp per env, 16 envs per CTA.
-__global__ void __launch_bounds__(kThreads, 1)
+template <int MT>
+__global__ void __launch_bounds__(512 * MT, 1)
     k_rollout_q(const __grid_constant__ DevCfg c, SimPtrs p, const uint8_t* __restrict__ img, ImgLayout L, int K,
                 const float* __restrict__ eps, ReplayDev rp, int use_replay, float* __restrict__ obs_out,
                 float* __restrict__ obs_seq, uint8_t* __restrict__ act_seq, float* __restrict__ rew_seq,
@@ -316,14 +331,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ __align__(16) uint8_t smem[];
   uint8_t* sw = smem;
   bf16* X = reinterpret_cast<bf16*>(smem + L.bytes);
-  bf16* H1 = X + kTile * L.ld1;
-  bf16* H2 = H1 + kTile * kLdh;
-  float* O = reinterpret_cast<float*>(H2 + kTile * kLdh);
+  constexpr int kRows = 16 * MT;
+  bf16* H1 = X + kRows * L.ld1;
+  bf16* H2 = H1 + kRows * kLdh;
+  float* O = reinterpret_cast<float*>(H2 + kRows * kLdh);
   stage_image(sw, img, L.bytes);
-  for (int i = threadIdx.x; i < kTile * L.ld1; i += blockDim.x) X[i] = __float2bfloat16_rn(0.0f);
+  for (int i = threadIdx.x; i < kRows * L.ld1; i += blockDim.x) X[i] = __float2bfloat16_rn(0.0f);
   const QW w = qw_at(sw, L);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int env = blockIdx.x * kTile + warp;
+  const int env = blockIdx.x * kRows + warp;
   const bool live = env < c.n_envs;
   const long long n = c.n_envs;
   EnvConst k;
@@ -347,7 +363,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   for (int i = 0; i < K; ++i) {
     if (live) obs_to_tile(X + warp * L.ld1, o, c.B, lane);
     __syncthreads();
-    mlp_tile(w, X, H1, H2, O, warp, lane);
+    mlp_tile<MT>(w, X, H1, H2, O, warp, lane);
     if (!live) continue;
     if ((i & 31) == 0) {
       // lane l draws the random action and the exploration uniform of step t + l
@@ -688,8 +704,8 @@ namespace {
     if (e_ != cudaSuccess) return sg_set_cuda_error(e_, #call); \
   } while (0)
 
-size_t fwd_smem(const ImgLayout& L) {
-  return (size_t)L.bytes + (size_t)kTile * L.ld1 * 2 + 2ull * kTile * kLdh * 2 + kTile * kOutPad * 4;
+size_t fwd_smem(const ImgLayout& L, int rows = kTile) {
+  return (size_t)L.bytes + (size_t)rows * L.ld1 * 2 + 2ull * rows * kLdh * 2 + (size_t)rows * kOutPad * 4;
 }
 size_t grad_smem(const ImgLayout& L) {
   return (size_t)L.bytes + (size_t)kTile * L.ld1 * 2 + 3ull * kTile * kLdh * 2 + 2ull * kTile * kOutPad * 4;
@@ -777,7 +793,8 @@ extern "C" int sg_qnet_create(int32_t n_in, int32_t max_batch, uint64_t seed, sg
   // cannot lower it below what a wider one launches with.
   const ImgLayout widest = img_layout(69);
   if ((rc = set_smem_attr((const void*)k_qnet_forward, fwd_smem(widest))) ||
-      (rc = set_smem_attr((const void*)k_rollout_q, fwd_smem(widest))) ||
+      (rc = set_smem_attr((const void*)k_rollout_q<1>, fwd_smem(widest))) ||
+      (rc = set_smem_attr((const void*)k_rollout_q<2>, fwd_smem(widest, 32))) ||
       (rc = set_smem_attr((const void*)k_td_target, fwd_smem(widest))) ||
       (rc = set_smem_attr((const void*)k_td_grad, grad_smem(widest)))) {
     free_qnet(q);
@@ -830,6 +847,12 @@ extern "C" int sg_qnet_get_optimizer(sg_qnet_t q, float* m_host, float* v_host, 
   if (m_host) SG_CUDA(cudaMemcpy(m_host, q->adam_m, (size_t)n * 4, cudaMemcpyDeviceToHost));
   if (v_host) SG_CUDA(cudaMemcpy(v_host, q->adam_v, (size_t)n * 4, cudaMemcpyDeviceToHost));
   if (steps) SG_CUDA(cudaMemcpy(steps, q->step, 8, cudaMemcpyDeviceToHost));
+  return SG_OK;
+}
+
+extern "C" int sg_qnet_set_rollout_rows(sg_qnet_t q, int32_t rows) {
+  if (!q || (rows != 0 && rows != 16 && rows != 32)) return SG_E_INVAL;
+  q->rollout_mt = rows / 16;
   return SG_OK;
 }
 
@@ -940,9 +963,19 @@ int sg_rollout_eps_q(sg_sim* sim, int K, sg_qnet* q, const float* eps, sg_replay
     if (rp->d.n_envs != sim->dc.n_envs || rp->d.obs_dim != sim->dc.obs_dim) return SG_E_INVAL;
     rd = rp->d;
   }
-  const int grid = (sim->dc.n_envs + kTile - 1) / kTile;
-  k_rollout_q<<<grid, kThreads, fwd_smem(q->IL), stream>>>(sim->dc, sg_sim_ptrs(sim), q->img, q->IL, K, eps, rd,
-                                                           rp ? 1 : 0, obs, obs_seq, act_seq, rew_seq, done_seq);
+  // 32 envs per CTA (two m-tiles) when that fills fewer waves than 16; the
+  // shared-memory image limits a CTA to one per SM either way
+  int sms = 0;
+  SG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, sim->device));
+  const int n = sim->dc.n_envs;
+  const int waves16 = ((n + 15) / 16 + sms - 1) / sms, waves32 = ((n + 31) / 32 + sms - 1) / sms;
+  const int mt = q->rollout_mt > 0 ? q->rollout_mt : (waves32 < waves16 ? 2 : 1);
+  if (mt == 2)
+    k_rollout_q<2><<<(n + 31) / 32, 1024, fwd_smem(q->IL, 32), stream>>>(
+        sim->dc, sg_sim_ptrs(sim), q->img, q->IL, K, eps, rd, rp ? 1 : 0, obs, obs_seq, act_seq, rew_seq, done_seq);
+  else
+    k_rollout_q<1><<<(n + 15) / 16, 512, fwd_smem(q->IL), stream>>>(
+        sim->dc, sg_sim_ptrs(sim), q->img, q->IL, K, eps, rd, rp ? 1 : 0, obs, obs_seq, act_seq, rew_seq, done_seq);
   SG_CUDA(cudaGetLastError());
   if (rp) {
     k_replay_advance<<<1, 1, 0, stream>>>(rp->d.steps, K);

@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(128) k_reset(const __grid_constant__ DevCfg c,
 }
 
 // One vectorized step; one warp per env.
-__global__ void __launch_bounds__(128) k_step(const __grid_constant__ DevCfg c, SimPtrs p, const uint8_t* __restrict__ act,
+__global__ void __launch_bounds__(128, 8) k_step(const __grid_constant__ DevCfg c, SimPtrs p, const uint8_t* __restrict__ act,
                                               float* __restrict__ obs, float* __restrict__ rew,
                                               uint8_t* __restrict__ done, float* __restrict__ term) {
   const int env = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -133,8 +133,57 @@ __device__ __forceinline__ void rollout_env(const DevCfg& c, const SimPtrs& p, i
   if (lane == 0) store_env(p, env, s);
 }
 
+// K steps of one env shared by W warps: every warp replays the pose chain of
+// every step (it never depends on the LiDAR when actions are random), and
+// warp w computes the observation and reward of the steps i with
+// i mod W == w.  All warps hold identical states; no synchronisation.
+__device__ __forceinline__ void rollout_env_split(const DevCfg& c, const SimPtrs& p, int env, int w, int W, int lane,
+                                                  int K, float* __restrict__ obs, float* __restrict__ obs_seq,
+                                                  uint8_t* __restrict__ act_seq, float* __restrict__ rew_seq,
+                                                  uint8_t* __restrict__ done_seq) {
+  const EnvConst k = env_const(c, p, env, lane);
+  Env s = load_env(p, env);
+  Env pre;
+  const uint64_t akey = sm_at(sm_at(c.seed, kStreamAction), (uint64_t)env);
+  ObsRegs o;
+  o.b0 = o.b1 = o.ex = 0.0f;
+  const long long n = c.n_envs;
+  uint32_t abatch = 0;
+  int mine = w;  // next step this warp observes
+  for (int i = 0; i < K; ++i) {
+    if ((i & 31) == 0) abatch = random_action_for(c, akey, s.t + (uint32_t)lane);
+    const uint32_t a = __shfl_sync(kFull, abatch, i & 31);
+    const uint32_t done = pose_step(c, p, k, s, pre, a, lane, w == 0);
+    if (i == mine) {
+      mine += W;
+      const float r = obs_step(c, k, s, pre, done, lane, o);
+      if (obs_seq) write_obs(obs_seq + ((long long)i * n + env) * c.obs_dim, o, c.B, lane);
+      if (lane == 0) {
+        if (act_seq) act_seq[i * n + env] = (uint8_t)a;
+        if (rew_seq) rew_seq[i * n + env] = r;
+        if (done_seq) done_seq[i * n + env] = (uint8_t)done;
+      }
+    }
+  }
+  if (obs && (K - 1) % W == w) write_obs(obs + (long long)env * c.obs_dim, o, c.B, lane);
+  if (w == 0 && lane == 0) store_env(p, env, s);
+}
+
+// W warps per env, E envs per CTA (blockDim = 32 W E).
+__global__ void __launch_bounds__(256, 4) k_rollout_random_split(const __grid_constant__ DevCfg c, SimPtrs p, int K,
+                                                              int W, float* __restrict__ obs,
+                                                              float* __restrict__ obs_seq,
+                                                              uint8_t* __restrict__ act_seq,
+                                                              float* __restrict__ rew_seq,
+                                                              uint8_t* __restrict__ done_seq) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int env = blockIdx.x * (blockDim.x / (32 * W)) + warp / W;
+  if (env >= c.n_envs) return;
+  rollout_env_split(c, p, env, warp % W, W, lane, K, obs, obs_seq, act_seq, rew_seq, done_seq);
+}
+
 // One warp per env, envs in index order.
-__global__ void __launch_bounds__(512) k_rollout_random(const __grid_constant__ DevCfg c, SimPtrs p, int K,
+__global__ void __launch_bounds__(512, 2) k_rollout_random(const __grid_constant__ DevCfg c, SimPtrs p, int K,
                                                         float* __restrict__ obs, float* __restrict__ obs_seq,
                                                         uint8_t* __restrict__ act_seq, float* __restrict__ rew_seq,
                                                         uint8_t* __restrict__ done_seq) {
@@ -148,7 +197,7 @@ __global__ void __launch_bounds__(512) k_rollout_random(const __grid_constant__ 
 // from a work list (typically sorted by cost, longest first) through a
 // device counter, so that envs with many beams or large maps start first and
 // short ones fill the tail.
-__global__ void __launch_bounds__(512) k_rollout_random_queue(const __grid_constant__ DevCfg c, SimPtrs p, int K,
+__global__ void __launch_bounds__(512, 2) k_rollout_random_queue(const __grid_constant__ DevCfg c, SimPtrs p, int K,
                                                               const int* __restrict__ order,
                                                               unsigned* __restrict__ next, float* __restrict__ obs,
                                                               float* __restrict__ obs_seq, uint8_t* __restrict__ act_seq,
@@ -435,7 +484,12 @@ extern "C" int sg_sim_rollout(sg_sim_t sim, int32_t K, int32_t policy, sg_qnet_t
   if (policy == SG_POLICY_RANDOM) {
     if (replay) return SG_E_INVAL;  // transitions are recorded by the Q-policy rollout
     const int wpb = sim->warps_per_block;
-    if (sim->persistent) {
+    if (sim->warps_per_env > 1) {
+      const int W = sim->warps_per_env;
+      const int E = wpb / W > 0 ? wpb / W : 1;
+      k_rollout_random_split<<<(sim->dc.n_envs + E - 1) / E, 32 * W * E, 0, stream>>>(
+          sim->dc, sg_sim_ptrs(sim), K, W, obs_dev, obs_seq_dev, act_seq_dev, rew_seq_dev, done_seq_dev);
+    } else if (sim->persistent) {
       SG_CUDA(cudaMemsetAsync(sim->queue_dev, 0, sizeof(unsigned), stream));
       k_rollout_random_queue<<<sim->persistent_blocks, 32 * wpb, 0, stream>>>(
           sim->dc, sg_sim_ptrs(sim), K, sim->order_dev, sim->queue_dev, obs_dev, obs_seq_dev, act_seq_dev,
@@ -456,8 +510,9 @@ extern "C" int sg_sim_rollout(sg_sim_t sim, int32_t K, int32_t policy, sg_qnet_t
 }
 
 extern "C" int sg_sim_set_launch(sg_sim_t sim, int32_t warps_per_block, int32_t persistent, int32_t blocks_per_sm,
-                                 int32_t order_mode) {
+                                 int32_t order_mode, int32_t warps_per_env) {
   if (!sim) return SG_E_INVAL;
+  if (warps_per_env < 1 || warps_per_env > 16 || (warps_per_env > 1 && persistent)) return SG_E_INVAL;
   if (warps_per_block != 1 && warps_per_block != 2 && warps_per_block != 4 && warps_per_block != 8 &&
       warps_per_block != 16)
     return SG_E_INVAL;
@@ -493,6 +548,7 @@ extern "C" int sg_sim_set_launch(sg_sim_t sim, int32_t warps_per_block, int32_t 
   sim->persistent = persistent;
   sim->persistent_blocks = persistent ? bps * sms : 0;
   sim->order_mode = order_mode;
+  sim->warps_per_env = warps_per_env;
   if (order_mode == 0 && sim->order_dev) {
     SG_CUDA(cudaFree(sim->order_dev));
     sim->order_dev = nullptr;

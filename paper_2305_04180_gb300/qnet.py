@@ -65,6 +65,10 @@ class QNet:
                                            C.byref(steps)), "sg_qnet_get_optimizer")
         return m, v, int(steps.value)
 
+    def set_rollout_rows(self, rows: int):
+        """Envs per CTA of the fused rollout (16, 32, or 0 = automatic)."""
+        check(self.L.sg_qnet_set_rollout_rows(self.handle, int(rows)), "sg_qnet_set_rollout_rows")
+
     def copy_from(self, src: "QNet", stream=None):
         """This network's online weights <- src's (model upload), stream-ordered."""
         check(self.L.sg_qnet_copy_params(self.handle, src.handle, _stream(stream)), "sg_qnet_copy_params")

@@ -118,10 +118,10 @@ class Sim:
               "sg_sim_rollout")
         return obs
 
-    def set_launch(self, warps_per_block=4, persistent=False, blocks_per_sm=0, order="index"):
+    def set_launch(self, warps_per_block=4, persistent=False, blocks_per_sm=0, order="index", warps_per_env=1):
         """Launch configuration of the network-free rollout (sg_sim_set_launch)."""
         check(self.L.sg_sim_set_launch(self.handle, int(warps_per_block), int(bool(persistent)), int(blocks_per_sm),
-                                       {"index": 0, "cost": 1}[order]), "sg_sim_set_launch")
+                                       {"index": 0, "cost": 1}[order], int(warps_per_env)), "sg_sim_set_launch")
 
     def get_state(self):
         """(f [9, N] float32, u [4, N] uint32) host copies of the env state."""

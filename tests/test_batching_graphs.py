@@ -39,10 +39,11 @@ def test_uneven_launch_configurations_agree_and_match_oracle():
     p, maps, env_map, beams = _uneven()
     K = 50
     results = []
-    for cfg in (None, (8, True, "cost"), (2, False, "index"), (16, True, "index")):
+    for cfg in (None, (8, True, "cost", 1), (2, False, "index", 1), (16, True, "index", 1), (8, False, "index", 3),
+                (8, False, "index", 4), (8, False, "index", 8), (4, False, "index", 5)):
         s = Sim(p, maps, env_map, beams)
         if cfg:
-            s.set_launch(cfg[0], cfg[1], 0, cfg[2])
+            s.set_launch(cfg[0], cfg[1], 0, cfg[2], cfg[3])
         s.reset()
         results.append((_run(s, K), s.get_state()))
     ref, (f0, u0) = results[0]
@@ -149,8 +150,7 @@ def test_autotune_applies_a_candidate_and_results_do_not_change(tmp_path):
     cache = str(tmp_path / "tune.json")
     res = autotune_rollout(a, K=8, reps=1, cache_path=cache)
     assert not res["cached"] and len(res["table"]) == len(CANDIDATES)
-    assert {k: res["config"][k] for k in ("warps_per_block", "persistent", "order")} in \
-        [{k: c[k] for k in ("warps_per_block", "persistent", "order")} for c in CANDIDATES]
+    assert res["config"] in CANDIDATES
     assert np.array_equal(bits(_run(a, 20)["rew"]), bits(_run(b, 20)["rew"]))
     again = autotune_rollout(a, K=8, reps=1, cache_path=cache)
     assert again["cached"] and again["config"] == res["config"]

@@ -78,16 +78,19 @@ def _margin_ok(q_ref, act, tol):
     return best - chosen <= tol
 
 
-def test_fused_rollout_teacher_forced():
+@pytest.mark.parametrize("rows", [16, 32])
+def test_fused_rollout_teacher_forced(rows):
     """Step by step (K = 1 rollouts) from the GPU's own state: every decision
-    checked, every simulator output bit-exact, the replay ring exact."""
+    checked, every simulator output bit-exact, the replay ring exact; for
+    CTAs of 16 and of 32 envs."""
     from paper_2305_04180_gb300 import Replay, Sim
 
-    w = workload("qnet4096", n_envs=64)
+    w = workload("qnet4096", n_envs=70)
     maps = w.maps()
     g = Sim(w.params, maps, w.env_map)
     o = OracleSim(w.params, maps, w.env_map, prec="f32")
     q = _qnet(g.obs_dim)
+    q.set_rollout_rows(rows)
     th = _theta(5, g.obs_dim, scale=3.0)
     q.set_params(th)
     p = OQ.unflatten(th.astype(np.float64), g.obs_dim)
@@ -157,6 +160,29 @@ def test_fused_rollout_free_running_matches_stepwise():
     for k in range(K):
         b.rollout(1, policy="eps_q", qnet=q, eps=eps, rew_seq=rb[k:k + 1], act_seq=ab[k:k + 1])
     assert torch.equal(aa, ab) and torch.equal(ra, rb)
+
+
+def test_fused_rollout_tile_heights_agree():
+    """CTAs of 16 and of 32 envs compute identical Q-values, so identical
+    trajectories (the same MMA order per row)."""
+    from paper_2305_04180_gb300 import Sim
+
+    w = workload("qnet4096", n_envs=100)
+    maps = w.maps()
+    q = _qnet(w.params["n_beams"] + 5)
+    q.set_params(_theta(12, q.n_in, scale=3.0))
+    eps = torch.from_numpy(w.eps).cuda()
+    out = []
+    for rows in (16, 32):
+        q.set_rollout_rows(rows)
+        s = Sim(w.params, maps, w.env_map)
+        s.reset()
+        act = torch.empty((60, s.n), dtype=torch.uint8, device="cuda")
+        rew = torch.empty((60, s.n), device="cuda")
+        s.rollout(60, policy="eps_q", qnet=q, eps=eps, act_seq=act, rew_seq=rew)
+        out.append((act, rew, s.get_state()))
+    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
+    assert np.array_equal(out[0][2][1], out[1][2][1])
 
 
 def _fill_replay(n_envs=64, steps=40, seed_theta=7):
