@@ -31,6 +31,7 @@ struct sg_sim {
   int order_mode = 0;
   int warps_per_env = 1;
   int* order_dev = nullptr;      // work list (cost-sorted env indices) or null
+  int* map_order_dev = nullptr;  // env indices grouped by map (stable), for per-CTA map locality
   unsigned* queue_dev = nullptr; // work-list cursor of the persistent kernel
 };
 

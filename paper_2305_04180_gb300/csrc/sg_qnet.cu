@@ -325,7 +325,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_qnet_forward(const uint8_t* __r
 template <int MT>
 __global__ void __launch_bounds__(512 * MT, 1)
     k_rollout_q(const __grid_constant__ DevCfg c, SimPtrs p, const uint8_t* __restrict__ img, ImgLayout L, int K,
-                const float* __restrict__ eps, ReplayDev rp, int use_replay, float* __restrict__ obs_out,
+                const float* __restrict__ eps, ReplayDev rp, int use_replay, const int* __restrict__ order,
+                float* __restrict__ obs_out,
                 float* __restrict__ obs_seq, uint8_t* __restrict__ act_seq, float* __restrict__ rew_seq,
                 uint8_t* __restrict__ done_seq) {
   extern __shared__ __align__(16) uint8_t smem[];
@@ -339,8 +340,10 @@ __global__ void __launch_bounds__(512 * MT, 1)
   for (int i = threadIdx.x; i < kRows * L.ld1; i += blockDim.x) X[i] = __float2bfloat16_rn(0.0f);
   const QW w = qw_at(sw, L);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int env = blockIdx.x * kRows + warp;
-  const bool live = env < c.n_envs;
+  // CTAs take envs grouped by map, so that one CTA's scans share cache lines
+  const int slot = blockIdx.x * kRows + warp;
+  const bool live = slot < c.n_envs;
+  const int env = live ? order[slot] : 0;
   const long long n = c.n_envs;
   EnvConst k;
   Env s;
@@ -972,10 +975,12 @@ int sg_rollout_eps_q(sg_sim* sim, int K, sg_qnet* q, const float* eps, sg_replay
   const int mt = q->rollout_mt > 0 ? q->rollout_mt : (waves32 < waves16 ? 2 : 1);
   if (mt == 2)
     k_rollout_q<2><<<(n + 31) / 32, 1024, fwd_smem(q->IL, 32), stream>>>(
-        sim->dc, sg_sim_ptrs(sim), q->img, q->IL, K, eps, rd, rp ? 1 : 0, obs, obs_seq, act_seq, rew_seq, done_seq);
+        sim->dc, sg_sim_ptrs(sim), q->img, q->IL, K, eps, rd, rp ? 1 : 0, sim->map_order_dev, obs, obs_seq, act_seq,
+        rew_seq, done_seq);
   else
     k_rollout_q<1><<<(n + 15) / 16, 512, fwd_smem(q->IL), stream>>>(
-        sim->dc, sg_sim_ptrs(sim), q->img, q->IL, K, eps, rd, rp ? 1 : 0, obs, obs_seq, act_seq, rew_seq, done_seq);
+        sim->dc, sg_sim_ptrs(sim), q->img, q->IL, K, eps, rd, rp ? 1 : 0, sim->map_order_dev, obs, obs_seq, act_seq,
+        rew_seq, done_seq);
   SG_CUDA(cudaGetLastError());
   if (rp) {
     k_replay_advance<<<1, 1, 0, stream>>>(rp->d.steps, K);

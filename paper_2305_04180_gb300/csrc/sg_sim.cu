@@ -18,53 +18,86 @@ using namespace sg;
 
 // ------------------------------------------------------------------ kernels
 
-// Pack one map: warp w of the grid turns 32 cells of a row into one word with
-// a ballot (bit b = cell 32*word + b).  Rows are padded to row_words words.
-__global__ void k_pack_map(const uint8_t* __restrict__ grid, int w, int h, int row_words, uint32_t* __restrict__ out) {
+// ---------------------------------------------------------------- maps
+// Map preprocessing runs over a group of maps staged together on the device:
+// item counts (words, rows, cells) are prefix-summed per map, and every
+// thread finds its map by binary search over the prefix.
+struct PrepMap {
+  long long src;        // first cell of the map in the staging grid
+  long long word_off;   // first word in the bit atlas
+  long long clr_off;    // first byte in the clearance atlas
+  int w, h, row_words, pad;
+};
+
+__device__ __forceinline__ int find_map(const long long* __restrict__ prefix, int n_maps, long long item) {
+  int lo = 0, hi = n_maps - 1;  // largest m with prefix[m] <= item
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= item) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Bits: warp per (map, row word); bit b of the word is cell 32 * word + b (a ballot).
+__global__ void k_pack_maps(const uint8_t* __restrict__ grid, const PrepMap* __restrict__ mp,
+                            const long long* __restrict__ word_prefix, int n_maps, long long total,
+                            uint32_t* __restrict__ atlas) {
   const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  const long long total = (long long)h * row_words;
-  if (gw >= total) return;  // whole warps exit together (gw is warp-uniform)
-  const int cy = (int)(gw / row_words);
-  const int wd = (int)(gw % row_words);
+  if (gw >= total) return;  // warp-uniform
+  const int m = find_map(word_prefix, n_maps, gw);
+  const PrepMap d = mp[m];
+  const long long local = gw - word_prefix[m];
+  const int cy = (int)(local / d.row_words), wd = (int)(local % d.row_words);
   const int cx = wd * 32 + lane;
-  const bool occ = cx < w && grid[(long long)cy * w + cx] != 0;
+  const bool occ = cx < d.w && grid[d.src + (long long)cy * d.w + cx] != 0;
   const uint32_t word = __ballot_sync(kFull, occ);
-  if (lane == 0) out[gw] = word;
+  if (lane == 0) atlas[d.word_off + local] = word;
 }
 
-// Clearance map, pass 1: per row, the distance to the nearest occupied cell
-// of the same row (outside counts as occupied), capped at 255.  One thread
-// per row, two sweeps.
-__global__ void k_clr_rows(const uint8_t* __restrict__ grid, int w, int h, uint8_t* __restrict__ g) {
-  const int cy = blockIdx.x * blockDim.x + threadIdx.x;
-  if (cy >= h) return;
-  const uint8_t* row = grid + (long long)cy * w;
-  uint8_t* out = g + (long long)cy * w;
-  int d = 0;  // distance to the last occupied cell on the left (x = -1 is outside)
-  for (int cx = 0; cx < w; ++cx) {
-    d = row[cx] ? 0 : d + 1;
-    out[cx] = (uint8_t)min(d, 255);
+// Clearance, pass 1: thread per (map, row): distance along the row to the
+// nearest occupied cell (outside counts as occupied), capped at 255.
+__global__ void k_clr_rows(const uint8_t* __restrict__ grid, const PrepMap* __restrict__ mp,
+                           const long long* __restrict__ row_prefix, int n_maps, long long total,
+                           uint8_t* __restrict__ g) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= total) return;
+  const int m = find_map(row_prefix, n_maps, r);
+  const PrepMap d = mp[m];
+  const int cy = (int)(r - row_prefix[m]);
+  const uint8_t* row = grid + d.src + (long long)cy * d.w;
+  uint8_t* out = g + d.src + (long long)cy * d.w;
+  int dist = 0;  // to the last occupied cell on the left (x = -1 is outside)
+  for (int cx = 0; cx < d.w; ++cx) {
+    dist = row[cx] ? 0 : dist + 1;
+    out[cx] = (uint8_t)min(dist, 255);
   }
-  d = 0;
-  for (int cx = w - 1; cx >= 0; --cx) {
-    d = row[cx] ? 0 : d + 1;
-    out[cx] = (uint8_t)min((int)out[cx], min(d, 255));
+  dist = 0;
+  for (int cx = d.w - 1; cx >= 0; --cx) {
+    dist = row[cx] ? 0 : dist + 1;
+    out[cx] = (uint8_t)min((int)out[cx], min(dist, 255));
   }
 }
 
-// Pass 2: Chebyshev distance d(x, y) = min over rows y' of max(g(x, y'), |y - y'|),
-// with the rows above and below the map (outside) at g = 0; capped at 255.
-__global__ void k_clr_cols(const uint8_t* __restrict__ g, int w, int h, uint8_t* __restrict__ clr) {
+// Pass 2: thread per (map, cell): Chebyshev distance
+// d(x, y) = min over rows y' of max(g(x, y'), |y - y'|), with the rows outside
+// the map at g = 0; capped at 255.
+__global__ void k_clr_cols(const uint8_t* __restrict__ g, const PrepMap* __restrict__ mp,
+                           const long long* __restrict__ cell_prefix, int n_maps, long long total,
+                           uint8_t* __restrict__ clr) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (long long)w * h) return;
-  const int cx = (int)(i % w), cy = (int)(i / w);
-  int best = min(min(cy + 1, h - cy), 255);
+  if (i >= total) return;
+  const int m = find_map(cell_prefix, n_maps, i);
+  const PrepMap d = mp[m];
+  const long long local = i - cell_prefix[m];
+  const int cx = (int)(local % d.w), cy = (int)(local / d.w);
+  const uint8_t* col = g + d.src + cx;
+  int best = min(min(cy + 1, d.h - cy), 255);
   for (int dd = 0; dd < best; ++dd) {
-    if (cy - dd >= 0) best = min(best, max((int)g[(long long)(cy - dd) * w + cx], dd));
-    if (cy + dd < h) best = min(best, max((int)g[(long long)(cy + dd) * w + cx], dd));
+    if (cy - dd >= 0) best = min(best, max((int)col[(long long)(cy - dd) * d.w], dd));
+    if (cy + dd < d.h) best = min(best, max((int)col[(long long)(cy + dd) * d.w], dd));
   }
-  clr[i] = (uint8_t)best;
+  clr[d.clr_off + local] = (uint8_t)best;
 }
 
 // Episode 0 of every env; one warp per env.
@@ -336,6 +369,7 @@ static void free_sim(sg_sim* s) {
   cudaFree(s->status_dev);
   cudaFree(s->order_dev);
   cudaFree(s->queue_dev);
+  cudaFree(s->map_order_dev);
   delete s;
 }
 
@@ -378,7 +412,6 @@ extern "C" int sg_sim_create(const sg_sim_config* cfg, int32_t n_maps, const uin
   s->atlas_words = words;
   s->clr_bytes = clr_bytes;
   cudaGetDevice(&s->device);
-  uint8_t* staging = nullptr;
   cudaError_t e = cudaSuccess;
   auto alloc = [&](void** ptr, size_t bytes) {
     if (e != cudaSuccess) return;
@@ -392,37 +425,88 @@ extern "C" int sg_sim_create(const sg_sim_config* cfg, int32_t n_maps, const uin
   alloc((void**)&s->fstate, sizeof(float) * 9 * (size_t)n);
   alloc((void**)&s->ustate, sizeof(uint32_t) * 4 * (size_t)n);
   alloc((void**)&s->status_dev, sizeof(uint32_t));
-  alloc((void**)&staging, max_cells * 2);
+  alloc((void**)&s->map_order_dev, sizeof(int) * n);
+  // maps are preprocessed in groups whose grids fit a staging budget
+  const size_t budget = std::max(max_cells, (size_t)256 << 20);
+  uint8_t* staging = nullptr;  // grids, then per-row distances
+  PrepMap* mp_dev = nullptr;
+  long long* prefix_dev = nullptr;  // [3][n_maps + 1]: words, rows, cells
+  alloc((void**)&staging, budget * 2);
+  alloc((void**)&mp_dev, sizeof(PrepMap) * n_maps);
+  alloc((void**)&prefix_dev, sizeof(long long) * 3 * (n_maps + 1));
   if (e != cudaSuccess) {
     cudaFree(staging);
+    cudaFree(mp_dev);
+    cudaFree(prefix_dev);
     free_sim(s);
     cuda_fail(e, "cudaMalloc");
     return SG_E_OOM;
   }
-  // pack every map on the device (synchronous, default stream)
-  for (int m = 0; m < n_maps && e == cudaSuccess; ++m) {
-    const size_t cells = (size_t)map_w[m] * map_h[m];
-    e = cudaMemcpy(staging, maps_host[m], cells, cudaMemcpyHostToDevice);
+  std::vector<PrepMap> mp;
+  std::vector<long long> pw, pr, pc;
+  int m0 = 0;
+  while (m0 < n_maps && e == cudaSuccess) {
+    mp.clear();
+    pw.assign(1, 0);
+    pr.assign(1, 0);
+    pc.assign(1, 0);
+    size_t used = 0;
+    int m1 = m0;
+    while (m1 < n_maps) {
+      const size_t cells = (size_t)map_w[m1] * map_h[m1];
+      if (m1 > m0 && used + cells > budget) break;
+      PrepMap d;
+      d.src = (long long)used;
+      d.word_off = md[m1].word_off;
+      d.clr_off = md[m1].clr_off;
+      d.w = map_w[m1];
+      d.h = map_h[m1];
+      d.row_words = md[m1].row_words;
+      d.pad = 0;
+      mp.push_back(d);
+      e = cudaMemcpyAsync(staging + used, maps_host[m1], cells, cudaMemcpyHostToDevice, 0);
+      if (e != cudaSuccess) break;
+      used += cells;
+      pw.push_back(pw.back() + (long long)d.row_words * d.h);
+      pr.push_back(pr.back() + d.h);
+      pc.push_back(pc.back() + (long long)cells);
+      ++m1;
+    }
     if (e != cudaSuccess) break;
-    const long long total_words = (long long)md[m].row_words * map_h[m];
-    const long long threads = total_words * 32;
-    const int blocks = (int)((threads + 255) / 256);
-    k_pack_map<<<blocks, 256>>>(staging, map_w[m], map_h[m], md[m].row_words, s->atlas + md[m].word_off);
-    e = cudaGetLastError();
+    const int nm = m1 - m0;
+    e = cudaMemcpyAsync(mp_dev, mp.data(), sizeof(PrepMap) * nm, cudaMemcpyHostToDevice, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(prefix_dev, pw.data(), sizeof(long long) * nm, cudaMemcpyHostToDevice, 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(prefix_dev + n_maps + 1, pr.data(), sizeof(long long) * nm, cudaMemcpyHostToDevice, 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(prefix_dev + 2 * (n_maps + 1), pc.data(), sizeof(long long) * nm, cudaMemcpyHostToDevice, 0);
     if (e != cudaSuccess) break;
-    k_clr_rows<<<(map_h[m] + 127) / 128, 128>>>(staging, map_w[m], map_h[m], staging + max_cells);
-    k_clr_cols<<<(int)((cells + 255) / 256), 256>>>(staging + max_cells, map_w[m], map_h[m], s->clr + md[m].clr_off);
+    const long long tw = pw.back(), tr = pr.back(), tc = pc.back();
+    k_pack_maps<<<(unsigned)((tw * 32 + 255) / 256), 256>>>(staging, mp_dev, prefix_dev, nm, tw, s->atlas);
+    k_clr_rows<<<(unsigned)((tr + 127) / 128), 128>>>(staging, mp_dev, prefix_dev + n_maps + 1, nm, tr,
+                                                       staging + budget);
+    k_clr_cols<<<(unsigned)((tc + 255) / 256), 256>>>(staging + budget, mp_dev, prefix_dev + 2 * (n_maps + 1), nm,
+                                                       tc, s->clr);
     e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();  // the staging buffer is reused by the next group
+    m0 = m1;
   }
+  cudaFree(staging);
+  cudaFree(mp_dev);
+  cudaFree(prefix_dev);
   if (e == cudaSuccess) e = cudaMemcpy(s->maps_dev, md.data(), sizeof(MapDesc) * n_maps, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(s->env_map_dev, env_map, sizeof(int) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    std::vector<int> order((size_t)n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return env_map[a] < env_map[b]; });
+    e = cudaMemcpy(s->map_order_dev, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess && env_beams)
     e = cudaMemcpy(s->env_beams_dev, env_beams, sizeof(int) * n, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(s->fstate, 0, sizeof(float) * 9 * (size_t)n);
   if (e == cudaSuccess) e = cudaMemset(s->ustate, 0, sizeof(uint32_t) * 4 * (size_t)n);
   if (e == cudaSuccess) e = cudaMemset(s->status_dev, 0, sizeof(uint32_t));
-  cudaFree(staging);
   if (e != cudaSuccess) {
     free_sim(s);
     return cuda_fail(e, "sg_sim_create");
