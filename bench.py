@@ -482,6 +482,31 @@ def run_full_loop(flush):
             "ring": f"{tr.replay.capacity} transitions (reserve 32 slots)", "graph_nodes": g.num_nodes()}
 
 
+def _recorded_traffic(n_envs, K):
+    """DRAM bytes per launch of the timed kernel from the committed ncu record,
+    if the kernel sources are unchanged since it was taken (else None)."""
+    import hashlib
+
+    try:
+        rec = {}
+        for line in open(os.path.join(ROOT, "profiles", "roofline_traffic.txt")):
+            line = line.strip()
+            if line and not line.startswith("#"):
+                for tok in line.split(" ") if not line.startswith("command=") else [line]:
+                    if "=" in tok:
+                        k, v = tok.split("=", 1)
+                        rec[k] = v
+        src = b"".join(open(os.path.join(ROOT, "paper_2305_04180_gb300", "csrc", f), "rb").read()
+                       for f in ("sg_device.cuh", "sg_sim.cu"))
+        if hashlib.sha1(src).hexdigest()[:16] != rec.get("source_sha1"):
+            return None
+        if int(rec["n_envs"]) != n_envs or int(rec["steps_per_launch"]) != K:
+            return None
+        return int(rec["dram_bytes_read"]) + int(rec["dram_bytes_write"])
+    except Exception:
+        return None
+
+
 def _measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -524,6 +549,8 @@ def main():
         samples_per_env_step = 1500.0
     out["roofline"] = roofline_alu(samples_per_env_step, n, K, ms_per_step, clk)
     out["roofline"]["samples_per_env_step"] = samples_per_env_step
+    out["roofline"]["traffic"] = _recorded_traffic(n, K)
+    out["roofline"]["traffic_unit"] = "DRAM bytes per launch (ncu record in profiles/)"
     # the streaming view: bytes a step must see if the map window and the SoA
     # state were streamed from HBM every step (the rollout keeps them on chip)
     peaks = _measured_peaks()
