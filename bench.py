@@ -92,6 +92,30 @@ def time_oracle(pool, cores, name, n_envs, K):
     return steps, wall, busy, samples
 
 
+# ------------------------------------------------------------ ranks
+def max_over_ranks(x: float, device="cuda") -> float:
+    """The largest x over all ranks (the job's time is its slowest rank's)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: int, world: int, slowest_s: float) -> float:
+    """Whole-job rate: every rank processes units_per_rank (independent
+    replicas, weak scaling), the job takes the slowest rank's time."""
+    return units_per_rank * world / slowest_s
+
+
+def replica_seed(base: int, rank: int) -> int:
+    """Each rank simulates its own replica of the workload."""
+    return base + 7919 * rank
+
+
 # ------------------------------------------------------------ clocks
 class Clocks:
     """nvidia-smi sampled every 200 ms while the timed region runs."""
@@ -165,7 +189,7 @@ def run_ours(a):
     maps = w.maps()
     sim = Sim(w.params, maps, w.env_map, w.env_beams)
     n = sim.n
-    sim.reset(seed=w.params["seed"] + 7919 * rank)
+    sim.reset(seed=replica_seed(w.params["seed"], rank))
     from paper_2305_04180_gb300.autotune import autotune_rollout
 
     if a.launch:
@@ -209,13 +233,8 @@ def run_ours(a):
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
     ms = [e0.elapsed_time(e1) for e0, e1 in ev]
-    tot_ms = sum(ms)
-    if world > 1:
-        t = torch.tensor([tot_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    env_steps = n * K * a.steps * world
-    value = env_steps / (tot_ms / 1e3)
+    tot_ms = max_over_ranks(sum(ms))
+    value = job_throughput(n * K * a.steps, world, tot_ms / 1e3)
     ms_per_step = tot_ms / a.steps
     st = sim.status()
 
@@ -235,11 +254,7 @@ def run_ours(a):
         rew_h.copy_(rew_seq, non_blocking=True)
         done_h.copy_(done_seq, non_blocking=True)
         torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps)
     h2d = int(f0.nbytes + u0.nbytes)
     d2h = int(rew_h.numel() * 4 + done_h.numel())
 
@@ -274,7 +289,7 @@ def run_ours(a):
                 "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                 "parallelism": "replicas" if world > 1 else "single GPU",
             },
-            "e2e": {"value": n * K * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "e2e": {"value": job_throughput(n * K, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": a.steps,
             "clocks": clk,

@@ -278,6 +278,10 @@ int sg_qnet_get_params(sg_qnet_t q, float* host, int64_t n, int32_t which);
 /* Adam first / second moments (either pointer may be NULL) and the number of
  * optimiser steps taken.  Synchronous. */
 int sg_qnet_get_optimizer(sg_qnet_t q, float* m_host, float* v_host, int64_t n, uint64_t* steps);
+/* Restore the Adam moments and the optimiser step count (checkpoint
+ * resume; with the parameters and the ring restored too, training continues
+ * bit-identically).  Synchronous. */
+int sg_qnet_set_optimizer(sg_qnet_t q, const float* m_host, const float* v_host, int64_t n, uint64_t steps);
 
 /*
  * Envs per CTA of the fused rollout: 16 or 32 (one warp each; the network's
@@ -325,6 +329,11 @@ int sg_replay_info(sg_replay_t r, int64_t* capacity, uint64_t* steps_recorded, v
  * Synchronous. */
 int sg_replay_read(sg_replay_t r, int64_t first, int64_t count, float* s_host, float* s2_host, uint8_t* a_host,
                    float* r_host, uint8_t* term_host);
+/* Write ring entries [first, first + count) from host arrays (all five
+ * required when count > 0) and set the recorded-step counter (checkpoint
+ * resume).  Synchronous. */
+int sg_replay_write(sg_replay_t r, int64_t first, int64_t count, const float* s_host, const float* s2_host,
+                    const uint8_t* a_host, const float* r_host, const uint8_t* term_host, uint64_t steps_recorded);
 
 /*
  * One optimisation step of the learner (Alg. 2 steps 1-2 with DDQN): sample

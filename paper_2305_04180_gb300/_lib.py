@@ -74,6 +74,7 @@ SIGNATURES = {
     "sg_qnet_set_params": (C.c_int, [_vp, _vp, C.c_int64, _i32]),
     "sg_qnet_get_params": (C.c_int, [_vp, _vp, C.c_int64, _i32]),
     "sg_qnet_get_optimizer": (C.c_int, [_vp, _vp, _vp, C.c_int64, _vp]),
+    "sg_qnet_set_optimizer": (C.c_int, [_vp, _vp, _vp, C.c_int64, C.c_uint64]),
     "sg_qnet_set_rollout_rows": (C.c_int, [_vp, _i32]),
     "sg_qnet_copy_params": (C.c_int, [_vp, _vp, _vp]),
     "sg_qnet_forward": (C.c_int, [_vp, _vp, _i32, _vp, _vp]),
@@ -81,6 +82,7 @@ SIGNATURES = {
     "sg_replay_destroy": (C.c_int, [_vp]),
     "sg_replay_info": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "sg_replay_read": (C.c_int, [_vp, C.c_int64, C.c_int64, _vp, _vp, _vp, _vp, _vp]),
+    "sg_replay_write": (C.c_int, [_vp, C.c_int64, C.c_int64, _vp, _vp, _vp, _vp, _vp, C.c_uint64]),
     "sg_td_train_step": (C.c_int, [_vp, _vp, _i32, C.c_float, C.c_float, _i32, C.c_uint64, _vp, _vp, _vp]),
     "sg_td_grad_noalloc": (C.c_int, [_vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _i32, C.c_float, _vp, _vp, _vp]),
     "sg_graph_begin": (C.c_int, [_vp]),

@@ -867,6 +867,17 @@ extern "C" int sg_qnet_copy_params(sg_qnet_t dst, sg_qnet_t src, sg_stream_t str
   return SG_OK;
 }
 
+extern "C" int sg_qnet_set_optimizer(sg_qnet_t q, const float* m_host, const float* v_host, int64_t n,
+                                     uint64_t steps) {
+  if (!q || !m_host || !v_host || n != q->PL.total) return SG_E_INVAL;
+  SG_CUDA(cudaDeviceSynchronize());
+  SG_CUDA(cudaMemcpy(q->adam_m, m_host, (size_t)n * 4, cudaMemcpyHostToDevice));
+  SG_CUDA(cudaMemcpy(q->adam_v, v_host, (size_t)n * 4, cudaMemcpyHostToDevice));
+  const unsigned long long st = steps;
+  SG_CUDA(cudaMemcpy(q->step, &st, 8, cudaMemcpyHostToDevice));
+  return SG_OK;
+}
+
 extern "C" int sg_qnet_forward(sg_qnet_t q, const float* obs_dev, int32_t M, float* q_dev, sg_stream_t stream) {
   if (!q || !obs_dev || !q_dev || M < 1) return SG_E_INVAL;
   k_qnet_forward<<<(M + kTile - 1) / kTile, kThreads, fwd_smem(q->IL), stream>>>(q->img, q->IL, obs_dev, M, q_dev);
@@ -954,6 +965,25 @@ extern "C" int sg_replay_read(sg_replay_t r, int64_t first, int64_t count, float
   if (a_host) SG_CUDA(cudaMemcpy(a_host, r->d.a + first, count, cudaMemcpyDeviceToHost));
   if (r_host) SG_CUDA(cudaMemcpy(r_host, r->d.r + first, count * 4, cudaMemcpyDeviceToHost));
   if (term_host) SG_CUDA(cudaMemcpy(term_host, r->d.term + first, count, cudaMemcpyDeviceToHost));
+  return SG_OK;
+}
+
+extern "C" int sg_replay_write(sg_replay_t r, int64_t first, int64_t count, const float* s_host, const float* s2_host,
+                               const uint8_t* a_host, const float* r_host, const uint8_t* term_host,
+                               uint64_t steps_recorded) {
+  if (!r || first < 0 || count < 0 || first + count > r->cap) return SG_E_INVAL;
+  if (count > 0 && (!s_host || !s2_host || !a_host || !r_host || !term_host)) return SG_E_INVAL;
+  SG_CUDA(cudaDeviceSynchronize());
+  const size_t od = (size_t)r->d.obs_dim;
+  if (count > 0) {
+    SG_CUDA(cudaMemcpy(r->d.s + first * od, s_host, count * od * 4, cudaMemcpyHostToDevice));
+    SG_CUDA(cudaMemcpy(r->d.s2 + first * od, s2_host, count * od * 4, cudaMemcpyHostToDevice));
+    SG_CUDA(cudaMemcpy(r->d.a + first, a_host, count, cudaMemcpyHostToDevice));
+    SG_CUDA(cudaMemcpy(r->d.r + first, r_host, count * 4, cudaMemcpyHostToDevice));
+    SG_CUDA(cudaMemcpy(r->d.term + first, term_host, count, cudaMemcpyHostToDevice));
+  }
+  const unsigned long long st = steps_recorded;
+  SG_CUDA(cudaMemcpy(r->d.steps, &st, 8, cudaMemcpyHostToDevice));
   return SG_OK;
 }
 

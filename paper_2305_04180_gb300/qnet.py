@@ -73,6 +73,23 @@ class QNet:
         """This network's online weights <- src's (model upload), stream-ordered."""
         check(self.L.sg_qnet_copy_params(self.handle, src.handle, _stream(stream)), "sg_qnet_copy_params")
 
+    def set_optimizer_state(self, m, v, steps: int):
+        m = np.ascontiguousarray(m, np.float32)
+        v = np.ascontiguousarray(v, np.float32)
+        check(self.L.sg_qnet_set_optimizer(self.handle, m.ctypes.data, v.ctypes.data, self.n_params, int(steps)),
+              "sg_qnet_set_optimizer")
+
+    def state_dict(self):
+        """Everything needed to resume learning: online and target
+        parameters, Adam moments, optimiser step count."""
+        m, v, steps = self.optimizer_state()
+        return dict(online=self.get_params("online"), target=self.get_params("target"), m=m, v=v, steps=steps)
+
+    def load_state_dict(self, d):
+        self.set_params(d["online"], "online")
+        self.set_params(d["target"], "target")
+        self.set_optimizer_state(d["m"], d["v"], d["steps"])
+
     def forward(self, obs: torch.Tensor, out=None, stream=None) -> torch.Tensor:
         assert obs.is_cuda and obs.dtype == torch.float32 and obs.shape[1] == self.n_in
         obs = obs.contiguous()
@@ -118,6 +135,19 @@ class Replay:
         v = C.c_uint64()
         check(self.L.sg_replay_info(self.handle, None, C.byref(v), None, None, None, None, None), "sg_replay_info")
         return int(v.value)
+
+    def write(self, first: int, s, s2, a, r, t, steps_recorded: int):
+        """Write entries [first, first+len(a)) and set the recorded-step count."""
+        arrs = [np.ascontiguousarray(x, dt) for x, dt in ((s, np.float32), (s2, np.float32), (a, np.uint8),
+                                                          (r, np.float32), (t, np.uint8))]
+        check(self.L.sg_replay_write(self.handle, int(first), int(arrs[2].size), *[x.ctypes.data for x in arrs],
+                                     int(steps_recorded)), "sg_replay_write")
+
+    def state_dict(self):
+        return dict(entries=self.read(0, self.capacity), steps=self.steps_recorded())
+
+    def load_state_dict(self, d):
+        self.write(0, *d["entries"], steps_recorded=d["steps"])
 
     def read(self, first: int, count: int):
         """Host copies (s, s2, a, r, term) of entries [first, first+count)."""

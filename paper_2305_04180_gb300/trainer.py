@@ -41,6 +41,24 @@ class ColorTrainer:
         self.s_learner = torch.cuda.Stream() if two_streams else torch.cuda.current_stream()
         self.loss = torch.zeros(1, device="cuda")
 
+    def state_dict(self):
+        """Checkpoint of the whole loop: env state, both networks with the
+        learner's optimiser, the ring, and the loop counters.  The
+        configuration (parameters, maps, seeds) is not part of it: restore
+        into a loop built with the same configuration."""
+        torch.cuda.synchronize()
+        return dict(sim=self.sim.get_state(), learner=self.learner.state_dict(),
+                    actor=self.actor.get_params("online"), replay=self.replay.state_dict(),
+                    counters=(self.updates, self.transitions, self._carry))
+
+    def load_state_dict(self, d):
+        torch.cuda.synchronize()
+        self.sim.set_state(*d["sim"])
+        self.learner.load_state_dict(d["learner"])
+        self.actor.set_params(d["actor"], "online")
+        self.replay.load_state_dict(d["replay"])
+        self.updates, self.transitions, self._carry = d["counters"]
+
     def steps_per_vec_step(self):
         """Optimisation steps per vectorized step (Eq. 2): N * TPS / B."""
         return self.sim.n * self.tps / self.batch

@@ -92,7 +92,7 @@ def test_graph_replay_equals_direct_calls():
     assert ua[2, 0] == 3 * 64  # 3 replays x 4 rollouts x 16 steps
 
 
-def _trainer(sim_seed=3):
+def _trainer(sim_seed=3, two_streams=True):
     from paper_2305_04180_gb300 import Sim
     from paper_2305_04180_gb300.trainer import ColorTrainer
 
@@ -100,7 +100,7 @@ def _trainer(sim_seed=3):
     maps = [make_map(s) for s in range(1, 5)]
     sim = Sim(dict(p, seed=sim_seed), maps, (np.arange(64) % 4).astype(np.int32))
     sim.reset()
-    return ColorTrainer(sim, batch=128, slots=32, lr=5e-4, learn_start=0, two_streams=True, seed=2)
+    return ColorTrainer(sim, batch=128, slots=32, lr=5e-4, tps=8, learn_start=0, two_streams=two_streams, seed=2)
 
 
 def test_graph_actor_learner_iteration_sequential_is_deterministic():
@@ -154,3 +154,24 @@ def test_autotune_applies_a_candidate_and_results_do_not_change(tmp_path):
     assert np.array_equal(bits(_run(a, 20)["rew"]), bits(_run(b, 20)["rew"]))
     again = autotune_rollout(a, K=8, reps=1, cache_path=cache)
     assert again["cached"] and again["config"] == res["config"]
+
+
+def test_checkpoint_resume_is_bit_identical():
+    """Train, checkpoint the whole loop (env state, networks, Adam moments,
+    ring, counters), continue; a loop with the same configuration that has
+    drifted elsewhere, restored from the checkpoint, continues to exactly the
+    same parameters and env state."""
+    ta = _trainer(sim_seed=6, two_streams=False)
+    ta.run(48, rollout_k=8)
+    ck = ta.state_dict()
+    ta.run(40, rollout_k=8)
+    tb = _trainer(sim_seed=6, two_streams=False)
+    tb.run(24, rollout_k=8)  # somewhere else; the checkpoint overwrites all of it
+    tb.load_state_dict(ck)
+    tb.run(40, rollout_k=8)
+    assert np.array_equal(ta.learner.get_params(), tb.learner.get_params())
+    assert np.array_equal(ta.learner.get_params("target"), tb.learner.get_params("target"))
+    fa, ua = ta.sim.get_state()
+    fb, ub = tb.sim.get_state()
+    assert np.array_equal(bits(fa), bits(fb)) and np.array_equal(ua, ub)
+    assert ta.updates == tb.updates and ta.replay.steps_recorded() == tb.replay.steps_recorded()
