@@ -197,12 +197,17 @@ int sg_sim_rollout(sg_sim_t sim, int32_t K, int32_t policy, sg_qnet_t qnet, cons
  *                    limit).
  *   order_mode       0: envs in index order; 1: work list sorted by cost
  *                    (beams x map size), longest first.
- *   warps_per_env    1..16 (not with persistent): W warps share one env.  With
+ *   warps_per_env    W in 1..16 (W > 1 not with persistent): W warps share one env.  With
  *                    random actions the pose chain (motion, collision,
  *                    arrival, AutoReset draws) never depends on the LiDAR, so
  *                    every warp replays it and warp w computes the scans,
  *                    observations and rewards of the steps i = w (mod W).  A
  *                    CTA then holds max(1, warps_per_block / W) envs.
+ *                    -P (P in 1..15): pipelined instead: one warp computes the
+ *                    pose chain of 32-step chunks into shared memory and P
+ *                    warps compute the scans, observations and rewards of the
+ *                    previous chunk; a CTA holds max(1, warps_per_block /
+ *                    (1 + P)) envs.
  * Synchronous (computes and uploads the work list on first use).
  */
 int sg_sim_set_launch(sg_sim_t sim, int32_t warps_per_block, int32_t persistent, int32_t blocks_per_sm,

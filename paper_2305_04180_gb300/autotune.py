@@ -21,7 +21,10 @@ CANDIDATES = ([dict(warps_per_block=w, persistent=p, order=o, warps_per_env=1)
                for w in (2, 4, 8, 16) for p in (False, True) for o in ("index", "cost")
                if not (o == "cost" and not p)]
               + [dict(warps_per_block=8, persistent=False, order="index", warps_per_env=W)
-                 for W in (2, 3, 4, 6, 8)])
+                 for W in (2, 3, 4, 6, 8)]
+              # pipelined: one pose warp and P observation warps per env
+              + [dict(warps_per_block=b, persistent=False, order="index", warps_per_env=-P)
+                 for P, b in ((2, 8), (3, 8), (4, 16), (5, 16), (7, 16))])
 KEYS = ("warps_per_block", "persistent", "order", "warps_per_env")
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 

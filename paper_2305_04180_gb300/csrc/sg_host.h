@@ -30,6 +30,7 @@ struct sg_sim {
   int persistent_blocks = 0;
   int order_mode = 0;
   int warps_per_env = 1;
+  int pipe_obs_warps = 0;  // > 0: pipelined rollout with this many observation warps per env
   int* order_dev = nullptr;      // work list (cost-sorted env indices) or null
   int* map_order_dev = nullptr;  // env indices grouped by map (stable), for per-CTA map locality
   unsigned* queue_dev = nullptr; // work-list cursor of the persistent kernel

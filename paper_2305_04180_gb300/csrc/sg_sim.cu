@@ -202,6 +202,103 @@ __device__ __forceinline__ void rollout_env_split(const DevCfg& c, const SimPtrs
   if (w == 0 && lane == 0) store_env(p, env, s);
 }
 
+// Pipelined variant: per env, one pose warp computes the state chain of a
+// chunk of kPipeChunk steps into a shared-memory record buffer while P
+// observation warps compute scans, observations and rewards of the previous
+// chunk (step i of a chunk by observation warp i mod P); the 1 + P warps of
+// an env meet at a named barrier once per chunk (double buffering).  The pose
+// chain runs once instead of once per warp.
+constexpr int kPipeChunk = 32;
+
+struct __align__(16) StepRec {
+  Env pre;         // after the motion, before a reset
+  Env post;        // the state the step ends in (reset when done)
+  uint32_t done;
+  uint32_t a;
+};
+static_assert(sizeof(StepRec) == 112, "step record is seven 16-byte words");
+
+__device__ __forceinline__ void named_barrier(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+__device__ __forceinline__ uint32_t fbits(float f) { return __float_as_uint(f); }
+
+// Lane 0 writes the record as seven 16-byte stores (all lanes hold the same
+// values).
+__device__ __forceinline__ void store_rec(StepRec* r, const Env& q, const Env& e, uint32_t done, uint32_t a,
+                                          int lane) {
+  if (lane != 0) return;
+  uint4* d = reinterpret_cast<uint4*>(r);
+  d[0] = make_uint4(fbits(q.x), fbits(q.y), fbits(q.phi), fbits(q.vl));
+  d[1] = make_uint4(fbits(q.va), fbits(q.dt), fbits(q.K), fbits(q.cap));
+  d[2] = make_uint4(fbits(q.sigma), q.ep_step, q.ep_id, q.t);
+  d[3] = make_uint4(q.fifo, fbits(e.x), fbits(e.y), fbits(e.phi));
+  d[4] = make_uint4(fbits(e.vl), fbits(e.va), fbits(e.dt), fbits(e.K));
+  d[5] = make_uint4(fbits(e.cap), fbits(e.sigma), e.ep_step, e.ep_id);
+  d[6] = make_uint4(e.t, e.fifo, done, a);
+}
+
+__global__ void __launch_bounds__(512, 2) k_rollout_random_pipe(const __grid_constant__ DevCfg c, SimPtrs p, int K,
+                                                                int P, float* __restrict__ obs,
+                                                                float* __restrict__ obs_seq,
+                                                                uint8_t* __restrict__ act_seq,
+                                                                float* __restrict__ rew_seq,
+                                                                uint8_t* __restrict__ done_seq) {
+  extern __shared__ __align__(16) unsigned char pipe_smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int G = 1 + P;  // warps per env
+  const int group = warp / G, role = warp % G;
+  const int E = blockDim.x / (32 * G);
+  const int env = blockIdx.x * E + group;
+  if (env >= c.n_envs) return;  // the whole group leaves together
+  StepRec* recs = reinterpret_cast<StepRec*>(pipe_smem) + (size_t)group * 2 * kPipeChunk;
+  const int bar = 1 + group, nthr = 32 * G;
+  const EnvConst k = env_const(c, p, env, lane);
+  const long long n = c.n_envs;
+  const int chunks = (K + kPipeChunk - 1) / kPipeChunk;
+  Env s, pre;
+  uint64_t akey = 0;
+  uint32_t abatch = 0;
+  if (role == 0) {
+    s = load_env(p, env);
+    akey = sm_at(sm_at(c.seed, kStreamAction), (uint64_t)env);
+  }
+  ObsRegs o;
+  o.b0 = o.b1 = o.ex = 0.0f;
+  for (int ch = 0; ch <= chunks; ++ch) {
+    if (role == 0 && ch < chunks) {
+      StepRec* buf = recs + (ch & 1) * kPipeChunk;
+      const int i0 = ch * kPipeChunk, i1 = min(K, i0 + kPipeChunk);
+      for (int i = i0; i < i1; ++i) {
+        if ((i & 31) == 0) abatch = random_action_for(c, akey, s.t + (uint32_t)lane);
+        const uint32_t a = __shfl_sync(kFull, abatch, i & 31);
+        const uint32_t done = pose_step(c, p, k, s, pre, a, lane, true);
+        store_rec(buf + (i - i0), pre, s, done, a, lane);
+      }
+    } else if (role > 0 && ch >= 1) {
+      const StepRec* buf = recs + ((ch - 1) & 1) * kPipeChunk;
+      const int i0 = (ch - 1) * kPipeChunk, i1 = min(K, i0 + kPipeChunk);
+      for (int i = i0 + role - 1; i < i1; i += P) {
+        const StepRec& r = buf[i - i0];
+        const Env post = r.post, rpre = r.pre;
+        const uint32_t done = r.done, a = r.a;
+        const float rew = obs_step(c, k, post, rpre, done, lane, o);
+        if (obs_seq) write_obs(obs_seq + ((long long)i * n + env) * c.obs_dim, o, c.B, lane);
+        if (lane == 0) {
+          if (act_seq) act_seq[i * n + env] = (uint8_t)a;
+          if (rew_seq) rew_seq[i * n + env] = rew;
+          if (done_seq) done_seq[i * n + env] = (uint8_t)done;
+        }
+      }
+    }
+    named_barrier(bar, nthr);
+  }
+  if (role > 0 && obs && (K - 1 - (chunks - 1) * kPipeChunk) % P == role - 1)
+    write_obs(obs + (long long)env * c.obs_dim, o, c.B, lane);
+  if (role == 0 && lane == 0) store_env(p, env, s);
+}
+
 // W warps per env, E envs per CTA (blockDim = 32 W E).
 __global__ void __launch_bounds__(256, 4) k_rollout_random_split(const __grid_constant__ DevCfg c, SimPtrs p, int K,
                                                               int W, float* __restrict__ obs,
@@ -568,7 +665,14 @@ extern "C" int sg_sim_rollout(sg_sim_t sim, int32_t K, int32_t policy, sg_qnet_t
   if (policy == SG_POLICY_RANDOM) {
     if (replay) return SG_E_INVAL;  // transitions are recorded by the Q-policy rollout
     const int wpb = sim->warps_per_block;
-    if (sim->warps_per_env > 1) {
+    if (sim->pipe_obs_warps > 0) {
+      const int G = 1 + sim->pipe_obs_warps;
+      const int E = wpb / G > 0 ? wpb / G : 1;
+      const size_t smem = (size_t)E * 2 * kPipeChunk * sizeof(StepRec);
+      k_rollout_random_pipe<<<(sim->dc.n_envs + E - 1) / E, 32 * G * E, smem, stream>>>(
+          sim->dc, sg_sim_ptrs(sim), K, sim->pipe_obs_warps, obs_dev, obs_seq_dev, act_seq_dev, rew_seq_dev,
+          done_seq_dev);
+    } else if (sim->warps_per_env > 1) {
       const int W = sim->warps_per_env;
       const int E = wpb / W > 0 ? wpb / W : 1;
       k_rollout_random_split<<<(sim->dc.n_envs + E - 1) / E, 32 * W * E, 0, stream>>>(
@@ -596,7 +700,9 @@ extern "C" int sg_sim_rollout(sg_sim_t sim, int32_t K, int32_t policy, sg_qnet_t
 extern "C" int sg_sim_set_launch(sg_sim_t sim, int32_t warps_per_block, int32_t persistent, int32_t blocks_per_sm,
                                  int32_t order_mode, int32_t warps_per_env) {
   if (!sim) return SG_E_INVAL;
-  if (warps_per_env < 1 || warps_per_env > 16 || (warps_per_env > 1 && persistent)) return SG_E_INVAL;
+  // warps_per_env < 0: the pipelined kernel with -warps_per_env observation warps
+  if (warps_per_env == 0 || warps_per_env > 16 || warps_per_env < -15 || (warps_per_env != 1 && persistent))
+    return SG_E_INVAL;
   if (warps_per_block != 1 && warps_per_block != 2 && warps_per_block != 4 && warps_per_block != 8 &&
       warps_per_block != 16)
     return SG_E_INVAL;
@@ -632,7 +738,8 @@ extern "C" int sg_sim_set_launch(sg_sim_t sim, int32_t warps_per_block, int32_t 
   sim->persistent = persistent;
   sim->persistent_blocks = persistent ? bps * sms : 0;
   sim->order_mode = order_mode;
-  sim->warps_per_env = warps_per_env;
+  sim->warps_per_env = warps_per_env > 0 ? warps_per_env : 1;
+  sim->pipe_obs_warps = warps_per_env < 0 ? -warps_per_env : 0;
   if (order_mode == 0 && sim->order_dev) {
     SG_CUDA(cudaFree(sim->order_dev));
     sim->order_dev = nullptr;

@@ -40,7 +40,8 @@ def test_uneven_launch_configurations_agree_and_match_oracle():
     K = 50
     results = []
     for cfg in (None, (8, True, "cost", 1), (2, False, "index", 1), (16, True, "index", 1), (8, False, "index", 3),
-                (8, False, "index", 4), (8, False, "index", 8), (4, False, "index", 5)):
+                (8, False, "index", 4), (8, False, "index", 8), (4, False, "index", 5), (8, False, "index", -3),
+                (16, False, "index", -4), (4, False, "index", -1), (16, False, "index", -7)):
         s = Sim(p, maps, env_map, beams)
         if cfg:
             s.set_launch(cfg[0], cfg[1], 0, cfg[2], cfg[3])
