@@ -49,7 +49,8 @@ def parse():
     ap.add_argument("--extras", default="qnet,td,step,uneven,full",
                     help="comma list of secondary measurements: qnet, td, step, uneven, full")
     ap.add_argument("--launch", default=None,
-                    help="fixed rollout launch 'warps_per_block,persistent,order,warps_per_env' (skips the autotuner)")
+                    help="fixed rollout launch 'kernel:key=val,...' e.g. 'lanes:envs_per_block=4,obs_warps=15,chunk=16'"
+                         " (skips the autotuner)")
     return ap.parse_args()
 
 
@@ -193,12 +194,12 @@ def run_ours(a):
     from paper_2305_04180_gb300.autotune import autotune_rollout
 
     if a.launch:
-        wpb, pers, order, wpe = a.launch.split(",")
-        tune = {"config": dict(warps_per_block=int(wpb), persistent=bool(int(pers)), order=order,
-                               warps_per_env=int(wpe))}
-        sim.set_launch(int(wpb), bool(int(pers)), 0, order, int(wpe))
+        kernel, _, rest = a.launch.partition(":")
+        kw = {k: (v if k == "order" else int(v)) for k, v in (t.split("=") for t in rest.split(",") if t)}
+        sim.set_launch(kernel, **kw)
+        tune = {"config": sim.launch_config()}
     else:
-        tune = autotune_rollout(sim, K=64, reps=2, cache_path=None)  # untimed; restores the env state
+        tune = autotune_rollout(sim, K=512, reps=2, cache_path=None)  # untimed; restores the env state
     obs = sim.new_obs()
     obs_seq = torch.empty((K, n, sim.obs_dim), dtype=torch.float32, device="cuda")
     rew_seq = torch.empty((K, n), dtype=torch.float32, device="cuda")
@@ -443,7 +444,7 @@ def run_uneven(flush):
     build_s = time.perf_counter() - t0
     sim.reset()
     K = w.steps
-    tune = autotune_rollout(sim, K=16, reps=2, cache_path=None)
+    tune = autotune_rollout(sim, K=64, reps=2, cache_path=None)
     rew = torch.empty((K, sim.n), device="cuda")
     done = torch.empty((K, sim.n), dtype=torch.uint8, device="cuda")
     st = torch.cuda.Stream()

@@ -189,29 +189,50 @@ int sg_sim_rollout(sg_sim_t sim, int32_t K, int32_t policy, sg_qnet_t qnet, cons
 
 /*
  * Launch configuration of the network-free rollout (uneven batching and the
- * autotuner; results do not depend on it):
- *   warps_per_block  1, 2, 4 (default), 8 or 16 envs per CTA (one warp each).
- *   persistent       0: one warp per env; 1: a fixed grid of warps pulls envs
- *                    from a work list through a device counter.
- *   blocks_per_sm    CTAs per SM of the persistent grid (0 = the occupancy
- *                    limit).
- *   order_mode       0: envs in index order; 1: work list sorted by cost
- *                    (beams x map size), longest first.
- *   warps_per_env    W in 1..16 (W > 1 not with persistent): W warps share one env.  With
- *                    random actions the pose chain (motion, collision,
- *                    arrival, AutoReset draws) never depends on the LiDAR, so
- *                    every warp replays it and warp w computes the scans,
- *                    observations and rewards of the steps i = w (mod W).  A
- *                    CTA then holds max(1, warps_per_block / W) envs.
- *                    -P (P in 1..15): pipelined instead: one warp computes the
- *                    pose chain of 32-step chunks into shared memory and P
- *                    warps compute the scans, observations and rewards of the
- *                    previous chunk; a CTA holds max(1, warps_per_block /
- *                    (1 + P)) envs.
+ * autotuner).  Results never depend on it: every kernel computes the same
+ * float32 step.  kernel:
+ *   SG_ROLLOUT_GRID   one warp per env, warps_per_block envs per CTA
+ *                     (1, 2, 4 (default), 8, 16).
+ *   SG_ROLLOUT_QUEUE  a persistent grid of warps_per_block-warp CTAs
+ *                     (blocks_per_sm per SM, 0 = the occupancy limit) pulls
+ *                     envs from a work list through a device counter; order
+ *                     0 = index order, 1 = sorted by cost (beams x map size),
+ *                     longest first.
+ *   SG_ROLLOUT_SPLIT  warps_per_env (2..16) warps share one env: with random
+ *                     actions the pose chain (motion, collision, arrival,
+ *                     AutoReset draws) never depends on the LiDAR, so every
+ *                     warp replays it and warp w computes the scans,
+ *                     observations and rewards of the steps i = w (mod W);
+ *                     max(1, warps_per_block / W) envs per CTA.
+ *   SG_ROLLOUT_PIPE   per env one warp computes the pose chain of 32-step
+ *                     chunks into shared memory and obs_warps (1..15) warps
+ *                     compute the scans, observations and rewards of the
+ *                     previous chunk; max(1, warps_per_block / (1 + obs_warps))
+ *                     envs per CTA.
+ *   SG_ROLLOUT_LANES  per CTA one warp computes the pose chains of
+ *                     envs_per_block (1..32) envs, one env per lane, in chunks
+ *                     of `chunk` steps (1..256) into shared memory, and
+ *                     obs_warps (1..31) warps compute the observation records
+ *                     of the previous chunk.
  * Synchronous (computes and uploads the work list on first use).
  */
-int sg_sim_set_launch(sg_sim_t sim, int32_t warps_per_block, int32_t persistent, int32_t blocks_per_sm,
-                      int32_t order_mode, int32_t warps_per_env);
+#define SG_ROLLOUT_GRID 0
+#define SG_ROLLOUT_QUEUE 1
+#define SG_ROLLOUT_SPLIT 2
+#define SG_ROLLOUT_PIPE 3
+#define SG_ROLLOUT_LANES 4
+typedef struct sg_launch {
+  int32_t kernel;
+  int32_t warps_per_block;
+  int32_t warps_per_env;
+  int32_t obs_warps;
+  int32_t envs_per_block;
+  int32_t blocks_per_sm;
+  int32_t order;
+  int32_t chunk;
+} sg_launch;
+int sg_sim_set_launch(sg_sim_t sim, const sg_launch* cfg);
+int sg_sim_get_launch(sg_sim_t sim, sg_launch* cfg);
 
 /*
  * Copy the complete env state to / from host memory (checkpoint / resume;

@@ -46,6 +46,15 @@ class sg_sim_config(C.Structure):
     ]
 
 
+class sg_launch(C.Structure):
+    _fields_ = [("kernel", C.c_int32), ("warps_per_block", C.c_int32), ("warps_per_env", C.c_int32),
+                ("obs_warps", C.c_int32), ("envs_per_block", C.c_int32), ("blocks_per_sm", C.c_int32),
+                ("order", C.c_int32), ("chunk", C.c_int32)]
+
+
+SG_ROLLOUT_KERNELS = {"grid": 0, "queue": 1, "split": 2, "pipe": 3, "lanes": 4}
+
+
 class sg_sim_info(C.Structure):
     _fields_ = [("n_envs", C.c_int32), ("n_beams", C.c_int32), ("obs_dim", C.c_int32), ("n_maps", C.c_int32),
                 ("atlas_words", C.c_int64), ("state_bytes", C.c_int64), ("device", C.c_int32),
@@ -62,7 +71,8 @@ SIGNATURES = {
     "sg_sim_reset": (C.c_int, [_vp, C.c_uint64, _vp, _vp]),
     "sg_sim_step": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "sg_sim_rollout": (C.c_int, [_vp, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
-    "sg_sim_set_launch": (C.c_int, [_vp, _i32, _i32, _i32, _i32, _i32]),
+    "sg_sim_set_launch": (C.c_int, [_vp, _vp]),
+    "sg_sim_get_launch": (C.c_int, [_vp, _vp]),
     "sg_sim_get_state": (C.c_int, [_vp, _vp, _vp]),
     "sg_sim_set_state": (C.c_int, [_vp, _vp, C.c_size_t]),
     "sg_sim_get_atlas": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),

@@ -1,8 +1,8 @@
 """Autotuner of the network-free rollout's launch configuration.
 
-For a given simulator it times every candidate (envs per CTA, warps per
-env, one warp per env vs a persistent work-list grid, index vs cost-sorted
-work list) on short rollouts, restoring the env state after each trial, and applies the fastest.
+For a given simulator it times every candidate (kernel variant: one warp
+per env, persistent work-list grid, warps sharing an env, pose/observation
+pipelines; envs per CTA and warps per env) on short rollouts, restoring the env state after each trial, and applies the fastest.
 Results are cached as JSON per (device, workload signature, rollout length),
 so later runs of the same workload reuse them without timing.  The choice
 never changes the results, only their speed.
@@ -17,15 +17,21 @@ import os
 import numpy as np
 import torch
 
-CANDIDATES = ([dict(warps_per_block=w, persistent=p, order=o, warps_per_env=1)
-               for w in (2, 4, 8, 16) for p in (False, True) for o in ("index", "cost")
-               if not (o == "cost" and not p)]
-              + [dict(warps_per_block=8, persistent=False, order="index", warps_per_env=W)
-                 for W in (2, 3, 4, 6, 8)]
-              # pipelined: one pose warp and P observation warps per env
-              + [dict(warps_per_block=b, persistent=False, order="index", warps_per_env=-P)
-                 for P, b in ((2, 8), (3, 8), (4, 16), (5, 16), (7, 16))])
-KEYS = ("warps_per_block", "persistent", "order", "warps_per_env")
+def _cand(kernel, **kw):
+    d = dict(kernel=kernel, warps_per_block=4, warps_per_env=1, obs_warps=0, envs_per_block=0, blocks_per_sm=0,
+             order="index", chunk=32)
+    d.update(kw)
+    return d
+
+
+CANDIDATES = ([_cand("grid", warps_per_block=w) for w in (2, 4, 8)]
+              + [_cand("queue", warps_per_block=w, order=o) for w in (2, 4, 8) for o in ("index", "cost")]
+              + [_cand("split", warps_per_block=8, warps_per_env=W) for W in (2, 3, 4)]
+              + [_cand("pipe", warps_per_block=b, obs_warps=P) for P, b in ((3, 8), (5, 16), (7, 16))]
+              + [_cand("lanes", envs_per_block=E, obs_warps=P, chunk=D)
+                 for E, P, D in ((2, 7, 32), (4, 15, 16), (4, 11, 16), (8, 15, 16), (2, 15, 32), (1, 7, 32))])
+KEYS = ("kernel", "warps_per_block", "warps_per_env", "obs_warps", "envs_per_block", "blocks_per_sm", "order",
+        "chunk")
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
 
@@ -64,7 +70,7 @@ def save_cache(path: str, cache: dict) -> None:
 
 
 def _apply(sim, cfg):
-    sim.set_launch(cfg["warps_per_block"], cfg["persistent"], 0, cfg["order"], cfg.get("warps_per_env", 1))
+    sim.set_launch(**{k: cfg[k] for k in KEYS})
 
 
 def _time_config(sim, cfg, K, reps, state):

@@ -67,6 +67,7 @@ struct SimPtrs {
 struct Env {
   float x, y, phi, vl, va, dt, K, cap, sigma;
   uint32_t ep_step, ep_id, t, fifo;  // fifo: q0 | q1 << 8 | delay << 16
+  float sphi, cphi;                  // f_sincos(phi), kept with phi (not stored)
 };
 
 // ------------------------------------------------------------- RNG
@@ -192,6 +193,7 @@ __device__ __forceinline__ Env load_env(const SimPtrs& p, int i) {
   s.ep_id = p.u[1 * n + i];
   s.t = p.u[2 * n + i];
   s.fifo = p.u[3 * n + i];
+  f_sincos(s.phi, s.sphi, s.cphi);
   return s;
 }
 
@@ -241,18 +243,20 @@ __device__ __forceinline__ Layout layout_of(const DevCfg& c, const MapDesc& m) {
 // samples k+1 .. k+c-2 all lie in free cells and the next sample that can hit
 // is k + max(1, c - 1).  The hit index is therefore the same as testing every
 // sample.
+template <bool kUnitStep>
 __device__ __forceinline__ int march(const uint8_t* __restrict__ clr, int W, int H, float x, float y, float ux,
                                      float uy, float delta, int kmax, int skip_ok) {
   int k = 1;
   while (k <= kmax) {
-    const float t = (float)k * delta;
+    // with a unit step, (float)k * 1.0f is (float)k exactly
+    const float t = kUnitStep ? (float)k : (float)k * delta;
     const float px = fmaf(t, ux, x);
     const float py = fmaf(t, uy, y);
     const int ix = __float2int_rd(px), iy = __float2int_rd(py);
     if ((unsigned)ix >= (unsigned)W || (unsigned)iy >= (unsigned)H) return k;
     const int c = __ldg(clr + iy * W + ix);
     if (c == 0) return k;
-    k += skip_ok ? max(1, c - 1) : 1;
+    k += (kUnitStep || skip_ok) ? max(1, c - 1) : 1;
   }
   return kmax + 1;
 }
@@ -324,6 +328,38 @@ __device__ __forceinline__ EnvConst env_const(const DevCfg& c, const SimPtrs& p,
   return k;
 }
 
+// The same collision test by one lane alone (rows in sequence).
+__device__ __forceinline__ bool collide_lane(const DevCfg& c, const MapDesc& m, const uint32_t* __restrict__ rows,
+                                             const uint8_t* __restrict__ clr, float x, float y) {
+  if (x < 0.0f || y < 0.0f || x >= (float)m.w || y >= (float)m.h) return true;
+  const int own = __ldg(clr + __float2int_rd(y) * m.w + __float2int_rd(x));
+  if (own >= c.clr_collide) return false;
+  const float r = c.robot_r;
+  const float r2 = r * r;
+  int cx0 = (int)floorf(x - r) - 1, cx1 = (int)floorf(x + r) + 1;
+  int cy0 = (int)floorf(y - r) - 1, cy1 = (int)floorf(y + r) + 1;
+  cx0 = max(cx0, 0);
+  cy0 = max(cy0, 0);
+  cx1 = min(cx1, m.w - 1);
+  cy1 = min(cy1, m.h - 1);
+  for (int cy = cy0; cy <= cy1; ++cy) {
+    const uint32_t* row = rows + (long long)cy * m.row_words;
+    for (int wd = cx0 >> 5; wd <= (cx1 >> 5); ++wd) {
+      const int lo = max(cx0 - wd * 32, 0), hi = min(cx1 - wd * 32, 31);
+      const uint32_t mask = (0xFFFFFFFFu >> (31 - hi)) & (0xFFFFFFFFu << lo);
+      uint32_t bits = __ldg(row + wd) & mask;
+      while (bits) {
+        const int b = __ffs(bits) - 1;
+        bits &= bits - 1;
+        const float dx = ((float)(wd * 32 + b) + 0.5f) - x;
+        const float dy = ((float)cy + 0.5f) - y;
+        if (fmaf(dx, dx, dy * dy) <= r2) return true;
+      }
+    }
+  }
+  return false;
+}
+
 // ---------------------------------------------------- observation
 // This lane's share of an observation row: beams lane and lane + 32, and
 // entry n_beams + lane for lanes 0..4.
@@ -371,7 +407,8 @@ __device__ __forceinline__ float beam_range(const DevCfg& c, const EnvConst& k, 
   const float beta = s.phi + off;
   float sn, cs;
   f_sincos(beta, sn, cs);
-  const int h = march(k.clr, k.m.w, k.m.h, s.x, s.y, -cs, -sn, c.delta, c.kmax, c.skip_ok);
+  const int h = c.delta == 1.0f ? march<true>(k.clr, k.m.w, k.m.h, s.x, s.y, -cs, -sn, c.delta, c.kmax, 1)
+                                 : march<false>(k.clr, k.m.w, k.m.h, s.x, s.y, -cs, -sn, c.delta, c.kmax, c.skip_ok);
   float r = fminf((float)h * c.delta, c.range_max);
   mn = fminf(mn, r);
   if (s.sigma > 0.0f) {
@@ -387,8 +424,7 @@ __device__ __forceinline__ void observe(const DevCfg& c, const EnvConst& k, cons
   // goal in the robot frame (forward (-cos phi, -sin phi), left = forward
   // turned by +90 degrees) and the heading-to-goal angle; independent of the
   // scan, so issued first
-  float sn, cs;
-  f_sincos(s.phi, sn, cs);
+  const float sn = s.sphi, cs = s.cphi;
   const float ddx = k.L.gx - s.x, ddy = k.L.gy - s.y;
   const float fwd = -(ddx * cs + ddy * sn);
   const float left = sn * ddx - cs * ddy;
@@ -420,6 +456,30 @@ __device__ __forceinline__ uint64_t shfl_u64(uint64_t v, int src) {
   return ((uint64_t)hi << 32) | lo;
 }
 
+// The episode draws (Sec. 3.2.4) from the eight slot hashes h[0..7] of
+// (seed, env, ep_id): parameters, start near S, random heading.
+__device__ __forceinline__ void apply_draws(const DevCfg& c, const Layout& L, Env& s, uint32_t ep_id, uint64_t h0,
+                                            uint64_t h1, uint64_t h2, uint64_t h3, uint64_t h4, uint64_t h5,
+                                            uint64_t h6, uint64_t h7) {
+  s.dt = c.dt_lo + u24_hi(h0) * (c.dt_hi - c.dt_lo);
+  const uint32_t d = (uint32_t)c.delay_lo + (uint32_t)(h1 >> 32) % (uint32_t)c.delay_span;
+  s.K = c.k_lo + u24_hi(h2) * (c.k_hi - c.k_lo);
+  s.cap = c.cap_lo + u24_hi(h3) * (c.cap_hi - c.cap_lo);
+  s.sigma = c.sig_lo + u24_hi(h4) * (c.sig_hi - c.sig_lo);
+  const float J = c.jitter;
+  const float jx = -J + u24_hi(h5) * (J - (-J));
+  const float jy = -J + u24_hi(h6) * (J - (-J));
+  s.x = L.sx + jx;
+  s.y = L.sy + jy;
+  s.phi = -kPi + u24_hi(h7) * (kPi - (-kPi));
+  f_sincos(s.phi, s.sphi, s.cphi);
+  s.vl = 0.0f;
+  s.va = 0.0f;
+  s.ep_step = 0;
+  s.ep_id = ep_id;
+  s.fifo = kNoAction | (kNoAction << 8) | (d << 16);
+}
+
 // New episode ep_id (Sec. 3.2.4): every randomised parameter re-drawn from
 // the counter RNG keyed by (seed, env, ep_id); start near S.  Lanes 0..7
 // draw one slot each.
@@ -429,22 +489,15 @@ __device__ __forceinline__ void reset_env(const DevCfg& c, const EnvConst& k, En
   const uint64_t h0 = shfl_u64(mine, 0), h1 = shfl_u64(mine, 1), h2 = shfl_u64(mine, 2);
   const uint64_t h3 = shfl_u64(mine, 3), h4 = shfl_u64(mine, 4), h5 = shfl_u64(mine, 5);
   const uint64_t h6 = shfl_u64(mine, 6), h7 = shfl_u64(mine, 7);
-  s.dt = c.dt_lo + u24_hi(h0) * (c.dt_hi - c.dt_lo);
-  const uint32_t d = (uint32_t)c.delay_lo + (uint32_t)(h1 >> 32) % (uint32_t)c.delay_span;
-  s.K = c.k_lo + u24_hi(h2) * (c.k_hi - c.k_lo);
-  s.cap = c.cap_lo + u24_hi(h3) * (c.cap_hi - c.cap_lo);
-  s.sigma = c.sig_lo + u24_hi(h4) * (c.sig_hi - c.sig_lo);
-  const float J = c.jitter;
-  const float jx = -J + u24_hi(h5) * (J - (-J));
-  const float jy = -J + u24_hi(h6) * (J - (-J));
-  s.x = k.L.sx + jx;
-  s.y = k.L.sy + jy;
-  s.phi = -kPi + u24_hi(h7) * (kPi - (-kPi));
-  s.vl = 0.0f;
-  s.va = 0.0f;
-  s.ep_step = 0;
-  s.ep_id = ep_id;
-  s.fifo = kNoAction | (kNoAction << 8) | (d << 16);
+  apply_draws(c, k.L, s, ep_id, h0, h1, h2, h3, h4, h5, h6, h7);
+}
+
+// The same draws by one lane alone (the lane simulates its own env).
+__device__ __forceinline__ void reset_env_lane(const DevCfg& c, const Layout& L, uint64_t rkey, Env& s,
+                                               uint32_t ep_id) {
+  const uint64_t pre = sm_at(rkey, (uint64_t)ep_id);
+  apply_draws(c, L, s, ep_id, sm_at(pre, 0ull), sm_at(pre, 1ull), sm_at(pre, 2ull), sm_at(pre, 3ull),
+              sm_at(pre, 4ull), sm_at(pre, 5ull), sm_at(pre, 6ull), sm_at(pre, 7ull));
 }
 
 // ------------------------------------------------------------- step
@@ -462,16 +515,16 @@ __device__ __forceinline__ bool kinematics(const DevCfg& c, Env& s, uint32_t a) 
   const float omk = 1.0f - s.K;
   s.vl = s.K * s.vl + omk * vhl;
   s.va = s.K * s.va + omk * vha;
-  float sn, cs;
-  f_sincos(s.phi, sn, cs);
-  s.x = s.x - s.dt * (s.vl * cs);
-  s.y = s.y - s.dt * (s.vl * sn);
+  // Eq. 6 uses the heading before the step: its sin/cos are cached in s
+  s.x = s.x - s.dt * (s.vl * s.cphi);
+  s.y = s.y - s.dt * (s.vl * s.sphi);
   float phi = s.phi + s.dt * s.va;
   if (phi >= kPi)
     phi = phi - 2.0f * kPi;
   else if (phi < -kPi)
     phi = phi + 2.0f * kPi;
   s.phi = phi;
+  f_sincos(phi, s.sphi, s.cphi);
   s.ep_step += 1u;
   s.t += 1u;
   return a >= (uint32_t)c.n_actions;

@@ -25,12 +25,8 @@ struct sg_sim {
   uint32_t* ustate = nullptr;  // [4][n]
   uint32_t* status_dev = nullptr;
   // launch configuration of the random rollout (sg_sim_set_launch)
-  int warps_per_block = 4;
-  int persistent = 0;
+  sg_launch launch = {SG_ROLLOUT_GRID, 4, 1, 0, 0, 0, 0, 32};
   int persistent_blocks = 0;
-  int order_mode = 0;
-  int warps_per_env = 1;
-  int pipe_obs_warps = 0;  // > 0: pipelined rollout with this many observation warps per env
   int* order_dev = nullptr;      // work list (cost-sorted env indices) or null
   int* map_order_dev = nullptr;  // env indices grouped by map (stable), for per-CTA map locality
   unsigned* queue_dev = nullptr; // work-list cursor of the persistent kernel

@@ -216,7 +216,7 @@ struct __align__(16) StepRec {
   uint32_t done;
   uint32_t a;
 };
-static_assert(sizeof(StepRec) == 112, "step record is seven 16-byte words");
+static_assert(sizeof(StepRec) == 128, "step record is eight 16-byte words");
 
 __device__ __forceinline__ void named_barrier(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(nthreads) : "memory");
@@ -224,7 +224,7 @@ __device__ __forceinline__ void named_barrier(int id, int nthreads) {
 
 __device__ __forceinline__ uint32_t fbits(float f) { return __float_as_uint(f); }
 
-// Lane 0 writes the record as seven 16-byte stores (all lanes hold the same
+// Lane 0 writes the record as eight 16-byte stores (all lanes hold the same
 // values).
 __device__ __forceinline__ void store_rec(StepRec* r, const Env& q, const Env& e, uint32_t done, uint32_t a,
                                           int lane) {
@@ -233,10 +233,11 @@ __device__ __forceinline__ void store_rec(StepRec* r, const Env& q, const Env& e
   d[0] = make_uint4(fbits(q.x), fbits(q.y), fbits(q.phi), fbits(q.vl));
   d[1] = make_uint4(fbits(q.va), fbits(q.dt), fbits(q.K), fbits(q.cap));
   d[2] = make_uint4(fbits(q.sigma), q.ep_step, q.ep_id, q.t);
-  d[3] = make_uint4(q.fifo, fbits(e.x), fbits(e.y), fbits(e.phi));
-  d[4] = make_uint4(fbits(e.vl), fbits(e.va), fbits(e.dt), fbits(e.K));
-  d[5] = make_uint4(fbits(e.cap), fbits(e.sigma), e.ep_step, e.ep_id);
-  d[6] = make_uint4(e.t, e.fifo, done, a);
+  d[3] = make_uint4(q.fifo, fbits(q.sphi), fbits(q.cphi), fbits(e.x));
+  d[4] = make_uint4(fbits(e.y), fbits(e.phi), fbits(e.vl), fbits(e.va));
+  d[5] = make_uint4(fbits(e.dt), fbits(e.K), fbits(e.cap), fbits(e.sigma));
+  d[6] = make_uint4(e.ep_step, e.ep_id, e.t, e.fifo);
+  d[7] = make_uint4(fbits(e.sphi), fbits(e.cphi), done, a);
 }
 
 __global__ void __launch_bounds__(512, 2) k_rollout_random_pipe(const __grid_constant__ DevCfg c, SimPtrs p, int K,
@@ -297,6 +298,133 @@ __global__ void __launch_bounds__(512, 2) k_rollout_random_pipe(const __grid_con
   if (role > 0 && obs && (K - 1 - (chunks - 1) * kPipeChunk) % P == role - 1)
     write_obs(obs + (long long)env * c.obs_dim, o, c.B, lane);
   if (role == 0 && lane == 0) store_env(p, env, s);
+}
+
+// Lane-parallel pose chain: warp 0 of a CTA simulates the pose chains of the
+// CTA's E envs, one env per lane, into a shared-memory chunk of step records;
+// warps 1..P compute the scans, observations and rewards of the previous
+// chunk, one record at a time (lanes = beams).  The whole CTA meets at one
+// barrier per chunk.  The pose chain then costs a fraction 1/E of a warp per
+// env-step, and nearly every resident warp works on observations.
+struct EnvShared {
+  MapDesc m;         // 24 B
+  Layout L;          // 20 B
+  float stepb;       // beam spacing fov / (nb - 1)
+  int nb;
+  int pad;
+  uint64_t nkey;     // noise key prefix
+};
+constexpr int kRecStride = 9;  // StepRec + 16 B of padding, in 16-byte words (conflict-free lane stores)
+
+__device__ __forceinline__ void store_rec_lane(uint4* d, const Env& q, const Env& e, uint32_t done, uint32_t a) {
+  d[0] = make_uint4(fbits(q.x), fbits(q.y), fbits(q.phi), fbits(q.vl));
+  d[1] = make_uint4(fbits(q.va), fbits(q.dt), fbits(q.K), fbits(q.cap));
+  d[2] = make_uint4(fbits(q.sigma), q.ep_step, q.ep_id, q.t);
+  d[3] = make_uint4(q.fifo, fbits(q.sphi), fbits(q.cphi), fbits(e.x));
+  d[4] = make_uint4(fbits(e.y), fbits(e.phi), fbits(e.vl), fbits(e.va));
+  d[5] = make_uint4(fbits(e.dt), fbits(e.K), fbits(e.cap), fbits(e.sigma));
+  d[6] = make_uint4(e.ep_step, e.ep_id, e.t, e.fifo);
+  d[7] = make_uint4(fbits(e.sphi), fbits(e.cphi), done, a);
+}
+
+__global__ void __launch_bounds__(512, 2) k_rollout_random_lanes(const __grid_constant__ DevCfg c, SimPtrs p, int K,
+                                                                 int E, int D, float* __restrict__ obs,
+                                                                 float* __restrict__ obs_seq,
+                                                                 uint8_t* __restrict__ act_seq,
+                                                                 float* __restrict__ rew_seq,
+                                                                 uint8_t* __restrict__ done_seq) {
+  extern __shared__ __align__(16) unsigned char lane_smem[];
+  EnvShared* es = reinterpret_cast<EnvShared*>(lane_smem);
+  uint4* recs = reinterpret_cast<uint4*>(lane_smem + ((E * sizeof(EnvShared) + 15) / 16) * 16);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int P = (blockDim.x >> 5) - 1;
+  const int env0 = blockIdx.x * E;
+  const int nE = min(E, c.n_envs - env0);
+  const long long n = c.n_envs;
+  // per-env constants, shared with the observation warps
+  Env s, pre;
+  MapDesc pm;
+  Layout pL;
+  uint64_t rkey = 0, akey = 0;
+  if (warp == 0 && lane < nE) {
+    const int env = env0 + lane;
+    pm = p.maps[p.env_map[env]];
+    pL = layout_of(c, pm);
+    const int nb = p.env_beams ? p.env_beams[env] : c.B;
+    EnvShared q;
+    q.m = pm;
+    q.L = pL;
+    q.stepb = c.fov / (float)(nb - 1);
+    q.nb = nb;
+    q.pad = 0;
+    q.nkey = sm_at(sm_at(c.seed, kStreamNoise), (uint64_t)env);
+    es[lane] = q;
+    rkey = sm_at(sm_at(c.seed, kStreamReset), (uint64_t)env);
+    akey = sm_at(sm_at(c.seed, kStreamAction), (uint64_t)env);
+    s = load_env(p, env);
+  }
+  __syncthreads();
+  const int chunks = (K + D - 1) / D;
+  for (int ch = 0; ch <= chunks; ++ch) {
+    if (warp == 0) {
+      if (ch < chunks && lane < nE) {
+        const uint32_t* rows = p.atlas + pm.word_off;
+        const uint8_t* clr = p.clr + pm.clr_off;
+        uint4* buf = recs + (size_t)(ch & 1) * D * E * kRecStride;
+        const int i0 = ch * D, i1 = min(K, i0 + D);
+        for (int i = i0; i < i1; ++i) {
+          const uint32_t a = random_action_for(c, akey, s.t);
+          if (kinematics(c, s, a)) atomicOr(p.status, 1u);
+          const bool col = collide_lane(c, pm, rows, clr, s.x, s.y);
+          const float ddx = pL.gx - s.x, ddy = pL.gy - s.y;
+          const float d1sq = fmaf(ddx, ddx, ddy * ddy);
+          const bool arrive = d1sq <= c.goal_r * c.goal_r;
+          const bool trunc = s.ep_step >= (uint32_t)c.t_max;
+          const uint32_t done = (col ? 1u : 0u) | (arrive ? 2u : 0u) | (trunc ? 4u : 0u);
+          pre = s;
+          if (done) reset_env_lane(c, pL, rkey, s, s.ep_id + 1u);
+          store_rec_lane(buf + ((size_t)(i - i0) * E + lane) * kRecStride, pre, s, done, a);
+        }
+      }
+    } else if (ch >= 1) {
+      const uint4* buf = recs + (size_t)((ch - 1) & 1) * D * E * kRecStride;
+      const int i0 = (ch - 1) * D, i1 = min(K, i0 + D);
+      const int R = (i1 - i0) * nE;
+      for (int r = warp - 1; r < R; r += P) {
+        const int e = r % nE, i = i0 + r / nE;
+        const StepRec& rec = *reinterpret_cast<const StepRec*>(buf + ((size_t)(i - i0) * E + e) * kRecStride);
+        const EnvShared q = es[e];
+        EnvConst k;
+        k.m = q.m;
+        k.rows = p.atlas + q.m.word_off;
+        k.clr = p.clr + q.m.clr_off;
+        k.L = q.L;
+        k.env = env0 + e;
+        k.nb = q.nb;
+        k.off0 = (float)lane * q.stepb - c.half_fov;
+        k.off1 = (float)(lane + 32) * q.stepb - c.half_fov;
+        k.nkey = q.nkey;
+        k.rkey = 0;
+        const Env post = rec.post, rpre = rec.pre;
+        ObsRegs o;
+        const float rew = obs_step(c, k, post, rpre, rec.done, lane, o);
+        const int env = env0 + e;
+        if (obs_seq) write_obs(obs_seq + ((long long)i * n + env) * c.obs_dim, o, c.B, lane);
+        if (obs && i == K - 1) write_obs(obs + (long long)env * c.obs_dim, o, c.B, lane);
+        if (lane == 0) {
+          if (act_seq) act_seq[i * n + env] = (uint8_t)rec.a;
+          if (rew_seq) rew_seq[i * n + env] = rew;
+          if (done_seq) done_seq[i * n + env] = (uint8_t)rec.done;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (warp == 0 && lane < nE) store_env(p, env0 + lane, s);
+}
+
+size_t lanes_smem(int E, int D) {
+  return ((E * sizeof(EnvShared) + 15) / 16) * 16 + (size_t)2 * D * E * kRecStride * 16;
 }
 
 // W warps per env, E envs per CTA (blockDim = 32 W E).
@@ -664,27 +792,42 @@ extern "C" int sg_sim_rollout(sg_sim_t sim, int32_t K, int32_t policy, sg_qnet_t
   if (((uintptr_t)obs_dev & 3) || ((uintptr_t)obs_seq_dev & 3) || ((uintptr_t)rew_seq_dev & 3)) return SG_E_ALIGN;
   if (policy == SG_POLICY_RANDOM) {
     if (replay) return SG_E_INVAL;  // transitions are recorded by the Q-policy rollout
-    const int wpb = sim->warps_per_block;
-    if (sim->pipe_obs_warps > 0) {
-      const int G = 1 + sim->pipe_obs_warps;
-      const int E = wpb / G > 0 ? wpb / G : 1;
-      const size_t smem = (size_t)E * 2 * kPipeChunk * sizeof(StepRec);
-      k_rollout_random_pipe<<<(sim->dc.n_envs + E - 1) / E, 32 * G * E, smem, stream>>>(
-          sim->dc, sg_sim_ptrs(sim), K, sim->pipe_obs_warps, obs_dev, obs_seq_dev, act_seq_dev, rew_seq_dev,
-          done_seq_dev);
-    } else if (sim->warps_per_env > 1) {
-      const int W = sim->warps_per_env;
-      const int E = wpb / W > 0 ? wpb / W : 1;
-      k_rollout_random_split<<<(sim->dc.n_envs + E - 1) / E, 32 * W * E, 0, stream>>>(
-          sim->dc, sg_sim_ptrs(sim), K, W, obs_dev, obs_seq_dev, act_seq_dev, rew_seq_dev, done_seq_dev);
-    } else if (sim->persistent) {
-      SG_CUDA(cudaMemsetAsync(sim->queue_dev, 0, sizeof(unsigned), stream));
-      k_rollout_random_queue<<<sim->persistent_blocks, 32 * wpb, 0, stream>>>(
-          sim->dc, sg_sim_ptrs(sim), K, sim->order_dev, sim->queue_dev, obs_dev, obs_seq_dev, act_seq_dev,
-          rew_seq_dev, done_seq_dev);
-    } else {
-      k_rollout_random<<<(sim->dc.n_envs + wpb - 1) / wpb, 32 * wpb, 0, stream>>>(
-          sim->dc, sg_sim_ptrs(sim), K, obs_dev, obs_seq_dev, act_seq_dev, rew_seq_dev, done_seq_dev);
+    const sg_launch& L = sim->launch;
+    const int n = sim->dc.n_envs;
+    const SimPtrs sp = sg_sim_ptrs(sim);
+    switch (L.kernel) {
+      case SG_ROLLOUT_LANES: {
+        const int E = L.envs_per_block;
+        k_rollout_random_lanes<<<(n + E - 1) / E, 32 * (1 + L.obs_warps), lanes_smem(E, L.chunk), stream>>>(
+            sim->dc, sp, K, E, L.chunk, obs_dev, obs_seq_dev, act_seq_dev, rew_seq_dev, done_seq_dev);
+        break;
+      }
+      case SG_ROLLOUT_PIPE: {
+        const int G = 1 + L.obs_warps;
+        const int E = L.warps_per_block / G > 0 ? L.warps_per_block / G : 1;
+        const size_t smem = (size_t)E * 2 * kPipeChunk * sizeof(StepRec);
+        k_rollout_random_pipe<<<(n + E - 1) / E, 32 * G * E, smem, stream>>>(
+            sim->dc, sp, K, L.obs_warps, obs_dev, obs_seq_dev, act_seq_dev, rew_seq_dev, done_seq_dev);
+        break;
+      }
+      case SG_ROLLOUT_SPLIT: {
+        const int W = L.warps_per_env;
+        const int E = L.warps_per_block / W > 0 ? L.warps_per_block / W : 1;
+        k_rollout_random_split<<<(n + E - 1) / E, 32 * W * E, 0, stream>>>(
+            sim->dc, sp, K, W, obs_dev, obs_seq_dev, act_seq_dev, rew_seq_dev, done_seq_dev);
+        break;
+      }
+      case SG_ROLLOUT_QUEUE:
+        SG_CUDA(cudaMemsetAsync(sim->queue_dev, 0, sizeof(unsigned), stream));
+        k_rollout_random_queue<<<sim->persistent_blocks, 32 * L.warps_per_block, 0, stream>>>(
+            sim->dc, sp, K, L.order ? sim->order_dev : nullptr, sim->queue_dev, obs_dev, obs_seq_dev, act_seq_dev,
+            rew_seq_dev, done_seq_dev);
+        break;
+      default: {
+        const int wpb = L.warps_per_block;
+        k_rollout_random<<<(n + wpb - 1) / wpb, 32 * wpb, 0, stream>>>(sim->dc, sp, K, obs_dev, obs_seq_dev,
+                                                                      act_seq_dev, rew_seq_dev, done_seq_dev);
+      }
     }
     SG_CUDA(cudaGetLastError());
     return SG_OK;
@@ -697,26 +840,47 @@ extern "C" int sg_sim_rollout(sg_sim_t sim, int32_t K, int32_t policy, sg_qnet_t
   return SG_E_INVAL;
 }
 
-extern "C" int sg_sim_set_launch(sg_sim_t sim, int32_t warps_per_block, int32_t persistent, int32_t blocks_per_sm,
-                                 int32_t order_mode, int32_t warps_per_env) {
-  if (!sim) return SG_E_INVAL;
-  // warps_per_env < 0: the pipelined kernel with -warps_per_env observation warps
-  if (warps_per_env == 0 || warps_per_env > 16 || warps_per_env < -15 || (warps_per_env != 1 && persistent))
-    return SG_E_INVAL;
-  if (warps_per_block != 1 && warps_per_block != 2 && warps_per_block != 4 && warps_per_block != 8 &&
-      warps_per_block != 16)
-    return SG_E_INVAL;
-  if (persistent < 0 || persistent > 1 || blocks_per_sm < 0 || blocks_per_sm > 64 || order_mode < 0 ||
-      order_mode > 1)
-    return SG_E_INVAL;
+extern "C" int sg_sim_set_launch(sg_sim_t sim, const sg_launch* cfg) {
+  if (!sim || !cfg) return SG_E_INVAL;
+  const sg_launch L = *cfg;
+  auto pow2 = [](int v) { return v == 1 || v == 2 || v == 4 || v == 8 || v == 16; };
+  switch (L.kernel) {
+    case SG_ROLLOUT_GRID:
+      if (!pow2(L.warps_per_block)) return SG_E_INVAL;
+      break;
+    case SG_ROLLOUT_QUEUE:
+      if (!pow2(L.warps_per_block) || L.blocks_per_sm < 0 || L.blocks_per_sm > 64 || L.order < 0 || L.order > 1)
+        return SG_E_INVAL;
+      break;
+    case SG_ROLLOUT_SPLIT:
+      if (L.warps_per_env < 1 || L.warps_per_env > 16 || L.warps_per_block < 1 || L.warps_per_block > 16)
+        return SG_E_INVAL;
+      break;
+    case SG_ROLLOUT_PIPE:
+      if (L.obs_warps < 1 || L.obs_warps > 15 || L.warps_per_block < 1 || L.warps_per_block > 16) return SG_E_INVAL;
+      break;
+    case SG_ROLLOUT_LANES:
+      if (L.obs_warps < 1 || L.obs_warps > 31 || L.envs_per_block < 1 || L.envs_per_block > 32 || L.chunk < 1 ||
+          L.chunk > 256)
+        return SG_E_INVAL;
+      break;
+    default:
+      return SG_E_INVAL;
+  }
+  if (L.kernel == SG_ROLLOUT_LANES) {
+    const size_t smem = lanes_smem(L.envs_per_block, L.chunk);
+    if (smem > 200 * 1024) return SG_E_INVAL;
+    SG_CUDA(cudaFuncSetAttribute((const void*)k_rollout_random_lanes, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+  }
   int sms = 0;
   SG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, sim->device));
-  int bps = blocks_per_sm;
-  if (persistent && bps == 0) {
-    SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_rollout_random_queue, 32 * warps_per_block, 0));
+  int bps = L.blocks_per_sm;
+  if (L.kernel == SG_ROLLOUT_QUEUE && bps == 0) {
+    SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_rollout_random_queue, 32 * L.warps_per_block, 0));
     if (bps < 1) bps = 1;
   }
-  if (order_mode == 1 && !sim->order_dev) {
+  if (L.kernel == SG_ROLLOUT_QUEUE && L.order == 1 && !sim->order_dev) {
     // longest first: beams x map size, ties by env index
     const int n = sim->dc.n_envs;
     std::vector<int> beams((size_t)n, sim->dc.B), emap((size_t)n);
@@ -733,17 +897,15 @@ extern "C" int sg_sim_set_launch(sg_sim_t sim, int32_t warps_per_block, int32_t 
     SG_CUDA(cudaMalloc(&sim->order_dev, sizeof(int) * n));
     SG_CUDA(cudaMemcpy(sim->order_dev, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
   }
-  if (persistent && !sim->queue_dev) SG_CUDA(cudaMalloc(&sim->queue_dev, sizeof(unsigned)));
-  sim->warps_per_block = warps_per_block;
-  sim->persistent = persistent;
-  sim->persistent_blocks = persistent ? bps * sms : 0;
-  sim->order_mode = order_mode;
-  sim->warps_per_env = warps_per_env > 0 ? warps_per_env : 1;
-  sim->pipe_obs_warps = warps_per_env < 0 ? -warps_per_env : 0;
-  if (order_mode == 0 && sim->order_dev) {
-    SG_CUDA(cudaFree(sim->order_dev));
-    sim->order_dev = nullptr;
-  }
+  if (L.kernel == SG_ROLLOUT_QUEUE && !sim->queue_dev) SG_CUDA(cudaMalloc(&sim->queue_dev, sizeof(unsigned)));
+  sim->launch = L;
+  sim->persistent_blocks = L.kernel == SG_ROLLOUT_QUEUE ? bps * sms : 0;
+  return SG_OK;
+}
+
+extern "C" int sg_sim_get_launch(sg_sim_t sim, sg_launch* cfg) {
+  if (!sim || !cfg) return SG_E_INVAL;
+  *cfg = sim->launch;
   return SG_OK;
 }
 

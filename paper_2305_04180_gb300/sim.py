@@ -118,10 +118,22 @@ class Sim:
               "sg_sim_rollout")
         return obs
 
-    def set_launch(self, warps_per_block=4, persistent=False, blocks_per_sm=0, order="index", warps_per_env=1):
-        """Launch configuration of the network-free rollout (sg_sim_set_launch)."""
-        check(self.L.sg_sim_set_launch(self.handle, int(warps_per_block), int(bool(persistent)), int(blocks_per_sm),
-                                       {"index": 0, "cost": 1}[order], int(warps_per_env)), "sg_sim_set_launch")
+    def set_launch(self, kernel="grid", warps_per_block=4, warps_per_env=1, obs_warps=0, envs_per_block=0,
+                   blocks_per_sm=0, order="index", chunk=32):
+        """Launch configuration of the network-free rollout (sg_sim_set_launch);
+        accepts the keys of ``launch_config()``."""
+        L = _lib.sg_launch(_lib.SG_ROLLOUT_KERNELS[kernel], int(warps_per_block), int(warps_per_env),
+                           int(obs_warps), int(envs_per_block), int(blocks_per_sm),
+                           {"index": 0, "cost": 1}[order], int(chunk))
+        check(self.L.sg_sim_set_launch(self.handle, C.byref(L)), "sg_sim_set_launch")
+
+    def launch_config(self) -> dict:
+        L = _lib.sg_launch()
+        check(self.L.sg_sim_get_launch(self.handle, C.byref(L)), "sg_sim_get_launch")
+        kinds = {v: k for k, v in _lib.SG_ROLLOUT_KERNELS.items()}
+        return dict(kernel=kinds[L.kernel], warps_per_block=L.warps_per_block, warps_per_env=L.warps_per_env,
+                    obs_warps=L.obs_warps, envs_per_block=L.envs_per_block, blocks_per_sm=L.blocks_per_sm,
+                    order={0: "index", 1: "cost"}[L.order], chunk=L.chunk)
 
     def get_state(self):
         """(f [9, N] float32, u [4, N] uint32) host copies of the env state."""

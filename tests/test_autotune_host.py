@@ -17,8 +17,8 @@ class FakeSim:
         self.state = ("s0",)
         self.set_calls = 0
 
-    def set_launch(self, w, p, b, o, W=1):
-        self.launch = (w, p, b, o, W)
+    def set_launch(self, **kw):
+        self.launch = kw
 
     def get_state(self):
         return self.state
@@ -29,17 +29,18 @@ class FakeSim:
 
 def test_sweep_picks_fastest_and_caches(tmp_path):
     sim = FakeSim()
-    key = lambda c: (c["warps_per_block"], c["persistent"], c["order"], c["warps_per_env"])  # noqa: E731
+    key = lambda c: tuple(sorted(c.items()))  # noqa: E731
     fake_ms = {key(c): 10.0 + i for i, c in enumerate(CANDIDATES)}
-    fake_ms[(8, True, "cost", 1)] = 1.0
+    best = CANDIDATES[7]
+    fake_ms[key(best)] = 1.0
 
     def timer(s, cfg, K, reps, state):
         return fake_ms[key(cfg)]
 
     path = str(tmp_path / "c.json")
     r = autotune_rollout(sim, K=16, cache_path=path, timer=timer)
-    assert r["config"] == {"warps_per_block": 8, "persistent": True, "order": "cost", "warps_per_env": 1}
-    assert sim.launch == (8, True, 0, "cost", 1) and sim.set_calls >= 1
+    assert r["config"] == best
+    assert sim.launch == best and sim.set_calls >= 1
     r2 = autotune_rollout(sim, K=16, cache_path=path, timer=lambda *a: 1 / 0)
     assert r2["cached"] and r2["config"] == r["config"]
     # another rollout length is another cache entry

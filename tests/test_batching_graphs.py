@@ -39,12 +39,18 @@ def test_uneven_launch_configurations_agree_and_match_oracle():
     p, maps, env_map, beams = _uneven()
     K = 50
     results = []
-    for cfg in (None, (8, True, "cost", 1), (2, False, "index", 1), (16, True, "index", 1), (8, False, "index", 3),
-                (8, False, "index", 4), (8, False, "index", 8), (4, False, "index", 5), (8, False, "index", -3),
-                (16, False, "index", -4), (4, False, "index", -1), (16, False, "index", -7)):
+    cfgs = (None, dict(kernel="queue", warps_per_block=8, order="cost"), dict(kernel="grid", warps_per_block=2),
+            dict(kernel="queue", warps_per_block=16), dict(kernel="split", warps_per_block=8, warps_per_env=3),
+            dict(kernel="split", warps_per_block=8, warps_per_env=8), dict(kernel="split", warps_per_block=4, warps_per_env=5),
+            dict(kernel="pipe", warps_per_block=8, obs_warps=3), dict(kernel="pipe", warps_per_block=16, obs_warps=4),
+            dict(kernel="pipe", warps_per_block=4, obs_warps=1), dict(kernel="lanes", envs_per_block=4, obs_warps=15, chunk=16),
+            dict(kernel="lanes", envs_per_block=7, obs_warps=3, chunk=5), dict(kernel="lanes", envs_per_block=32, obs_warps=1, chunk=8),
+            dict(kernel="lanes", envs_per_block=1, obs_warps=2, chunk=17))
+    for cfg in cfgs:
         s = Sim(p, maps, env_map, beams)
         if cfg:
-            s.set_launch(cfg[0], cfg[1], 0, cfg[2], cfg[3])
+            s.set_launch(**cfg)
+            assert s.launch_config()["kernel"] == cfg["kernel"]
         s.reset()
         results.append((_run(s, K), s.get_state()))
     ref, (f0, u0) = results[0]
