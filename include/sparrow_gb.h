@@ -198,17 +198,21 @@ int sg_sim_rollout(sg_sim_t sim, int32_t K, int32_t policy, sg_qnet_t qnet, cons
  *                     envs from a work list through a device counter; order
  *                     0 = index order, 1 = sorted by cost (beams x map size),
  *                     longest first.
- *   SG_ROLLOUT_SPLIT  warps_per_env (2..16) warps share one env: with random
+ *   SG_ROLLOUT_SPLIT  warps_per_env (1..8) warps share one env: with random
  *                     actions the pose chain (motion, collision, arrival,
  *                     AutoReset draws) never depends on the LiDAR, so every
  *                     warp replays it and warp w computes the scans,
  *                     observations and rewards of the steps i = w (mod W);
- *                     max(1, warps_per_block / W) envs per CTA.
+ *                     max(1, warps_per_block / W) envs per CTA,
+ *                     warps_per_block 1..8.
  *   SG_ROLLOUT_PIPE   per env one warp computes the pose chain of 32-step
- *                     chunks into shared memory and obs_warps (1..15) warps
- *                     compute the scans, observations and rewards of the
- *                     previous chunk; max(1, warps_per_block / (1 + obs_warps))
- *                     envs per CTA.
+ *                     chunks into shared memory (motion run ahead through
+ *                     the chunk, the chunk's steps tested together, restart
+ *                     after each episode end) and then joins obs_warps
+ *                     (1..15) warps that compute the scans, observations and
+ *                     rewards of the previous chunk, taking steps from a
+ *                     shared counter; max(1, warps_per_block /
+ *                     (1 + obs_warps)) envs per CTA, warps_per_block 1..16.
  *   SG_ROLLOUT_LANES  per CTA one warp computes the pose chains of
  *                     envs_per_block (1..32) envs, one env per lane, in chunks
  *                     of `chunk` steps (1..256) into shared memory, and

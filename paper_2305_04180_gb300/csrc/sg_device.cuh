@@ -262,15 +262,11 @@ __device__ __forceinline__ int march(const uint8_t* __restrict__ clr, int W, int
 }
 
 // Robot disc against the occupied cells: the centre leaving the map, or an
-// occupied cell centre within robot_r (fma(dx,dx,dy*dy) <= r*r).  Lanes take
-// rows of the candidate box; only set bits reach the distance test.
-__device__ __forceinline__ bool collide_warp(const DevCfg& c, const MapDesc& m, const uint32_t* __restrict__ rows,
-                                             const uint8_t* __restrict__ clr, float x, float y, int lane) {
-  if (x < 0.0f || y < 0.0f || x >= (float)m.w || y >= (float)m.h) return true;
-  // every occupied cell centre is at least clearance - 0.5 cells away from a
-  // point of this cell: far enough means no cell can be within robot_r
-  const int own = __ldg(clr + __float2int_rd(y) * m.w + __float2int_rd(x));
-  if (own >= c.clr_collide) return false;
+// occupied cell centre within robot_r (fma(dx,dx,dy*dy) <= r*r).  This part
+// tests the bit rows of the candidate box around an in-map centre: lanes take
+// rows, only set bits reach the distance test.
+__device__ __forceinline__ bool collide_rows_warp(const DevCfg& c, const MapDesc& m,
+                                                  const uint32_t* __restrict__ rows, float x, float y, int lane) {
   const float r = c.robot_r;
   const float r2 = r * r;
   int cx0 = (int)floorf(x - r) - 1, cx1 = (int)floorf(x + r) + 1;
@@ -296,6 +292,17 @@ __device__ __forceinline__ bool collide_warp(const DevCfg& c, const MapDesc& m, 
     }
   }
   return __any_sync(kFull, hit);
+}
+
+// The whole test.  Every occupied cell centre is at least clearance - 0.5
+// cells away from a point of the centre's cell, so a large enough clearance
+// there rules out any occupied cell within robot_r without reading the rows.
+__device__ __forceinline__ bool collide_warp(const DevCfg& c, const MapDesc& m, const uint32_t* __restrict__ rows,
+                                             const uint8_t* __restrict__ clr, float x, float y, int lane) {
+  if (x < 0.0f || y < 0.0f || x >= (float)m.w || y >= (float)m.h) return true;
+  const int own = __ldg(clr + __float2int_rd(y) * m.w + __float2int_rd(x));
+  if (own >= c.clr_collide) return false;
+  return collide_rows_warp(c, m, rows, x, y, lane);
 }
 
 // ------------------------------------------------- per-env constants

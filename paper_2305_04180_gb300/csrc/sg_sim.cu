@@ -203,18 +203,19 @@ __device__ __forceinline__ void rollout_env_split(const DevCfg& c, const SimPtrs
 }
 
 // Pipelined variant: per env, one pose warp computes the state chain of a
-// chunk of kPipeChunk steps into a shared-memory record buffer while P
-// observation warps compute scans, observations and rewards of the previous
-// chunk (step i of a chunk by observation warp i mod P); the 1 + P warps of
-// an env meet at a named barrier once per chunk (double buffering).  The pose
-// chain runs once instead of once per warp.
+// chunk of kPipeChunk steps into a shared-memory record buffer while the
+// other P warps of the env compute scans, observations and rewards of the
+// previous chunk; once its chunk is written the pose warp joins them.  Steps
+// are handed out through a shared counter, so no warp waits on another's
+// share.  The 1 + P warps of an env meet at a named barrier once per chunk
+// (double buffering).
 constexpr int kPipeChunk = 32;
 
 struct __align__(16) StepRec {
-  Env pre;         // after the motion, before a reset
   Env post;        // the state the step ends in (reset when done)
+  uint32_t a;      // the action taken
+  Env pre;         // after the motion, before the reset (written for done steps only)
   uint32_t done;
-  uint32_t a;
 };
 static_assert(sizeof(StepRec) == 128, "step record is eight 16-byte words");
 
@@ -223,21 +224,97 @@ __device__ __forceinline__ void named_barrier(int id, int nthreads) {
 }
 
 __device__ __forceinline__ uint32_t fbits(float f) { return __float_as_uint(f); }
+__device__ __forceinline__ float bitsf(uint32_t u) { return __uint_as_float(u); }
 
-// Lane 0 writes the record as eight 16-byte stores (all lanes hold the same
-// values).
-__device__ __forceinline__ void store_rec(StepRec* r, const Env& q, const Env& e, uint32_t done, uint32_t a,
-                                          int lane) {
-  if (lane != 0) return;
-  uint4* d = reinterpret_cast<uint4*>(r);
+// An Env and one extra word as four 16-byte words.
+__device__ __forceinline__ void pack_env(uint4* d, const Env& q, uint32_t w) {
   d[0] = make_uint4(fbits(q.x), fbits(q.y), fbits(q.phi), fbits(q.vl));
   d[1] = make_uint4(fbits(q.va), fbits(q.dt), fbits(q.K), fbits(q.cap));
   d[2] = make_uint4(fbits(q.sigma), q.ep_step, q.ep_id, q.t);
-  d[3] = make_uint4(q.fifo, fbits(q.sphi), fbits(q.cphi), fbits(e.x));
-  d[4] = make_uint4(fbits(e.y), fbits(e.phi), fbits(e.vl), fbits(e.va));
-  d[5] = make_uint4(fbits(e.dt), fbits(e.K), fbits(e.cap), fbits(e.sigma));
-  d[6] = make_uint4(e.ep_step, e.ep_id, e.t, e.fifo);
-  d[7] = make_uint4(fbits(e.sphi), fbits(e.cphi), done, a);
+  d[3] = make_uint4(q.fifo, fbits(q.sphi), fbits(q.cphi), w);
+}
+__device__ __forceinline__ Env unpack_env(const uint4* d) {
+  const uint4 a = d[0], b = d[1], e = d[2], f = d[3];
+  Env q;
+  q.x = bitsf(a.x), q.y = bitsf(a.y), q.phi = bitsf(a.z), q.vl = bitsf(a.w);
+  q.va = bitsf(b.x), q.dt = bitsf(b.y), q.K = bitsf(b.z), q.cap = bitsf(b.w);
+  q.sigma = bitsf(e.x), q.ep_step = e.y, q.ep_id = e.z, q.t = e.w;
+  q.fifo = f.x, q.sphi = bitsf(f.y), q.cphi = bitsf(f.z);
+  return q;
+}
+
+// The pose chain of one chunk (n <= 32 steps, actions in lane j of abatch)
+// by one warp, into the records buf[0..n).  The motion of a step (delay,
+// Eq. 5, Eq. 6) needs the previous state only, and an episode end changes
+// the chain only through the reset.  So the warp runs the motion through the
+// rest of the chunk as if no episode ended (lane j keeps the position of step
+// j), tests all those steps at once (lane j: centre out of the map, clearance
+// around the centre, arrival, truncation), runs the bit-row collision test of
+// the steps that need it in order with the whole warp, and takes the first
+// step that ends the episode: the steps before it stand, it is reset, and the
+// chain runs again from the step after it.  Every value equals that of
+// stepping one step at a time.
+__device__ __forceinline__ void pose_chunk(const DevCfg& c, const SimPtrs& p, const EnvConst& k, Env& s, int n,
+                                           uint32_t abatch, StepRec* buf, int lane) {
+  bool bad = false;
+  int j0 = 0;
+  while (j0 < n) {
+    Env q = s;
+    float mx = 0.0f, my = 0.0f;
+    uint32_t mep = 0;
+#pragma unroll 4
+    for (int j = j0; j < n; ++j) {
+      const uint32_t a = __shfl_sync(kFull, abatch, j);
+      bad |= kinematics(c, q, a);
+      mx = lane == j ? q.x : mx;
+      my = lane == j ? q.y : my;
+      mep = lane == j ? q.ep_step : mep;
+      if (lane == 0) pack_env(reinterpret_cast<uint4*>(&buf[j].post), q, a);
+    }
+    uint32_t done = 0;
+    bool slow = false;
+    if (lane >= j0 && lane < n) {
+      if (mx < 0.0f || my < 0.0f || mx >= (float)k.m.w || my >= (float)k.m.h) {
+        done = 1u;
+      } else {
+        const int own = __ldg(k.clr + __float2int_rd(my) * k.m.w + __float2int_rd(mx));
+        slow = own < c.clr_collide;
+      }
+      const float ddx = k.L.gx - mx, ddy = k.L.gy - my;
+      if (fmaf(ddx, ddx, ddy * ddy) <= c.goal_r * c.goal_r) done |= 2u;
+      if (mep >= (uint32_t)c.t_max) done |= 4u;
+    }
+    uint32_t donem = __ballot_sync(kFull, done != 0u);
+    uint32_t slowm = __ballot_sync(kFull, slow);
+    while (slowm) {
+      const int j = __ffs(slowm) - 1;
+      slowm &= slowm - 1u;
+      if (donem & ((1u << j) - 1u)) break;  // an earlier step ends the episode
+      const float xj = __shfl_sync(kFull, mx, j), yj = __shfl_sync(kFull, my, j);
+      if (collide_rows_warp(c, k.m, k.rows, xj, yj, lane)) {
+        if (lane == j) done |= 1u;
+        donem |= 1u << j;
+      }
+    }
+    const int d = donem ? __ffs(donem) - 1 : n;
+    if (lane >= j0 && lane < d) buf[lane].done = 0u;
+    if (d == n) {
+      s = q;
+      break;
+    }
+    // step d ends the episode: its record keeps the state before the reset
+    const uint32_t dd = __shfl_sync(kFull, done, d);
+    const uint32_t ad = __shfl_sync(kFull, abatch, d);
+    __syncwarp();
+    Env e = unpack_env(reinterpret_cast<const uint4*>(&buf[d].post));
+    __syncwarp();
+    if (lane == 0) pack_env(reinterpret_cast<uint4*>(&buf[d].pre), e, dd);
+    reset_env(c, k, e, e.ep_id + 1u, lane);
+    if (lane == 0) pack_env(reinterpret_cast<uint4*>(&buf[d].post), e, ad);
+    s = e;
+    j0 = d + 1;
+  }
+  if (bad && lane == 0) atomicOr(p.status, 1u);
 }
 
 __global__ void __launch_bounds__(512, 2) k_rollout_random_pipe(const __grid_constant__ DevCfg c, SimPtrs p, int K,
@@ -247,6 +324,7 @@ __global__ void __launch_bounds__(512, 2) k_rollout_random_pipe(const __grid_con
                                                                 float* __restrict__ rew_seq,
                                                                 uint8_t* __restrict__ done_seq) {
   extern __shared__ __align__(16) unsigned char pipe_smem[];
+  __shared__ unsigned next_step[16][2];  // per env group and buffer: next record to take
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int G = 1 + P;  // warps per env
   const int group = warp / G, role = warp % G;
@@ -258,33 +336,36 @@ __global__ void __launch_bounds__(512, 2) k_rollout_random_pipe(const __grid_con
   const EnvConst k = env_const(c, p, env, lane);
   const long long n = c.n_envs;
   const int chunks = (K + kPipeChunk - 1) / kPipeChunk;
-  Env s, pre;
-  uint64_t akey = 0;
-  uint32_t abatch = 0;
-  if (role == 0) {
-    s = load_env(p, env);
-    akey = sm_at(sm_at(c.seed, kStreamAction), (uint64_t)env);
-  }
   ObsRegs o;
   o.b0 = o.b1 = o.ex = 0.0f;
+  bool has_last = false;
   for (int ch = 0; ch <= chunks; ++ch) {
     if (role == 0 && ch < chunks) {
-      StepRec* buf = recs + (ch & 1) * kPipeChunk;
+      if (lane == 0) next_step[group][ch & 1] = 0u;
+      // the state carried between chunks is the last record's post state, so
+      // nothing of the pose chain stays live while this warp takes records
+      Env s = ch == 0 ? load_env(p, env)
+                      : unpack_env(reinterpret_cast<const uint4*>(&recs[((ch - 1) & 1) * kPipeChunk + kPipeChunk - 1].post));
       const int i0 = ch * kPipeChunk, i1 = min(K, i0 + kPipeChunk);
-      for (int i = i0; i < i1; ++i) {
-        if ((i & 31) == 0) abatch = random_action_for(c, akey, s.t + (uint32_t)lane);
-        const uint32_t a = __shfl_sync(kFull, abatch, i & 31);
-        const uint32_t done = pose_step(c, p, k, s, pre, a, lane, true);
-        store_rec(buf + (i - i0), pre, s, done, a, lane);
-      }
-    } else if (role > 0 && ch >= 1) {
-      const StepRec* buf = recs + ((ch - 1) & 1) * kPipeChunk;
+      // lane l draws the action of step i0 + l (t counts every step)
+      const uint64_t akey = sm_at(sm_at(c.seed, kStreamAction), (uint64_t)env);
+      const uint32_t abatch = random_action_for(c, akey, s.t + (uint32_t)lane);
+      pose_chunk(c, p, k, s, i1 - i0, abatch, recs + (ch & 1) * kPipeChunk, lane);
+    }
+    if (ch >= 1) {
+      const int b = (ch - 1) & 1;
+      const StepRec* buf = recs + b * kPipeChunk;
       const int i0 = (ch - 1) * kPipeChunk, i1 = min(K, i0 + kPipeChunk);
-      for (int i = i0 + role - 1; i < i1; i += P) {
-        const StepRec& r = buf[i - i0];
-        const Env post = r.post, rpre = r.pre;
-        const uint32_t done = r.done, a = r.a;
+      for (;;) {
+        unsigned r = 0;
+        if (lane == 0) r = atomicAdd(&next_step[group][b], 1u);
+        const int i = i0 + (int)__shfl_sync(kFull, r, 0);
+        if (i >= i1) break;
+        const StepRec& rec = buf[i - i0];
+        const Env post = rec.post, rpre = rec.pre;
+        const uint32_t done = rec.done, a = rec.a;
         const float rew = obs_step(c, k, post, rpre, done, lane, o);
+        if (i == K - 1) has_last = true;
         if (obs_seq) write_obs(obs_seq + ((long long)i * n + env) * c.obs_dim, o, c.B, lane);
         if (lane == 0) {
           if (act_seq) act_seq[i * n + env] = (uint8_t)a;
@@ -295,9 +376,11 @@ __global__ void __launch_bounds__(512, 2) k_rollout_random_pipe(const __grid_con
     }
     named_barrier(bar, nthr);
   }
-  if (role > 0 && obs && (K - 1 - (chunks - 1) * kPipeChunk) % P == role - 1)
-    write_obs(obs + (long long)env * c.obs_dim, o, c.B, lane);
-  if (role == 0 && lane == 0) store_env(p, env, s);
+  if (obs && has_last) write_obs(obs + (long long)env * c.obs_dim, o, c.B, lane);
+  if (role == 0 && lane == 0 && chunks > 0) {
+    const int last = ((chunks - 1) & 1) * kPipeChunk + (K - 1 - (chunks - 1) * kPipeChunk);
+    store_env(p, env, unpack_env(reinterpret_cast<const uint4*>(&recs[last].post)));
+  }
 }
 
 // Lane-parallel pose chain: warp 0 of a CTA simulates the pose chains of the
@@ -317,14 +400,8 @@ struct EnvShared {
 constexpr int kRecStride = 9;  // StepRec + 16 B of padding, in 16-byte words (conflict-free lane stores)
 
 __device__ __forceinline__ void store_rec_lane(uint4* d, const Env& q, const Env& e, uint32_t done, uint32_t a) {
-  d[0] = make_uint4(fbits(q.x), fbits(q.y), fbits(q.phi), fbits(q.vl));
-  d[1] = make_uint4(fbits(q.va), fbits(q.dt), fbits(q.K), fbits(q.cap));
-  d[2] = make_uint4(fbits(q.sigma), q.ep_step, q.ep_id, q.t);
-  d[3] = make_uint4(q.fifo, fbits(q.sphi), fbits(q.cphi), fbits(e.x));
-  d[4] = make_uint4(fbits(e.y), fbits(e.phi), fbits(e.vl), fbits(e.va));
-  d[5] = make_uint4(fbits(e.dt), fbits(e.K), fbits(e.cap), fbits(e.sigma));
-  d[6] = make_uint4(e.ep_step, e.ep_id, e.t, e.fifo);
-  d[7] = make_uint4(fbits(e.sphi), fbits(e.cphi), done, a);
+  pack_env(d, e, a);
+  pack_env(d + 4, q, done);
 }
 
 __global__ void __launch_bounds__(512, 2) k_rollout_random_lanes(const __grid_constant__ DevCfg c, SimPtrs p, int K,
@@ -853,7 +930,8 @@ extern "C" int sg_sim_set_launch(sg_sim_t sim, const sg_launch* cfg) {
         return SG_E_INVAL;
       break;
     case SG_ROLLOUT_SPLIT:
-      if (L.warps_per_env < 1 || L.warps_per_env > 16 || L.warps_per_block < 1 || L.warps_per_block > 16)
+      // the kernel is compiled for at most 256 threads per CTA
+      if (L.warps_per_env < 1 || L.warps_per_env > 8 || L.warps_per_block < 1 || L.warps_per_block > 8)
         return SG_E_INVAL;
       break;
     case SG_ROLLOUT_PIPE:
@@ -866,6 +944,13 @@ extern "C" int sg_sim_set_launch(sg_sim_t sim, const sg_launch* cfg) {
       break;
     default:
       return SG_E_INVAL;
+  }
+  if (L.kernel == SG_ROLLOUT_PIPE) {
+    const int G = 1 + L.obs_warps;
+    const int E = L.warps_per_block / G > 0 ? L.warps_per_block / G : 1;
+    const size_t smem = (size_t)E * 2 * kPipeChunk * sizeof(StepRec);
+    SG_CUDA(cudaFuncSetAttribute((const void*)k_rollout_random_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
   }
   if (L.kernel == SG_ROLLOUT_LANES) {
     const size_t smem = lanes_smem(L.envs_per_block, L.chunk);

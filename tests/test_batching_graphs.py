@@ -69,6 +69,50 @@ def test_uneven_launch_configurations_agree_and_match_oracle():
             assert np.array_equal(bits(obs), bits(ref["obs_seq"][k, i]))
 
 
+def test_pipelined_pose_chain_with_frequent_episode_ends():
+    """Fast robots (dt up to 1 s), a short episode limit and a wide robot
+    disc end episodes by collision, arrival and truncation several times per
+    32-step chunk: the pipelined kernel's chunked pose chain (motion run ahead,
+    steps tested together, restart after each episode end) must give the
+    one-step-at-a-time results, and sampled envs must match the oracle."""
+    from paper_2305_04180_gb300 import Sim
+
+    rng = np.random.default_rng(7)
+    sides = [128, 128, 256, 366]
+    maps = [make_map(500 + m, sides[m % 4]) for m in range(8)]
+    n = 40
+    env_map = rng.integers(0, 8, n).astype(np.int32)
+    beams = rng.choice([16, 32, 64], n).astype(np.int32)
+    p = base_params(n_beams=64, **dict(DR_RANGES, dt_lo=0.2, dt_hi=1.0, cap_hi=2.0), t_max=9, robot_radius=12.0,
+                    goal_radius=90.0)
+    K = 100
+    results = []
+    for cfg in (None, dict(kernel="pipe", warps_per_block=16, obs_warps=7),
+                dict(kernel="pipe", warps_per_block=8, obs_warps=3), dict(kernel="pipe", warps_per_block=2, obs_warps=1)):
+        s = Sim(p, maps, env_map, beams)
+        if cfg:
+            s.set_launch(**cfg)
+        s.reset()
+        results.append((_run(s, K), s.get_state()))
+    ref, (f0, u0) = results[0]
+    d = ref["done"]
+    assert (d & 1).any() and (d & 2).any() and (d & 4).any()
+    per_chunk = np.stack([(d[c:c + 32] != 0).sum(axis=0) for c in range(0, K, 32)])
+    assert per_chunk.max() >= 3  # several restarts of the chain inside one chunk
+    for r, (f, u) in results[1:]:
+        for k in ref:
+            assert np.array_equal(bits(r[k]) if r[k].dtype == np.float32 else r[k],
+                                  bits(ref[k]) if ref[k].dtype == np.float32 else ref[k]), k
+        assert np.array_equal(bits(f), bits(f0)) and np.array_equal(u, u0)
+    o = OracleSim(p, maps, env_map, beams, prec="f32")
+    for i in (0, 9, 23, 39):
+        o.reset_env(i, 0)
+        for k in range(K):
+            obs, rew, done, _ = o.step_one(i, o.random_action(i, k))
+            assert done == d[k, i] and bits(np.float32(rew)) == bits(ref["rew"][k, i]), (i, k)
+            assert np.array_equal(bits(obs), bits(ref["obs_seq"][k, i])), (i, k)
+
+
 def test_graph_replay_equals_direct_calls():
     from paper_2305_04180_gb300 import Sim
     from paper_2305_04180_gb300.graph import Graph

@@ -138,12 +138,16 @@ def test_step_degenerate_cases():
     assert g.status() == 0  # reading clears it
 
 
-def test_rollout_random_free_running_bit_exact():
+@pytest.mark.parametrize("launch", [None, dict(kernel="pipe", warps_per_block=16, obs_warps=7)])
+def test_rollout_random_free_running_bit_exact(launch):
     """1000 free-running steps with on-device random actions: every step's
     action, reward, done flags and observation, and the final state, equal
-    the oracle's."""
+    the oracle's (one warp per env, and the pipelined kernel the benchmark
+    times)."""
     w = workload("plain16")
     g, o, _ = _pair(w)
+    if launch:
+        g.set_launch(**launch)
     g.reset()
     o.reset()
     K = 1000
@@ -188,13 +192,16 @@ def test_rollout_continues_across_calls_and_matches_steps():
     assert np.array_equal(bits(fa), bits(fb)) and np.array_equal(ua, ub)
 
 
-def test_rollout_full_size_sampled_against_oracle():
-    """The 1024-env, 32-map domain-randomised workload in the launch
-    configuration the benchmark times: 300 steps on the GPU, then a sample of
-    envs replayed one by one on the oracle from the same start."""
+@pytest.mark.parametrize("launch", [None, dict(kernel="pipe", warps_per_block=16, obs_warps=7)])
+def test_rollout_full_size_sampled_against_oracle(launch):
+    """The 1024-env, 32-map domain-randomised workload (one warp per env, and
+    the pipelined launch the benchmark times): 300 steps on the GPU, then a
+    sample of envs replayed one by one on the oracle from the same start."""
     w = workload("dr1024")
     maps = w.maps()
     g = _sim(w.params, maps, w.env_map)
+    if launch:
+        g.set_launch(**launch)
     g.reset()
     K = 300
     rew = torch.empty((K, g.n), device="cuda")
