@@ -409,37 +409,61 @@ __device__ __forceinline__ Noise noise_for(const EnvConst& k, float sigma, uint3
   return z;
 }
 
-__device__ __forceinline__ float beam_range(const DevCfg& c, const EnvConst& k, const Env& s, float off, float nz,
-                                            float& mn) {
-  const float beta = s.phi + off;
+// Normalised range of the beam at heading offset `off` from the pose (x, y,
+// phi), with noise sigma * nz; mn takes the minimum noise-free range.
+__device__ __forceinline__ float beam_at(const DevCfg& c, const EnvConst& k, float x, float y, float phi,
+                                         float sigma, float off, float nz, float& mn) {
+  const float beta = phi + off;
   float sn, cs;
   f_sincos(beta, sn, cs);
-  const int h = c.delta == 1.0f ? march<true>(k.clr, k.m.w, k.m.h, s.x, s.y, -cs, -sn, c.delta, c.kmax, 1)
-                                 : march<false>(k.clr, k.m.w, k.m.h, s.x, s.y, -cs, -sn, c.delta, c.kmax, c.skip_ok);
+  const int h = c.delta == 1.0f ? march<true>(k.clr, k.m.w, k.m.h, x, y, -cs, -sn, c.delta, c.kmax, 1)
+                                 : march<false>(k.clr, k.m.w, k.m.h, x, y, -cs, -sn, c.delta, c.kmax, c.skip_ok);
   float r = fminf((float)h * c.delta, c.range_max);
   mn = fminf(mn, r);
-  if (s.sigma > 0.0f) {
+  if (sigma > 0.0f) {
     // additive Gaussian sensor noise on the reported range, clamped
-    r = r + s.sigma * nz;
+    r = r + sigma * nz;
     r = fminf(fmaxf(r, 0.0f), c.range_max);
   }
   return r / c.range_max;
 }
 
+__device__ __forceinline__ float beam_range(const DevCfg& c, const EnvConst& k, const Env& s, float off, float nz,
+                                            float& mn) {
+  return beam_at(c, k, s.x, s.y, s.phi, s.sigma, off, nz, mn);
+}
+
+// Goal in the robot frame (forward (-cos phi, -sin phi), left = forward
+// turned by +90 degrees) and the heading-to-goal angle.
+struct GoalFrame {
+  float ddx, ddy, fwd, left, alpha;
+};
+__device__ __forceinline__ GoalFrame goal_frame(const Layout& L, const Env& s) {
+  GoalFrame g;
+  const float sn = s.sphi, cs = s.cphi;
+  g.ddx = L.gx - s.x;
+  g.ddy = L.gy - s.y;
+  g.fwd = -(g.ddx * cs + g.ddy * sn);
+  g.left = sn * g.ddx - cs * g.ddy;
+  g.alpha = f_atan2(g.left, g.fwd);
+  return g;
+}
+
+// Observation entry B + q (q = 0..4): fwd/D, left/D, alpha/pi, vl/v_nom,
+// va/w_nom (q >= 4 gives the last).
+__device__ __forceinline__ float obs_extra(const DevCfg& c, const Layout& L, const Env& s, const GoalFrame& g,
+                                           int q) {
+  const float num = q == 0 ? g.fwd : q == 1 ? g.left : q == 2 ? g.alpha : q == 3 ? s.vl : s.va;
+  const float den = q < 2 ? L.D : q == 2 ? kPi : q == 3 ? c.v_nom : c.w_nom;
+  return num / den;
+}
+
 __device__ __forceinline__ void observe(const DevCfg& c, const EnvConst& k, const Env& s, const Noise& z, int lane,
                                         ObsRegs& o, Aux& aux) {
-  // goal in the robot frame (forward (-cos phi, -sin phi), left = forward
-  // turned by +90 degrees) and the heading-to-goal angle; independent of the
-  // scan, so issued first
-  const float sn = s.sphi, cs = s.cphi;
-  const float ddx = k.L.gx - s.x, ddy = k.L.gy - s.y;
-  const float fwd = -(ddx * cs + ddy * sn);
-  const float left = sn * ddx - cs * ddy;
-  const float alpha = f_atan2(left, fwd);
-  // lanes 0..4 hold fwd/D, left/D, alpha/pi, vl/v_nom, va/w_nom: one division
-  const float num = lane == 0 ? fwd : lane == 1 ? left : lane == 2 ? alpha : lane == 3 ? s.vl : s.va;
-  const float den = lane < 2 ? k.L.D : lane == 2 ? kPi : lane == 3 ? c.v_nom : c.w_nom;
-  o.ex = num / den;
+  // independent of the scan, so issued first; lanes 0..4 hold the extras
+  const GoalFrame g = goal_frame(k.L, s);
+  const float ddx = g.ddx, ddy = g.ddy, alpha = g.alpha;
+  o.ex = obs_extra(c, k.L, s, g, lane);
   float mn = c.range_max;
   o.b0 = lane < k.nb ? beam_range(c, k, s, k.off0, z.n0, mn) : 1.0f;
   o.b1 = lane + 32 < k.nb ? beam_range(c, k, s, k.off1, z.n1, mn) : 1.0f;
@@ -542,11 +566,11 @@ struct StepOut {
   uint32_t done;
 };
 
-// Eq. 11 for a live (not collided, not arrived) step: 0.3 r_d1 + 0.1 r_d2 +
-// 0.3 r_v + 0.3 r_alpha + 0.1 r_d at the state `s` whose scan gave `aux`.
-__device__ __forceinline__ float shaped_reward(const DevCfg& c, const EnvConst& k, const Env& s, const Aux& aux) {
-  const Layout& L = k.L;
-  const float d1sq = fmaf(aux.ddx, aux.ddx, aux.ddy * aux.ddy);
+// The terms of Eq. 11 that do not need the scan, summed in order:
+// ((0.3 r_d1 + 0.1 r_d2) + 0.3 r_v) + 0.3 r_alpha.
+__device__ __forceinline__ float reward_partial(const DevCfg& c, const Layout& L, const Env& s, float alpha,
+                                                float ddx, float ddy) {
+  const float d1sq = fmaf(ddx, ddx, ddy * ddy);
   const float d1 = sqrtf(d1sq);
   const float rd1 = 1.0f - d1 / L.D;
   const float ex = L.gx - L.sx, ey = L.gy - L.sy;
@@ -556,14 +580,24 @@ __device__ __forceinline__ float shaped_reward(const DevCfg& c, const EnvConst& 
   const float rd2 = 1.0f - (t2 + t2);
   const float vmax = c.v_nom * s.cap;
   const float rv = s.vl > 0.5f * vmax ? 1.0f : 0.0f;
-  const float ra = 1.0f - fabsf(aux.alpha) / kPi;
-  const float rdn = aux.min_range < c.near_dist ? -1.0f : 0.0f;
+  const float ra = 1.0f - fabsf(alpha) / kPi;
   float r = 0.3f * rd1;
   r = r + 0.1f * rd2;
   r = r + 0.3f * rv;
   r = r + 0.3f * ra;
-  r = r + 0.1f * rdn;
   return r;
+}
+
+// The last term, r_d, from the scan's minimum noise-free range.
+__device__ __forceinline__ float reward_finish(const DevCfg& c, float partial, float min_range) {
+  const float rdn = min_range < c.near_dist ? -1.0f : 0.0f;
+  return partial + 0.1f * rdn;
+}
+
+// Eq. 11 for a live (not collided, not arrived) step: 0.3 r_d1 + 0.1 r_d2 +
+// 0.3 r_v + 0.3 r_alpha + 0.1 r_d at the state `s` whose scan gave `aux`.
+__device__ __forceinline__ float shaped_reward(const DevCfg& c, const EnvConst& k, const Env& s, const Aux& aux) {
+  return reward_finish(c, reward_partial(c, k.L, s, aux.alpha, aux.ddx, aux.ddy), aux.min_range);
 }
 
 // One full step of one env by its warp.  `term_row` (may be null) receives

@@ -203,12 +203,14 @@ __device__ __forceinline__ void rollout_env_split(const DevCfg& c, const SimPtrs
 }
 
 // Pipelined variant: per env, one pose warp computes the state chain of a
-// chunk of kPipeChunk steps into a shared-memory record buffer while the
-// other P warps of the env compute scans, observations and rewards of the
-// previous chunk; once its chunk is written the pose warp joins them.  Steps
-// are handed out through a shared counter, so no warp waits on another's
-// share.  The 1 + P warps of an env meet at a named barrier once per chunk
-// (double buffering).
+// chunk of kPipeChunk steps and, one lane per step, everything of those
+// steps that does not need the scan (goal frame, atan2, the five observation
+// extras, the scan-free terms of Eq. 11, the noise key) into a shared-memory
+// record buffer, while the other P warps of the env compute the scans,
+// observations and rewards of the previous chunk; once its chunk is written
+// the pose warp joins them.  Steps are handed out through a shared counter,
+// so no warp waits on another's share.  The 1 + P warps of an env meet at a
+// named barrier once per chunk (double-buffered observation records).
 constexpr int kPipeChunk = 32;
 
 struct __align__(16) StepRec {
@@ -241,6 +243,69 @@ __device__ __forceinline__ Env unpack_env(const uint4* d) {
   q.sigma = bitsf(e.x), q.ep_step = e.y, q.ep_id = e.z, q.t = e.w;
   q.fifo = f.x, q.sphi = bitsf(f.y), q.cphi = bitsf(f.z);
   return q;
+}
+
+// What the scan of one step still needs.
+struct __align__(16) ObsRec {
+  float x, y, phi, sigma;  // the state observed (after the step, reset when done)
+  uint32_t nlo, nhi;       // its noise key
+  float rpart;             // scan-free part of Eq. 11 (of the pre-reset state when truncated)
+  uint32_t da;             // done | action << 8
+  float ex[5];             // observation entries B .. B + 4
+  float px, py, pphi;      // pre-reset state (truncated steps)
+  float psigma;
+  uint32_t pnlo, pnhi;
+  uint32_t pad;
+};
+static_assert(sizeof(ObsRec) == 80, "observation record is five 16-byte words");
+
+__device__ __forceinline__ uint64_t noise_key(const EnvConst& k, const Env& s) {
+  return sm_at(k.nkey, ((uint64_t)s.ep_id << 32) | s.ep_step);
+}
+
+// Lane j: record j of the chunk from its step record.
+__device__ __forceinline__ void derive_rec(const DevCfg& c, const EnvConst& k, const StepRec& r, ObsRec& o) {
+  const Env s = r.post;
+  const uint32_t done = r.done;
+  const GoalFrame g = goal_frame(k.L, s);
+  const uint64_t nk = noise_key(k, s);
+  float e[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) e[q] = obs_extra(c, k.L, s, g, q);
+  float rp = 0.0f;
+  if (!done) rp = reward_partial(c, k.L, s, g.alpha, g.ddx, g.ddy);
+  uint4* w = reinterpret_cast<uint4*>(&o);
+  w[0] = make_uint4(fbits(s.x), fbits(s.y), fbits(s.phi), fbits(s.sigma));
+  w[1] = make_uint4((uint32_t)nk, (uint32_t)(nk >> 32), fbits(rp), done | (r.a << 8));
+  w[2] = make_uint4(fbits(e[0]), fbits(e[1]), fbits(e[2]), fbits(e[3]));
+  if (done && !(done & 3u)) {
+    // truncated only: the reward comes from the scan before the reset
+    const Env q = r.pre;
+    const GoalFrame gp = goal_frame(k.L, q);
+    const uint64_t pk = noise_key(k, q);
+    o.rpart = reward_partial(c, k.L, q, gp.alpha, gp.ddx, gp.ddy);
+    w[3] = make_uint4(fbits(e[4]), fbits(q.x), fbits(q.y), fbits(q.phi));
+    w[4] = make_uint4(fbits(q.sigma), (uint32_t)pk, (uint32_t)(pk >> 32), 0u);
+  } else {
+    o.ex[4] = e[4];
+  }
+}
+
+// The scan of one pose by a whole warp: this lane's beams (with noise drawn
+// from key nk when sigma > 0) into o.b0 / o.b1; returns the minimum
+// noise-free range over all beams.
+__device__ __forceinline__ float scan_pose(const DevCfg& c, const EnvConst& k, float x, float y, float phi,
+                                           float sigma, uint64_t nk, int lane, ObsRegs& o) {
+  float n0 = 0.0f, n1 = 0.0f;
+  if (sigma > 0.0f) {
+    n0 = box_muller(sm_at(nk, (uint64_t)lane));
+    if (k.nb > 32) n1 = box_muller(sm_at(nk, (uint64_t)(lane + 32)));
+  }
+  float mn = c.range_max;
+  o.b0 = lane < k.nb ? beam_at(c, k, x, y, phi, sigma, k.off0, n0, mn) : 1.0f;
+  o.b1 = lane + 32 < k.nb ? beam_at(c, k, x, y, phi, sigma, k.off1, n1, mn) : 1.0f;
+  // ranges are >= 0, so their bit patterns order like the values
+  return __uint_as_float(__reduce_min_sync(kFull, __float_as_uint(mn)));
 }
 
 // The pose chain of one chunk (n <= 32 steps, actions in lane j of abatch)
@@ -331,7 +396,10 @@ __global__ void __launch_bounds__(512, 2) k_rollout_random_pipe(const __grid_con
   const int E = blockDim.x / (32 * G);
   const int env = blockIdx.x * E + group;
   if (env >= c.n_envs) return;  // the whole group leaves together
-  StepRec* recs = reinterpret_cast<StepRec*>(pipe_smem) + (size_t)group * 2 * kPipeChunk;
+  // per group: kPipeChunk step records, then 2 x kPipeChunk observation records
+  unsigned char* base = pipe_smem + (size_t)group * kPipeChunk * (sizeof(StepRec) + 2 * sizeof(ObsRec));
+  StepRec* st = reinterpret_cast<StepRec*>(base);
+  ObsRec* ob = reinterpret_cast<ObsRec*>(base + kPipeChunk * sizeof(StepRec));
   const int bar = 1 + group, nthr = 32 * G;
   const EnvConst k = env_const(c, p, env, lane);
   const long long n = c.n_envs;
@@ -342,33 +410,46 @@ __global__ void __launch_bounds__(512, 2) k_rollout_random_pipe(const __grid_con
   for (int ch = 0; ch <= chunks; ++ch) {
     if (role == 0 && ch < chunks) {
       if (lane == 0) next_step[group][ch & 1] = 0u;
-      // the state carried between chunks is the last record's post state, so
-      // nothing of the pose chain stays live while this warp takes records
-      Env s = ch == 0 ? load_env(p, env)
-                      : unpack_env(reinterpret_cast<const uint4*>(&recs[((ch - 1) & 1) * kPipeChunk + kPipeChunk - 1].post));
-      const int i0 = ch * kPipeChunk, i1 = min(K, i0 + kPipeChunk);
+      // the state carried between chunks is the last step record's post
+      // state, so nothing of the pose chain stays live while this warp takes
+      // observation records
+      Env s = ch == 0 ? load_env(p, env) : unpack_env(reinterpret_cast<const uint4*>(&st[kPipeChunk - 1].post));
+      const int i0 = ch * kPipeChunk, nst = min(K, i0 + kPipeChunk) - i0;
       // lane l draws the action of step i0 + l (t counts every step)
       const uint64_t akey = sm_at(sm_at(c.seed, kStreamAction), (uint64_t)env);
       const uint32_t abatch = random_action_for(c, akey, s.t + (uint32_t)lane);
-      pose_chunk(c, p, k, s, i1 - i0, abatch, recs + (ch & 1) * kPipeChunk, lane);
+      pose_chunk(c, p, k, s, nst, abatch, st, lane);
+      __syncwarp();
+      if (lane < nst) derive_rec(c, k, st[lane], ob[(ch & 1) * kPipeChunk + lane]);
     }
     if (ch >= 1) {
       const int b = (ch - 1) & 1;
-      const StepRec* buf = recs + b * kPipeChunk;
+      const ObsRec* buf = ob + b * kPipeChunk;
       const int i0 = (ch - 1) * kPipeChunk, i1 = min(K, i0 + kPipeChunk);
       for (;;) {
         unsigned r = 0;
         if (lane == 0) r = atomicAdd(&next_step[group][b], 1u);
         const int i = i0 + (int)__shfl_sync(kFull, r, 0);
         if (i >= i1) break;
-        const StepRec& rec = buf[i - i0];
-        const Env post = rec.post, rpre = rec.pre;
-        const uint32_t done = rec.done, a = rec.a;
-        const float rew = obs_step(c, k, post, rpre, done, lane, o);
+        const ObsRec& R = buf[i - i0];
+        const uint32_t da = R.da, done = da & 0xFFu;
+        float rew = 0.0f;
+        if (done & 1u) {
+          rew = -10.0f;
+        } else if (done & 2u) {
+          rew = 75.0f;
+        } else if (done) {
+          const uint64_t pk = ((uint64_t)R.pnhi << 32) | R.pnlo;
+          rew = reward_finish(c, R.rpart, scan_pose(c, k, R.px, R.py, R.pphi, R.psigma, pk, lane, o));
+        }
+        const uint64_t nk = ((uint64_t)R.nhi << 32) | R.nlo;
+        const float mn = scan_pose(c, k, R.x, R.y, R.phi, R.sigma, nk, lane, o);
+        if (!done) rew = reward_finish(c, R.rpart, mn);
+        o.ex = lane < 5 ? R.ex[lane] : 0.0f;
         if (i == K - 1) has_last = true;
         if (obs_seq) write_obs(obs_seq + ((long long)i * n + env) * c.obs_dim, o, c.B, lane);
         if (lane == 0) {
-          if (act_seq) act_seq[i * n + env] = (uint8_t)a;
+          if (act_seq) act_seq[i * n + env] = (uint8_t)(da >> 8);
           if (rew_seq) rew_seq[i * n + env] = rew;
           if (done_seq) done_seq[i * n + env] = (uint8_t)done;
         }
@@ -377,11 +458,11 @@ __global__ void __launch_bounds__(512, 2) k_rollout_random_pipe(const __grid_con
     named_barrier(bar, nthr);
   }
   if (obs && has_last) write_obs(obs + (long long)env * c.obs_dim, o, c.B, lane);
-  if (role == 0 && lane == 0 && chunks > 0) {
-    const int last = ((chunks - 1) & 1) * kPipeChunk + (K - 1 - (chunks - 1) * kPipeChunk);
-    store_env(p, env, unpack_env(reinterpret_cast<const uint4*>(&recs[last].post)));
-  }
+  if (role == 0 && lane == 0 && chunks > 0)
+    store_env(p, env, unpack_env(reinterpret_cast<const uint4*>(&st[K - 1 - (chunks - 1) * kPipeChunk].post)));
 }
+
+size_t pipe_smem_bytes(int E) { return (size_t)E * kPipeChunk * (sizeof(StepRec) + 2 * sizeof(ObsRec)); }
 
 // Lane-parallel pose chain: warp 0 of a CTA simulates the pose chains of the
 // CTA's E envs, one env per lane, into a shared-memory chunk of step records;
@@ -882,7 +963,7 @@ extern "C" int sg_sim_rollout(sg_sim_t sim, int32_t K, int32_t policy, sg_qnet_t
       case SG_ROLLOUT_PIPE: {
         const int G = 1 + L.obs_warps;
         const int E = L.warps_per_block / G > 0 ? L.warps_per_block / G : 1;
-        const size_t smem = (size_t)E * 2 * kPipeChunk * sizeof(StepRec);
+        const size_t smem = pipe_smem_bytes(E);
         k_rollout_random_pipe<<<(n + E - 1) / E, 32 * G * E, smem, stream>>>(
             sim->dc, sp, K, L.obs_warps, obs_dev, obs_seq_dev, act_seq_dev, rew_seq_dev, done_seq_dev);
         break;
@@ -948,7 +1029,7 @@ extern "C" int sg_sim_set_launch(sg_sim_t sim, const sg_launch* cfg) {
   if (L.kernel == SG_ROLLOUT_PIPE) {
     const int G = 1 + L.obs_warps;
     const int E = L.warps_per_block / G > 0 ? L.warps_per_block / G : 1;
-    const size_t smem = (size_t)E * 2 * kPipeChunk * sizeof(StepRec);
+    const size_t smem = pipe_smem_bytes(E);
     SG_CUDA(cudaFuncSetAttribute((const void*)k_rollout_random_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
   }
