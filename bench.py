@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--extras", default="qnet,td,step,uneven,full",
                     help="comma list of secondary measurements: qnet, td, step, uneven, full")
     ap.add_argument("--launch", default=None,
-                    help="fixed rollout launch 'kernel:key=val,...' e.g. 'lanes:envs_per_block=4,obs_warps=15,chunk=16'"
+                    help="fixed rollout launch 'kernel:key=val,...' e.g. 'pipe:warps_per_block=8,obs_warps=7,order=map'"
                          " (skips the autotuner)")
     return ap.parse_args()
 
@@ -534,7 +534,7 @@ def _measured_peaks():
 
 def roofline_alu(samples_per_env_step, n, K, ms_per_step, clk):
     """March samples of the step definition per second against the lane-issue
-    bound of the SMs (see DESIGN: 152 SMs x 128 lanes x SM clock / 8 lane
+    bound of the SMs (152 SMs x 128 lanes x SM clock / 8 lane
     instructions per sample)."""
     mhz = (clk or {}).get("sm_mhz") or 2070.0
     peak = 152 * 128 * mhz * 1e6 / 8.0 / 1e9  # Gsample/s

@@ -211,20 +211,16 @@ int sg_sim_rollout(sg_sim_t sim, int32_t K, int32_t policy, sg_qnet_t qnet, cons
  *                     after each episode end) and then joins obs_warps
  *                     (1..15) warps that compute the scans, observations and
  *                     rewards of the previous chunk, taking steps from a
- *                     shared counter; max(1, warps_per_block /
- *                     (1 + obs_warps)) envs per CTA, warps_per_block 1..16.
- *   SG_ROLLOUT_LANES  per CTA one warp computes the pose chains of
- *                     envs_per_block (1..32) envs, one env per lane, in chunks
- *                     of `chunk` steps (1..256) into shared memory, and
- *                     obs_warps (1..31) warps compute the observation records
- *                     of the previous chunk.
+ *                     shared counter; min(3, max(1, warps_per_block /
+ *                     (1 + obs_warps))) envs per CTA, warps_per_block 1..16;
+ *                     order 0 = index order, 1 = envs grouped by map (CTAs
+ *                     share maps, so fewer maps compete for each SM's L1).
  * Synchronous (computes and uploads the work list on first use).
  */
 #define SG_ROLLOUT_GRID 0
 #define SG_ROLLOUT_QUEUE 1
 #define SG_ROLLOUT_SPLIT 2
 #define SG_ROLLOUT_PIPE 3
-#define SG_ROLLOUT_LANES 4
 typedef struct sg_launch {
   int32_t kernel;
   int32_t warps_per_block;

@@ -52,7 +52,7 @@ class sg_launch(C.Structure):
                 ("order", C.c_int32), ("chunk", C.c_int32)]
 
 
-SG_ROLLOUT_KERNELS = {"grid": 0, "queue": 1, "split": 2, "pipe": 3, "lanes": 4}
+SG_ROLLOUT_KERNELS = {"grid": 0, "queue": 1, "split": 2, "pipe": 3}
 
 
 class sg_sim_info(C.Structure):

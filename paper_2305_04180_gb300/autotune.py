@@ -27,9 +27,9 @@ def _cand(kernel, **kw):
 CANDIDATES = ([_cand("grid", warps_per_block=w) for w in (2, 4, 8)]
               + [_cand("queue", warps_per_block=w, order=o) for w in (2, 4, 8) for o in ("index", "cost")]
               + [_cand("split", warps_per_block=8, warps_per_env=W) for W in (2, 3, 4)]
-              + [_cand("pipe", warps_per_block=b, obs_warps=P) for P, b in ((3, 8), (5, 16), (7, 16))]
-              + [_cand("lanes", envs_per_block=E, obs_warps=P, chunk=D)
-                 for E, P, D in ((2, 7, 32), (4, 15, 16), (4, 11, 16), (8, 15, 16), (2, 15, 32), (1, 7, 32))])
+              + [_cand("pipe", warps_per_block=b, obs_warps=P, order=o)
+                 for P, b, o in ((7, 8, "map"), (7, 16, "map"), (7, 16, "index"), (3, 8, "map"), (3, 4, "map"),
+                                 (5, 12, "map"), (15, 16, "map"))])
 KEYS = ("kernel", "warps_per_block", "warps_per_env", "obs_warps", "envs_per_block", "blocks_per_sm", "order",
         "chunk")
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")

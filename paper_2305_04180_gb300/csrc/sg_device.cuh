@@ -335,38 +335,6 @@ __device__ __forceinline__ EnvConst env_const(const DevCfg& c, const SimPtrs& p,
   return k;
 }
 
-// The same collision test by one lane alone (rows in sequence).
-__device__ __forceinline__ bool collide_lane(const DevCfg& c, const MapDesc& m, const uint32_t* __restrict__ rows,
-                                             const uint8_t* __restrict__ clr, float x, float y) {
-  if (x < 0.0f || y < 0.0f || x >= (float)m.w || y >= (float)m.h) return true;
-  const int own = __ldg(clr + __float2int_rd(y) * m.w + __float2int_rd(x));
-  if (own >= c.clr_collide) return false;
-  const float r = c.robot_r;
-  const float r2 = r * r;
-  int cx0 = (int)floorf(x - r) - 1, cx1 = (int)floorf(x + r) + 1;
-  int cy0 = (int)floorf(y - r) - 1, cy1 = (int)floorf(y + r) + 1;
-  cx0 = max(cx0, 0);
-  cy0 = max(cy0, 0);
-  cx1 = min(cx1, m.w - 1);
-  cy1 = min(cy1, m.h - 1);
-  for (int cy = cy0; cy <= cy1; ++cy) {
-    const uint32_t* row = rows + (long long)cy * m.row_words;
-    for (int wd = cx0 >> 5; wd <= (cx1 >> 5); ++wd) {
-      const int lo = max(cx0 - wd * 32, 0), hi = min(cx1 - wd * 32, 31);
-      const uint32_t mask = (0xFFFFFFFFu >> (31 - hi)) & (0xFFFFFFFFu << lo);
-      uint32_t bits = __ldg(row + wd) & mask;
-      while (bits) {
-        const int b = __ffs(bits) - 1;
-        bits &= bits - 1;
-        const float dx = ((float)(wd * 32 + b) + 0.5f) - x;
-        const float dy = ((float)cy + 0.5f) - y;
-        if (fmaf(dx, dx, dy * dy) <= r2) return true;
-      }
-    }
-  }
-  return false;
-}
-
 // ---------------------------------------------------- observation
 // This lane's share of an observation row: beams lane and lane + 32, and
 // entry n_beams + lane for lanes 0..4.
@@ -521,14 +489,6 @@ __device__ __forceinline__ void reset_env(const DevCfg& c, const EnvConst& k, En
   const uint64_t h3 = shfl_u64(mine, 3), h4 = shfl_u64(mine, 4), h5 = shfl_u64(mine, 5);
   const uint64_t h6 = shfl_u64(mine, 6), h7 = shfl_u64(mine, 7);
   apply_draws(c, k.L, s, ep_id, h0, h1, h2, h3, h4, h5, h6, h7);
-}
-
-// The same draws by one lane alone (the lane simulates its own env).
-__device__ __forceinline__ void reset_env_lane(const DevCfg& c, const Layout& L, uint64_t rkey, Env& s,
-                                               uint32_t ep_id) {
-  const uint64_t pre = sm_at(rkey, (uint64_t)ep_id);
-  apply_draws(c, L, s, ep_id, sm_at(pre, 0ull), sm_at(pre, 1ull), sm_at(pre, 2ull), sm_at(pre, 3ull),
-              sm_at(pre, 4ull), sm_at(pre, 5ull), sm_at(pre, 6ull), sm_at(pre, 7ull));
 }
 
 // ------------------------------------------------------------- step

@@ -224,6 +224,12 @@ static_assert(sizeof(StepRec) == 128, "step record is eight 16-byte words");
 __device__ __forceinline__ void named_barrier(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(nthreads) : "memory");
 }
+// Arrive without waiting (the other side of a producer / consumer barrier);
+// the fence orders this warp's shared-memory accesses before the arrival.
+__device__ __forceinline__ void named_arrive(int id, int nthreads) {
+  __threadfence_block();
+  asm volatile("bar.arrive %0, %1;\n" ::"r"(id), "r"(nthreads) : "memory");
+}
 
 __device__ __forceinline__ uint32_t fbits(float f) { return __float_as_uint(f); }
 __device__ __forceinline__ float bitsf(uint32_t u) { return __uint_as_float(u); }
@@ -382,208 +388,123 @@ __device__ __forceinline__ void pose_chunk(const DevCfg& c, const SimPtrs& p, co
   if (bad && lane == 0) atomicOr(p.status, 1u);
 }
 
+// Consume the observation records of one chunk (steps i0 .. i1-1) through
+// the shared counter: scan, observation, reward, outputs.
+__device__ __forceinline__ void consume_chunk(const DevCfg& c, const EnvConst& k, const ObsRec* buf, unsigned* next,
+                                              int i0, int i1, int K, int env, long long n, int lane, ObsRegs& o,
+                                              bool& has_last, float* __restrict__ obs_seq,
+                                              uint8_t* __restrict__ act_seq, float* __restrict__ rew_seq,
+                                              uint8_t* __restrict__ done_seq) {
+  for (;;) {
+    unsigned r = 0;
+    if (lane == 0) r = atomicAdd(next, 1u);
+    const int i = i0 + (int)__shfl_sync(kFull, r, 0);
+    if (i >= i1) break;
+    const ObsRec& R = buf[i - i0];
+    const uint32_t da = R.da, done = da & 0xFFu;
+    float rew = 0.0f;
+    if (done & 1u) {
+      rew = -10.0f;
+    } else if (done & 2u) {
+      rew = 75.0f;
+    } else if (done) {
+      const uint64_t pk = ((uint64_t)R.pnhi << 32) | R.pnlo;
+      rew = reward_finish(c, R.rpart, scan_pose(c, k, R.px, R.py, R.pphi, R.psigma, pk, lane, o));
+    }
+    const uint64_t nk = ((uint64_t)R.nhi << 32) | R.nlo;
+    const float mn = scan_pose(c, k, R.x, R.y, R.phi, R.sigma, nk, lane, o);
+    if (!done) rew = reward_finish(c, R.rpart, mn);
+    o.ex = lane < 5 ? R.ex[lane] : 0.0f;
+    if (i == K - 1) has_last = true;
+    if (obs_seq) write_obs(obs_seq + ((long long)i * n + env) * c.obs_dim, o, c.B, lane);
+    if (lane == 0) {
+      if (act_seq) act_seq[i * n + env] = (uint8_t)(da >> 8);
+      if (rew_seq) rew_seq[i * n + env] = rew;
+      if (done_seq) done_seq[i * n + env] = (uint8_t)done;
+    }
+  }
+}
+
+// Named barriers of env group g: full(b) = 1 + 4g + b (records of buffer b
+// written: the pose warp arrives, the observation warps wait), free(b) =
+// 3 + 4g + b (buffer b consumed: the observation warps arrive, the pose warp
+// waits before writing it again).  At most kPipeMaxGroups groups per CTA.
+constexpr int kPipeMaxGroups = 3;
+
 __global__ void __launch_bounds__(512, 2) k_rollout_random_pipe(const __grid_constant__ DevCfg c, SimPtrs p, int K,
-                                                                int P, float* __restrict__ obs,
+                                                                int P, const int* __restrict__ order,
+                                                                float* __restrict__ obs,
                                                                 float* __restrict__ obs_seq,
                                                                 uint8_t* __restrict__ act_seq,
                                                                 float* __restrict__ rew_seq,
                                                                 uint8_t* __restrict__ done_seq) {
   extern __shared__ __align__(16) unsigned char pipe_smem[];
-  __shared__ unsigned next_step[16][2];  // per env group and buffer: next record to take
+  __shared__ unsigned next_step[kPipeMaxGroups][2];  // per env group and buffer: next record to take
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int G = 1 + P;  // warps per env
   const int group = warp / G, role = warp % G;
   const int E = blockDim.x / (32 * G);
-  const int env = blockIdx.x * E + group;
-  if (env >= c.n_envs) return;  // the whole group leaves together
+  const int slot = blockIdx.x * E + group;
+  if (slot >= c.n_envs) return;  // the whole group leaves together
+  const int env = order ? order[slot] : slot;
   // per group: kPipeChunk step records, then 2 x kPipeChunk observation records
   unsigned char* base = pipe_smem + (size_t)group * kPipeChunk * (sizeof(StepRec) + 2 * sizeof(ObsRec));
   StepRec* st = reinterpret_cast<StepRec*>(base);
   ObsRec* ob = reinterpret_cast<ObsRec*>(base + kPipeChunk * sizeof(StepRec));
-  const int bar = 1 + group, nthr = 32 * G;
+  const int bfull = 1 + 4 * group, bfree = 3 + 4 * group, nthr = 32 * G;
   const EnvConst k = env_const(c, p, env, lane);
   const long long n = c.n_envs;
   const int chunks = (K + kPipeChunk - 1) / kPipeChunk;
   ObsRegs o;
   o.b0 = o.b1 = o.ex = 0.0f;
   bool has_last = false;
-  for (int ch = 0; ch <= chunks; ++ch) {
-    if (role == 0 && ch < chunks) {
-      if (lane == 0) next_step[group][ch & 1] = 0u;
-      // the state carried between chunks is the last step record's post
-      // state, so nothing of the pose chain stays live while this warp takes
-      // observation records
-      Env s = ch == 0 ? load_env(p, env) : unpack_env(reinterpret_cast<const uint4*>(&st[kPipeChunk - 1].post));
-      const int i0 = ch * kPipeChunk, nst = min(K, i0 + kPipeChunk) - i0;
-      // lane l draws the action of step i0 + l (t counts every step)
-      const uint64_t akey = sm_at(sm_at(c.seed, kStreamAction), (uint64_t)env);
-      const uint32_t abatch = random_action_for(c, akey, s.t + (uint32_t)lane);
-      pose_chunk(c, p, k, s, nst, abatch, st, lane);
-      __syncwarp();
-      if (lane < nst) derive_rec(c, k, st[lane], ob[(ch & 1) * kPipeChunk + lane]);
-    }
-    if (ch >= 1) {
-      const int b = (ch - 1) & 1;
-      const ObsRec* buf = ob + b * kPipeChunk;
-      const int i0 = (ch - 1) * kPipeChunk, i1 = min(K, i0 + kPipeChunk);
-      for (;;) {
-        unsigned r = 0;
-        if (lane == 0) r = atomicAdd(&next_step[group][b], 1u);
-        const int i = i0 + (int)__shfl_sync(kFull, r, 0);
-        if (i >= i1) break;
-        const ObsRec& R = buf[i - i0];
-        const uint32_t da = R.da, done = da & 0xFFu;
-        float rew = 0.0f;
-        if (done & 1u) {
-          rew = -10.0f;
-        } else if (done & 2u) {
-          rew = 75.0f;
-        } else if (done) {
-          const uint64_t pk = ((uint64_t)R.pnhi << 32) | R.pnlo;
-          rew = reward_finish(c, R.rpart, scan_pose(c, k, R.px, R.py, R.pphi, R.psigma, pk, lane, o));
-        }
-        const uint64_t nk = ((uint64_t)R.nhi << 32) | R.nlo;
-        const float mn = scan_pose(c, k, R.x, R.y, R.phi, R.sigma, nk, lane, o);
-        if (!done) rew = reward_finish(c, R.rpart, mn);
-        o.ex = lane < 5 ? R.ex[lane] : 0.0f;
-        if (i == K - 1) has_last = true;
-        if (obs_seq) write_obs(obs_seq + ((long long)i * n + env) * c.obs_dim, o, c.B, lane);
-        if (lane == 0) {
-          if (act_seq) act_seq[i * n + env] = (uint8_t)(da >> 8);
-          if (rew_seq) rew_seq[i * n + env] = rew;
-          if (done_seq) done_seq[i * n + env] = (uint8_t)done;
-        }
+  if (role == 0) {
+    for (int ch = 0; ch <= chunks; ++ch) {
+      if (ch < chunks) {
+        const int b = ch & 1;
+        if (ch >= 2) named_barrier(bfree + b, nthr);  // chunk ch - 2 consumed
+        if (lane == 0) next_step[group][b] = 0u;
+        // the state carried between chunks is the last step record's post
+        // state, so nothing of the pose chain stays live while this warp
+        // takes observation records
+        Env s = ch == 0 ? load_env(p, env) : unpack_env(reinterpret_cast<const uint4*>(&st[kPipeChunk - 1].post));
+        const int i0 = ch * kPipeChunk, nst = min(K, i0 + kPipeChunk) - i0;
+        // lane l draws the action of step i0 + l (t counts every step)
+        const uint64_t akey = sm_at(sm_at(c.seed, kStreamAction), (uint64_t)env);
+        const uint32_t abatch = random_action_for(c, akey, s.t + (uint32_t)lane);
+        pose_chunk(c, p, k, s, nst, abatch, st, lane);
+        __syncwarp();
+        if (lane < nst) derive_rec(c, k, st[lane], ob[b * kPipeChunk + lane]);
+        named_arrive(bfull + b, nthr);
+      }
+      if (ch >= 1) {
+        const int b = (ch - 1) & 1, i0 = (ch - 1) * kPipeChunk;
+        consume_chunk(c, k, ob + b * kPipeChunk, &next_step[group][b], i0, min(K, i0 + kPipeChunk), K, env, n,
+                      lane, o, has_last, obs_seq, act_seq, rew_seq, done_seq);
       }
     }
-    named_barrier(bar, nthr);
+    // the last two chunks' consumption completes the free barriers' phases
+    for (int ch = max(chunks, 2); ch < chunks + 2; ++ch) named_barrier(bfree + (ch & 1), nthr);
+    if (lane == 0 && chunks > 0)
+      store_env(p, env, unpack_env(reinterpret_cast<const uint4*>(&st[K - 1 - (chunks - 1) * kPipeChunk].post)));
+  } else {
+    for (int ch = 1; ch <= chunks; ++ch) {
+      const int b = (ch - 1) & 1, i0 = (ch - 1) * kPipeChunk;
+      named_barrier(bfull + b, nthr);  // chunk ch - 1 written
+      consume_chunk(c, k, ob + b * kPipeChunk, &next_step[group][b], i0, min(K, i0 + kPipeChunk), K, env, n, lane,
+                    o, has_last, obs_seq, act_seq, rew_seq, done_seq);
+      named_arrive(bfree + b, nthr);
+    }
   }
   if (obs && has_last) write_obs(obs + (long long)env * c.obs_dim, o, c.B, lane);
-  if (role == 0 && lane == 0 && chunks > 0)
-    store_env(p, env, unpack_env(reinterpret_cast<const uint4*>(&st[K - 1 - (chunks - 1) * kPipeChunk].post)));
 }
 
-size_t pipe_smem_bytes(int E) { return (size_t)E * kPipeChunk * (sizeof(StepRec) + 2 * sizeof(ObsRec)); }
-
-// Lane-parallel pose chain: warp 0 of a CTA simulates the pose chains of the
-// CTA's E envs, one env per lane, into a shared-memory chunk of step records;
-// warps 1..P compute the scans, observations and rewards of the previous
-// chunk, one record at a time (lanes = beams).  The whole CTA meets at one
-// barrier per chunk.  The pose chain then costs a fraction 1/E of a warp per
-// env-step, and nearly every resident warp works on observations.
-struct EnvShared {
-  MapDesc m;         // 24 B
-  Layout L;          // 20 B
-  float stepb;       // beam spacing fov / (nb - 1)
-  int nb;
-  int pad;
-  uint64_t nkey;     // noise key prefix
-};
-constexpr int kRecStride = 9;  // StepRec + 16 B of padding, in 16-byte words (conflict-free lane stores)
-
-__device__ __forceinline__ void store_rec_lane(uint4* d, const Env& q, const Env& e, uint32_t done, uint32_t a) {
-  pack_env(d, e, a);
-  pack_env(d + 4, q, done);
+static size_t pipe_smem_bytes(int E) { return (size_t)E * kPipeChunk * (sizeof(StepRec) + 2 * sizeof(ObsRec)); }
+static int pipe_envs_per_block(const sg_launch& L) {
+  const int E = L.warps_per_block / (1 + L.obs_warps);
+  return E < 1 ? 1 : (E > kPipeMaxGroups ? kPipeMaxGroups : E);
 }
 
-__global__ void __launch_bounds__(512, 2) k_rollout_random_lanes(const __grid_constant__ DevCfg c, SimPtrs p, int K,
-                                                                 int E, int D, float* __restrict__ obs,
-                                                                 float* __restrict__ obs_seq,
-                                                                 uint8_t* __restrict__ act_seq,
-                                                                 float* __restrict__ rew_seq,
-                                                                 uint8_t* __restrict__ done_seq) {
-  extern __shared__ __align__(16) unsigned char lane_smem[];
-  EnvShared* es = reinterpret_cast<EnvShared*>(lane_smem);
-  uint4* recs = reinterpret_cast<uint4*>(lane_smem + ((E * sizeof(EnvShared) + 15) / 16) * 16);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int P = (blockDim.x >> 5) - 1;
-  const int env0 = blockIdx.x * E;
-  const int nE = min(E, c.n_envs - env0);
-  const long long n = c.n_envs;
-  // per-env constants, shared with the observation warps
-  Env s, pre;
-  MapDesc pm;
-  Layout pL;
-  uint64_t rkey = 0, akey = 0;
-  if (warp == 0 && lane < nE) {
-    const int env = env0 + lane;
-    pm = p.maps[p.env_map[env]];
-    pL = layout_of(c, pm);
-    const int nb = p.env_beams ? p.env_beams[env] : c.B;
-    EnvShared q;
-    q.m = pm;
-    q.L = pL;
-    q.stepb = c.fov / (float)(nb - 1);
-    q.nb = nb;
-    q.pad = 0;
-    q.nkey = sm_at(sm_at(c.seed, kStreamNoise), (uint64_t)env);
-    es[lane] = q;
-    rkey = sm_at(sm_at(c.seed, kStreamReset), (uint64_t)env);
-    akey = sm_at(sm_at(c.seed, kStreamAction), (uint64_t)env);
-    s = load_env(p, env);
-  }
-  __syncthreads();
-  const int chunks = (K + D - 1) / D;
-  for (int ch = 0; ch <= chunks; ++ch) {
-    if (warp == 0) {
-      if (ch < chunks && lane < nE) {
-        const uint32_t* rows = p.atlas + pm.word_off;
-        const uint8_t* clr = p.clr + pm.clr_off;
-        uint4* buf = recs + (size_t)(ch & 1) * D * E * kRecStride;
-        const int i0 = ch * D, i1 = min(K, i0 + D);
-        for (int i = i0; i < i1; ++i) {
-          const uint32_t a = random_action_for(c, akey, s.t);
-          if (kinematics(c, s, a)) atomicOr(p.status, 1u);
-          const bool col = collide_lane(c, pm, rows, clr, s.x, s.y);
-          const float ddx = pL.gx - s.x, ddy = pL.gy - s.y;
-          const float d1sq = fmaf(ddx, ddx, ddy * ddy);
-          const bool arrive = d1sq <= c.goal_r * c.goal_r;
-          const bool trunc = s.ep_step >= (uint32_t)c.t_max;
-          const uint32_t done = (col ? 1u : 0u) | (arrive ? 2u : 0u) | (trunc ? 4u : 0u);
-          pre = s;
-          if (done) reset_env_lane(c, pL, rkey, s, s.ep_id + 1u);
-          store_rec_lane(buf + ((size_t)(i - i0) * E + lane) * kRecStride, pre, s, done, a);
-        }
-      }
-    } else if (ch >= 1) {
-      const uint4* buf = recs + (size_t)((ch - 1) & 1) * D * E * kRecStride;
-      const int i0 = (ch - 1) * D, i1 = min(K, i0 + D);
-      const int R = (i1 - i0) * nE;
-      for (int r = warp - 1; r < R; r += P) {
-        const int e = r % nE, i = i0 + r / nE;
-        const StepRec& rec = *reinterpret_cast<const StepRec*>(buf + ((size_t)(i - i0) * E + e) * kRecStride);
-        const EnvShared q = es[e];
-        EnvConst k;
-        k.m = q.m;
-        k.rows = p.atlas + q.m.word_off;
-        k.clr = p.clr + q.m.clr_off;
-        k.L = q.L;
-        k.env = env0 + e;
-        k.nb = q.nb;
-        k.off0 = (float)lane * q.stepb - c.half_fov;
-        k.off1 = (float)(lane + 32) * q.stepb - c.half_fov;
-        k.nkey = q.nkey;
-        k.rkey = 0;
-        const Env post = rec.post, rpre = rec.pre;
-        ObsRegs o;
-        const float rew = obs_step(c, k, post, rpre, rec.done, lane, o);
-        const int env = env0 + e;
-        if (obs_seq) write_obs(obs_seq + ((long long)i * n + env) * c.obs_dim, o, c.B, lane);
-        if (obs && i == K - 1) write_obs(obs + (long long)env * c.obs_dim, o, c.B, lane);
-        if (lane == 0) {
-          if (act_seq) act_seq[i * n + env] = (uint8_t)rec.a;
-          if (rew_seq) rew_seq[i * n + env] = rew;
-          if (done_seq) done_seq[i * n + env] = (uint8_t)rec.done;
-        }
-      }
-    }
-    __syncthreads();
-  }
-  if (warp == 0 && lane < nE) store_env(p, env0 + lane, s);
-}
-
-size_t lanes_smem(int E, int D) {
-  return ((E * sizeof(EnvShared) + 15) / 16) * 16 + (size_t)2 * D * E * kRecStride * 16;
-}
 
 // W warps per env, E envs per CTA (blockDim = 32 W E).
 __global__ void __launch_bounds__(256, 4) k_rollout_random_split(const __grid_constant__ DevCfg c, SimPtrs p, int K,
@@ -954,18 +875,13 @@ extern "C" int sg_sim_rollout(sg_sim_t sim, int32_t K, int32_t policy, sg_qnet_t
     const int n = sim->dc.n_envs;
     const SimPtrs sp = sg_sim_ptrs(sim);
     switch (L.kernel) {
-      case SG_ROLLOUT_LANES: {
-        const int E = L.envs_per_block;
-        k_rollout_random_lanes<<<(n + E - 1) / E, 32 * (1 + L.obs_warps), lanes_smem(E, L.chunk), stream>>>(
-            sim->dc, sp, K, E, L.chunk, obs_dev, obs_seq_dev, act_seq_dev, rew_seq_dev, done_seq_dev);
-        break;
-      }
       case SG_ROLLOUT_PIPE: {
         const int G = 1 + L.obs_warps;
-        const int E = L.warps_per_block / G > 0 ? L.warps_per_block / G : 1;
+        const int E = pipe_envs_per_block(L);
         const size_t smem = pipe_smem_bytes(E);
         k_rollout_random_pipe<<<(n + E - 1) / E, 32 * G * E, smem, stream>>>(
-            sim->dc, sp, K, L.obs_warps, obs_dev, obs_seq_dev, act_seq_dev, rew_seq_dev, done_seq_dev);
+            sim->dc, sp, K, L.obs_warps, L.order ? sim->map_order_dev : nullptr, obs_dev, obs_seq_dev, act_seq_dev,
+            rew_seq_dev, done_seq_dev);
         break;
       }
       case SG_ROLLOUT_SPLIT: {
@@ -1016,27 +932,16 @@ extern "C" int sg_sim_set_launch(sg_sim_t sim, const sg_launch* cfg) {
         return SG_E_INVAL;
       break;
     case SG_ROLLOUT_PIPE:
-      if (L.obs_warps < 1 || L.obs_warps > 15 || L.warps_per_block < 1 || L.warps_per_block > 16) return SG_E_INVAL;
-      break;
-    case SG_ROLLOUT_LANES:
-      if (L.obs_warps < 1 || L.obs_warps > 31 || L.envs_per_block < 1 || L.envs_per_block > 32 || L.chunk < 1 ||
-          L.chunk > 256)
+      if (L.obs_warps < 1 || L.obs_warps > 15 || L.warps_per_block < 1 || L.warps_per_block > 16 || L.order < 0 ||
+          L.order > 1)
         return SG_E_INVAL;
       break;
     default:
       return SG_E_INVAL;
   }
   if (L.kernel == SG_ROLLOUT_PIPE) {
-    const int G = 1 + L.obs_warps;
-    const int E = L.warps_per_block / G > 0 ? L.warps_per_block / G : 1;
-    const size_t smem = pipe_smem_bytes(E);
+    const size_t smem = pipe_smem_bytes(pipe_envs_per_block(L));
     SG_CUDA(cudaFuncSetAttribute((const void*)k_rollout_random_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem));
-  }
-  if (L.kernel == SG_ROLLOUT_LANES) {
-    const size_t smem = lanes_smem(L.envs_per_block, L.chunk);
-    if (smem > 200 * 1024) return SG_E_INVAL;
-    SG_CUDA(cudaFuncSetAttribute((const void*)k_rollout_random_lanes, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
   }
   int sms = 0;

@@ -122,9 +122,13 @@ class Sim:
                    blocks_per_sm=0, order="index", chunk=32):
         """Launch configuration of the network-free rollout (sg_sim_set_launch);
         accepts the keys of ``launch_config()``."""
+        # order 1 is "cost" (longest first) for the work-list kernel and "map"
+        # (envs grouped by map) for the pipelined one
+        orders = {"queue": ("index", "cost"), "pipe": ("index", "map")}.get(kernel, ("index",))
+        if order not in orders:
+            raise ValueError(f"order {order!r} is not one of {orders} for kernel {kernel!r}")
         L = _lib.sg_launch(_lib.SG_ROLLOUT_KERNELS[kernel], int(warps_per_block), int(warps_per_env),
-                           int(obs_warps), int(envs_per_block), int(blocks_per_sm),
-                           {"index": 0, "cost": 1}[order], int(chunk))
+                           int(obs_warps), int(envs_per_block), int(blocks_per_sm), orders.index(order), int(chunk))
         check(self.L.sg_sim_set_launch(self.handle, C.byref(L)), "sg_sim_set_launch")
 
     def launch_config(self) -> dict:
@@ -133,7 +137,8 @@ class Sim:
         kinds = {v: k for k, v in _lib.SG_ROLLOUT_KERNELS.items()}
         return dict(kernel=kinds[L.kernel], warps_per_block=L.warps_per_block, warps_per_env=L.warps_per_env,
                     obs_warps=L.obs_warps, envs_per_block=L.envs_per_block, blocks_per_sm=L.blocks_per_sm,
-                    order={0: "index", 1: "cost"}[L.order], chunk=L.chunk)
+                    order="index" if L.order == 0 else ("map" if L.kernel == _lib.SG_ROLLOUT_KERNELS["pipe"]
+                                                         else "cost"), chunk=L.chunk)
 
     def get_state(self):
         """(f [9, N] float32, u [4, N] uint32) host copies of the env state."""

@@ -43,9 +43,8 @@ def test_uneven_launch_configurations_agree_and_match_oracle():
             dict(kernel="queue", warps_per_block=16), dict(kernel="split", warps_per_block=8, warps_per_env=3),
             dict(kernel="split", warps_per_block=8, warps_per_env=8), dict(kernel="split", warps_per_block=4, warps_per_env=5),
             dict(kernel="pipe", warps_per_block=8, obs_warps=3), dict(kernel="pipe", warps_per_block=16, obs_warps=4),
-            dict(kernel="pipe", warps_per_block=4, obs_warps=1), dict(kernel="lanes", envs_per_block=4, obs_warps=15, chunk=16),
-            dict(kernel="lanes", envs_per_block=7, obs_warps=3, chunk=5), dict(kernel="lanes", envs_per_block=32, obs_warps=1, chunk=8),
-            dict(kernel="lanes", envs_per_block=1, obs_warps=2, chunk=17))
+            dict(kernel="pipe", warps_per_block=4, obs_warps=1), dict(kernel="pipe", warps_per_block=12, obs_warps=3, order="map"),
+            dict(kernel="pipe", warps_per_block=8, obs_warps=7, order="map"))
     for cfg in cfgs:
         s = Sim(p, maps, env_map, beams)
         if cfg:
@@ -88,7 +87,8 @@ def test_pipelined_pose_chain_with_frequent_episode_ends():
     K = 100
     results = []
     for cfg in (None, dict(kernel="pipe", warps_per_block=16, obs_warps=7),
-                dict(kernel="pipe", warps_per_block=8, obs_warps=3), dict(kernel="pipe", warps_per_block=2, obs_warps=1)):
+                dict(kernel="pipe", warps_per_block=8, obs_warps=3, order="map"),
+                dict(kernel="pipe", warps_per_block=2, obs_warps=1)):
         s = Sim(p, maps, env_map, beams)
         if cfg:
             s.set_launch(**cfg)
@@ -111,6 +111,44 @@ def test_pipelined_pose_chain_with_frequent_episode_ends():
             obs, rew, done, _ = o.step_one(i, o.random_action(i, k))
             assert done == d[k, i] and bits(np.float32(rew)) == bits(ref["rew"][k, i]), (i, k)
             assert np.array_equal(bits(obs), bits(ref["obs_seq"][k, i])), (i, k)
+
+
+@pytest.mark.parametrize("K", [1, 31, 32, 33, 64, 97])
+def test_pipelined_rollout_lengths(K):
+    """Rollouts of 1 to 4 chunks, full and ragged: the pipelined kernel's
+    chunk hand-over (records written / consumed) gives the one-warp-per-env
+    results and final state."""
+    from paper_2305_04180_gb300 import Sim
+
+    p, maps, env_map, beams = _uneven(50, seed=3)
+    out = []
+    for cfg in (None, dict(kernel="pipe", warps_per_block=16, obs_warps=7), dict(kernel="pipe", warps_per_block=16,
+                                                                                obs_warps=4),
+                dict(kernel="pipe", warps_per_block=16, obs_warps=7, order="map")):
+        s = Sim(p, maps, env_map, beams)
+        if cfg:
+            s.set_launch(**cfg)
+        s.reset()
+        obs = s.new_obs()
+        r = _run_obs(s, K, obs)
+        out.append((r, obs.cpu().numpy(), s.get_state()))
+    (ref, obs0, (f0, u0)) = out[0]
+    for r, ob, (f, u) in out[1:]:
+        for k in ref:
+            assert np.array_equal(bits(r[k]) if r[k].dtype == np.float32 else r[k],
+                                  bits(ref[k]) if ref[k].dtype == np.float32 else ref[k]), k
+        assert np.array_equal(bits(ob), bits(obs0))
+        assert np.array_equal(bits(f), bits(f0)) and np.array_equal(u, u0)
+
+
+def _run_obs(sim, K, obs):
+    n = sim.n
+    out = dict(obs_seq=torch.empty((K, n, sim.obs_dim), device="cuda"),
+               rew=torch.empty((K, n), device="cuda"),
+               done=torch.empty((K, n), dtype=torch.uint8, device="cuda"))
+    sim.rollout(K, obs=obs, obs_seq=out["obs_seq"], rew_seq=out["rew"], done_seq=out["done"])
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
 
 
 def test_graph_replay_equals_direct_calls():
