@@ -226,10 +226,9 @@ typedef struct sg_launch {
   int32_t warps_per_block;
   int32_t warps_per_env;
   int32_t obs_warps;
-  int32_t envs_per_block;
   int32_t blocks_per_sm;
   int32_t order;
-  int32_t chunk;
+  int32_t reserved[2]; /* 0 */
 } sg_launch;
 int sg_sim_set_launch(sg_sim_t sim, const sg_launch* cfg);
 int sg_sim_get_launch(sg_sim_t sim, sg_launch* cfg);

@@ -18,8 +18,7 @@ import numpy as np
 import torch
 
 def _cand(kernel, **kw):
-    d = dict(kernel=kernel, warps_per_block=4, warps_per_env=1, obs_warps=0, envs_per_block=0, blocks_per_sm=0,
-             order="index", chunk=32)
+    d = dict(kernel=kernel, warps_per_block=4, warps_per_env=1, obs_warps=0, blocks_per_sm=0, order="index")
     d.update(kw)
     return d
 
@@ -30,8 +29,7 @@ CANDIDATES = ([_cand("grid", warps_per_block=w) for w in (2, 4, 8)]
               + [_cand("pipe", warps_per_block=b, obs_warps=P, order=o)
                  for P, b, o in ((7, 8, "map"), (7, 16, "map"), (7, 16, "index"), (3, 8, "map"), (3, 4, "map"),
                                  (5, 12, "map"), (15, 16, "map"))])
-KEYS = ("kernel", "warps_per_block", "warps_per_env", "obs_warps", "envs_per_block", "blocks_per_sm", "order",
-        "chunk")
+KEYS = ("kernel", "warps_per_block", "warps_per_env", "obs_warps", "blocks_per_sm", "order")
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
 

@@ -118,8 +118,8 @@ class Sim:
               "sg_sim_rollout")
         return obs
 
-    def set_launch(self, kernel="grid", warps_per_block=4, warps_per_env=1, obs_warps=0, envs_per_block=0,
-                   blocks_per_sm=0, order="index", chunk=32):
+    def set_launch(self, kernel="grid", warps_per_block=4, warps_per_env=1, obs_warps=0, blocks_per_sm=0,
+                   order="index"):
         """Launch configuration of the network-free rollout (sg_sim_set_launch);
         accepts the keys of ``launch_config()``."""
         # order 1 is "cost" (longest first) for the work-list kernel and "map"
@@ -128,7 +128,7 @@ class Sim:
         if order not in orders:
             raise ValueError(f"order {order!r} is not one of {orders} for kernel {kernel!r}")
         L = _lib.sg_launch(_lib.SG_ROLLOUT_KERNELS[kernel], int(warps_per_block), int(warps_per_env),
-                           int(obs_warps), int(envs_per_block), int(blocks_per_sm), orders.index(order), int(chunk))
+                           int(obs_warps), int(blocks_per_sm), orders.index(order))
         check(self.L.sg_sim_set_launch(self.handle, C.byref(L)), "sg_sim_set_launch")
 
     def launch_config(self) -> dict:
@@ -136,9 +136,9 @@ class Sim:
         check(self.L.sg_sim_get_launch(self.handle, C.byref(L)), "sg_sim_get_launch")
         kinds = {v: k for k, v in _lib.SG_ROLLOUT_KERNELS.items()}
         return dict(kernel=kinds[L.kernel], warps_per_block=L.warps_per_block, warps_per_env=L.warps_per_env,
-                    obs_warps=L.obs_warps, envs_per_block=L.envs_per_block, blocks_per_sm=L.blocks_per_sm,
+                    obs_warps=L.obs_warps, blocks_per_sm=L.blocks_per_sm,
                     order="index" if L.order == 0 else ("map" if L.kernel == _lib.SG_ROLLOUT_KERNELS["pipe"]
-                                                         else "cost"), chunk=L.chunk)
+                                                         else "cost"))
 
     def get_state(self):
         """(f [9, N] float32, u [4, N] uint32) host copies of the env state."""

@@ -138,7 +138,7 @@ def test_step_degenerate_cases():
     assert g.status() == 0  # reading clears it
 
 
-@pytest.mark.parametrize("launch", [None, dict(kernel="pipe", warps_per_block=16, obs_warps=7)])
+@pytest.mark.parametrize("launch", [None, dict(kernel="pipe", warps_per_block=8, obs_warps=7, order="map")])
 def test_rollout_random_free_running_bit_exact(launch):
     """1000 free-running steps with on-device random actions: every step's
     action, reward, done flags and observation, and the final state, equal
@@ -192,7 +192,7 @@ def test_rollout_continues_across_calls_and_matches_steps():
     assert np.array_equal(bits(fa), bits(fb)) and np.array_equal(ua, ub)
 
 
-@pytest.mark.parametrize("launch", [None, dict(kernel="pipe", warps_per_block=16, obs_warps=7)])
+@pytest.mark.parametrize("launch", [None, dict(kernel="pipe", warps_per_block=8, obs_warps=7, order="map")])
 def test_rollout_full_size_sampled_against_oracle(launch):
     """The 1024-env, 32-map domain-randomised workload (one warp per env, and
     the pipelined launch the benchmark times): 300 steps on the GPU, then a
