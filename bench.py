@@ -458,8 +458,22 @@ def run_uneven(flush):
         ms = _time_cuda(lambda: g.launch(st), 5, flush)
     return {"workload": w.name, "n_envs": sim.n, "maps": sim.n_maps, "steps_per_graph": K,
             "value": sim.n * K / (ms / 1e3), "unit": UNIT, "ms_per_graph": ms,
-            "autotuned": tune["config"], "autotune_table_ms": {f"{r['warps_per_block']}w-{'pq' if r['persistent'] else 'grid'}-{r['order']}": round(r["ms"], 4) for r in tune["table"]},
+            "autotuned": tune["config"], "autotune_table_ms": {launch_label(r): round(r["ms"], 4) for r in tune["table"]},
             "atlas_build_s": build_s}
+
+
+def launch_label(r):
+    """Short name of a launch configuration, e.g. 'pipe:8w:7obs:map'."""
+    s = f"{r['kernel']}:{r['warps_per_block']}w"
+    if r["kernel"] == "split":
+        s += f":{r['warps_per_env']}wpe"
+    if r["kernel"] == "pipe":
+        s += f":{r['obs_warps']}obs"
+    if r.get("blocks_per_sm"):
+        s += f":{r['blocks_per_sm']}bps"
+    if r.get("order", "index") != "index":
+        s += f":{r['order']}"
+    return s
 
 
 def run_full_loop(flush):
@@ -498,9 +512,10 @@ def run_full_loop(flush):
             "ring": f"{tr.replay.capacity} transitions (reserve 32 slots)", "graph_nodes": g.num_nodes()}
 
 
-def _recorded_traffic(n_envs, K):
+def _recorded_traffic(n_envs, K, kernel):
     """DRAM bytes per launch of the timed kernel from the committed ncu record,
-    if the kernel sources are unchanged since it was taken (else None)."""
+    if it was taken on this kernel and workload and the kernel sources are
+    unchanged since (else None)."""
     import hashlib
 
     try:
@@ -516,7 +531,7 @@ def _recorded_traffic(n_envs, K):
                        for f in ("sg_device.cuh", "sg_sim.cu"))
         if hashlib.sha1(src).hexdigest()[:16] != rec.get("source_sha1"):
             return None
-        if int(rec["n_envs"]) != n_envs or int(rec["steps_per_launch"]) != K:
+        if int(rec["n_envs"]) != n_envs or int(rec["steps_per_launch"]) != K or rec.get("kernel") != kernel:
             return None
         return int(rec["dram_bytes_read"]) + int(rec["dram_bytes_write"])
     except Exception:
@@ -565,7 +580,10 @@ def main():
         samples_per_env_step = 1500.0
     out["roofline"] = roofline_alu(samples_per_env_step, n, K, ms_per_step, clk)
     out["roofline"]["samples_per_env_step"] = samples_per_env_step
-    out["roofline"]["traffic"] = _recorded_traffic(n, K)
+    kname = {"grid": "k_rollout_random"}.get(out["config"]["launch"]["kernel"],
+                                              "k_rollout_random_" + out["config"]["launch"]["kernel"])
+    out["roofline"]["kernel"] = kname
+    out["roofline"]["traffic"] = _recorded_traffic(n, K, kname)
     out["roofline"]["traffic_unit"] = "DRAM bytes per launch (ncu record in profiles/)"
     # the streaming view: bytes a step must see if the map window and the SoA
     # state were streamed from HBM every step (the rollout keeps them on chip)
