@@ -199,7 +199,9 @@ def run_ours(a):
         sim.set_launch(kernel, **kw)
         tune = {"config": sim.launch_config()}
     else:
-        tune = autotune_rollout(sim, K=512, reps=2, cache_path=None)  # untimed; restores the env state
+        # untimed; restores the env state.  2,048-step trials: long enough for
+        # the CTA waves of a 10,000-step rollout to show
+        tune = autotune_rollout(sim, K=2048, reps=2, cache_path=None)
     obs = sim.new_obs()
     obs_seq = torch.empty((K, n, sim.obs_dim), dtype=torch.float32, device="cuda")
     rew_seq = torch.empty((K, n), dtype=torch.float32, device="cuda")
@@ -512,7 +514,11 @@ def run_full_loop(flush):
             "ring": f"{tr.replay.capacity} transitions (reserve 32 slots)", "graph_nodes": g.num_nodes()}
 
 
-def _recorded_traffic(n_envs, K, kernel):
+# vectorized steps of the CPU-oracle sample (about 10 s on 16 cores at 1,024 envs)
+CPU_SAMPLE_STEPS = 16000
+
+
+def _recorded_traffic(n_envs, K, kernel, launch):
     """DRAM bytes per launch of the timed kernel from the committed ncu record,
     if it was taken on this kernel and workload and the kernel sources are
     unchanged since (else None)."""
@@ -531,7 +537,8 @@ def _recorded_traffic(n_envs, K, kernel):
                        for f in ("sg_device.cuh", "sg_sim.cu"))
         if hashlib.sha1(src).hexdigest()[:16] != rec.get("source_sha1"):
             return None
-        if int(rec["n_envs"]) != n_envs or int(rec["steps_per_launch"]) != K or rec.get("kernel") != kernel:
+        if (int(rec["n_envs"]) != n_envs or int(rec["steps_per_launch"]) != K or rec.get("kernel") != kernel
+                or rec.get("launch") != launch):
             return None
         return int(rec["dram_bytes_read"]) + int(rec["dram_bytes_write"])
     except Exception:
@@ -569,10 +576,10 @@ def main():
     cores = os.cpu_count() or 1
     samples_per_env_step = None
     if pool is not None:
-        steps, wall, busy, samples = time_oracle(pool, cores, a.workload, n, 1000)
+        steps, wall, busy, samples = time_oracle(pool, cores, a.workload, n, CPU_SAMPLE_STEPS)
         samples_per_env_step = samples / steps
         out["cpu_baseline"] = {"value": steps / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
-                               "sample": f"{n} envs x 1000 steps of the same workload (f32 oracle, "
+                               "sample": f"{n} envs x {CPU_SAMPLE_STEPS} steps of the same workload (f32 oracle, "
                                          f"{cores} spawned processes sharded by env)",
                                "wall_s": wall}
         pool.close()
@@ -583,7 +590,7 @@ def main():
     kname = {"grid": "k_rollout_random"}.get(out["config"]["launch"]["kernel"],
                                               "k_rollout_random_" + out["config"]["launch"]["kernel"])
     out["roofline"]["kernel"] = kname
-    out["roofline"]["traffic"] = _recorded_traffic(n, K, kname)
+    out["roofline"]["traffic"] = _recorded_traffic(n, K, kname, launch_label(out["config"]["launch"]))
     out["roofline"]["traffic_unit"] = "DRAM bytes per launch (ncu record in profiles/)"
     # the streaming view: bytes a step must see if the map window and the SoA
     # state were streamed from HBM every step (the rollout keeps them on chip)
