@@ -377,6 +377,23 @@ int sg_td_train_step(sg_qnet_t q, sg_replay_t replay, int32_t batch, float gamma
                      uint64_t seed, float* loss_dev, float* grad_dev, sg_stream_t stream);
 
 /*
+ * VEM exploration noise (Sec. 3.1.1, "Vectorized data collection"; schedule
+ * values of the hyper-parameter table): writes eps_dev[i] for the sim's n
+ * envs at the current number of interacting steps T = n * t, where t is env
+ * 0's step counter on the device (so a captured graph advances the schedule
+ * as it replays).  The exploring interval
+ *     OR(T) = or_start + (or_final - or_start) * min(1, T / decay_steps)
+ * (a real number of envs) takes the last envs of the index range: env i with
+ * i >= n - OR gets e_min + e_max * (i - (n - OR)) / (OR - 1), the others (the
+ * exploiting interval) get e_min.  With OR = n this is e_min for env 0 up to
+ * e_min + e_max for env n - 1.  Evaluated in float64, stored as float.
+ *   2 <= or_final <= n, 2 <= or_start <= n, decay_steps > 0, e_min, e_max >= 0.
+ * eps_dev: n floats, caller-owned device memory.  Asynchronous on stream.
+ */
+int sg_vem_eps(sg_sim_t sim, float e_min, float e_max, double or_start, double or_final, double decay_steps,
+               float* eps_dev, sg_stream_t stream);
+
+/*
  * TD loss and gradient that allocates nothing (the paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory --
  * code under a fixed memory budget, inside another framework's allocator, or

@@ -987,6 +987,34 @@ extern "C" int sg_replay_write(sg_replay_t r, int64_t first, int64_t count, cons
   return SG_OK;
 }
 
+// VEM noise per env at T = n * t (t: env 0's step counter); see sg_vem_eps.
+__global__ void k_vem_eps(const uint32_t* __restrict__ t_dev, int n, float e_min, float e_max, double or_start,
+                          double or_final, double decay, float* __restrict__ eps) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double T = (double)n * (double)t_dev[0];
+  const double frac = T / decay < 1.0 ? T / decay : 1.0;
+  const double OR = or_start + (or_final - or_start) * frac;
+  const double first = (double)n - OR;
+  double e = (double)e_min;
+  if ((double)i >= first) e = (double)e_min + (double)e_max * (((double)i - first) / (OR - 1.0));
+  eps[i] = (float)e;
+}
+
+extern "C" int sg_vem_eps(sg_sim_t sim, float e_min, float e_max, double or_start, double or_final,
+                          double decay_steps, float* eps_dev, sg_stream_t stream) {
+  if (!sim || !eps_dev) return SG_E_INVAL;
+  const int n = sim->dc.n_envs;
+  if (!(or_final >= 2.0 && or_final <= n && or_start >= 2.0 && or_start <= n && decay_steps > 0.0 &&
+        e_min >= 0.0f && e_max >= 0.0f))
+    return SG_E_INVAL;
+  // u is [4][n]: ep_step, ep_id, t, fifo
+  k_vem_eps<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(sim->ustate + 2 * (size_t)n, n, e_min, e_max, or_start,
+                                                               or_final, decay_steps, eps_dev);
+  SG_CUDA(cudaGetLastError());
+  return SG_OK;
+}
+
 int sg_rollout_eps_q(sg_sim* sim, int K, sg_qnet* q, const float* eps, sg_replay* rp, float* obs, float* obs_seq,
                      uint8_t* act_seq, float* rew_seq, uint8_t* done_seq, cudaStream_t stream) {
   if (q->n_in != sim->dc.obs_dim) return SG_E_INVAL;

@@ -109,6 +109,18 @@ class Sim:
                                  _stream(stream)), "sg_sim_step")
         return obs, rew, done
 
+    def vem_eps(self, e_min=0.01, e_max=0.8, or_start=None, or_final=None, decay_steps=500_000, out=None,
+                stream=None):
+        """VEM exploration noise per env at the current interacting-step count
+        (sg_vem_eps).  OR defaults to the paper's Sparrow schedule scaled to N:
+        from N envs down to 3/16 of them (16 -> 3 at N = 16)."""
+        out = torch.empty(self.n, dtype=torch.float32, device=self.device) if out is None else out
+        or_start = float(self.n if or_start is None else or_start)
+        or_final = float(max(2.0, 3.0 * self.n / 16.0) if or_final is None else or_final)
+        check(self.L.sg_vem_eps(self.handle, float(e_min), float(e_max), or_start, or_final, float(decay_steps),
+                                _ptr(out), _stream(stream)), "sg_vem_eps")
+        return out
+
     def rollout(self, K, policy="random", qnet=None, eps=None, replay=None, obs=None, obs_seq=None, act_seq=None,
                 rew_seq=None, done_seq=None, stream=None):
         pol = {"random": _lib.SG_POLICY_RANDOM, "eps_q": _lib.SG_POLICY_EPS_Q}[policy]

@@ -201,6 +201,7 @@ def test_graph_actor_learner_iteration_sequential_is_deterministic():
     g = ta.capture_iteration(8, 4, concurrent=False)
     for _ in range(5):
         g.launch(ta.s_actor)
+        tb.sim.vem_eps(**tb.vem, out=tb.eps)  # the graph recomputes the VEM noise before its rollout
         tb.sim.rollout(8, policy="eps_q", qnet=tb.actor, eps=tb.eps, replay=tb.replay)
         for _ in range(4):
             tb.learner.train_step(tb.replay, tb.batch, lr=tb.lr, target_every=tb.target_every, seed=tb.seed)
