@@ -491,6 +491,15 @@ __device__ __forceinline__ void reset_env(const DevCfg& c, const EnvConst& k, En
   apply_draws(c, k.L, s, ep_id, h0, h1, h2, h3, h4, h5, h6, h7);
 }
 
+// The same draws by one lane alone (the lane holds its own env): slot j of
+// the episode hash is sm_at(pre, j), as reset_env's lane j computes it.
+__device__ __forceinline__ void reset_env_lane(const DevCfg& c, const Layout& L, uint64_t rkey, Env& s,
+                                               uint32_t ep_id) {
+  const uint64_t pre = sm_at(rkey, (uint64_t)ep_id);
+  apply_draws(c, L, s, ep_id, sm_at(pre, 0ull), sm_at(pre, 1ull), sm_at(pre, 2ull), sm_at(pre, 3ull),
+              sm_at(pre, 4ull), sm_at(pre, 5ull), sm_at(pre, 6ull), sm_at(pre, 7ull));
+}
+
 // ------------------------------------------------------------- step
 // Control delay, target velocity, Eq. 5, Eq. 6 (new velocity, old heading),
 // heading wrap into [-pi, pi).

@@ -118,22 +118,162 @@ __global__ void __launch_bounds__(128) k_reset(const __grid_constant__ DevCfg c,
 }
 
 // One vectorized step; one warp per env.
-__global__ void __launch_bounds__(128, 8) k_step(const __grid_constant__ DevCfg c, SimPtrs p, const uint8_t* __restrict__ act,
-                                              float* __restrict__ obs, float* __restrict__ rew,
-                                              uint8_t* __restrict__ done, float* __restrict__ term) {
-  const int env = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (env >= c.n_envs) return;
-  const EnvConst k = env_const(c, p, env, lane);
-  Env s = load_env(p, env);
-  ObsRegs o;
-  const StepOut r = env_step(c, p, k, s, (uint32_t)act[env], lane, o,
-                             term ? term + (long long)env * c.obs_dim : nullptr);
-  write_obs(obs + (long long)env * c.obs_dim, o, c.B, lane);
-  if (lane == 0) {
-    rew[env] = r.rew;
-    done[env] = (uint8_t)r.done;
-    store_env(p, env, s);
+// One vectorized step of every env (sg_sim_step).  A CTA takes 32 envs
+// (consecutive in the env order grouped by map).
+// Warp 0 runs the scalar part of the step lane-parallel, one env per lane:
+// state load, delay, Eq. 5, Eq. 6, the collision test's map-bounds and
+// clearance parts, arrival, truncation, the AutoReset draws and everything of
+// the observation and of Eq. 11 that does not need a scan; envs whose
+// collision test needs the bit rows get it from the whole warp.  Then the 8
+// warps scan the 32 envs (lane j marches beam j), four envs each: the
+// post-motion state always (the observation, or the terminal observation and
+// the reward of a done env), the reset state of a done env.  Every value is
+// the one-env-per-warp step's, in the same float32 expressions.
+constexpr int kStepEnvs = 32;
+constexpr int kStepWarps = 8;
+
+struct __align__(16) StepScanRec {
+  float ax, ay, aphi, asigma;  // post-motion state (scan A)
+  uint32_t anlo, anhi;         // its noise key
+  float rpart;                 // scan-free part of Eq. 11 at the post-motion state
+  uint32_t done;
+  float exa[5];                // observation entries B .. B + 4 of scan A
+  float bx, by, bphi;          // reset state (scan B, done envs)
+  float bsigma;
+  uint32_t bnlo, bnhi;
+  int map, nb;
+  float exb[5];                // observation entries of scan B
+  float stepb;                 // beam spacing of the env
+  int env;
+  int pad[3];
+};
+static_assert(sizeof(StepScanRec) == 128, "step scan record is eight 16-byte words");
+
+// Scan of one pose by the warp for an env of map m with nb beams: this
+// lane's normalised ranges into b0 / b1; returns the minimum noise-free range.
+__device__ __forceinline__ float scan_env(const DevCfg& c, const SimPtrs& p, const MapDesc& m, int nb, float stepb,
+                                          float x, float y, float phi, float sigma, uint64_t nk, int lane,
+                                          float& b0, float& b1) {
+  EnvConst k;
+  k.m = m;
+  k.clr = p.clr + m.clr_off;
+  k.nb = nb;
+  const float off0 = (float)lane * stepb - c.half_fov;
+  const float off1 = (float)(lane + 32) * stepb - c.half_fov;
+  float n0 = 0.0f, n1 = 0.0f;
+  if (sigma > 0.0f) {
+    n0 = box_muller(sm_at(nk, (uint64_t)lane));
+    if (nb > 32) n1 = box_muller(sm_at(nk, (uint64_t)(lane + 32)));
+  }
+  float mn = c.range_max;
+  b0 = lane < nb ? beam_at(c, k, x, y, phi, sigma, off0, n0, mn) : 1.0f;
+  b1 = lane + 32 < nb ? beam_at(c, k, x, y, phi, sigma, off1, n1, mn) : 1.0f;
+  return __uint_as_float(__reduce_min_sync(kFull, __float_as_uint(mn)));
+}
+
+__device__ __forceinline__ void write_row(float* row, float b0, float b1, const float* ex, int B, int lane) {
+  if (lane < B) row[lane] = b0;
+  if (lane + 32 < B) row[lane + 32] = b1;
+  if (lane < 5) row[B + lane] = ex[lane];
+}
+
+__global__ void __launch_bounds__(256, 4) k_step(const __grid_constant__ DevCfg c, SimPtrs p,
+                                                 const int* __restrict__ order, const uint8_t* __restrict__ act,
+                                                 float* __restrict__ obs, float* __restrict__ rew,
+                                                 uint8_t* __restrict__ done, float* __restrict__ term) {
+  __shared__ StepScanRec rec[kStepEnvs];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int base = blockIdx.x * kStepEnvs;
+  const int nv = min(kStepEnvs, c.n_envs - base);
+  if (warp == 0) {
+    // envs grouped by map, so that the CTA's scans share cache lines
+    const bool live = lane < nv;
+    const int i = live ? order[base + lane] : 0;
+    Env s;
+    MapDesc m;
+    Layout L;
+    int mid = 0, nb = c.B;
+    uint32_t d = 0;
+    bool slow = false;
+    if (live) {
+      mid = p.env_map[i];
+      m = p.maps[mid];
+      L = layout_of(c, m);
+      nb = p.env_beams ? p.env_beams[i] : c.B;
+      s = load_env(p, i);
+      if (kinematics(c, s, (uint32_t)act[i])) atomicOr(p.status, 1u);
+      if (s.x < 0.0f || s.y < 0.0f || s.x >= (float)m.w || s.y >= (float)m.h) {
+        d = 1u;
+      } else {
+        const int own = __ldg(p.clr + m.clr_off + __float2int_rd(s.y) * m.w + __float2int_rd(s.x));
+        slow = own < c.clr_collide;
+      }
+      const float ddx = L.gx - s.x, ddy = L.gy - s.y;
+      if (fmaf(ddx, ddx, ddy * ddy) <= c.goal_r * c.goal_r) d |= 2u;
+      if (s.ep_step >= (uint32_t)c.t_max) d |= 4u;
+    }
+    // collision tests that need the bit rows, one env at a time
+    unsigned sm = __ballot_sync(kFull, slow);
+    while (sm) {
+      const int e = __ffs(sm) - 1;
+      sm &= sm - 1u;
+      const MapDesc me = p.maps[__shfl_sync(kFull, mid, e)];
+      const float xe = __shfl_sync(kFull, live ? s.x : 0.0f, e), ye = __shfl_sync(kFull, live ? s.y : 0.0f, e);
+      if (collide_rows_warp(c, me, p.atlas + me.word_off, xe, ye, lane) && lane == e) d |= 1u;
+    }
+    if (live) {
+      StepScanRec& r = rec[lane];
+      const uint64_t nkey = sm_at(sm_at(c.seed, kStreamNoise), (uint64_t)i);
+      const GoalFrame g = goal_frame(L, s);
+      const uint64_t nka = sm_at(nkey, ((uint64_t)s.ep_id << 32) | s.ep_step);
+      r.ax = s.x, r.ay = s.y, r.aphi = s.phi, r.asigma = s.sigma;
+      r.anlo = (uint32_t)nka, r.anhi = (uint32_t)(nka >> 32);
+      for (int q = 0; q < 5; ++q) r.exa[q] = obs_extra(c, L, s, g, q);
+      r.rpart = (d & 3u) ? 0.0f : reward_partial(c, L, s, g.alpha, g.ddx, g.ddy);
+      r.done = d;
+      r.map = mid;
+      r.env = i;
+      r.nb = nb;
+      r.stepb = c.fov / (float)(nb - 1);
+      if (d) {
+        // AutoReset (Sec. 3.2.5): a new episode, observed at its step 0
+        const uint64_t rkey = sm_at(sm_at(c.seed, kStreamReset), (uint64_t)i);
+        reset_env_lane(c, L, rkey, s, s.ep_id + 1u);
+        const GoalFrame gb = goal_frame(L, s);
+        const uint64_t nkb = sm_at(nkey, ((uint64_t)s.ep_id << 32) | s.ep_step);
+        r.bx = s.x, r.by = s.y, r.bphi = s.phi, r.bsigma = s.sigma;
+        r.bnlo = (uint32_t)nkb, r.bnhi = (uint32_t)(nkb >> 32);
+        for (int q = 0; q < 5; ++q) r.exb[q] = obs_extra(c, L, s, gb, q);
+      }
+      store_env(p, i, s);
+      done[i] = (uint8_t)d;
+    }
+  }
+  __syncthreads();
+  for (int e = warp; e < nv; e += kStepWarps) {
+    const StepScanRec& r = rec[e];
+    const int i = r.env;
+    const MapDesc m = p.maps[r.map];
+    const uint32_t d = r.done;
+    float b0, b1;
+    const float mn = scan_env(c, p, m, r.nb, r.stepb, r.ax, r.ay, r.aphi, r.asigma,
+                              ((uint64_t)r.anhi << 32) | r.anlo, lane, b0, b1);
+    float rw;
+    if (d & 1u)
+      rw = -10.0f;
+    else if (d & 2u)
+      rw = 75.0f;
+    else
+      rw = reward_finish(c, r.rpart, mn);
+    if (!d) {
+      write_row(obs + (long long)i * c.obs_dim, b0, b1, r.exa, c.B, lane);
+    } else {
+      if (term) write_row(term + (long long)i * c.obs_dim, b0, b1, r.exa, c.B, lane);
+      scan_env(c, p, m, r.nb, r.stepb, r.bx, r.by, r.bphi, r.bsigma, ((uint64_t)r.bnhi << 32) | r.bnlo, lane, b0,
+               b1);
+      write_row(obs + (long long)i * c.obs_dim, b0, b1, r.exb, c.B, lane);
+    }
+    if (lane == 0) rew[i] = rw;
   }
 }
 
@@ -854,8 +994,8 @@ extern "C" int sg_sim_step(sg_sim_t sim, const uint8_t* act_dev, float* obs_dev,
                            uint8_t* done_dev, float* term_obs_dev, sg_stream_t stream) {
   if (!sim || !act_dev || !obs_dev || !rew_dev || !done_dev) return SG_E_INVAL;
   if (((uintptr_t)obs_dev & 3) || ((uintptr_t)rew_dev & 3) || ((uintptr_t)term_obs_dev & 3)) return SG_E_ALIGN;
-  k_step<<<grid_for(sim->dc.n_envs), 32 * kWarpsPerBlock, 0, stream>>>(sim->dc, sg_sim_ptrs(sim), act_dev, obs_dev,
-                                                                        rew_dev, done_dev, term_obs_dev);
+  k_step<<<(sim->dc.n_envs + kStepEnvs - 1) / kStepEnvs, 32 * kStepWarps, 0, stream>>>(
+      sim->dc, sg_sim_ptrs(sim), sim->map_order_dev, act_dev, obs_dev, rew_dev, done_dev, term_obs_dev);
   SG_CUDA(cudaGetLastError());
   return SG_OK;
 }
