@@ -258,12 +258,14 @@ int sg_sim_get_atlas(sg_sim_t sim, uint32_t* atlas_host, size_t* words, int64_t*
                      int32_t* row_words_host);
 
 /*
- * Copy the clearance maps to the host (an acceleration structure of the ray
+ * Copy the skip maps to the host (the acceleration structure of the ray
  * march, not part of the paper's step): for map m, byte offs_host[m] +
- * cy * W + cx is min(255, Chebyshev distance in cells from cell (cx, cy) to
- * the nearest occupied cell), cells outside the map counting as occupied; 0
- * on occupied cells.  *bytes: in = capacity of host, out = total bytes.
- * host and offs_host may be NULL.  Synchronous.
+ * cy * W + cx is 0 on occupied cells and max(1, c - 1) on free cells, where
+ * c = min(255, Chebyshev distance in cells from cell (cx, cy) to the nearest
+ * occupied cell), cells outside the map counting as occupied (the number of
+ * march samples that can be skipped from there).  *bytes: in = capacity of
+ * host, out = total bytes (sum of W x H).  host and offs_host may be NULL.
+ * Synchronous.
  */
 int sg_sim_get_clearance(sg_sim_t sim, uint8_t* host, size_t* bytes, int64_t* offs_host);
 

@@ -29,19 +29,24 @@ constexpr float kTwoPow24Inv = 5.9604644775390625e-08f;
 // Clearance: byte clr_off + cy * w + cx holds min(255, Chebyshev distance in
 // cells from (cx, cy) to the nearest occupied cell, cells outside the map
 // counting as occupied); 0 exactly on occupied cells.
+// Skip maps (the march's acceleration structure) carry a border of
+// kClrBorder zero cells on every side, so a march that starts inside the map
+// needs no bounds test (see march()).
+constexpr int kClrBorder = 2;
+
 struct MapDesc {
   long long word_off;
-  long long clr_off;
+  long long clr_off;   // interior cell (0, 0) of the map's skip map
   int w, h;
   int row_words;
-  int pad;
+  int clr_ld;          // row stride of the skip map, w + 2 * kClrBorder
 };
 
 // Launch-time copy of the configuration (float32 values).
 struct DevCfg {
   int n_envs, B, obs_dim, n_actions, t_max, kmax, delay_lo, delay_span;
   int skip_ok;      // march_step <= 1: clearance skipping is exact
-  int clr_collide;  // clearance at which the collision disc cannot touch a wall
+  int clr_collide;  // skip value from which the collision disc cannot touch a wall
   float fov, half_fov, range_max, delta, robot_r, goal_r, near_dist, start_offset, jitter;
   float dt_lo, dt_hi, k_lo, k_hi, cap_lo, cap_hi, sig_lo, sig_hi;
   float v_nom, w_nom;
@@ -54,7 +59,7 @@ struct SimPtrs {
   float* f;               // [9][n]: x y phi vl va dt K cap sigma
   uint32_t* u;            // [4][n]: ep_step ep_id t fifo
   const uint32_t* atlas;  // bit-packed maps
-  const uint8_t* clr;     // clearance maps
+  const uint8_t* clr;     // skip maps (see march())
   const MapDesc* maps;
   const int* env_map;
   const int* env_beams;   // nullptr: every env uses B beams
@@ -234,29 +239,44 @@ __device__ __forceinline__ Layout layout_of(const DevCfg& c, const MapDesc& m) {
 // Fixed-step ray march: sample k = 1..kmax at (fma(k d, ux, x), fma(k d, uy, y));
 // the first sample whose cell is occupied or outside the map is the hit.
 //
-// The march reads the clearance map instead of the bits: clearance 0 is an
-// occupied cell, and clearance c >= 1 says every cell within Chebyshev
-// distance c - 1 is free and inside the map.  With march_step <= 1 and
-// |ux|, |uy| <= 1 the sample cell moves by at most j + 1 cells per axis over
-// j samples (j cells of travel plus one for the rounding of the two fma
-// results, which is below 2^-9 cells for maps up to 16384 cells), so the
-// samples k+1 .. k+c-2 all lie in free cells and the next sample that can hit
-// is k + max(1, c - 1).  The hit index is therefore the same as testing every
-// sample.
+// The march reads the skip map instead of the bits: with c the clearance of a
+// cell (0 on occupied cells; c >= 1 says every cell within Chebyshev distance
+// c - 1 is free and inside the map), the map holds s = 0 for c = 0 and
+// s = max(1, c - 1) otherwise, and a border of kClrBorder zero cells around
+// the map.  With march_step <= 1 and |ux|, |uy| <= 1 the sample cell moves by
+// at most j + 1 cells per axis over j samples (j cells of travel plus one for
+// the rounding of the two fma results, which is below 2^-9 cells for maps up
+// to 16384 cells), so the samples k+1 .. k+c-2 all lie in free cells and the
+// next sample that can hit is k + s: the hit index is the same as testing
+// every sample.  The same bound puts the next sample at most c cells from the
+// current one (2 when c = 1), so from an origin inside the map no sample
+// leaves the border before a zero stops the march: that loop has no bounds
+// test.  Origins outside the map, and steps above one cell (no skipping), use
+// the bounds-tested loop.
 template <bool kUnitStep>
-__device__ __forceinline__ int march(const uint8_t* __restrict__ clr, int W, int H, float x, float y, float ux,
-                                     float uy, float delta, int kmax, int skip_ok) {
+__device__ __forceinline__ int march(const uint8_t* __restrict__ clr, int W, int H, int ld, float x, float y,
+                                     float ux, float uy, float delta, int kmax, int skip_ok) {
   int k = 1;
+  if ((kUnitStep || skip_ok) && x >= 0.0f && y >= 0.0f && x < (float)W && y < (float)H) {
+    while (k <= kmax) {
+      // with a unit step, (float)k * 1.0f is (float)k exactly
+      const float t = kUnitStep ? (float)k : (float)k * delta;
+      const int ix = __float2int_rd(fmaf(t, ux, x)), iy = __float2int_rd(fmaf(t, uy, y));
+      const int s = __ldg(clr + iy * ld + ix);
+      if (s == 0) return k;
+      k += s;
+    }
+    return kmax + 1;
+  }
   while (k <= kmax) {
-    // with a unit step, (float)k * 1.0f is (float)k exactly
     const float t = kUnitStep ? (float)k : (float)k * delta;
     const float px = fmaf(t, ux, x);
     const float py = fmaf(t, uy, y);
     const int ix = __float2int_rd(px), iy = __float2int_rd(py);
     if ((unsigned)ix >= (unsigned)W || (unsigned)iy >= (unsigned)H) return k;
-    const int c = __ldg(clr + iy * W + ix);
-    if (c == 0) return k;
-    k += (kUnitStep || skip_ok) ? max(1, c - 1) : 1;
+    const int s = __ldg(clr + iy * ld + ix);
+    if (s == 0) return k;
+    k += (kUnitStep || skip_ok) ? s : 1;
   }
   return kmax + 1;
 }
@@ -296,11 +316,12 @@ __device__ __forceinline__ bool collide_rows_warp(const DevCfg& c, const MapDesc
 
 // The whole test.  Every occupied cell centre is at least clearance - 0.5
 // cells away from a point of the centre's cell, so a large enough clearance
-// there rules out any occupied cell within robot_r without reading the rows.
+// there (skip value >= clr_collide, i.e. clearance >= ceil(r) + 2) rules out
+// any occupied cell within robot_r without reading the rows.
 __device__ __forceinline__ bool collide_warp(const DevCfg& c, const MapDesc& m, const uint32_t* __restrict__ rows,
                                              const uint8_t* __restrict__ clr, float x, float y, int lane) {
   if (x < 0.0f || y < 0.0f || x >= (float)m.w || y >= (float)m.h) return true;
-  const int own = __ldg(clr + __float2int_rd(y) * m.w + __float2int_rd(x));
+  const int own = __ldg(clr + __float2int_rd(y) * m.clr_ld + __float2int_rd(x));
   if (own >= c.clr_collide) return false;
   return collide_rows_warp(c, m, rows, x, y, lane);
 }
@@ -384,8 +405,9 @@ __device__ __forceinline__ float beam_at(const DevCfg& c, const EnvConst& k, flo
   const float beta = phi + off;
   float sn, cs;
   f_sincos(beta, sn, cs);
-  const int h = c.delta == 1.0f ? march<true>(k.clr, k.m.w, k.m.h, x, y, -cs, -sn, c.delta, c.kmax, 1)
-                                 : march<false>(k.clr, k.m.w, k.m.h, x, y, -cs, -sn, c.delta, c.kmax, c.skip_ok);
+  const int h = c.delta == 1.0f
+                    ? march<true>(k.clr, k.m.w, k.m.h, k.m.clr_ld, x, y, -cs, -sn, c.delta, c.kmax, 1)
+                    : march<false>(k.clr, k.m.w, k.m.h, k.m.clr_ld, x, y, -cs, -sn, c.delta, c.kmax, c.skip_ok);
   float r = fminf((float)h * c.delta, c.range_max);
   mn = fminf(mn, r);
   if (sigma > 0.0f) {

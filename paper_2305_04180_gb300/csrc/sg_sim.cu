@@ -25,8 +25,8 @@ using namespace sg;
 struct PrepMap {
   long long src;        // first cell of the map in the staging grid
   long long word_off;   // first word in the bit atlas
-  long long clr_off;    // first byte in the clearance atlas
-  int w, h, row_words, pad;
+  long long clr_off;    // interior cell (0, 0) in the skip-map atlas
+  int w, h, row_words, clr_ld;
 };
 
 __device__ __forceinline__ int find_map(const long long* __restrict__ prefix, int n_maps, long long item) {
@@ -81,7 +81,8 @@ __global__ void k_clr_rows(const uint8_t* __restrict__ grid, const PrepMap* __re
 
 // Pass 2: thread per (map, cell): Chebyshev distance
 // d(x, y) = min over rows y' of max(g(x, y'), |y - y'|), with the rows outside
-// the map at g = 0; capped at 255.
+// the map at g = 0; capped at 255; stored as the march's skip value
+// (0 if d = 0, else max(1, d - 1)) inside the zero border.
 __global__ void k_clr_cols(const uint8_t* __restrict__ g, const PrepMap* __restrict__ mp,
                            const long long* __restrict__ cell_prefix, int n_maps, long long total,
                            uint8_t* __restrict__ clr) {
@@ -97,7 +98,7 @@ __global__ void k_clr_cols(const uint8_t* __restrict__ g, const PrepMap* __restr
     if (cy - dd >= 0) best = min(best, max((int)col[(long long)(cy - dd) * d.w], dd));
     if (cy + dd < d.h) best = min(best, max((int)col[(long long)(cy + dd) * d.w], dd));
   }
-  clr[d.clr_off + local] = (uint8_t)best;
+  clr[d.clr_off + (long long)cy * d.clr_ld + cx] = (uint8_t)(best == 0 ? 0 : max(1, best - 1));
 }
 
 // Episode 0 of every env; one warp per env.
@@ -205,7 +206,7 @@ __global__ void __launch_bounds__(256, 4) k_step(const __grid_constant__ DevCfg 
       if (s.x < 0.0f || s.y < 0.0f || s.x >= (float)m.w || s.y >= (float)m.h) {
         d = 1u;
       } else {
-        const int own = __ldg(p.clr + m.clr_off + __float2int_rd(s.y) * m.w + __float2int_rd(s.x));
+        const int own = __ldg(p.clr + m.clr_off + __float2int_rd(s.y) * m.clr_ld + __float2int_rd(s.x));
         slow = own < c.clr_collide;
       }
       const float ddx = L.gx - s.x, ddy = L.gy - s.y;
@@ -488,7 +489,7 @@ __device__ __forceinline__ void pose_chunk(const DevCfg& c, const SimPtrs& p, co
       if (mx < 0.0f || my < 0.0f || mx >= (float)k.m.w || my >= (float)k.m.h) {
         done = 1u;
       } else {
-        const int own = __ldg(k.clr + __float2int_rd(my) * k.m.w + __float2int_rd(mx));
+        const int own = __ldg(k.clr + __float2int_rd(my) * k.m.clr_ld + __float2int_rd(mx));
         slow = own < c.clr_collide;
       }
       const float ddx = k.L.gx - mx, ddy = k.L.gy - my;
@@ -758,7 +759,7 @@ static int make_devcfg(const sg_sim_config* cfg, DevCfg* dc) {
   // a point of a cell with clearance c is at least c - 0.5 cells from every
   // occupied cell centre; keep a margin of one cell above the radius so that
   // the rounded disc test could not have fired either
-  dc->clr_collide = (int)std::ceil(cfg->robot_radius) + 2;
+  dc->clr_collide = (int)std::ceil(cfg->robot_radius) + 1;
   dc->fov = cfg->fov;
   dc->half_fov = cfg->fov * 0.5f;
   dc->range_max = cfg->range_max;
@@ -837,10 +838,10 @@ extern "C" int sg_sim_create(const sg_sim_config* cfg, int32_t n_maps, const uin
     md[m].w = map_w[m];
     md[m].h = map_h[m];
     md[m].row_words = ((map_w[m] + 127) / 128) * 4;  // rows padded to 16 bytes
-    md[m].pad = 0;
-    md[m].clr_off = clr_bytes;
+    md[m].clr_ld = map_w[m] + 2 * kClrBorder;
+    md[m].clr_off = clr_bytes + (long long)kClrBorder * md[m].clr_ld + kClrBorder;
     words += (long long)md[m].row_words * map_h[m];
-    clr_bytes += (long long)map_w[m] * map_h[m];
+    clr_bytes += (long long)md[m].clr_ld * (map_h[m] + 2 * kClrBorder);
     max_cells = std::max(max_cells, (size_t)map_w[m] * (size_t)map_h[m]);
   }
   for (int i = 0; i < n; ++i) {
@@ -886,6 +887,7 @@ extern "C" int sg_sim_create(const sg_sim_config* cfg, int32_t n_maps, const uin
     cuda_fail(e, "cudaMalloc");
     return SG_E_OOM;
   }
+  e = cudaMemset(s->clr, 0, (size_t)clr_bytes);  // the zero borders of the skip maps
   std::vector<PrepMap> mp;
   std::vector<long long> pw, pr, pc;
   int m0 = 0;
@@ -906,7 +908,7 @@ extern "C" int sg_sim_create(const sg_sim_config* cfg, int32_t n_maps, const uin
       d.w = map_w[m1];
       d.h = map_h[m1];
       d.row_words = md[m1].row_words;
-      d.pad = 0;
+      d.clr_ld = md[m1].clr_ld;
       mp.push_back(d);
       e = cudaMemcpyAsync(staging + used, maps_host[m1], cells, cudaMemcpyHostToDevice, 0);
       if (e != cudaSuccess) break;
@@ -1165,14 +1167,27 @@ extern "C" int sg_sim_get_atlas(sg_sim_t sim, uint32_t* atlas_host, size_t* word
 
 extern "C" int sg_sim_get_clearance(sg_sim_t sim, uint8_t* host, size_t* bytes, int64_t* offs_host) {
   if (!sim || !bytes) return SG_E_INVAL;
+  size_t total = 0;
+  for (int m = 0; m < sim->n_maps; ++m) total += (size_t)sim->maps_host[m].w * sim->maps_host[m].h;
   if (host) {
-    if (*bytes < (size_t)sim->clr_bytes) return SG_E_INVAL;
+    if (*bytes < total) return SG_E_INVAL;
     SG_CUDA(cudaDeviceSynchronize());
-    SG_CUDA(cudaMemcpy(host, sim->clr, (size_t)sim->clr_bytes, cudaMemcpyDeviceToHost));
+    size_t off = 0;
+    for (int m = 0; m < sim->n_maps; ++m) {
+      const MapDesc& d = sim->maps_host[m];
+      SG_CUDA(cudaMemcpy2D(host + off, (size_t)d.w, sim->clr + d.clr_off, (size_t)d.clr_ld, (size_t)d.w,
+                           (size_t)d.h, cudaMemcpyDeviceToHost));
+      off += (size_t)d.w * d.h;
+    }
   }
-  *bytes = (size_t)sim->clr_bytes;
-  if (offs_host)
-    for (int m = 0; m < sim->n_maps; ++m) offs_host[m] = sim->maps_host[m].clr_off;
+  *bytes = total;
+  if (offs_host) {
+    int64_t off = 0;
+    for (int m = 0; m < sim->n_maps; ++m) {
+      offs_host[m] = off;
+      off += (int64_t)sim->maps_host[m].w * sim->maps_host[m].h;
+    }
+  }
   return SG_OK;
 }
 

@@ -256,9 +256,9 @@ def test_against_float64_oracle_tolerances():
 
 
 def test_clearance_matches_chessboard_distance_transform():
-    """The march's clearance map equals scipy's chessboard distance transform
-    of the free cells, with the outside of the map counted as occupied and
-    values capped at 255."""
+    """The march's skip map is the skip value of scipy's chessboard distance
+    transform of the free cells (outside of the map counted as occupied,
+    capped at 255): 0 on occupied cells, max(1, c - 1) elsewhere."""
     ndimage = pytest.importorskip("scipy.ndimage")
     maps = [make_map(1), make_map(2, 128), make_map(3, 200, 77), random_tiny_map(4, 33, 5, 0.5),
             np.ones((1, 1), np.uint8), empty_map(700), empty_map(9, 600)]
@@ -269,7 +269,8 @@ def test_clearance_matches_chessboard_distance_transform():
         pad = np.ones((h + 2, w + 2), np.uint8)
         pad[1:-1, 1:-1] = grid != 0
         ref = ndimage.distance_transform_cdt(pad == 0, metric="chessboard")[1:-1, 1:-1]
-        ref = np.minimum(ref, 255).astype(np.uint8)
+        ref = np.minimum(ref, 255).astype(np.int32)
+        ref = np.where(ref == 0, 0, np.maximum(1, ref - 1)).astype(np.uint8)
         got = clr[offs[m]: offs[m] + h * w].reshape(h, w)
         assert np.array_equal(got, ref), m
 
