@@ -263,6 +263,23 @@ __device__ __forceinline__ void mlp_tile(const QW& w, const bf16* X, bf16* H1, b
   __syncthreads();
 }
 
+__device__ __forceinline__ void group_barrier(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// The forward of one 16-row tile by a group of 16 warps that synchronise
+// among themselves on named barrier `bar` (the other warps of the CTA run
+// on); wg = the warp's index in its group.
+__device__ __forceinline__ void mlp_tile_group(const QW& w, const bf16* X, bf16* H1, bf16* H2, float* O, int wg,
+                                               int lane, int bar) {
+  hidden_layer<1>(X, w.ld1, w.k1, w.W1, w.ld1, w.b1, H1, wg, lane);
+  group_barrier(bar, 512);
+  hidden_layer<1>(H1, kLdh, kHid, w.W2, kLdh, w.b2, H2, wg, lane);
+  group_barrier(bar, 512);
+  if (wg == 0) head_layer(H2, w, O, 0, lane);
+  group_barrier(bar, 512);
+}
+
 // Dueling combine and greedy action of one row of head outputs:
 // Q_a = (V + A_a) - mean(A), argmax with the lowest index on ties.
 __device__ __forceinline__ uint32_t greedy_action(const float* o, float* qv = nullptr) {
@@ -318,10 +335,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_qnet_forward(const uint8_t* __r
 }
 
 // VEM eps-greedy rollout with the network fused in: per step, the 16 envs of
-// a CTA write their observations to a BF16 tile, the tile goes through the
+// a group write their observations to a BF16 tile, the tile goes through the
 // network on the tensor cores, every env takes argmax Q or (with probability
 // eps_i) the random action, then steps; the transition is appended to the
-// replay ring.  One warp per env, 16 envs per CTA.
+// replay ring.  One warp per env; 16 envs per group, MT groups per CTA
+// sharing the weight image.  The groups synchronise only among themselves
+// (named barriers), so one group's env step overlaps the other's network.
 template <int MT>
 __global__ void __launch_bounds__(512 * MT, 1)
     k_rollout_q(const __grid_constant__ DevCfg c, SimPtrs p, const uint8_t* __restrict__ img, ImgLayout L, int K,
@@ -340,6 +359,11 @@ __global__ void __launch_bounds__(512 * MT, 1)
   for (int i = threadIdx.x; i < kRows * L.ld1; i += blockDim.x) X[i] = __float2bfloat16_rn(0.0f);
   const QW w = qw_at(sw, L);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = warp >> 4, wg = warp & 15, bar = 1 + grp;
+  bf16* Xg = X + grp * 16 * L.ld1;
+  bf16* H1g = H1 + grp * 16 * kLdh;
+  bf16* H2g = H2 + grp * 16 * kLdh;
+  float* Og = O + grp * 16 * kOutPad;
   // CTAs take envs grouped by map, so that one CTA's scans share cache lines
   const int slot = blockIdx.x * kRows + warp;
   const bool live = slot < c.n_envs;
@@ -364,9 +388,9 @@ __global__ void __launch_bounds__(512 * MT, 1)
   uint32_t ra_batch = 0, ex_batch = 0;
   __syncthreads();
   for (int i = 0; i < K; ++i) {
-    if (live) obs_to_tile(X + warp * L.ld1, o, c.B, lane);
-    __syncthreads();
-    mlp_tile<MT>(w, X, H1, H2, O, warp, lane);
+    if (live) obs_to_tile(Xg + wg * L.ld1, o, c.B, lane);
+    group_barrier(bar, 512);
+    mlp_tile_group(w, Xg, H1g, H2g, Og, wg, lane, bar);
     if (!live) continue;
     if ((i & 31) == 0) {
       // lane l draws the random action and the exploration uniform of step t + l
@@ -376,7 +400,7 @@ __global__ void __launch_bounds__(512 * MT, 1)
     }
     const uint32_t ra = __shfl_sync(kFull, ra_batch, i & 31);
     const bool explore = (ex_batch >> (i & 31)) & 1u;
-    const uint32_t greedy = greedy_action(O + warp * kOutPad);
+    const uint32_t greedy = greedy_action(Og + wg * kOutPad);
     const uint32_t a = explore ? ra : greedy;
     long long e = 0;
     float* srow = nullptr;
