@@ -672,4 +672,118 @@ __device__ __forceinline__ uint32_t random_action_for(const DevCfg& c, uint64_t 
   return (uint32_t)(ha >> 32) % (uint32_t)c.n_actions;
 }
 
+// ------------------------------------------------- lane-parallel step
+struct __align__(16) StepScanRec {
+  float ax, ay, aphi, asigma;  // post-motion state (scan A)
+  uint32_t anlo, anhi;         // its noise key
+  float rpart;                 // scan-free part of Eq. 11 at the post-motion state
+  uint32_t done;
+  float exa[5];                // observation entries B .. B + 4 of scan A
+  float bx, by, bphi;          // reset state (scan B, done envs)
+  float bsigma;
+  uint32_t bnlo, bnhi;
+  int map, nb;
+  float exb[5];                // observation entries of scan B
+  float stepb;                 // beam spacing of the env
+  int env;
+  int pad[3];
+};
+static_assert(sizeof(StepScanRec) == 128, "step scan record is eight 16-byte words");
+
+// Scan of one pose by the warp for an env of map m with nb beams: this
+// lane's normalised ranges into b0 / b1; returns the minimum noise-free range.
+__device__ __forceinline__ float scan_env(const DevCfg& c, const SimPtrs& p, const MapDesc& m, int nb, float stepb,
+                                          float x, float y, float phi, float sigma, uint64_t nk, int lane,
+                                          float& b0, float& b1) {
+  EnvConst k;
+  k.m = m;
+  k.clr = p.clr + m.clr_off;
+  k.nb = nb;
+  const float off0 = (float)lane * stepb - c.half_fov;
+  const float off1 = (float)(lane + 32) * stepb - c.half_fov;
+  float n0 = 0.0f, n1 = 0.0f;
+  if (sigma > 0.0f) {
+    n0 = box_muller(sm_at(nk, (uint64_t)lane));
+    if (nb > 32) n1 = box_muller(sm_at(nk, (uint64_t)(lane + 32)));
+  }
+  float mn = c.range_max;
+  b0 = lane < nb ? beam_at(c, k, x, y, phi, sigma, off0, n0, mn) : 1.0f;
+  b1 = lane + 32 < nb ? beam_at(c, k, x, y, phi, sigma, off1, n1, mn) : 1.0f;
+  return __uint_as_float(__reduce_min_sync(kFull, __float_as_uint(mn)));
+}
+
+__device__ __forceinline__ void write_row(float* row, float b0, float b1, const float* ex, int B, int lane) {
+  if (lane < B) row[lane] = b0;
+  if (lane + 32 < B) row[lane + 32] = b1;
+  if (lane < 5) row[B + lane] = ex[lane];
+}
+
+
+// One step of one env per lane (sg_sim_step and the fused Q-net rollout):
+// delay, Eq. 5, Eq. 6, the collision test (map bounds and clearance per lane,
+// the bit rows for the envs that need them with the whole warp), arrival,
+// truncation, the AutoReset draws, and everything of the observation and of
+// Eq. 11 that does not need a scan, into the env's record r (scan A: the
+// post-motion state; scan B: the reset state of a done env).  s: the env's
+// state in, the state after the step out.  Lanes with live = false take part
+// in the warp-wide collision tests only.  Returns the done flags.
+__device__ __forceinline__ uint32_t lane_step(const DevCfg& c, const SimPtrs& p, int i, bool live, Env& s,
+                                              uint32_t a, StepScanRec& r, int lane) {
+  MapDesc m;
+  Layout L;
+  int mid = 0, nb = c.B;
+  uint32_t d = 0;
+  bool slow = false;
+  if (live) {
+    mid = p.env_map[i];
+    m = p.maps[mid];
+    L = layout_of(c, m);
+    nb = p.env_beams ? p.env_beams[i] : c.B;
+    if (kinematics(c, s, a)) atomicOr(p.status, 1u);
+    if (s.x < 0.0f || s.y < 0.0f || s.x >= (float)m.w || s.y >= (float)m.h) {
+      d = 1u;
+    } else {
+      const int own = __ldg(p.clr + m.clr_off + __float2int_rd(s.y) * m.clr_ld + __float2int_rd(s.x));
+      slow = own < c.clr_collide;
+    }
+    const float ddx = L.gx - s.x, ddy = L.gy - s.y;
+    if (fmaf(ddx, ddx, ddy * ddy) <= c.goal_r * c.goal_r) d |= 2u;
+    if (s.ep_step >= (uint32_t)c.t_max) d |= 4u;
+  }
+  // collision tests that need the bit rows, one env at a time
+  unsigned sm = __ballot_sync(kFull, slow);
+  while (sm) {
+    const int e = __ffs(sm) - 1;
+    sm &= sm - 1u;
+    const MapDesc me = p.maps[__shfl_sync(kFull, mid, e)];
+    const float xe = __shfl_sync(kFull, live ? s.x : 0.0f, e), ye = __shfl_sync(kFull, live ? s.y : 0.0f, e);
+    if (collide_rows_warp(c, me, p.atlas + me.word_off, xe, ye, lane) && lane == e) d |= 1u;
+  }
+  if (live) {
+    const uint64_t nkey = sm_at(sm_at(c.seed, kStreamNoise), (uint64_t)i);
+    const GoalFrame g = goal_frame(L, s);
+    const uint64_t nka = sm_at(nkey, ((uint64_t)s.ep_id << 32) | s.ep_step);
+    r.ax = s.x, r.ay = s.y, r.aphi = s.phi, r.asigma = s.sigma;
+    r.anlo = (uint32_t)nka, r.anhi = (uint32_t)(nka >> 32);
+    for (int q = 0; q < 5; ++q) r.exa[q] = obs_extra(c, L, s, g, q);
+    r.rpart = (d & 3u) ? 0.0f : reward_partial(c, L, s, g.alpha, g.ddx, g.ddy);
+    r.done = d;
+    r.map = mid;
+    r.env = i;
+    r.nb = nb;
+    r.stepb = c.fov / (float)(nb - 1);
+    if (d) {
+      // AutoReset (Sec. 3.2.5): a new episode, observed at its step 0
+      const uint64_t rkey = sm_at(sm_at(c.seed, kStreamReset), (uint64_t)i);
+      reset_env_lane(c, L, rkey, s, s.ep_id + 1u);
+      const GoalFrame gb = goal_frame(L, s);
+      const uint64_t nkb = sm_at(nkey, ((uint64_t)s.ep_id << 32) | s.ep_step);
+      r.bx = s.x, r.by = s.y, r.bphi = s.phi, r.bsigma = s.sigma;
+      r.bnlo = (uint32_t)nkb, r.bnhi = (uint32_t)(nkb >> 32);
+      for (int q = 0; q < 5; ++q) r.exb[q] = obs_extra(c, L, s, gb, q);
+    }
+  }
+  return d;
+}
+
 }  // namespace sg
