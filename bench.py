@@ -519,28 +519,25 @@ CPU_SAMPLE_STEPS = 16000
 
 
 def _recorded_traffic(n_envs, K, kernel, launch):
-    """DRAM bytes per launch of the timed kernel from the committed ncu record,
-    if it was taken on this kernel and workload and the kernel sources are
+    """DRAM bytes per launch of the timed kernel from the committed ncu
+    records (one line per kernel, workload and launch configuration), if one
+    was taken on this kernel, workload and launch and the kernel sources are
     unchanged since (else None)."""
     import hashlib
 
     try:
-        rec = {}
-        for line in open(os.path.join(ROOT, "profiles", "roofline_traffic.txt")):
-            line = line.strip()
-            if line and not line.startswith("#"):
-                for tok in line.split(" ") if not line.startswith("command=") else [line]:
-                    if "=" in tok:
-                        k, v = tok.split("=", 1)
-                        rec[k] = v
         src = b"".join(open(os.path.join(ROOT, "paper_2305_04180_gb300", "csrc", f), "rb").read()
                        for f in ("sg_device.cuh", "sg_sim.cu"))
-        if hashlib.sha1(src).hexdigest()[:16] != rec.get("source_sha1"):
-            return None
-        if (int(rec["n_envs"]) != n_envs or int(rec["steps_per_launch"]) != K or rec.get("kernel") != kernel
-                or rec.get("launch") != launch):
-            return None
-        return int(rec["dram_bytes_read"]) + int(rec["dram_bytes_write"])
+        sha = hashlib.sha1(src).hexdigest()[:16]
+        for line in open(os.path.join(ROOT, "profiles", "roofline_traffic.txt")):
+            line = line.strip()
+            if not line.startswith("kernel="):
+                continue
+            rec = dict(tok.split("=", 1) for tok in line.split(" ") if "=" in tok)
+            if (rec.get("source_sha1") == sha and rec.get("kernel") == kernel and rec.get("launch") == launch
+                    and int(rec["n_envs"]) == n_envs and int(rec["steps_per_launch"]) == K):
+                return int(rec["dram_bytes_read"]) + int(rec["dram_bytes_write"])
+        return None
     except Exception:
         return None
 
