@@ -1,5 +1,5 @@
-"""Float64 oracle of the learned part: dueling MLP Q-network, double-DQN TD
-loss with Huber, its gradient, and Adam.
+"""Float64 oracle of the learned part: the Q-networks, double-DQN TD loss with
+Huber, its gradient, and Adam.
 
 TEST INFRASTRUCTURE (see the package docstring): only tests, the smoke check
 and the benchmark's CPU legs use it.
@@ -9,7 +9,11 @@ Passages followed:
   state to actions with the policy net, the learner samples a mini-batch and
   optimises with the underlying DRL algorithm, DDQN (Sec. 4.1, double
   Q-learning: the online net picks the next action, the target net values it).
-* Dueling architecture (cited in Sec. 2 as Dueling DQN): Q = V + A - mean(A).
+* Two networks: "dueling", in -> 256 -> 256 -> (1 + 5) with
+  Q = V + A - mean(A) (the dueling architecture cited in Sec. 2); "paper",
+  the four fully connected layers [32, 256, 128, 5] of Sec. 4.3.2
+  ("Task2Task generalization"), in -> 256 -> 128 -> 5 with Q the outputs.
+  Both use ReLU between layers.
 * Appendix hyperparameter table, Sparrow column: gamma 0.98, lr 1e-4, Adam,
   batch 256, target update every 200 optimisation steps.
 Readings where the paper is silent: Huber loss with delta 1 on the TD error,
@@ -18,8 +22,9 @@ terminal = collided or arrived (truncation bootstraps); ties in argmax go to
 the lowest index.
 
 Parameter layout (flat, float, the order the library's qnet_set/get_params
-use): W1 [256][in], b1 [256], W2 [256][256], b2 [256], W3 [6][256], b3 [6];
-row 0 of W3 / b3 is the value head, rows 1..5 the advantages.
+use): W1 [h1][in], b1 [h1], W2 [h2][h1], b2 [h2], W3 [out][h2], b3 [out];
+for "dueling" row 0 of W3 / b3 is the value head, rows 1..5 the advantages.
+The architecture of a parameter dict follows from its shapes.
 """
 
 from __future__ import annotations
@@ -29,20 +34,26 @@ import numpy as np
 HIDDEN = 256
 N_ACT = 5
 N_OUT = N_ACT + 1
+# hidden widths and head outputs of the two networks
+ARCHS = {"dueling": (256, 256, N_ACT + 1), "paper": (256, 128, N_ACT)}
 
 
-def param_shapes(n_in: int = 37):
-    return [("W1", (HIDDEN, n_in)), ("b1", (HIDDEN,)), ("W2", (HIDDEN, HIDDEN)), ("b2", (HIDDEN,)),
-            ("W3", (N_OUT, HIDDEN)), ("b3", (N_OUT,))]
+def param_shapes(n_in: int = 37, arch: str = "dueling"):
+    h1, h2, out = ARCHS[arch]
+    return [("W1", (h1, n_in)), ("b1", (h1,)), ("W2", (h2, h1)), ("b2", (h2,)), ("W3", (out, h2)), ("b3", (out,))]
 
 
-def n_params(n_in: int = 37) -> int:
-    return sum(int(np.prod(s)) for _, s in param_shapes(n_in))
+def arch_of(p: dict) -> str:
+    return "dueling" if p["W3"].shape[0] == N_ACT + 1 else "paper"
 
 
-def unflatten(theta, n_in: int = 37) -> dict:
+def n_params(n_in: int = 37, arch: str = "dueling") -> int:
+    return sum(int(np.prod(s)) for _, s in param_shapes(n_in, arch))
+
+
+def unflatten(theta, n_in: int = 37, arch: str = "dueling") -> dict:
     out, o = {}, 0
-    for name, shp in param_shapes(n_in):
+    for name, shp in param_shapes(n_in, arch):
         k = int(np.prod(shp))
         out[name] = np.asarray(theta[o:o + k], np.float64).reshape(shp)
         o += k
@@ -51,7 +62,8 @@ def unflatten(theta, n_in: int = 37) -> dict:
 
 
 def flatten(p: dict) -> np.ndarray:
-    return np.concatenate([np.asarray(p[name], np.float64).ravel() for name, _ in param_shapes(p["W1"].shape[1])])
+    return np.concatenate([np.asarray(p[name], np.float64).ravel()
+                           for name, _ in param_shapes(p["W1"].shape[1], arch_of(p))])
 
 
 def bf16_round(x) -> np.ndarray:
@@ -90,9 +102,12 @@ def forward(p: dict, s, bf16: bool = False, keep: bool = False):
     if bf16:
         h2 = bf16_round(h2).astype(np.float64)
     o = h2 @ W3.T + b3
-    V = o[:, :1]
-    A = o[:, 1:]
-    Q = V + A - A.mean(axis=1, keepdims=True)
+    if o.shape[1] == N_ACT:
+        Q = o  # the paper's network: the outputs are the Q-values
+    else:
+        V = o[:, :1]
+        A = o[:, 1:]
+        Q = V + A - A.mean(axis=1, keepdims=True)
     if keep:
         return Q, dict(s=s, z1=z1, h1=h1, z2=z2, h2=h2, o=o)
     return Q
@@ -131,8 +146,11 @@ def td_loss_grad(p_online: dict, p_target: dict, batch: dict, gamma: float, bf16
     g = np.clip(d, -1.0, 1.0) / B                  # dL/dq_sa
     dQ = np.zeros_like(Q)
     dQ[np.arange(B), a] = g
-    # Q_k = V + A_k - mean(A):  dV = sum_k dQ_k,  dA_j = dQ_j - mean_k dQ_k
-    do = np.concatenate([dQ.sum(axis=1, keepdims=True), dQ - dQ.mean(axis=1, keepdims=True)], axis=1)
+    if arch_of(p_online) == "paper":
+        do = dQ  # the outputs are the Q-values
+    else:
+        # Q_k = V + A_k - mean(A):  dV = sum_k dQ_k,  dA_j = dQ_j - mean_k dQ_k
+        do = np.concatenate([dQ.sum(axis=1, keepdims=True), dQ - dQ.mean(axis=1, keepdims=True)], axis=1)
     W2 = p_online["W2"]
     W3 = p_online["W3"]
     if bf16:
@@ -160,13 +178,14 @@ def adam_step(theta, g, m, v, t: int, lr: float = 1e-4, b1: float = 0.9, b2: flo
     return theta - lr * mh / (np.sqrt(vh) + eps), m, v
 
 
-def init_params(seed: int, n_in: int = 37) -> dict:
+def init_params(seed: int, n_in: int = 37, arch: str = "dueling") -> dict:
     """A seeded uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) initialisation (the
     library draws its own; tests set parameters explicitly)."""
     rng = np.random.default_rng(seed)
     p = {}
-    for name, shp in param_shapes(n_in):
-        fan_in = shp[1] if len(shp) == 2 else (n_in if name == "b1" else HIDDEN)
+    shapes = param_shapes(n_in, arch)
+    for i, (name, shp) in enumerate(shapes):
+        fan_in = shp[1] if len(shp) == 2 else shapes[i - 1][1][1]
         bound = 1.0 / np.sqrt(fan_in)
         p[name] = rng.uniform(-bound, bound, size=shp)
     return p

@@ -46,6 +46,26 @@ def test_forward_against_explicit_loops():
             assert abs(q[b, a] - (o[0] + o[1 + a] - mean_a)) < 1e-10
 
 
+def test_paper_network_count_and_explicit_loops():
+    """The [32, 256, 128, 5] network of the Task2Task experiment: parameter
+    count by hand, and a tiny instance evaluated neuron by neuron (the
+    outputs are the Q-values, no value/advantage split)."""
+    assert Q.n_params(32, "paper") == 32 * 256 + 256 + 256 * 128 + 128 + 128 * 5 + 5 == 41989
+    p = Q.init_params(7, 32, "paper")
+    assert Q.arch_of(p) == "paper" and np.array_equal(Q.flatten(Q.unflatten(Q.flatten(p), 32, "paper")), Q.flatten(p))
+    rng = np.random.default_rng(8)
+    p = Q.init_params(8, 3, "paper")
+    s = rng.normal(size=(2, 3))
+    q = Q.forward(p, s)
+    assert q.shape == (2, 5)
+    for b in range(2):
+        h1 = [max(0.0, sum(p["W1"][j, i] * s[b, i] for i in range(3)) + p["b1"][j]) for j in range(256)]
+        h2 = [max(0.0, sum(p["W2"][j, i] * h1[i] for i in range(256)) + p["b2"][j]) for j in range(128)]
+        for a in range(5):
+            o = sum(p["W3"][a, i] * h2[i] for i in range(128)) + p["b3"][a]
+            assert abs(q[b, a] - o) < 1e-10
+
+
 def test_argmax_ties_go_low():
     assert list(Q.argmax_lowest(np.array([[1, 3, 3, 0, 3], [2, 2, 2, 2, 2]]))) == [1, 0]
 
@@ -69,21 +89,22 @@ def test_double_dqn_target_uses_online_argmax_and_target_value():
     assert np.allclose(y, [0.5 + 0.98 * qt[2], 0.5])
 
 
-def test_td_gradient_matches_central_finite_differences():
+@pytest.mark.parametrize("arch", ["dueling", "paper"])
+def test_td_gradient_matches_central_finite_differences(arch):
     rng = np.random.default_rng(3)
     n_in = 6
-    p = Q.init_params(3, n_in)
+    p = Q.init_params(3, n_in, arch)
     # larger weights so that the Huber loss sees both branches
     for k in p:
         p[k] = p[k] * 3.0
-    pt = Q.init_params(4, n_in)
+    pt = Q.init_params(4, n_in, arch)
     batch = _batch(rng, B=10, n_in=n_in)
     batch["r"] = batch["r"] * 3
     loss, g = Q.td_loss_grad(p, pt, batch, 0.98)
     y = Q.td_targets(p, pt, batch["r"], batch["s2"], batch["term"], 0.98)
 
     def loss_at(theta):
-        pp = Q.unflatten(theta, n_in)
+        pp = Q.unflatten(theta, n_in, arch)
         q = Q.forward(pp, batch["s"])
         d = q[np.arange(10), batch["a"]] - y  # target held constant
         return Q.huber(d).mean()
@@ -100,11 +121,12 @@ def test_td_gradient_matches_central_finite_differences():
     assert abs(loss_at(th) - loss) < 1e-12
 
 
-def test_td_gradient_matches_torch_autograd():
+@pytest.mark.parametrize("arch", ["dueling", "paper"])
+def test_td_gradient_matches_torch_autograd(arch):
     torch = pytest.importorskip("torch")
     rng = np.random.default_rng(5)
-    p = Q.init_params(5)
-    pt = Q.init_params(6)
+    p = Q.init_params(5, 37, arch)
+    pt = Q.init_params(6, 37, arch)
     batch = _batch(rng, B=32)
     loss, g = Q.td_loss_grad(p, pt, batch, 0.98)
     y = torch.tensor(Q.td_targets(p, pt, batch["r"], batch["s2"], batch["term"], 0.98))
@@ -113,7 +135,7 @@ def test_td_gradient_matches_torch_autograd():
     h1 = torch.relu(s @ tp["W1"].T + tp["b1"])
     h2 = torch.relu(h1 @ tp["W2"].T + tp["b2"])
     o = h2 @ tp["W3"].T + tp["b3"]
-    q = o[:, :1] + o[:, 1:] - o[:, 1:].mean(dim=1, keepdim=True)
+    q = o if arch == "paper" else o[:, :1] + o[:, 1:] - o[:, 1:].mean(dim=1, keepdim=True)
     qsa = q[torch.arange(32), torch.tensor(batch["a"])]
     tl = torch.nn.functional.huber_loss(qsa, y, delta=1.0)
     tl.backward()
