@@ -280,23 +280,35 @@ int sg_sim_status(sg_sim_t sim, uint32_t* device_status);
 /* ---------------------------------------------------------------------- */
 
 /*
- * Dueling Q-network in -> 256 -> 256 -> (1 value + 5 advantages), ReLU,
- * Q = V + A - mean(A) (the dueling architecture the paper cites in Sec. 2;
- * 5 discrete actions of Sec. 4.3.1).  Inference and learning run on the
- * tensor cores with BF16 weights/activations and FP32 accumulation; FP32
- * master weights, a target copy and Adam moments stay on the device.
+ * Q-network of one of two architectures, ReLU between layers, 5 discrete
+ * actions (Sec. 4.3.1):
+ *   SG_QNET_DUELING  in -> 256 -> 256 -> (1 value + 5 advantages),
+ *                    Q = V + A - mean(A) (the dueling architecture the paper
+ *                    cites in Sec. 2).  Flat parameter order (set/get):
+ *                    W1[256][n_in], b1[256], W2[256][256], b2[256], W3[6][256],
+ *                    b3[6]; row 0 of W3/b3 is the value head.
+ *   SG_QNET_PAPER    the paper's four fully connected layers [32, 256, 128, 5]
+ *                    of the Task2Task experiment (Sec. 4.3.2): in -> 256 ->
+ *                    128 -> 5, the outputs are the Q-values.  Flat order
+ *                    W1[256][n_in], b1[256], W2[128][256], b2[128], W3[5][128],
+ *                    b3[5].
+ * Inference and learning run on the tensor cores with BF16 weights and
+ * activations and FP32 accumulation; FP32 master weights, a target copy and
+ * Adam moments stay on the device.
  *   n_in       input width = the simulator's obs_dim, in [1, 69].
  *   max_batch  largest sg_td_train_step batch, in [1, 65536] (sizes the
  *              learner's scratch buffers).
- *   seed       parameters start uniform in +-1/sqrt(fan_in), drawn from the
- *              counter RNG with this seed; the target copy equals them.
- * Flat parameter order (set/get): W1[256][n_in], b1[256], W2[256][256],
- * b2[256], W3[6][256], b3[6]; row 0 of W3/b3 is the value head.
+ *   seed       parameters start uniform in +-1/sqrt(fan_in), parameter j of
+ *              the flat order drawn from the counter RNG with this seed; the
+ *              target copy equals them.
  * Synchronous.
  */
-int sg_qnet_create(int32_t n_in, int32_t max_batch, uint64_t seed, sg_qnet_t* out);
+#define SG_QNET_DUELING 0
+#define SG_QNET_PAPER 1
+int sg_qnet_create(int32_t n_in, int32_t arch, int32_t max_batch, uint64_t seed, sg_qnet_t* out);
 int sg_qnet_destroy(sg_qnet_t q);
-/* Number of parameters (77,062 for n_in = 37). */
+/* Number of parameters of the network's flat order (77,062 for the dueling
+ * network at n_in = 37, 41,989 for the paper's at n_in = 32). */
 int sg_qnet_num_params(sg_qnet_t q, int64_t* n);
 /* Copy parameters from / to host floats; which: 0 online, 1 target, 2 both
  * (set only).  Setting rebuilds the BF16 copies.  Synchronous. */

@@ -21,6 +21,7 @@ SG_E_DEVICE = -5
 SG_E_TIMEOUT = -6
 SG_DEV_BAD_ACTION = 0x1
 SG_DEV_TIMEOUT = 0x2
+SG_QNET_ARCHS = {"dueling": 0, "paper": 1}
 SG_POLICY_RANDOM = 0
 SG_POLICY_EPS_Q = 1
 
@@ -78,7 +79,7 @@ SIGNATURES = {
     "sg_sim_get_atlas": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "sg_sim_get_clearance": (C.c_int, [_vp, _vp, _vp, _vp]),
     "sg_sim_status": (C.c_int, [_vp, _vp]),
-    "sg_qnet_create": (C.c_int, [_i32, _i32, C.c_uint64, _vp]),
+    "sg_qnet_create": (C.c_int, [_i32, _i32, _i32, C.c_uint64, _vp]),
     "sg_qnet_destroy": (C.c_int, [_vp]),
     "sg_qnet_num_params": (C.c_int, [_vp, _vp]),
     "sg_qnet_set_params": (C.c_int, [_vp, _vp, C.c_int64, _i32]),

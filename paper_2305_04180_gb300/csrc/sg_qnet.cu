@@ -4,11 +4,18 @@
 // (Alg. 1 step 5, Alg. 2 step 1) and the double-DQN learner with Adam
 // (Alg. 2 step 2; appendix hyperparameter table).
 //
-// Network: in -> 256 -> 256 -> 6 (value + 5 advantages), ReLU,
-// Q = V + A - mean(A).  Weights are BF16 on the tensor cores with FP32
-// accumulation; FP32 master weights, Adam moments and a target copy live on
-// the device.  Flat parameter order (sg_qnet_set/get_params):
-// W1[256][in] b1[256] W2[256][256] b2[256] W3[6][256] b3[6].
+// Networks (SG_QNET_DUELING): in -> 256 -> 256 -> 6 (value + 5 advantages),
+// ReLU, Q = V + A - mean(A); (SG_QNET_PAPER) the paper's in -> 256 -> 128 ->
+// 5 with Q the outputs (Sec. 4.3.2).  The kernels run both at the dueling
+// shapes: the paper network's 128 second-layer units and 5 outputs sit in
+// the first rows of the 256-unit / 6-output storage and every other weight
+// and bias stays exactly zero (its pre-activation is 0, so the ReLU mask
+// zeroes its gradient and Adam never moves it, and adding its zero products
+// leaves the other sums unchanged); only the head differs.  Weights are BF16
+// on the tensor cores with FP32 accumulation; FP32 master weights, Adam
+// moments and a target copy live on the device.  Flat parameter order inside
+// (padded): W1[256][in] b1[256] W2[256][256] b2[256] W3[6][256] b3[6]; the
+// C ABI shows each network's own (compact) order.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -40,11 +47,13 @@ constexpr uint32_t kStreamInit = 5;
 struct ImgLayout {
   int n_in, k1, ld1;   // input width, padded to 16, row stride
   int w1, w2, w3, b1, b2, b3, bytes;
+  int plain;           // 1: the outputs are the Q-values (the paper's network)
 };
 
-ImgLayout img_layout(int n_in) {
+ImgLayout img_layout(int n_in, int plain = 0) {
   ImgLayout L;
   L.n_in = n_in;
+  L.plain = plain;
   L.k1 = (n_in + 15) / 16 * 16;
   L.ld1 = L.k1 + 8;
   L.w1 = 0;
@@ -73,6 +82,30 @@ ParamLayout param_layout(int n_in) {
   return P;
 }
 
+// The paper network's compact parameter index of padded index i, or -1 for a
+// padding entry (always zero): W1[256][in] b1[256] W2[128][256] b2[128]
+// W3[5][128] b3[5].
+constexpr int kPaperH2 = 128;
+__host__ __device__ inline int paper_index(int i, const ParamLayout& P, int n_in) {
+  if (i < P.w2) return i;  // W1, b1 unchanged
+  const int c_w2 = P.w2, c_b2 = c_w2 + kPaperH2 * kHid, c_w3 = c_b2 + kPaperH2, c_b3 = c_w3 + 5 * kPaperH2;
+  if (i < P.b2) {
+    const int j = i - P.w2, r = j / kHid, k = j % kHid;
+    return r < kPaperH2 ? c_w2 + r * kHid + k : -1;
+  }
+  if (i < P.w3) {
+    const int r = i - P.b2;
+    return r < kPaperH2 ? c_b2 + r : -1;
+  }
+  if (i < P.b3) {
+    const int j = i - P.w3, o = j / kHid, k = j % kHid;
+    return o < 5 && k < kPaperH2 ? c_w3 + o * kPaperH2 + k : -1;
+  }
+  const int o = i - P.b3;
+  return o < 5 ? c_b3 + o : -1;
+}
+inline int paper_params(int n_in) { return kHid * n_in + kHid + kPaperH2 * kHid + kPaperH2 + 5 * kPaperH2 + 5; }
+
 }  // namespace
 
 // Device view of a replay ring: slot-major SoA, entry e = slot * n_envs + env.
@@ -95,6 +128,7 @@ struct sg_replay {
 
 struct sg_qnet {
   int n_in = 0;
+  int arch = SG_QNET_DUELING;
   int device = 0;
   ImgLayout IL;
   ParamLayout PL;
@@ -149,13 +183,19 @@ __global__ void k_build_image(const float* __restrict__ th, uint8_t* __restrict_
 
 static int image_elems(const ImgLayout& L) { return kHid * L.ld1 + kHid * kLdh + kOutPad * kLdh + 2 * kHid + kOutPad; }
 
-// Seeded uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) initialisation.
-__global__ void k_init_params(float* __restrict__ th, ParamLayout P, int n_in, unsigned long long seed) {
+// Seeded uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) initialisation; parameter
+// j of the network's own (compact) order draws counter j, padding stays 0.
+__global__ void k_init_params(float* __restrict__ th, ParamLayout P, int n_in, int plain, unsigned long long seed) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= P.total) return;
-  const float fan = i < P.w2 ? (float)n_in : (float)kHid;
+  const int j = plain ? paper_index(i, P, n_in) : i;
+  if (j < 0) {
+    th[i] = 0.0f;
+    return;
+  }
+  const float fan = i < P.w2 ? (float)n_in : (i < P.w3 || !plain ? (float)kHid : (float)kPaperH2);
   const float bound = 1.0f / sqrtf(fan);
-  const float u = u24_hi(sm_at(sm_at(sm_at(seed, kStreamInit), 0ull), (uint64_t)i));
+  const float u = u24_hi(sm_at(sm_at(sm_at(seed, kStreamInit), 0ull), (uint64_t)j));
   th[i] = -bound + u * (bound + bound);
 }
 
@@ -282,7 +322,22 @@ __device__ __forceinline__ void mlp_tile_group(const QW& w, const bf16* X, bf16*
 
 // Dueling combine and greedy action of one row of head outputs:
 // Q_a = (V + A_a) - mean(A), argmax with the lowest index on ties.
-__device__ __forceinline__ uint32_t greedy_action(const float* o, float* qv = nullptr) {
+__device__ __forceinline__ uint32_t greedy_action(const float* o, float* qv = nullptr, int plain = 0) {
+  if (plain) {
+    // the paper's network: the outputs are the Q-values
+    uint32_t best = 0;
+    float bq = o[0];
+    if (qv) qv[0] = bq;
+#pragma unroll
+    for (int a = 1; a < kOut - 1; ++a) {
+      if (qv) qv[a] = o[a];
+      if (o[a] > bq) {
+        bq = o[a];
+        best = (uint32_t)a;
+      }
+    }
+    return best;
+  }
   const float V = o[0];
   const float meanA = ((((o[1] + o[2]) + o[3]) + o[4]) + o[5]) / 5.0f;
   uint32_t best = 0;
@@ -329,7 +384,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_qnet_forward(const uint8_t* __r
   mlp_tile(w, X, H1, H2, O, warp, lane);
   if (row < M && lane == 0) {
     float qv[5];
-    greedy_action(O + warp * kOutPad, qv);
+    greedy_action(O + warp * kOutPad, qv, L.plain);
     for (int a = 0; a < 5; ++a) qout[(long long)row * 5 + a] = qv[a];
   }
 }
@@ -400,7 +455,7 @@ __global__ void __launch_bounds__(512 * MT, 1)
     }
     const uint32_t ra = __shfl_sync(kFull, ra_batch, i & 31);
     const bool explore = (ex_batch >> (i & 31)) & 1u;
-    const uint32_t greedy = greedy_action(Og + wg * kOutPad);
+    const uint32_t greedy = greedy_action(Og + wg * kOutPad, nullptr, L.plain);
     const uint32_t a = explore ? ra : greedy;
     long long e = 0;
     float* srow = nullptr;
@@ -489,14 +544,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   gather_tile(X, L.ld1, rp.s2, rows, rp.obs_dim, warp, lane);
   __syncthreads();
   mlp_tile(qw_at(sw, L), X, H1, H2, O, warp, lane);
-  if (lane == 0) astar[warp] = (int)greedy_action(O + warp * kOutPad);
+  if (lane == 0) astar[warp] = (int)greedy_action(O + warp * kOutPad, nullptr, L.plain);
   __syncthreads();
   stage_image(sw, img_t, L.bytes);
   __syncthreads();
   mlp_tile(qw_at(sw, L), X, H1, H2, O, warp, lane);
   if (lane == 0 && i < batch) {
     float qv[5];
-    greedy_action(O + warp * kOutPad, qv);
+    greedy_action(O + warp * kOutPad, qv, L.plain);
     const int e = rows[warp];
     const float r = e >= 0 ? rp.r[e] : 0.0f;
     const float nt = (e >= 0 && rp.term[e]) ? 0.0f : 1.0f;
@@ -535,7 +590,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   // dL/dQ and back through Q_a = V + A_a - mean(A)
   if (lane == 0) {
     float qv[5];
-    greedy_action(O + warp * kOutPad, qv);
+    greedy_action(O + warp * kOutPad, qv, L.plain);
     const int e = rows[warp];
     float gq = 0.0f, hl = 0.0f;
     if (e >= 0) {
@@ -544,8 +599,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       const float ad = fabsf(d);
       hl = ad <= 1.0f ? 0.5f * d * d : ad - 0.5f;
       gq = fminf(fmaxf(d, -1.0f), 1.0f) / (float)batch;
-      DO[warp * kOutPad + 0] = gq;
-      for (int k = 0; k < 5; ++k) DO[warp * kOutPad + 1 + k] = (k == a ? gq : 0.0f) - gq / 5.0f;
+      if (L.plain) {
+        for (int k = 0; k < 5; ++k) DO[warp * kOutPad + k] = k == a ? gq : 0.0f;
+        DO[warp * kOutPad + 5] = 0.0f;
+      } else {
+        DO[warp * kOutPad + 0] = gq;
+        for (int k = 0; k < 5; ++k) DO[warp * kOutPad + 1 + k] = (k == a ? gq : 0.0f) - gq / 5.0f;
+      }
     } else {
       for (int k = 0; k < 6; ++k) DO[warp * kOutPad + k] = 0.0f;
     }
@@ -677,7 +737,10 @@ __global__ void k_adam(float* __restrict__ th, float* __restrict__ m, float* __r
   if (i >= P.total) return;
   float gsum = 0.0f;
   for (int b = 0; b < nblk; ++b) gsum += partial[(long long)b * (P.total + 1) + i];
-  if (grad_out) grad_out[i] = gsum;
+  if (grad_out) {
+    const int j = L.plain ? paper_index(i, P, L.n_in) : i;
+    if (j >= 0) grad_out[j] = gsum;
+  }
   if (lr == 0.0f) return;
   const float t = (float)(*step + 1ull);
   const float mi = b1 * m[i] + (1.0f - b1) * gsum;
@@ -766,13 +829,15 @@ void free_qnet(sg_qnet* q) {
 }
 }  // namespace
 
-extern "C" int sg_qnet_create(int32_t n_in, int32_t max_batch, uint64_t seed, sg_qnet_t* out) {
+extern "C" int sg_qnet_create(int32_t n_in, int32_t arch, int32_t max_batch, uint64_t seed, sg_qnet_t* out) {
   if (!out || n_in < 1 || n_in > 69 || max_batch < 1 || max_batch > (1 << 16)) return SG_E_INVAL;
+  if (arch != SG_QNET_DUELING && arch != SG_QNET_PAPER) return SG_E_INVAL;
   *out = nullptr;
   sg_qnet* q = new (std::nothrow) sg_qnet();
   if (!q) return SG_E_OOM;
   q->n_in = n_in;
-  q->IL = img_layout(n_in);
+  q->arch = arch;
+  q->IL = img_layout(n_in, arch == SG_QNET_PAPER ? 1 : 0);
   q->PL = param_layout(n_in);
   q->max_batch = (max_batch + kTile - 1) / kTile * kTile;
   cudaGetDevice(&q->device);
@@ -804,7 +869,7 @@ extern "C" int sg_qnet_create(int32_t n_in, int32_t max_batch, uint64_t seed, sg
   if (e == cudaSuccess) e = cudaMemset(q->img, 0, (size_t)q->IL.bytes);
   if (e == cudaSuccess) e = cudaMemset(q->img_t, 0, (size_t)q->IL.bytes);
   if (e == cudaSuccess) {
-    k_init_params<<<((int)P + 255) / 256, 256>>>(q->master, q->PL, n_in, seed);
+    k_init_params<<<((int)P + 255) / 256, 256>>>(q->master, q->PL, n_in, q->IL.plain, seed);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) rc = rebuild_image(q, q->master, q->img, 0);
@@ -838,23 +903,52 @@ extern "C" int sg_qnet_destroy(sg_qnet_t q) {
   return SG_OK;
 }
 
+// The network's own (compact) parameter vector <-> the padded one the
+// kernels use (identity for the dueling network).
+static int64_t compact_params(const sg_qnet* q) { return q->IL.plain ? paper_params(q->n_in) : q->PL.total; }
+static void to_padded(const sg_qnet* q, const float* compact, std::vector<float>& padded) {
+  padded.assign((size_t)q->PL.total, 0.0f);
+  for (int i = 0; i < q->PL.total; ++i) {
+    const int j = q->IL.plain ? paper_index(i, q->PL, q->n_in) : i;
+    if (j >= 0) padded[(size_t)i] = compact[j];
+  }
+}
+static void to_compact(const sg_qnet* q, const std::vector<float>& padded, float* compact) {
+  for (int i = 0; i < q->PL.total; ++i) {
+    const int j = q->IL.plain ? paper_index(i, q->PL, q->n_in) : i;
+    if (j >= 0) compact[j] = padded[(size_t)i];
+  }
+}
+static int upload(const sg_qnet* q, float* dev, const float* host) {
+  std::vector<float> v;
+  to_padded(q, host, v);
+  SG_CUDA(cudaMemcpy(dev, v.data(), v.size() * 4, cudaMemcpyHostToDevice));
+  return SG_OK;
+}
+static int download(const sg_qnet* q, const float* dev, float* host) {
+  std::vector<float> v((size_t)q->PL.total);
+  SG_CUDA(cudaMemcpy(v.data(), dev, v.size() * 4, cudaMemcpyDeviceToHost));
+  to_compact(q, v, host);
+  return SG_OK;
+}
+
 extern "C" int sg_qnet_num_params(sg_qnet_t q, int64_t* n) {
   if (!q || !n) return SG_E_INVAL;
-  *n = q->PL.total;
+  *n = compact_params(q);
   return SG_OK;
 }
 
 extern "C" int sg_qnet_set_params(sg_qnet_t q, const float* host, int64_t n, int32_t which) {
-  if (!q || !host || n != q->PL.total || which < 0 || which > 2) return SG_E_INVAL;
+  if (!q || !host || n != compact_params(q) || which < 0 || which > 2) return SG_E_INVAL;
   SG_CUDA(cudaDeviceSynchronize());
   if (which == 0 || which == 2) {
-    SG_CUDA(cudaMemcpy(q->master, host, (size_t)n * 4, cudaMemcpyHostToDevice));
-    int rc = rebuild_image(q, q->master, q->img, 0);
+    int rc = upload(q, q->master, host);
+    if (!rc) rc = rebuild_image(q, q->master, q->img, 0);
     if (rc) return rc;
   }
   if (which == 1 || which == 2) {
-    SG_CUDA(cudaMemcpy(q->target, host, (size_t)n * 4, cudaMemcpyHostToDevice));
-    int rc = rebuild_image(q, q->target, q->img_t, 0);
+    int rc = upload(q, q->target, host);
+    if (!rc) rc = rebuild_image(q, q->target, q->img_t, 0);
     if (rc) return rc;
   }
   SG_CUDA(cudaDeviceSynchronize());
@@ -862,17 +956,18 @@ extern "C" int sg_qnet_set_params(sg_qnet_t q, const float* host, int64_t n, int
 }
 
 extern "C" int sg_qnet_get_params(sg_qnet_t q, float* host, int64_t n, int32_t which) {
-  if (!q || !host || n != q->PL.total || which < 0 || which > 1) return SG_E_INVAL;
+  if (!q || !host || n != compact_params(q) || which < 0 || which > 1) return SG_E_INVAL;
   SG_CUDA(cudaDeviceSynchronize());
-  SG_CUDA(cudaMemcpy(host, which == 0 ? q->master : q->target, (size_t)n * 4, cudaMemcpyDeviceToHost));
-  return SG_OK;
+  return download(q, which == 0 ? q->master : q->target, host);
 }
 
 extern "C" int sg_qnet_get_optimizer(sg_qnet_t q, float* m_host, float* v_host, int64_t n, uint64_t* steps) {
-  if (!q || n != q->PL.total) return SG_E_INVAL;
+  if (!q || n != compact_params(q)) return SG_E_INVAL;
   SG_CUDA(cudaDeviceSynchronize());
-  if (m_host) SG_CUDA(cudaMemcpy(m_host, q->adam_m, (size_t)n * 4, cudaMemcpyDeviceToHost));
-  if (v_host) SG_CUDA(cudaMemcpy(v_host, q->adam_v, (size_t)n * 4, cudaMemcpyDeviceToHost));
+  int rc = SG_OK;
+  if (m_host) rc = download(q, q->adam_m, m_host);
+  if (!rc && v_host) rc = download(q, q->adam_v, v_host);
+  if (rc) return rc;
   if (steps) SG_CUDA(cudaMemcpy(steps, q->step, 8, cudaMemcpyDeviceToHost));
   return SG_OK;
 }
@@ -884,7 +979,7 @@ extern "C" int sg_qnet_set_rollout_rows(sg_qnet_t q, int32_t rows) {
 }
 
 extern "C" int sg_qnet_copy_params(sg_qnet_t dst, sg_qnet_t src, sg_stream_t stream) {
-  if (!dst || !src || dst->n_in != src->n_in) return SG_E_INVAL;
+  if (!dst || !src || dst->n_in != src->n_in || dst->arch != src->arch) return SG_E_INVAL;
   const size_t P = (size_t)src->PL.total;
   SG_CUDA(cudaMemcpyAsync(dst->master, src->master, P * 4, cudaMemcpyDeviceToDevice, stream));
   SG_CUDA(cudaMemcpyAsync(dst->img, src->img, (size_t)src->IL.bytes, cudaMemcpyDeviceToDevice, stream));
@@ -893,10 +988,11 @@ extern "C" int sg_qnet_copy_params(sg_qnet_t dst, sg_qnet_t src, sg_stream_t str
 
 extern "C" int sg_qnet_set_optimizer(sg_qnet_t q, const float* m_host, const float* v_host, int64_t n,
                                      uint64_t steps) {
-  if (!q || !m_host || !v_host || n != q->PL.total) return SG_E_INVAL;
+  if (!q || !m_host || !v_host || n != compact_params(q)) return SG_E_INVAL;
   SG_CUDA(cudaDeviceSynchronize());
-  SG_CUDA(cudaMemcpy(q->adam_m, m_host, (size_t)n * 4, cudaMemcpyHostToDevice));
-  SG_CUDA(cudaMemcpy(q->adam_v, v_host, (size_t)n * 4, cudaMemcpyHostToDevice));
+  int rc = upload(q, q->adam_m, m_host);
+  if (!rc) rc = upload(q, q->adam_v, v_host);
+  if (rc) return rc;
   const unsigned long long st = steps;
   SG_CUDA(cudaMemcpy(q->step, &st, 8, cudaMemcpyHostToDevice));
   return SG_OK;
@@ -1148,14 +1244,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   gather_tile(X, L.ld1, b.s2, rows, b.obs_dim, warp, lane);
   __syncthreads();
   mlp_tile(qw_at(sw, L), X, H1, H2, O, warp, lane);
-  if (lane == 0) astar[warp] = (int)greedy_action(O + warp * kOutPad);
+  if (lane == 0) astar[warp] = (int)greedy_action(O + warp * kOutPad, nullptr, L.plain);
   __syncthreads();
   stage_image(sw, img_t, L.bytes);
   __syncthreads();
   mlp_tile(qw_at(sw, L), X, H1, H2, O, warp, lane);
   if (lane == 0 && i < batch) {
     float qv[5];
-    greedy_action(O + warp * kOutPad, qv);
+    greedy_action(O + warp * kOutPad, qv, L.plain);
     const float nt = b.term[i] ? 0.0f : 1.0f;
     y[i] = b.r[i] + gamma * nt * qv[astar[warp]];
   }

@@ -22,14 +22,17 @@ def _stream(stream):
 
 
 class QNet:
-    """Dueling Q-network on the device (``sg_qnet_t``)."""
+    """Q-network on the device (``sg_qnet_t``): arch "dueling" (256-256, value
+    and advantage heads) or "paper" (the paper's 256-128 network, plain
+    Q-value head)."""
 
-    def __init__(self, n_in: int, max_batch: int = 256, seed: int = 0):
+    def __init__(self, n_in: int, max_batch: int = 256, seed: int = 0, arch: str = "dueling"):
         self.L = _lib.load()
         self.n_in = int(n_in)
+        self.arch = arch
         self.handle = C.c_void_p()
-        check(self.L.sg_qnet_create(self.n_in, int(max_batch), int(seed) & (2**64 - 1), C.byref(self.handle)),
-              "sg_qnet_create")
+        check(self.L.sg_qnet_create(self.n_in, _lib.SG_QNET_ARCHS[arch], int(max_batch), int(seed) & (2**64 - 1),
+                                    C.byref(self.handle)), "sg_qnet_create")
         n = C.c_int64()
         check(self.L.sg_qnet_num_params(self.handle, C.byref(n)), "sg_qnet_num_params")
         self.n_params = int(n.value)

@@ -52,16 +52,17 @@ def _params(**overrides):
     return base_params(**overrides)
 
 
-def make_setup(kind: str, n_envs: int = 16, seed: int = 0) -> Sim:
-    """The training simulator of the Grey or the Color setup."""
+def make_setup(kind: str, n_envs: int = 16, seed: int = 0, beams: int = 32) -> Sim:
+    """The training simulator of the Grey or the Color setup (beams: LiDAR
+    beams; the paper's robot has 27, a 32-entry state)."""
     if kind == "grey":
         maps = _maps(TRAIN_SEEDS[:1])
         env_map = np.zeros(n_envs, np.int32)
-        p = _params(seed=seed)
+        p = _params(seed=seed, n_beams=beams)
     elif kind == "color":
         maps = _maps(TRAIN_SEEDS)
         env_map = (np.arange(n_envs) % len(maps)).astype(np.int32)
-        p = _params(seed=seed, **COLOR_RANGES)
+        p = _params(seed=seed, n_beams=beams, **COLOR_RANGES)
     else:
         raise ValueError(f"unknown setup {kind!r}")
     sim = Sim(p, maps, env_map)
@@ -70,12 +71,12 @@ def make_setup(kind: str, n_envs: int = 16, seed: int = 0) -> Sim:
 
 
 def evaluate(qnet, seeds=TEST_SEEDS, envs_per_map: int = 8, max_steps: int = 2000, seed: int = 12345,
-             chunk: int = 250) -> dict:
+             chunk: int = 250, beams: int = 32) -> dict:
     """Greedy arrival rate of qnet on the maps of `seeds` with nominal
     parameters: envs_per_map envs per map, each env's first episode."""
     maps = _maps(seeds)
     n = len(maps) * envs_per_map
-    sim = Sim(_params(seed=seed), maps, (np.arange(n) % len(maps)).astype(np.int32))
+    sim = Sim(_params(seed=seed, n_beams=beams), maps, (np.arange(n) % len(maps)).astype(np.int32))
     sim.reset()
     eps = torch.zeros(n, device=sim.device)
     done = torch.empty((chunk, n), dtype=torch.uint8, device=sim.device)
@@ -99,24 +100,25 @@ def evaluate(qnet, seeds=TEST_SEEDS, envs_per_map: int = 8, max_steps: int = 200
 
 
 def train_and_evaluate(kind: str, transitions: int, n_envs: int = 16, seed: int = 0, tps: int = 256,
-                       batch: int = 256, rollout_k: int = 8, eval_envs_per_map: int = 8) -> dict:
+                       batch: int = 256, rollout_k: int = 8, eval_envs_per_map: int = 8, arch: str = "dueling",
+                       beams: int = 32) -> dict:
     """Train one setup with the ASL loop (the paper's Sparrow hyper-parameters:
     TPS 256, batch 256, learning start 30K transitions, lr 1e-4, gamma 0.98,
     target update 200, upload every 50, VEM with OR N -> 3N/16 over 500K)
     for `transitions` interacting steps; evaluate on the training maps and
     on the held-out maps."""
-    sim = make_setup(kind, n_envs, seed)
+    sim = make_setup(kind, n_envs, seed, beams)
     tr = ColorTrainer(sim, batch=batch, slots=max(64, 1_000_000 // n_envs), tps=tps, learn_start=30_000, lr=1e-4,
                       gamma=0.98, target_every=200, upload_every=50, seed=seed, two_streams=True,
-                      max_rollout_k=rollout_k)
+                      max_rollout_k=rollout_k, arch=arch)
     t0 = time.perf_counter()
     tr.run(max(1, transitions // n_envs), rollout_k=rollout_k)
     train_s = time.perf_counter() - t0
     train_seeds = TRAIN_SEEDS[:1] if kind == "grey" else TRAIN_SEEDS
-    return dict(setup=kind, seed=seed, n_envs=n_envs, transitions=tr.transitions, updates=tr.updates,
-                train_seconds=train_s, tfm=tr.tfm_report(),
-                train_maps=evaluate(tr.learner, train_seeds, eval_envs_per_map),
-                test_maps=evaluate(tr.learner, TEST_SEEDS, eval_envs_per_map))
+    return dict(setup=kind, seed=seed, n_envs=n_envs, arch=arch, beams=beams, transitions=tr.transitions,
+                updates=tr.updates, train_seconds=train_s, tfm=tr.tfm_report(),
+                train_maps=evaluate(tr.learner, train_seeds, eval_envs_per_map, beams=beams),
+                test_maps=evaluate(tr.learner, TEST_SEEDS, eval_envs_per_map, beams=beams))
 
 
 def main(argv=None):
@@ -124,10 +126,14 @@ def main(argv=None):
     ap.add_argument("--transitions", type=int, default=500_000)
     ap.add_argument("--seeds", type=int, default=1)
     ap.add_argument("--envs", type=int, default=16)
+    ap.add_argument("--arch", default="dueling", choices=["dueling", "paper"],
+                    help="Q-network: dueling 256-256, or the paper's [32, 256, 128, 5]")
+    ap.add_argument("--beams", type=int, default=32, help="LiDAR beams (the paper's robot: 27)")
     a = ap.parse_args(argv)
     for seed in range(a.seeds):
         for kind in ("grey", "color"):
-            print(json.dumps(train_and_evaluate(kind, a.transitions, a.envs, seed)), flush=True)
+            print(json.dumps(train_and_evaluate(kind, a.transitions, a.envs, seed, arch=a.arch, beams=a.beams)),
+                  flush=True)
 
 
 if __name__ == "__main__":

@@ -35,17 +35,19 @@ from .qnet import QNet, Replay
 
 class ColorTrainer:
     def __init__(self, sim, *, batch=256, slots=128, gamma=0.98, lr=1e-4, target_every=200, upload_every=50,
-                 tps=256, learn_start=30000, eps=None, vem="paper", seed=0, two_streams=False, max_rollout_k=8):
+                 tps=256, learn_start=30000, eps=None, vem="paper", seed=0, two_streams=False, max_rollout_k=8,
+                 arch="dueling"):
         """eps: a fixed per-env noise tensor (no schedule); otherwise vem is
         "paper", a dict of sg_vem_eps arguments, or None (fixed linear
-        0.01 .. 0.81 over the envs)."""
+        0.01 .. 0.81 over the envs).  arch: the Q-network ("dueling" or the
+        paper's "paper")."""
         self.sim = sim
         n = sim.n
         self.batch, self.gamma, self.lr = batch, gamma, lr
         self.target_every, self.upload_every, self.tps = target_every, upload_every, tps
         self.learn_start, self.seed = learn_start, seed
-        self.learner = QNet(sim.obs_dim, batch, seed=seed)
-        self.actor = QNet(sim.obs_dim, batch, seed=seed)
+        self.learner = QNet(sim.obs_dim, batch, seed=seed, arch=arch)
+        self.actor = QNet(sim.obs_dim, batch, seed=seed, arch=arch)
         self.actor.copy_from(self.learner)
         # concurrent rollouts of up to max_rollout_k steps must not be sampled
         self.max_rollout_k = max_rollout_k

@@ -28,39 +28,46 @@ pytestmark = pytest.mark.gpu
 Q_REL_TOL = 4e-3  # max |Q_gpu - Q_bf16_recipe| / max|Q| (float32 vs float64 sums, bf16 re-rounding)
 
 
-def _theta(seed, n_in=37, scale=1.0):
-    p = OQ.init_params(seed, n_in)
+def _theta(seed, n_in=37, scale=1.0, arch="dueling"):
+    p = OQ.init_params(seed, n_in, arch)
     for k in p:
         p[k] = p[k] * scale
     return OQ.flatten(p).astype(np.float32)
 
 
-def _qnet(n_in=37, max_batch=256, seed=0):
+def _qnet(n_in=37, max_batch=256, seed=0, arch="dueling"):
     from paper_2305_04180_gb300 import QNet
 
-    return QNet(n_in, max_batch, seed)
+    return QNet(n_in, max_batch, seed, arch=arch)
 
 
-def test_params_roundtrip_and_count():
-    q = _qnet()
-    assert q.n_params == 77062
-    th = _theta(1)
+@pytest.mark.parametrize("arch,n_in,count", [("dueling", 37, 77062), ("paper", 32, 41989)])
+def test_params_roundtrip_and_count(arch, n_in, count):
+    q = _qnet(n_in, arch=arch)
+    assert q.n_params == count == OQ.n_params(n_in, arch)
+    # the library's own initialisation is finite, non-zero and in the fan-in bounds
+    th0 = q.get_params("online")
+    assert np.isfinite(th0).all() and np.abs(th0).max() <= 1.0 / np.sqrt(min(n_in, 128)) + 1e-6
+    assert np.count_nonzero(th0) > 0.99 * th0.size
+    th = _theta(1, n_in, arch=arch)
     q.set_params(th)
     assert np.array_equal(q.get_params("online"), th) and np.array_equal(q.get_params("target"), th)
-    th2 = _theta(2)
+    th2 = _theta(2, n_in, arch=arch)
     q.set_params(th2, "target")
     assert np.array_equal(q.get_params("online"), th) and np.array_equal(q.get_params("target"), th2)
 
 
-@pytest.mark.parametrize("n_in,M", [(37, 1), (37, 53), (37, 4096), (69, 300), (21, 17)])
-def test_forward_against_oracle(n_in, M):
+@pytest.mark.parametrize("n_in,M,arch", [(37, 1, "dueling"), (37, 53, "dueling"), (37, 4096, "dueling"),
+                                         (69, 300, "dueling"), (21, 17, "dueling"), (32, 300, "paper"),
+                                         (32, 1, "paper"), (37, 77, "paper")])
+def test_forward_against_oracle(n_in, M, arch):
     rng = np.random.default_rng(n_in + M)
-    q = _qnet(n_in)
-    th = _theta(3, n_in, scale=2.0)
+    q = _qnet(n_in, arch=arch)
+    th = _theta(3, n_in, scale=2.0, arch=arch)
     q.set_params(th)
     obs = rng.uniform(-1, 1, size=(M, n_in)).astype(np.float32)
     got = q.forward(torch.from_numpy(obs).cuda()).cpu().numpy().astype(np.float64)
-    p = OQ.unflatten(th.astype(np.float64), n_in)
+    p = OQ.unflatten(th.astype(np.float64), n_in, arch)
     ref_bf = OQ.forward(p, obs, bf16=True)
     ref_64 = OQ.forward(p, obs)
     scale = np.abs(ref_64).max()
@@ -78,8 +85,8 @@ def _margin_ok(q_ref, act, tol):
     return best - chosen <= tol
 
 
-@pytest.mark.parametrize("rows", [16, 32])
-def test_fused_rollout_teacher_forced(rows):
+@pytest.mark.parametrize("rows,arch", [(16, "dueling"), (32, "dueling"), (32, "paper")])
+def test_fused_rollout_teacher_forced(rows, arch):
     """Step by step (K = 1 rollouts) from the GPU's own state: every decision
     checked, every simulator output bit-exact, the replay ring exact; for
     CTAs of 16 and of 32 envs."""
@@ -89,11 +96,11 @@ def test_fused_rollout_teacher_forced(rows):
     maps = w.maps()
     g = Sim(w.params, maps, w.env_map)
     o = OracleSim(w.params, maps, w.env_map, prec="f32")
-    q = _qnet(g.obs_dim)
+    q = _qnet(g.obs_dim, arch=arch)
     q.set_rollout_rows(rows)
-    th = _theta(5, g.obs_dim, scale=3.0)
+    th = _theta(5, g.obs_dim, scale=3.0, arch=arch)
     q.set_params(th)
-    p = OQ.unflatten(th.astype(np.float64), g.obs_dim)
+    p = OQ.unflatten(th.astype(np.float64), g.obs_dim, arch)
     n = g.n
     rp = Replay(8, n, g.obs_dim)
     eps = torch.from_numpy(w.eps).cuda()
@@ -185,13 +192,13 @@ def test_fused_rollout_tile_heights_agree():
     assert np.array_equal(out[0][2][1], out[1][2][1])
 
 
-def _fill_replay(n_envs=64, steps=40, seed_theta=7):
+def _fill_replay(n_envs=64, steps=40, seed_theta=7, arch="dueling"):
     from paper_2305_04180_gb300 import Replay, Sim
 
     w = workload("qnet4096", n_envs=n_envs)
     g = Sim(w.params, w.maps(), w.env_map)
-    q = _qnet(g.obs_dim)
-    q.set_params(_theta(seed_theta, g.obs_dim, scale=2.0))
+    q = _qnet(g.obs_dim, arch=arch)
+    q.set_params(_theta(seed_theta, g.obs_dim, scale=2.0, arch=arch))
     rp = Replay(32, g.n, g.obs_dim)
     g.reset()
     g.rollout(steps, policy="eps_q", qnet=q, eps=torch.from_numpy(w.eps).cuda(), replay=rp)
@@ -207,11 +214,11 @@ def _oracle_batch(rp, seed, tstep, batch):
                      s2=s2[idx].astype(np.float64), term=t[idx].astype(np.float64))
 
 
-@pytest.mark.parametrize("batch", [256, 100])
-def test_td_loss_and_gradient_against_oracle(batch):
-    g, q, rp = _fill_replay()
-    th_on = _theta(8, g.obs_dim, scale=2.0)
-    th_tg = _theta(9, g.obs_dim, scale=2.0)
+@pytest.mark.parametrize("batch,arch", [(256, "dueling"), (100, "dueling"), (256, "paper"), (37, "paper")])
+def test_td_loss_and_gradient_against_oracle(batch, arch):
+    g, q, rp = _fill_replay(arch=arch)
+    th_on = _theta(8, g.obs_dim, scale=2.0, arch=arch)
+    th_tg = _theta(9, g.obs_dim, scale=2.0, arch=arch)
     q.set_params(th_on, "online")
     q.set_params(th_tg, "target")
     seed = 1234
@@ -219,8 +226,8 @@ def test_td_loss_and_gradient_against_oracle(batch):
     grad = torch.zeros(q.n_params, device="cuda")
     q.train_step(rp, batch, gamma=0.98, lr=0.0, seed=seed, loss=loss, grad=grad)
     _, bt = _oracle_batch(rp, seed, 0, batch)
-    pon = OQ.unflatten(th_on.astype(np.float64), g.obs_dim)
-    ptg = OQ.unflatten(th_tg.astype(np.float64), g.obs_dim)
+    pon = OQ.unflatten(th_on.astype(np.float64), g.obs_dim, arch)
+    ptg = OQ.unflatten(th_tg.astype(np.float64), g.obs_dim, arch)
     ref_loss, ref_g = OQ.td_loss_grad(pon, ptg, bt, 0.98, bf16=True)
     _, ref_g64 = OQ.td_loss_grad(pon, ptg, bt, 0.98, bf16=False)
     gl = float(loss.item())
@@ -235,25 +242,26 @@ def test_td_loss_and_gradient_against_oracle(batch):
     assert rel_g <= 3e-2
     assert rel_g64 <= 1e-1
     # every block of the gradient, not just the norm
-    for name, sl in _blocks(g.obs_dim):
+    for name, sl in _blocks(g.obs_dim, arch):
         nb = np.linalg.norm(rflat[sl])
         if nb > 0:
             assert np.linalg.norm(gg[sl] - rflat[sl]) / nb <= 6e-2, name
 
 
-def _blocks(n_in):
+def _blocks(n_in, arch="dueling"):
     o = 0
     out = []
-    for name, shp in OQ.param_shapes(n_in):
+    for name, shp in OQ.param_shapes(n_in, arch):
         k = int(np.prod(shp))
         out.append((name, slice(o, o + k)))
         o += k
     return out
 
 
-def test_adam_step_and_target_sync():
-    g, q, rp = _fill_replay()
-    th = _theta(10, g.obs_dim, scale=1.0)
+@pytest.mark.parametrize("arch", ["dueling", "paper"])
+def test_adam_step_and_target_sync(arch):
+    g, q, rp = _fill_replay(arch=arch)
+    th = _theta(10, g.obs_dim, scale=1.0, arch=arch)
     q.set_params(th)
     grad = torch.zeros(q.n_params, device="cuda")
     q.train_step(rp, 64, lr=0.0, seed=7, grad=grad)  # gradient at step 0
@@ -273,6 +281,6 @@ def test_adam_step_and_target_sync():
     assert np.array_equal(q.get_params("target"), q.get_params("online"))
     # the inference copy follows the master weights: forward equals a fresh net with those weights
     obs = torch.rand((40, g.obs_dim), device="cuda")
-    q2 = _qnet(g.obs_dim)
+    q2 = _qnet(g.obs_dim, arch=arch)
     q2.set_params(q.get_params("online"))
     assert torch.equal(q.forward(obs), q2.forward(obs))

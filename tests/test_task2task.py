@@ -25,10 +25,13 @@ def test_setups_differ_as_described():
     assert fc[5].min() >= COLOR_RANGES["dt_lo"] and fc[5].max() <= COLOR_RANGES["dt_hi"]
 
 
-def test_short_training_and_evaluation_account_for_every_episode():
+@pytest.mark.parametrize("arch,beams", [("dueling", 32), ("paper", 27)])
+def test_short_training_and_evaluation_account_for_every_episode(arch, beams):
+    """Also with the paper's robot and network: 27 beams (a 32-entry state)
+    and the [32, 256, 128, 5] Q-network."""
     from paper_2305_04180_gb300.task2task import train_and_evaluate
 
-    r = train_and_evaluate("color", 40_000, n_envs=16, seed=2, eval_envs_per_map=2)
+    r = train_and_evaluate("color", 40_000, n_envs=16, seed=2, eval_envs_per_map=2, arch=arch, beams=beams)
     # 2,500 vectorized steps in chunks of 8; learning starts with the chunk
     # that reaches 30,000 transitions (the 235th, 128 transitions each), so
     # 2,500 - 8 x 234 = 628 steps train at rho = 16 x 256 / 256 = 16
