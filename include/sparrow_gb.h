@@ -276,7 +276,7 @@ int sg_sim_get_clearance(sg_sim_t sim, uint8_t* host, size_t* bytes, int64_t* of
 int sg_sim_status(sg_sim_t sim, uint32_t* device_status);
 
 /* ---------------------------------------------------------------------- */
-/* Learned part: dueling Q-network, replay ring, TD learner                */
+/* Learned part: Q-networks, replay ring, TD learner                        */
 /* ---------------------------------------------------------------------- */
 
 /*
@@ -416,8 +416,9 @@ int sg_vem_eps(sg_sim_t sim, float e_min, float e_max, double or_start, double o
  * instead of ring samples: y_i = r_i + gamma (1 - term_i)
  * Q_target(s2_i, argmax_a Q(s2_i, a)), loss = mean Huber(Q(s_i, a_i) - y_i),
  * and its gradient w.r.t. the online parameters.
- *   params_dev, target_params_dev  flat FP32 parameters (layout of
- *                 sg_qnet_set_params) of the online and the target network.
+ *   params_dev, target_params_dev  flat FP32 parameters (the dueling
+ *                 network's order of sg_qnet_set_params) of the online and the
+ *                 target network.
  *   n_in          input width, in [1, 69].
  *   s_dev, s2_dev batch x n_in floats; a_dev, term_dev batch uint8 (a < 5);
  *                 r_dev batch floats.  All caller-owned device memory.

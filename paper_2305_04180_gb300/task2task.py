@@ -16,8 +16,9 @@ arrival rate on held-out maps.
   the others).
 
 The maps are the seeded synthetic grids of ``workloads.maps``; the network is
-this library's dueling MLP.  Run as a script for a JSON line per setup:
-``python -m paper_2305_04180_gb300.task2task --transitions 500000``.
+this library's dueling MLP or (``--arch paper --beams 27``) the paper's own
+[32, 256, 128, 5] network on a 27-beam robot.  Run as a script for a JSON line
+per setup: ``python -m paper_2305_04180_gb300.task2task --transitions 500000``.
 """
 
 from __future__ import annotations
