@@ -296,6 +296,7 @@ int sg_sim_status(sg_sim_t sim, uint32_t* device_status);
  * activations and FP32 accumulation; FP32 master weights, a target copy and
  * Adam moments stay on the device.
  *   n_in       input width = the simulator's obs_dim, in [1, 69].
+ *   arch       SG_QNET_DUELING or SG_QNET_PAPER (else SG_E_INVAL).
  *   max_batch  largest sg_td_train_step batch, in [1, 65536] (sizes the
  *              learner's scratch buffers).
  *   seed       parameters start uniform in +-1/sqrt(fan_in), parameter j of
