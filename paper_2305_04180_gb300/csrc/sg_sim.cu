@@ -119,65 +119,65 @@ __global__ void __launch_bounds__(128) k_reset(const __grid_constant__ DevCfg c,
 }
 
 // One vectorized step; one warp per env.
-// One vectorized step of every env (sg_sim_step).  A CTA takes 32 envs
-// (consecutive in the env order grouped by map).
-// Warp 0 runs the scalar part of the step lane-parallel, one env per lane:
-// state load, delay, Eq. 5, Eq. 6, the collision test's map-bounds and
-// clearance parts, arrival, truncation, the AutoReset draws and everything of
-// the observation and of Eq. 11 that does not need a scan; envs whose
-// collision test needs the bit rows get it from the whole warp.  Then the 8
-// warps scan the 32 envs (lane j marches beam j), four envs each: the
+// One vectorized step of every env (sg_sim_step).  A warp takes kStepEnvsPerWarp
+// envs (consecutive in the env order grouped by map): its lanes 0.. run the
+// scalar part of the step for one env each (lane_step: state load, delay,
+// Eq. 5, Eq. 6, collision, arrival, truncation, AutoReset draws and the
+// scan-free terms of the observation and of Eq. 11, into shared records),
+// then the whole warp scans each of its envs (lane j marches beam j): the
 // post-motion state always (the observation, or the terminal observation and
-// the reward of a done env), the reset state of a done env.  Every value is
-// the one-env-per-warp step's, in the same float32 expressions.
-constexpr int kStepEnvs = 32;
+// the reward of a done env), the reset state of a done env.  No warp waits on
+// another.  Every value is the one-env-per-warp step's, in the same float32
+// expressions.
+constexpr int kStepEnvsPerWarp = 4;
 constexpr int kStepWarps = 8;
 
-__global__ void __launch_bounds__(256, 4) k_step(const __grid_constant__ DevCfg c, SimPtrs p,
-                                                 const int* __restrict__ order, const uint8_t* __restrict__ act,
-                                                 float* __restrict__ obs, float* __restrict__ rew,
-                                                 uint8_t* __restrict__ done, float* __restrict__ term) {
-  __shared__ StepScanRec rec[kStepEnvs];
+__global__ void __launch_bounds__(32 * kStepWarps, 4) k_step(const __grid_constant__ DevCfg c, SimPtrs p,
+                                                             const int* __restrict__ order,
+                                                             const uint8_t* __restrict__ act,
+                                                             float* __restrict__ obs, float* __restrict__ rew,
+                                                             uint8_t* __restrict__ done, float* __restrict__ term) {
+  __shared__ StepScanRec rec[kStepWarps][kStepEnvsPerWarp];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int base = blockIdx.x * kStepEnvs;
-  const int nv = min(kStepEnvs, c.n_envs - base);
-  if (warp == 0) {
-    // envs grouped by map, so that the CTA's scans share cache lines
-    const bool live = lane < nv;
-    const int i = live ? order[base + lane] : 0;
-    Env s;
-    if (live) s = load_env(p, i);
-    const uint32_t d = lane_step(c, p, i, live, s, live ? (uint32_t)act[i] : 0u, rec[lane], lane);
-    if (live) {
-      store_env(p, i, s);
-      done[i] = (uint8_t)d;
-    }
+  const int base = (blockIdx.x * kStepWarps + warp) * kStepEnvsPerWarp;
+  if (base >= c.n_envs) return;  // warp-uniform
+  const int nv = min(kStepEnvsPerWarp, c.n_envs - base);
+  const bool live = lane < nv;
+  const int i = live ? order[base + lane] : 0;
+  Env s;
+  if (live) s = load_env(p, i);
+  // lanes past the warp's envs take part in the warp-wide collision tests only
+  const uint32_t d =
+      lane_step(c, p, i, live, s, live ? (uint32_t)act[i] : 0u, rec[warp][live ? lane : 0], lane);
+  if (live) {
+    store_env(p, i, s);
+    done[i] = (uint8_t)d;
   }
-  __syncthreads();
-  for (int e = warp; e < nv; e += kStepWarps) {
-    const StepScanRec& r = rec[e];
-    const int i = r.env;
+  __syncwarp();
+  for (int e = 0; e < nv; ++e) {
+    const StepScanRec& r = rec[warp][e];
+    const int ie = r.env;
     const MapDesc m = p.maps[r.map];
-    const uint32_t d = r.done;
+    const uint32_t de = r.done;
     float b0, b1;
     const float mn = scan_env(c, p, m, r.nb, r.stepb, r.ax, r.ay, r.aphi, r.asigma,
                               ((uint64_t)r.anhi << 32) | r.anlo, lane, b0, b1);
     float rw;
-    if (d & 1u)
+    if (de & 1u)
       rw = -10.0f;
-    else if (d & 2u)
+    else if (de & 2u)
       rw = 75.0f;
     else
       rw = reward_finish(c, r.rpart, mn);
-    if (!d) {
-      write_row(obs + (long long)i * c.obs_dim, b0, b1, r.exa, c.B, lane);
+    if (!de) {
+      write_row(obs + (long long)ie * c.obs_dim, b0, b1, r.exa, c.B, lane);
     } else {
-      if (term) write_row(term + (long long)i * c.obs_dim, b0, b1, r.exa, c.B, lane);
+      if (term) write_row(term + (long long)ie * c.obs_dim, b0, b1, r.exa, c.B, lane);
       scan_env(c, p, m, r.nb, r.stepb, r.bx, r.by, r.bphi, r.bsigma, ((uint64_t)r.bnhi << 32) | r.bnlo, lane, b0,
                b1);
-      write_row(obs + (long long)i * c.obs_dim, b0, b1, r.exb, c.B, lane);
+      write_row(obs + (long long)ie * c.obs_dim, b0, b1, r.exb, c.B, lane);
     }
-    if (lane == 0) rew[i] = rw;
+    if (lane == 0) rew[ie] = rw;
   }
 }
 
@@ -899,7 +899,8 @@ extern "C" int sg_sim_step(sg_sim_t sim, const uint8_t* act_dev, float* obs_dev,
                            uint8_t* done_dev, float* term_obs_dev, sg_stream_t stream) {
   if (!sim || !act_dev || !obs_dev || !rew_dev || !done_dev) return SG_E_INVAL;
   if (((uintptr_t)obs_dev & 3) || ((uintptr_t)rew_dev & 3) || ((uintptr_t)term_obs_dev & 3)) return SG_E_ALIGN;
-  k_step<<<(sim->dc.n_envs + kStepEnvs - 1) / kStepEnvs, 32 * kStepWarps, 0, stream>>>(
+  constexpr int kPerBlock = kStepWarps * kStepEnvsPerWarp;
+  k_step<<<(sim->dc.n_envs + kPerBlock - 1) / kPerBlock, 32 * kStepWarps, 0, stream>>>(
       sim->dc, sg_sim_ptrs(sim), sim->map_order_dev, act_dev, obs_dev, rew_dev, done_dev, term_obs_dev);
   SG_CUDA(cudaGetLastError());
   return SG_OK;
