@@ -104,9 +104,37 @@ def test_step_teacher_forced_plain16():
 
 def test_step_teacher_forced_domain_randomised():
     """1024 envs over 32 maps with every randomisation on (delay, K, cap,
-    noise, control interval): 200 steps = 204,800 env-steps."""
+    noise, control interval): 1,000 steps = 1,024,000 env-steps, every one
+    teacher-forced from the GPU's state."""
     g, o, _ = _pair(workload("dr1024"))
-    assert _teacher_forced(g, o, 200, seed=1) == 204800
+    assert _teacher_forced(g, o, 1000, seed=1) == 1024000
+
+
+@pytest.mark.parametrize("launch", [None, dict(kernel="pipe", warps_per_block=8, obs_warps=7, order="map")])
+def test_rollout_plain16_million_env_steps(launch):
+    """The 16-env workload free-running for 62,500 steps (10^6 env-steps):
+    every step's action, reward and done flags and the final state equal the
+    oracle's."""
+    w = workload("plain16")
+    g, o, _ = _pair(w)
+    if launch:
+        g.set_launch(**launch)
+    g.reset()
+    o.reset()
+    K = 62500
+    n = g.n
+    act = torch.empty((K, n), dtype=torch.uint8, device="cuda")
+    rew = torch.empty((K, n), dtype=torch.float32, device="cuda")
+    done = torch.empty((K, n), dtype=torch.uint8, device="cuda")
+    obs = g.new_obs()
+    g.rollout(K, obs=obs, act_seq=act, rew_seq=rew, done_seq=done)
+    oobs, oact, orew, odone = o.rollout_random(K, 0)
+    assert np.array_equal(act.cpu().numpy(), oact)
+    assert np.array_equal(done.cpu().numpy(), odone)
+    assert np.array_equal(bits(rew.cpu().numpy()), bits(orew))
+    assert np.array_equal(bits(obs.cpu().numpy()), bits(oobs))
+    _assert_state_equal(g, o, K)
+    assert int((odone != 0).sum()) > 1000
 
 
 def test_step_uneven_beams_and_ragged_batch():
