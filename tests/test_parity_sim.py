@@ -248,6 +248,47 @@ def test_rollout_full_size_sampled_against_oracle(launch):
         assert np.array_equal(o.u[:, i], u[:2, i])
 
 
+@pytest.mark.parametrize("launch", [None, dict(kernel="pipe", warps_per_block=8, obs_warps=7, order="map")])
+def test_uneven_full_size_sampled_against_oracle(launch):
+    """The 8,192-env uneven workload at full size (one map per env, sides
+    128..1,024, 16/32/64 beams, per-env dynamics): 64 steps on the GPU, then
+    sampled envs (every map size and beam count) replayed one by one on the
+    oracle, which holds only their maps (1x1 placeholders for the others, so
+    env indices and random streams are unchanged)."""
+    w = workload("uneven8192")
+    maps = w.maps()
+    g = _sim(w.params, maps, w.env_map, w.env_beams)
+    if launch:
+        g.set_launch(**launch)
+    g.reset()
+    K = w.steps
+    rew = torch.empty((K, g.n), device="cuda")
+    done = torch.empty((K, g.n), dtype=torch.uint8, device="cuda")
+    g.rollout(K, rew_seq=rew, done_seq=done)
+    rew = rew.cpu().numpy()
+    done = done.cpu().numpy()
+    f, u = g.get_state()
+    sides = np.array([m.shape[1] for m in maps])
+    sample = [0, 1, 8191]
+    for side in np.unique(sides):
+        for nb in (16, 32, 64):
+            cand = np.flatnonzero((sides[w.env_map] == side) & (w.env_beams == nb))
+            if cand.size:
+                sample.append(int(cand[len(cand) // 2]))
+    keep = {int(w.env_map[i]) for i in sample}
+    tiny = np.ones((1, 1), np.uint8)
+    o = OracleSim(w.params, [maps[m] if m in keep else tiny for m in range(len(maps))], w.env_map, w.env_beams,
+                  prec="f32")
+    for i in sample:
+        o.reset_env(i, 0)
+        for k in range(K):
+            _, orew, odone, _ = o.step_one(i, o.random_action(i, k))
+            assert odone == done[k, i] and bits(np.float32(orew)) == bits(rew[k, i]), (i, k)
+        assert np.array_equal(bits(o.f[:, i]), bits(f[:, i])), i
+        assert np.array_equal(o.u[:, i], u[:2, i]), i
+    assert len(sample) >= 12
+
+
 def test_against_float64_oracle_tolerances():
     """Teacher forced against the float64 oracle (noise off so that ranges
     are comparable): pose/velocity within 1e-5 relative; ranges equal in
