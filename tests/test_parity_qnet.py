@@ -192,6 +192,49 @@ def test_fused_rollout_tile_heights_agree():
     assert np.array_equal(out[0][2][1], out[1][2][1])
 
 
+def test_full_learned_workload_sampled_against_oracle():
+    """The 65,536-env learned-loop workload at full size (1,024 maps of sides
+    256..1,024, 16..64 beams, every randomisation on) through the fused
+    rollout: 32 steps on the GPU with its actions recorded, then sampled envs
+    replayed on the oracle with those actions: the exploration decision and
+    random action of every step exact, the simulator part (rewards, done
+    flags, final state) bit-exact."""
+    from paper_2305_04180_gb300 import Sim
+
+    w = workload("full65536")
+    maps = w.maps()
+    g = Sim(w.params, maps, w.env_map, w.env_beams)
+    q = _qnet(g.obs_dim, max_batch=256)
+    q.set_params(_theta(12, g.obs_dim, scale=2.0))
+    g.reset()
+    K = 32
+    act = torch.empty((K, g.n), dtype=torch.uint8, device="cuda")
+    rew = torch.empty((K, g.n), device="cuda")
+    done = torch.empty((K, g.n), dtype=torch.uint8, device="cuda")
+    g.rollout(K, policy="eps_q", qnet=q, eps=torch.from_numpy(w.eps).cuda(), act_seq=act, rew_seq=rew,
+              done_seq=done)
+    act, rew, done = act.cpu().numpy(), rew.cpu().numpy(), done.cpu().numpy()
+    f, u = g.get_state()
+    sample = [0, 1, 1023, 1024, 30000, 65535] + list(range(5, 65536, 6553))
+    keep = {int(w.env_map[i]) for i in sample}
+    tiny = np.ones((1, 1), np.uint8)
+    o = OracleSim(w.params, [maps[m] if m in keep else tiny for m in range(len(maps))], w.env_map, w.env_beams,
+                  prec="f32")
+    n_explore = 0
+    for i in sample:
+        o.reset_env(i, 0)
+        for k in range(K):
+            a = int(act[k, i])
+            if o.L.orc_explore_uniform(C.byref(o.cfg), i, k) < w.eps[i]:
+                assert a == o.random_action(i, k), (i, k)
+                n_explore += 1
+            _, orew, odone, _ = o.step_one(i, a)
+            assert odone == done[k, i] and bits(np.float32(orew)) == bits(rew[k, i]), (i, k)
+        assert np.array_equal(bits(o.f[:, i]), bits(f[:, i])), i
+        assert np.array_equal(o.u[:, i], u[:2, i]), i
+    assert n_explore > 10
+
+
 def _fill_replay(n_envs=64, steps=40, seed_theta=7, arch="dueling"):
     from paper_2305_04180_gb300 import Replay, Sim
 
