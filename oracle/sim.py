@@ -47,7 +47,7 @@ def build_oracle(force: bool = False) -> None:
 class _Config(C.Structure):
     _fields_ = [
         ("n_beams", C.c_int32), ("n_actions", C.c_int32), ("t_max", C.c_int32),
-        ("delay_lo", C.c_int32), ("delay_hi", C.c_int32), ("pad0", C.c_int32),
+        ("delay_lo", C.c_int32), ("delay_hi", C.c_int32), ("n_dyn", C.c_int32),
         ("fov", C.c_double), ("range_max", C.c_double), ("march_step", C.c_double),
         ("robot_radius", C.c_double), ("goal_radius", C.c_double), ("near_dist", C.c_double),
         ("start_offset", C.c_double), ("start_jitter", C.c_double),
@@ -56,6 +56,8 @@ class _Config(C.Structure):
         ("v_nom", C.c_double), ("w_nom", C.c_double),
         ("action_v", C.c_double * 8), ("action_w", C.c_double * 8),
         ("seed", C.c_uint64),
+        ("dyn_radius", C.c_double), ("dyn_speed_lo", C.c_double), ("dyn_speed_hi", C.c_double),
+        ("dyn_keepout", C.c_double),
     ]
 
 
@@ -67,7 +69,7 @@ class _Maps(C.Structure):
 class _Envs(C.Structure):
     _fields_ = [("n_envs", C.c_int32), ("pad0", C.c_int32),
                 ("env_map", C.c_void_p), ("env_beams", C.c_void_p),
-                ("f", C.c_void_p), ("u", C.c_void_p), ("b", C.c_void_p)]
+                ("f", C.c_void_p), ("u", C.c_void_p), ("b", C.c_void_p), ("dyn", C.c_void_p)]
 
 
 def lib(prec: str = "f32"):
@@ -89,6 +91,10 @@ def lib(prec: str = "f32"):
             L.orc_log.argtypes = [R]
             L.orc_pack_map.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, vp]
             L.orc_lidar.argtypes = [vp, vp, C.c_int32, R, R, R, C.c_int32, vp, vp]
+            L.orc_lidar_dyn.argtypes = [vp, vp, C.c_int32, vp, C.c_int32, R, R, R, C.c_int32, vp, vp]
+            L.orc_dyn_advance.argtypes = [vp, vp, vp, C.c_int32, R]
+            L.orc_dyn_collide.restype = C.c_int32
+            L.orc_dyn_collide.argtypes = [vp, vp, C.c_int32, R, R]
             L.orc_collide.restype = C.c_int32
             L.orc_collide.argtypes = [vp, vp, C.c_int32, R, R]
             L.orc_reset_env.argtypes = [vp, vp, vp, C.c_int32, C.c_uint32, vp]
@@ -140,6 +146,10 @@ def make_config(params: dict) -> _Config:
         c.action_v[i] = float(v)
         c.action_w[i] = float(w)
     c.seed = int(params["seed"]) & 0xFFFFFFFFFFFFFFFF
+    # dynamic obstacles (optional; none by default)
+    c.n_dyn = int(params.get("n_dyn", 0))
+    for k in ("dyn_radius", "dyn_speed_lo", "dyn_speed_hi", "dyn_keepout"):
+        setattr(c, k, float(params.get(k, 0.0)))
     return c
 
 
@@ -149,7 +159,8 @@ class OracleSim:
     ``prec`` selects strict float32 ('f32') or float64 ('f64').  State lives
     in three numpy arrays: ``f`` [9, n] reals (x, y, phi, vl, va, dt, K, cap,
     sigma), ``u`` [2, n] uint32 (ep_step, ep_id) and ``b`` [3, n] uint8
-    (q0, q1, delay).
+    (q0, q1, delay); with dynamic obstacles also ``dyn`` [4 n_dyn, n] reals
+    (obstacle o at rows 4o..4o+3: x, y, vx, vy).
     """
 
     def __init__(self, params: dict, maps, env_map, env_beams=None, prec: str = "f32"):
@@ -175,18 +186,42 @@ class OracleSim:
         self.u = np.zeros((N_U, self.n), np.uint32)
         self.b = np.zeros((N_B, self.n), np.uint8)
         self.status = np.zeros(1, np.uint32)
+        self.n_dyn = int(self.cfg.n_dyn)
+        self.dyn = np.zeros((4 * self.n_dyn, self.n), self.dtype)
         self.cenvs = _Envs(self.n, 0, self.env_map.ctypes.data,
                            self.env_beams.ctypes.data if self.env_beams is not None else None,
-                           self.f.ctypes.data, self.u.ctypes.data, self.b.ctypes.data)
+                           self.f.ctypes.data, self.u.ctypes.data, self.b.ctypes.data,
+                           self.dyn.ctypes.data if self.n_dyn else None)
 
     # -- state ------------------------------------------------------------
-    def set_state(self, f, u, b):
+    def set_state(self, f, u, b, dyn=None):
         self.f[...] = np.asarray(f, self.dtype)
         self.u[...] = u
         self.b[...] = b
+        if self.n_dyn:
+            self.dyn[...] = np.asarray(dyn, self.dtype).reshape(self.dyn.shape)
 
     def state(self):
-        return self.f.copy(), self.u.copy(), self.b.copy()
+        """(f, u, b), plus dyn when the envs have dynamic obstacles."""
+        base = (self.f.copy(), self.u.copy(), self.b.copy())
+        return base + (self.dyn.copy(),) if self.n_dyn else base
+
+    def dyn_advance(self, i: int, dt: float):
+        """One motion step of env i's obstacles alone (dt: control interval)."""
+        self.L.orc_dyn_advance(C.byref(self.cfg), C.byref(self.cmaps), C.byref(self.cenvs), int(i), dt)
+
+    def dyn_collide(self, i: int, x: float, y: float) -> bool:
+        return bool(self.L.orc_dyn_collide(C.byref(self.cfg), C.byref(self.cenvs), int(i), x, y))
+
+    def lidar_dyn(self, map_id: int, discs, x: float, y: float, phi: float, nb: int):
+        """Hit indices and noise-free ranges of nb beams with obstacle discs
+        (centres [(x, y), ...]) in the way."""
+        d = np.ascontiguousarray(np.asarray(discs, self.dtype).reshape(-1))
+        hits = np.zeros(nb, np.int32)
+        ranges = np.zeros(nb, self.dtype)
+        self.L.orc_lidar_dyn(C.byref(self.cfg), C.byref(self.cmaps), int(map_id), d.ctypes.data if d.size else None,
+                             d.size // 2, x, y, phi, int(nb), hits.ctypes.data, ranges.ctypes.data)
+        return hits, ranges
 
     # -- calls ------------------------------------------------------------
     def reset(self):

@@ -31,6 +31,8 @@
  *   Sec. 4.3.1      5-action table, reward Eq. 11 (-10 collide, +75 arrive)
  *   sim-parameter table: K 0.6, control interval 0.1 s, delay 0.1 s,
  *                   18 cm/s, 1 rad/s, noise 1 cm
+ *   Sec. 5          dynamic obstacles, named in the conclusion as the
+ *                   simulator's next capability; optional (n_dyn = 0 leaves the step as above)
  * Readings where the paper is silent (beam layout, march, collision disc,
  * delay FIFO, d1/d2/alpha, random numbers) are listed in the design notes;
  * each is restated at the point of use below.
@@ -71,13 +73,16 @@ typedef struct {
   int32_t n_actions;
   int32_t t_max;
   int32_t delay_lo, delay_hi;
-  int32_t pad0;
+  int32_t n_dyn;   /* dynamic obstacles per env, 0..8 (0: none) */
   double fov, range_max, march_step, robot_radius, goal_radius, near_dist;
   double start_offset, start_jitter;
   double dt_lo, dt_hi, k_lo, k_hi, cap_lo, cap_hi, sigma_lo, sigma_hi;
   double v_nom, w_nom;
   double action_v[8], action_w[8];
   uint64_t seed;
+  double dyn_radius;                 /* obstacle disc radius, cells */
+  double dyn_speed_lo, dyn_speed_hi; /* obstacle speed range, cells / s */
+  double dyn_keepout;                /* no obstacle starts this close to S or G */
 } orc_config;
 
 typedef struct {
@@ -97,6 +102,7 @@ typedef struct {
   R* f;        /* [9][n]: x y phi vl va dt K cap sigma */
   uint32_t* u; /* [2][n]: ep_step ep_id */
   uint8_t* b;  /* [3][n]: q0 (last action) q1 (the one before) delay */
+  R* dyn;      /* [4 n_dyn][n]: obstacle o at rows 4o..4o+3 (x y vx vy); NULL when n_dyn = 0 */
 } orc_envs;
 
 enum { F_X, F_Y, F_PHI, F_VL, F_VA, F_DT, F_K, F_CAP, F_SIGMA, F_COUNT };
@@ -262,7 +268,16 @@ static uint64_t g_samples = 0; /* march samples evaluated (instrumentation) */
 uint64_t orc_march_samples(void) { return g_samples; }
 void orc_reset_march_samples(void) { g_samples = 0; }
 
-static int32_t march(const orc_maps* m, int32_t map, R x, R y, R ux, R uy, R delta, int32_t kmax) {
+/* Sample point k of a ray lies in obstacle disc (ox, oy) of radius r when
+ * fma(ex, ex, ey*ey) <= r*r with (ex, ey) = sample - centre. */
+static int in_disc(R px, R py, R ox, R oy, R r2) {
+  R ex = px - ox, ey = py - oy;
+  return FMA(ex, ex, ey * ey) <= r2;
+}
+
+/* discs: nd obstacle centres as (x, y) pairs; a sample inside one is a hit */
+static int32_t march(const orc_maps* m, int32_t map, const R* discs, int32_t nd, R r2, R x, R y, R ux, R uy,
+                     R delta, int32_t kmax) {
   for (int32_t k = 1; k <= kmax; ++k) {
     ++g_samples;
     R t = (R)k * delta;
@@ -271,6 +286,8 @@ static int32_t march(const orc_maps* m, int32_t map, R x, R y, R ux, R uy, R del
     R fx = FLOOR(px), fy = FLOOR(py);
     if (fx < (R)0 || fy < (R)0 || fx >= (R)m->w[map] || fy >= (R)m->h[map]) return k;
     if (occupied(m, map, (int64_t)fx, (int64_t)fy)) return k;
+    for (int32_t o = 0; o < nd; ++o)
+      if (in_disc(px, py, discs[2 * o], discs[2 * o + 1], r2)) return k;
   }
   return kmax + 1;
 }
@@ -288,20 +305,29 @@ static R beam_offset(const orc_config* c, int32_t j, int32_t nb) {
   return (R)j * stepb - half;
 }
 
-/* Ranges of nb beams from pose (x, y, phi); writes hit indices and
+/* Ranges of nb beams from pose (x, y, phi) with nd obstacle discs (centres
+ * as (x, y) pairs, radius dyn_radius) in the way; writes hit indices and
  * noise-free ranges min(h * delta, range_max). */
-void orc_lidar(const orc_config* c, const orc_maps* m, int32_t map, R x, R y, R phi, int32_t nb,
-               int32_t* hits, R* ranges) {
+void orc_lidar_dyn(const orc_config* c, const orc_maps* m, int32_t map, const R* discs, int32_t nd, R x, R y,
+                   R phi, int32_t nb, int32_t* hits, R* ranges) {
   R delta = (R)c->march_step, rmax = (R)c->range_max;
+  R rd = (R)c->dyn_radius;
+  R r2 = rd * rd;
   int32_t kmax = kmax_of(c);
   for (int32_t j = 0; j < nb; ++j) {
     R beta = phi + beam_offset(c, j, nb);
     R s, co;
     sincos_r(beta, &s, &co);
-    int32_t h = march(m, map, x, y, -co, -s, delta, kmax);
+    int32_t h = march(m, map, discs, nd, r2, x, y, -co, -s, delta, kmax);
     hits[j] = h;
     ranges[j] = RMIN((R)h * delta, rmax);
   }
+}
+
+/* The same without obstacles. */
+void orc_lidar(const orc_config* c, const orc_maps* m, int32_t map, R x, R y, R phi, int32_t nb,
+               int32_t* hits, R* ranges) {
+  orc_lidar_dyn(c, m, map, 0, 0, x, y, phi, nb, hits, ranges);
 }
 
 /* --------------------------------------------------------- collision */
@@ -373,7 +399,13 @@ static obs_aux observe(const orc_config* c, const orc_maps* m, const orc_envs* e
   R rmax = (R)c->range_max;
   int32_t hits[64];
   R ranges[64];
-  orc_lidar(c, m, map, x, y, phi, nb, hits, ranges);
+  R discs[16];
+  int32_t nd = c->n_dyn;
+  for (int32_t o = 0; o < nd; ++o) {
+    discs[2 * o] = e->dyn[(4 * o + 0) * n + i];
+    discs[2 * o + 1] = e->dyn[(4 * o + 1) * n + i];
+  }
+  orc_lidar_dyn(c, m, map, discs, nd, x, y, phi, nb, hits, ranges);
   obs_aux aux;
   aux.min_range = rmax;
   for (int32_t j = 0; j < nb; ++j) aux.min_range = RMIN(aux.min_range, ranges[j]);
@@ -417,6 +449,112 @@ static obs_aux observe(const orc_config* c, const orc_maps* m, const orc_envs* e
   return aux;
 }
 
+/* ------------------------------------------------ dynamic obstacles */
+/* The paper leaves dynamic obstacles to future work (Sec. 5).  Reading used
+ * here: each env has n_dyn discs of radius r_o moving in straight lines at a
+ * constant speed, re-drawn at every episode start like the other randomised
+ * parameters.  Per step, after the robot's motion, each disc advances by
+ * dt * v (the env's control interval); a centre that leaves [r_o, W - r_o]
+ * (resp. H) is mirrored back into it and that velocity component changes
+ * sign; a centre that would enter an occupied cell stays where it was and
+ * the velocity is reversed.  The robot collides with a disc when the centres
+ * are within robot_radius + r_o (fma(dx,dx,dy*dy) <= (r + r_o)^2), and the
+ * LiDAR sees the discs (a march sample inside a disc is a hit). */
+
+/* Mirror coordinate v into [lo, hi]; flips *vel when it mirrors. */
+static R dyn_reflect(R v, R lo, R hi, R* vel) {
+  if (v < lo) {
+    v = lo + (lo - v);
+    *vel = -*vel;
+  } else if (v > hi) {
+    v = hi - (v - hi);
+    *vel = -*vel;
+  }
+  return RMIN(RMAX(v, lo), hi);
+}
+
+/* One step of obstacle o of env i with control interval dt. */
+static void dyn_move(const orc_config* c, const orc_maps* m, orc_envs* e, int32_t i, int32_t o, R dt) {
+  int32_t n = e->n_envs, map = e->env_map[i];
+  R* ox = &e->dyn[(4 * o + 0) * n + i];
+  R* oy = &e->dyn[(4 * o + 1) * n + i];
+  R* vx = &e->dyn[(4 * o + 2) * n + i];
+  R* vy = &e->dyn[(4 * o + 3) * n + i];
+  R r = (R)c->dyn_radius;
+  R hx = (R)m->w[map] - r, hy = (R)m->h[map] - r;
+  R nvx = *vx, nvy = *vy;
+  R nx = *ox + dt * nvx;
+  R ny = *oy + dt * nvy;
+  nx = dyn_reflect(nx, r, hx, &nvx);
+  ny = dyn_reflect(ny, r, hy, &nvy);
+  if (occupied(m, map, (int64_t)FLOOR(nx), (int64_t)FLOOR(ny))) {
+    *vx = -*vx;
+    *vy = -*vy;
+    return;
+  }
+  *ox = nx;
+  *oy = ny;
+  *vx = nvx;
+  *vy = nvy;
+}
+
+/* Whether the robot at (x, y) touches one of env i's discs. */
+static int dyn_collide(const orc_config* c, const orc_envs* e, int32_t i, R x, R y) {
+  int32_t n = e->n_envs;
+  R rr = (R)c->robot_radius + (R)c->dyn_radius;
+  R rr2 = rr * rr;
+  for (int32_t o = 0; o < c->n_dyn; ++o) {
+    R dx = e->dyn[(4 * o + 0) * n + i] - x;
+    R dy = e->dyn[(4 * o + 1) * n + i] - y;
+    if (FMA(dx, dx, dy * dy) <= rr2) return 1;
+  }
+  return 0;
+}
+
+/* Episode draws of obstacle o: up to 8 candidate centres, uniform over
+ * [r_o, W - r_o] x [r_o, H - r_o] from slots 16 + 16 o + a of the episode
+ * hash (x from the top 24 bits, y from bits 16..39); the first one on a free
+ * cell and farther than dyn_keepout from S and from G is taken (the last one
+ * when none is).  Heading uniform in [-pi, pi) and speed uniform in
+ * [speed_lo, speed_hi] from slot 16 + 16 o + 8. */
+static void dyn_draw(const orc_config* c, const orc_maps* m, orc_envs* e, int32_t i, uint32_t ep_id, int32_t o,
+                     R sx, R sy, R gx, R gy) {
+  int32_t n = e->n_envs, map = e->env_map[i];
+  R r = (R)c->dyn_radius;
+  R hx = (R)m->w[map] - r, hy = (R)m->h[map] - r;
+  R kp = (R)c->dyn_keepout;
+  R keep2 = kp * kp;
+  R px = r, py = r;
+  for (uint64_t a = 0; a < 8; ++a) {
+    uint64_t hp = orc_rng(c->seed, STREAM_RESET, (uint64_t)i, ep_id, 16u + 16u * (uint64_t)o + a);
+    px = r + u24(hp) * (hx - r);
+    py = r + u24b(hp) * (hy - r);
+    R dsx = px - sx, dsy = py - sy, dgx = px - gx, dgy = py - gy;
+    int ok = !occupied(m, map, (int64_t)FLOOR(px), (int64_t)FLOOR(py)) && FMA(dsx, dsx, dsy * dsy) > keep2 &&
+             FMA(dgx, dgx, dgy * dgy) > keep2;
+    if (ok) break;
+  }
+  uint64_t hv = orc_rng(c->seed, STREAM_RESET, (uint64_t)i, ep_id, 16u + 16u * (uint64_t)o + 8u);
+  R pi = PI_R;
+  R th = -pi + u24(hv) * (pi - (-pi));
+  R lo = (R)c->dyn_speed_lo, hi = (R)c->dyn_speed_hi;
+  R sp = lo + u24b(hv) * (hi - lo);
+  R sn, cs;
+  sincos_r(th, &sn, &cs);
+  e->dyn[(4 * o + 0) * n + i] = px;
+  e->dyn[(4 * o + 1) * n + i] = py;
+  e->dyn[(4 * o + 2) * n + i] = sp * cs;
+  e->dyn[(4 * o + 3) * n + i] = sp * sn;
+}
+
+/* One motion step of all of env i's obstacles (exported for the pins). */
+void orc_dyn_advance(const orc_config* c, const orc_maps* m, orc_envs* e, int32_t i, R dt) {
+  for (int32_t o = 0; o < c->n_dyn; ++o) dyn_move(c, m, e, i, o, dt);
+}
+int32_t orc_dyn_collide(const orc_config* c, const orc_envs* e, int32_t i, R x, R y) {
+  return dyn_collide(c, e, i, x, y);
+}
+
 static R lerp_r(double lo, double hi, R u) {
   R l = (R)lo, hh = (R)hi;
   return l + u * (hh - l);
@@ -450,6 +588,7 @@ void orc_reset_env(const orc_config* c, const orc_maps* m, orc_envs* e, int32_t 
   e->u[U_EPID * n + i] = ep_id;
   e->b[B_Q0 * n + i] = NONE_ACTION;
   e->b[B_Q1 * n + i] = NONE_ACTION;
+  for (int32_t o = 0; o < c->n_dyn; ++o) dyn_draw(c, m, e, i, ep_id, o, L.sx, L.sy, L.gx, L.gy);
   observe(c, m, e, i, obs);
 }
 
@@ -459,8 +598,9 @@ void orc_reset(const orc_config* c, const orc_maps* m, orc_envs* e, R* obs) {
 }
 
 /* One step of env i with action a.  Order: delay queue, target velocity,
- * Eq. 5, Eq. 6 (old heading), heading wrap, collision, LiDAR + noise,
- * arrival / truncation, reward Eq. 11, observation, AutoReset. */
+ * Eq. 5, Eq. 6 (old heading), heading wrap, obstacle motion, collision,
+ * LiDAR + noise, arrival / truncation, reward Eq. 11, observation,
+ * AutoReset. */
 static void step_env(const orc_config* c, const orc_maps* m, orc_envs* e, int32_t i, uint8_t a, R* obs,
                      R* rew, uint8_t* done, R* term_obs, uint32_t* status) {
   int32_t n = e->n_envs;
@@ -507,7 +647,10 @@ static void step_env(const orc_config* c, const orc_maps* m, orc_envs* e, int32_
   uint32_t ep_step = e->u[U_STEP * n + i] + 1u;
   e->u[U_STEP * n + i] = ep_step;
 
-  int32_t collide = orc_collide(c, m, map, x, y);
+  /* obstacles move with the env's control interval, then the collision
+   * test sees the map and the moved discs */
+  for (int32_t o = 0; o < c->n_dyn; ++o) dyn_move(c, m, e, i, o, dt);
+  int32_t collide = orc_collide(c, m, map, x, y) || dyn_collide(c, e, i, x, y);
   obs_aux aux = observe(c, m, e, i, obs);
   R d1sq = FMA(aux.ddx, aux.ddx, aux.ddy * aux.ddy);
   R rg = (R)c->goal_radius;
