@@ -46,8 +46,8 @@ def parse():
     ap.add_argument("--rollout-steps", type=int, default=None, help="vectorized steps per bench step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
-    ap.add_argument("--extras", default="qnet,td,step,uneven,full",
-                    help="comma list of secondary measurements: qnet, td, step, uneven, full")
+    ap.add_argument("--extras", default="qnet,td,step,uneven,full,dyn",
+                    help="comma list of secondary measurements: qnet, td, step, uneven, full, dyn")
     ap.add_argument("--launch", default=None,
                     help="fixed rollout launch 'kernel:key=val,...' e.g. 'pipe:warps_per_block=8,obs_warps=7,order=map'"
                          " (skips the autotuner)")
@@ -405,6 +405,8 @@ def _run_extras_tail(out, flush, which):
             out["uneven_batching"] = run_uneven(flush)
         if "full" in which:
             out["full_learned_loop"] = run_full_loop(flush)
+        if "dyn" in which:
+            out["moving_obstacles"] = run_dyn(flush)
         return out
     # single-step kernel with state in HBM, 65,536 envs over the 32 randomised maps
     w2 = workload("dr1024", n_envs=65536)
@@ -427,6 +429,61 @@ def _run_extras_tail(out, flush, which):
         out["uneven_batching"] = run_uneven(flush)
     if "full" in which:
         out["full_learned_loop"] = run_full_loop(flush)
+    if "dyn" in which:
+        out["moving_obstacles"] = run_dyn(flush)
+    return out
+
+
+def run_dyn(flush):
+    """Moving obstacles (four discs per env) on the 1,024-env domain-randomised
+    maps: the autotuned rollout (one warp per env, the only launches that take
+    obstacles) of 1,000 steps and the single-step kernel at 65,536 envs, each
+    beside the same launch without obstacles."""
+    import torch
+
+    from paper_2305_04180_gb300 import Sim
+    from paper_2305_04180_gb300.autotune import autotune_rollout
+    from workloads import workload
+
+    out = {}
+    K = 1000
+    rows = {}
+    tuned = None
+    for name in ("dyn1024", "dr1024"):
+        w = workload(name)
+        sim = Sim(w.params, w.maps(), w.env_map)
+        sim.reset()
+        if tuned is None:
+            tuned = autotune_rollout(sim, K=64, reps=2, cache_path=None)["config"]
+        else:
+            sim.set_launch(**tuned)
+        rew = torch.empty((K, sim.n), device="cuda")
+        done = torch.empty((K, sim.n), dtype=torch.uint8, device="cuda")
+        f = lambda: sim.rollout(K, rew_seq=rew, done_seq=done)  # noqa: E731
+        for _ in range(2):
+            f()
+        ms = _time_cuda(f, 5, flush)
+        rows[name] = {"ms_per_rollout": ms, "value": sim.n * K / (ms / 1e3),
+                      "collisions_per_1k_env_steps": float((done & 1).sum().item()) / (sim.n * K) * 1e3}
+        del sim, rew, done
+    out["rollout"] = {"workload": workload("dyn1024").name, "n_envs": 1024, "steps_per_call": K, "unit": UNIT,
+                      "launch": launch_label(tuned), "with_obstacles": rows["dyn1024"],
+                      "without_obstacles_same_launch": rows["dr1024"]}
+    steps = {}
+    for name in ("dyn1024", "dr1024"):
+        w = workload(name, n_envs=65536)
+        sim = Sim(w.params, w.maps(), w.env_map)
+        obs = sim.reset()
+        act = torch.randint(0, 5, (sim.n,), dtype=torch.uint8, device="cuda")
+        rew = torch.empty(sim.n, device="cuda")
+        done = torch.empty(sim.n, dtype=torch.uint8, device="cuda")
+        fs = lambda: sim.step(act, obs=obs, rew=rew, done=done)  # noqa: E731
+        for _ in range(3):
+            fs()
+        ms = _time_cuda(fs, 20, flush)
+        steps[name] = {"us_per_launch": ms * 1e3, "value": sim.n / (ms / 1e3)}
+        del sim, obs
+    out["sim_step_65536"] = {"unit": UNIT, "with_obstacles": steps["dyn1024"], "without_obstacles": steps["dr1024"]}
     return out
 
 

@@ -90,6 +90,26 @@ typedef struct sg_sim_config {
   float action_v[8];         /* target linear velocity of each action */
   float action_w[8];         /* target angular velocity of each action */
   uint64_t seed;             /* counter-RNG key of every random draw */
+  /*
+   * Dynamic obstacles (optional; the paper's Sec. 5 names them as the
+   * simulator's next capability, without a model).  n_dyn discs of radius
+   * dyn_radius per env, re-drawn at every episode start: centre uniform over
+   * [r, W - r] x [r, H - r] on a free cell farther than dyn_keepout from S and
+   * G (first of up to 8 candidates), heading uniform, speed uniform in
+   * [dyn_speed_lo, dyn_speed_hi] cells/s.  Each step, after the robot's
+   * motion, a disc moves by dt * v; a centre leaving [r, W - r] (resp. H) is
+   * mirrored back and that velocity component flips; a centre that would
+   * enter an occupied cell stays and the velocity reverses.  The robot
+   * collides when the centres are within robot_radius + dyn_radius; a LiDAR
+   * sample inside a disc is a hit.  n_dyn = 0 (default): no obstacles, the
+   * other fields are ignored.  Requires 2 r < every map side.  The SPLIT and
+   * PIPE rollout kernels do not support obstacles (sg_sim_set_launch rejects
+   * them).
+   */
+  int32_t n_dyn;             /* 0..8 */
+  float dyn_radius;          /* > 0 when n_dyn > 0, cells */
+  float dyn_speed_lo, dyn_speed_hi; /* 0 <= lo <= hi, cells / s */
+  float dyn_keepout;         /* >= 0, cells */
 } sg_sim_config;
 
 /* Read-only facts about a simulator (sg_sim_info). */
@@ -241,6 +261,8 @@ int sg_sim_get_launch(sg_sim_t sim, sg_launch* cfg);
  *   uint32_t [3][N]  ep_step, ep_id, t (steps since reset)
  *   uint32_t [1][N]  fifo: last action | previous action << 8 | delay << 16
  *                    (255 = no action yet)
+ *   float    [4 n_dyn][N]  dynamic obstacles (only when n_dyn > 0): obstacle
+ *                    o at rows 4o..4o+3 = centre x, y, velocity vx, vy
  * *bytes: in = size of host_buf, out = bytes used (info.state_bytes).
  * Synchronous.
  */

@@ -44,6 +44,8 @@ class sg_sim_config(C.Structure):
         ("v_nom", C.c_float), ("w_nom", C.c_float),
         ("action_v", C.c_float * 8), ("action_w", C.c_float * 8),
         ("seed", C.c_uint64),
+        ("n_dyn", C.c_int32), ("dyn_radius", C.c_float), ("dyn_speed_lo", C.c_float),
+        ("dyn_speed_hi", C.c_float), ("dyn_keepout", C.c_float),
     ]
 
 

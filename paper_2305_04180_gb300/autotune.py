@@ -48,6 +48,8 @@ def signature(sim, K: int) -> str:
     h.update(np.asarray(sim.env_beams if sim.env_beams is not None else [], np.int32).tobytes())
     h.update(np.asarray(sim.map_shapes, np.int32).tobytes())
     h.update(np.asarray(sim.env_map_host, np.int32).tobytes())
+    if getattr(sim, "n_dyn", 0):
+        h.update(f"dyn{sim.n_dyn}".encode())
     return h.hexdigest()
 
 
@@ -93,6 +95,9 @@ def autotune_rollout(sim, K: int = 32, reps: int = 3, cache_path: str | None = D
     `timer(sim, cfg, K, reps, state) -> ms` may replace the CUDA-event timer.
     """
     candidates = list(candidates or CANDIDATES)
+    if getattr(sim, "n_dyn", 0):
+        # moving obstacles need the LiDAR in the pose chain: one warp per env
+        candidates = [c for c in candidates if c["kernel"] in ("grid", "queue")]
     key = signature(sim, K)
     cache = load_cache(cache_path) if cache_path else {}
     if key in cache:

@@ -52,6 +52,13 @@ struct DevCfg {
   float v_nom, w_nom;
   float av[8], aw[8];
   unsigned long long seed;
+  // dynamic obstacles (n_dyn = 0: none)
+  int n_dyn;
+  float dyn_r, dyn_r2;  // disc radius r_o and r_o^2
+  float dyn_rr2;        // (robot_r + r_o)^2
+  float dyn_keep2;      // squared keep-out distance from S and G at the draws
+  float dyn_vlo, dyn_vhi;
+  float dyn_re;         // radius of the scan's candidate band, r_o + delta + 0.25
 };
 
 // Device buffers of a simulator (structure of arrays, stride n).
@@ -64,6 +71,7 @@ struct SimPtrs {
   const int* env_map;
   const int* env_beams;   // nullptr: every env uses B beams
   uint32_t* status;       // SG_DEV_* bits
+  float* dyn;             // [4 n_dyn][n]: obstacle o at rows 4o..4o+3 (x y vx vy); null when n_dyn = 0
   int n;
   int pad;
 };
@@ -326,6 +334,171 @@ __device__ __forceinline__ bool collide_warp(const DevCfg& c, const MapDesc& m, 
   return collide_rows_warp(c, m, rows, x, y, lane);
 }
 
+// ------------------------------------------------ dynamic obstacles
+// Optional moving discs (the extension Sec. 5 names as the simulator's next
+// capability).  Each env has n_dyn discs of radius r_o moving in straight
+// lines: per step, after the robot's motion, a disc advances by dt * v (the
+// env's control interval); a centre leaving [r_o, W - r_o] (resp. H) is
+// mirrored back and that velocity component flips; a centre that would enter
+// an occupied cell stays put and the velocity reverses.  The robot collides
+// with a disc when the centres are within robot_r + r_o, and a LiDAR sample
+// inside a disc is a hit.  Discs are re-drawn at every episode start.
+constexpr int kMaxDyn = 8;
+
+struct Obst {
+  float x, y, vx, vy;
+};
+// Disc centres of one env, the same in every lane of the warp (or in shared
+// memory for the lane-per-env step).
+struct Discs {
+  float x[kMaxDyn], y[kMaxDyn];
+};
+
+__device__ __forceinline__ Obst load_obst(const SimPtrs& p, int o, int i) {
+  const int n = p.n;
+  Obst b;
+  b.x = p.dyn[(4 * o + 0) * n + i];
+  b.y = p.dyn[(4 * o + 1) * n + i];
+  b.vx = p.dyn[(4 * o + 2) * n + i];
+  b.vy = p.dyn[(4 * o + 3) * n + i];
+  return b;
+}
+
+__device__ __forceinline__ void store_obst(const SimPtrs& p, int o, int i, const Obst& b) {
+  const int n = p.n;
+  p.dyn[(4 * o + 0) * n + i] = b.x;
+  p.dyn[(4 * o + 1) * n + i] = b.y;
+  p.dyn[(4 * o + 2) * n + i] = b.vx;
+  p.dyn[(4 * o + 3) * n + i] = b.vy;
+}
+
+// Mirror coordinate v into [lo, hi]; flips vel when it mirrors.
+__device__ __forceinline__ float dyn_reflect(float v, float lo, float hi, float& vel) {
+  if (v < lo) {
+    v = lo + (lo - v);
+    vel = -vel;
+  } else if (v > hi) {
+    v = hi - (v - hi);
+    vel = -vel;
+  }
+  return fminf(fmaxf(v, lo), hi);
+}
+
+// One motion step of a disc of map m (skip map clr: 0 exactly on occupied
+// cells) with control interval dt.
+__device__ __forceinline__ void dyn_move(const DevCfg& c, const MapDesc& m, const uint8_t* __restrict__ clr, float dt,
+                                         Obst& b) {
+  const float r = c.dyn_r;
+  const float hx = (float)m.w - r, hy = (float)m.h - r;
+  float vx = b.vx, vy = b.vy;
+  float nx = b.x + dt * vx;
+  float ny = b.y + dt * vy;
+  nx = dyn_reflect(nx, r, hx, vx);
+  ny = dyn_reflect(ny, r, hy, vy);
+  // nx in [r, W - r] with r > 0: the cell is inside the map
+  if (__ldg(clr + __float2int_rd(ny) * m.clr_ld + __float2int_rd(nx)) == 0) {
+    b.vx = -b.vx;
+    b.vy = -b.vy;
+    return;
+  }
+  b.x = nx;
+  b.y = ny;
+  b.vx = vx;
+  b.vy = vy;
+}
+
+// Whether the robot centre (x, y) is within robot_r + r_o of the disc.
+__device__ __forceinline__ bool dyn_touch(const DevCfg& c, const Obst& b, float x, float y) {
+  const float dx = b.x - x, dy = b.y - y;
+  return fmaf(dx, dx, dy * dy) <= c.dyn_rr2;
+}
+
+// Episode draws of disc o from the episode hash prefix pre: up to eight
+// candidate centres uniform over [r_o, W - r_o] x [r_o, H - r_o] (slots
+// 16 + 16 o + a; x from the top 24 bits, y from bits 16..39), the first on a
+// free cell and farther than the keep-out from S and G taken (else the last);
+// heading uniform in [-pi, pi) and speed uniform in [v_lo, v_hi] from slot
+// 16 + 16 o + 8.
+__device__ __forceinline__ Obst dyn_draw(const DevCfg& c, const MapDesc& m, const uint8_t* __restrict__ clr,
+                                         const Layout& L, uint64_t pre, int o) {
+  const float r = c.dyn_r;
+  const float hx = (float)m.w - r, hy = (float)m.h - r;
+  float px = r, py = r;
+  for (int a = 0; a < 8; ++a) {
+    const uint64_t hp = sm_at(pre, (uint64_t)(16 + 16 * o + a));
+    px = r + u24_hi(hp) * (hx - r);
+    py = r + u24_mid(hp) * (hy - r);
+    const float dsx = px - L.sx, dsy = py - L.sy, dgx = px - L.gx, dgy = py - L.gy;
+    const bool ok = __ldg(clr + __float2int_rd(py) * m.clr_ld + __float2int_rd(px)) != 0 &&
+                    fmaf(dsx, dsx, dsy * dsy) > c.dyn_keep2 && fmaf(dgx, dgx, dgy * dgy) > c.dyn_keep2;
+    if (ok) break;
+  }
+  const uint64_t hv = sm_at(pre, (uint64_t)(16 + 16 * o + 8));
+  const float th = -kPi + u24_hi(hv) * (kPi - (-kPi));
+  const float sp = c.dyn_vlo + u24_mid(hv) * (c.dyn_vhi - c.dyn_vlo);
+  float sn, cs;
+  f_sincos(th, sn, cs);
+  Obst b;
+  b.x = px;
+  b.y = py;
+  b.vx = sp * cs;
+  b.vy = sp * sn;
+  return b;
+}
+
+// The disc centres of the warp's env, held by lanes 0 .. n_dyn - 1, in every
+// lane (n_dyn is warp-uniform).
+__device__ __forceinline__ void gather_discs(const DevCfg& c, const Obst& b, Discs& d) {
+#pragma unroll
+  for (int o = 0; o < kMaxDyn; ++o)
+    if (o < c.n_dyn) {
+      d.x[o] = __shfl_sync(kFull, b.x, o);
+      d.y[o] = __shfl_sync(kFull, b.y, o);
+    }
+}
+
+// First sample k in [1, hmax) of the ray (x, y) + k delta (ux, uy) inside the
+// disc centred at (ox, oy): fma(ex, ex, ey*ey) <= r_o^2 with (ex, ey) the
+// sample minus the centre (the march's sample expression); hmax when none.
+// Only samples near the ray-circle intersection are tested: every sample the
+// rounded test accepts lies within r_o + 0.01 cells of the centre (maps up to
+// 16384 cells), so it falls in the band of half-width sqrt(re^2 - d^2) around
+// the projection tc of the centre (d: the centre's distance from the ray,
+// re = r_o + delta + 0.25), widened by one sample on each side.
+template <bool kUnitStep>
+__device__ __forceinline__ int disc_first(const DevCfg& c, float x, float y, float ux, float uy, float ox, float oy,
+                                          int hmax) {
+  const float dx = ox - x, dy = oy - y;
+  const float tc = dx * ux + dy * uy;
+  const float dp = dx * uy - dy * ux;
+  const float re = c.dyn_re;
+  if (!(fabsf(dp) <= re)) return hmax;
+  const float half = sqrtf(fmaxf(re * re - dp * dp, 0.0f));
+  const float k0f = floorf((tc - half) / c.delta) - 1.0f;
+  const float k1f = ceilf((tc + half) / c.delta) + 1.0f;
+  const float top = (float)(hmax - 1);
+  if (!(k1f >= 1.0f) || !(k0f <= top)) return hmax;
+  int k = (int)fmaxf(k0f, 1.0f);
+  const int k1 = (int)fminf(k1f, top);
+  for (; k <= k1; ++k) {
+    const float t = kUnitStep ? (float)k : (float)k * c.delta;
+    const float ex = fmaf(t, ux, x) - ox;
+    const float ey = fmaf(t, uy, y) - oy;
+    if (fmaf(ex, ex, ey * ey) <= c.dyn_r2) return k;
+  }
+  return hmax;
+}
+
+// The first hit of the ray among the map hit h and the env's discs.
+template <bool kUnitStep>
+__device__ __forceinline__ int discs_first(const DevCfg& c, const Discs& d, float x, float y, float ux, float uy,
+                                           int h) {
+#pragma unroll
+  for (int o = 0; o < kMaxDyn; ++o)
+    if (o < c.n_dyn) h = disc_first<kUnitStep>(c, x, y, ux, uy, d.x[o], d.y[o], h);
+  return h;
+}
+
 // ------------------------------------------------- per-env constants
 // Quantities that do not change between the steps of one launch.
 struct EnvConst {
@@ -399,15 +572,19 @@ __device__ __forceinline__ Noise noise_for(const EnvConst& k, float sigma, uint3
 }
 
 // Normalised range of the beam at heading offset `off` from the pose (x, y,
-// phi), with noise sigma * nz; mn takes the minimum noise-free range.
+// phi), with noise sigma * nz; mn takes the minimum noise-free range.  With
+// kDyn the discs d are in the way too.
+template <bool kDyn = false>
 __device__ __forceinline__ float beam_at(const DevCfg& c, const EnvConst& k, float x, float y, float phi,
-                                         float sigma, float off, float nz, float& mn) {
+                                         float sigma, float off, float nz, float& mn, const Discs* d = nullptr) {
   const float beta = phi + off;
   float sn, cs;
   f_sincos(beta, sn, cs);
-  const int h = c.delta == 1.0f
-                    ? march<true>(k.clr, k.m.w, k.m.h, k.m.clr_ld, x, y, -cs, -sn, c.delta, c.kmax, 1)
-                    : march<false>(k.clr, k.m.w, k.m.h, k.m.clr_ld, x, y, -cs, -sn, c.delta, c.kmax, c.skip_ok);
+  int h = c.delta == 1.0f
+              ? march<true>(k.clr, k.m.w, k.m.h, k.m.clr_ld, x, y, -cs, -sn, c.delta, c.kmax, 1)
+              : march<false>(k.clr, k.m.w, k.m.h, k.m.clr_ld, x, y, -cs, -sn, c.delta, c.kmax, c.skip_ok);
+  if (kDyn)
+    h = c.delta == 1.0f ? discs_first<true>(c, *d, x, y, -cs, -sn, h) : discs_first<false>(c, *d, x, y, -cs, -sn, h);
   float r = fminf((float)h * c.delta, c.range_max);
   mn = fminf(mn, r);
   if (sigma > 0.0f) {
@@ -418,9 +595,10 @@ __device__ __forceinline__ float beam_at(const DevCfg& c, const EnvConst& k, flo
   return r / c.range_max;
 }
 
+template <bool kDyn = false>
 __device__ __forceinline__ float beam_range(const DevCfg& c, const EnvConst& k, const Env& s, float off, float nz,
-                                            float& mn) {
-  return beam_at(c, k, s.x, s.y, s.phi, s.sigma, off, nz, mn);
+                                            float& mn, const Discs* d = nullptr) {
+  return beam_at<kDyn>(c, k, s.x, s.y, s.phi, s.sigma, off, nz, mn, d);
 }
 
 // Goal in the robot frame (forward (-cos phi, -sin phi), left = forward
@@ -448,15 +626,16 @@ __device__ __forceinline__ float obs_extra(const DevCfg& c, const Layout& L, con
   return num / den;
 }
 
+template <bool kDyn = false>
 __device__ __forceinline__ void observe(const DevCfg& c, const EnvConst& k, const Env& s, const Noise& z, int lane,
-                                        ObsRegs& o, Aux& aux) {
+                                        ObsRegs& o, Aux& aux, const Discs* d = nullptr) {
   // independent of the scan, so issued first; lanes 0..4 hold the extras
   const GoalFrame g = goal_frame(k.L, s);
   const float ddx = g.ddx, ddy = g.ddy, alpha = g.alpha;
   o.ex = obs_extra(c, k.L, s, g, lane);
   float mn = c.range_max;
-  o.b0 = lane < k.nb ? beam_range(c, k, s, k.off0, z.n0, mn) : 1.0f;
-  o.b1 = lane + 32 < k.nb ? beam_range(c, k, s, k.off1, z.n1, mn) : 1.0f;
+  o.b0 = lane < k.nb ? beam_range<kDyn>(c, k, s, k.off0, z.n0, mn, d) : 1.0f;
+  o.b1 = lane + 32 < k.nb ? beam_range<kDyn>(c, k, s, k.off1, z.n1, mn, d) : 1.0f;
   // ranges are >= 0, so their bit patterns order like the values
   aux.min_range = __uint_as_float(__reduce_min_sync(kFull, __float_as_uint(mn)));
   aux.alpha = alpha;
@@ -503,14 +682,21 @@ __device__ __forceinline__ void apply_draws(const DevCfg& c, const Layout& L, En
 
 // New episode ep_id (Sec. 3.2.4): every randomised parameter re-drawn from
 // the counter RNG keyed by (seed, env, ep_id); start near S.  Lanes 0..7
-// draw one slot each.
-__device__ __forceinline__ void reset_env(const DevCfg& c, const EnvConst& k, Env& s, uint32_t ep_id, int lane) {
+// draw one slot each.  With kDyn lane o < n_dyn draws disc o into *b and
+// every lane receives the new centres in *d.
+template <bool kDyn = false>
+__device__ __forceinline__ void reset_env(const DevCfg& c, const EnvConst& k, Env& s, uint32_t ep_id, int lane,
+                                          Obst* b = nullptr, Discs* d = nullptr) {
   const uint64_t pre = sm_at(k.rkey, (uint64_t)ep_id);
   const uint64_t mine = sm_at(pre, (uint64_t)(lane & 7));
   const uint64_t h0 = shfl_u64(mine, 0), h1 = shfl_u64(mine, 1), h2 = shfl_u64(mine, 2);
   const uint64_t h3 = shfl_u64(mine, 3), h4 = shfl_u64(mine, 4), h5 = shfl_u64(mine, 5);
   const uint64_t h6 = shfl_u64(mine, 6), h7 = shfl_u64(mine, 7);
   apply_draws(c, k.L, s, ep_id, h0, h1, h2, h3, h4, h5, h6, h7);
+  if (kDyn) {
+    if (lane < c.n_dyn) *b = dyn_draw(c, k.m, k.clr, k.L, pre, lane);
+    gather_discs(c, *b, *d);
+  }
 }
 
 // The same draws by one lane alone (the lane holds its own env): slot j of
@@ -593,16 +779,30 @@ __device__ __forceinline__ float shaped_reward(const DevCfg& c, const EnvConst& 
 
 // One full step of one env by its warp.  `term_row` (may be null) receives
 // the pre-reset observation of a done env; `o` returns this lane's share of
-// the observation after the step (after the reset when done).
+// the observation after the step (after the reset when done).  With kDyn,
+// lane o < n_dyn holds disc o in *b and every lane the centres in *d (both
+// updated: motion, and the new episode's draws when done).
+template <bool kDyn = false>
 __device__ __forceinline__ StepOut env_step(const DevCfg& c, const SimPtrs& p, const EnvConst& k, Env& s,
-                                            uint32_t a, int lane, ObsRegs& o, float* term_row) {
+                                            uint32_t a, int lane, ObsRegs& o, float* term_row, Obst* b = nullptr,
+                                            Discs* d = nullptr) {
   // noise of the observation this step produces, drawn before the scan
   const Noise z = noise_for(k, s.sigma, s.ep_id, s.ep_step + 1u, lane);
   const bool bad = kinematics(c, s, a);
   if (bad && lane == 0) atomicOr(p.status, 1u);
-  const bool col = collide_warp(c, k.m, k.rows, k.clr, s.x, s.y, lane);
+  bool col = collide_warp(c, k.m, k.rows, k.clr, s.x, s.y, lane);
+  if (kDyn) {
+    // the discs move with the env's control interval before the tests
+    bool touch = false;
+    if (lane < c.n_dyn) {
+      dyn_move(c, k.m, k.clr, s.dt, *b);
+      touch = dyn_touch(c, *b, s.x, s.y);
+    }
+    col = __any_sync(kFull, touch) || col;
+    gather_discs(c, *b, *d);
+  }
   Aux aux;
-  observe(c, k, s, z, lane, o, aux);
+  observe<kDyn>(c, k, s, z, lane, o, aux, d);
   const float d1sq = fmaf(aux.ddx, aux.ddx, aux.ddy * aux.ddy);
   const bool arrive = d1sq <= c.goal_r * c.goal_r;
   const bool trunc = s.ep_step >= (uint32_t)c.t_max;
@@ -617,9 +817,9 @@ __device__ __forceinline__ StepOut env_step(const DevCfg& c, const SimPtrs& p, c
   if (out.done) {
     // AutoReset (Sec. 3.2.5): keep s' for the caller, then a new episode
     if (term_row) write_obs(term_row, o, c.B, lane);
-    reset_env(c, k, s, s.ep_id + 1u, lane);
+    reset_env<kDyn>(c, k, s, s.ep_id + 1u, lane, b, d);
     const Noise z0 = noise_for(k, s.sigma, s.ep_id, 0u, lane);
-    observe(c, k, s, z0, lane, o, aux);
+    observe<kDyn>(c, k, s, z0, lane, o, aux, d);
   }
   return out;
 }
@@ -692,9 +892,10 @@ static_assert(sizeof(StepScanRec) == 128, "step scan record is eight 16-byte wor
 
 // Scan of one pose by the warp for an env of map m with nb beams: this
 // lane's normalised ranges into b0 / b1; returns the minimum noise-free range.
+template <bool kDyn = false>
 __device__ __forceinline__ float scan_env(const DevCfg& c, const SimPtrs& p, const MapDesc& m, int nb, float stepb,
                                           float x, float y, float phi, float sigma, uint64_t nk, int lane,
-                                          float& b0, float& b1) {
+                                          float& b0, float& b1, const Discs* d = nullptr) {
   EnvConst k;
   k.m = m;
   k.clr = p.clr + m.clr_off;
@@ -707,8 +908,8 @@ __device__ __forceinline__ float scan_env(const DevCfg& c, const SimPtrs& p, con
     if (nb > 32) n1 = box_muller(sm_at(nk, (uint64_t)(lane + 32)));
   }
   float mn = c.range_max;
-  b0 = lane < nb ? beam_at(c, k, x, y, phi, sigma, off0, n0, mn) : 1.0f;
-  b1 = lane + 32 < nb ? beam_at(c, k, x, y, phi, sigma, off1, n1, mn) : 1.0f;
+  b0 = lane < nb ? beam_at<kDyn>(c, k, x, y, phi, sigma, off0, n0, mn, d) : 1.0f;
+  b1 = lane + 32 < nb ? beam_at<kDyn>(c, k, x, y, phi, sigma, off1, n1, mn, d) : 1.0f;
   return __uint_as_float(__reduce_min_sync(kFull, __float_as_uint(mn)));
 }
 
@@ -726,9 +927,14 @@ __device__ __forceinline__ void write_row(float* row, float b0, float b1, const 
 // Eq. 11 that does not need a scan, into the env's record r (scan A: the
 // post-motion state; scan B: the reset state of a done env).  s: the env's
 // state in, the state after the step out.  Lanes with live = false take part
-// in the warp-wide collision tests only.  Returns the done flags.
+// in the warp-wide collision tests only.  With kDyn the env's discs move
+// (and collide) here too; their centres for scan A go to da, those of the
+// reset state to db, and the discs' new state to global memory.  Returns the
+// done flags.
+template <bool kDyn = false>
 __device__ __forceinline__ uint32_t lane_step(const DevCfg& c, const SimPtrs& p, int i, bool live, Env& s,
-                                              uint32_t a, StepScanRec& r, int lane) {
+                                              uint32_t a, StepScanRec& r, int lane, Discs* da = nullptr,
+                                              Discs* db = nullptr) {
   MapDesc m;
   Layout L;
   int mid = 0, nb = c.B;
@@ -749,6 +955,17 @@ __device__ __forceinline__ uint32_t lane_step(const DevCfg& c, const SimPtrs& p,
     const float ddx = L.gx - s.x, ddy = L.gy - s.y;
     if (fmaf(ddx, ddx, ddy * ddy) <= c.goal_r * c.goal_r) d |= 2u;
     if (s.ep_step >= (uint32_t)c.t_max) d |= 4u;
+    if (kDyn) {
+      const uint8_t* clr = p.clr + m.clr_off;
+      for (int o = 0; o < c.n_dyn; ++o) {
+        Obst b = load_obst(p, o, i);
+        dyn_move(c, m, clr, s.dt, b);
+        if (dyn_touch(c, b, s.x, s.y)) d |= 1u;
+        da->x[o] = b.x;
+        da->y[o] = b.y;
+        store_obst(p, o, i, b);
+      }
+    }
   }
   // collision tests that need the bit rows, one env at a time
   unsigned sm = __ballot_sync(kFull, slow);
@@ -776,6 +993,15 @@ __device__ __forceinline__ uint32_t lane_step(const DevCfg& c, const SimPtrs& p,
       // AutoReset (Sec. 3.2.5): a new episode, observed at its step 0
       const uint64_t rkey = sm_at(sm_at(c.seed, kStreamReset), (uint64_t)i);
       reset_env_lane(c, L, rkey, s, s.ep_id + 1u);
+      if (kDyn) {
+        const uint64_t pre = sm_at(rkey, (uint64_t)s.ep_id);
+        for (int o = 0; o < c.n_dyn; ++o) {
+          const Obst b = dyn_draw(c, m, p.clr + m.clr_off, L, pre, o);
+          db->x[o] = b.x;
+          db->y[o] = b.y;
+          store_obst(p, o, i, b);
+        }
+      }
       const GoalFrame gb = goal_frame(L, s);
       const uint64_t nkb = sm_at(nkey, ((uint64_t)s.ep_id << 32) | s.ep_step);
       r.bx = s.x, r.by = s.y, r.bphi = s.phi, r.bsigma = s.sigma;

@@ -23,6 +23,7 @@ struct sg_sim {
   int* env_beams_dev = nullptr;
   float* fstate = nullptr;     // [9][n]
   uint32_t* ustate = nullptr;  // [4][n]
+  float* dyn = nullptr;        // [4 n_dyn][n] dynamic obstacles (null when n_dyn = 0)
   uint32_t* status_dev = nullptr;
   // launch configuration of the random rollout (sg_sim_set_launch)
   sg_launch launch = {SG_ROLLOUT_GRID, 4, 1, 0, 0, 0, {0, 0}};

@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_qnet_forward(const uint8_t* __r
 // replay ring.  One warp per env; 16 envs per group, MT groups per CTA
 // sharing the weight image.  The groups synchronise only among themselves
 // (named barriers), so one group's env step overlaps the other's network.
-template <int MT>
+template <int MT, bool kDyn>
 __global__ void __launch_bounds__(512 * MT, 1)
     k_rollout_q(const __grid_constant__ DevCfg c, SimPtrs p, const uint8_t* __restrict__ img, ImgLayout L, int K,
                 const float* __restrict__ eps, ReplayDev rp, int use_replay, const int* __restrict__ order,
@@ -430,12 +430,19 @@ __global__ void __launch_bounds__(512 * MT, 1)
   o.b0 = o.b1 = o.ex = 0.0f;
   float eps_i = 0.0f;
   uint64_t akey = 0;
+  // dynamic obstacles: lane o holds disc o, every lane the centres
+  Obst b = {0.0f, 0.0f, 0.0f, 0.0f};
+  Discs dsc;
   if (live) {
     k = env_const(c, p, env, lane);
     s = load_env(p, env);
+    if (kDyn) {
+      if (lane < c.n_dyn) b = load_obst(p, lane, env);
+      gather_discs(c, b, dsc);
+    }
     const Noise z = noise_for(k, s.sigma, s.ep_id, s.ep_step, lane);
     Aux aux;
-    observe(c, k, s, z, lane, o, aux);  // the current observation, from the state
+    observe<kDyn>(c, k, s, z, lane, o, aux, &dsc);  // the current observation, from the state
     eps_i = eps[env];
     akey = sm_at(sm_at(c.seed, kStreamAction), (uint64_t)env);
   }
@@ -466,7 +473,7 @@ __global__ void __launch_bounds__(512 * MT, 1)
       s2row = rp.s2 + e * rp.obs_dim;
       write_obs(srow, o, c.B, lane);
     }
-    const StepOut r = env_step(c, p, k, s, a, lane, o, s2row);
+    const StepOut r = env_step<kDyn>(c, p, k, s, a, lane, o, s2row, &b, &dsc);
     if (use_replay) {
       if (!r.done) write_obs(s2row, o, c.B, lane);
       if (lane == 0) {
@@ -485,6 +492,7 @@ __global__ void __launch_bounds__(512 * MT, 1)
   if (live) {
     if (obs_out) write_obs(obs_out + (long long)env * c.obs_dim, o, c.B, lane);
     if (lane == 0) store_env(p, env, s);
+    if (kDyn && lane < c.n_dyn) store_obst(p, lane, env, b);
   }
 }
 
@@ -885,8 +893,10 @@ extern "C" int sg_qnet_create(int32_t n_in, int32_t arch, int32_t max_batch, uin
   // cannot lower it below what a wider one launches with.
   const ImgLayout widest = img_layout(69);
   if ((rc = set_smem_attr((const void*)k_qnet_forward, fwd_smem(widest))) ||
-      (rc = set_smem_attr((const void*)k_rollout_q<1>, fwd_smem(widest))) ||
-      (rc = set_smem_attr((const void*)k_rollout_q<2>, fwd_smem(widest, 32))) ||
+      (rc = set_smem_attr((const void*)k_rollout_q<1, false>, fwd_smem(widest))) ||
+      (rc = set_smem_attr((const void*)k_rollout_q<2, false>, fwd_smem(widest, 32))) ||
+      (rc = set_smem_attr((const void*)k_rollout_q<1, true>, fwd_smem(widest))) ||
+      (rc = set_smem_attr((const void*)k_rollout_q<2, true>, fwd_smem(widest, 32))) ||
       (rc = set_smem_attr((const void*)k_td_target, fwd_smem(widest))) ||
       (rc = set_smem_attr((const void*)k_td_grad, grad_smem(widest)))) {
     free_qnet(q);
@@ -1150,13 +1160,16 @@ int sg_rollout_eps_q(sg_sim* sim, int K, sg_qnet* q, const float* eps, sg_replay
   SG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, sim->device));
   const int n = sim->dc.n_envs;
   const int waves16 = ((n + 15) / 16 + sms - 1) / sms, waves32 = ((n + 31) / 32 + sms - 1) / sms;
-  const int mt = q->rollout_mt > 0 ? q->rollout_mt : (waves32 < waves16 ? 2 : 1);
+  // with dynamic obstacles the 32-env CTA (64 registers a thread) spills the
+  // disc registers: 16 envs per CTA unless asked otherwise
+  const bool dyn = sim->dc.n_dyn > 0;
+  const int mt = q->rollout_mt > 0 ? q->rollout_mt : (!dyn && waves32 < waves16 ? 2 : 1);
   if (mt == 2)
-    k_rollout_q<2><<<(n + 31) / 32, 1024, fwd_smem(q->IL, 32), stream>>>(
+    (dyn ? k_rollout_q<2, true> : k_rollout_q<2, false>)<<<(n + 31) / 32, 1024, fwd_smem(q->IL, 32), stream>>>(
         sim->dc, sg_sim_ptrs(sim), q->img, q->IL, K, eps, rd, rp ? 1 : 0, sim->map_order_dev, obs, obs_seq, act_seq,
         rew_seq, done_seq);
   else
-    k_rollout_q<1><<<(n + 15) / 16, 512, fwd_smem(q->IL), stream>>>(
+    (dyn ? k_rollout_q<1, true> : k_rollout_q<1, false>)<<<(n + 15) / 16, 512, fwd_smem(q->IL), stream>>>(
         sim->dc, sg_sim_ptrs(sim), q->img, q->IL, K, eps, rd, rp ? 1 : 0, sim->map_order_dev, obs, obs_seq, act_seq,
         rew_seq, done_seq);
   SG_CUDA(cudaGetLastError());

@@ -102,6 +102,7 @@ __global__ void k_clr_cols(const uint8_t* __restrict__ g, const PrepMap* __restr
 }
 
 // Episode 0 of every env; one warp per env.
+template <bool kDyn>
 __global__ void __launch_bounds__(128) k_reset(const __grid_constant__ DevCfg c, SimPtrs p, float* __restrict__ obs) {
   const int env = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
@@ -109,13 +110,16 @@ __global__ void __launch_bounds__(128) k_reset(const __grid_constant__ DevCfg c,
   const EnvConst k = env_const(c, p, env, lane);
   Env s;
   s.t = 0;
-  reset_env(c, k, s, 0u, lane);
+  Obst b = {0.0f, 0.0f, 0.0f, 0.0f};
+  Discs d;
+  reset_env<kDyn>(c, k, s, 0u, lane, &b, &d);
   const Noise z = noise_for(k, s.sigma, s.ep_id, 0u, lane);
   ObsRegs o;
   Aux aux;
-  observe(c, k, s, z, lane, o, aux);
+  observe<kDyn>(c, k, s, z, lane, o, aux, &d);
   if (obs) write_obs(obs + (long long)env * c.obs_dim, o, c.B, lane);
   if (lane == 0) store_env(p, env, s);
+  if (kDyn && lane < c.n_dyn) store_obst(p, lane, env, b);
 }
 
 // One vectorized step; one warp per env.
@@ -132,12 +136,19 @@ __global__ void __launch_bounds__(128) k_reset(const __grid_constant__ DevCfg c,
 constexpr int kStepEnvsPerWarp = 4;
 constexpr int kStepWarps = 8;
 
+// Disc centres of an env for its two scans (dynamic obstacles only).
+struct DiscRec {
+  Discs a, b;
+};
+
+template <bool kDyn>
 __global__ void __launch_bounds__(32 * kStepWarps, 4) k_step(const __grid_constant__ DevCfg c, SimPtrs p,
                                                              const int* __restrict__ order,
                                                              const uint8_t* __restrict__ act,
                                                              float* __restrict__ obs, float* __restrict__ rew,
                                                              uint8_t* __restrict__ done, float* __restrict__ term) {
   __shared__ StepScanRec rec[kStepWarps][kStepEnvsPerWarp];
+  __shared__ DiscRec drec[kDyn ? kStepWarps : 1][kDyn ? kStepEnvsPerWarp : 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int base = (blockIdx.x * kStepWarps + warp) * kStepEnvsPerWarp;
   if (base >= c.n_envs) return;  // warp-uniform
@@ -147,8 +158,9 @@ __global__ void __launch_bounds__(32 * kStepWarps, 4) k_step(const __grid_consta
   Env s;
   if (live) s = load_env(p, i);
   // lanes past the warp's envs take part in the warp-wide collision tests only
-  const uint32_t d =
-      lane_step(c, p, i, live, s, live ? (uint32_t)act[i] : 0u, rec[warp][live ? lane : 0], lane);
+  DiscRec* dr = kDyn ? &drec[warp][live ? lane : 0] : nullptr;
+  const uint32_t d = lane_step<kDyn>(c, p, i, live, s, live ? (uint32_t)act[i] : 0u, rec[warp][live ? lane : 0],
+                                     lane, kDyn ? &dr->a : nullptr, kDyn ? &dr->b : nullptr);
   if (live) {
     store_env(p, i, s);
     done[i] = (uint8_t)d;
@@ -160,8 +172,9 @@ __global__ void __launch_bounds__(32 * kStepWarps, 4) k_step(const __grid_consta
     const MapDesc m = p.maps[r.map];
     const uint32_t de = r.done;
     float b0, b1;
-    const float mn = scan_env(c, p, m, r.nb, r.stepb, r.ax, r.ay, r.aphi, r.asigma,
-                              ((uint64_t)r.anhi << 32) | r.anlo, lane, b0, b1);
+    const DiscRec* de_ = kDyn ? &drec[warp][e] : nullptr;
+    const float mn = scan_env<kDyn>(c, p, m, r.nb, r.stepb, r.ax, r.ay, r.aphi, r.asigma,
+                                    ((uint64_t)r.anhi << 32) | r.anlo, lane, b0, b1, kDyn ? &de_->a : nullptr);
     float rw;
     if (de & 1u)
       rw = -10.0f;
@@ -173,8 +186,8 @@ __global__ void __launch_bounds__(32 * kStepWarps, 4) k_step(const __grid_consta
       write_row(obs + (long long)ie * c.obs_dim, b0, b1, r.exa, c.B, lane);
     } else {
       if (term) write_row(term + (long long)ie * c.obs_dim, b0, b1, r.exa, c.B, lane);
-      scan_env(c, p, m, r.nb, r.stepb, r.bx, r.by, r.bphi, r.bsigma, ((uint64_t)r.bnhi << 32) | r.bnlo, lane, b0,
-               b1);
+      scan_env<kDyn>(c, p, m, r.nb, r.stepb, r.bx, r.by, r.bphi, r.bsigma, ((uint64_t)r.bnhi << 32) | r.bnlo, lane,
+                     b0, b1, kDyn ? &de_->b : nullptr);
       write_row(obs + (long long)ie * c.obs_dim, b0, b1, r.exb, c.B, lane);
     }
     if (lane == 0) rew[ie] = rw;
@@ -182,14 +195,19 @@ __global__ void __launch_bounds__(32 * kStepWarps, 4) k_step(const __grid_consta
 }
 
 // K steps of one env with uniformly random actions drawn on the device; the
-// env stays in registers between steps.  Per-step outputs are optional:
-// obs_seq [K][n][obs_dim], act/rew/done_seq [K][n].
+// env (and, with kDyn, its discs: lane o holds disc o) stays in registers
+// between steps.  Per-step outputs are optional: obs_seq [K][n][obs_dim],
+// act/rew/done_seq [K][n].
+template <bool kDyn>
 __device__ __forceinline__ void rollout_env(const DevCfg& c, const SimPtrs& p, int env, int lane, int K,
                                             float* __restrict__ obs, float* __restrict__ obs_seq,
                                             uint8_t* __restrict__ act_seq, float* __restrict__ rew_seq,
                                             uint8_t* __restrict__ done_seq) {
   const EnvConst k = env_const(c, p, env, lane);
   Env s = load_env(p, env);
+  Obst b = {0.0f, 0.0f, 0.0f, 0.0f};
+  Discs dsc;
+  if (kDyn && lane < c.n_dyn) b = load_obst(p, lane, env);
   const uint64_t akey = sm_at(sm_at(c.seed, kStreamAction), (uint64_t)env);
   ObsRegs o;
   o.b0 = o.b1 = o.ex = 0.0f;
@@ -198,7 +216,7 @@ __device__ __forceinline__ void rollout_env(const DevCfg& c, const SimPtrs& p, i
   for (int i = 0; i < K; ++i) {
     if ((i & 31) == 0) abatch = random_action_for(c, akey, s.t + (uint32_t)lane);
     const uint32_t a = __shfl_sync(kFull, abatch, i & 31);
-    const StepOut r = env_step(c, p, k, s, a, lane, o, nullptr);
+    const StepOut r = env_step<kDyn>(c, p, k, s, a, lane, o, nullptr, &b, &dsc);
     if (obs_seq) write_obs(obs_seq + ((long long)i * n + env) * c.obs_dim, o, c.B, lane);
     if (lane == 0) {
       if (act_seq) act_seq[i * n + env] = (uint8_t)a;
@@ -208,6 +226,7 @@ __device__ __forceinline__ void rollout_env(const DevCfg& c, const SimPtrs& p, i
   }
   if (obs) write_obs(obs + (long long)env * c.obs_dim, o, c.B, lane);
   if (lane == 0) store_env(p, env, s);
+  if (kDyn && lane < c.n_dyn) store_obst(p, lane, env, b);
 }
 
 // K steps of one env shared by W warps: every warp replays the pose chain of
@@ -564,6 +583,7 @@ __global__ void __launch_bounds__(256, 4) k_rollout_random_split(const __grid_co
 }
 
 // One warp per env, envs in index order.
+template <bool kDyn>
 __global__ void __launch_bounds__(512, 2) k_rollout_random(const __grid_constant__ DevCfg c, SimPtrs p, int K,
                                                         float* __restrict__ obs, float* __restrict__ obs_seq,
                                                         uint8_t* __restrict__ act_seq, float* __restrict__ rew_seq,
@@ -571,13 +591,14 @@ __global__ void __launch_bounds__(512, 2) k_rollout_random(const __grid_constant
   const int env = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (env >= c.n_envs) return;
-  rollout_env(c, p, env, lane, K, obs, obs_seq, act_seq, rew_seq, done_seq);
+  rollout_env<kDyn>(c, p, env, lane, K, obs, obs_seq, act_seq, rew_seq, done_seq);
 }
 
 // Persistent variant for uneven batches: a fixed grid of warps pulls envs
 // from a work list (typically sorted by cost, longest first) through a
 // device counter, so that envs with many beams or large maps start first and
 // short ones fill the tail.
+template <bool kDyn>
 __global__ void __launch_bounds__(512, 2) k_rollout_random_queue(const __grid_constant__ DevCfg c, SimPtrs p, int K,
                                                               const int* __restrict__ order,
                                                               unsigned* __restrict__ next, float* __restrict__ obs,
@@ -591,7 +612,7 @@ __global__ void __launch_bounds__(512, 2) k_rollout_random_queue(const __grid_co
     w = __shfl_sync(kFull, w, 0);
     if (w >= (unsigned)c.n_envs) break;
     const int env = order ? order[w] : (int)w;
-    rollout_env(c, p, env, lane, K, obs, obs_seq, act_seq, rew_seq, done_seq);
+    rollout_env<kDyn>(c, p, env, lane, K, obs, obs_seq, act_seq, rew_seq, done_seq);
   }
 }
 
@@ -649,6 +670,13 @@ static int make_devcfg(const sg_sim_config* cfg, DevCfg* dc) {
     if (!std::isfinite(pr[0]) || !std::isfinite(pr[1]) || pr[0] > pr[1]) return SG_E_INVAL;
   if (cfg->sigma_lo < 0.0f) return SG_E_INVAL;
   if (!(cfg->v_nom > 0.0f) || !(cfg->w_nom > 0.0f)) return SG_E_INVAL;
+  if (cfg->n_dyn < 0 || cfg->n_dyn > kMaxDyn) return SG_E_INVAL;
+  if (cfg->n_dyn > 0) {
+    if (!(cfg->dyn_radius > 0.0f) || !std::isfinite(cfg->dyn_radius)) return SG_E_INVAL;
+    if (!finite_nonneg(cfg->dyn_speed_lo) || !std::isfinite(cfg->dyn_speed_hi) ||
+        cfg->dyn_speed_lo > cfg->dyn_speed_hi || !finite_nonneg(cfg->dyn_keepout))
+      return SG_E_INVAL;
+  }
   std::memset(dc, 0, sizeof(*dc));
   dc->n_envs = cfg->n_envs;
   dc->B = cfg->n_beams;
@@ -687,6 +715,18 @@ static int make_devcfg(const sg_sim_config* cfg, DevCfg* dc) {
     dc->aw[i] = cfg->action_w[i];
   }
   dc->seed = cfg->seed;
+  dc->n_dyn = cfg->n_dyn;
+  if (cfg->n_dyn > 0) {
+    // float32 products, as the step evaluates them
+    const float r = cfg->dyn_radius, rr = cfg->robot_radius + cfg->dyn_radius, kp = cfg->dyn_keepout;
+    dc->dyn_r = r;
+    dc->dyn_r2 = r * r;
+    dc->dyn_rr2 = rr * rr;
+    dc->dyn_keep2 = kp * kp;
+    dc->dyn_vlo = cfg->dyn_speed_lo;
+    dc->dyn_vhi = cfg->dyn_speed_hi;
+    dc->dyn_re = r + cfg->march_step + 0.25f;
+  }
   return SG_OK;
 }
 
@@ -700,6 +740,7 @@ SimPtrs sg_sim_ptrs(sg_sim* s) {
   p.env_map = s->env_map_dev;
   p.env_beams = s->env_beams_dev;
   p.status = s->status_dev;
+  p.dyn = s->dyn;
   p.n = s->dc.n_envs;
   p.pad = 0;
   return p;
@@ -718,6 +759,7 @@ static void free_sim(sg_sim* s) {
   cudaFree(s->order_dev);
   cudaFree(s->queue_dev);
   cudaFree(s->map_order_dev);
+  cudaFree(s->dyn);
   delete s;
 }
 
@@ -737,6 +779,10 @@ extern "C" int sg_sim_create(const sg_sim_config* cfg, int32_t n_maps, const uin
   size_t max_cells = 0;
   for (int m = 0; m < n_maps; ++m) {
     if (!maps_host[m] || map_w[m] < 1 || map_h[m] < 1 || map_w[m] > 16384 || map_h[m] > 16384) return SG_E_INVAL;
+    // a disc must fit between the walls: r_o < W - r_o (in float32)
+    if (cfg->n_dyn > 0 && !((float)map_w[m] - cfg->dyn_radius > cfg->dyn_radius &&
+                            (float)map_h[m] - cfg->dyn_radius > cfg->dyn_radius))
+      return SG_E_INVAL;
     md[m].word_off = words;
     md[m].w = map_w[m];
     md[m].h = map_h[m];
@@ -774,6 +820,7 @@ extern "C" int sg_sim_create(const sg_sim_config* cfg, int32_t n_maps, const uin
   alloc((void**)&s->ustate, sizeof(uint32_t) * 4 * (size_t)n);
   alloc((void**)&s->status_dev, sizeof(uint32_t));
   alloc((void**)&s->map_order_dev, sizeof(int) * n);
+  if (cfg->n_dyn > 0) alloc((void**)&s->dyn, sizeof(float) * 4 * cfg->n_dyn * (size_t)n);
   // maps are preprocessed in groups whose grids fit a staging budget
   const size_t budget = std::max(max_cells, (size_t)256 << 20);
   uint8_t* staging = nullptr;  // grids, then per-row distances
@@ -856,6 +903,7 @@ extern "C" int sg_sim_create(const sg_sim_config* cfg, int32_t n_maps, const uin
   if (e == cudaSuccess) e = cudaMemset(s->fstate, 0, sizeof(float) * 9 * (size_t)n);
   if (e == cudaSuccess) e = cudaMemset(s->ustate, 0, sizeof(uint32_t) * 4 * (size_t)n);
   if (e == cudaSuccess) e = cudaMemset(s->status_dev, 0, sizeof(uint32_t));
+  if (e == cudaSuccess && s->dyn) e = cudaMemset(s->dyn, 0, sizeof(float) * 4 * cfg->n_dyn * (size_t)n);
   if (e != cudaSuccess) {
     free_sim(s);
     return cuda_fail(e, "sg_sim_create");
@@ -884,13 +932,16 @@ extern "C" int sg_sim_info_get(sg_sim_t sim, sg_sim_info* info) {
   return SG_OK;
 }
 
-long long sg_state_bytes(const sg_sim* s) { return (long long)s->dc.n_envs * (9 * 4 + 4 * 4); }
+long long sg_state_bytes(const sg_sim* s) { return (long long)s->dc.n_envs * (9 * 4 + 4 * 4 + 16 * s->dc.n_dyn); }
 
 extern "C" int sg_sim_reset(sg_sim_t sim, uint64_t seed, float* obs_dev, sg_stream_t stream) {
   if (!sim) return SG_E_INVAL;
   sim->dc.seed = seed;
   sim->cfg.seed = seed;
-  k_reset<<<grid_for(sim->dc.n_envs), 32 * kWarpsPerBlock, 0, stream>>>(sim->dc, sg_sim_ptrs(sim), obs_dev);
+  if (sim->dc.n_dyn > 0)
+    k_reset<true><<<grid_for(sim->dc.n_envs), 32 * kWarpsPerBlock, 0, stream>>>(sim->dc, sg_sim_ptrs(sim), obs_dev);
+  else
+    k_reset<false><<<grid_for(sim->dc.n_envs), 32 * kWarpsPerBlock, 0, stream>>>(sim->dc, sg_sim_ptrs(sim), obs_dev);
   SG_CUDA(cudaGetLastError());
   return SG_OK;
 }
@@ -900,7 +951,8 @@ extern "C" int sg_sim_step(sg_sim_t sim, const uint8_t* act_dev, float* obs_dev,
   if (!sim || !act_dev || !obs_dev || !rew_dev || !done_dev) return SG_E_INVAL;
   if (((uintptr_t)obs_dev & 3) || ((uintptr_t)rew_dev & 3) || ((uintptr_t)term_obs_dev & 3)) return SG_E_ALIGN;
   constexpr int kPerBlock = kStepWarps * kStepEnvsPerWarp;
-  k_step<<<(sim->dc.n_envs + kPerBlock - 1) / kPerBlock, 32 * kStepWarps, 0, stream>>>(
+  auto kern = sim->dc.n_dyn > 0 ? k_step<true> : k_step<false>;
+  kern<<<(sim->dc.n_envs + kPerBlock - 1) / kPerBlock, 32 * kStepWarps, 0, stream>>>(
       sim->dc, sg_sim_ptrs(sim), sim->map_order_dev, act_dev, obs_dev, rew_dev, done_dev, term_obs_dev);
   SG_CUDA(cudaGetLastError());
   return SG_OK;
@@ -937,16 +989,19 @@ extern "C" int sg_sim_rollout(sg_sim_t sim, int32_t K, int32_t policy, sg_qnet_t
             sim->dc, sp, K, W, obs_dev, obs_seq_dev, act_seq_dev, rew_seq_dev, done_seq_dev);
         break;
       }
-      case SG_ROLLOUT_QUEUE:
+      case SG_ROLLOUT_QUEUE: {
         SG_CUDA(cudaMemsetAsync(sim->queue_dev, 0, sizeof(unsigned), stream));
-        k_rollout_random_queue<<<sim->persistent_blocks, 32 * L.warps_per_block, 0, stream>>>(
+        auto kern = sim->dc.n_dyn > 0 ? k_rollout_random_queue<true> : k_rollout_random_queue<false>;
+        kern<<<sim->persistent_blocks, 32 * L.warps_per_block, 0, stream>>>(
             sim->dc, sp, K, L.order ? sim->order_dev : nullptr, sim->queue_dev, obs_dev, obs_seq_dev, act_seq_dev,
             rew_seq_dev, done_seq_dev);
         break;
+      }
       default: {
         const int wpb = L.warps_per_block;
-        k_rollout_random<<<(n + wpb - 1) / wpb, 32 * wpb, 0, stream>>>(sim->dc, sp, K, obs_dev, obs_seq_dev,
-                                                                      act_seq_dev, rew_seq_dev, done_seq_dev);
+        auto kern = sim->dc.n_dyn > 0 ? k_rollout_random<true> : k_rollout_random<false>;
+        kern<<<(n + wpb - 1) / wpb, 32 * wpb, 0, stream>>>(sim->dc, sp, K, obs_dev, obs_seq_dev, act_seq_dev,
+                                                            rew_seq_dev, done_seq_dev);
       }
     }
     SG_CUDA(cudaGetLastError());
@@ -973,11 +1028,14 @@ extern "C" int sg_sim_set_launch(sg_sim_t sim, const sg_launch* cfg) {
         return SG_E_INVAL;
       break;
     case SG_ROLLOUT_SPLIT:
-      // the kernel is compiled for at most 256 threads per CTA
+      // the kernel is compiled for at most 256 threads per CTA; it replays
+      // the pose chain without the LiDAR, which moving discs do not allow
+      if (sim->dc.n_dyn > 0) return SG_E_INVAL;
       if (L.warps_per_env < 1 || L.warps_per_env > 8 || L.warps_per_block < 1 || L.warps_per_block > 8)
         return SG_E_INVAL;
       break;
     case SG_ROLLOUT_PIPE:
+      if (sim->dc.n_dyn > 0) return SG_E_INVAL;  // same reason as SPLIT
       if (L.obs_warps < 1 || L.obs_warps > 15 || L.warps_per_block < 1 || L.warps_per_block > 16 || L.order < 0 ||
           L.order > 1)
         return SG_E_INVAL;
@@ -994,7 +1052,9 @@ extern "C" int sg_sim_set_launch(sg_sim_t sim, const sg_launch* cfg) {
   SG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, sim->device));
   int bps = L.blocks_per_sm;
   if (L.kernel == SG_ROLLOUT_QUEUE && bps == 0) {
-    SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_rollout_random_queue, 32 * L.warps_per_block, 0));
+    SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &bps, sim->dc.n_dyn > 0 ? k_rollout_random_queue<true> : k_rollout_random_queue<false>,
+        32 * L.warps_per_block, 0));
     if (bps < 1) bps = 1;
   }
   if (L.kernel == SG_ROLLOUT_QUEUE && L.order == 1 && !sim->order_dev) {
@@ -1038,6 +1098,8 @@ extern "C" int sg_sim_get_state(sg_sim_t sim, void* host_buf, size_t* bytes) {
   SG_CUDA(cudaDeviceSynchronize());
   SG_CUDA(cudaMemcpy(host_buf, sim->fstate, 9 * 4 * n, cudaMemcpyDeviceToHost));
   SG_CUDA(cudaMemcpy((char*)host_buf + 9 * 4 * n, sim->ustate, 4 * 4 * n, cudaMemcpyDeviceToHost));
+  if (sim->dc.n_dyn > 0)
+    SG_CUDA(cudaMemcpy((char*)host_buf + 13 * 4 * n, sim->dyn, 16 * (size_t)sim->dc.n_dyn * n, cudaMemcpyDeviceToHost));
   *bytes = need;
   return SG_OK;
 }
@@ -1050,6 +1112,9 @@ extern "C" int sg_sim_set_state(sg_sim_t sim, const void* host_buf, size_t bytes
   SG_CUDA(cudaDeviceSynchronize());
   SG_CUDA(cudaMemcpy(sim->fstate, host_buf, 9 * 4 * n, cudaMemcpyHostToDevice));
   SG_CUDA(cudaMemcpy(sim->ustate, (const char*)host_buf + 9 * 4 * n, 4 * 4 * n, cudaMemcpyHostToDevice));
+  if (sim->dc.n_dyn > 0)
+    SG_CUDA(cudaMemcpy(sim->dyn, (const char*)host_buf + 13 * 4 * n, 16 * (size_t)sim->dc.n_dyn * n,
+                       cudaMemcpyHostToDevice));
   return SG_OK;
 }
 

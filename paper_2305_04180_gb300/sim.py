@@ -32,6 +32,10 @@ def make_config(params: dict, n_envs: int) -> _lib.sg_sim_config:
         c.action_v[i] = float(v)
         c.action_w[i] = float(w)
     c.seed = int(params["seed"]) & 0xFFFFFFFFFFFFFFFF
+    # dynamic obstacles: optional, none by default
+    c.n_dyn = int(params.get("n_dyn", 0))
+    for k in ("dyn_radius", "dyn_speed_lo", "dyn_speed_hi", "dyn_keepout"):
+        setattr(c, k, float(params.get(k, 0.0)))
     return c
 
 
@@ -58,6 +62,7 @@ class Sim:
         env_map = np.ascontiguousarray(env_map, dtype=np.int32)
         self.n = int(env_map.size)
         self.cfg = make_config(params, self.n)
+        self.n_dyn = int(self.cfg.n_dyn)
         self.params = dict(params)
         grids = [np.ascontiguousarray(m, dtype=np.uint8) for m in maps]
         ptrs = (C.c_void_p * len(grids))(*[g.ctypes.data for g in grids])
@@ -153,18 +158,25 @@ class Sim:
                                                          else "cost"))
 
     def get_state(self):
-        """(f [9, N] float32, u [4, N] uint32) host copies of the env state."""
+        """(f [9, N] float32, u [4, N] uint32) host copies of the env state,
+        plus dyn [4 n_dyn, N] float32 when the envs have dynamic obstacles."""
         nbytes = C.c_size_t(int(self.info.state_bytes))
         buf = np.zeros(int(self.info.state_bytes), np.uint8)
         check(self.L.sg_sim_get_state(self.handle, buf.ctypes.data, C.byref(nbytes)), "sg_sim_get_state")
         f = buf[: 36 * self.n].view(np.float32).reshape(9, self.n).copy()
-        u = buf[36 * self.n:].view(np.uint32).reshape(4, self.n).copy()
-        return f, u
+        u = buf[36 * self.n:52 * self.n].view(np.uint32).reshape(4, self.n).copy()
+        if not self.n_dyn:
+            return f, u
+        d = buf[52 * self.n:].view(np.float32).reshape(4 * self.n_dyn, self.n).copy()
+        return f, u, d
 
-    def set_state(self, f, u):
+    def set_state(self, f, u, dyn=None):
         f = np.ascontiguousarray(f, np.float32).reshape(9, self.n)
         u = np.ascontiguousarray(u, np.uint32).reshape(4, self.n)
-        buf = np.concatenate([f.ravel().view(np.uint8), u.ravel().view(np.uint8)])
+        parts = [f.ravel().view(np.uint8), u.ravel().view(np.uint8)]
+        if self.n_dyn:
+            parts.append(np.ascontiguousarray(dyn, np.float32).reshape(4 * self.n_dyn, self.n).ravel().view(np.uint8))
+        buf = np.concatenate(parts)
         check(self.L.sg_sim_set_state(self.handle, buf.ctypes.data, buf.size), "sg_sim_set_state")
 
     def atlas(self):

@@ -7,12 +7,14 @@ from __future__ import annotations
 import numpy as np
 
 
-def gpu_state_to_oracle(f, u):
-    """Library state (f [9,N] f32; u [4,N]: ep_step, ep_id, t, fifo) ->
-    oracle arrays (f [9,N]; u [2,N]; b [3,N]: q0, q1, delay)."""
+def gpu_state_to_oracle(f, u, dyn=None):
+    """Library state (f [9,N] f32; u [4,N]: ep_step, ep_id, t, fifo; dyn
+    [4 n_dyn, N] with moving obstacles) -> oracle arrays (f [9,N]; u [2,N];
+    b [3,N]: q0, q1, delay; dyn passed through)."""
     fifo = u[3].astype(np.uint32)
     b = np.stack([fifo & 0xFF, (fifo >> 8) & 0xFF, (fifo >> 16) & 0xFF]).astype(np.uint8)
-    return f.copy(), u[:2].copy(), b
+    out = (f.copy(), u[:2].copy(), b)
+    return out if dyn is None else out + (dyn.copy(),)
 
 
 def oracle_state_to_gpu(f, u2, b, t):

@@ -73,6 +73,12 @@ DR_RANGES = dict(
 )
 
 
+# Moving obstacles (the extension the paper's Sec. 5 names as future work):
+# four discs of radius 8 cm per env, 4..30 cm/s (the robot's nominal top
+# speed is 18 cm/s), none starting within 60 cm of S or G.
+DYN_RANGES = dict(n_dyn=4, dyn_radius=8.0, dyn_speed_lo=4.0, dyn_speed_hi=30.0, dyn_keepout=60.0)
+
+
 @dataclass
 class Workload:
     name: str
@@ -119,6 +125,14 @@ def workload(name: str, n_envs: int | None = None, steps: int | None = None) -> 
             n_envs=n, map_specs=[(1 + m, 366) for m in range(n_maps)],
             env_map=(np.arange(n) % n_maps).astype(np.int32), env_beams=None,
             params=base_params(**DR_RANGES), steps=steps or 10000, policy="random")
+    if name == "dyn1024":
+        n = n_envs or 1024
+        n_maps = min(32, n)
+        return Workload(
+            name="domain-randomized sim with 4 moving obstacles per env, 1024 envs over 32 maps 366x366, 32 beams",
+            n_envs=n, map_specs=[(1 + m, 366) for m in range(n_maps)],
+            env_map=(np.arange(n) % n_maps).astype(np.int32), env_beams=None,
+            params=base_params(**DR_RANGES, **DYN_RANGES), steps=steps or 10000, policy="random")
     if name == "uneven8192":
         n = n_envs or 8192
         rng = np.random.default_rng(3)
@@ -155,4 +169,4 @@ def workload(name: str, n_envs: int | None = None, steps: int | None = None) -> 
     raise KeyError(name)
 
 
-WORKLOADS = ("plain16", "dr1024", "uneven8192", "qnet4096", "full65536")
+WORKLOADS = ("plain16", "dr1024", "uneven8192", "qnet4096", "full65536", "dyn1024")
