@@ -199,9 +199,9 @@ def run_ours(a):
         sim.set_launch(kernel, **kw)
         tune = {"config": sim.launch_config()}
     else:
-        # untimed; restores the env state.  2,048-step trials: long enough for
-        # the CTA waves of a 10,000-step rollout to show
-        tune = autotune_rollout(sim, K=2048, reps=2, cache_path=None)
+        # untimed; restores the env state.  Trials of the timed rollout's own
+        # length, so that CTA waves and time slicing show as they will
+        tune = autotune_rollout(sim, K=K, reps=2, cache_path=None)
     obs = sim.new_obs()
     obs_seq = torch.empty((K, n, sim.obs_dim), dtype=torch.float32, device="cuda")
     rew_seq = torch.empty((K, n), dtype=torch.float32, device="cuda")
@@ -532,6 +532,8 @@ def launch_label(r):
         s += f":{r['blocks_per_sm']}bps"
     if r.get("order", "index") != "index":
         s += f":{r['order']}"
+    if r.get("segment"):
+        s += f":seg{r['segment']}"
     return s
 
 

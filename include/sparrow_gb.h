@@ -235,6 +235,14 @@ int sg_sim_rollout(sg_sim_t sim, int32_t K, int32_t policy, sg_qnet_t qnet, cons
  *                     (1 + obs_warps))) envs per CTA, warps_per_block 1..16;
  *                     order 0 = index order, 1 = envs grouped by map (CTAs
  *                     share maps, so fewer maps compete for each SM's L1).
+ *                     segment > 0 (a multiple of 32, at most 1 << 20) slices
+ *                     the rollout in time: a resident grid takes (segment,
+ *                     CTA's envs) items in order, each after the previous
+ *                     segment of its envs is stored, so that no CTA slot
+ *                     idles in a last partial wave; segment 0 (default) runs
+ *                     every env's K steps in one CTA.  The waits are
+ *                     bounded: on timeout the status word gets
+ *                     SG_DEV_TIMEOUT and the outputs are incomplete.
  * Synchronous (computes and uploads the work list on first use).
  */
 #define SG_ROLLOUT_GRID 0
@@ -248,7 +256,8 @@ typedef struct sg_launch {
   int32_t obs_warps;
   int32_t blocks_per_sm;
   int32_t order;
-  int32_t reserved[2]; /* 0 */
+  int32_t segment;     /* SG_ROLLOUT_PIPE time slicing, steps; 0 = none */
+  int32_t reserved;    /* 0 */
 } sg_launch;
 int sg_sim_set_launch(sg_sim_t sim, const sg_launch* cfg);
 int sg_sim_get_launch(sg_sim_t sim, sg_launch* cfg);

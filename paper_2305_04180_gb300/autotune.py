@@ -2,7 +2,9 @@
 
 For a given simulator it times every candidate (kernel variant: one warp
 per env, persistent work-list grid, warps sharing an env, pose/observation
-pipelines; envs per CTA and warps per env) on short rollouts, restoring the env state after each trial, and applies the fastest.
+pipelines with and without time slicing; envs per CTA and warps per env) on
+rollouts of the requested length, restoring the env state after each trial,
+and applies the fastest.
 Results are cached as JSON per (device, workload signature, rollout length),
 so later runs of the same workload reuse them without timing.  The choice
 never changes the results, only their speed.
@@ -18,7 +20,8 @@ import numpy as np
 import torch
 
 def _cand(kernel, **kw):
-    d = dict(kernel=kernel, warps_per_block=4, warps_per_env=1, obs_warps=0, blocks_per_sm=0, order="index")
+    d = dict(kernel=kernel, warps_per_block=4, warps_per_env=1, obs_warps=0, blocks_per_sm=0, order="index",
+             segment=0)
     d.update(kw)
     return d
 
@@ -28,8 +31,10 @@ CANDIDATES = ([_cand("grid", warps_per_block=w) for w in (2, 4, 8)]
               + [_cand("split", warps_per_block=8, warps_per_env=W) for W in (2, 3, 4)]
               + [_cand("pipe", warps_per_block=b, obs_warps=P, order=o)
                  for P, b, o in ((7, 8, "map"), (7, 16, "map"), (7, 16, "index"), (3, 8, "map"), (3, 4, "map"),
-                                 (5, 12, "map"), (15, 16, "map"))])
-KEYS = ("kernel", "warps_per_block", "warps_per_env", "obs_warps", "blocks_per_sm", "order")
+                                 (5, 12, "map"), (15, 16, "map"))]
+              + [_cand("pipe", warps_per_block=8, obs_warps=7, order="map", segment=S) for S in (256, 512, 1024, 2048)]
+              + [_cand("pipe", warps_per_block=16, obs_warps=7, order="map", segment=1024)])
+KEYS = ("kernel", "warps_per_block", "warps_per_env", "obs_warps", "blocks_per_sm", "order", "segment")
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
 

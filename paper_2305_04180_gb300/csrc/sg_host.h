@@ -26,11 +26,13 @@ struct sg_sim {
   float* dyn = nullptr;        // [4 n_dyn][n] dynamic obstacles (null when n_dyn = 0)
   uint32_t* status_dev = nullptr;
   // launch configuration of the random rollout (sg_sim_set_launch)
-  sg_launch launch = {SG_ROLLOUT_GRID, 4, 1, 0, 0, 0, {0, 0}};
+  sg_launch launch = {SG_ROLLOUT_GRID, 4, 1, 0, 0, 0, 0, 0};
   int persistent_blocks = 0;
   int* order_dev = nullptr;      // work list (cost-sorted env indices) or null
   int* map_order_dev = nullptr;  // env indices grouped by map (stable), for per-CTA map locality
   unsigned* queue_dev = nullptr; // work-list cursor of the persistent kernel
+  unsigned* pipe_sync_dev = nullptr;  // time-sliced pipelined rollout: segment flags, item counter, abort word
+  size_t pipe_sync_words = 0;
 };
 
 sg::SimPtrs sg_sim_ptrs(sg_sim* s);

@@ -494,8 +494,49 @@ __device__ __forceinline__ void consume_chunk(const DevCfg& c, const EnvConst& k
 // waits before writing it again).  At most kPipeMaxGroups groups per CTA.
 constexpr int kPipeMaxGroups = 3;
 
+// Time slicing (seg > 0): the rollout is cut into segments of seg steps and
+// a persistent grid takes work items (segment, CTA's envs) in segment-major
+// order from a device counter, so that every resident CTA stays busy to the
+// end instead of the last wave running part-empty.  An item starts after the
+// previous segment of its envs has stored their state: its CTA waits on a
+// per-envs flag (bounded; on timeout the status word gets SG_DEV_TIMEOUT, an
+// abort word stops the other CTAs, and the launch's outputs are incomplete).
+// sync: [nblk] flags (segments done), item counter, abort word; zero at launch.
+constexpr unsigned kPipeWaitIters = 1u << 22;  // x ~256 ns sleeps: about a second
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* a) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu(unsigned* a, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;\n" ::"l"(a), "r"(v) : "memory");
+}
+
+// State of env i through L2 (another SM may have written it in this launch).
+__device__ __forceinline__ Env load_env_cg(const SimPtrs& p, int i) {
+  Env s;
+  const int n = p.n;
+  s.x = __ldcg(p.f + 0 * n + i);
+  s.y = __ldcg(p.f + 1 * n + i);
+  s.phi = __ldcg(p.f + 2 * n + i);
+  s.vl = __ldcg(p.f + 3 * n + i);
+  s.va = __ldcg(p.f + 4 * n + i);
+  s.dt = __ldcg(p.f + 5 * n + i);
+  s.K = __ldcg(p.f + 6 * n + i);
+  s.cap = __ldcg(p.f + 7 * n + i);
+  s.sigma = __ldcg(p.f + 8 * n + i);
+  s.ep_step = __ldcg(p.u + 0 * n + i);
+  s.ep_id = __ldcg(p.u + 1 * n + i);
+  s.t = __ldcg(p.u + 2 * n + i);
+  s.fifo = __ldcg(p.u + 3 * n + i);
+  f_sincos(s.phi, s.sphi, s.cphi);
+  return s;
+}
+
 __global__ void __launch_bounds__(512, 2) k_rollout_random_pipe(const __grid_constant__ DevCfg c, SimPtrs p, int K,
-                                                                int P, const int* __restrict__ order,
+                                                                int P, const int* __restrict__ order, int seg,
+                                                                unsigned* __restrict__ sync,
                                                                 float* __restrict__ obs,
                                                                 float* __restrict__ obs_seq,
                                                                 uint8_t* __restrict__ act_seq,
@@ -503,63 +544,110 @@ __global__ void __launch_bounds__(512, 2) k_rollout_random_pipe(const __grid_con
                                                                 uint8_t* __restrict__ done_seq) {
   extern __shared__ __align__(16) unsigned char pipe_smem[];
   __shared__ unsigned next_step[kPipeMaxGroups][2];  // per env group and buffer: next record to take
+  __shared__ int item_sh;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int G = 1 + P;  // warps per env
   const int group = warp / G, role = warp % G;
   const int E = blockDim.x / (32 * G);
-  const int slot = blockIdx.x * E + group;
-  if (slot >= c.n_envs) return;  // the whole group leaves together
-  const int env = order ? order[slot] : slot;
+  const int nblk = (c.n_envs + E - 1) / E;
+  const int seglen = seg > 0 ? seg : K;  // a multiple of kPipeChunk when seg > 0
+  const int nseg = (K + seglen - 1) / seglen;
+  const long long nitems = (long long)nblk * nseg;
   // per group: kPipeChunk step records, then 2 x kPipeChunk observation records
   unsigned char* base = pipe_smem + (size_t)group * kPipeChunk * (sizeof(StepRec) + 2 * sizeof(ObsRec));
   StepRec* st = reinterpret_cast<StepRec*>(base);
   ObsRec* ob = reinterpret_cast<ObsRec*>(base + kPipeChunk * sizeof(StepRec));
   const int bfull = 1 + 4 * group, bfree = 3 + 4 * group, nthr = 32 * G;
-  const EnvConst k = env_const(c, p, env, lane);
   const long long n = c.n_envs;
-  const int chunks = (K + kPipeChunk - 1) / kPipeChunk;
-  ObsRegs o;
-  o.b0 = o.b1 = o.ex = 0.0f;
-  bool has_last = false;
-  if (role == 0) {
-    for (int ch = 0; ch <= chunks; ++ch) {
-      if (ch < chunks) {
-        const int b = ch & 1;
-        if (ch >= 2) named_barrier(bfree + b, nthr);  // chunk ch - 2 consumed
-        if (lane == 0) next_step[group][b] = 0u;
-        // the state carried between chunks is the last step record's post
-        // state, so nothing of the pose chain stays live while this warp
-        // takes observation records
-        Env s = ch == 0 ? load_env(p, env) : unpack_env(reinterpret_cast<const uint4*>(&st[kPipeChunk - 1].post));
-        const int i0 = ch * kPipeChunk, nst = min(K, i0 + kPipeChunk) - i0;
-        // lane l draws the action of step i0 + l (t counts every step)
-        const uint64_t akey = sm_at(sm_at(c.seed, kStreamAction), (uint64_t)env);
-        const uint32_t abatch = random_action_for(c, akey, s.t + (uint32_t)lane);
-        pose_chunk(c, p, k, s, nst, abatch, st, lane);
-        __syncwarp();
-        if (lane < nst) derive_rec(c, k, st[lane], ob[b * kPipeChunk + lane]);
-        named_arrive(bfull + b, nthr);
+  for (int iter = 0;; ++iter) {
+    // next item: its segment and CTA's envs, after the previous segment of
+    // those envs is stored
+    if (threadIdx.x == 0) {
+      long long it;
+      if (!sync)
+        it = iter == 0 ? (long long)blockIdx.x : nitems;
+      else
+        it = __ldcg(&sync[nblk + 1]) ? nitems : (long long)atomicAdd(&sync[nblk], 1u);
+      if (sync && it < nitems && it >= nblk) {
+        const unsigned need = (unsigned)(it / nblk);
+        unsigned w = 0;
+        while (ld_acquire_gpu(&sync[it % nblk]) < need) {
+          if (++w > kPipeWaitIters || ld_acquire_gpu(&sync[nblk + 1])) {
+            atomicOr(p.status, SG_DEV_TIMEOUT);
+            atomicExch(&sync[nblk + 1], 1u);
+            it = nitems;
+            break;
+          }
+          __nanosleep(256);
+        }
       }
-      if (ch >= 1) {
-        const int b = (ch - 1) & 1, i0 = (ch - 1) * kPipeChunk;
-        consume_chunk(c, k, ob + b * kPipeChunk, &next_step[group][b], i0, min(K, i0 + kPipeChunk), K, env, n,
-                      lane, o, has_last, obs_seq, act_seq, rew_seq, done_seq);
-      }
+      item_sh = it < nitems ? (int)it : -1;
     }
-    // the last two chunks' consumption completes the free barriers' phases
-    for (int ch = max(chunks, 2); ch < chunks + 2; ++ch) named_barrier(bfree + (ch & 1), nthr);
-    if (lane == 0 && chunks > 0)
-      store_env(p, env, unpack_env(reinterpret_cast<const uint4*>(&st[K - 1 - (chunks - 1) * kPipeChunk].post)));
-  } else {
-    for (int ch = 1; ch <= chunks; ++ch) {
-      const int b = (ch - 1) & 1, i0 = (ch - 1) * kPipeChunk;
-      named_barrier(bfull + b, nthr);  // chunk ch - 1 written
-      consume_chunk(c, k, ob + b * kPipeChunk, &next_step[group][b], i0, min(K, i0 + kPipeChunk), K, env, n, lane,
-                    o, has_last, obs_seq, act_seq, rew_seq, done_seq);
-      named_arrive(bfree + b, nthr);
+    __syncthreads();
+    const int item = item_sh;
+    __syncthreads();  // item_sh is rewritten by the next iteration
+    if (item < 0) break;
+    const int blk = item % nblk, sg_i = item / nblk;
+    const int s0 = sg_i * seglen, s1 = min(K, s0 + seglen), Kl = s1 - s0;
+    const int slot = blk * E + group;
+    if (slot < c.n_envs) {  // the whole group takes part or not
+      const int env = order ? order[slot] : slot;
+      const EnvConst k = env_const(c, p, env, lane);
+      const int chunks = (Kl + kPipeChunk - 1) / kPipeChunk;
+      ObsRegs o;
+      o.b0 = o.b1 = o.ex = 0.0f;
+      bool has_last = false;
+      if (role == 0) {
+        for (int ch = 0; ch <= chunks; ++ch) {
+          if (ch < chunks) {
+            const int b = ch & 1;
+            if (ch >= 2) named_barrier(bfree + b, nthr);  // chunk ch - 2 consumed
+            if (lane == 0) next_step[group][b] = 0u;
+            // the state carried between chunks is the last step record's post
+            // state, so nothing of the pose chain stays live while this warp
+            // takes observation records
+            Env s = ch > 0 ? unpack_env(reinterpret_cast<const uint4*>(&st[kPipeChunk - 1].post))
+                           : (sync ? load_env_cg(p, env) : load_env(p, env));
+            const int i0 = ch * kPipeChunk, nst = min(Kl, i0 + kPipeChunk) - i0;
+            // lane l draws the action of step i0 + l (t counts every step)
+            const uint64_t akey = sm_at(sm_at(c.seed, kStreamAction), (uint64_t)env);
+            const uint32_t abatch = random_action_for(c, akey, s.t + (uint32_t)lane);
+            pose_chunk(c, p, k, s, nst, abatch, st, lane);
+            __syncwarp();
+            if (lane < nst) derive_rec(c, k, st[lane], ob[b * kPipeChunk + lane]);
+            named_arrive(bfull + b, nthr);
+          }
+          if (ch >= 1) {
+            const int b = (ch - 1) & 1, i0 = s0 + (ch - 1) * kPipeChunk;
+            consume_chunk(c, k, ob + b * kPipeChunk, &next_step[group][b], i0, min(s1, i0 + kPipeChunk), K, env,
+                          n, lane, o, has_last, obs_seq, act_seq, rew_seq, done_seq);
+          }
+        }
+        // the last two chunks' consumption completes the free barriers' phases
+        for (int ch = max(chunks, 2); ch < chunks + 2; ++ch) named_barrier(bfree + (ch & 1), nthr);
+        if (lane == 0 && chunks > 0) {
+          store_env(p, env, unpack_env(reinterpret_cast<const uint4*>(&st[Kl - 1 - (chunks - 1) * kPipeChunk].post)));
+          if (sync) __threadfence();
+        }
+      } else {
+        for (int ch = 1; ch <= chunks; ++ch) {
+          const int b = (ch - 1) & 1, i0 = s0 + (ch - 1) * kPipeChunk;
+          named_barrier(bfull + b, nthr);  // chunk ch - 1 written
+          consume_chunk(c, k, ob + b * kPipeChunk, &next_step[group][b], i0, min(s1, i0 + kPipeChunk), K, env, n,
+                        lane, o, has_last, obs_seq, act_seq, rew_seq, done_seq);
+          named_arrive(bfree + b, nthr);
+        }
+      }
+      if (obs && has_last) write_obs(obs + (long long)env * c.obs_dim, o, c.B, lane);
+    }
+    if (!sync) break;
+    // every group's state is stored: publish this segment of the CTA's envs
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      st_release_gpu(&sync[blk], (unsigned)(sg_i + 1));
     }
   }
-  if (obs && has_last) write_obs(obs + (long long)env * c.obs_dim, o, c.B, lane);
 }
 
 static size_t pipe_smem_bytes(int E) { return (size_t)E * kPipeChunk * (sizeof(StepRec) + 2 * sizeof(ObsRec)); }
@@ -760,6 +848,7 @@ static void free_sim(sg_sim* s) {
   cudaFree(s->queue_dev);
   cudaFree(s->map_order_dev);
   cudaFree(s->dyn);
+  cudaFree(s->pipe_sync_dev);
   delete s;
 }
 
@@ -977,9 +1066,19 @@ extern "C" int sg_sim_rollout(sg_sim_t sim, int32_t K, int32_t policy, sg_qnet_t
         const int G = 1 + L.obs_warps;
         const int E = pipe_envs_per_block(L);
         const size_t smem = pipe_smem_bytes(E);
-        k_rollout_random_pipe<<<(n + E - 1) / E, 32 * G * E, smem, stream>>>(
-            sim->dc, sp, K, L.obs_warps, L.order ? sim->map_order_dev : nullptr, obs_dev, obs_seq_dev, act_seq_dev,
-            rew_seq_dev, done_seq_dev);
+        const int nblk = (n + E - 1) / E;
+        int seg = L.segment < K ? L.segment : 0;  // one segment needs no slicing
+        long long grid = nblk;
+        if (seg > 0) {
+          // items are counted in 32 bits: lengthen the segments if needed
+          while ((long long)nblk * ((K + seg - 1) / seg) >= (1ll << 31)) seg *= 2;
+          const long long nitems = (long long)nblk * ((K + seg - 1) / seg);
+          grid = std::min<long long>(nitems, (long long)sim->persistent_blocks);
+          SG_CUDA(cudaMemsetAsync(sim->pipe_sync_dev, 0, sizeof(unsigned) * (size_t)(nblk + 2), stream));
+        }
+        k_rollout_random_pipe<<<(unsigned)grid, 32 * G * E, smem, stream>>>(
+            sim->dc, sp, K, L.obs_warps, L.order ? sim->map_order_dev : nullptr, seg,
+            seg > 0 ? sim->pipe_sync_dev : nullptr, obs_dev, obs_seq_dev, act_seq_dev, rew_seq_dev, done_seq_dev);
         break;
       }
       case SG_ROLLOUT_SPLIT: {
@@ -1039,18 +1138,35 @@ extern "C" int sg_sim_set_launch(sg_sim_t sim, const sg_launch* cfg) {
       if (L.obs_warps < 1 || L.obs_warps > 15 || L.warps_per_block < 1 || L.warps_per_block > 16 || L.order < 0 ||
           L.order > 1)
         return SG_E_INVAL;
+      if (L.segment < 0 || L.segment > (1 << 20) || L.segment % kPipeChunk != 0) return SG_E_INVAL;
       break;
     default:
       return SG_E_INVAL;
   }
-  if (L.kernel == SG_ROLLOUT_PIPE) {
-    const size_t smem = pipe_smem_bytes(pipe_envs_per_block(L));
-    SG_CUDA(cudaFuncSetAttribute((const void*)k_rollout_random_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem));
-  }
   int sms = 0;
   SG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, sim->device));
   int bps = L.blocks_per_sm;
+  if (L.kernel == SG_ROLLOUT_PIPE) {
+    const int E = pipe_envs_per_block(L);
+    const size_t smem = pipe_smem_bytes(E);
+    SG_CUDA(cudaFuncSetAttribute((const void*)k_rollout_random_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+    if (L.segment > 0) {
+      // time slicing: a resident grid and the per-CTA segment flags
+      SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_rollout_random_pipe,
+                                                            32 * (1 + L.obs_warps) * E, smem));
+      if (bps < 1) bps = 1;
+      if (L.blocks_per_sm > 0) bps = std::min(bps, L.blocks_per_sm);
+      const size_t words = (size_t)((sim->dc.n_envs + E - 1) / E) + 2;
+      if (words > sim->pipe_sync_words) {
+        cudaFree(sim->pipe_sync_dev);
+        sim->pipe_sync_dev = nullptr;
+        sim->pipe_sync_words = 0;
+        SG_CUDA(cudaMalloc(&sim->pipe_sync_dev, sizeof(unsigned) * words));
+        sim->pipe_sync_words = words;
+      }
+    }
+  }
   if (L.kernel == SG_ROLLOUT_QUEUE && bps == 0) {
     SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         &bps, sim->dc.n_dyn > 0 ? k_rollout_random_queue<true> : k_rollout_random_queue<false>,
@@ -1076,7 +1192,8 @@ extern "C" int sg_sim_set_launch(sg_sim_t sim, const sg_launch* cfg) {
   }
   if (L.kernel == SG_ROLLOUT_QUEUE && !sim->queue_dev) SG_CUDA(cudaMalloc(&sim->queue_dev, sizeof(unsigned)));
   sim->launch = L;
-  sim->persistent_blocks = L.kernel == SG_ROLLOUT_QUEUE ? bps * sms : 0;
+  sim->persistent_blocks =
+      (L.kernel == SG_ROLLOUT_QUEUE || (L.kernel == SG_ROLLOUT_PIPE && L.segment > 0)) ? bps * sms : 0;
   return SG_OK;
 }
 

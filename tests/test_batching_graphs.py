@@ -124,13 +124,44 @@ def test_pipelined_rollout_lengths(K):
     out = []
     for cfg in (None, dict(kernel="pipe", warps_per_block=16, obs_warps=7), dict(kernel="pipe", warps_per_block=16,
                                                                                 obs_warps=4),
-                dict(kernel="pipe", warps_per_block=16, obs_warps=7, order="map")):
+                dict(kernel="pipe", warps_per_block=16, obs_warps=7, order="map"),
+                dict(kernel="pipe", warps_per_block=8, obs_warps=7, order="map", segment=32),
+                dict(kernel="pipe", warps_per_block=16, obs_warps=4, segment=64)):
         s = Sim(p, maps, env_map, beams)
         if cfg:
             s.set_launch(**cfg)
         s.reset()
         obs = s.new_obs()
         r = _run_obs(s, K, obs)
+        out.append((r, obs.cpu().numpy(), s.get_state()))
+    (ref, obs0, (f0, u0)) = out[0]
+    for r, ob, (f, u) in out[1:]:
+        for k in ref:
+            assert np.array_equal(bits(r[k]) if r[k].dtype == np.float32 else r[k],
+                                  bits(ref[k]) if ref[k].dtype == np.float32 else ref[k]), k
+        assert np.array_equal(bits(ob), bits(obs0))
+        assert np.array_equal(bits(f), bits(f0)) and np.array_equal(u, u0)
+
+
+@pytest.mark.parametrize("n,K,seg,cfg", [(4, 640, 32, dict(warps_per_block=8, obs_warps=7)),
+                                         (7, 333, 64, dict(warps_per_block=16, obs_warps=7)),
+                                         (50, 500, 96, dict(warps_per_block=12, obs_warps=3, order="map"))])
+def test_time_sliced_pipelined_rollout(n, K, seg, cfg):
+    """The time-sliced pipelined rollout: with few envs and many segments
+    nearly every item waits for the previous segment of its envs on another
+    CTA.  Every output and the final state equal the unsliced launch's, no
+    wait times out, and the slicing repeats bit for bit."""
+    from paper_2305_04180_gb300 import Sim
+
+    p, maps, env_map, beams = _uneven(n, seed=5)
+    out = []
+    for c in (dict(cfg, kernel="pipe"), dict(cfg, kernel="pipe", segment=seg), dict(cfg, kernel="pipe", segment=seg)):
+        s = Sim(p, maps, env_map, beams)
+        s.set_launch(**c)
+        s.reset()
+        obs = s.new_obs()
+        r = _run_obs(s, K, obs)
+        assert s.status() == 0
         out.append((r, obs.cpu().numpy(), s.get_state()))
     (ref, obs0, (f0, u0)) = out[0]
     for r, ob, (f, u) in out[1:]:

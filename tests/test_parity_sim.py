@@ -110,7 +110,8 @@ def test_step_teacher_forced_domain_randomised():
     assert _teacher_forced(g, o, 1000, seed=1) == 1024000
 
 
-@pytest.mark.parametrize("launch", [None, dict(kernel="pipe", warps_per_block=8, obs_warps=7, order="map")])
+@pytest.mark.parametrize("launch", [None, dict(kernel="pipe", warps_per_block=8, obs_warps=7, order="map"),
+                                    dict(kernel="pipe", warps_per_block=8, obs_warps=7, order="map", segment=512)])
 def test_rollout_plain16_million_env_steps(launch):
     """The 16-env workload free-running for 62,500 steps (10^6 env-steps):
     every step's action, reward and done flags and the final state equal the
@@ -166,7 +167,8 @@ def test_step_degenerate_cases():
     assert g.status() == 0  # reading clears it
 
 
-@pytest.mark.parametrize("launch", [None, dict(kernel="pipe", warps_per_block=8, obs_warps=7, order="map")])
+@pytest.mark.parametrize("launch", [None, dict(kernel="pipe", warps_per_block=8, obs_warps=7, order="map"),
+                                    dict(kernel="pipe", warps_per_block=8, obs_warps=7, order="map", segment=512)])
 def test_rollout_random_free_running_bit_exact(launch):
     """1000 free-running steps with on-device random actions: every step's
     action, reward, done flags and observation, and the final state, equal
@@ -220,7 +222,8 @@ def test_rollout_continues_across_calls_and_matches_steps():
     assert np.array_equal(bits(fa), bits(fb)) and np.array_equal(ua, ub)
 
 
-@pytest.mark.parametrize("launch", [None, dict(kernel="pipe", warps_per_block=8, obs_warps=7, order="map")])
+@pytest.mark.parametrize("launch", [None, dict(kernel="pipe", warps_per_block=8, obs_warps=7, order="map"),
+                                    dict(kernel="pipe", warps_per_block=8, obs_warps=7, order="map", segment=512)])
 def test_rollout_full_size_sampled_against_oracle(launch):
     """The 1024-env, 32-map domain-randomised workload (one warp per env, and
     the pipelined launch the benchmark times): 300 steps on the GPU, then a
@@ -248,7 +251,8 @@ def test_rollout_full_size_sampled_against_oracle(launch):
         assert np.array_equal(o.u[:, i], u[:2, i])
 
 
-@pytest.mark.parametrize("launch", [None, dict(kernel="pipe", warps_per_block=8, obs_warps=7, order="map")])
+@pytest.mark.parametrize("launch", [None, dict(kernel="pipe", warps_per_block=8, obs_warps=7, order="map"),
+                                    dict(kernel="pipe", warps_per_block=8, obs_warps=7, order="map", segment=512)])
 def test_uneven_full_size_sampled_against_oracle(launch):
     """The 8,192-env uneven workload at full size (one map per env, sides
     128..1,024, 16/32/64 beams, per-env dynamics): 64 steps on the GPU, then
