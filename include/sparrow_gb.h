@@ -241,8 +241,11 @@ int sg_sim_rollout(sg_sim_t sim, int32_t K, int32_t policy, sg_qnet_t qnet, cons
  *                     segment of its envs is stored, so that no CTA slot
  *                     idles in a last partial wave; segment 0 (default) runs
  *                     every env's K steps in one CTA.  The waits are
- *                     bounded: on timeout the status word gets
- *                     SG_DEV_TIMEOUT and the outputs are incomplete.
+ *                     bounded (wait_iters sleeps of ~256 ns each; 0 = the
+ *                     default 2^22, about a second): on timeout the status
+ *                     word gets SG_DEV_TIMEOUT, the other CTAs stop at
+ *                     their next item, and the outputs and env state of
+ *                     that launch are incomplete.
  * Synchronous (computes and uploads the work list on first use).
  */
 #define SG_ROLLOUT_GRID 0
@@ -257,7 +260,7 @@ typedef struct sg_launch {
   int32_t blocks_per_sm;
   int32_t order;
   int32_t segment;     /* SG_ROLLOUT_PIPE time slicing, steps; 0 = none */
-  int32_t reserved;    /* 0 */
+  int32_t wait_iters;  /* bound of a time-sliced item's wait; 0 = default */
 } sg_launch;
 int sg_sim_set_launch(sg_sim_t sim, const sg_launch* cfg);
 int sg_sim_get_launch(sg_sim_t sim, sg_launch* cfg);

@@ -52,7 +52,7 @@ class sg_sim_config(C.Structure):
 class sg_launch(C.Structure):
     _fields_ = [("kernel", C.c_int32), ("warps_per_block", C.c_int32), ("warps_per_env", C.c_int32),
                 ("obs_warps", C.c_int32), ("blocks_per_sm", C.c_int32), ("order", C.c_int32),
-                ("segment", C.c_int32), ("reserved", C.c_int32)]
+                ("segment", C.c_int32), ("wait_iters", C.c_int32)]
 
 
 SG_ROLLOUT_KERNELS = {"grid": 0, "queue": 1, "split": 2, "pipe": 3}

@@ -26,7 +26,7 @@ struct sg_sim {
   float* dyn = nullptr;        // [4 n_dyn][n] dynamic obstacles (null when n_dyn = 0)
   uint32_t* status_dev = nullptr;
   // launch configuration of the random rollout (sg_sim_set_launch)
-  sg_launch launch = {SG_ROLLOUT_GRID, 4, 1, 0, 0, 0, 0, 0};
+  sg_launch launch = {SG_ROLLOUT_GRID, 4, 1, 0, 0, 0, 0, 0};  // no slicing, default wait bound
   int persistent_blocks = 0;
   int* order_dev = nullptr;      // work list (cost-sorted env indices) or null
   int* map_order_dev = nullptr;  // env indices grouped by map (stable), for per-CTA map locality

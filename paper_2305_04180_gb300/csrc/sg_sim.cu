@@ -502,7 +502,7 @@ constexpr int kPipeMaxGroups = 3;
 // per-envs flag (bounded; on timeout the status word gets SG_DEV_TIMEOUT, an
 // abort word stops the other CTAs, and the launch's outputs are incomplete).
 // sync: [nblk] flags (segments done), item counter, abort word; zero at launch.
-constexpr unsigned kPipeWaitIters = 1u << 22;  // x ~256 ns sleeps: about a second
+constexpr unsigned kPipeWaitIters = 1u << 22;  // default bound, x ~256 ns sleeps: about a second
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* a) {
   unsigned v;
@@ -536,7 +536,7 @@ __device__ __forceinline__ Env load_env_cg(const SimPtrs& p, int i) {
 
 __global__ void __launch_bounds__(512, 2) k_rollout_random_pipe(const __grid_constant__ DevCfg c, SimPtrs p, int K,
                                                                 int P, const int* __restrict__ order, int seg,
-                                                                unsigned* __restrict__ sync,
+                                                                unsigned* __restrict__ sync, unsigned wait_iters,
                                                                 float* __restrict__ obs,
                                                                 float* __restrict__ obs_seq,
                                                                 uint8_t* __restrict__ act_seq,
@@ -572,7 +572,7 @@ __global__ void __launch_bounds__(512, 2) k_rollout_random_pipe(const __grid_con
         const unsigned need = (unsigned)(it / nblk);
         unsigned w = 0;
         while (ld_acquire_gpu(&sync[it % nblk]) < need) {
-          if (++w > kPipeWaitIters || ld_acquire_gpu(&sync[nblk + 1])) {
+          if (++w > wait_iters || ld_acquire_gpu(&sync[nblk + 1])) {
             atomicOr(p.status, SG_DEV_TIMEOUT);
             atomicExch(&sync[nblk + 1], 1u);
             it = nitems;
@@ -1078,7 +1078,8 @@ extern "C" int sg_sim_rollout(sg_sim_t sim, int32_t K, int32_t policy, sg_qnet_t
         }
         k_rollout_random_pipe<<<(unsigned)grid, 32 * G * E, smem, stream>>>(
             sim->dc, sp, K, L.obs_warps, L.order ? sim->map_order_dev : nullptr, seg,
-            seg > 0 ? sim->pipe_sync_dev : nullptr, obs_dev, obs_seq_dev, act_seq_dev, rew_seq_dev, done_seq_dev);
+            seg > 0 ? sim->pipe_sync_dev : nullptr, L.wait_iters > 0 ? (unsigned)L.wait_iters : kPipeWaitIters,
+            obs_dev, obs_seq_dev, act_seq_dev, rew_seq_dev, done_seq_dev);
         break;
       }
       case SG_ROLLOUT_SPLIT: {
@@ -1138,7 +1139,8 @@ extern "C" int sg_sim_set_launch(sg_sim_t sim, const sg_launch* cfg) {
       if (L.obs_warps < 1 || L.obs_warps > 15 || L.warps_per_block < 1 || L.warps_per_block > 16 || L.order < 0 ||
           L.order > 1)
         return SG_E_INVAL;
-      if (L.segment < 0 || L.segment > (1 << 20) || L.segment % kPipeChunk != 0) return SG_E_INVAL;
+      if (L.segment < 0 || L.segment > (1 << 20) || L.segment % kPipeChunk != 0 || L.wait_iters < 0)
+        return SG_E_INVAL;
       break;
     default:
       return SG_E_INVAL;

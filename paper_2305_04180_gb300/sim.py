@@ -136,17 +136,19 @@ class Sim:
         return obs
 
     def set_launch(self, kernel="grid", warps_per_block=4, warps_per_env=1, obs_warps=0, blocks_per_sm=0,
-                   order="index", segment=0):
+                   order="index", segment=0, wait_iters=0):
         """Launch configuration of the network-free rollout (sg_sim_set_launch);
         accepts the keys of ``launch_config()``.  segment: time slicing of the
-        pipelined kernel (steps, a multiple of 32; 0 = none)."""
+        pipelined kernel (steps, a multiple of 32; 0 = none); wait_iters: the
+        bound of its waits (0 = about a second)."""
         # order 1 is "cost" (longest first) for the work-list kernel and "map"
         # (envs grouped by map) for the pipelined one
         orders = {"queue": ("index", "cost"), "pipe": ("index", "map")}.get(kernel, ("index",))
         if order not in orders:
             raise ValueError(f"order {order!r} is not one of {orders} for kernel {kernel!r}")
         L = _lib.sg_launch(_lib.SG_ROLLOUT_KERNELS[kernel], int(warps_per_block), int(warps_per_env),
-                           int(obs_warps), int(blocks_per_sm), orders.index(order), int(segment))
+                           int(obs_warps), int(blocks_per_sm), orders.index(order), int(segment),
+                           int(wait_iters))
         check(self.L.sg_sim_set_launch(self.handle, C.byref(L)), "sg_sim_set_launch")
 
     def launch_config(self) -> dict:
@@ -157,7 +159,7 @@ class Sim:
                     obs_warps=L.obs_warps, blocks_per_sm=L.blocks_per_sm,
                     order="index" if L.order == 0 else ("map" if L.kernel == _lib.SG_ROLLOUT_KERNELS["pipe"]
                                                          else "cost"),
-                    segment=L.segment)
+                    segment=L.segment, wait_iters=L.wait_iters)
 
     def get_state(self):
         """(f [9, N] float32, u [4, N] uint32) host copies of the env state,

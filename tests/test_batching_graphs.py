@@ -172,6 +172,36 @@ def test_time_sliced_pipelined_rollout(n, K, seg, cfg):
         assert np.array_equal(bits(f), bits(f0)) and np.array_equal(u, u0)
 
 
+def test_time_sliced_wait_bound_reports_timeout_and_recovers():
+    """Failure detection of the time-sliced rollout's bounded waits: with a
+    one-sleep bound, an item that must wait for the previous segment of its
+    envs gives up at once.  The launch ends, the status word reads
+    SG_DEV_TIMEOUT, and the next launches on the same context (default
+    bound) give the unsliced results."""
+    from paper_2305_04180_gb300 import Sim
+
+    p, maps, env_map, beams = _uneven(4, seed=6)
+    K = 640
+    s = Sim(p, maps, env_map, beams)
+    s.set_launch(kernel="pipe", warps_per_block=8, obs_warps=7, segment=32, wait_iters=1)
+    s.reset()
+    rew = torch.empty((K, 4), device="cuda")
+    s.rollout(K, rew_seq=rew)
+    torch.cuda.synchronize()
+    assert s.status() == 2  # SG_DEV_TIMEOUT
+    assert s.status() == 0  # reading clears it
+    ref = Sim(p, maps, env_map, beams)
+    ref.set_launch(kernel="pipe", warps_per_block=8, obs_warps=7)
+    ref.reset()
+    r0 = _run_obs(ref, K, ref.new_obs())
+    s.set_launch(kernel="pipe", warps_per_block=8, obs_warps=7, segment=32)
+    s.reset()
+    r1 = _run_obs(s, K, s.new_obs())
+    assert s.status() == 0
+    for k in r0:
+        assert np.array_equal(r0[k].view(np.uint8), r1[k].view(np.uint8)), k
+
+
 def _run_obs(sim, K, obs):
     n = sim.n
     out = dict(obs_seq=torch.empty((K, n, sim.obs_dim), device="cuda"),
