@@ -638,6 +638,11 @@ def main():
                                "sample": f"{n} envs x {CPU_SAMPLE_STEPS} steps of the same workload (f32 oracle, "
                                          f"{cores} spawned processes sharded by env)",
                                "wall_s": wall}
+        # one core: a single process over a slice of the same envs (stepping time only)
+        n1 = min(n, 64)
+        s1, _, busy1, _ = time_oracle(pool, 1, a.workload, n1, 2000)
+        out["cpu_baseline"]["single_thread"] = {"value": s1 / busy1, "unit": UNIT, "cores": 1,
+                                                "sample": f"{n1} envs x 2000 steps, one process"}
         pool.close()
     if samples_per_env_step is None:
         samples_per_env_step = 1500.0
