@@ -436,9 +436,8 @@ def _run_extras_tail(out, flush, which):
 
 def run_dyn(flush):
     """Moving obstacles (four discs per env) on the 1,024-env domain-randomised
-    maps: the autotuned rollout (one warp per env, the only launches that take
-    obstacles) of 1,000 steps and the single-step kernel at 65,536 envs, each
-    beside the same launch without obstacles."""
+    maps: the autotuned rollout of 1,000 steps and the single-step kernel at
+    65,536 envs, each beside the same launch without obstacles."""
     import torch
 
     from paper_2305_04180_gb300 import Sim
@@ -454,7 +453,7 @@ def run_dyn(flush):
         sim = Sim(w.params, w.maps(), w.env_map)
         sim.reset()
         if tuned is None:
-            tuned = autotune_rollout(sim, K=64, reps=2, cache_path=None)["config"]
+            tuned = autotune_rollout(sim, K=K, reps=2, cache_path=None)["config"]
         else:
             sim.set_launch(**tuned)
         rew = torch.empty((K, sim.n), device="cuda")

@@ -102,9 +102,8 @@ typedef struct sg_sim_config {
    * enter an occupied cell stays and the velocity reverses.  The robot
    * collides when the centres are within robot_radius + dyn_radius; a LiDAR
    * sample inside a disc is a hit.  n_dyn = 0 (default): no obstacles, the
-   * other fields are ignored.  Requires 2 r < every map side.  The SPLIT and
-   * PIPE rollout kernels do not support obstacles (sg_sim_set_launch rejects
-   * them).
+   * other fields are ignored.  Requires 2 r < every map side.  The SPLIT
+   * rollout kernel does not support obstacles (sg_sim_set_launch rejects it).
    */
   int32_t n_dyn;             /* 0..8 */
   float dyn_radius;          /* > 0 when n_dyn > 0, cells */

@@ -101,8 +101,8 @@ def autotune_rollout(sim, K: int = 32, reps: int = 3, cache_path: str | None = D
     """
     candidates = list(candidates or CANDIDATES)
     if getattr(sim, "n_dyn", 0):
-        # moving obstacles need the LiDAR in the pose chain: one warp per env
-        candidates = [c for c in candidates if c["kernel"] in ("grid", "queue")]
+        # the split launch replays the pose chain per warp without the discs
+        candidates = [c for c in candidates if c["kernel"] != "split"]
     key = signature(sim, K)
     cache = load_cache(cache_path) if cache_path else {}
     if key in cache:

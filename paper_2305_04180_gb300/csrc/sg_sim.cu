@@ -363,16 +363,17 @@ __device__ __forceinline__ void derive_rec(const DevCfg& c, const EnvConst& k, c
 // The scan of one pose by a whole warp: this lane's beams (with noise drawn
 // from key nk when sigma > 0) into o.b0 / o.b1; returns the minimum
 // noise-free range over all beams.
+template <bool kDyn = false>
 __device__ __forceinline__ float scan_pose(const DevCfg& c, const EnvConst& k, float x, float y, float phi,
-                                           float sigma, uint64_t nk, int lane, ObsRegs& o) {
+                                           float sigma, uint64_t nk, int lane, ObsRegs& o, const Discs* d = nullptr) {
   float n0 = 0.0f, n1 = 0.0f;
   if (sigma > 0.0f) {
     n0 = box_muller(sm_at(nk, (uint64_t)lane));
     if (k.nb > 32) n1 = box_muller(sm_at(nk, (uint64_t)(lane + 32)));
   }
   float mn = c.range_max;
-  o.b0 = lane < k.nb ? beam_at(c, k, x, y, phi, sigma, k.off0, n0, mn) : 1.0f;
-  o.b1 = lane + 32 < k.nb ? beam_at(c, k, x, y, phi, sigma, k.off1, n1, mn) : 1.0f;
+  o.b0 = lane < k.nb ? beam_at<kDyn>(c, k, x, y, phi, sigma, k.off0, n0, mn, d) : 1.0f;
+  o.b1 = lane + 32 < k.nb ? beam_at<kDyn>(c, k, x, y, phi, sigma, k.off1, n1, mn, d) : 1.0f;
   // ranges are >= 0, so their bit patterns order like the values
   return __uint_as_float(__reduce_min_sync(kFull, __float_as_uint(mn)));
 }
@@ -387,24 +388,39 @@ __device__ __forceinline__ float scan_pose(const DevCfg& c, const EnvConst& k, f
 // the steps that need it in order with the whole warp, and takes the first
 // step that ends the episode: the steps before it stand, it is reset, and the
 // chain runs again from the step after it.  Every value equals that of
-// stepping one step at a time.
+// stepping one step at a time.  With kDyn the env's discs (lane o holds disc
+// o; its state between chunks in dst) move along with the pose chain, their
+// centres after step j go to dpost[j] (the new episode's for a done step,
+// whose pre-reset centres go to dpre[j]), and lane j's tests include them.
+template <bool kDyn = false>
 __device__ __forceinline__ void pose_chunk(const DevCfg& c, const SimPtrs& p, const EnvConst& k, Env& s, int n,
-                                           uint32_t abatch, StepRec* buf, int lane) {
+                                           uint32_t abatch, StepRec* buf, int lane, Obst* dst = nullptr,
+                                           Discs* dpost = nullptr, Discs* dpre = nullptr) {
   bool bad = false;
   int j0 = 0;
+  Obst b = {0.0f, 0.0f, 0.0f, 0.0f};
+  if (kDyn && lane < c.n_dyn) b = dst[lane];
   while (j0 < n) {
     Env q = s;
+    Obst bq = b;
     float mx = 0.0f, my = 0.0f;
     uint32_t mep = 0;
 #pragma unroll 4
     for (int j = j0; j < n; ++j) {
       const uint32_t a = __shfl_sync(kFull, abatch, j);
+      const float dt = q.dt;  // the discs move with the episode's control interval
       bad |= kinematics(c, q, a);
       mx = lane == j ? q.x : mx;
       my = lane == j ? q.y : my;
       mep = lane == j ? q.ep_step : mep;
       if (lane == 0) pack_env(reinterpret_cast<uint4*>(&buf[j].post), q, a);
+      if (kDyn && lane < c.n_dyn) {
+        dyn_move(c, k.m, k.clr, dt, bq);
+        dpost[j].x[lane] = bq.x;
+        dpost[j].y[lane] = bq.y;
+      }
     }
+    if (kDyn) __syncwarp();
     uint32_t done = 0;
     bool slow = false;
     if (lane >= j0 && lane < n) {
@@ -417,6 +433,11 @@ __device__ __forceinline__ void pose_chunk(const DevCfg& c, const SimPtrs& p, co
       const float ddx = k.L.gx - mx, ddy = k.L.gy - my;
       if (fmaf(ddx, ddx, ddy * ddy) <= c.goal_r * c.goal_r) done |= 2u;
       if (mep >= (uint32_t)c.t_max) done |= 4u;
+      if (kDyn)
+        for (int o = 0; o < c.n_dyn; ++o) {
+          const float dx = dpost[lane].x[o] - mx, dy = dpost[lane].y[o] - my;
+          if (fmaf(dx, dx, dy * dy) <= c.dyn_rr2) done |= 1u;
+        }
     }
     uint32_t donem = __ballot_sync(kFull, done != 0u);
     uint32_t slowm = __ballot_sync(kFull, slow);
@@ -434,6 +455,7 @@ __device__ __forceinline__ void pose_chunk(const DevCfg& c, const SimPtrs& p, co
     if (lane >= j0 && lane < d) buf[lane].done = 0u;
     if (d == n) {
       s = q;
+      b = bq;
       break;
     }
     // step d ends the episode: its record keeps the state before the reset
@@ -443,21 +465,40 @@ __device__ __forceinline__ void pose_chunk(const DevCfg& c, const SimPtrs& p, co
     Env e = unpack_env(reinterpret_cast<const uint4*>(&buf[d].post));
     __syncwarp();
     if (lane == 0) pack_env(reinterpret_cast<uint4*>(&buf[d].pre), e, dd);
-    reset_env(c, k, e, e.ep_id + 1u, lane);
+    if (kDyn) {
+      Discs nd;
+      if (lane < c.n_dyn) {
+        dpre[d].x[lane] = dpost[d].x[lane];
+        dpre[d].y[lane] = dpost[d].y[lane];
+      }
+      reset_env<true>(c, k, e, e.ep_id + 1u, lane, &b, &nd);
+      if (lane < c.n_dyn) {
+        dpost[d].x[lane] = b.x;
+        dpost[d].y[lane] = b.y;
+      }
+      __syncwarp();
+    } else {
+      reset_env(c, k, e, e.ep_id + 1u, lane);
+    }
     if (lane == 0) pack_env(reinterpret_cast<uint4*>(&buf[d].post), e, ad);
     s = e;
     j0 = d + 1;
   }
+  if (kDyn && lane < c.n_dyn) dst[lane] = b;
   if (bad && lane == 0) atomicOr(p.status, 1u);
 }
 
 // Consume the observation records of one chunk (steps i0 .. i1-1) through
-// the shared counter: scan, observation, reward, outputs.
+// the shared counter: scan, observation, reward, outputs.  With kDyn the
+// scans see the recorded disc centres of each step (dpost; dpre for the
+// pre-reset scan of a truncated step).
+template <bool kDyn = false>
 __device__ __forceinline__ void consume_chunk(const DevCfg& c, const EnvConst& k, const ObsRec* buf, unsigned* next,
                                               int i0, int i1, int K, int env, long long n, int lane, ObsRegs& o,
                                               bool& has_last, float* __restrict__ obs_seq,
                                               uint8_t* __restrict__ act_seq, float* __restrict__ rew_seq,
-                                              uint8_t* __restrict__ done_seq) {
+                                              uint8_t* __restrict__ done_seq, const Discs* dpost = nullptr,
+                                              const Discs* dpre = nullptr) {
   for (;;) {
     unsigned r = 0;
     if (lane == 0) r = atomicAdd(next, 1u);
@@ -472,10 +513,11 @@ __device__ __forceinline__ void consume_chunk(const DevCfg& c, const EnvConst& k
       rew = 75.0f;
     } else if (done) {
       const uint64_t pk = ((uint64_t)R.pnhi << 32) | R.pnlo;
-      rew = reward_finish(c, R.rpart, scan_pose(c, k, R.px, R.py, R.pphi, R.psigma, pk, lane, o));
+      rew = reward_finish(c, R.rpart, scan_pose<kDyn>(c, k, R.px, R.py, R.pphi, R.psigma, pk, lane, o,
+                                                      kDyn ? dpre + (i - i0) : nullptr));
     }
     const uint64_t nk = ((uint64_t)R.nhi << 32) | R.nlo;
-    const float mn = scan_pose(c, k, R.x, R.y, R.phi, R.sigma, nk, lane, o);
+    const float mn = scan_pose<kDyn>(c, k, R.x, R.y, R.phi, R.sigma, nk, lane, o, kDyn ? dpost + (i - i0) : nullptr);
     if (!done) rew = reward_finish(c, R.rpart, mn);
     o.ex = lane < 5 ? R.ex[lane] : 0.0f;
     if (i == K - 1) has_last = true;
@@ -493,6 +535,13 @@ __device__ __forceinline__ void consume_chunk(const DevCfg& c, const EnvConst& k
 // 3 + 4g + b (buffer b consumed: the observation warps arrive, the pose warp
 // waits before writing it again).  At most kPipeMaxGroups groups per CTA.
 constexpr int kPipeMaxGroups = 3;
+
+// Shared memory of one env group of the pipelined kernel.
+__host__ __device__ constexpr size_t pipe_group_bytes(bool dyn) {
+  return kPipeChunk * (sizeof(StepRec) + 2 * sizeof(ObsRec)) +
+         (dyn ? 4 * kPipeChunk * sizeof(Discs) + kMaxDyn * sizeof(Obst) : 0);
+}
+static_assert(pipe_group_bytes(false) % 16 == 0 && pipe_group_bytes(true) % 16 == 0, "16-byte aligned groups");
 
 // Time slicing (seg > 0): the rollout is cut into segments of seg steps and
 // a persistent grid takes work items (segment, CTA's envs) in segment-major
@@ -533,7 +582,17 @@ __device__ __forceinline__ Env load_env_cg(const SimPtrs& p, int i) {
   f_sincos(s.phi, s.sphi, s.cphi);
   return s;
 }
+__device__ __forceinline__ Obst load_obst_cg(const SimPtrs& p, int o, int i) {
+  const int n = p.n;
+  Obst b;
+  b.x = __ldcg(p.dyn + (4 * o + 0) * n + i);
+  b.y = __ldcg(p.dyn + (4 * o + 1) * n + i);
+  b.vx = __ldcg(p.dyn + (4 * o + 2) * n + i);
+  b.vy = __ldcg(p.dyn + (4 * o + 3) * n + i);
+  return b;
+}
 
+template <bool kDyn>
 __global__ void __launch_bounds__(512, 2) k_rollout_random_pipe(const __grid_constant__ DevCfg c, SimPtrs p, int K,
                                                                 int P, const int* __restrict__ order, int seg,
                                                                 unsigned* __restrict__ sync, unsigned wait_iters,
@@ -553,10 +612,15 @@ __global__ void __launch_bounds__(512, 2) k_rollout_random_pipe(const __grid_con
   const int seglen = seg > 0 ? seg : K;  // a multiple of kPipeChunk when seg > 0
   const int nseg = (K + seglen - 1) / seglen;
   const long long nitems = (long long)nblk * nseg;
-  // per group: kPipeChunk step records, then 2 x kPipeChunk observation records
-  unsigned char* base = pipe_smem + (size_t)group * kPipeChunk * (sizeof(StepRec) + 2 * sizeof(ObsRec));
+  // per group: kPipeChunk step records, 2 x kPipeChunk observation records,
+  // and with discs 2 x kPipeChunk centre sets after each step, 2 x kPipeChunk
+  // before a reset, and the disc state between chunks
+  unsigned char* base = pipe_smem + (size_t)group * pipe_group_bytes(kDyn);
   StepRec* st = reinterpret_cast<StepRec*>(base);
   ObsRec* ob = reinterpret_cast<ObsRec*>(base + kPipeChunk * sizeof(StepRec));
+  Discs* dpost = reinterpret_cast<Discs*>(ob + 2 * kPipeChunk);
+  Discs* dpre = dpost + 2 * kPipeChunk;
+  Obst* dst = reinterpret_cast<Obst*>(dpre + 2 * kPipeChunk);
   const int bfull = 1 + 4 * group, bfree = 3 + 4 * group, nthr = 32 * G;
   const long long n = c.n_envs;
   for (int iter = 0;; ++iter) {
@@ -608,33 +672,37 @@ __global__ void __launch_bounds__(512, 2) k_rollout_random_pipe(const __grid_con
             // takes observation records
             Env s = ch > 0 ? unpack_env(reinterpret_cast<const uint4*>(&st[kPipeChunk - 1].post))
                            : (sync ? load_env_cg(p, env) : load_env(p, env));
+            if (kDyn && ch == 0 && lane < c.n_dyn) dst[lane] = sync ? load_obst_cg(p, lane, env) : load_obst(p, lane, env);
             const int i0 = ch * kPipeChunk, nst = min(Kl, i0 + kPipeChunk) - i0;
             // lane l draws the action of step i0 + l (t counts every step)
             const uint64_t akey = sm_at(sm_at(c.seed, kStreamAction), (uint64_t)env);
             const uint32_t abatch = random_action_for(c, akey, s.t + (uint32_t)lane);
-            pose_chunk(c, p, k, s, nst, abatch, st, lane);
+            pose_chunk<kDyn>(c, p, k, s, nst, abatch, st, lane, dst, dpost + b * kPipeChunk,
+                             dpre + b * kPipeChunk);
             __syncwarp();
             if (lane < nst) derive_rec(c, k, st[lane], ob[b * kPipeChunk + lane]);
             named_arrive(bfull + b, nthr);
           }
           if (ch >= 1) {
             const int b = (ch - 1) & 1, i0 = s0 + (ch - 1) * kPipeChunk;
-            consume_chunk(c, k, ob + b * kPipeChunk, &next_step[group][b], i0, min(s1, i0 + kPipeChunk), K, env,
-                          n, lane, o, has_last, obs_seq, act_seq, rew_seq, done_seq);
+            consume_chunk<kDyn>(c, k, ob + b * kPipeChunk, &next_step[group][b], i0, min(s1, i0 + kPipeChunk), K,
+                                env, n, lane, o, has_last, obs_seq, act_seq, rew_seq, done_seq,
+                                dpost + b * kPipeChunk, dpre + b * kPipeChunk);
           }
         }
         // the last two chunks' consumption completes the free barriers' phases
         for (int ch = max(chunks, 2); ch < chunks + 2; ++ch) named_barrier(bfree + (ch & 1), nthr);
-        if (lane == 0 && chunks > 0) {
+        if (lane == 0 && chunks > 0)
           store_env(p, env, unpack_env(reinterpret_cast<const uint4*>(&st[Kl - 1 - (chunks - 1) * kPipeChunk].post)));
-          if (sync) __threadfence();
-        }
+        if (kDyn && lane < c.n_dyn) store_obst(p, lane, env, dst[lane]);
+        if (sync) __threadfence();
       } else {
         for (int ch = 1; ch <= chunks; ++ch) {
           const int b = (ch - 1) & 1, i0 = s0 + (ch - 1) * kPipeChunk;
           named_barrier(bfull + b, nthr);  // chunk ch - 1 written
-          consume_chunk(c, k, ob + b * kPipeChunk, &next_step[group][b], i0, min(s1, i0 + kPipeChunk), K, env, n,
-                        lane, o, has_last, obs_seq, act_seq, rew_seq, done_seq);
+          consume_chunk<kDyn>(c, k, ob + b * kPipeChunk, &next_step[group][b], i0, min(s1, i0 + kPipeChunk), K, env,
+                              n, lane, o, has_last, obs_seq, act_seq, rew_seq, done_seq, dpost + b * kPipeChunk,
+                              dpre + b * kPipeChunk);
           named_arrive(bfree + b, nthr);
         }
       }
@@ -650,7 +718,7 @@ __global__ void __launch_bounds__(512, 2) k_rollout_random_pipe(const __grid_con
   }
 }
 
-static size_t pipe_smem_bytes(int E) { return (size_t)E * kPipeChunk * (sizeof(StepRec) + 2 * sizeof(ObsRec)); }
+static size_t pipe_smem_bytes(int E, bool dyn) { return (size_t)E * pipe_group_bytes(dyn); }
 static int pipe_envs_per_block(const sg_launch& L) {
   const int E = L.warps_per_block / (1 + L.obs_warps);
   return E < 1 ? 1 : (E > kPipeMaxGroups ? kPipeMaxGroups : E);
@@ -1065,7 +1133,8 @@ extern "C" int sg_sim_rollout(sg_sim_t sim, int32_t K, int32_t policy, sg_qnet_t
       case SG_ROLLOUT_PIPE: {
         const int G = 1 + L.obs_warps;
         const int E = pipe_envs_per_block(L);
-        const size_t smem = pipe_smem_bytes(E);
+        const bool dyn = sim->dc.n_dyn > 0;
+        const size_t smem = pipe_smem_bytes(E, dyn);
         const int nblk = (n + E - 1) / E;
         int seg = L.segment < K ? L.segment : 0;  // one segment needs no slicing
         long long grid = nblk;
@@ -1076,7 +1145,8 @@ extern "C" int sg_sim_rollout(sg_sim_t sim, int32_t K, int32_t policy, sg_qnet_t
           grid = std::min<long long>(nitems, (long long)sim->persistent_blocks);
           SG_CUDA(cudaMemsetAsync(sim->pipe_sync_dev, 0, sizeof(unsigned) * (size_t)(nblk + 2), stream));
         }
-        k_rollout_random_pipe<<<(unsigned)grid, 32 * G * E, smem, stream>>>(
+        (dyn ? k_rollout_random_pipe<true> : k_rollout_random_pipe<false>)<<<(unsigned)grid, 32 * G * E, smem,
+                                                                          stream>>>(
             sim->dc, sp, K, L.obs_warps, L.order ? sim->map_order_dev : nullptr, seg,
             seg > 0 ? sim->pipe_sync_dev : nullptr, L.wait_iters > 0 ? (unsigned)L.wait_iters : kPipeWaitIters,
             obs_dev, obs_seq_dev, act_seq_dev, rew_seq_dev, done_seq_dev);
@@ -1128,14 +1198,13 @@ extern "C" int sg_sim_set_launch(sg_sim_t sim, const sg_launch* cfg) {
         return SG_E_INVAL;
       break;
     case SG_ROLLOUT_SPLIT:
-      // the kernel is compiled for at most 256 threads per CTA; it replays
-      // the pose chain without the LiDAR, which moving discs do not allow
+      // the kernel is compiled for at most 256 threads per CTA; its warps
+      // replay the pose chain without the discs
       if (sim->dc.n_dyn > 0) return SG_E_INVAL;
       if (L.warps_per_env < 1 || L.warps_per_env > 8 || L.warps_per_block < 1 || L.warps_per_block > 8)
         return SG_E_INVAL;
       break;
     case SG_ROLLOUT_PIPE:
-      if (sim->dc.n_dyn > 0) return SG_E_INVAL;  // same reason as SPLIT
       if (L.obs_warps < 1 || L.obs_warps > 15 || L.warps_per_block < 1 || L.warps_per_block > 16 || L.order < 0 ||
           L.order > 1)
         return SG_E_INVAL;
@@ -1150,12 +1219,13 @@ extern "C" int sg_sim_set_launch(sg_sim_t sim, const sg_launch* cfg) {
   int bps = L.blocks_per_sm;
   if (L.kernel == SG_ROLLOUT_PIPE) {
     const int E = pipe_envs_per_block(L);
-    const size_t smem = pipe_smem_bytes(E);
-    SG_CUDA(cudaFuncSetAttribute((const void*)k_rollout_random_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem));
+    const bool dyn = sim->dc.n_dyn > 0;
+    const size_t smem = pipe_smem_bytes(E, dyn);
+    auto kern = dyn ? k_rollout_random_pipe<true> : k_rollout_random_pipe<false>;
+    SG_CUDA(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (L.segment > 0) {
       // time slicing: a resident grid and the per-CTA segment flags
-      SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_rollout_random_pipe,
+      SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern,
                                                             32 * (1 + L.obs_warps) * E, smem));
       if (bps < 1) bps = 1;
       if (L.blocks_per_sm > 0) bps = std::min(bps, L.blocks_per_sm);

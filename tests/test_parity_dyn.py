@@ -1,8 +1,8 @@
 """GPU parity of the moving-obstacle extension against the strict-float32
-oracle (through the C ABI): reset, the lane-per-env step, the one-warp-per-env
-and work-list rollouts and the fused Q-network rollout, all bit-exact in
+oracle (through the C ABI): reset, the lane-per-env step, the one-warp-per-env,
+work-list and pipelined rollouts and the fused Q-network rollout, all bit-exact in
 observations, rewards, done flags, terminal observations and the whole state
-including the discs.  The pipelined and split rollouts refuse obstacles.
+including the discs.  The split rollout refuses obstacles.
 """
 
 import numpy as np
@@ -100,7 +100,9 @@ def test_step_fast_crowded_obstacles_small_maps():
 
 
 @pytest.mark.parametrize("launch", [dict(kernel="grid", warps_per_block=4),
-                                    dict(kernel="queue", warps_per_block=8, order="cost")])
+                                    dict(kernel="queue", warps_per_block=8, order="cost"),
+                                    dict(kernel="pipe", warps_per_block=8, obs_warps=7, order="map"),
+                                    dict(kernel="pipe", warps_per_block=16, obs_warps=7, order="map", segment=64)])
 def test_rollout_free_running_with_obstacles(launch):
     """400 free-running steps with on-device random actions: every step's
     action, reward, done flags and observation, and the final state, equal
@@ -169,15 +171,53 @@ def test_q_rollout_with_obstacles(rows):
     _assert_state_equal(g, o, K)
 
 
-def test_pipelined_and_split_rollouts_refuse_obstacles():
+def test_split_rollout_refuses_obstacles():
     from paper_2305_04180_gb300._lib import SgError
 
     g, _, _ = _w_pair(n=8)
     with pytest.raises(SgError):
-        g.set_launch(kernel="pipe", warps_per_block=8, obs_warps=7, order="map")
-    with pytest.raises(SgError):
         g.set_launch(kernel="split", warps_per_block=8, warps_per_env=2)
     assert g.launch_config()["kernel"] == "grid"
+
+
+@pytest.mark.parametrize("cfg", [dict(warps_per_block=8, obs_warps=7),
+                                 dict(warps_per_block=16, obs_warps=3, order="map", segment=32)])
+def test_pipelined_rollout_with_obstacles_and_frequent_episode_ends(cfg):
+    """The pipelined rollout's pose warp runs the discs ahead with the pose
+    chain and restarts after every episode end inside a chunk: eight fast
+    discs on small maps, truncation every 37 steps (scans of the pre-reset
+    discs), collisions with discs and walls.  Every step's action, reward,
+    done flags and observation and the final state equal the oracle's."""
+    p = base_params(n_beams=32, t_max=37, n_dyn=8, dyn_radius=10.0, dyn_speed_lo=40.0, dyn_speed_hi=300.0,
+                    dyn_keepout=15.0, **DR_RANGES)
+    maps = [make_map(31, 128), random_tiny_map(32, 70, 70, 0.12), make_map(33, 256)]
+    n = 48
+    env_map = (np.arange(n) % 3).astype(np.int32)
+    g, o = _pair(p, maps, env_map)
+    g.set_launch(kernel="pipe", **cfg)
+    g.reset()
+    o.reset()
+    K = 300
+    obs = g.new_obs()
+    obs_seq = torch.empty((K, n, g.obs_dim), dtype=torch.float32, device="cuda")
+    act = torch.empty((K, n), dtype=torch.uint8, device="cuda")
+    rew = torch.empty((K, n), dtype=torch.float32, device="cuda")
+    done = torch.empty((K, n), dtype=torch.uint8, device="cuda")
+    g.rollout(K, obs=obs, obs_seq=obs_seq, act_seq=act, rew_seq=rew, done_seq=done)
+    assert g.status() == 0
+    act, rew, done, obs_seq = act.cpu().numpy(), rew.cpu().numpy(), done.cpu().numpy(), obs_seq.cpu().numpy()
+    kinds = np.zeros(3, int)
+    for k in range(K):
+        a = o.random_actions(k)
+        assert np.array_equal(act[k], a), k
+        oobs, orew, odone, _ = o.step(a)
+        assert np.array_equal(done[k], odone), k
+        assert np.array_equal(bits(rew[k]), bits(orew)), k
+        assert np.array_equal(bits(obs_seq[k]), bits(oobs)), k
+        kinds += [int(((odone & 1) != 0).sum()), int(((odone & 2) != 0).sum()), int((odone == 4).sum())]
+    assert np.array_equal(bits(obs.cpu().numpy()), bits(oobs))
+    _assert_state_equal(g, o, K)
+    assert kinds[0] > 50 and kinds[2] > 50
 
 
 def test_checkpoint_resume_with_obstacles():
