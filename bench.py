@@ -381,6 +381,24 @@ def run_extras(flush, which):
     h = torch.relu(torch.relu(x @ W1.T + b1) @ W2.T + b2) @ W3.T + b3
     qref = h[:, :1] + h[:, 1:] - h[:, 1:].mean(dim=1, keepdim=True)
     out["qnet_rollout"]["max_rel_q_error_vs_fp64"] = float((qg - qref).abs().max() / qref.abs().max())
+    # batched forward on the tcgen05 kernel (sg_qnet_forward), 2^20 rows:
+    # algorithmic FLOPs of the 37-256-256-6 network per row against the
+    # measured dense BF16 peak
+    Mf = 1 << 20
+    xf = torch.rand((Mf, sim.obs_dim), device="cuda") * 2 - 1
+    qf = torch.empty((Mf, 5), device="cuda")
+    for _ in range(3):
+        q.forward(xf, out=qf)
+    ms_f = _time_cuda(lambda: q.forward(xf, out=qf), 10, flush)
+    flop_row = 2.0 * (sim.obs_dim * 256 + 256 * 256 + 256 * 6)
+    peak_tf = _measured_peaks()["bf16_tflops"]
+    out["qnet_forward"] = {"rows": Mf, "us": ms_f * 1e3, "rows_per_s": Mf / (ms_f / 1e3),
+                           "roofline": {"bound": "tensor", "achieved": Mf * flop_row / (ms_f / 1e3) / 1e12,
+                                        "peak": peak_tf, "unit": "TFLOP/s",
+                                        "frac": Mf * flop_row / (ms_f / 1e3) / 1e12 / peak_tf,
+                                        "flop_per_row": flop_row},
+                           "kernel": "k_qnet_forward_tc (tcgen05, TMEM accumulators)", "gpu_launches_per_call": 1}
+    del xf, qf
     # learner: one TD step at batch 256 from the ring filled above
     loss = torch.zeros(1, device="cuda")
     ft = lambda: q.train_step(rp, w.extra["batch"], gamma=w.extra["gamma"], lr=w.extra["lr"],  # noqa: E731

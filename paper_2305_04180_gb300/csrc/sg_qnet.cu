@@ -28,6 +28,7 @@
 #include "sg_device.cuh"
 #include "sg_host.h"
 #include "sg_mma.cuh"
+#include "sg_tc.cuh"
 #include "sparrow_gb.h"
 
 using namespace sg;
@@ -362,31 +363,201 @@ __device__ __forceinline__ void obs_to_tile(bf16* row, const ObsRegs& o, int B, 
   if (lane < 5) row[B + lane] = __float2bfloat16_rn(o.ex);
 }
 
-// Standalone batched inference: Q[M][5] of obs[M][n_in].  16 rows per CTA.
-__global__ void __launch_bounds__(kThreads, 1) k_qnet_forward(const uint8_t* __restrict__ img, ImgLayout L,
-                                                              const float* __restrict__ obs, int M,
-                                                              float* __restrict__ qout) {
-  extern __shared__ __align__(16) uint8_t smem[];
-  uint8_t* sw = smem;
-  bf16* X = reinterpret_cast<bf16*>(smem + L.bytes);
-  bf16* H1 = X + kTile * L.ld1;
-  bf16* H2 = H1 + kTile * kLdh;
-  float* O = reinterpret_cast<float*>(H2 + kTile * kLdh);
-  stage_image(sw, img, L.bytes);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row = blockIdx.x * kTile + warp;
-  for (int k = lane; k < L.ld1; k += 32) {
-    const float v = (row < M && k < L.n_in) ? obs[(long long)row * L.n_in + k] : 0.0f;
-    X[warp * L.ld1 + k] = __float2bfloat16_rn(v);
+// ------------------------------------------------ tcgen05 batched forward
+// Q[M][5] of obs[M][n_in] with 128 rows per CTA on the fifth-generation
+// tensor cores: the BF16 operands sit in shared memory in the canonical
+// K-major layout (sg_tc.cuh), one thread issues the MMAs, the FP32
+// accumulators live in tensor memory (256 columns), and the four warps read
+// their 32 rows back for the bias / ReLU / BF16 epilogue, which writes the
+// next layer's A operand.  Layer 2's weights are staged in two halves of 128
+// output units (the second half once the first half's MMAs are complete), so
+// that the CTA fits in shared memory:
+//   X 128 x k1 | W1 256 x k1 | H 128 x 256 (H1, then H2) | W2 half 128 x 256 | W3 16 x 256.
+// Same BF16 recipe as the mma.sync kernels (BF16 inputs, weights and hidden
+// activations, FP32 sums); only the summation order differs.
+constexpr int kTcRows = 128;
+constexpr uint32_t kTcTries = 1u << 24;  // bound of every mbarrier wait (polls)
+// The launch takes the whole shared memory of an SM (one CTA per SM either
+// way), so that every descriptor-addressed byte lies inside the allocation.
+constexpr uint32_t kTcSmemLaunch = 227u * 1024u - 2048u;
+
+struct TcSmem {
+  uint32_t x, w1, h, w2, w3, bytes;
+};
+__host__ __device__ inline uint32_t tc_up(uint32_t v) { return (v + 1023u) & ~1023u; }
+__host__ __device__ inline TcSmem tc_smem(int k1) {
+  TcSmem t;
+  t.x = 0;
+  t.w1 = tc_up(t.x + (uint32_t)(kTcRows * k1 * 2));
+  t.h = tc_up(t.w1 + (uint32_t)(kHid * k1 * 2));
+  t.w2 = tc_up(t.h + (uint32_t)(kTcRows * kHid * 2));
+  t.w3 = tc_up(t.w2 + (uint32_t)(128 * kHid * 2));
+  t.bytes = tc_up(t.w3 + (uint32_t)(16 * kHid * 2));
+  return t;
+}
+
+// Rows [128 h, 128 h + 128) of W2 (image rows of kLdh elements) into the
+// canonical layout of a 128-row operand.
+__device__ __forceinline__ void tc_stage_w2_half(const uint8_t* __restrict__ img, const ImgLayout& L, uint8_t* w2s,
+                                                 int h, int tid) {
+  for (int c = tid; c < 128 * (kHid / 8); c += kTcRows) {
+    const int n = c % 128, kg = c / 128;
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(img + L.w2 + ((size_t)(128 * h + n) * kLdh + kg * 8) * 2));
+    *reinterpret_cast<uint4*>(w2s + kmajor_offset(n, kg * 8, 128)) = v;
   }
+}
+
+// Hidden-layer epilogue of this thread's row r: columns [0, 256) of the
+// accumulator plus bias, ReLU, rounded to BF16 into the H operand.
+__device__ __forceinline__ void tc_epilogue_hidden(uint32_t tacc, const float* __restrict__ bias, uint8_t* hs,
+                                                   int warp, int lane) {
+  const int r = warp * 32 + lane;
+  for (int c = 0; c < kHid; c += 32) {
+    float v[32];
+    tmem_ld32(tacc + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      uint32_t w[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int k = c + 8 * g + 2 * j;
+        w[j] = pack_bf16x2(fmaxf(v[8 * g + 2 * j] + __ldg(bias + k), 0.f),
+                           fmaxf(v[8 * g + 2 * j + 1] + __ldg(bias + k + 1), 0.f));
+      }
+      *reinterpret_cast<uint4*>(hs + kmajor_offset(r, c + 8 * g, kTcRows)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+}
+
+// Issue one layer: D[tacc] = A (R = 128 rows) x B (Rb rows)^T over K, then
+// commit to the barrier (thread 0 only).
+__device__ __forceinline__ void tc_layer(uint32_t tacc, const uint8_t* a, const uint8_t* b, int Rb, int K,
+                                         uint64_t* bar) {
+  const uint32_t idesc = idesc_bf16_f32(kTcRows, Rb);
+  const uint32_t sa = smem_u32(a), sb = smem_u32(b);
+  const uint32_t la = kTcRows * 16, lb = (uint32_t)Rb * 16;
+  for (int ks = 0; ks < K / 16; ++ks)
+    tc_mma_bf16(tacc, smem_desc(sa + (uint32_t)ks * 2 * la, la, 128), smem_desc(sb + (uint32_t)ks * 2 * lb, lb, 128),
+                idesc, ks > 0 ? 1u : 0u);
+  tc_commit(bar);
+}
+
+__global__ void __launch_bounds__(kTcRows, 1) k_qnet_forward_tc(const uint8_t* __restrict__ img, ImgLayout L,
+                                                                const float* __restrict__ obs, int M,
+                                                                float* __restrict__ qout) {
+  extern __shared__ __align__(1024) uint8_t tsm[];
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tslot;
+  const TcSmem T = tc_smem(L.k1);
+  uint8_t* xs = tsm + T.x;
+  uint8_t* w1s = tsm + T.w1;
+  uint8_t* hs = tsm + T.h;
+  uint8_t* w2s = tsm + T.w2;
+  uint8_t* w3s = tsm + T.w3;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int grow = blockIdx.x * kTcRows + tid;  // this thread's row
+  const int K1 = L.k1;
+  if (warp == 0) tmem_alloc(&tslot, 256);
+  if (tid == 0) mbar_init(&bar, 1);
+  // X tile (row tid), W1, W3 (rows 8..15 zero)
+  for (int kg = 0; kg < K1 / 8; ++kg) {
+    float v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int k = kg * 8 + j;
+      v[j] = (grow < M && k < L.n_in) ? __ldg(obs + (long long)grow * L.n_in + k) : 0.0f;
+    }
+    *reinterpret_cast<uint4*>(xs + kmajor_offset(tid, kg * 8, kTcRows)) =
+        make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
+                   pack_bf16x2(v[6], v[7]));
+  }
+  for (int c = tid; c < kHid * (K1 / 8); c += kTcRows) {
+    const int n = c % kHid, kg = c / kHid;
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(img + L.w1 + ((size_t)n * L.ld1 + kg * 8) * 2));
+    *reinterpret_cast<uint4*>(w1s + kmajor_offset(n, kg * 8, kHid)) = v;
+  }
+  for (int c = tid; c < 16 * (kHid / 8); c += kTcRows) {
+    const int n = c % 16, kg = c / 16;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (n < kOutPad) v = __ldg(reinterpret_cast<const uint4*>(img + L.w3 + ((size_t)n * kLdh + kg * 8) * 2));
+    *reinterpret_cast<uint4*>(w3s + kmajor_offset(n, kg * 8, 16)) = v;
+  }
+  fence_async_smem();
+  tc_fence_before();
   __syncthreads();
-  const QW w = qw_at(sw, L);
-  mlp_tile(w, X, H1, H2, O, warp, lane);
-  if (row < M && lane == 0) {
-    float qv[5];
-    greedy_action(O + warp * kOutPad, qv, L.plain);
-    for (int a = 0; a < 5; ++a) qout[(long long)row * 5 + a] = qv[a];
+  tc_fence_after();
+  const uint32_t tacc = tslot;
+  const float* b1 = reinterpret_cast<const float*>(img + L.b1);
+  const float* b2 = reinterpret_cast<const float*>(img + L.b2);
+  const float* b3 = reinterpret_cast<const float*>(img + L.b3);
+  uint32_t phase = 0;
+  bool ok = true;
+  // layer 1: H1 accumulators in columns 0..255; W2's first half loads meanwhile
+  if (tid == 0) tc_layer(tacc, xs, w1s, kHid, K1, &bar);
+  tc_stage_w2_half(img, L, w2s, 0, tid);
+  ok = __syncthreads_and(mbar_wait(&bar, phase, kTcTries));
+  if (ok) phase ^= 1u;
+  if (ok) {
+    tc_fence_after();
+    tc_epilogue_hidden(tacc, b1, hs, warp, lane);
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    // layer 2, units 0..127 into columns 0..127
+    if (tid == 0) tc_layer(tacc, hs, w2s, 128, kHid, &bar);
+    ok = __syncthreads_and(mbar_wait(&bar, phase, kTcTries));
+    if (ok) phase ^= 1u;
   }
+  if (ok) {
+    // the first half is consumed: units 128..255 into columns 128..255
+    tc_stage_w2_half(img, L, w2s, 1, tid);
+    fence_async_smem();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0) tc_layer(tacc + 128u, hs, w2s, 128, kHid, &bar);
+    ok = __syncthreads_and(mbar_wait(&bar, phase, kTcTries));
+    if (ok) phase ^= 1u;
+  }
+  if (ok) {
+    tc_fence_after();
+    tc_epilogue_hidden(tacc, b2, hs, warp, lane);  // H2 over H1 (layer 2 is complete)
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    // head: 16 columns (6 used)
+    if (tid == 0) tc_layer(tacc, hs, w3s, 16, kHid, &bar);
+    ok = __syncthreads_and(mbar_wait(&bar, phase, kTcTries));
+    if (ok) phase ^= 1u;
+  }
+  float v[32];
+  if (ok) {
+    tc_fence_after();
+    tmem_ld32(tacc + ((uint32_t)(warp * 32) << 16), v);
+  }
+  if (grow < M) {
+    float qv[5];
+    if (ok) {
+      float o[kOut];
+#pragma unroll
+      for (int j = 0; j < kOut; ++j) o[j] = v[j] + __ldg(b3 + j);
+      greedy_action(o, qv, L.plain);
+    } else {
+      // a wait ran out: the row's values are marked invalid
+#pragma unroll
+      for (int a = 0; a < 5; ++a) qv[a] = __int_as_float(0x7fc00000);
+    }
+#pragma unroll
+    for (int a = 0; a < 5; ++a) qout[(long long)grow * 5 + a] = qv[a];
+  }
+  // free the tensor memory once no MMA is in flight (bounded: the phase that
+  // ran out gets one more wait)
+  if (!ok) mbar_wait(&bar, phase, kTcTries);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_free(tacc, 256);
 }
 
 // VEM eps-greedy rollout with the network fused in: per step, the 16 envs of
@@ -892,7 +1063,7 @@ extern "C" int sg_qnet_create(int32_t n_in, int32_t arch, int32_t max_batch, uin
   // the widest supported input so that a narrower network created later
   // cannot lower it below what a wider one launches with.
   const ImgLayout widest = img_layout(69);
-  if ((rc = set_smem_attr((const void*)k_qnet_forward, fwd_smem(widest))) ||
+  if ((rc = set_smem_attr((const void*)k_qnet_forward_tc, kTcSmemLaunch)) ||
       (rc = set_smem_attr((const void*)k_rollout_q<1, false>, fwd_smem(widest))) ||
       (rc = set_smem_attr((const void*)k_rollout_q<2, false>, fwd_smem(widest, 32))) ||
       (rc = set_smem_attr((const void*)k_rollout_q<1, true>, fwd_smem(widest))) ||
@@ -1010,7 +1181,8 @@ extern "C" int sg_qnet_set_optimizer(sg_qnet_t q, const float* m_host, const flo
 
 extern "C" int sg_qnet_forward(sg_qnet_t q, const float* obs_dev, int32_t M, float* q_dev, sg_stream_t stream) {
   if (!q || !obs_dev || !q_dev || M < 1) return SG_E_INVAL;
-  k_qnet_forward<<<(M + kTile - 1) / kTile, kThreads, fwd_smem(q->IL), stream>>>(q->img, q->IL, obs_dev, M, q_dev);
+  k_qnet_forward_tc<<<(M + kTcRows - 1) / kTcRows, kTcRows, kTcSmemLaunch, stream>>>(q->img, q->IL, obs_dev, M,
+                                                                                    q_dev);
   SG_CUDA(cudaGetLastError());
   return SG_OK;
 }
