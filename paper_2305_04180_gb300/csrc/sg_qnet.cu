@@ -18,6 +18,7 @@
 // C ABI shows each network's own (compact) order.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -146,6 +147,8 @@ struct sg_qnet {
   float* y = nullptr;        // [max_batch] TD targets
   int* idx = nullptr;        // [max_batch] sampled ring entries
   int rollout_mt = 0;        // m-tiles per CTA of the fused rollout (0 = choose by waves)
+  uint8_t* img_tc = nullptr; // the online weights in the tensor cores' shared-memory layout (batched forward)
+  int sms = 0;               // multiprocessors of the device (persistent grids)
 };
 
 // --------------------------------------------------------------- kernels
@@ -364,18 +367,23 @@ __device__ __forceinline__ void obs_to_tile(bf16* row, const ObsRegs& o, int B, 
 }
 
 // ------------------------------------------------ tcgen05 batched forward
-// Q[M][5] of obs[M][n_in] with 128 rows per CTA on the fifth-generation
-// tensor cores: the BF16 operands sit in shared memory in the canonical
-// K-major layout (sg_tc.cuh), one thread issues the MMAs, the FP32
-// accumulators live in tensor memory (256 columns), and the four warps read
-// their 32 rows back for the bias / ReLU / BF16 epilogue, which writes the
-// next layer's A operand.  Layer 2's weights are staged in two halves of 128
-// output units (the second half once the first half's MMAs are complete), so
-// that the CTA fits in shared memory:
-//   X 128 x k1 | W1 256 x k1 | H 128 x 256 (H1, then H2) | W2 half 128 x 256 | W3 16 x 256.
-// Same BF16 recipe as the mma.sync kernels (BF16 inputs, weights and hidden
-// activations, FP32 sums); only the summation order differs.
+// Q[M][5] of obs[M][n_in] on the fifth-generation tensor cores, 128 rows per
+// tile.  A persistent CTA (one per SM) keeps W1 and W3 in shared memory and
+// streams the two 128-unit halves of W2 per tile; all weights arrive by bulk
+// asynchronous copies (TMA) from a copy of the online network in the
+// tensor cores' shared-memory layout (k_tc_image), completing on an
+// mbarrier.  Per tile: the threads convert the 128 input rows to BF16, one
+// thread issues the MMAs of a layer (tcgen05.mma, FP32 accumulators in 256
+// tensor-memory columns) and commits them to a second mbarrier, the eight
+// warps read the accumulators back (tcgen05.ld; warps w and w + 4 take the
+// rows of lane quarter w % 4 and half of the columns each) for the bias /
+// ReLU / BF16 epilogue that writes the next layer's A operand.  Shared memory:
+//   X 128 x k1 | W1 256 x k1 | H 128 x 256 (H1, then H2) | W2 half 128 x 256 | W3 16 x 256
+// in the canonical K-major layout of sg_tc.cuh.  Same BF16 recipe as the
+// mma.sync kernels (BF16 inputs, weights and hidden activations, FP32 sums);
+// only the summation order differs.
 constexpr int kTcRows = 128;
+constexpr int kTcThreads = 256;  // 8 warps: warps w and w + 4 share lane quarter w % 4 and split the columns
 constexpr uint32_t kTcTries = 1u << 24;  // bound of every mbarrier wait (polls)
 // The launch takes the whole shared memory of an SM (one CTA per SM either
 // way), so that every descriptor-addressed byte lies inside the allocation.
@@ -395,26 +403,56 @@ __host__ __device__ inline TcSmem tc_smem(int k1) {
   t.bytes = tc_up(t.w3 + (uint32_t)(16 * kHid * 2));
   return t;
 }
+// The weight copy in global memory: blocks identical to their shared-memory
+// images, so that each is one bulk copy.
+struct TcImg {
+  uint32_t w1, w2a, w2b, w3, bytes;
+};
+__host__ __device__ inline TcImg tc_img(int k1) {
+  TcImg t;
+  t.w1 = 0;
+  t.w2a = (uint32_t)(kHid * k1 * 2);
+  t.w2b = t.w2a + 128u * kHid * 2u;
+  t.w3 = t.w2b + 128u * kHid * 2u;
+  t.bytes = t.w3 + 16u * kHid * 2u;
+  return t;
+}
 
-// Rows [128 h, 128 h + 128) of W2 (image rows of kLdh elements) into the
-// canonical layout of a 128-row operand.
-__device__ __forceinline__ void tc_stage_w2_half(const uint8_t* __restrict__ img, const ImgLayout& L, uint8_t* w2s,
-                                                 int h, int tid) {
-  for (int c = tid; c < 128 * (kHid / 8); c += kTcRows) {
-    const int n = c % 128, kg = c / 128;
-    const uint4 v = __ldg(reinterpret_cast<const uint4*>(img + L.w2 + ((size_t)(128 * h + n) * kLdh + kg * 8) * 2));
-    *reinterpret_cast<uint4*>(w2s + kmajor_offset(n, kg * 8, 128)) = v;
+// The online weights from the BF16 image (rows of ld1 / kLdh elements) into
+// the canonical layout: W1 (256 rows), W2 rows 0..127 and 128..255 (two
+// 128-row operands), W3 (16 rows, 6 used).
+__global__ void k_tc_image(const uint8_t* __restrict__ img, ImgLayout L, uint8_t* __restrict__ out) {
+  const TcImg T = tc_img(L.k1);
+  const int n1 = kHid * (L.k1 / 8), n2 = kHid * (kHid / 8), n3 = 16 * (kHid / 8);
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n1 + n2 + n3; c += gridDim.x * blockDim.x) {
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    uint32_t dst;
+    if (c < n1) {
+      const int n = c % kHid, kg = c / kHid;
+      v = __ldg(reinterpret_cast<const uint4*>(img + L.w1 + ((size_t)n * L.ld1 + kg * 8) * 2));
+      dst = T.w1 + kmajor_offset(n, kg * 8, kHid);
+    } else if (c < n1 + n2) {
+      const int j = c - n1, n = j % kHid, kg = j / kHid;
+      v = __ldg(reinterpret_cast<const uint4*>(img + L.w2 + ((size_t)n * kLdh + kg * 8) * 2));
+      dst = n < 128 ? T.w2a + kmajor_offset(n, kg * 8, 128) : T.w2b + kmajor_offset(n - 128, kg * 8, 128);
+    } else {
+      const int j = c - n1 - n2, n = j % 16, kg = j / 16;
+      if (n < kOutPad) v = __ldg(reinterpret_cast<const uint4*>(img + L.w3 + ((size_t)n * kLdh + kg * 8) * 2));
+      dst = T.w3 + kmajor_offset(n, kg * 8, 16);
+    }
+    *reinterpret_cast<uint4*>(out + dst) = v;
   }
 }
 
-// Hidden-layer epilogue of this thread's row r: columns [0, 256) of the
-// accumulator plus bias, ReLU, rounded to BF16 into the H operand.
+// Hidden-layer epilogue: this thread's row r = 32 (warp % 4) + lane, columns
+// [128 (warp / 4), + 128) of the accumulator plus bias, ReLU, rounded to BF16
+// into the H operand.
 __device__ __forceinline__ void tc_epilogue_hidden(uint32_t tacc, const float* __restrict__ bias, uint8_t* hs,
                                                    int warp, int lane) {
-  const int r = warp * 32 + lane;
-  for (int c = 0; c < kHid; c += 32) {
+  const int quarter = warp & 3, r = quarter * 32 + lane, c0 = (warp >> 2) * 128;
+  for (int c = c0; c < c0 + 128; c += 32) {
     float v[32];
-    tmem_ld32(tacc + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+    tmem_ld32(tacc + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c, v);
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
       uint32_t w[4];
@@ -429,7 +467,7 @@ __device__ __forceinline__ void tc_epilogue_hidden(uint32_t tacc, const float* _
   }
 }
 
-// Issue one layer: D[tacc] = A (R = 128 rows) x B (Rb rows)^T over K, then
+// Issue one layer: D[tacc] = A (128 rows) x B (Rb rows)^T over K, then
 // commit to the barrier (thread 0 only).
 __device__ __forceinline__ void tc_layer(uint32_t tacc, const uint8_t* a, const uint8_t* b, int Rb, int K,
                                          uint64_t* bar) {
@@ -442,118 +480,180 @@ __device__ __forceinline__ void tc_layer(uint32_t tacc, const uint8_t* a, const 
   tc_commit(bar);
 }
 
-__global__ void __launch_bounds__(kTcRows, 1) k_qnet_forward_tc(const uint8_t* __restrict__ img, ImgLayout L,
-                                                                const float* __restrict__ obs, int M,
-                                                                float* __restrict__ qout) {
-  extern __shared__ __align__(1024) uint8_t tsm[];
-  __shared__ uint64_t bar;
-  __shared__ uint32_t tslot;
-  const TcSmem T = tc_smem(L.k1);
-  uint8_t* xs = tsm + T.x;
-  uint8_t* w1s = tsm + T.w1;
-  uint8_t* hs = tsm + T.h;
-  uint8_t* w2s = tsm + T.w2;
-  uint8_t* w3s = tsm + T.w3;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int grow = blockIdx.x * kTcRows + tid;  // this thread's row
-  const int K1 = L.k1;
-  if (warp == 0) tmem_alloc(&tslot, 256);
-  if (tid == 0) mbar_init(&bar, 1);
-  // X tile (row tid), W1, W3 (rows 8..15 zero)
-  for (int kg = 0; kg < K1 / 8; ++kg) {
+// Input rows of a tile into the X operand (BF16, zero padded); the two
+// threads of a row take alternate 8-column groups.
+__device__ __forceinline__ void tc_load_x(uint8_t* xs, const float* __restrict__ obs, const ImgLayout& L, int M,
+                                          int tile, int tid) {
+  const int row = tid & (kTcRows - 1), grow = tile * kTcRows + row;
+  for (int kg = tid >> 7; kg < L.k1 / 8; kg += 2) {
     float v[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const int k = kg * 8 + j;
       v[j] = (grow < M && k < L.n_in) ? __ldg(obs + (long long)grow * L.n_in + k) : 0.0f;
     }
-    *reinterpret_cast<uint4*>(xs + kmajor_offset(tid, kg * 8, kTcRows)) =
-        make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
-                   pack_bf16x2(v[6], v[7]));
-  }
-  for (int c = tid; c < kHid * (K1 / 8); c += kTcRows) {
-    const int n = c % kHid, kg = c / kHid;
-    const uint4 v = __ldg(reinterpret_cast<const uint4*>(img + L.w1 + ((size_t)n * L.ld1 + kg * 8) * 2));
-    *reinterpret_cast<uint4*>(w1s + kmajor_offset(n, kg * 8, kHid)) = v;
-  }
-  for (int c = tid; c < 16 * (kHid / 8); c += kTcRows) {
-    const int n = c % 16, kg = c / 16;
-    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-    if (n < kOutPad) v = __ldg(reinterpret_cast<const uint4*>(img + L.w3 + ((size_t)n * kLdh + kg * 8) * 2));
-    *reinterpret_cast<uint4*>(w3s + kmajor_offset(n, kg * 8, 16)) = v;
+    *reinterpret_cast<uint4*>(xs + kmajor_offset(row, kg * 8, kTcRows)) =
+        make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
   }
   fence_async_smem();
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_qnet_forward_tc(const uint8_t* __restrict__ img,
+                                                                const uint8_t* __restrict__ timg, ImgLayout L,
+                                                                const float* __restrict__ obs, int M,
+                                                                float* __restrict__ qout) {
+  extern __shared__ __align__(1024) uint8_t tsm[];
+  __shared__ uint64_t bar_mma, bar_ld;
+  __shared__ uint32_t tslot;
+  const TcSmem T = tc_smem(L.k1);
+  const TcImg G = tc_img(L.k1);
+  uint8_t* xs = tsm + T.x;
+  uint8_t* w1s = tsm + T.w1;
+  uint8_t* hs = tsm + T.h;
+  uint8_t* w2s = tsm + T.w2;
+  uint8_t* w3s = tsm + T.w3;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int K1 = L.k1;
+  const int ntiles = (M + kTcRows - 1) / kTcRows;
+  const float* b1 = reinterpret_cast<const float*>(img + L.b1);
+  const float* b2 = reinterpret_cast<const float*>(img + L.b2);
+  const float* b3 = reinterpret_cast<const float*>(img + L.b3);
+  if (warp == 0) tmem_alloc(&tslot, 256);
+  if (tid == 0) {
+    mbar_init(&bar_mma, 1);
+    mbar_init(&bar_ld, 1);
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tacc = tslot;
-  const float* b1 = reinterpret_cast<const float*>(img + L.b1);
-  const float* b2 = reinterpret_cast<const float*>(img + L.b2);
-  const float* b3 = reinterpret_cast<const float*>(img + L.b3);
-  uint32_t phase = 0;
+  bool ld_out = (int)blockIdx.x < ntiles, mma_out = false;  // completions still to come
+  if (tid == 0 && ld_out) {
+    // resident W1 and W3, and the first tile's W2 half 0
+    mbar_expect_tx(&bar_ld, G.w2a + 128u * kHid * 2u + 16u * kHid * 2u);
+    bulk_g2s(w1s, timg + G.w1, G.w2a, &bar_ld);
+    bulk_g2s(w3s, timg + G.w3, 16u * kHid * 2u, &bar_ld);
+    bulk_g2s(w2s, timg + G.w2a, 128u * kHid * 2u, &bar_ld);
+  }
+  uint32_t pm = 0, pl = 0;  // phases of the two barriers
   bool ok = true;
-  // layer 1: H1 accumulators in columns 0..255; W2's first half loads meanwhile
-  if (tid == 0) tc_layer(tacc, xs, w1s, kHid, K1, &bar);
-  tc_stage_w2_half(img, L, w2s, 0, tid);
-  ok = __syncthreads_and(mbar_wait(&bar, phase, kTcTries));
-  if (ok) phase ^= 1u;
-  if (ok) {
-    tc_fence_after();
-    tc_epilogue_hidden(tacc, b1, hs, warp, lane);
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    // layer 2, units 0..127 into columns 0..127
-    if (tid == 0) tc_layer(tacc, hs, w2s, 128, kHid, &bar);
-    ok = __syncthreads_and(mbar_wait(&bar, phase, kTcTries));
-    if (ok) phase ^= 1u;
-  }
-  if (ok) {
-    // the first half is consumed: units 128..255 into columns 128..255
-    tc_stage_w2_half(img, L, w2s, 1, tid);
-    fence_async_smem();
-    __syncthreads();
-    tc_fence_after();
-    if (tid == 0) tc_layer(tacc + 128u, hs, w2s, 128, kHid, &bar);
-    ok = __syncthreads_and(mbar_wait(&bar, phase, kTcTries));
-    if (ok) phase ^= 1u;
-  }
-  if (ok) {
-    tc_fence_after();
-    tc_epilogue_hidden(tacc, b2, hs, warp, lane);  // H2 over H1 (layer 2 is complete)
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    // head: 16 columns (6 used)
-    if (tid == 0) tc_layer(tacc, hs, w3s, 16, kHid, &bar);
-    ok = __syncthreads_and(mbar_wait(&bar, phase, kTcTries));
-    if (ok) phase ^= 1u;
-  }
-  float v[32];
-  if (ok) {
-    tc_fence_after();
-    tmem_ld32(tacc + ((uint32_t)(warp * 32) << 16), v);
-  }
-  if (grow < M) {
-    float qv[5];
+  const int row = tid & (kTcRows - 1);  // this thread's row of the tile
+  // the first tile's inputs; later tiles' inputs are converted while the
+  // previous tile's first layer-2 MMAs run (X is free once layer 1 is done)
+  if ((int)blockIdx.x < ntiles) tc_load_x(xs, obs, L, M, blockIdx.x, tid);
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int grow = tile * kTcRows + row;
     if (ok) {
-      float o[kOut];
-#pragma unroll
-      for (int j = 0; j < kOut; ++j) o[j] = v[j] + __ldg(b3 + j);
-      greedy_action(o, qv, L.plain);
-    } else {
-      // a wait ran out: the row's values are marked invalid
-#pragma unroll
-      for (int a = 0; a < 5; ++a) qv[a] = __int_as_float(0x7fc00000);
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+      // this tile's W2 half 0 (and on the first tile W1, W3) has arrived
+      ok = __syncthreads_and(mbar_wait(&bar_ld, pl, kTcTries));
+      if (ok) {
+        pl ^= 1u;
+        ld_out = false;
+      }
     }
+    if (ok) {
+      if (tid == 0) tc_layer(tacc, xs, w1s, kHid, K1, &bar_mma);
+      mma_out = true;
+      ok = __syncthreads_and(mbar_wait(&bar_mma, pm, kTcTries));
+      if (ok) {
+        pm ^= 1u;
+        mma_out = false;
+      }
+    }
+    if (ok) {
+      tc_fence_after();
+      tc_epilogue_hidden(tacc, b1, hs, warp, lane);
+      fence_async_smem();
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+      // layer 2, units 0..127 into columns 0..127
+      if (tid == 0) tc_layer(tacc, hs, w2s, 128, kHid, &bar_mma);
+      mma_out = true;
+      if (tile + (int)gridDim.x < ntiles) tc_load_x(xs, obs, L, M, tile + gridDim.x, tid);
+      ok = __syncthreads_and(mbar_wait(&bar_mma, pm, kTcTries));
+      if (ok) {
+        pm ^= 1u;
+        mma_out = false;
+      }
+    }
+    if (ok) {
+      // half 0 is consumed: half 1 over it, units 128..255 into columns 128..255
+      if (tid == 0) {
+        mbar_expect_tx(&bar_ld, 128u * kHid * 2u);
+        bulk_g2s(w2s, timg + G.w2b, 128u * kHid * 2u, &bar_ld);
+      }
+      ld_out = true;
+      ok = __syncthreads_and(mbar_wait(&bar_ld, pl, kTcTries));
+      if (ok) {
+        pl ^= 1u;
+        ld_out = false;
+      }
+    }
+    if (ok) {
+      if (tid == 0) tc_layer(tacc + 128u, hs, w2s, 128, kHid, &bar_mma);
+      mma_out = true;
+      ok = __syncthreads_and(mbar_wait(&bar_mma, pm, kTcTries));
+      if (ok) {
+        pm ^= 1u;
+        mma_out = false;
+      }
+    }
+    if (ok) {
+      // the next tile's W2 half 0 streams in while this tile finishes
+      if (tile + (int)gridDim.x < ntiles) {
+        if (tid == 0) {
+          mbar_expect_tx(&bar_ld, 128u * kHid * 2u);
+          bulk_g2s(w2s, timg + G.w2a, 128u * kHid * 2u, &bar_ld);
+        }
+        ld_out = true;
+      }
+      tc_fence_after();
+      tc_epilogue_hidden(tacc, b2, hs, warp, lane);  // H2 over H1 (layer 2 is complete)
+      fence_async_smem();
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+      // head: 16 columns (6 used)
+      if (tid == 0) tc_layer(tacc, hs, w3s, 16, kHid, &bar_mma);
+      mma_out = true;
+      ok = __syncthreads_and(mbar_wait(&bar_mma, pm, kTcTries));
+      if (ok) {
+        pm ^= 1u;
+        mma_out = false;
+      }
+    }
+    float v[32];
+    if (ok && warp < 4) {
+      tc_fence_after();
+      tmem_ld32(tacc + ((uint32_t)(warp * 32) << 16), v);
+    }
+    if (warp < 4 && grow < M) {
+      float qv[5];
+      if (ok) {
+        float o[kOut];
 #pragma unroll
-    for (int a = 0; a < 5; ++a) qout[(long long)grow * 5 + a] = qv[a];
+        for (int j = 0; j < kOut; ++j) o[j] = v[j] + __ldg(b3 + j);
+        greedy_action(o, qv, L.plain);
+      } else {
+        // a wait ran out: the row's values are marked invalid
+#pragma unroll
+        for (int a = 0; a < 5; ++a) qv[a] = __int_as_float(0x7fc00000);
+      }
+#pragma unroll
+      for (int a = 0; a < 5; ++a) qout[(long long)grow * 5 + a] = qv[a];
+    }
+    // the tensor memory and the X / H tiles are reused by the next tile
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
   }
-  // free the tensor memory once no MMA is in flight (bounded: the phase that
-  // ran out gets one more wait)
-  if (!ok) mbar_wait(&bar, phase, kTcTries);
+  // free the tensor memory once nothing is in flight (bounded waits)
+  if (mma_out) mbar_wait(&bar_mma, pm, kTcTries);
+  if (ld_out) mbar_wait(&bar_ld, pl, kTcTries);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -1004,6 +1104,7 @@ void free_qnet(sg_qnet* q) {
   cudaFree(q->partial);
   cudaFree(q->y);
   cudaFree(q->idx);
+  cudaFree(q->img_tc);
   delete q;
 }
 }  // namespace
@@ -1036,6 +1137,8 @@ extern "C" int sg_qnet_create(int32_t n_in, int32_t arch, int32_t max_batch, uin
   alloc((void**)&q->partial, nblk * (P + 1) * 4);
   alloc((void**)&q->y, (size_t)q->max_batch * 4);
   alloc((void**)&q->idx, (size_t)q->max_batch * 4);
+  alloc((void**)&q->img_tc, tc_img(q->IL.k1).bytes);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&q->sms, cudaDevAttrMultiProcessorCount, q->device);
   if (e != cudaSuccess) {
     free_qnet(q);
     sg_set_cuda_error(e, "cudaMalloc");
@@ -1181,8 +1284,12 @@ extern "C" int sg_qnet_set_optimizer(sg_qnet_t q, const float* m_host, const flo
 
 extern "C" int sg_qnet_forward(sg_qnet_t q, const float* obs_dev, int32_t M, float* q_dev, sg_stream_t stream) {
   if (!q || !obs_dev || !q_dev || M < 1) return SG_E_INVAL;
-  k_qnet_forward_tc<<<(M + kTcRows - 1) / kTcRows, kTcRows, kTcSmemLaunch, stream>>>(q->img, q->IL, obs_dev, M,
-                                                                                    q_dev);
+  // the online weights in the shared-memory layout, then a persistent grid
+  k_tc_image<<<44, 256, 0, stream>>>(q->img, q->IL, q->img_tc);
+  SG_CUDA(cudaGetLastError());
+  const int ntiles = (M + kTcRows - 1) / kTcRows;
+  k_qnet_forward_tc<<<std::min(ntiles, q->sms), kTcThreads, kTcSmemLaunch, stream>>>(q->img, q->img_tc, q->IL,
+                                                                                     obs_dev, M, q_dev);
   SG_CUDA(cudaGetLastError());
   return SG_OK;
 }

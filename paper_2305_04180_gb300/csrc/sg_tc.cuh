@@ -1,7 +1,8 @@
 // sg_tc.cuh -- fifth-generation tensor core (tcgen05) building blocks:
 // tensor-memory allocation, shared-memory matrix descriptors, the BF16 MMA
-// with an FP32 accumulator in tensor memory, commit to an mbarrier, bounded
-// mbarrier waits and tensor-memory loads.  Inline PTX (sm_100 family ISA).
+// with an FP32 accumulator in tensor memory, commit to an mbarrier, bulk
+// asynchronous copies into shared memory, bounded mbarrier waits and
+// tensor-memory loads.  Inline PTX (sm_100 family ISA).
 //
 // Operand layout in shared memory (both A and B "K-major", no swizzle): a
 // matrix of R rows (M or N) and K BF16 columns is stored as core matrices of
@@ -95,6 +96,21 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
     if (ok) return true;
   }
   return false;
+}
+
+// Bulk asynchronous copy (TMA engine) of `bytes` (a multiple of 16, both
+// addresses 16-byte aligned) from global to shared memory, completing as
+// transaction bytes on the mbarrier; expect_tx arms the barrier's current
+// phase with one arrival and the byte count of the copies that follow.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
 }
 
 // 32 consecutive FP32 columns of this thread's tensor-memory lane (the warp
