@@ -387,7 +387,7 @@ constexpr int kTcThreads = 256;  // 8 warps: warps w and w + 4 share lane quarte
 constexpr uint32_t kTcTries = 1u << 24;  // bound of every mbarrier wait (polls)
 // The launch takes the whole shared memory of an SM (one CTA per SM either
 // way), so that every descriptor-addressed byte lies inside the allocation.
-constexpr uint32_t kTcSmemLaunch = 227u * 1024u - 2048u;
+constexpr uint32_t kTcSmemLaunch = 227u * 1024u - 4096u;
 
 struct TcSmem {
   uint32_t x, w1, h, w2, w3, bytes;
@@ -447,7 +447,7 @@ __global__ void k_tc_image(const uint8_t* __restrict__ img, ImgLayout L, uint8_t
 // Hidden-layer epilogue: this thread's row r = 32 (warp % 4) + lane, columns
 // [128 (warp / 4), + 128) of the accumulator plus bias, ReLU, rounded to BF16
 // into the H operand.
-__device__ __forceinline__ void tc_epilogue_hidden(uint32_t tacc, const float* __restrict__ bias, uint8_t* hs,
+__device__ __forceinline__ void tc_epilogue_hidden(uint32_t tacc, const float* bias, uint8_t* hs,
                                                    int warp, int lane) {
   const int quarter = warp & 3, r = quarter * 32 + lane, c0 = (warp >> 2) * 128;
   for (int c = c0; c < c0 + 128; c += 32) {
@@ -459,8 +459,7 @@ __device__ __forceinline__ void tc_epilogue_hidden(uint32_t tacc, const float* _
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int k = c + 8 * g + 2 * j;
-        w[j] = pack_bf16x2(fmaxf(v[8 * g + 2 * j] + __ldg(bias + k), 0.f),
-                           fmaxf(v[8 * g + 2 * j + 1] + __ldg(bias + k + 1), 0.f));
+        w[j] = pack_bf16x2(fmaxf(v[8 * g + 2 * j] + bias[k], 0.f), fmaxf(v[8 * g + 2 * j + 1] + bias[k + 1], 0.f));
       }
       *reinterpret_cast<uint4*>(hs + kmajor_offset(r, c + 8 * g, kTcRows)) = make_uint4(w[0], w[1], w[2], w[3]);
     }
@@ -505,6 +504,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_qnet_forward_tc(const uint8_t
   extern __shared__ __align__(1024) uint8_t tsm[];
   __shared__ uint64_t bar_mma, bar_ld;
   __shared__ uint32_t tslot;
+  __shared__ float sb1[kHid], sb2[kHid], sb3[kOutPad];
   const TcSmem T = tc_smem(L.k1);
   const TcImg G = tc_img(L.k1);
   uint8_t* xs = tsm + T.x;
@@ -515,9 +515,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_qnet_forward_tc(const uint8_t
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int K1 = L.k1;
   const int ntiles = (M + kTcRows - 1) / kTcRows;
-  const float* b1 = reinterpret_cast<const float*>(img + L.b1);
-  const float* b2 = reinterpret_cast<const float*>(img + L.b2);
-  const float* b3 = reinterpret_cast<const float*>(img + L.b3);
+  for (int i = tid; i < kHid; i += kTcThreads) {
+    sb1[i] = __ldg(reinterpret_cast<const float*>(img + L.b1) + i);
+    sb2[i] = __ldg(reinterpret_cast<const float*>(img + L.b2) + i);
+  }
+  if (tid < kOutPad) sb3[tid] = __ldg(reinterpret_cast<const float*>(img + L.b3) + tid);
+  const float* b1 = sb1;
+  const float* b2 = sb2;
+  const float* b3 = sb3;
   if (warp == 0) tmem_alloc(&tslot, 256);
   if (tid == 0) {
     mbar_init(&bar_mma, 1);
@@ -636,7 +641,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_qnet_forward_tc(const uint8_t
       if (ok) {
         float o[kOut];
 #pragma unroll
-        for (int j = 0; j < kOut; ++j) o[j] = v[j] + __ldg(b3 + j);
+        for (int j = 0; j < kOut; ++j) o[j] = v[j] + b3[j];
         greedy_action(o, qv, L.plain);
       } else {
         // a wait ran out: the row's values are marked invalid
@@ -1085,11 +1090,19 @@ int set_smem_attr(const void* fn, size_t bytes) {
   return SG_OK;
 }
 
+// The online weights' copy in the tensor cores' layout follows every change
+// of the online image (stream-ordered, so also inside captured graphs).
+int refresh_tc_image(sg_qnet* q, cudaStream_t st) {
+  k_tc_image<<<44, 256, 0, st>>>(q->img, q->IL, q->img_tc);
+  SG_CUDA(cudaGetLastError());
+  return SG_OK;
+}
+
 int rebuild_image(sg_qnet* q, const float* th, uint8_t* img, cudaStream_t st) {
   const int n = image_elems(q->IL);
   k_build_image<<<(n + 255) / 256, 256, 0, st>>>(th, img, q->IL, q->PL);
   SG_CUDA(cudaGetLastError());
-  return SG_OK;
+  return img == q->img ? refresh_tc_image(q, st) : SG_OK;
 }
 
 void free_qnet(sg_qnet* q) {
@@ -1267,6 +1280,7 @@ extern "C" int sg_qnet_copy_params(sg_qnet_t dst, sg_qnet_t src, sg_stream_t str
   const size_t P = (size_t)src->PL.total;
   SG_CUDA(cudaMemcpyAsync(dst->master, src->master, P * 4, cudaMemcpyDeviceToDevice, stream));
   SG_CUDA(cudaMemcpyAsync(dst->img, src->img, (size_t)src->IL.bytes, cudaMemcpyDeviceToDevice, stream));
+  SG_CUDA(cudaMemcpyAsync(dst->img_tc, src->img_tc, tc_img(src->IL.k1).bytes, cudaMemcpyDeviceToDevice, stream));
   return SG_OK;
 }
 
@@ -1284,9 +1298,7 @@ extern "C" int sg_qnet_set_optimizer(sg_qnet_t q, const float* m_host, const flo
 
 extern "C" int sg_qnet_forward(sg_qnet_t q, const float* obs_dev, int32_t M, float* q_dev, sg_stream_t stream) {
   if (!q || !obs_dev || !q_dev || M < 1) return SG_E_INVAL;
-  // the online weights in the shared-memory layout, then a persistent grid
-  k_tc_image<<<44, 256, 0, stream>>>(q->img, q->IL, q->img_tc);
-  SG_CUDA(cudaGetLastError());
+  // a persistent grid over the 128-row tiles
   const int ntiles = (M + kTcRows - 1) / kTcRows;
   k_qnet_forward_tc<<<std::min(ntiles, q->sms), kTcThreads, kTcSmemLaunch, stream>>>(q->img, q->img_tc, q->IL,
                                                                                      obs_dev, M, q_dev);
@@ -1475,6 +1487,7 @@ extern "C" int sg_td_train_step(sg_qnet_t q, sg_replay_t rp, int32_t batch, floa
   k_adam<<<(P + 255) / 256, 256, 0, stream>>>(q->master, q->adam_m, q->adam_v, q->partial, nblk, q->PL, q->IL, q->img,
                                                q->step, lr, 0.9f, 0.999f, 1e-8f, loss_dev, grad_dev, batch);
   SG_CUDA(cudaGetLastError());
+  if (int rc = refresh_tc_image(q, stream)) return rc;
   if (lr > 0.0f) {
     k_step_advance<<<1, 1, 0, stream>>>(q->step);
     SG_CUDA(cudaGetLastError());
