@@ -357,10 +357,15 @@ int sg_qnet_get_optimizer(sg_qnet_t q, float* m_host, float* v_host, int64_t n, 
 int sg_qnet_set_optimizer(sg_qnet_t q, const float* m_host, const float* v_host, int64_t n, uint64_t steps);
 
 /*
- * Envs per CTA of the fused rollout: 16 or 32 (one warp each; the network's
- * BF16 weights take most of an SM's shared memory, so one CTA runs per SM),
- * or 0 (default) to take 32 when that needs fewer waves over the SMs.  The
- * results do not depend on it.
+ * Envs per CTA of the fused rollout: 16 or 32 (one warp each, the network on
+ * mma.sync tiles; the network's BF16 weights take most of an SM's shared
+ * memory, so one CTA runs per SM), 128 (the tcgen05 kernel: 4 envs per warp,
+ * the network as one 128-row tile on the fifth-generation tensor cores), or
+ * 0 (default): 128 when the envs fill every SM with 128-env CTAs and there
+ * are no moving obstacles, else 32 when that needs fewer waves than 16.
+ * The simulator values do not depend on it; the Q values of the tcgen05
+ * kernel differ in the FP32 summation order only (so greedy actions can
+ * differ where two actions' Q values are within that rounding).
  */
 int sg_qnet_set_rollout_rows(sg_qnet_t q, int32_t rows);
 

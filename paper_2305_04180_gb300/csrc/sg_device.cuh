@@ -920,6 +920,29 @@ __device__ __forceinline__ void write_row(float* row, float b0, float b1, const 
 }
 
 
+// The scan-free part of the observation of env i at its current state s (one
+// lane), into the scan-A fields of r: the first observation of a rollout
+// whose steps run lane_step.
+__device__ __forceinline__ void lane_observe(const DevCfg& c, const SimPtrs& p, int i, const Env& s,
+                                             StepScanRec& r) {
+  const int mid = p.env_map[i];
+  const MapDesc m = p.maps[mid];
+  const Layout L = layout_of(c, m);
+  const int nb = p.env_beams ? p.env_beams[i] : c.B;
+  const uint64_t nkey = sm_at(sm_at(c.seed, kStreamNoise), (uint64_t)i);
+  const GoalFrame g = goal_frame(L, s);
+  const uint64_t nka = sm_at(nkey, ((uint64_t)s.ep_id << 32) | s.ep_step);
+  r.ax = s.x, r.ay = s.y, r.aphi = s.phi, r.asigma = s.sigma;
+  r.anlo = (uint32_t)nka, r.anhi = (uint32_t)(nka >> 32);
+  for (int q = 0; q < 5; ++q) r.exa[q] = obs_extra(c, L, s, g, q);
+  r.rpart = 0.0f;
+  r.done = 0u;
+  r.map = mid;
+  r.env = i;
+  r.nb = nb;
+  r.stepb = c.fov / (float)(nb - 1);
+}
+
 // One step of one env per lane (sg_sim_step and the fused Q-net rollout):
 // delay, Eq. 5, Eq. 6, the collision test (map bounds and clearance per lane,
 // the bit rows for the envs that need them with the whole warp), arrival,

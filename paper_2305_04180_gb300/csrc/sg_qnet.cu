@@ -772,6 +772,291 @@ __global__ void __launch_bounds__(512 * MT, 1)
   }
 }
 
+// ---------------------------------------- tcgen05 fused eps-greedy rollout
+// For large env counts: 128 envs per CTA form one 128-row tile of the
+// network.  Per step the 32 warps run the network on the tile exactly as
+// k_qnet_forward_tc does (tcgen05 MMAs into tensor memory, epilogues split
+// over the 8 warps of each lane quarter, W2 halves streamed by bulk copies),
+// warps 0-3 take the greedy actions from the head, and then every warp steps
+// its 4 envs the way sg_sim_step does (lanes 0-3: the scalar part, lane_step;
+// the whole warp: the scans), writing the next observation as the tile's
+// BF16 row and the FP32 outputs and ring entries.  Same VEM draws, same
+// simulator values as k_rollout_q; the Q values differ from it only in the
+// summation order.
+constexpr int kQtEnvs = 128;
+constexpr int kQtWarps = 32;
+constexpr int kQtThreads = kQtWarps * 32;
+
+struct QtSmem {
+  uint32_t x, w1, h, w2, w3, rec, greedy, bytes;
+};
+__host__ __device__ inline QtSmem qt_smem(int k1) {
+  QtSmem t;
+  t.x = 0;
+  t.w1 = tc_up((uint32_t)(kQtEnvs * k1 * 2));
+  t.h = tc_up(t.w1 + (uint32_t)(kHid * k1 * 2));
+  t.w2 = tc_up(t.h + (uint32_t)(kQtEnvs * kHid * 2));
+  t.w3 = tc_up(t.w2 + (uint32_t)(128 * kHid * 2));
+  t.rec = tc_up(t.w3 + (uint32_t)(16 * kHid * 2));
+  t.greedy = t.rec + (uint32_t)(kQtEnvs * sizeof(StepScanRec));
+  t.bytes = tc_up(t.greedy + (uint32_t)(kQtEnvs * 4));
+  return t;
+}
+
+// Epilogue of a hidden layer by 32 warps: warp w takes the rows of lane
+// quarter w % 4 and columns [32 (w / 4), + 32).
+__device__ __forceinline__ void qt_epilogue(uint32_t tacc, const float* bias, uint8_t* hs, int warp, int lane) {
+  const int quarter = warp & 3, r = quarter * 32 + lane, c = (warp >> 2) * 32;
+  float v[32];
+  tmem_ld32(tacc + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c, v);
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    uint32_t w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int k = c + 8 * g + 2 * j;
+      w[j] = pack_bf16x2(fmaxf(v[8 * g + 2 * j] + bias[k], 0.f), fmaxf(v[8 * g + 2 * j + 1] + bias[k + 1], 0.f));
+    }
+    *reinterpret_cast<uint4*>(hs + kmajor_offset(r, c + 8 * g, kQtEnvs)) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+// This lane's share of an observation row into row r of the BF16 input tile.
+__device__ __forceinline__ void qt_obs_to_tile(uint8_t* xs, int r, float b0, float b1, float ex, int B, int lane) {
+  if (lane < B) *reinterpret_cast<bf16*>(xs + kmajor_offset(r, lane, kQtEnvs)) = __float2bfloat16_rn(b0);
+  if (lane + 32 < B) *reinterpret_cast<bf16*>(xs + kmajor_offset(r, lane + 32, kQtEnvs)) = __float2bfloat16_rn(b1);
+  if (lane < 5) *reinterpret_cast<bf16*>(xs + kmajor_offset(r, B + lane, kQtEnvs)) = __float2bfloat16_rn(ex);
+}
+
+__global__ void __launch_bounds__(kQtThreads, 1)
+    k_rollout_q_tc(const __grid_constant__ DevCfg c, SimPtrs p, const uint8_t* __restrict__ img,
+                   const uint8_t* __restrict__ timg, ImgLayout L, int K, const float* __restrict__ eps, ReplayDev rp,
+                   int use_replay, const int* __restrict__ order, float* __restrict__ obs_out,
+                   float* __restrict__ obs_seq, uint8_t* __restrict__ act_seq, float* __restrict__ rew_seq,
+                   uint8_t* __restrict__ done_seq) {
+  extern __shared__ __align__(1024) uint8_t tsm[];
+  __shared__ uint64_t bar_mma, bar_ld;
+  __shared__ uint32_t tslot;
+  __shared__ float sb1[kHid], sb2[kHid], sb3[kOutPad];
+  const QtSmem T = qt_smem(L.k1);
+  const TcImg G = tc_img(L.k1);
+  uint8_t* xs = tsm + T.x;
+  uint8_t* w1s = tsm + T.w1;
+  uint8_t* hs = tsm + T.h;
+  uint8_t* w2s = tsm + T.w2;
+  uint8_t* w3s = tsm + T.w3;
+  StepScanRec* rec = reinterpret_cast<StepScanRec*>(tsm + T.rec);
+  int* greedy = reinterpret_cast<int*>(tsm + T.greedy);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long n = c.n_envs;
+  for (int i = tid; i < kHid; i += kQtThreads) {
+    sb1[i] = __ldg(reinterpret_cast<const float*>(img + L.b1) + i);
+    sb2[i] = __ldg(reinterpret_cast<const float*>(img + L.b2) + i);
+  }
+  if (tid < kOutPad) sb3[tid] = __ldg(reinterpret_cast<const float*>(img + L.b3) + tid);
+  // the input tile's padding columns (and the rows without an env) stay zero
+  for (int i = tid; i < kQtEnvs * L.k1 / 8; i += kQtThreads)
+    reinterpret_cast<uint4*>(xs)[i] = make_uint4(0u, 0u, 0u, 0u);
+  if (warp == 0) tmem_alloc(&tslot, 256);
+  if (tid == 0) {
+    mbar_init(&bar_mma, 1);
+    mbar_init(&bar_ld, 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tacc = tslot;
+  if (tid == 0) {
+    mbar_expect_tx(&bar_ld, G.w2a + 128u * kHid * 2u + 16u * kHid * 2u);
+    bulk_g2s(w1s, timg + G.w1, G.w2a, &bar_ld);
+    bulk_g2s(w3s, timg + G.w3, 16u * kHid * 2u, &bar_ld);
+    bulk_g2s(w2s, timg + G.w2a, 128u * kHid * 2u, &bar_ld);
+  }
+  bool ld_out = true, mma_out = false, ok = true;
+  uint32_t pm = 0, pl = 0;
+  // this warp's envs: tile rows 4 warp + l, l < nv
+  const int row0 = warp * 4;
+  const int slot0 = blockIdx.x * kQtEnvs + row0;
+  const int nv = max(0, min(4, (int)n - slot0));
+  const bool live = lane < nv;
+  const int env = live ? order[slot0 + lane] : 0;
+  const unsigned long long rbase = use_replay ? *rp.steps : 0ull;
+  const int B = c.B;
+  // the first observation of every env: its current state, scanned
+  if (live) lane_observe(c, p, env, load_env(p, env), rec[row0 + lane]);
+  __syncwarp();
+  for (int e = 0; e < nv; ++e) {
+    const StepScanRec& r = rec[row0 + e];
+    float b0, b1;
+    scan_env(c, p, p.maps[r.map], r.nb, r.stepb, r.ax, r.ay, r.aphi, r.asigma, ((uint64_t)r.anhi << 32) | r.anlo,
+             lane, b0, b1);
+    qt_obs_to_tile(xs, row0 + e, b0, b1, lane < 5 ? r.exa[lane] : 0.0f, B, lane);
+    if (use_replay) {
+      const long long en = (long long)(rbase % (unsigned long long)rp.slots) * rp.n_envs + r.env;
+      write_row(rp.s + en * rp.obs_dim, b0, b1, r.exa, B, lane);
+    }
+  }
+  fence_async_smem();
+  for (int t = 0; t < K; ++t) {
+    // ---- the network on the tile of observations t ----
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (ok) {
+      ok = __syncthreads_and(mbar_wait(&bar_ld, pl, kTcTries));
+      if (ok) {
+        pl ^= 1u;
+        ld_out = false;
+      }
+    }
+    if (ok) {
+      if (tid == 0) tc_layer(tacc, xs, w1s, kHid, L.k1, &bar_mma);
+      mma_out = true;
+      ok = __syncthreads_and(mbar_wait(&bar_mma, pm, kTcTries));
+      if (ok) {
+        pm ^= 1u;
+        mma_out = false;
+      }
+    }
+    if (ok) {
+      tc_fence_after();
+      qt_epilogue(tacc, sb1, hs, warp, lane);
+      fence_async_smem();
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+      if (tid == 0) tc_layer(tacc, hs, w2s, 128, kHid, &bar_mma);
+      mma_out = true;
+      ok = __syncthreads_and(mbar_wait(&bar_mma, pm, kTcTries));
+      if (ok) {
+        pm ^= 1u;
+        mma_out = false;
+      }
+    }
+    if (ok) {
+      if (tid == 0) {
+        mbar_expect_tx(&bar_ld, 128u * kHid * 2u);
+        bulk_g2s(w2s, timg + G.w2b, 128u * kHid * 2u, &bar_ld);
+      }
+      ld_out = true;
+      ok = __syncthreads_and(mbar_wait(&bar_ld, pl, kTcTries));
+      if (ok) {
+        pl ^= 1u;
+        ld_out = false;
+      }
+    }
+    if (ok) {
+      if (tid == 0) tc_layer(tacc + 128u, hs, w2s, 128, kHid, &bar_mma);
+      mma_out = true;
+      ok = __syncthreads_and(mbar_wait(&bar_mma, pm, kTcTries));
+      if (ok) {
+        pm ^= 1u;
+        mma_out = false;
+      }
+    }
+    if (ok) {
+      if (t + 1 < K) {
+        if (tid == 0) {
+          mbar_expect_tx(&bar_ld, 128u * kHid * 2u);
+          bulk_g2s(w2s, timg + G.w2a, 128u * kHid * 2u, &bar_ld);
+        }
+        ld_out = true;
+      }
+      tc_fence_after();
+      qt_epilogue(tacc, sb2, hs, warp, lane);
+      fence_async_smem();
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+      if (tid == 0) tc_layer(tacc, hs, w3s, 16, kHid, &bar_mma);
+      mma_out = true;
+      ok = __syncthreads_and(mbar_wait(&bar_mma, pm, kTcTries));
+      if (ok) {
+        pm ^= 1u;
+        mma_out = false;
+      }
+    }
+    if (!ok) {
+      if (tid == 0) atomicOr(p.status, SG_DEV_TIMEOUT);
+      break;  // CTA-uniform: the launch's outputs from here on are incomplete
+    }
+    if (warp < 4) {
+      float v[32];
+      tc_fence_after();
+      tmem_ld32(tacc + ((uint32_t)(warp * 32) << 16), v);
+      float o[kOut];
+#pragma unroll
+      for (int j = 0; j < kOut; ++j) o[j] = v[j] + sb3[j];
+      greedy[warp * 32 + lane] = (int)greedy_action(o, nullptr, L.plain);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    // ---- the env step of this warp's envs ----
+    Env s;
+    uint32_t a = 0;
+    if (live) {
+      s = load_env(p, env);
+      // VEM (Sec. 3.1.1): with probability eps_i the random action of step t
+      const uint64_t h = sm_at(sm_at(sm_at(c.seed, kStreamAction), (uint64_t)env), (uint64_t)s.t);
+      const uint32_t ra = (uint32_t)(sm_at(h, 0ull) >> 32) % (uint32_t)c.n_actions;
+      const bool explore = u24_hi(sm_at(h, 1ull)) < __ldg(eps + env);
+      a = explore ? ra : (uint32_t)greedy[row0 + lane];
+    }
+    const uint32_t d = lane_step(c, p, env, live, s, a, rec[row0 + (live ? lane : 0)], lane);
+    if (live) {
+      store_env(p, env, s);
+      if (act_seq) act_seq[(long long)t * n + env] = (uint8_t)a;
+      if (done_seq) done_seq[(long long)t * n + env] = (uint8_t)d;
+    }
+    __syncwarp();
+    const long long slot_t = use_replay ? (long long)((rbase + (unsigned long long)t) % (unsigned long long)rp.slots) : 0;
+    const long long slot_n =
+        use_replay ? (long long)((rbase + (unsigned long long)t + 1ull) % (unsigned long long)rp.slots) : 0;
+    for (int e = 0; e < nv; ++e) {
+      const StepScanRec& r = rec[row0 + e];
+      const int ie = r.env;
+      const uint32_t de = r.done;
+      const MapDesc m = p.maps[r.map];
+      float b0, b1;
+      const float mn = scan_env(c, p, m, r.nb, r.stepb, r.ax, r.ay, r.aphi, r.asigma,
+                                ((uint64_t)r.anhi << 32) | r.anlo, lane, b0, b1);
+      const float rw = (de & 1u) ? -10.0f : (de & 2u) ? 75.0f : reward_finish(c, r.rpart, mn);
+      const uint32_t ae = __shfl_sync(kFull, a, e);
+      if (use_replay) {
+        // transition t: s2 is the observation after the step, before a reset
+        const long long en = slot_t * rp.n_envs + ie;
+        write_row(rp.s2 + en * rp.obs_dim, b0, b1, r.exa, B, lane);
+        if (lane == 0) {
+          rp.a[en] = (uint8_t)ae;
+          rp.r[en] = rw;
+          rp.term[en] = (de & 3u) ? 1 : 0;
+        }
+      }
+      if (lane == 0 && rew_seq) rew_seq[(long long)t * n + ie] = rw;
+      const float* ex = r.exa;
+      if (de) {
+        scan_env(c, p, m, r.nb, r.stepb, r.bx, r.by, r.bphi, r.bsigma, ((uint64_t)r.bnhi << 32) | r.bnlo, lane, b0,
+                 b1);
+        ex = r.exb;
+      }
+      // the observation t + 1: the next tile row, the outputs, the next ring entry's s
+      qt_obs_to_tile(xs, row0 + e, b0, b1, lane < 5 ? ex[lane] : 0.0f, B, lane);
+      if (obs_seq) write_row(obs_seq + ((long long)t * n + ie) * c.obs_dim, b0, b1, ex, B, lane);
+      if (t == K - 1 && obs_out) write_row(obs_out + (long long)ie * c.obs_dim, b0, b1, ex, B, lane);
+      if (use_replay && t + 1 < K) write_row(rp.s + (slot_n * rp.n_envs + ie) * rp.obs_dim, b0, b1, ex, B, lane);
+    }
+    fence_async_smem();
+  }
+  // free the tensor memory once nothing is in flight (bounded waits)
+  if (mma_out) mbar_wait(&bar_mma, pm, kTcTries);
+  if (ld_out) mbar_wait(&bar_ld, pl, kTcTries);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_free(tacc, 256);
+}
+
 __global__ void k_replay_advance(unsigned long long* steps, int K) { *steps += (unsigned long long)K; }
 
 // ------------------------------------------------------------ learner
@@ -1180,6 +1465,7 @@ extern "C" int sg_qnet_create(int32_t n_in, int32_t arch, int32_t max_batch, uin
   // cannot lower it below what a wider one launches with.
   const ImgLayout widest = img_layout(69);
   if ((rc = set_smem_attr((const void*)k_qnet_forward_tc, kTcSmemLaunch)) ||
+      (rc = set_smem_attr((const void*)k_rollout_q_tc, kTcSmemLaunch)) ||
       (rc = set_smem_attr((const void*)k_rollout_q<1, false>, fwd_smem(widest))) ||
       (rc = set_smem_attr((const void*)k_rollout_q<2, false>, fwd_smem(widest, 32))) ||
       (rc = set_smem_attr((const void*)k_rollout_q<1, true>, fwd_smem(widest))) ||
@@ -1270,7 +1556,7 @@ extern "C" int sg_qnet_get_optimizer(sg_qnet_t q, float* m_host, float* v_host, 
 }
 
 extern "C" int sg_qnet_set_rollout_rows(sg_qnet_t q, int32_t rows) {
-  if (!q || (rows != 0 && rows != 16 && rows != 32)) return SG_E_INVAL;
+  if (!q || (rows != 0 && rows != 16 && rows != 32 && rows != 128)) return SG_E_INVAL;
   q->rollout_mt = rows / 16;
   return SG_OK;
 }
@@ -1454,8 +1740,15 @@ int sg_rollout_eps_q(sg_sim* sim, int K, sg_qnet* q, const float* eps, sg_replay
   // with dynamic obstacles the 32-env CTA (64 registers a thread) spills the
   // disc registers: 16 envs per CTA unless asked otherwise
   const bool dyn = sim->dc.n_dyn > 0;
-  const int mt = q->rollout_mt > 0 ? q->rollout_mt : (!dyn && waves32 < waves16 ? 2 : 1);
-  if (mt == 2)
+  // 128 envs per CTA on the tcgen05 kernel when they fill every SM at least
+  // once (or when asked for), without dynamic obstacles
+  const bool tc = !dyn && (q->rollout_mt == 8 || (q->rollout_mt == 0 && n >= kQtEnvs * sms));
+  const int mt = q->rollout_mt > 0 && q->rollout_mt <= 2 ? q->rollout_mt : (!dyn && waves32 < waves16 ? 2 : 1);
+  if (tc)
+    k_rollout_q_tc<<<(n + kQtEnvs - 1) / kQtEnvs, kQtThreads, kTcSmemLaunch, stream>>>(
+        sim->dc, sg_sim_ptrs(sim), q->img, q->img_tc, q->IL, K, eps, rd, rp ? 1 : 0, sim->map_order_dev, obs,
+        obs_seq, act_seq, rew_seq, done_seq);
+  else if (mt == 2)
     (dyn ? k_rollout_q<2, true> : k_rollout_q<2, false>)<<<(n + 31) / 32, 1024, fwd_smem(q->IL, 32), stream>>>(
         sim->dc, sg_sim_ptrs(sim), q->img, q->IL, K, eps, rd, rp ? 1 : 0, sim->map_order_dev, obs, obs_seq, act_seq,
         rew_seq, done_seq);

@@ -69,7 +69,8 @@ class QNet:
         return m, v, int(steps.value)
 
     def set_rollout_rows(self, rows: int):
-        """Envs per CTA of the fused rollout (16, 32, or 0 = automatic)."""
+        """Envs per CTA of the fused rollout (16 or 32 on the mma.sync kernel,
+        128 on the tcgen05 kernel, or 0 = automatic)."""
         check(self.L.sg_qnet_set_rollout_rows(self.handle, int(rows)), "sg_qnet_set_rollout_rows")
 
     def copy_from(self, src: "QNet", stream=None):

@@ -85,11 +85,12 @@ def _margin_ok(q_ref, act, tol):
     return best - chosen <= tol
 
 
-@pytest.mark.parametrize("rows,arch", [(16, "dueling"), (32, "dueling"), (32, "paper")])
+@pytest.mark.parametrize("rows,arch", [(16, "dueling"), (32, "dueling"), (32, "paper"), (128, "dueling"),
+                                       (128, "paper")])
 def test_fused_rollout_teacher_forced(rows, arch):
     """Step by step (K = 1 rollouts) from the GPU's own state: every decision
     checked, every simulator output bit-exact, the replay ring exact; for
-    CTAs of 16 and of 32 envs."""
+    CTAs of 16 and of 32 envs (mma.sync) and of 128 envs (tcgen05)."""
     from paper_2305_04180_gb300 import Replay, Sim
 
     w = workload("qnet4096", n_envs=70)
@@ -145,15 +146,19 @@ def test_fused_rollout_teacher_forced(rows, arch):
     assert n_greedy > 1000 and n_explore > 50
 
 
-def test_fused_rollout_free_running_matches_stepwise():
-    """A K-step fused rollout equals K single-step rollouts from the same start."""
+@pytest.mark.parametrize("rows", [0, 128])
+def test_fused_rollout_free_running_matches_stepwise(rows):
+    """A K-step fused rollout equals K single-step rollouts from the same start
+    (the default CTAs, and the tcgen05 kernel's 128-env CTAs over a ragged
+    last CTA)."""
     from paper_2305_04180_gb300 import Sim
 
-    w = workload("qnet4096", n_envs=48)
+    w = workload("qnet4096", n_envs=48 if rows == 0 else 300)
     maps = w.maps()
     a = Sim(w.params, maps, w.env_map)
     b = Sim(w.params, maps, w.env_map)
     q = _qnet(a.obs_dim)
+    q.set_rollout_rows(rows)
     q.set_params(_theta(6, a.obs_dim, scale=3.0))
     eps = torch.from_numpy(w.eps).cuda()
     a.reset()
