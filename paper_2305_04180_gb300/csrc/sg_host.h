@@ -33,6 +33,7 @@ struct sg_sim {
   unsigned* queue_dev = nullptr; // work-list cursor of the persistent kernel
   unsigned* pipe_sync_dev = nullptr;  // time-sliced pipelined rollout: segment flags, item counter, abort word
   size_t pipe_sync_words = 0;
+  unsigned* q_sync_dev = nullptr;  // time-sliced fused Q rollout: per-block segment flags, item counter, abort word
 };
 
 sg::SimPtrs sg_sim_ptrs(sg_sim* s);

@@ -828,15 +828,54 @@ __device__ __forceinline__ void qt_obs_to_tile(uint8_t* xs, int r, float b0, flo
   if (lane < 5) *reinterpret_cast<bf16*>(xs + kmajor_offset(r, B + lane, kQtEnvs)) = __float2bfloat16_rn(ex);
 }
 
+// State of env i through L2: with time slicing another SM may have written
+// it during this launch.
+__device__ __forceinline__ Env load_env_l2(const SimPtrs& p, int i) {
+  Env s;
+  const int n = p.n;
+  s.x = __ldcg(p.f + 0 * n + i);
+  s.y = __ldcg(p.f + 1 * n + i);
+  s.phi = __ldcg(p.f + 2 * n + i);
+  s.vl = __ldcg(p.f + 3 * n + i);
+  s.va = __ldcg(p.f + 4 * n + i);
+  s.dt = __ldcg(p.f + 5 * n + i);
+  s.K = __ldcg(p.f + 6 * n + i);
+  s.cap = __ldcg(p.f + 7 * n + i);
+  s.sigma = __ldcg(p.f + 8 * n + i);
+  s.ep_step = __ldcg(p.u + 0 * n + i);
+  s.ep_id = __ldcg(p.u + 1 * n + i);
+  s.t = __ldcg(p.u + 2 * n + i);
+  s.fifo = __ldcg(p.u + 3 * n + i);
+  f_sincos(s.phi, s.sphi, s.cphi);
+  return s;
+}
+
+__device__ __forceinline__ unsigned qt_ld_acquire(const unsigned* a) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ void qt_st_release(unsigned* a, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;\n" ::"l"(a), "r"(v) : "memory");
+}
+constexpr unsigned kQtWaitIters = 1u << 22;  // x ~256 ns sleeps: about a second
+
+// Time slicing (sync != null): a resident grid takes (segment of seg steps,
+// 128-env block) items in segment-major order from a device counter; an item
+// waits (bounded) until the previous segment of its block is published, and
+// takes its first observation from the replay ring (the entry the previous
+// segment wrote), or scans it when there is no ring.  sync: [nblk] segments
+// done per block, item counter, abort word; zero at launch.
 __global__ void __launch_bounds__(kQtThreads, 1)
     k_rollout_q_tc(const __grid_constant__ DevCfg c, SimPtrs p, const uint8_t* __restrict__ img,
                    const uint8_t* __restrict__ timg, ImgLayout L, int K, const float* __restrict__ eps, ReplayDev rp,
-                   int use_replay, const int* __restrict__ order, float* __restrict__ obs_out,
-                   float* __restrict__ obs_seq, uint8_t* __restrict__ act_seq, float* __restrict__ rew_seq,
-                   uint8_t* __restrict__ done_seq) {
+                   int use_replay, const int* __restrict__ order, int seg, unsigned* __restrict__ sync,
+                   float* __restrict__ obs_out, float* __restrict__ obs_seq, uint8_t* __restrict__ act_seq,
+                   float* __restrict__ rew_seq, uint8_t* __restrict__ done_seq) {
   extern __shared__ __align__(1024) uint8_t tsm[];
   __shared__ uint64_t bar_mma, bar_ld;
   __shared__ uint32_t tslot;
+  __shared__ int item_sh;
   __shared__ float sb1[kHid], sb2[kHid], sb3[kOutPad];
   const QtSmem T = qt_smem(L.k1);
   const TcImg G = tc_img(L.k1);
@@ -849,14 +888,15 @@ __global__ void __launch_bounds__(kQtThreads, 1)
   int* greedy = reinterpret_cast<int*>(tsm + T.greedy);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long long n = c.n_envs;
+  const int nblk = (int)((n + kQtEnvs - 1) / kQtEnvs);
+  const int seglen = seg > 0 ? seg : K;
+  const int nseg = (K + seglen - 1) / seglen;
+  const long long nitems = (long long)nblk * nseg;
   for (int i = tid; i < kHid; i += kQtThreads) {
     sb1[i] = __ldg(reinterpret_cast<const float*>(img + L.b1) + i);
     sb2[i] = __ldg(reinterpret_cast<const float*>(img + L.b2) + i);
   }
   if (tid < kOutPad) sb3[tid] = __ldg(reinterpret_cast<const float*>(img + L.b3) + tid);
-  // the input tile's padding columns (and the rows without an env) stay zero
-  for (int i = tid; i < kQtEnvs * L.k1 / 8; i += kQtThreads)
-    reinterpret_cast<uint4*>(xs)[i] = make_uint4(0u, 0u, 0u, 0u);
   if (warp == 0) tmem_alloc(&tslot, 256);
   if (tid == 0) {
     mbar_init(&bar_mma, 1);
@@ -872,181 +912,242 @@ __global__ void __launch_bounds__(kQtThreads, 1)
     bulk_g2s(w3s, timg + G.w3, 16u * kHid * 2u, &bar_ld);
     bulk_g2s(w2s, timg + G.w2a, 128u * kHid * 2u, &bar_ld);
   }
-  bool ld_out = true, mma_out = false, ok = true;
+  // W2's buffer: half 0 in flight (ld_out) or resident (w2a), else half 1
+  bool ld_out = true, w2a = false, mma_out = false, ok = true;
   uint32_t pm = 0, pl = 0;
-  // this warp's envs: tile rows 4 warp + l, l < nv
-  const int row0 = warp * 4;
-  const int slot0 = blockIdx.x * kQtEnvs + row0;
-  const int nv = max(0, min(4, (int)n - slot0));
-  const bool live = lane < nv;
-  const int env = live ? order[slot0 + lane] : 0;
   const unsigned long long rbase = use_replay ? *rp.steps : 0ull;
   const int B = c.B;
-  // the first observation of every env: its current state, scanned
-  if (live) lane_observe(c, p, env, load_env(p, env), rec[row0 + lane]);
-  __syncwarp();
-  for (int e = 0; e < nv; ++e) {
-    const StepScanRec& r = rec[row0 + e];
-    float b0, b1;
-    scan_env(c, p, p.maps[r.map], r.nb, r.stepb, r.ax, r.ay, r.aphi, r.asigma, ((uint64_t)r.anhi << 32) | r.anlo,
-             lane, b0, b1);
-    qt_obs_to_tile(xs, row0 + e, b0, b1, lane < 5 ? r.exa[lane] : 0.0f, B, lane);
-    if (use_replay) {
-      const long long en = (long long)(rbase % (unsigned long long)rp.slots) * rp.n_envs + r.env;
-      write_row(rp.s + en * rp.obs_dim, b0, b1, r.exa, B, lane);
+  const int row0 = warp * 4;
+  for (int iter = 0;; ++iter) {
+    // ---- the next item: a segment of one 128-env block ----
+    if (tid == 0) {
+      long long it;
+      if (!sync)
+        it = iter == 0 ? (long long)blockIdx.x : nitems;
+      else
+        it = (!ok || __ldcg(&sync[nblk + 1])) ? nitems : (long long)atomicAdd(&sync[nblk], 1u);
+      if (sync && it < nitems && it >= nblk) {
+        const unsigned need = (unsigned)(it / nblk);
+        unsigned w = 0;
+        while (qt_ld_acquire(&sync[it % nblk]) < need) {
+          if (++w > kQtWaitIters || qt_ld_acquire(&sync[nblk + 1])) {
+            atomicOr(p.status, SG_DEV_TIMEOUT);
+            atomicExch(&sync[nblk + 1], 1u);
+            it = nitems;
+            break;
+          }
+          __nanosleep(256);
+        }
+      }
+      item_sh = (ok && it < nitems) ? (int)it : -1;
     }
-  }
-  fence_async_smem();
-  for (int t = 0; t < K; ++t) {
-    // ---- the network on the tile of observations t ----
-    tc_fence_before();
     __syncthreads();
-    tc_fence_after();
-    if (ok) {
-      ok = __syncthreads_and(mbar_wait(&bar_ld, pl, kTcTries));
-      if (ok) {
-        pl ^= 1u;
-        ld_out = false;
+    const int item = item_sh;
+    __syncthreads();  // item_sh is rewritten by the next iteration
+    if (item < 0) break;
+    const int blk = item % nblk, s0 = (item / nblk) * seglen, s1 = min(K, s0 + seglen);
+    const int slot0 = blk * kQtEnvs + row0;
+    const int nv = max(0, min(4, (int)n - slot0));
+    const bool live = lane < nv;
+    const int env = live ? order[slot0 + lane] : 0;
+    // the tile: zero (padding columns, rows without an env), then the first
+    // observation of the segment
+    for (int i = tid; i < kQtEnvs * L.k1 / 8; i += kQtThreads)
+      reinterpret_cast<uint4*>(xs)[i] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    if (s0 > 0 && use_replay) {
+      const long long sl = (long long)((rbase + (unsigned long long)s0) % (unsigned long long)rp.slots);
+      for (int e = 0; e < nv; ++e) {
+        const int ie = __shfl_sync(kFull, env, e);
+        const float* src = rp.s + (sl * rp.n_envs + ie) * rp.obs_dim;
+        for (int k = lane; k < c.obs_dim; k += 32)
+          *reinterpret_cast<bf16*>(xs + kmajor_offset(row0 + e, k, kQtEnvs)) = __float2bfloat16_rn(__ldcg(src + k));
+      }
+    } else {
+      if (live) lane_observe(c, p, env, load_env_l2(p, env), rec[row0 + lane]);
+      __syncwarp();
+      for (int e = 0; e < nv; ++e) {
+        const StepScanRec& r = rec[row0 + e];
+        float b0, b1;
+        scan_env(c, p, p.maps[r.map], r.nb, r.stepb, r.ax, r.ay, r.aphi, r.asigma,
+                 ((uint64_t)r.anhi << 32) | r.anlo, lane, b0, b1);
+        qt_obs_to_tile(xs, row0 + e, b0, b1, lane < 5 ? r.exa[lane] : 0.0f, B, lane);
+        if (use_replay) {
+          const long long sl = (long long)((rbase + (unsigned long long)s0) % (unsigned long long)rp.slots);
+          write_row(rp.s + (sl * rp.n_envs + r.env) * rp.obs_dim, b0, b1, r.exa, B, lane);
+        }
       }
     }
-    if (ok) {
-      if (tid == 0) tc_layer(tacc, xs, w1s, kHid, L.k1, &bar_mma);
-      mma_out = true;
-      ok = __syncthreads_and(mbar_wait(&bar_mma, pm, kTcTries));
-      if (ok) {
-        pm ^= 1u;
-        mma_out = false;
-      }
-    }
-    if (ok) {
-      tc_fence_after();
-      qt_epilogue(tacc, sb1, hs, warp, lane);
-      fence_async_smem();
+    fence_async_smem();
+    for (int t = s0; t < s1; ++t) {
+      // ---- the network on the tile of observations t ----
       tc_fence_before();
       __syncthreads();
       tc_fence_after();
-      if (tid == 0) tc_layer(tacc, hs, w2s, 128, kHid, &bar_mma);
-      mma_out = true;
-      ok = __syncthreads_and(mbar_wait(&bar_mma, pm, kTcTries));
-      if (ok) {
-        pm ^= 1u;
-        mma_out = false;
-      }
-    }
-    if (ok) {
-      if (tid == 0) {
-        mbar_expect_tx(&bar_ld, 128u * kHid * 2u);
-        bulk_g2s(w2s, timg + G.w2b, 128u * kHid * 2u, &bar_ld);
-      }
-      ld_out = true;
-      ok = __syncthreads_and(mbar_wait(&bar_ld, pl, kTcTries));
-      if (ok) {
-        pl ^= 1u;
-        ld_out = false;
-      }
-    }
-    if (ok) {
-      if (tid == 0) tc_layer(tacc + 128u, hs, w2s, 128, kHid, &bar_mma);
-      mma_out = true;
-      ok = __syncthreads_and(mbar_wait(&bar_mma, pm, kTcTries));
-      if (ok) {
-        pm ^= 1u;
-        mma_out = false;
-      }
-    }
-    if (ok) {
-      if (t + 1 < K) {
+      if (ok && !w2a && !ld_out) {
+        // half 0 for this step (the previous item's last step left half 1)
         if (tid == 0) {
           mbar_expect_tx(&bar_ld, 128u * kHid * 2u);
           bulk_g2s(w2s, timg + G.w2a, 128u * kHid * 2u, &bar_ld);
         }
         ld_out = true;
       }
-      tc_fence_after();
-      qt_epilogue(tacc, sb2, hs, warp, lane);
-      fence_async_smem();
+      if (ok && ld_out) {
+        ok = __syncthreads_and(mbar_wait(&bar_ld, pl, kTcTries));
+        if (ok) {
+          pl ^= 1u;
+          ld_out = false;
+          w2a = true;
+        }
+      }
+      if (ok) {
+        if (tid == 0) tc_layer(tacc, xs, w1s, kHid, L.k1, &bar_mma);
+        mma_out = true;
+        ok = __syncthreads_and(mbar_wait(&bar_mma, pm, kTcTries));
+        if (ok) {
+          pm ^= 1u;
+          mma_out = false;
+        }
+      }
+      if (ok) {
+        tc_fence_after();
+        qt_epilogue(tacc, sb1, hs, warp, lane);
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0) tc_layer(tacc, hs, w2s, 128, kHid, &bar_mma);
+        mma_out = true;
+        ok = __syncthreads_and(mbar_wait(&bar_mma, pm, kTcTries));
+        if (ok) {
+          pm ^= 1u;
+          mma_out = false;
+        }
+      }
+      if (ok) {
+        if (tid == 0) {
+          mbar_expect_tx(&bar_ld, 128u * kHid * 2u);
+          bulk_g2s(w2s, timg + G.w2b, 128u * kHid * 2u, &bar_ld);
+        }
+        ld_out = true;
+        w2a = false;
+        ok = __syncthreads_and(mbar_wait(&bar_ld, pl, kTcTries));
+        if (ok) {
+          pl ^= 1u;
+          ld_out = false;
+        }
+      }
+      if (ok) {
+        if (tid == 0) tc_layer(tacc + 128u, hs, w2s, 128, kHid, &bar_mma);
+        mma_out = true;
+        ok = __syncthreads_and(mbar_wait(&bar_mma, pm, kTcTries));
+        if (ok) {
+          pm ^= 1u;
+          mma_out = false;
+        }
+      }
+      if (ok) {
+        if (t + 1 < s1) {
+          // the next step's half 0 streams in while this step finishes
+          if (tid == 0) {
+            mbar_expect_tx(&bar_ld, 128u * kHid * 2u);
+            bulk_g2s(w2s, timg + G.w2a, 128u * kHid * 2u, &bar_ld);
+          }
+          ld_out = true;
+        }
+        tc_fence_after();
+        qt_epilogue(tacc, sb2, hs, warp, lane);
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0) tc_layer(tacc, hs, w3s, 16, kHid, &bar_mma);
+        mma_out = true;
+        ok = __syncthreads_and(mbar_wait(&bar_mma, pm, kTcTries));
+        if (ok) {
+          pm ^= 1u;
+          mma_out = false;
+        }
+      }
+      if (!ok) {
+        if (tid == 0) atomicOr(p.status, SG_DEV_TIMEOUT);
+        break;  // CTA-uniform: the launch's outputs from here on are incomplete
+      }
+      if (warp < 4) {
+        float v[32];
+        tc_fence_after();
+        tmem_ld32(tacc + ((uint32_t)(warp * 32) << 16), v);
+        float o[kOut];
+#pragma unroll
+        for (int j = 0; j < kOut; ++j) o[j] = v[j] + sb3[j];
+        greedy[warp * 32 + lane] = (int)greedy_action(o, nullptr, L.plain);
+      }
       tc_fence_before();
       __syncthreads();
       tc_fence_after();
-      if (tid == 0) tc_layer(tacc, hs, w3s, 16, kHid, &bar_mma);
-      mma_out = true;
-      ok = __syncthreads_and(mbar_wait(&bar_mma, pm, kTcTries));
-      if (ok) {
-        pm ^= 1u;
-        mma_out = false;
+      // ---- the env step of this warp's envs ----
+      Env s;
+      uint32_t a = 0;
+      if (live) {
+        s = load_env_l2(p, env);
+        // VEM (Sec. 3.1.1): with probability eps_i the random action of step t
+        const uint64_t h = sm_at(sm_at(sm_at(c.seed, kStreamAction), (uint64_t)env), (uint64_t)s.t);
+        const uint32_t ra = (uint32_t)(sm_at(h, 0ull) >> 32) % (uint32_t)c.n_actions;
+        const bool explore = u24_hi(sm_at(h, 1ull)) < __ldg(eps + env);
+        a = explore ? ra : (uint32_t)greedy[row0 + lane];
       }
-    }
-    if (!ok) {
-      if (tid == 0) atomicOr(p.status, SG_DEV_TIMEOUT);
-      break;  // CTA-uniform: the launch's outputs from here on are incomplete
-    }
-    if (warp < 4) {
-      float v[32];
-      tc_fence_after();
-      tmem_ld32(tacc + ((uint32_t)(warp * 32) << 16), v);
-      float o[kOut];
-#pragma unroll
-      for (int j = 0; j < kOut; ++j) o[j] = v[j] + sb3[j];
-      greedy[warp * 32 + lane] = (int)greedy_action(o, nullptr, L.plain);
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    // ---- the env step of this warp's envs ----
-    Env s;
-    uint32_t a = 0;
-    if (live) {
-      s = load_env(p, env);
-      // VEM (Sec. 3.1.1): with probability eps_i the random action of step t
-      const uint64_t h = sm_at(sm_at(sm_at(c.seed, kStreamAction), (uint64_t)env), (uint64_t)s.t);
-      const uint32_t ra = (uint32_t)(sm_at(h, 0ull) >> 32) % (uint32_t)c.n_actions;
-      const bool explore = u24_hi(sm_at(h, 1ull)) < __ldg(eps + env);
-      a = explore ? ra : (uint32_t)greedy[row0 + lane];
-    }
-    const uint32_t d = lane_step(c, p, env, live, s, a, rec[row0 + (live ? lane : 0)], lane);
-    if (live) {
-      store_env(p, env, s);
-      if (act_seq) act_seq[(long long)t * n + env] = (uint8_t)a;
-      if (done_seq) done_seq[(long long)t * n + env] = (uint8_t)d;
-    }
-    __syncwarp();
-    const long long slot_t = use_replay ? (long long)((rbase + (unsigned long long)t) % (unsigned long long)rp.slots) : 0;
-    const long long slot_n =
-        use_replay ? (long long)((rbase + (unsigned long long)t + 1ull) % (unsigned long long)rp.slots) : 0;
-    for (int e = 0; e < nv; ++e) {
-      const StepScanRec& r = rec[row0 + e];
-      const int ie = r.env;
-      const uint32_t de = r.done;
-      const MapDesc m = p.maps[r.map];
-      float b0, b1;
-      const float mn = scan_env(c, p, m, r.nb, r.stepb, r.ax, r.ay, r.aphi, r.asigma,
-                                ((uint64_t)r.anhi << 32) | r.anlo, lane, b0, b1);
-      const float rw = (de & 1u) ? -10.0f : (de & 2u) ? 75.0f : reward_finish(c, r.rpart, mn);
-      const uint32_t ae = __shfl_sync(kFull, a, e);
-      if (use_replay) {
-        // transition t: s2 is the observation after the step, before a reset
-        const long long en = slot_t * rp.n_envs + ie;
-        write_row(rp.s2 + en * rp.obs_dim, b0, b1, r.exa, B, lane);
-        if (lane == 0) {
-          rp.a[en] = (uint8_t)ae;
-          rp.r[en] = rw;
-          rp.term[en] = (de & 3u) ? 1 : 0;
+      const uint32_t d = lane_step(c, p, env, live, s, a, rec[row0 + (live ? lane : 0)], lane);
+      if (live) {
+        store_env(p, env, s);
+        if (act_seq) act_seq[(long long)t * n + env] = (uint8_t)a;
+        if (done_seq) done_seq[(long long)t * n + env] = (uint8_t)d;
+      }
+      __syncwarp();
+      const long long slot_t =
+          use_replay ? (long long)((rbase + (unsigned long long)t) % (unsigned long long)rp.slots) : 0;
+      const long long slot_n =
+          use_replay ? (long long)((rbase + (unsigned long long)t + 1ull) % (unsigned long long)rp.slots) : 0;
+      for (int e = 0; e < nv; ++e) {
+        const StepScanRec& r = rec[row0 + e];
+        const int ie = r.env;
+        const uint32_t de = r.done;
+        const MapDesc m = p.maps[r.map];
+        float b0, b1;
+        const float mn = scan_env(c, p, m, r.nb, r.stepb, r.ax, r.ay, r.aphi, r.asigma,
+                                  ((uint64_t)r.anhi << 32) | r.anlo, lane, b0, b1);
+        const float rw = (de & 1u) ? -10.0f : (de & 2u) ? 75.0f : reward_finish(c, r.rpart, mn);
+        const uint32_t ae = __shfl_sync(kFull, a, e);
+        if (use_replay) {
+          // transition t: s2 is the observation after the step, before a reset
+          const long long en = slot_t * rp.n_envs + ie;
+          write_row(rp.s2 + en * rp.obs_dim, b0, b1, r.exa, B, lane);
+          if (lane == 0) {
+            rp.a[en] = (uint8_t)ae;
+            rp.r[en] = rw;
+            rp.term[en] = (de & 3u) ? 1 : 0;
+          }
         }
+        if (lane == 0 && rew_seq) rew_seq[(long long)t * n + ie] = rw;
+        const float* ex = r.exa;
+        if (de) {
+          scan_env(c, p, m, r.nb, r.stepb, r.bx, r.by, r.bphi, r.bsigma, ((uint64_t)r.bnhi << 32) | r.bnlo, lane,
+                   b0, b1);
+          ex = r.exb;
+        }
+        // the observation t + 1: the next tile row, the outputs, the next ring entry's s
+        qt_obs_to_tile(xs, row0 + e, b0, b1, lane < 5 ? ex[lane] : 0.0f, B, lane);
+        if (obs_seq) write_row(obs_seq + ((long long)t * n + ie) * c.obs_dim, b0, b1, ex, B, lane);
+        if (t == K - 1 && obs_out) write_row(obs_out + (long long)ie * c.obs_dim, b0, b1, ex, B, lane);
+        if (use_replay && t + 1 < K)
+          write_row(rp.s + (slot_n * rp.n_envs + ie) * rp.obs_dim, b0, b1, ex, B, lane);
       }
-      if (lane == 0 && rew_seq) rew_seq[(long long)t * n + ie] = rw;
-      const float* ex = r.exa;
-      if (de) {
-        scan_env(c, p, m, r.nb, r.stepb, r.bx, r.by, r.bphi, r.bsigma, ((uint64_t)r.bnhi << 32) | r.bnlo, lane, b0,
-                 b1);
-        ex = r.exb;
-      }
-      // the observation t + 1: the next tile row, the outputs, the next ring entry's s
-      qt_obs_to_tile(xs, row0 + e, b0, b1, lane < 5 ? ex[lane] : 0.0f, B, lane);
-      if (obs_seq) write_row(obs_seq + ((long long)t * n + ie) * c.obs_dim, b0, b1, ex, B, lane);
-      if (t == K - 1 && obs_out) write_row(obs_out + (long long)ie * c.obs_dim, b0, b1, ex, B, lane);
-      if (use_replay && t + 1 < K) write_row(rp.s + (slot_n * rp.n_envs + ie) * rp.obs_dim, b0, b1, ex, B, lane);
+      fence_async_smem();
     }
-    fence_async_smem();
+    if (!sync) break;
+    // publish the block's segment: its env state and ring entries are stored
+    __threadfence();
+    __syncthreads();
+    if (tid == 0 && ok) qt_st_release(&sync[blk], (unsigned)(s0 / seglen + 1));
   }
   // free the tensor memory once nothing is in flight (bounded waits)
   if (mma_out) mbar_wait(&bar_mma, pm, kTcTries);
@@ -1744,11 +1845,20 @@ int sg_rollout_eps_q(sg_sim* sim, int K, sg_qnet* q, const float* eps, sg_replay
   // once (or when asked for), without dynamic obstacles
   const bool tc = !dyn && (q->rollout_mt == 8 || (q->rollout_mt == 0 && n >= kQtEnvs * sms));
   const int mt = q->rollout_mt > 0 && q->rollout_mt <= 2 ? q->rollout_mt : (!dyn && waves32 < waves16 ? 2 : 1);
-  if (tc)
-    k_rollout_q_tc<<<(n + kQtEnvs - 1) / kQtEnvs, kQtThreads, kTcSmemLaunch, stream>>>(
-        sim->dc, sg_sim_ptrs(sim), q->img, q->img_tc, q->IL, K, eps, rd, rp ? 1 : 0, sim->map_order_dev, obs,
-        obs_seq, act_seq, rew_seq, done_seq);
-  else if (mt == 2)
+  if (tc) {
+    // more than one wave of 128-env CTAs: slice the rollout into 4 segments
+    // over a resident grid so that no SM idles in a part-empty last wave
+    const int nblk = (n + kQtEnvs - 1) / kQtEnvs;
+    const int seg = (nblk > sms && K >= 4) ? (K + 3) / 4 : 0;
+    int grid = nblk;
+    if (seg > 0) {
+      grid = std::min(nblk * ((K + seg - 1) / seg), sms);
+      SG_CUDA(cudaMemsetAsync(sim->q_sync_dev, 0, sizeof(unsigned) * (size_t)(nblk + 2), stream));
+    }
+    k_rollout_q_tc<<<grid, kQtThreads, kTcSmemLaunch, stream>>>(
+        sim->dc, sg_sim_ptrs(sim), q->img, q->img_tc, q->IL, K, eps, rd, rp ? 1 : 0, sim->map_order_dev, seg,
+        seg > 0 ? sim->q_sync_dev : nullptr, obs, obs_seq, act_seq, rew_seq, done_seq);
+  } else if (mt == 2)
     (dyn ? k_rollout_q<2, true> : k_rollout_q<2, false>)<<<(n + 31) / 32, 1024, fwd_smem(q->IL, 32), stream>>>(
         sim->dc, sg_sim_ptrs(sim), q->img, q->IL, K, eps, rd, rp ? 1 : 0, sim->map_order_dev, obs, obs_seq, act_seq,
         rew_seq, done_seq);

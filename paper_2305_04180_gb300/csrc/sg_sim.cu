@@ -917,6 +917,7 @@ static void free_sim(sg_sim* s) {
   cudaFree(s->map_order_dev);
   cudaFree(s->dyn);
   cudaFree(s->pipe_sync_dev);
+  cudaFree(s->q_sync_dev);
   delete s;
 }
 
@@ -978,6 +979,7 @@ extern "C" int sg_sim_create(const sg_sim_config* cfg, int32_t n_maps, const uin
   alloc((void**)&s->status_dev, sizeof(uint32_t));
   alloc((void**)&s->map_order_dev, sizeof(int) * n);
   if (cfg->n_dyn > 0) alloc((void**)&s->dyn, sizeof(float) * 4 * cfg->n_dyn * (size_t)n);
+  alloc((void**)&s->q_sync_dev, sizeof(unsigned) * ((size_t)(n + 127) / 128 + 2));
   // maps are preprocessed in groups whose grids fit a staging budget
   const size_t budget = std::max(max_cells, (size_t)256 << 20);
   uint8_t* staging = nullptr;  // grids, then per-row distances

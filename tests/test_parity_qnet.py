@@ -174,6 +174,51 @@ def test_fused_rollout_free_running_matches_stepwise(rows):
     assert torch.equal(aa, ab) and torch.equal(ra, rb)
 
 
+def test_time_sliced_tc_rollout_equals_single_steps():
+    """More than one wave of 128-env CTAs (20,480 envs): the tcgen05 rollout
+    is sliced into segments over a resident grid, and a later segment takes
+    its first observation from the replay ring.  A 16-step rollout equals 16
+    single-step rollouts (no slicing, every first observation scanned from
+    the state): actions, rewards, done flags, ring contents, final state."""
+    from paper_2305_04180_gb300 import Replay, Sim
+
+    w = workload("qnet4096", n_envs=20480)
+    maps = w.maps()
+    q = _qnet(w.params["n_beams"] + 5)
+    q.set_params(_theta(21, q.n_in, scale=3.0))
+    q.set_rollout_rows(128)
+    eps = torch.from_numpy(_eps_spread(20480)).cuda()
+    out = []
+    for stepwise in (False, True):
+        s = Sim(w.params, maps, w.env_map)
+        rp = Replay(24, s.n, s.obs_dim)
+        s.reset()
+        K = 16
+        act = torch.empty((K, s.n), dtype=torch.uint8, device="cuda")
+        rew = torch.empty((K, s.n), device="cuda")
+        done = torch.empty((K, s.n), dtype=torch.uint8, device="cuda")
+        if stepwise:
+            for k in range(K):
+                s.rollout(1, policy="eps_q", qnet=q, eps=eps, replay=rp, act_seq=act[k:k + 1], rew_seq=rew[k:k + 1],
+                          done_seq=done[k:k + 1])
+        else:
+            s.rollout(K, policy="eps_q", qnet=q, eps=eps, replay=rp, act_seq=act, rew_seq=rew, done_seq=done)
+        torch.cuda.synchronize()
+        assert s.status() == 0
+        out.append((act.cpu().numpy(), rew.cpu().numpy(), done.cpu().numpy(), rp.read(0, K * s.n), s.get_state()))
+    (a0, r0, d0, ring0, st0), (a1, r1, d1, ring1, st1) = out
+    assert np.array_equal(a0, a1) and np.array_equal(bits(r0), bits(r1)) and np.array_equal(d0, d1)
+    for x, y in zip(ring0, ring1):
+        assert np.array_equal(x.view(np.uint8), y.view(np.uint8))
+    for x, y in zip(st0, st1):
+        assert np.array_equal(x.view(np.uint32), y.view(np.uint32))
+    assert (d0 != 0).sum() > 100
+
+
+def _eps_spread(n):
+    return np.linspace(0.01, 0.3, n).astype(np.float32)
+
+
 def test_fused_rollout_tile_heights_agree():
     """CTAs of 16 and of 32 envs compute identical Q-values, so identical
     trajectories (the same MMA order per row)."""
