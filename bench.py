@@ -57,12 +57,13 @@ def parse():
 # ------------------------------------------------------------ CPU oracle
 def _oracle_shard(args):
     """Worker: run envs [i0, i1) of the workload on the CPU oracle."""
-    name, i0, i1, K, t0 = args
+    name, i0, i1, K, t0 = args[:5]
+    prec = args[5] if len(args) > 5 else "f32"
     from oracle.sim import OracleSim
     from workloads import workload
 
     w = workload(name)
-    o = OracleSim(w.params, w.maps(), w.env_map, w.env_beams, prec="f32")
+    o = OracleSim(w.params, w.maps(), w.env_map, w.env_beams, prec=prec)
     for i in range(i0, i1):
         o.reset_env(i, 0)
     o.L.orc_reset_march_samples()
@@ -78,12 +79,12 @@ def oracle_pool(cores):
     return mp.get_context("spawn").Pool(cores)
 
 
-def time_oracle(pool, cores, name, n_envs, K):
+def time_oracle(pool, cores, name, n_envs, K, prec="f32"):
     """Env-steps/s of the oracle over all n_envs envs for K steps, sharded by
     env over `cores` processes (envs are independent).  Wall time of the
     slowest shard counts."""
     per = math.ceil(n_envs / cores)
-    jobs = [(name, i, min(n_envs, i + per), K, 0) for i in range(0, n_envs, per)]
+    jobs = [(name, i, min(n_envs, i + per), K, 0, prec) for i in range(0, n_envs, per)]
     t = time.perf_counter()
     res = pool.map(_oracle_shard, jobs)
     wall = time.perf_counter() - t
@@ -660,6 +661,9 @@ def main():
         s1, _, busy1, _ = time_oracle(pool, 1, a.workload, n1, 2000)
         out["cpu_baseline"]["single_thread"] = {"value": s1 / busy1, "unit": UNIT, "cores": 1,
                                                 "sample": f"{n1} envs x 2000 steps, one process"}
+        s2, _, busy2, _ = time_oracle(pool, 1, a.workload, n1, 1000, prec="f64")
+        out["cpu_baseline"]["single_thread_f64"] = {"value": s2 / busy2, "unit": UNIT, "cores": 1,
+                                                    "sample": f"{n1} envs x 1000 steps, one process, float64 oracle"}
         pool.close()
     out["roofline"] = roofline_alu(samples_per_env_step, n, K, ms_per_step, clk)
     out["roofline"]["samples_per_env_step"] = samples_per_env_step
