@@ -405,8 +405,10 @@ __host__ __device__ inline TcSmem tc_smem(int k1) {
 }
 // The weight copy in global memory: blocks identical to their shared-memory
 // images, so that each is one bulk copy.
+// For the fused rollout also W1 in two 128-row halves and W2 in four
+// 64-row quarters (each its own canonical operand).
 struct TcImg {
-  uint32_t w1, w2a, w2b, w3, bytes;
+  uint32_t w1, w2a, w2b, w3, w1h, w2q, bytes;
 };
 __host__ __device__ inline TcImg tc_img(int k1) {
   TcImg t;
@@ -414,7 +416,9 @@ __host__ __device__ inline TcImg tc_img(int k1) {
   t.w2a = (uint32_t)(kHid * k1 * 2);
   t.w2b = t.w2a + 128u * kHid * 2u;
   t.w3 = t.w2b + 128u * kHid * 2u;
-  t.bytes = t.w3 + 16u * kHid * 2u;
+  t.w1h = t.w3 + 16u * kHid * 2u;
+  t.w2q = t.w1h + (uint32_t)(kHid * k1 * 2);
+  t.bytes = t.w2q + (uint32_t)(kHid * kHid * 2);
   return t;
 }
 
@@ -431,10 +435,16 @@ __global__ void k_tc_image(const uint8_t* __restrict__ img, ImgLayout L, uint8_t
       const int n = c % kHid, kg = c / kHid;
       v = __ldg(reinterpret_cast<const uint4*>(img + L.w1 + ((size_t)n * L.ld1 + kg * 8) * 2));
       dst = T.w1 + kmajor_offset(n, kg * 8, kHid);
+      // the same chunk in its 128-row half
+      *reinterpret_cast<uint4*>(out + T.w1h + (uint32_t)((n >> 7) * 128 * L.k1 * 2) +
+                                kmajor_offset(n & 127, kg * 8, 128)) = v;
     } else if (c < n1 + n2) {
       const int j = c - n1, n = j % kHid, kg = j / kHid;
       v = __ldg(reinterpret_cast<const uint4*>(img + L.w2 + ((size_t)n * kLdh + kg * 8) * 2));
       dst = n < 128 ? T.w2a + kmajor_offset(n, kg * 8, 128) : T.w2b + kmajor_offset(n - 128, kg * 8, 128);
+      // and in its 64-row quarter
+      *reinterpret_cast<uint4*>(out + T.w2q + (uint32_t)((n >> 6) * 64 * kHid * 2) +
+                                kmajor_offset(n & 63, kg * 8, 64)) = v;
     } else {
       const int j = c - n1 - n2, n = j % 16, kg = j / 16;
       if (n < kOutPad) v = __ldg(reinterpret_cast<const uint4*>(img + L.w3 + ((size_t)n * kLdh + kg * 8) * 2));
@@ -774,32 +784,36 @@ __global__ void __launch_bounds__(512 * MT, 1)
 
 // ---------------------------------------- tcgen05 fused eps-greedy rollout
 // For large env counts: 128 envs per CTA form one 128-row tile of the
-// network.  Per step the 32 warps run the network on the tile exactly as
-// k_qnet_forward_tc does (tcgen05 MMAs into tensor memory, epilogues split
-// over the 8 warps of each lane quarter, W2 halves streamed by bulk copies),
-// warps 0-3 take the greedy actions from the head, and then every warp steps
-// its 4 envs the way sg_sim_step does (lanes 0-3: the scalar part, lane_step;
-// the whole warp: the scans), writing the next observation as the tile's
-// BF16 row and the FP32 outputs and ring entries.  Same VEM draws, same
-// simulator values as k_rollout_q; the Q values differ from it only in the
-// summation order.
+// network.  Per step the network runs on the tile on the tensor cores
+// (tcgen05 MMAs into 256 tensor-memory columns, epilogues split over the 8
+// warps of each lane quarter), warps 0-3 take the greedy actions from the
+// head, and then every warp steps its 4 envs the way sg_sim_step does (lanes
+// 0-3: the scalar part, lane_step; the whole warp: the scans), writing the
+// next observation as the tile's BF16 row and the FP32 outputs and ring
+// entries.  Same VEM draws, same simulator values as k_rollout_q; the Q
+// values differ from it only in the summation order.
+//
+// Shared memory is kept small (136 KB) so that L1 keeps room for the maps the
+// scans read: the input tile lives inside the hidden-activation buffer (it is
+// dead once layer 1 has run), the step records inside a weight buffer (free
+// during the env steps), and all of W1 (two 128-row halves) and W2 (four
+// 64-row quarters) stream through two 32 KB buffers by bulk copies every step,
+// each copy issued as soon as its buffer's previous MMAs are done; W3 stays.
 constexpr int kQtEnvs = 128;
 constexpr int kQtWarps = 32;
 constexpr int kQtThreads = kQtWarps * 32;
+constexpr uint32_t kQtBuf = 32u * 1024u;
 
 struct QtSmem {
-  uint32_t x, w1, h, w2, w3, rec, greedy, bytes;
+  uint32_t hx, b0, b1, w3, bytes;
 };
-__host__ __device__ inline QtSmem qt_smem(int k1) {
+__host__ __device__ inline QtSmem qt_smem() {
   QtSmem t;
-  t.x = 0;
-  t.w1 = tc_up((uint32_t)(kQtEnvs * k1 * 2));
-  t.h = tc_up(t.w1 + (uint32_t)(kHid * k1 * 2));
-  t.w2 = tc_up(t.h + (uint32_t)(kQtEnvs * kHid * 2));
-  t.w3 = tc_up(t.w2 + (uint32_t)(128 * kHid * 2));
-  t.rec = tc_up(t.w3 + (uint32_t)(16 * kHid * 2));
-  t.greedy = t.rec + (uint32_t)(kQtEnvs * sizeof(StepScanRec));
-  t.bytes = tc_up(t.greedy + (uint32_t)(kQtEnvs * 4));
+  t.hx = 0;
+  t.b0 = (uint32_t)(kQtEnvs * kHid * 2);
+  t.b1 = t.b0 + kQtBuf;
+  t.w3 = t.b1 + kQtBuf;
+  t.bytes = t.w3 + 16u * kHid * 2u;
   return t;
 }
 
@@ -827,6 +841,61 @@ __device__ __forceinline__ void qt_obs_to_tile(uint8_t* xs, int r, float b0, flo
   if (lane + 32 < B) *reinterpret_cast<bf16*>(xs + kmajor_offset(r, lane + 32, kQtEnvs)) = __float2bfloat16_rn(b1);
   if (lane < 5) *reinterpret_cast<bf16*>(xs + kmajor_offset(r, B + lane, kQtEnvs)) = __float2bfloat16_rn(ex);
 }
+
+// The weight stream of the fused rollout, run by the CTA's thread 0: chunk
+// copies into two buffers (one mbarrier each for the copy, one for the MMAs
+// that read the buffer) with every copy and every MMA group waited exactly
+// once, in order.
+struct QtStream {
+  uint64_t* ld;    // [2] copy complete
+  uint64_t* mm;    // [2] MMAs reading the buffer complete
+  uint8_t* buf[2];
+  uint32_t pl[2], pm[2];
+  bool ld_out[2], mm_out[2];
+  bool ok;
+  // copy `bytes` from src into buffer b once its previous MMAs are done
+  __device__ __forceinline__ void load(int b, const void* src, uint32_t bytes) {
+    if (!ok) return;
+    if (mm_out[b]) {
+      ok = mbar_wait(&mm[b], pm[b], kTcTries);
+      pm[b] ^= 1u;
+      mm_out[b] = false;
+      if (!ok) return;
+    }
+    mbar_expect_tx(&ld[b], bytes);
+    bulk_g2s(buf[b], src, bytes, &ld[b]);
+    ld_out[b] = true;
+  }
+  // MMAs D[tacc] (+)= A x buffer b^T (Rb rows, K), then commits: the buffer's
+  // barrier, and the layer barrier when `last`
+  __device__ __forceinline__ void mma(int b, uint32_t tacc, const uint8_t* a, int Rb, int K, uint64_t* layer,
+                                      bool last) {
+    if (!ok) return;
+    if (ld_out[b]) {
+      ok = mbar_wait(&ld[b], pl[b], kTcTries);
+      pl[b] ^= 1u;
+      ld_out[b] = false;
+      if (!ok) return;
+    }
+    tc_fence_after();
+    const uint32_t idesc = idesc_bf16_f32(kQtEnvs, Rb);
+    const uint32_t sa = smem_u32(a), sb = smem_u32(buf[b]);
+    const uint32_t la = kQtEnvs * 16, lb = (uint32_t)Rb * 16;
+    for (int ks = 0; ks < K / 16; ++ks)
+      tc_mma_bf16(tacc, smem_desc(sa + (uint32_t)ks * 2 * la, la, 128),
+                  smem_desc(sb + (uint32_t)ks * 2 * lb, lb, 128), idesc, ks > 0 ? 1u : 0u);
+    tc_commit(&mm[b]);
+    mm_out[b] = true;
+    if (last) tc_commit(layer);
+  }
+  // bounded waits for whatever is still in flight
+  __device__ __forceinline__ void drain() {
+    for (int b = 0; b < 2; ++b) {
+      if (mm_out[b]) mbar_wait(&mm[b], pm[b], kTcTries);
+      if (ld_out[b]) mbar_wait(&ld[b], pl[b], kTcTries);
+    }
+  }
+};
 
 // State of env i through L2: with time slicing another SM may have written
 // it during this launch.
@@ -873,48 +942,55 @@ __global__ void __launch_bounds__(kQtThreads, 1)
                    float* __restrict__ obs_out, float* __restrict__ obs_seq, uint8_t* __restrict__ act_seq,
                    float* __restrict__ rew_seq, uint8_t* __restrict__ done_seq) {
   extern __shared__ __align__(1024) uint8_t tsm[];
-  __shared__ uint64_t bar_mma, bar_ld;
+  __shared__ uint64_t bar_ld[2], bar_mm[2], bar_layer;
   __shared__ uint32_t tslot;
   __shared__ int item_sh;
+  __shared__ int ok_sh;
+  __shared__ int greedy[kQtEnvs];
   __shared__ float sb1[kHid], sb2[kHid], sb3[kOutPad];
-  const QtSmem T = qt_smem(L.k1);
+  const QtSmem T = qt_smem();
   const TcImg G = tc_img(L.k1);
-  uint8_t* xs = tsm + T.x;
-  uint8_t* w1s = tsm + T.w1;
-  uint8_t* hs = tsm + T.h;
-  uint8_t* w2s = tsm + T.w2;
+  uint8_t* hx = tsm + T.hx;  // the input tile, then H1, then H2
   uint8_t* w3s = tsm + T.w3;
-  StepScanRec* rec = reinterpret_cast<StepScanRec*>(tsm + T.rec);
-  int* greedy = reinterpret_cast<int*>(tsm + T.greedy);
+  StepScanRec* rec = reinterpret_cast<StepScanRec*>(tsm + T.b1);  // during the env steps only
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long long n = c.n_envs;
   const int nblk = (int)((n + kQtEnvs - 1) / kQtEnvs);
   const int seglen = seg > 0 ? seg : K;
   const int nseg = (K + seglen - 1) / seglen;
   const long long nitems = (long long)nblk * nseg;
+  const uint32_t w1h_bytes = 128u * (uint32_t)L.k1 * 2u, w2q_bytes = 64u * kHid * 2u;
   for (int i = tid; i < kHid; i += kQtThreads) {
     sb1[i] = __ldg(reinterpret_cast<const float*>(img + L.b1) + i);
     sb2[i] = __ldg(reinterpret_cast<const float*>(img + L.b2) + i);
   }
   if (tid < kOutPad) sb3[tid] = __ldg(reinterpret_cast<const float*>(img + L.b3) + tid);
+  for (int i = tid; i < (int)(16u * kHid * 2u / 16u); i += kQtThreads)
+    reinterpret_cast<uint4*>(w3s)[i] = __ldg(reinterpret_cast<const uint4*>(timg + G.w3) + i);
   if (warp == 0) tmem_alloc(&tslot, 256);
   if (tid == 0) {
-    mbar_init(&bar_mma, 1);
-    mbar_init(&bar_ld, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&bar_ld[b], 1);
+      mbar_init(&bar_mm[b], 1);
+    }
+    mbar_init(&bar_layer, 1);
+    ok_sh = 1;
   }
+  fence_async_smem();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tacc = tslot;
-  if (tid == 0) {
-    mbar_expect_tx(&bar_ld, G.w2a + 128u * kHid * 2u + 16u * kHid * 2u);
-    bulk_g2s(w1s, timg + G.w1, G.w2a, &bar_ld);
-    bulk_g2s(w3s, timg + G.w3, 16u * kHid * 2u, &bar_ld);
-    bulk_g2s(w2s, timg + G.w2a, 128u * kHid * 2u, &bar_ld);
-  }
-  // W2's buffer: half 0 in flight (ld_out) or resident (w2a), else half 1
-  bool ld_out = true, w2a = false, mma_out = false, ok = true;
-  uint32_t pm = 0, pl = 0;
+  QtStream S;  // meaningful in thread 0
+  S.ld = bar_ld;
+  S.mm = bar_mm;
+  S.buf[0] = tsm + T.b0;
+  S.buf[1] = tsm + T.b1;
+  S.pl[0] = S.pl[1] = S.pm[0] = S.pm[1] = 0u;
+  S.ld_out[0] = S.ld_out[1] = S.mm_out[0] = S.mm_out[1] = false;
+  S.ok = true;
+  uint32_t player = 0;  // phase of the layer barrier
+  bool layer_out = false, ok = true;
   const unsigned long long rbase = use_replay ? *rp.steps : 0ull;
   const int B = c.B;
   const int row0 = warp * 4;
@@ -953,7 +1029,7 @@ __global__ void __launch_bounds__(kQtThreads, 1)
     // the tile: zero (padding columns, rows without an env), then the first
     // observation of the segment
     for (int i = tid; i < kQtEnvs * L.k1 / 8; i += kQtThreads)
-      reinterpret_cast<uint4*>(xs)[i] = make_uint4(0u, 0u, 0u, 0u);
+      reinterpret_cast<uint4*>(hx)[i] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
     if (s0 > 0 && use_replay) {
       const long long sl = (long long)((rbase + (unsigned long long)s0) % (unsigned long long)rp.slots);
@@ -961,7 +1037,7 @@ __global__ void __launch_bounds__(kQtThreads, 1)
         const int ie = __shfl_sync(kFull, env, e);
         const float* src = rp.s + (sl * rp.n_envs + ie) * rp.obs_dim;
         for (int k = lane; k < c.obs_dim; k += 32)
-          *reinterpret_cast<bf16*>(xs + kmajor_offset(row0 + e, k, kQtEnvs)) = __float2bfloat16_rn(__ldcg(src + k));
+          *reinterpret_cast<bf16*>(hx + kmajor_offset(row0 + e, k, kQtEnvs)) = __float2bfloat16_rn(__ldcg(src + k));
       }
     } else {
       if (live) lane_observe(c, p, env, load_env_l2(p, env), rec[row0 + lane]);
@@ -971,7 +1047,7 @@ __global__ void __launch_bounds__(kQtThreads, 1)
         float b0, b1;
         scan_env(c, p, p.maps[r.map], r.nb, r.stepb, r.ax, r.ay, r.aphi, r.asigma,
                  ((uint64_t)r.anhi << 32) | r.anlo, lane, b0, b1);
-        qt_obs_to_tile(xs, row0 + e, b0, b1, lane < 5 ? r.exa[lane] : 0.0f, B, lane);
+        qt_obs_to_tile(hx, row0 + e, b0, b1, lane < 5 ? r.exa[lane] : 0.0f, B, lane);
         if (use_replay) {
           const long long sl = (long long)((rbase + (unsigned long long)s0) % (unsigned long long)rp.slots);
           write_row(rp.s + (sl * rp.n_envs + r.env) * rp.obs_dim, b0, b1, r.exa, B, lane);
@@ -984,95 +1060,68 @@ __global__ void __launch_bounds__(kQtThreads, 1)
       tc_fence_before();
       __syncthreads();
       tc_fence_after();
-      if (ok && !w2a && !ld_out) {
-        // half 0 for this step (the previous item's last step left half 1)
-        if (tid == 0) {
-          mbar_expect_tx(&bar_ld, 128u * kHid * 2u);
-          bulk_g2s(w2s, timg + G.w2a, 128u * kHid * 2u, &bar_ld);
-        }
-        ld_out = true;
+      // layer 1: two 128-unit halves of W1 through the buffers
+      if (tid == 0) {
+        if (!S.ld_out[0]) S.load(0, timg + G.w1h, w1h_bytes);
+        S.load(1, timg + G.w1h + w1h_bytes, w1h_bytes);
+        S.mma(0, tacc, hx, 128, L.k1, &bar_layer, false);
+        S.mma(1, tacc + 128u, hx, 128, L.k1, &bar_layer, true);
+        S.load(0, timg + G.w2q, w2q_bytes);  // W2 quarter 0, once half 0 of W1 is consumed
+        if (!S.ok) ok_sh = 0;
       }
-      if (ok && ld_out) {
-        ok = __syncthreads_and(mbar_wait(&bar_ld, pl, kTcTries));
-        if (ok) {
-          pl ^= 1u;
-          ld_out = false;
-          w2a = true;
-        }
+      layer_out = true;
+      __syncthreads();  // ok_sh as thread 0 left it
+      ok = __syncthreads_and(ok_sh && mbar_wait(&bar_layer, player, kTcTries));
+      if (!ok) break;
+      player ^= 1u;
+      layer_out = false;
+      tc_fence_after();
+      qt_epilogue(tacc, sb1, hx, warp, lane);  // H1 over the input tile
+      fence_async_smem();
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+      // layer 2: four 64-unit quarters of W2 through the buffers
+      if (tid == 0) {
+        S.mma(0, tacc, hx, 64, kHid, &bar_layer, false);
+        S.load(1, timg + G.w2q + w2q_bytes, w2q_bytes);
+        S.mma(1, tacc + 64u, hx, 64, kHid, &bar_layer, false);
+        S.load(0, timg + G.w2q + 2u * w2q_bytes, w2q_bytes);
+        S.mma(0, tacc + 128u, hx, 64, kHid, &bar_layer, false);
+        S.load(1, timg + G.w2q + 3u * w2q_bytes, w2q_bytes);
+        S.mma(1, tacc + 192u, hx, 64, kHid, &bar_layer, true);
+        if (!S.ok) ok_sh = 0;
       }
-      if (ok) {
-        if (tid == 0) tc_layer(tacc, xs, w1s, kHid, L.k1, &bar_mma);
-        mma_out = true;
-        ok = __syncthreads_and(mbar_wait(&bar_mma, pm, kTcTries));
-        if (ok) {
-          pm ^= 1u;
-          mma_out = false;
-        }
-      }
-      if (ok) {
+      layer_out = true;
+      __syncthreads();  // ok_sh as thread 0 left it
+      ok = __syncthreads_and(ok_sh && mbar_wait(&bar_layer, player, kTcTries));
+      if (!ok) break;
+      player ^= 1u;
+      layer_out = false;
+      tc_fence_after();
+      qt_epilogue(tacc, sb2, hx, warp, lane);  // H2 over H1 (layer 2 is complete)
+      fence_async_smem();
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+      // head (W3 resident), and the next step's W1 half 0 into buffer 0
+      if (tid == 0) {
         tc_fence_after();
-        qt_epilogue(tacc, sb1, hs, warp, lane);
-        fence_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        if (tid == 0) tc_layer(tacc, hs, w2s, 128, kHid, &bar_mma);
-        mma_out = true;
-        ok = __syncthreads_and(mbar_wait(&bar_mma, pm, kTcTries));
-        if (ok) {
-          pm ^= 1u;
-          mma_out = false;
-        }
+        const uint32_t idesc = idesc_bf16_f32(kQtEnvs, 16);
+        const uint32_t sa = smem_u32(hx), sw = smem_u32(w3s);
+        for (int ks = 0; ks < kHid / 16; ++ks)
+          tc_mma_bf16(tacc, smem_desc(sa + (uint32_t)ks * 2 * (kQtEnvs * 16), kQtEnvs * 16, 128),
+                      smem_desc(sw + (uint32_t)ks * 2 * 256, 256, 128), idesc, ks > 0 ? 1u : 0u);
+        tc_commit(&bar_layer);
+        if (t + 1 < s1) S.load(0, timg + G.w1h, w1h_bytes);
+        if (!S.ok) ok_sh = 0;
       }
-      if (ok) {
-        if (tid == 0) {
-          mbar_expect_tx(&bar_ld, 128u * kHid * 2u);
-          bulk_g2s(w2s, timg + G.w2b, 128u * kHid * 2u, &bar_ld);
-        }
-        ld_out = true;
-        w2a = false;
-        ok = __syncthreads_and(mbar_wait(&bar_ld, pl, kTcTries));
-        if (ok) {
-          pl ^= 1u;
-          ld_out = false;
-        }
-      }
-      if (ok) {
-        if (tid == 0) tc_layer(tacc + 128u, hs, w2s, 128, kHid, &bar_mma);
-        mma_out = true;
-        ok = __syncthreads_and(mbar_wait(&bar_mma, pm, kTcTries));
-        if (ok) {
-          pm ^= 1u;
-          mma_out = false;
-        }
-      }
-      if (ok) {
-        if (t + 1 < s1) {
-          // the next step's half 0 streams in while this step finishes
-          if (tid == 0) {
-            mbar_expect_tx(&bar_ld, 128u * kHid * 2u);
-            bulk_g2s(w2s, timg + G.w2a, 128u * kHid * 2u, &bar_ld);
-          }
-          ld_out = true;
-        }
-        tc_fence_after();
-        qt_epilogue(tacc, sb2, hs, warp, lane);
-        fence_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        if (tid == 0) tc_layer(tacc, hs, w3s, 16, kHid, &bar_mma);
-        mma_out = true;
-        ok = __syncthreads_and(mbar_wait(&bar_mma, pm, kTcTries));
-        if (ok) {
-          pm ^= 1u;
-          mma_out = false;
-        }
-      }
-      if (!ok) {
-        if (tid == 0) atomicOr(p.status, SG_DEV_TIMEOUT);
-        break;  // CTA-uniform: the launch's outputs from here on are incomplete
-      }
+      layer_out = true;
+      __syncthreads();  // ok_sh as thread 0 left it
+      ok = __syncthreads_and(ok_sh && mbar_wait(&bar_layer, player, kTcTries));
+      if (!ok) break;
+      player ^= 1u;
+      layer_out = false;
       if (warp < 4) {
         float v[32];
         tc_fence_after();
@@ -1082,6 +1131,9 @@ __global__ void __launch_bounds__(kQtThreads, 1)
         for (int j = 0; j < kOut; ++j) o[j] = v[j] + sb3[j];
         greedy[warp * 32 + lane] = (int)greedy_action(o, nullptr, L.plain);
       }
+      // the next input tile starts from zero (H2 is dead after the head)
+      for (int i = tid; i < kQtEnvs * L.k1 / 8; i += kQtThreads)
+        reinterpret_cast<uint4*>(hx)[i] = make_uint4(0u, 0u, 0u, 0u);
       tc_fence_before();
       __syncthreads();
       tc_fence_after();
@@ -1135,7 +1187,7 @@ __global__ void __launch_bounds__(kQtThreads, 1)
           ex = r.exb;
         }
         // the observation t + 1: the next tile row, the outputs, the next ring entry's s
-        qt_obs_to_tile(xs, row0 + e, b0, b1, lane < 5 ? ex[lane] : 0.0f, B, lane);
+        qt_obs_to_tile(hx, row0 + e, b0, b1, lane < 5 ? ex[lane] : 0.0f, B, lane);
         if (obs_seq) write_row(obs_seq + ((long long)t * n + ie) * c.obs_dim, b0, b1, ex, B, lane);
         if (t == K - 1 && obs_out) write_row(obs_out + (long long)ie * c.obs_dim, b0, b1, ex, B, lane);
         if (use_replay && t + 1 < K)
@@ -1143,15 +1195,19 @@ __global__ void __launch_bounds__(kQtThreads, 1)
       }
       fence_async_smem();
     }
+    if (!ok) {
+      if (tid == 0) atomicOr(p.status, SG_DEV_TIMEOUT);
+      break;  // CTA-uniform: the launch's outputs from here on are incomplete
+    }
     if (!sync) break;
     // publish the block's segment: its env state and ring entries are stored
     __threadfence();
     __syncthreads();
-    if (tid == 0 && ok) qt_st_release(&sync[blk], (unsigned)(s0 / seglen + 1));
+    if (tid == 0) qt_st_release(&sync[blk], (unsigned)(s0 / seglen + 1));
   }
   // free the tensor memory once nothing is in flight (bounded waits)
-  if (mma_out) mbar_wait(&bar_mma, pm, kTcTries);
-  if (ld_out) mbar_wait(&bar_ld, pl, kTcTries);
+  if (tid == 0) S.drain();
+  if (layer_out && ok_sh) mbar_wait(&bar_layer, player, kTcTries);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -1566,7 +1622,7 @@ extern "C" int sg_qnet_create(int32_t n_in, int32_t arch, int32_t max_batch, uin
   // cannot lower it below what a wider one launches with.
   const ImgLayout widest = img_layout(69);
   if ((rc = set_smem_attr((const void*)k_qnet_forward_tc, kTcSmemLaunch)) ||
-      (rc = set_smem_attr((const void*)k_rollout_q_tc, kTcSmemLaunch)) ||
+      (rc = set_smem_attr((const void*)k_rollout_q_tc, qt_smem().bytes)) ||
       (rc = set_smem_attr((const void*)k_rollout_q<1, false>, fwd_smem(widest))) ||
       (rc = set_smem_attr((const void*)k_rollout_q<2, false>, fwd_smem(widest, 32))) ||
       (rc = set_smem_attr((const void*)k_rollout_q<1, true>, fwd_smem(widest))) ||
@@ -1855,7 +1911,7 @@ int sg_rollout_eps_q(sg_sim* sim, int K, sg_qnet* q, const float* eps, sg_replay
       grid = std::min(nblk * ((K + seg - 1) / seg), sms);
       SG_CUDA(cudaMemsetAsync(sim->q_sync_dev, 0, sizeof(unsigned) * (size_t)(nblk + 2), stream));
     }
-    k_rollout_q_tc<<<grid, kQtThreads, kTcSmemLaunch, stream>>>(
+    k_rollout_q_tc<<<grid, kQtThreads, qt_smem().bytes, stream>>>(
         sim->dc, sg_sim_ptrs(sim), q->img, q->img_tc, q->IL, K, eps, rd, rp ? 1 : 0, sim->map_order_dev, seg,
         seg > 0 ? sim->q_sync_dev : nullptr, obs, obs_seq, act_seq, rew_seq, done_seq);
   } else if (mt == 2)
