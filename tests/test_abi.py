@@ -76,3 +76,45 @@ def test_create_rejects_bad_config_without_touching_the_gpu():
     em_bad = (C.c_int32 * 4)(0, 0, 0, 3)  # map index out of range
     assert lib.sg_sim_create(C.byref(cfg), 1, ptrs, w, w, em_bad, None, C.byref(h)) == _lib.SG_E_INVAL
     assert lib.sg_sim_step(None, None, None, None, None, None, None) == _lib.SG_E_INVAL
+
+
+@pytest.mark.parametrize("field,value", [("n_envs", 0), ("n_envs", (1 << 24) + 1), ("n_beams", 65),
+                                         ("range_max", 4097.0), ("march_step", 0.0), ("t_max", 0),
+                                         ("delay_hi", 3), ("n_dyn", -1)])
+def test_create_rejects_each_limit_plus_one(field, value):
+    """One past each documented limit is refused on the host (the limits
+    themselves: 2^24 envs, 64 beams, 4,096 samples per beam, map sides of
+    16,384, are exercised on the GPU)."""
+    from paper_2305_04180_gb300 import _lib
+    from paper_2305_04180_gb300.sim import make_config
+    from workloads.configs import base_params
+
+    lib = _lib.load()
+    cfg = make_config(base_params(march_step=1.0), 4)
+    setattr(cfg, field, value)
+    h = C.c_void_p()
+    grid = (C.c_uint8 * 16)()
+    ptrs = (C.c_void_p * 1)(C.addressof(grid))
+    w = (C.c_int32 * 1)(4)
+    em = (C.c_int32 * 4)(0, 0, 0, 0)
+    assert lib.sg_sim_create(C.byref(cfg), 1, ptrs, w, w, em, None, C.byref(h)) == _lib.SG_E_INVAL
+    assert not h.value
+
+
+@pytest.mark.parametrize("side", [(16385, 4), (4, 16385), (0, 4)])
+def test_create_rejects_map_sides_past_the_limit(side):
+    from paper_2305_04180_gb300 import _lib
+    from paper_2305_04180_gb300.sim import make_config
+    from workloads.configs import base_params
+
+    lib = _lib.load()
+    cfg = make_config(base_params(), 1)
+    h = C.c_void_p()
+    grid = (C.c_uint8 * 16)()
+    ptrs = (C.c_void_p * 1)(C.addressof(grid))
+    mw = (C.c_int32 * 1)(side[0])
+    mh = (C.c_int32 * 1)(side[1])
+    em = (C.c_int32 * 1)(0)
+    assert lib.sg_sim_create(C.byref(cfg), 1, ptrs, mw, mh, em, None, C.byref(h)) == _lib.SG_E_INVAL
+    assert lib.sg_sim_create(C.byref(cfg), 0, ptrs, mw, mh, em, None, C.byref(h)) == _lib.SG_E_INVAL
+    assert lib.sg_sim_rollout(None, 0, 0, *([None] * 9)) == _lib.SG_E_INVAL

@@ -357,3 +357,74 @@ def test_step_other_march_steps(delta, rmax):
     env_map = (np.arange(40) % 5).astype(np.int32)
     g, o, _ = _pair(p, maps, env_map)
     _teacher_forced(g, o, 60, seed=5)
+
+
+def test_maximum_map_range_and_beams():
+    """The largest map side (16,384 cells), the longest range (4,096 samples
+    per beam) and the most beams (64): teacher-forced steps bit-exact against
+    the oracle, and a pipelined rollout from the same start equal to it."""
+    side = 16384
+    grid = empty_map(side)
+    rng = np.random.default_rng(8)
+    for _ in range(300):
+        x0, y0 = rng.integers(0, 4000, 2)
+        wx, wy = rng.integers(2, 60, 2)
+        grid[y0:y0 + wy, x0:x0 + wx] = 1
+    grid[:80, :80] = 0  # a clear start
+    p = base_params(n_beams=64, range_max=4096.0, march_step=1.0, **{k: v for k, v in workload("dr1024").params.items()
+                                                                       if k.endswith(("_lo", "_hi"))})
+    n = 6
+    env_map = np.zeros(n, np.int32)
+    g, o, _ = _pair(p, [grid], env_map)
+    _teacher_forced(g, o, 25, seed=9)
+    # the pipelined kernel from a fresh start against the one-warp-per-env kernel
+    runs = []
+    for launch in (None, dict(kernel="pipe", warps_per_block=8, obs_warps=7, segment=32)):
+        s = _sim(p, [grid], env_map)
+        if launch:
+            s.set_launch(**launch)
+        s.reset()
+        rew = torch.empty((100, n), device="cuda")
+        obs = s.new_obs()
+        s.rollout(100, obs=obs, rew_seq=rew)
+        torch.cuda.synchronize()
+        assert s.status() == 0
+        runs.append((rew.cpu().numpy(), obs.cpu().numpy(), s.get_state()))
+    (r0, b0, (f0, u0)), (r1, b1, (f1, u1)) = runs
+    assert np.array_equal(bits(r0), bits(r1)) and np.array_equal(bits(b0), bits(b1))
+    assert np.array_equal(bits(f0), bits(f1)) and np.array_equal(u0, u1)
+
+
+@pytest.mark.parametrize("launch", [None, dict(kernel="pipe", warps_per_block=8, obs_warps=7, order="map",
+                                                segment=32)])
+def test_maximum_env_count_sampled_against_oracle(launch):
+    """2^24 envs (the largest batch) on the 32-map domain-randomised
+    workload: 64 free-running steps (two 32-step segments in the time-sliced
+    launch), then envs at both ends and in between replayed one by one on
+    the oracle."""
+    n = 1 << 24
+    w = workload("dr1024", n_envs=n)
+    maps = w.maps()
+    g = _sim(w.params, maps, w.env_map)
+    if launch:
+        g.set_launch(**launch)
+    g.reset()
+    K = 64
+    rew = torch.empty((K, n), device="cuda")
+    done = torch.empty((K, n), dtype=torch.uint8, device="cuda")
+    obs = g.new_obs()
+    g.rollout(K, obs=obs, rew_seq=rew, done_seq=done)
+    torch.cuda.synchronize()
+    assert g.status() == 0
+    sample = np.array([0, 1, 31, 4095, 1 << 20, (1 << 23) + 7, n - 33, n - 2, n - 1])
+    idx = torch.from_numpy(sample).cuda()
+    rew_s = rew[:, idx].cpu().numpy()
+    done_s = done[:, idx].cpu().numpy()
+    obs_s = obs[idx].cpu().numpy()
+    o = OracleSim(w.params, maps, w.env_map, prec="f32")
+    for j, i in enumerate(sample):
+        o.reset_env(int(i), 0)
+        for k in range(K):
+            oobs, orew, odone, _ = o.step_one(int(i), o.random_action(int(i), k))
+            assert odone == done_s[k, j] and bits(np.float32(orew)) == bits(rew_s[k, j]), (i, k)
+        assert np.array_equal(bits(oobs), bits(obs_s[j])), i
