@@ -378,6 +378,83 @@ __device__ __forceinline__ float scan_pose(const DevCfg& c, const EnvConst& k, f
   return __uint_as_float(__reduce_min_sync(kFull, __float_as_uint(mn)));
 }
 
+// The motion (delay, Eq. 5, Eq. 6) of steps j0 .. n-1 from state s as if no
+// episode ended, lane j taking what belongs to step j (actions in lane j of
+// abatch).  Only the velocity / heading recurrences and the position sums run
+// in step order (every lane the same); the delayed action, the target
+// velocities, sin/cos of each step's heading and the Eq. 6 increments are
+// lane-parallel.  Every value is the float32 expression of kinematics(),
+// evaluated in the same order.  Lane j writes step j's post state (with its
+// action) to buf[j].post and returns its position and episode step in mx,
+// my, mep; bad is set in the lanes whose action index is out of range.
+__device__ __forceinline__ void motion_run(const DevCfg& c, const Env& s, int j0, int n, uint32_t abatch,
+                                           StepRec* buf, int lane, bool& bad, float& mx, float& my,
+                                           uint32_t& mep) {
+  const bool mine = lane >= j0 && lane < n;
+  const uint32_t q0 = s.fifo & 0xFFu, q1 = (s.fifo >> 8) & 0xFFu, d = (s.fifo >> 16) & 0xFFu;
+  const uint32_t a = abatch;
+  // the actions one and two steps back: this run's, else the FIFO's
+  const uint32_t up1 = __shfl_up_sync(kFull, a & 0xFFu, 1), up2 = __shfl_up_sync(kFull, a & 0xFFu, 2);
+  const uint32_t am1 = lane - 1 >= j0 ? up1 : q0;
+  const uint32_t am2 = lane - 2 >= j0 ? up2 : (lane - 1 == j0 ? q0 : q1);
+  const uint32_t ahat = d == 0 ? a : (d == 1 ? am1 : am2);
+  const uint32_t fifo = (a & 0xFFu) | (am1 << 8) | (d << 16);
+  float vhl = 0.0f, vha = 0.0f;
+  if (ahat < (uint32_t)c.n_actions) {
+    vhl = c.av[ahat] * s.cap;
+    vha = c.aw[ahat] * s.cap;
+  }
+  const float omk = 1.0f - s.K;
+  const float pl = omk * vhl, pa = omk * vha;
+  if (mine && a >= (uint32_t)c.n_actions) bad = true;
+  // Eq. 5 and the heading part of Eq. 6, in step order
+  float vl = s.vl, va = s.va, phi = s.phi;
+  float jvl = 0.0f, jva = 0.0f, jphi = s.phi;
+  for (int j = j0; j < n; ++j) {
+    const float plj = __shfl_sync(kFull, pl, j), paj = __shfl_sync(kFull, pa, j);
+    vl = s.K * vl + plj;
+    va = s.K * va + paj;
+    float ph = phi + s.dt * va;
+    if (ph >= kPi)
+      ph = ph - 2.0f * kPi;
+    else if (ph < -kPi)
+      ph = ph + 2.0f * kPi;
+    phi = ph;
+    if (lane == j) {
+      jvl = vl;
+      jva = va;
+      jphi = phi;
+    }
+  }
+  float sn = s.sphi, cs = s.cphi;
+  if (mine) f_sincos(jphi, sn, cs);
+  // the position part of Eq. 6 uses the heading before the step: step j0's
+  // from s, step j's from lane j - 1
+  const float cu = __shfl_up_sync(kFull, cs, 1), su = __shfl_up_sync(kFull, sn, 1);
+  const float cprev = lane == j0 ? s.cphi : cu, sprev = lane == j0 ? s.sphi : su;
+  const float tx = s.dt * (jvl * cprev), ty = s.dt * (jvl * sprev);
+  float x = s.x, y = s.y, jx = s.x, jy = s.y;
+  for (int j = j0; j < n; ++j) {
+    x = x - __shfl_sync(kFull, tx, j);
+    y = y - __shfl_sync(kFull, ty, j);
+    if (lane == j) {
+      jx = x;
+      jy = y;
+    }
+  }
+  const uint32_t steps = (uint32_t)(lane - j0 + 1);
+  if (mine) {
+    Env e = s;
+    e.x = jx, e.y = jy, e.phi = jphi, e.vl = jvl, e.va = jva;
+    e.ep_step = s.ep_step + steps, e.t = s.t + steps, e.fifo = fifo;
+    e.sphi = sn, e.cphi = cs;
+    pack_env(reinterpret_cast<uint4*>(&buf[lane].post), e, a);
+  }
+  mx = jx;
+  my = jy;
+  mep = s.ep_step + steps;
+}
+
 // The pose chain of one chunk (n <= 32 steps, actions in lane j of abatch)
 // by one warp, into the records buf[0..n).  The motion of a step (delay,
 // Eq. 5, Eq. 6) needs the previous state only, and an episode end changes
@@ -401,26 +478,20 @@ __device__ __forceinline__ void pose_chunk(const DevCfg& c, const SimPtrs& p, co
   Obst b = {0.0f, 0.0f, 0.0f, 0.0f};
   if (kDyn && lane < c.n_dyn) b = dst[lane];
   while (j0 < n) {
-    Env q = s;
     Obst bq = b;
-    float mx = 0.0f, my = 0.0f;
-    uint32_t mep = 0;
-#pragma unroll 4
-    for (int j = j0; j < n; ++j) {
-      const uint32_t a = __shfl_sync(kFull, abatch, j);
-      const float dt = q.dt;  // the discs move with the episode's control interval
-      bad |= kinematics(c, q, a);
-      mx = lane == j ? q.x : mx;
-      my = lane == j ? q.y : my;
-      mep = lane == j ? q.ep_step : mep;
-      if (lane == 0) pack_env(reinterpret_cast<uint4*>(&buf[j].post), q, a);
-      if (kDyn && lane < c.n_dyn) {
-        dyn_move(c, k.m, k.clr, dt, bq);
-        dpost[j].x[lane] = bq.x;
-        dpost[j].y[lane] = bq.y;
-      }
+    float mx, my;
+    uint32_t mep;
+    motion_run(c, s, j0, n, abatch, buf, lane, bad, mx, my, mep);
+    if (kDyn) {
+      // the discs move with the episode's control interval
+      if (lane < c.n_dyn)
+        for (int j = j0; j < n; ++j) {
+          dyn_move(c, k.m, k.clr, s.dt, bq);
+          dpost[j].x[lane] = bq.x;
+          dpost[j].y[lane] = bq.y;
+        }
     }
-    if (kDyn) __syncwarp();
+    __syncwarp();
     uint32_t done = 0;
     bool slow = false;
     if (lane >= j0 && lane < n) {
@@ -454,7 +525,7 @@ __device__ __forceinline__ void pose_chunk(const DevCfg& c, const SimPtrs& p, co
     const int d = donem ? __ffs(donem) - 1 : n;
     if (lane >= j0 && lane < d) buf[lane].done = 0u;
     if (d == n) {
-      s = q;
+      s = unpack_env(reinterpret_cast<const uint4*>(&buf[n - 1].post));
       b = bq;
       break;
     }
@@ -485,7 +556,7 @@ __device__ __forceinline__ void pose_chunk(const DevCfg& c, const SimPtrs& p, co
     j0 = d + 1;
   }
   if (kDyn && lane < c.n_dyn) dst[lane] = b;
-  if (bad && lane == 0) atomicOr(p.status, 1u);
+  if (__any_sync(kFull, bad) && lane == 0) atomicOr(p.status, 1u);
 }
 
 // Consume the observation records of one chunk (steps i0 .. i1-1) through
