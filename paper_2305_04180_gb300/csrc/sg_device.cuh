@@ -266,11 +266,24 @@ __device__ __forceinline__ int march(const uint8_t* __restrict__ clr, int W, int
                                      float ux, float uy, float delta, int kmax, int skip_ok) {
   int k = 1;
   if ((kUnitStep || skip_ok) && x >= 0.0f && y >= 0.0f && x < (float)W && y < (float)H) {
+    // Conversions on the FP32 and integer pipes instead of the conversion
+    // unit: for an integer or float v with |v| < 2^22, v + 1.5 * 2^23 lies in
+    // [2^23, 2^24), where the floats are exactly the integers, so the bit
+    // pattern of that sum minus the pattern of 1.5 * 2^23 is the integer.
+    // (uint)k + pattern, reinterpreted, minus 1.5 * 2^23 is (float)k; the
+    // sum rounded down is floor(v).  Sample cells lie in [-2, 16386), the
+    // map offset iy * ld + ix in int range, so it is taken modulo 2^32 from
+    // the two patterns (bias folds in the two subtracted patterns).
+    constexpr float kMagic = 12582912.0f;
+    constexpr uint32_t kMagicBits = 0x4B400000u;
+    const uint32_t bias = 0u - kMagicBits * (uint32_t)(ld + 1);
     while (k <= kmax) {
+      const float kf = __uint_as_float((uint32_t)k + kMagicBits) - kMagic;
       // with a unit step, (float)k * 1.0f is (float)k exactly
-      const float t = kUnitStep ? (float)k : (float)k * delta;
-      const int ix = __float2int_rd(fmaf(t, ux, x)), iy = __float2int_rd(fmaf(t, uy, y));
-      const int s = __ldg(clr + iy * ld + ix);
+      const float t = kUnitStep ? kf : kf * delta;
+      const uint32_t bx = __float_as_uint(__fadd_rd(fmaf(t, ux, x), kMagic));
+      const uint32_t by = __float_as_uint(__fadd_rd(fmaf(t, uy, y), kMagic));
+      const int s = __ldg(clr + (int)(by * (uint32_t)ld + bx + bias));
       if (s == 0) return k;
       k += s;
     }
