@@ -947,6 +947,8 @@ __global__ void __launch_bounds__(kQtThreads, 1)
   __shared__ int item_sh;
   __shared__ int ok_sh;
   __shared__ int greedy[kQtEnvs];
+  __shared__ uint8_t act_sh[kQtEnvs];
+  __shared__ int scan_next;
   __shared__ float sb1[kHid], sb2[kHid], sb3[kOutPad];
   const QtSmem T = qt_smem();
   const TcImg G = tc_img(L.k1);
@@ -1134,6 +1136,7 @@ __global__ void __launch_bounds__(kQtThreads, 1)
       // the next input tile starts from zero (H2 is dead after the head)
       for (int i = tid; i < kQtEnvs * L.k1 / 8; i += kQtThreads)
         reinterpret_cast<uint4*>(hx)[i] = make_uint4(0u, 0u, 0u, 0u);
+      if (tid == 0) scan_next = 0;
       tc_fence_before();
       __syncthreads();
       tc_fence_after();
@@ -1151,16 +1154,25 @@ __global__ void __launch_bounds__(kQtThreads, 1)
       const uint32_t d = lane_step(c, p, env, live, s, a, rec[row0 + (live ? lane : 0)], lane);
       if (live) {
         store_env(p, env, s);
+        act_sh[row0 + lane] = (uint8_t)a;
         if (act_seq) act_seq[(long long)t * n + env] = (uint8_t)a;
         if (done_seq) done_seq[(long long)t * n + env] = (uint8_t)d;
       }
-      __syncwarp();
+      // every record of the tile is written; the scans (one or two per env,
+      // 16 to 64 beams) are handed out row by row through a shared counter,
+      // so that no warp waits at the next step's barrier for a slow one
+      __syncthreads();
       const long long slot_t =
           use_replay ? (long long)((rbase + (unsigned long long)t) % (unsigned long long)rp.slots) : 0;
       const long long slot_n =
           use_replay ? (long long)((rbase + (unsigned long long)t + 1ull) % (unsigned long long)rp.slots) : 0;
-      for (int e = 0; e < nv; ++e) {
-        const StepScanRec& r = rec[row0 + e];
+      const int rows = (int)min((long long)kQtEnvs, n - (long long)blk * kQtEnvs);
+      for (;;) {
+        int e = 0;
+        if (lane == 0) e = atomicAdd(&scan_next, 1);
+        e = __shfl_sync(kFull, e, 0);
+        if (e >= rows) break;
+        const StepScanRec& r = rec[e];
         const int ie = r.env;
         const uint32_t de = r.done;
         const MapDesc m = p.maps[r.map];
@@ -1168,7 +1180,7 @@ __global__ void __launch_bounds__(kQtThreads, 1)
         const float mn = scan_env(c, p, m, r.nb, r.stepb, r.ax, r.ay, r.aphi, r.asigma,
                                   ((uint64_t)r.anhi << 32) | r.anlo, lane, b0, b1);
         const float rw = (de & 1u) ? -10.0f : (de & 2u) ? 75.0f : reward_finish(c, r.rpart, mn);
-        const uint32_t ae = __shfl_sync(kFull, a, e);
+        const uint32_t ae = act_sh[e];
         if (use_replay) {
           // transition t: s2 is the observation after the step, before a reset
           const long long en = slot_t * rp.n_envs + ie;
@@ -1187,7 +1199,7 @@ __global__ void __launch_bounds__(kQtThreads, 1)
           ex = r.exb;
         }
         // the observation t + 1: the next tile row, the outputs, the next ring entry's s
-        qt_obs_to_tile(hx, row0 + e, b0, b1, lane < 5 ? ex[lane] : 0.0f, B, lane);
+        qt_obs_to_tile(hx, e, b0, b1, lane < 5 ? ex[lane] : 0.0f, B, lane);
         if (obs_seq) write_row(obs_seq + ((long long)t * n + ie) * c.obs_dim, b0, b1, ex, B, lane);
         if (t == K - 1 && obs_out) write_row(obs_out + (long long)ie * c.obs_dim, b0, b1, ex, B, lane);
         if (use_replay && t + 1 < K)
