@@ -794,15 +794,19 @@ __global__ void __launch_bounds__(512 * MT, 1)
 // values differ from it only in the summation order.
 //
 // Shared memory is kept small (136 KB) so that L1 keeps room for the maps the
-// scans read: the input tile lives inside the hidden-activation buffer (it is
-// dead once layer 1 has run), the step records inside a weight buffer (free
-// during the env steps), and all of W1 (two 128-row halves) and W2 (four
-// 64-row quarters) stream through two 32 KB buffers by bulk copies every step,
-// each copy issued as soon as its buffer's previous MMAs are done; W3 stays.
+// scans read: the input tile (at most 20 KB) and the step records (16 KB,
+// from byte 32 K) live inside the hidden-activation buffer, which holds H1
+// and H2 during the network only, and all of W1 (two 128-row halves) and W2
+// (four 64-row quarters) stream through two 32 KB buffers by bulk copies
+// every step, each copy issued as soon as its buffer's previous MMAs are
+// done (both W1 halves during the env steps, two W2 quarters during the
+// layer-1 epilogue); W3 stays.
 constexpr int kQtEnvs = 128;
 constexpr int kQtWarps = 32;
 constexpr int kQtThreads = kQtWarps * 32;
 constexpr uint32_t kQtBuf = 32u * 1024u;
+constexpr uint32_t kQtRecOff = 32u * 1024u;  // records in the activation buffer (input tile: 256 k1 <= 20 KB)
+static_assert(kQtRecOff + kQtEnvs * 128u <= (uint32_t)(kQtEnvs * kHid * 2), "records fit the activation buffer");
 
 struct QtSmem {
   uint32_t hx, b0, b1, w3, bytes;
@@ -954,7 +958,7 @@ __global__ void __launch_bounds__(kQtThreads, 1)
   const TcImg G = tc_img(L.k1);
   uint8_t* hx = tsm + T.hx;  // the input tile, then H1, then H2
   uint8_t* w3s = tsm + T.w3;
-  StepScanRec* rec = reinterpret_cast<StepScanRec*>(tsm + T.b1);  // during the env steps only
+  StepScanRec* rec = reinterpret_cast<StepScanRec*>(tsm + T.hx + kQtRecOff);  // during the env steps only
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long long n = c.n_envs;
   const int nblk = (int)((n + kQtEnvs - 1) / kQtEnvs);
@@ -1062,13 +1066,16 @@ __global__ void __launch_bounds__(kQtThreads, 1)
       tc_fence_before();
       __syncthreads();
       tc_fence_after();
-      // layer 1: two 128-unit halves of W1 through the buffers
+      // layer 1: two 128-unit halves of W1 through the buffers (normally
+      // loaded during the previous env steps), then W2 quarters 0 and 1 into
+      // them as soon as each half's MMAs are done
       if (tid == 0) {
         if (!S.ld_out[0]) S.load(0, timg + G.w1h, w1h_bytes);
-        S.load(1, timg + G.w1h + w1h_bytes, w1h_bytes);
+        if (!S.ld_out[1]) S.load(1, timg + G.w1h + w1h_bytes, w1h_bytes);
         S.mma(0, tacc, hx, 128, L.k1, &bar_layer, false);
         S.mma(1, tacc + 128u, hx, 128, L.k1, &bar_layer, true);
-        S.load(0, timg + G.w2q, w2q_bytes);  // W2 quarter 0, once half 0 of W1 is consumed
+        S.load(0, timg + G.w2q, w2q_bytes);
+        S.load(1, timg + G.w2q + w2q_bytes, w2q_bytes);
         if (!S.ok) ok_sh = 0;
       }
       layer_out = true;
@@ -1083,14 +1090,14 @@ __global__ void __launch_bounds__(kQtThreads, 1)
       tc_fence_before();
       __syncthreads();
       tc_fence_after();
-      // layer 2: four 64-unit quarters of W2 through the buffers
+      // layer 2: four 64-unit quarters of W2 through the buffers; quarters
+      // 2 and 3 are both in flight before either is needed
       if (tid == 0) {
         S.mma(0, tacc, hx, 64, kHid, &bar_layer, false);
-        S.load(1, timg + G.w2q + w2q_bytes, w2q_bytes);
         S.mma(1, tacc + 64u, hx, 64, kHid, &bar_layer, false);
         S.load(0, timg + G.w2q + 2u * w2q_bytes, w2q_bytes);
-        S.mma(0, tacc + 128u, hx, 64, kHid, &bar_layer, false);
         S.load(1, timg + G.w2q + 3u * w2q_bytes, w2q_bytes);
+        S.mma(0, tacc + 128u, hx, 64, kHid, &bar_layer, false);
         S.mma(1, tacc + 192u, hx, 64, kHid, &bar_layer, true);
         if (!S.ok) ok_sh = 0;
       }
@@ -1106,7 +1113,7 @@ __global__ void __launch_bounds__(kQtThreads, 1)
       tc_fence_before();
       __syncthreads();
       tc_fence_after();
-      // head (W3 resident), and the next step's W1 half 0 into buffer 0
+      // head (W3 resident), and the next step's W1 halves into the buffers
       if (tid == 0) {
         tc_fence_after();
         const uint32_t idesc = idesc_bf16_f32(kQtEnvs, 16);
@@ -1115,7 +1122,10 @@ __global__ void __launch_bounds__(kQtThreads, 1)
           tc_mma_bf16(tacc, smem_desc(sa + (uint32_t)ks * 2 * (kQtEnvs * 16), kQtEnvs * 16, 128),
                       smem_desc(sw + (uint32_t)ks * 2 * 256, 256, 128), idesc, ks > 0 ? 1u : 0u);
         tc_commit(&bar_layer);
-        if (t + 1 < s1) S.load(0, timg + G.w1h, w1h_bytes);
+        if (t + 1 < s1) {
+          S.load(0, timg + G.w1h, w1h_bytes);
+          S.load(1, timg + G.w1h + w1h_bytes, w1h_bytes);
+        }
         if (!S.ok) ok_sh = 0;
       }
       layer_out = true;
