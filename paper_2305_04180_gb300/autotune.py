@@ -33,7 +33,7 @@ CANDIDATES = ([_cand("grid", warps_per_block=w) for w in (2, 4, 8)]
                  for P, b, o in ((7, 8, "map"), (7, 16, "map"), (7, 16, "index"), (3, 8, "map"), (3, 4, "map"),
                                  (5, 12, "map"), (15, 16, "map"))]
               + [_cand("pipe", warps_per_block=8, obs_warps=7, order="map", segment=S) for S in (256, 512, 1024, 2048)]
-              + [_cand("pipe", warps_per_block=16, obs_warps=7, order="map", segment=1024)])
+              + [_cand("pipe", warps_per_block=16, obs_warps=7, order="map", segment=S) for S in (512, 1024, 2048)])
 KEYS = ("kernel", "warps_per_block", "warps_per_env", "obs_warps", "blocks_per_sm", "order", "segment")
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
