@@ -953,6 +953,8 @@ __global__ void __launch_bounds__(kQtThreads, 1)
   __shared__ int greedy[kQtEnvs];
   __shared__ uint8_t act_sh[kQtEnvs];
   __shared__ int scan_next;
+  __shared__ Env env_sh[kQtEnvs];                 // the tile's env states within a segment
+  __shared__ unsigned long long akey_sh[kQtEnvs];  // their action-stream keys
   __shared__ float sb1[kHid], sb2[kHid], sb3[kOutPad];
   const QtSmem T = qt_smem();
   const TcImg G = tc_img(L.k1);
@@ -1154,16 +1156,20 @@ __global__ void __launch_bounds__(kQtThreads, 1)
       Env s;
       uint32_t a = 0;
       if (live) {
-        s = load_env_l2(p, env);
+        // the state stays in shared memory between the steps of a segment
+        // (stored to global memory at its last step)
+        s = t == s0 ? load_env_l2(p, env) : env_sh[row0 + lane];
+        if (t == s0) akey_sh[row0 + lane] = sm_at(sm_at(c.seed, kStreamAction), (uint64_t)env);
         // VEM (Sec. 3.1.1): with probability eps_i the random action of step t
-        const uint64_t h = sm_at(sm_at(sm_at(c.seed, kStreamAction), (uint64_t)env), (uint64_t)s.t);
+        const uint64_t h = sm_at(akey_sh[row0 + lane], (uint64_t)s.t);
         const uint32_t ra = (uint32_t)(sm_at(h, 0ull) >> 32) % (uint32_t)c.n_actions;
         const bool explore = u24_hi(sm_at(h, 1ull)) < __ldg(eps + env);
         a = explore ? ra : (uint32_t)greedy[row0 + lane];
       }
       const uint32_t d = lane_step(c, p, env, live, s, a, rec[row0 + (live ? lane : 0)], lane);
       if (live) {
-        store_env(p, env, s);
+        env_sh[row0 + lane] = s;
+        if (t + 1 == s1) store_env(p, env, s);
         act_sh[row0 + lane] = (uint8_t)a;
         if (act_seq) act_seq[(long long)t * n + env] = (uint8_t)a;
         if (done_seq) done_seq[(long long)t * n + env] = (uint8_t)d;
