@@ -72,6 +72,10 @@ ImgLayout img_layout(int n_in, int plain = 0) {
 struct ParamLayout {
   int w1, b1, w2, b2, w3, b3, total;
 };
+// Floats per CTA row of the gradient partials: every parameter, the Huber
+// sum, padded to a multiple of 4 so that rows start 16-byte aligned.
+__host__ __device__ constexpr long long partial_stride(int total) { return (total + 1 + 3) / 4 * 4; }
+
 ParamLayout param_layout(int n_in) {
   ParamLayout P;
   P.w1 = 0;
@@ -208,6 +212,22 @@ __device__ __forceinline__ void stage_image(uint8_t* dst, const uint8_t* __restr
   const int4* s = reinterpret_cast<const int4*>(src);
   int4* d = reinterpret_cast<int4*>(dst);
   for (int i = threadIdx.x; i < bytes / 16; i += blockDim.x) d[i] = __ldg(s + i);
+}
+
+// The same through the bulk-copy engine: thread 0 issues the copies (image
+// bytes are a multiple of 16, both ends 16-byte aligned) on the mbarrier
+// `bar` (initialised by the caller with one arrival), every thread waits
+// for its phase `parity` (bounded).  CTA-wide; false when the copy did not
+// complete within the bound.
+constexpr int kStageChunk = 32 * 1024;
+__device__ __forceinline__ bool stage_image_bulk(uint8_t* dst, const uint8_t* __restrict__ src, int bytes,
+                                                 uint64_t* bar, uint32_t parity, uint32_t tries) {
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(bar, (uint32_t)bytes);
+    for (int off = 0; off < bytes; off += kStageChunk)
+      bulk_g2s(dst + off, src + off, (uint32_t)min(kStageChunk, bytes - off), bar);
+  }
+  return __syncthreads_and(mbar_wait(bar, parity, tries));
 }
 
 // Pointers into a shared-memory copy of the image.
@@ -1287,23 +1307,29 @@ __global__ void __launch_bounds__(kThreads, 1)
   float* O = reinterpret_cast<float*>(H2 + kTile * kLdh);
   __shared__ int rows[kTile];
   __shared__ int astar[kTile];
+  __shared__ uint64_t bar_img;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.x * kTile + warp;
   if (lane == 0) {
     rows[warp] = i < batch ? (int)sample_entry(seed, *step, i, rp) : -1;
     if (i < batch) idx[i] = rows[warp];
   }
-  stage_image(sw, img, L.bytes);
+  if (threadIdx.x == 0) mbar_init(&bar_img, 1);
   __syncthreads();
+  // online image (phase 0) while the tile is gathered; a copy that does not
+  // complete makes the targets NaN
+  bool ok = stage_image_bulk(sw, img, L.bytes, &bar_img, 0u, kTcTries);
   gather_tile(X, L.ld1, rp.s2, rows, rp.obs_dim, warp, lane);
   __syncthreads();
-  mlp_tile(qw_at(sw, L), X, H1, H2, O, warp, lane);
+  if (ok) mlp_tile(qw_at(sw, L), X, H1, H2, O, warp, lane);
   if (lane == 0) astar[warp] = (int)greedy_action(O + warp * kOutPad, nullptr, L.plain);
+  fence_async_smem();  // this thread's reads of the online image before the bulk copy overwrites it
   __syncthreads();
-  stage_image(sw, img_t, L.bytes);
-  __syncthreads();
-  mlp_tile(qw_at(sw, L), X, H1, H2, O, warp, lane);
-  if (lane == 0 && i < batch) {
+  // the target image over it (phase 1)
+  if (ok) ok = stage_image_bulk(sw, img_t, L.bytes, &bar_img, 1u, kTcTries);
+  if (ok) mlp_tile(qw_at(sw, L), X, H1, H2, O, warp, lane);
+  if (lane == 0 && i < batch && !ok) y[i] = __int_as_float(0x7fc00000);
+  if (lane == 0 && i < batch && ok) {
     float qv[5];
     greedy_action(O + warp * kOutPad, qv, L.plain);
     const int e = rows[warp];
@@ -1331,12 +1357,18 @@ __global__ void __launch_bounds__(kThreads, 1)
   float* DO = O + kTile * kOutPad;  // dL/d(head outputs) [16][8]
   __shared__ int rows[kTile];
   __shared__ float hub[kTile];
+  __shared__ uint64_t bar_img;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane >> 2, q = lane & 3;
   const int i = blockIdx.x * kTile + warp;
   if (lane == 0) rows[warp] = i < batch ? idx[i] : -1;
-  stage_image(sw, img, L.bytes);
+  if (threadIdx.x == 0) mbar_init(&bar_img, 1);
   __syncthreads();
+  if (!stage_image_bulk(sw, img, L.bytes, &bar_img, 0u, kTcTries)) {
+    // the image copy did not complete: this CTA's loss term is NaN
+    if (threadIdx.x == 0) partial[(long long)blockIdx.x * partial_stride(P.total) + P.total] = __int_as_float(0x7fc00000);
+    return;
+  }
   gather_tile(S, L.ld1, rp.s, rows, rp.obs_dim, warp, lane);
   __syncthreads();
   const QW w = qw_at(sw, L);
@@ -1368,7 +1400,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     hub[warp] = hl;
   }
   __syncthreads();
-  float* pg = partial + (long long)blockIdx.x * (P.total + 1);
+  float* pg = partial + (long long)blockIdx.x * partial_stride(P.total);
   // head gradient on the CUDA cores: dW3[o][j] = sum_s DO[s][o] H2[s][j],
   // db3[o] = sum_s DO[s][o]; dH2 = DO W3 (BF16 W3 as in the forward), masked
   // by the ReLU into dZ2 (written over H2 after a barrier)
@@ -1418,10 +1450,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     mma_bf16(acc, a, b0, b1);
     float* dst = pg + P.w2;
-    dst[(m0 + g) * kHid + n0 + 2 * q] = acc[0];
-    dst[(m0 + g) * kHid + n0 + 2 * q + 1] = acc[1];
-    dst[(m0 + g + 8) * kHid + n0 + 2 * q] = acc[2];
-    dst[(m0 + g + 8) * kHid + n0 + 2 * q + 1] = acc[3];
+    *reinterpret_cast<float2*>(dst + (m0 + g) * kHid + n0 + 2 * q) = make_float2(acc[0], acc[1]);
+    *reinterpret_cast<float2*>(dst + (m0 + g + 8) * kHid + n0 + 2 * q) = make_float2(acc[2], acc[3]);
   }
   // dH1 = dZ2 W2 (B = W2 stored [out][in] -> "row" layout), masked -> dZ1
 #pragma unroll
@@ -1485,12 +1515,12 @@ __global__ void k_adam(float* __restrict__ th, float* __restrict__ m, float* __r
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0 && loss) {
     float acc = 0.0f;
-    for (int b = 0; b < nblk; ++b) acc += partial[(long long)b * (P.total + 1) + P.total];
+    for (int b = 0; b < nblk; ++b) acc += partial[(long long)b * partial_stride(P.total) + P.total];
     *loss = acc / (float)batch;
   }
   if (i >= P.total) return;
   float gsum = 0.0f;
-  for (int b = 0; b < nblk; ++b) gsum += partial[(long long)b * (P.total + 1) + i];
+  for (int b = 0; b < nblk; ++b) gsum += partial[(long long)b * partial_stride(P.total) + i];
   if (grad_out) {
     const int j = L.plain ? paper_index(i, P, L.n_in) : i;
     if (j >= 0) grad_out[j] = gsum;
@@ -1617,7 +1647,7 @@ extern "C" int sg_qnet_create(int32_t n_in, int32_t arch, int32_t max_batch, uin
   alloc((void**)&q->img, (size_t)q->IL.bytes);
   alloc((void**)&q->img_t, (size_t)q->IL.bytes);
   alloc((void**)&q->step, 8);
-  alloc((void**)&q->partial, nblk * (P + 1) * 4);
+  alloc((void**)&q->partial, nblk * partial_stride(P) * 4);
   alloc((void**)&q->y, (size_t)q->max_batch * 4);
   alloc((void**)&q->idx, (size_t)q->max_batch * 4);
   alloc((void**)&q->img_tc, tc_img(q->IL.k1).bytes);
@@ -2008,7 +2038,7 @@ constexpr int kNaMaxParams = kHid * kNaMaxIn + kHid + kHid * kHid + kHid + kOut 
 constexpr long long kNaOffY = 2ll * kNaImgSlot;
 constexpr long long kNaOffIdx = kNaOffY + kNaMaxBatch * 4;
 constexpr long long kNaOffPartial = (kNaOffIdx + kNaMaxBatch * 4 + 255) / 256 * 256;
-constexpr long long kNaBytes = kNaOffPartial + (long long)kNaMaxBlk * (kNaMaxParams + 1) * 4;
+constexpr long long kNaBytes = kNaOffPartial + (long long)kNaMaxBlk * partial_stride(kNaMaxParams) * 4;
 }  // namespace
 
 static __device__ __align__(256) unsigned char g_td_noalloc_scratch[kNaBytes];
