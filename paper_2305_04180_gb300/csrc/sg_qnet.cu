@@ -807,8 +807,9 @@ __global__ void __launch_bounds__(512 * MT, 1)
 // network.  Per step the network runs on the tile on the tensor cores
 // (tcgen05 MMAs into 256 tensor-memory columns, epilogues split over the 8
 // warps of each lane quarter), warps 0-3 take the greedy actions from the
-// head, and then every warp steps its 4 envs the way sg_sim_step does (lanes
-// 0-3: the scalar part, lane_step; the whole warp: the scans), writing the
+// head, the first 16 warps step the tile's envs the way sg_sim_step does (8
+// envs per warp, one per lane: the scalar part, lane_step), and then every
+// warp takes whole-warp scans row by row from a shared counter, writing the
 // next observation as the tile's BF16 row and the FP32 outputs and ring
 // entries.  Same VEM draws, same simulator values as k_rollout_q; the Q
 // values differ from it only in the summation order.
@@ -825,7 +826,12 @@ constexpr int kQtEnvs = 128;
 constexpr int kQtWarps = 32;
 constexpr int kQtThreads = kQtWarps * 32;
 constexpr uint32_t kQtBuf = 32u * 1024u;
-constexpr uint32_t kQtRecOff = 32u * 1024u;  // records in the activation buffer (input tile: 256 k1 <= 20 KB)
+constexpr uint32_t kQtRecOff = 32u * 1024u;
+// The env steps of a tile (the scalar part, lane_step) run on the first
+// kQtEnvs / kQtStepLanes warps, kQtStepLanes envs per warp (one per lane):
+// 16 warps of 8 envs measured fastest (32 x 4: 406.2, 16 x 8: 414.5,
+// 8 x 16: 411.4, 4 x 32: 400.5 M env-steps/s at 65,536 envs).
+constexpr int kQtStepLanes = 8;  // records in the activation buffer (input tile: 256 k1 <= 20 KB)
 static_assert(kQtRecOff + kQtEnvs * 128u <= (uint32_t)(kQtEnvs * kHid * 2), "records fit the activation buffer");
 
 struct QtSmem {
@@ -1054,6 +1060,11 @@ __global__ void __launch_bounds__(kQtThreads, 1)
     const int nv = max(0, min(4, (int)n - slot0));
     const bool live = lane < nv;
     const int env = live ? order[slot0 + lane] : 0;
+    // the env-step lanes: row srow of the tile
+    const bool stepper = warp < kQtEnvs / kQtStepLanes;
+    const int srow = warp * kQtStepLanes + lane;
+    const bool slive = stepper && lane < kQtStepLanes && (long long)blk * kQtEnvs + srow < n;
+    const int senv = slive ? order[blk * kQtEnvs + srow] : 0;
     // the tile: zero (padding columns, rows without an env), then the first
     // observation of the segment
     for (int i = tid; i < kQtEnvs * L.k1 / 8; i += kQtThreads)
@@ -1172,27 +1183,29 @@ __global__ void __launch_bounds__(kQtThreads, 1)
       tc_fence_before();
       __syncthreads();
       tc_fence_after();
-      // ---- the env step of this warp's envs ----
-      Env s;
-      uint32_t a = 0;
-      if (live) {
-        // the state stays in shared memory between the steps of a segment
-        // (stored to global memory at its last step)
-        s = t == s0 ? load_env_l2(p, env) : env_sh[row0 + lane];
-        if (t == s0) akey_sh[row0 + lane] = sm_at(sm_at(c.seed, kStreamAction), (uint64_t)env);
-        // VEM (Sec. 3.1.1): with probability eps_i the random action of step t
-        const uint64_t h = sm_at(akey_sh[row0 + lane], (uint64_t)s.t);
-        const uint32_t ra = (uint32_t)(sm_at(h, 0ull) >> 32) % (uint32_t)c.n_actions;
-        const bool explore = u24_hi(sm_at(h, 1ull)) < __ldg(eps + env);
-        a = explore ? ra : (uint32_t)greedy[row0 + lane];
-      }
-      const uint32_t d = lane_step(c, p, env, live, s, a, rec[row0 + (live ? lane : 0)], lane);
-      if (live) {
-        env_sh[row0 + lane] = s;
-        if (t + 1 == s1) store_env(p, env, s);
-        act_sh[row0 + lane] = (uint8_t)a;
-        if (act_seq) act_seq[(long long)t * n + env] = (uint8_t)a;
-        if (done_seq) done_seq[(long long)t * n + env] = (uint8_t)d;
+      // ---- the env steps of the tile: one env per lane of the stepping warps ----
+      if (stepper) {
+        Env s;
+        uint32_t a = 0;
+        if (slive) {
+          // the state stays in shared memory between the steps of a segment
+          // (stored to global memory at its last step)
+          s = t == s0 ? load_env_l2(p, senv) : env_sh[srow];
+          if (t == s0) akey_sh[srow] = sm_at(sm_at(c.seed, kStreamAction), (uint64_t)senv);
+          // VEM (Sec. 3.1.1): with probability eps_i the random action of step t
+          const uint64_t h = sm_at(akey_sh[srow], (uint64_t)s.t);
+          const uint32_t ra = (uint32_t)(sm_at(h, 0ull) >> 32) % (uint32_t)c.n_actions;
+          const bool explore = u24_hi(sm_at(h, 1ull)) < __ldg(eps + senv);
+          a = explore ? ra : (uint32_t)greedy[srow];
+        }
+        const uint32_t d = lane_step(c, p, senv, slive, s, a, rec[slive ? srow : 0], lane);
+        if (slive) {
+          env_sh[srow] = s;
+          if (t + 1 == s1) store_env(p, senv, s);
+          act_sh[srow] = (uint8_t)a;
+          if (act_seq) act_seq[(long long)t * n + senv] = (uint8_t)a;
+          if (done_seq) done_seq[(long long)t * n + senv] = (uint8_t)d;
+        }
       }
       // every record of the tile is written; the scans (one or two per env,
       // 16 to 64 beams) are handed out row by row through a shared counter,
