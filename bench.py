@@ -46,8 +46,10 @@ def parse():
     ap.add_argument("--rollout-steps", type=int, default=None, help="vectorized steps per bench step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
-    ap.add_argument("--extras", default="qnet,td,step,uneven,full,dyn",
-                    help="comma list of secondary measurements: qnet, td, step, uneven, full, dyn")
+    ap.add_argument("--extras", default="qnet,td,step,uneven,qtc,full,dyn",
+                    help="comma list of secondary measurements: qnet, td, step, uneven, qtc, full, dyn")
+    ap.add_argument("--qtc-slots", type=int, default=64,
+                    help="replay slots per env of the qtc leg (64 = the learned loop's 4M-transition ring)")
     ap.add_argument("--launch", default=None,
                     help="fixed rollout launch 'kernel:key=val,...' e.g. 'pipe:warps_per_block=8,obs_warps=7,order=map'"
                          " (skips the autotuner)")
@@ -264,7 +266,7 @@ def run_ours(a):
 
     extras = None
     if not a.no_extras and rank == 0:
-        extras = run_extras(flush, set(a.extras.split(",")))
+        extras = run_extras(flush, ExtrasSel(a.extras.split(","), a.qtc_slots))
     out = None
     if rank == 0:
         out = {
@@ -324,6 +326,14 @@ def _time_cuda(fn, reps, flush=None):
         torch.cuda.synchronize()
         tot += e0.elapsed_time(e1)
     return tot / reps
+
+
+class ExtrasSel(set):
+    """The selected secondary measurements, with the qtc leg's ring size."""
+
+    def __init__(self, items, qtc_slots=64):
+        super().__init__(items)
+        self.qtc_slots = int(qtc_slots)
 
 
 def run_extras(flush, which):
@@ -422,6 +432,8 @@ def _run_extras_tail(out, flush, which):
     if "step" not in which:
         if "uneven" in which:
             out["uneven_batching"] = run_uneven(flush)
+        if "qtc" in which:
+            out["fused_rollout_65536"] = run_fused_rollout_full(flush, which)
         if "full" in which:
             out["full_learned_loop"] = run_full_loop(flush)
         if "dyn" in which:
@@ -446,11 +458,38 @@ def _run_extras_tail(out, flush, which):
     del sim2, obs2
     if "uneven" in which:
         out["uneven_batching"] = run_uneven(flush)
+    if "qtc" in which:
+        out["fused_rollout_65536"] = run_fused_rollout_full(flush, which)
     if "full" in which:
         out["full_learned_loop"] = run_full_loop(flush)
     if "dyn" in which:
         out["moving_obstacles"] = run_dyn(flush)
     return out
+
+
+def run_fused_rollout_full(flush, which):
+    """The fused eps-greedy rollout alone on the full learned-loop workload
+    (65,536 envs over 1,024 maps, beams 16..64): 32-step calls appending to
+    the replay ring (tcgen05 kernel, time-sliced over a resident grid)."""
+    import torch
+
+    from paper_2305_04180_gb300 import QNet, Replay, Sim
+    from workloads import workload
+
+    w = workload("full65536")
+    sim = Sim(w.params, w.maps(), w.env_map, w.env_beams)
+    sim.reset()
+    q = QNet(sim.obs_dim, 256, seed=1)
+    slots = getattr(which, "qtc_slots", 64)
+    rp = Replay(slots, sim.n, sim.obs_dim)
+    eps = torch.from_numpy(w.eps).cuda()
+    f = lambda: sim.rollout(32, policy="eps_q", qnet=q, eps=eps, replay=rp)  # noqa: E731
+    for _ in range(3):
+        f()
+    ms = _time_cuda(f, 5, flush)
+    return {"workload": w.name, "n_envs": sim.n, "maps": sim.n_maps, "steps_per_call": 32,
+            "value": sim.n * 32 / (ms / 1e3), "unit": UNIT, "ms_per_call": ms,
+            "kernel": "k_rollout_q_tc (tcgen05, 128-env tiles)", "replay": f"{rp.capacity} transitions"}
 
 
 def run_dyn(flush):
