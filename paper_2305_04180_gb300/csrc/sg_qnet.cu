@@ -1056,6 +1056,7 @@ __global__ void __launch_bounds__(kQtThreads, 1)
     __syncthreads();  // item_sh is rewritten by the next iteration
     if (item < 0) break;
     const int blk = item % nblk, s0 = (item / nblk) * seglen, s1 = min(K, s0 + seglen);
+    // the segment's first observation: four rows per warp (row0 .. row0 + 3)
     const int slot0 = blk * kQtEnvs + row0;
     const int nv = max(0, min(4, (int)n - slot0));
     const bool live = lane < nv;
