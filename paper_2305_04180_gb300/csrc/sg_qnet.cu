@@ -2048,6 +2048,9 @@ constexpr int kNaMaxBlk = kNaMaxBatch / kTile;
 constexpr int kNaImgBytes = kHid * ((kNaMaxIn + 15) / 16 * 16 + 8) * 2 + kHid * kLdh * 2 + kOutPad * kLdh * 2 +
                             2 * kHid * 4 + kOutPad * 4;
 constexpr int kNaImgSlot = (kNaImgBytes + 255) / 256 * 256;
+// The widest image (69 inputs) is staged by the TD kernels in one mbarrier
+// phase, whose transaction count holds at most 2^20 - 1 bytes.
+static_assert(kNaImgBytes + 16 < (1 << 20), "one weight image fits an mbarrier phase's transaction count");
 constexpr int kNaMaxParams = kHid * kNaMaxIn + kHid + kHid * kHid + kHid + kOut * kHid + kOut;
 constexpr long long kNaOffY = 2ll * kNaImgSlot;
 constexpr long long kNaOffIdx = kNaOffY + kNaMaxBatch * 4;
