@@ -1,6 +1,6 @@
 """Shared test plumbing: state conversion between the library blob and the
-oracle's arrays, and small input builders.  Holds none of the step's
-arithmetic."""
+oracle's arrays, small input builders, and the error measure of the float64
+tolerance checks.  Holds none of the step's arithmetic."""
 
 from __future__ import annotations
 
@@ -43,3 +43,34 @@ def ring_sample_entries(seed, tstep, batch, steps, slots, n_envs, reserve=0):
         slot = (steps - 1 - j // n_envs) % slots
         out.append(slot * n_envs + j % n_envs)
     return np.array(out)
+
+
+def step_rel_error(f_old, f_new, f_ref):
+    """Relative error of a float32 step's pose and velocity (rows x, y, phi,
+    v_l, v_a of the [9, N] state) against the float64 oracle's step from the
+    same state f_old.
+
+    Each component is a sum of two terms (Eq. 5: K v + (1 - K) v_hat; Eq. 6:
+    x - dt v_l cos(phi), y - dt v_l sin(phi), phi + dt v_a, then the wrap by
+    2 pi), and float32 rounds a sum relative to the size of its terms, so the
+    error is divided by |term 1| + |term 2| (the terms taken from f_old and
+    the float64 result; 2 pi added where the heading wrapped).  Where the two
+    terms do not cancel this is |x| within a factor 2; where they do (a
+    heading or angular velocity passing through zero) dividing by |x| alone
+    would turn one float32 rounding of the terms into an arbitrarily large
+    "relative" error.  Returns a [5, N] array."""
+    o = np.asarray(f_old, np.float64)
+    r = np.asarray(f_ref, np.float64)
+    g = np.asarray(f_new, np.float64)
+    dt, K = o[5], o[6]
+    c, s = np.cos(o[2]), np.sin(o[2])
+    wrapped = np.abs(o[2] + dt * r[4] - r[2]) > np.pi
+    scale = np.stack([
+        np.abs(o[0]) + np.abs(dt * r[3] * c),
+        np.abs(o[1]) + np.abs(dt * r[3] * s),
+        np.abs(o[2]) + np.abs(dt * r[4]) + np.where(wrapped, 2 * np.pi, 0.0),
+        np.abs(K * o[3]) + np.abs(r[3] - K * o[3]),
+        np.abs(K * o[4]) + np.abs(r[4] - K * o[4]),
+    ])
+    err = np.abs(g[:5] - r[:5])
+    return np.where(err == 0, 0.0, err / np.maximum(scale, np.finfo(np.float64).tiny))

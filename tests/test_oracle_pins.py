@@ -13,6 +13,7 @@ import os
 import numpy as np
 import pytest
 
+from tests._helpers import step_rel_error
 from oracle.sim import OracleSim, lib, pack_map, sincos
 from workloads.configs import ACTION_TABLE, base_params
 from workloads.maps import empty_map, make_map, random_tiny_map
@@ -108,9 +109,9 @@ def test_pack_map_matches_numpy_packbits():
 
 
 # ---------------------------------------------------------- kinematics
-def _kin_sim(prec, K, dt, actions, w=2048, delay=0):
+def _kin_sim(prec, K, dt, actions, w=2048, delay=0, cap=1.0):
     p = base_params(k_lo=K, k_hi=K, dt_lo=dt, dt_hi=dt, delay_lo=delay, delay_hi=delay,
-                    actions=actions, t_max=10 ** 6, cap_lo=1.0, cap_hi=1.0)
+                    actions=actions, t_max=10 ** 6, cap_lo=cap, cap_hi=cap)
     return OracleSim(p, [empty_map(w)], np.zeros(1, np.int32), prec=prec)
 
 
@@ -175,6 +176,41 @@ def test_arc_uses_old_heading(prec, tol):
         ys -= dt * vn * math.sin(phi_prev)
         f = o.f[:, 0]
         assert abs(f[0] - xs) <= tol * 10 and abs(f[1] - ys) <= tol * 10
+
+
+@pytest.mark.parametrize("cap", [0.5, 1.5])
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-9), ("f32", 2e-4)])
+def test_velocity_cap_scales_both_targets(prec, tol, cap):
+    """Velocity range (Sec. 4.3.2, reading 6): the episode's factor cap scales
+    both entries of the action table, so from rest with action (v, w) the
+    closed forms of the straight-line and rotation cases hold with cap v and
+    cap w: v_n = cap v (1 - K^n), w_n = cap w (1 - K^n), and the heading
+    advances by dt cap w (n - K (1 - K^n) / (1 - K)).  A dropped cap, or a cap
+    on one of the two targets only, fails one of the three."""
+    K, dt, v, w = 0.6, 0.1, 18.0, 1.0
+    o = _kin_sim(prec, K, dt, [(v, 0.0), (0.0, w)], cap=cap)
+    x0, y0, phi0 = 1000.5, 1000.25, 0.3
+    _place(o, x0, y0, phi0)
+    assert o.f[7, 0] == np.asarray(cap, o.dtype)  # lo == hi: the draw is cap itself
+    for n in range(1, 121):
+        o.step([0])
+        f = o.f[:, 0]
+        vn = cap * v * (1 - K ** n)
+        disp = dt * cap * v * (n - K * (1 - K ** n) / (1 - K))
+        assert abs(f[3] - vn) <= tol * max(1, vn)
+        assert abs(f[0] - (x0 - disp * math.cos(phi0))) <= tol * max(1.0, disp)
+        assert abs(f[1] - (y0 - disp * math.sin(phi0))) <= tol * max(1.0, disp)
+    o = _kin_sim(prec, K, dt, [(v, 0.0), (0.0, w)], cap=cap)
+    phi0 = -2.0
+    _place(o, x0, y0, phi0)
+    for n in range(1, 41):
+        o.step([1])
+        f = o.f[:, 0]
+        ang = phi0 + dt * cap * w * (n - K * (1 - K ** n) / (1 - K))
+        wrapped = (ang + math.pi) % (2 * math.pi) - math.pi
+        assert abs(f[2] - wrapped) <= tol * 4
+        assert abs(f[4] - cap * w * (1 - K ** n)) <= tol
+        assert f[3] == 0.0
 
 
 def test_inertia_limits():
@@ -506,6 +542,69 @@ def test_reward_velocity_and_near_obstacle_terms():
     assert abs(rew[0] - exp) < 1e-9
 
 
+@pytest.mark.parametrize("cap", [0.5, 1.5])
+def test_velocity_observation_terms_use_nominal_maxima(cap):
+    """Observation (reading 16): the last two entries are v_l / 18 and
+    v_a / 1, the nominal maxima of the simulation-parameter table, not the
+    episode's capped maxima; checked at a hand-set velocity with cap != 1
+    (K = 1 keeps the velocity through the step)."""
+    W = 366
+    o = _reward_sim(empty_map(W), cap_lo=cap, cap_hi=cap)
+    B = 32
+    for vl, va in ((10.0, 0.5), (3.25, -0.75), (0.0, 1.25)):
+        _place(o, 150.0, 120.0, 0.7, vl=vl, va=va)
+        obs = o.step([2])[0][0]
+        assert o.f[7, 0] == cap
+        assert abs(obs[B + 3] - vl / 18.0) < 1e-12
+        assert abs(obs[B + 4] - va / 1.0) < 1e-12
+
+
+def test_velocity_reward_threshold_scales_with_cap():
+    """r_v = [v_l > v_max / 2] with v_max the episode's capped maximum
+    18 cap (reading 15): the reward jumps by the weight 0.3 as v_l crosses
+    9 cap, and does not jump at the uncapped threshold 9."""
+    W = 366
+
+    def rew(cap, vl):
+        o = _reward_sim(empty_map(W), cap_lo=cap, cap_hi=cap)
+        _place(o, 150.0, 120.0, 0.7, vl=vl)
+        obs, r, done, _ = o.step([2])
+        assert done[0] == 0 and obs[0, :32].min() == 1.0  # no obstacle: r_d = 0
+        return float(r[0])
+
+    for cap in (0.5, 1.5):
+        thr = 9.0 * cap
+        jump = rew(cap, thr + 0.01) - rew(cap, thr - 0.01)
+        assert abs(jump - 0.3) < 1e-4, (cap, jump)
+        flat = rew(cap, 9.0 + 0.01) - rew(cap, 9.0 - 0.01)
+        assert abs(flat) < 1e-4, (cap, flat)
+
+
+def test_near_obstacle_term_uses_noise_free_ranges():
+    """r_d = -1 when the nearest noise-free range is below 30 (reading 17):
+    with sensor noise sigma = 2 the reward equals the noise-free run's bit for
+    bit, while the noisy minimum lands on the other side of 30 in many of the
+    same steps (so a reward that read the noisy ranges would differ)."""
+    W = 400
+    g = np.zeros((W, W), np.uint8)
+    g[:, 300:] = 1  # half plane: the nearest beam sees the wall at about 300 - x
+    crossed = steps = 0
+    for x in np.arange(268.0, 273.0, 0.25):
+        a = _reward_sim(g, sigma_lo=0.0, sigma_hi=0.0)
+        b = _reward_sim(g, sigma_lo=2.0, sigma_hi=2.0)
+        for o in (a, b):
+            _place(o, float(x), 200.0, math.pi)  # heading +x, the wall straight ahead
+        for _ in range(12):
+            oa, ra, da, _ = a.step([2])
+            ob, rb, db, _ = b.step([2])
+            assert da[0] == 0 and db[0] == 0
+            assert ra[0] == rb[0]
+            clean, noisy = oa[0, :32].min() * 100.0, ob[0, :32].min() * 100.0
+            crossed += (clean < 30.0) != (noisy < 30.0)
+            steps += 1
+    assert crossed >= steps // 10, (crossed, steps)
+
+
 def test_terminal_rewards_and_autoreset():
     W = 366
     g = empty_map(W, border=True)
@@ -638,12 +737,13 @@ def test_f32_and_f64_oracles_agree_on_a_rollout():
     b.reset()
     for t in range(200):
         b.set_state(a.f.astype(np.float64), a.u, a.b)
+        f_old = a.f.copy()
         act = a.random_actions(t)
         _, _, da, _ = a.step(act)
         _, _, db, _ = b.step(act)
         assert np.array_equal(da, db)
         live = da == 0
-        rel = np.abs(a.f[:5, live] - b.f[:5, live]) / np.maximum(1.0, np.abs(b.f[:5, live]))
+        rel = step_rel_error(f_old[:, live], a.f[:, live], b.f[:, live])
         assert rel.max() <= 1e-5
 
 

@@ -13,7 +13,7 @@ import pytest
 import torch
 
 from oracle.sim import OracleSim, pack_map
-from tests._helpers import bits, gpu_state_to_oracle, oracle_state_to_gpu
+from tests._helpers import bits, gpu_state_to_oracle, oracle_state_to_gpu, step_rel_error
 from workloads import workload
 from workloads.configs import base_params
 from workloads.maps import empty_map, make_map, random_tiny_map
@@ -316,7 +316,7 @@ def test_against_float64_oracle_tolerances():
         d = done.cpu().numpy()
         live = (d == 0) & (odone == 0)
         f2, _ = g.get_state()
-        rel = np.abs(f2[:5, live] - o.f[:5, live]) / np.maximum(1.0, np.abs(o.f[:5, live]))
+        rel = step_rel_error(f[:, live], f2[:, live], o.f[:, live])
         assert rel.max() <= 1e-5
         gr = np.rint(obs.cpu().numpy()[live, :32] * 100.0)
         orr = np.rint(oobs[live, :32] * 100.0)
