@@ -50,6 +50,8 @@ def parse():
                     help="comma list of secondary measurements: qnet, td, step, uneven, qtc, full, dyn")
     ap.add_argument("--qtc-slots", type=int, default=64,
                     help="replay slots per env of the qtc leg (64 = the learned loop's 4M-transition ring)")
+    ap.add_argument("--march-sectors", type=int, default=None,
+                    help="direction sectors of the march's skip planes (default: the library's choice)")
     ap.add_argument("--launch", default=None,
                     help="fixed rollout launch 'kernel:key=val,...' e.g. 'pipe:warps_per_block=8,obs_warps=7,order=map'"
                          " (skips the autotuner)")
@@ -65,7 +67,7 @@ def _oracle_shard(args):
     from workloads import workload
 
     w = workload(name)
-    o = OracleSim(w.params, w.maps(), w.env_map, w.env_beams, prec=prec)
+    o = OracleSim(wparams(w), w.maps(), w.env_map, w.env_beams, prec=prec)
     for i in range(i0, i1):
         o.reset_env(i, 0)
     o.L.orc_reset_march_samples()
@@ -94,6 +96,15 @@ def time_oracle(pool, cores, name, n_envs, K, prec="f32"):
     samples = sum(r[2] for r in res)
     busy = max(r[1] for r in res)
     return steps, wall, busy, samples
+
+
+# Sector planes of the march (None: the library's choice); set from the command line.
+MARCH_SECTORS = None
+
+
+def wparams(w):
+    """The workload's simulator parameters with the chosen march sectors."""
+    return w.params if MARCH_SECTORS is None else dict(w.params, march_sectors=MARCH_SECTORS)
 
 
 # ------------------------------------------------------------ ranks
@@ -191,7 +202,7 @@ def run_ours(a):
     w = workload(a.workload)
     K = a.rollout_steps or w.steps
     maps = w.maps()
-    sim = Sim(w.params, maps, w.env_map, w.env_beams)
+    sim = Sim(wparams(w), maps, w.env_map, w.env_beams)
     n = sim.n
     sim.reset(seed=replica_seed(w.params["seed"], rank))
     from paper_2305_04180_gb300.autotune import autotune_rollout
@@ -290,6 +301,7 @@ def run_ours(a):
                 "env_steps_per_bench_step": n * K,
                 "policy": "random (on-device counter RNG)",
                 "launch": tune["config"],
+                "march_sectors": int(sim.info.march_sectors),
                 "outputs_per_env_step": "observation (obs_dim floats), reward, done flags",
                 "obs_dim": sim.obs_dim,
                 "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
@@ -351,7 +363,7 @@ def run_extras(flush, which):
         return _run_extras_tail(out, flush, which)
     # fused eps-greedy Q-net rollout vs plain random rollout (4,096 envs, 32 maps)
     w = workload("qnet4096")
-    sim = Sim(w.params, w.maps(), w.env_map)
+    sim = Sim(wparams(w), w.maps(), w.env_map)
     sim.reset()
     q = QNet(sim.obs_dim, w.extra["batch"], seed=1)
     slots = w.extra["ring"] // sim.n
@@ -441,7 +453,7 @@ def _run_extras_tail(out, flush, which):
         return out
     # single-step kernel with state in HBM, 65,536 envs over the 32 randomised maps
     w2 = workload("dr1024", n_envs=65536)
-    sim2 = Sim(w2.params, w2.maps(), w2.env_map)
+    sim2 = Sim(wparams(w2), w2.maps(), w2.env_map)
     obs2 = sim2.reset()
     act = torch.randint(0, 5, (sim2.n,), dtype=torch.uint8, device="cuda")
     rew2 = torch.empty(sim2.n, device="cuda")
@@ -477,7 +489,7 @@ def run_fused_rollout_full(flush, which):
     from workloads import workload
 
     w = workload("full65536")
-    sim = Sim(w.params, w.maps(), w.env_map, w.env_beams)
+    sim = Sim(wparams(w), w.maps(), w.env_map, w.env_beams)
     sim.reset()
     q = QNet(sim.obs_dim, 256, seed=1)
     slots = getattr(which, "qtc_slots", 64)
@@ -508,7 +520,7 @@ def run_dyn(flush):
     tuned = None
     for name in ("dyn1024", "dr1024"):
         w = workload(name)
-        sim = Sim(w.params, w.maps(), w.env_map)
+        sim = Sim(wparams(w), w.maps(), w.env_map)
         sim.reset()
         if tuned is None:
             tuned = autotune_rollout(sim, K=K, reps=2, cache_path=None)["config"]
@@ -529,7 +541,7 @@ def run_dyn(flush):
     steps = {}
     for name in ("dyn1024", "dr1024"):
         w = workload(name, n_envs=65536)
-        sim = Sim(w.params, w.maps(), w.env_map)
+        sim = Sim(wparams(w), w.maps(), w.env_map)
         obs = sim.reset()
         act = torch.randint(0, 5, (sim.n,), dtype=torch.uint8, device="cuda")
         rew = torch.empty(sim.n, device="cuda")
@@ -556,7 +568,7 @@ def run_uneven(flush):
 
     w = workload("uneven8192")
     t0 = time.perf_counter()
-    sim = Sim(w.params, w.maps(), w.env_map, w.env_beams)
+    sim = Sim(wparams(w), w.maps(), w.env_map, w.env_beams)
     build_s = time.perf_counter() - t0
     sim.reset()
     K = w.steps
@@ -607,7 +619,7 @@ def run_full_loop(flush):
     from workloads import workload
 
     w = workload("full65536")
-    sim = Sim(w.params, w.maps(), w.env_map, w.env_beams)
+    sim = Sim(wparams(w), w.maps(), w.env_map, w.env_beams)
     sim.reset()
     slots = w.extra["ring"] // sim.n
     tr = ColorTrainer(sim, batch=w.extra["batch"], slots=slots, gamma=w.extra["gamma"], lr=w.extra["lr"],
@@ -691,7 +703,9 @@ def roofline_alu(samples_per_env_step, n, K, ms_per_step, clk):
 
 
 def main():
+    global MARCH_SECTORS
     a = parse()
+    MARCH_SECTORS = a.march_sectors
     if a.impl == "reference":
         return run_reference(a)
     out, pool, (w, n, K, ms_per_step, clk) = run_ours(a)

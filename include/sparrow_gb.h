@@ -74,7 +74,7 @@ typedef struct sg_sim_config {
   int32_t t_max;       /* episode truncation length (steps), >= 1 */
   int32_t delay_lo;    /* control delay in steps, 0 <= lo <= hi <= 2 */
   int32_t delay_hi;
-  float fov;           /* LiDAR fan, radians; beam j at phi - fov/2 + j fov/(nb-1) */
+  float fov;           /* LiDAR fan, radians, in [0, 2 pi]; beam j at phi - fov/2 + j fov/(nb-1) */
   float range_max;     /* R_max, cells, > 0 */
   float march_step;    /* ray-march sample spacing, cells, > 0; R_max/step <= 4096 */
   float robot_radius;  /* collision disc radius, cells */
@@ -109,6 +109,19 @@ typedef struct sg_sim_config {
   float dyn_radius;          /* > 0 when n_dyn > 0, cells */
   float dyn_speed_lo, dyn_speed_hi; /* 0 <= lo <= hi, cells / s */
   float dyn_keepout;         /* >= 0, cells */
+  /*
+   * Direction sectors of the march's acceleration structure (not part of the
+   * step: hit indices are those of the plain march whatever the value).
+   * 1: one skip map per map (Chebyshev clearance).  4, 8, 16 or 32: as many
+   * "sector skip" planes per map in addition, each giving the number of
+   * samples a ray of that direction sector can skip from a cell (about 2x
+   * fewer march iterations at 16 on the benchmark maps); they cost
+   * march_sectors bytes per map cell and are built at creation.  0: 16 when
+   * the planes take at most 16 GiB and a quarter of the free device memory,
+   * else 8 or 4 under the same limit, else 1.  Ignored (1) when
+   * march_step > 1, where the march tests every sample.
+   */
+  int32_t march_sectors;
 } sg_sim_config;
 
 /* Read-only facts about a simulator (sg_sim_info). */
@@ -120,7 +133,7 @@ typedef struct sg_sim_info {
   int64_t atlas_words;   /* 32-bit words of the bit-packed map atlas */
   int64_t state_bytes;   /* size of the sg_sim_get_state / set_state blob */
   int32_t device;        /* CUDA device ordinal the simulator lives on */
-  int32_t pad0;
+  int32_t march_sectors; /* sector planes per map in use (1: none) */
 } sg_sim_info;
 
 /* ---------------------------------------------------------------------- */
@@ -303,6 +316,19 @@ int sg_sim_get_atlas(sg_sim_t sim, uint32_t* atlas_host, size_t* words, int64_t*
 int sg_sim_get_clearance(sg_sim_t sim, uint8_t* host, size_t* bytes, int64_t* offs_host);
 
 /*
+ * Copy the sector skip planes to the host (see march_sectors in
+ * sg_sim_config; an acceleration structure, not part of the paper's step).
+ * Plane s of map m: byte offs_host[m] + s * W * H + cy * W + cx, for the ray
+ * directions whose angle lies in [-pi + s 2pi/S, -pi + (s+1) 2pi/S), S =
+ * march_sectors: 0 on occupied cells, else a number of march samples J >= 1
+ * such that from a sample in cell (cx, cy) the next J - 1 samples of such a
+ * ray lie in free cells of the map.  *bytes: in = capacity of host, out =
+ * total bytes (S x sum of W x H; 0 when S = 1).  host and offs_host may be
+ * NULL.  Synchronous.
+ */
+int sg_sim_get_sector_skip(sg_sim_t sim, uint8_t* host, size_t* bytes, int64_t* offs_host);
+
+/*
  * Read (synchronously) and clear the device status word: SG_DEV_* bits.
  * Returns SG_E_DEVICE if any bit was set, SG_OK otherwise.
  */
@@ -428,6 +454,13 @@ int sg_replay_write(sg_replay_t r, int64_t first, int64_t count, const float* s_
  *   loss_dev    NULL or 1 float: the batch loss.
  *   grad_dev    NULL or num_params floats: the summed gradient.
  * The replay's obs_dim must equal n_in; batch in [1, max_batch].
+ * Device-side failure: when a weight-image copy into shared memory does not
+ * complete within its bounded wait, or a sampled transition's action is not
+ * below 5 (possible only for entries written by sg_replay_write), the step
+ * makes no update: loss_dev and every grad_dev entry are NaN, and the
+ * parameters, the target copy, the Adam moments and the step count stay as
+ * they were.  The return code is SG_OK (the failure is found on the device,
+ * after the call returned); check loss_dev for NaN.
  */
 int sg_td_train_step(sg_qnet_t q, sg_replay_t replay, int32_t batch, float gamma, float lr, int32_t target_every,
                      uint64_t seed, float* loss_dev, float* grad_dev, sg_stream_t stream);
@@ -466,10 +499,14 @@ int sg_vem_eps(sg_sim_t sim, float e_min, float e_max, double or_start, double o
  *                 r_dev batch floats.  All caller-owned device memory.
  *   batch         in [1, 256].
  *   loss_dev      NULL or 1 float; grad_dev num_params floats (outputs).
+ * An action index of 5 or more in a_dev, or a weight-image copy that does
+ * not complete within its bounded wait, makes the whole result NaN (loss_dev
+ * and every grad_dev entry), never a partial or a previous call's gradient.
  * Scratch: one file-scope device array of about 5.8 MB (BF16 weight images,
- * targets, per-CTA partial gradients) that every GPU loading the library
- * holds until the process exits.  Every call shares it and overwrites all of
- * it that it reads, so nothing carries over between calls; calls that
+ * targets, per-CTA partial gradients, a failure word) that every GPU loading
+ * the library holds until the process exits.  Every call shares it, clears
+ * its failure word and overwrites all of it that it reads, so nothing
+ * carries over between calls; calls that
  * overlap on the GPU (two streams, two threads) race on it and must be
  * serialised by the caller.  The first call on a device looks up the array's
  * device address and sets kernel attributes (no allocation); make that first

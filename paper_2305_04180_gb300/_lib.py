@@ -46,6 +46,7 @@ class sg_sim_config(C.Structure):
         ("seed", C.c_uint64),
         ("n_dyn", C.c_int32), ("dyn_radius", C.c_float), ("dyn_speed_lo", C.c_float),
         ("dyn_speed_hi", C.c_float), ("dyn_keepout", C.c_float),
+        ("march_sectors", C.c_int32),
     ]
 
 
@@ -61,7 +62,7 @@ SG_ROLLOUT_KERNELS = {"grid": 0, "queue": 1, "split": 2, "pipe": 3}
 class sg_sim_info(C.Structure):
     _fields_ = [("n_envs", C.c_int32), ("n_beams", C.c_int32), ("obs_dim", C.c_int32), ("n_maps", C.c_int32),
                 ("atlas_words", C.c_int64), ("state_bytes", C.c_int64), ("device", C.c_int32),
-                ("pad0", C.c_int32)]
+                ("march_sectors", C.c_int32)]
 
 
 _vp = C.c_void_p
@@ -80,6 +81,7 @@ SIGNATURES = {
     "sg_sim_set_state": (C.c_int, [_vp, _vp, C.c_size_t]),
     "sg_sim_get_atlas": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "sg_sim_get_clearance": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "sg_sim_get_sector_skip": (C.c_int, [_vp, _vp, _vp, _vp]),
     "sg_sim_status": (C.c_int, [_vp, _vp]),
     "sg_qnet_create": (C.c_int, [_i32, _i32, _i32, C.c_uint64, _vp]),
     "sg_qnet_destroy": (C.c_int, [_vp]),

@@ -37,16 +37,39 @@ constexpr int kClrBorder = 2;
 struct MapDesc {
   long long word_off;
   long long clr_off;   // interior cell (0, 0) of the map's skip map
+  long long sec_off;   // interior cell (0, 0) of sector plane 0 (see sector skip maps below)
+  long long sec_plane; // bytes between consecutive sector planes of the map
   int w, h;
   int row_words;
-  int clr_ld;          // row stride of the skip map, w + 2 * kClrBorder
+  int clr_ld;          // row stride of the skip map and of the sector planes, w + 2 * kClrBorder
 };
+
+// Sector skip maps (optional, n_sec > 1 planes per map; an acceleration
+// structure of the march, not part of the step's definition).  The
+// directions of travel are cut into n_sec equal sectors; sector s holds the
+// directions whose angle lies in [-pi + s 2pi/n_sec, -pi + (s+1) 2pi/n_sec).
+// Plane s stores, for every free cell c, a number J >= 1 of march samples
+// that can be skipped by a ray of a sector-s direction whose current sample
+// lies in c: J = max(ceil(SC - 0.01), Chebyshev skip of c), where SC is the
+// smallest distance from a point of c, along a direction of the sector
+// widened by 0.01 rad on each side, to a point of an occupied or outside
+// cell, capped at kSecRadius.  The planes have the skip map's layout (zero
+// border, 0 on occupied cells).  Why J is exact for march steps <= 1 cell:
+// from sample k (in c) the displacement to sample k + j is j u plus two
+// float32 roundings (< 0.003 cells on maps up to 16384), so it points
+// within 0.003 rad of u for j >= 1 and is shorter than j + 0.003 < SC for
+// j < J; the samples k+1 .. k+J-1 therefore lie in free cells and the first
+// sample that can hit is k + J, as with the Chebyshev skip.
+constexpr int kSecRadius = 48;
+constexpr int kMaxSectors = 32;
 
 // Launch-time copy of the configuration (float32 values).
 struct DevCfg {
   int n_envs, B, obs_dim, n_actions, t_max, kmax, delay_lo, delay_span;
   int skip_ok;      // march_step <= 1: clearance skipping is exact
   int clr_collide;  // skip value from which the collision disc cannot touch a wall
+  int n_sec;        // sector skip planes per map (1: the Chebyshev skip map only)
+  float sec_scale;  // n_sec / (2 pi): beam angle beta -> sector of u = -(cos beta, sin beta)
   float fov, half_fov, range_max, delta, robot_r, goal_r, near_dist, start_offset, jitter;
   float dt_lo, dt_hi, k_lo, k_hi, cap_lo, cap_hi, sig_lo, sig_hi;
   float v_nom, w_nom;
@@ -67,6 +90,7 @@ struct SimPtrs {
   uint32_t* u;            // [4][n]: ep_step ep_id t fifo
   const uint32_t* atlas;  // bit-packed maps
   const uint8_t* clr;     // skip maps (see march())
+  const uint8_t* sec;     // sector skip planes (n_sec > 1), else null
   const MapDesc* maps;
   const int* env_map;
   const int* env_beams;   // nullptr: every env uses B beams
@@ -260,7 +284,9 @@ __device__ __forceinline__ Layout layout_of(const DevCfg& c, const MapDesc& m) {
 // current one (2 when c = 1), so from an origin inside the map no sample
 // leaves the border before a zero stops the march: that loop has no bounds
 // test.  Origins outside the map, and steps above one cell (no skipping), use
-// the bounds-tested loop.
+// the bounds-tested loop.  The same loop runs on a sector plane (see
+// MapDesc): its values are skips of the same meaning for the rays of its
+// sector, with the same zero border.
 template <bool kUnitStep>
 __device__ __forceinline__ int march(const uint8_t* __restrict__ clr, int W, int H, int ld, float x, float y,
                                      float ux, float uy, float delta, int kmax, int skip_ok) {
@@ -518,6 +544,7 @@ struct EnvConst {
   MapDesc m;
   const uint32_t* rows;  // this env's bit rows
   const uint8_t* clr;    // this env's clearance map
+  const uint8_t* sec;    // this env's sector plane 0 (n_sec > 1)
   Layout L;
   int env, nb;
   float off0, off1;      // heading offsets of this lane's beams (lane, lane + 32)
@@ -531,6 +558,7 @@ __device__ __forceinline__ EnvConst env_const(const DevCfg& c, const SimPtrs& p,
   k.m = p.maps[p.env_map[env]];
   k.rows = p.atlas + k.m.word_off;
   k.clr = p.clr + k.m.clr_off;
+  k.sec = p.sec ? p.sec + k.m.sec_off : nullptr;
   k.L = layout_of(c, k.m);
   k.nb = p.env_beams ? p.env_beams[env] : c.B;
   // beam j points at phi + j * (fov / (nb - 1)) - fov / 2
@@ -593,9 +621,13 @@ __device__ __forceinline__ float beam_at(const DevCfg& c, const EnvConst& k, flo
   const float beta = phi + off;
   float sn, cs;
   f_sincos(beta, sn, cs);
+  // the skip values of this beam's sector: u = -(cos beta, sin beta) has
+  // angle beta + pi, whose sector index is floor(beta n_sec / 2pi) mod n_sec
+  const uint8_t* skip =
+      c.n_sec > 1 ? k.sec + (long long)(__float2int_rd(beta * c.sec_scale) & (c.n_sec - 1)) * k.m.sec_plane : k.clr;
   int h = c.delta == 1.0f
-              ? march<true>(k.clr, k.m.w, k.m.h, k.m.clr_ld, x, y, -cs, -sn, c.delta, c.kmax, 1)
-              : march<false>(k.clr, k.m.w, k.m.h, k.m.clr_ld, x, y, -cs, -sn, c.delta, c.kmax, c.skip_ok);
+              ? march<true>(skip, k.m.w, k.m.h, k.m.clr_ld, x, y, -cs, -sn, c.delta, c.kmax, 1)
+              : march<false>(skip, k.m.w, k.m.h, k.m.clr_ld, x, y, -cs, -sn, c.delta, c.kmax, c.skip_ok);
   if (kDyn)
     h = c.delta == 1.0f ? discs_first<true>(c, *d, x, y, -cs, -sn, h) : discs_first<false>(c, *d, x, y, -cs, -sn, h);
   float r = fminf((float)h * c.delta, c.range_max);
@@ -912,6 +944,7 @@ __device__ __forceinline__ float scan_env(const DevCfg& c, const SimPtrs& p, con
   EnvConst k;
   k.m = m;
   k.clr = p.clr + m.clr_off;
+  k.sec = p.sec ? p.sec + m.sec_off : nullptr;
   k.nb = nb;
   const float off0 = (float)lane * stepb - c.half_fov;
   const float off1 = (float)(lane + 32) * stepb - c.half_fov;

@@ -18,6 +18,8 @@ struct sg_sim {
   std::vector<sg::MapDesc> maps_host;
   uint32_t* atlas = nullptr;
   uint8_t* clr = nullptr;
+  uint8_t* sec = nullptr;      // sector skip planes (dc.n_sec > 1), else null
+  long long sec_bytes = 0;
   sg::MapDesc* maps_dev = nullptr;
   int* env_map_dev = nullptr;
   int* env_beams_dev = nullptr;

@@ -145,6 +145,7 @@ struct sg_qnet {
   uint8_t* img = nullptr;    // online BF16 image
   uint8_t* img_t = nullptr;  // target BF16 image
   unsigned long long* step = nullptr;  // optimiser steps taken (device)
+  unsigned* td_fail = nullptr;         // SG_TD_FAIL_* bits of the current TD step (device), cleared per step
   // learner scratch, sized for max_batch
   int max_batch = 0;
   float* partial = nullptr;  // [max_batch / kTile][P + 1] (last entry: loss)
@@ -1279,6 +1280,13 @@ __global__ void __launch_bounds__(kQtThreads, 1)
 __global__ void k_replay_advance(unsigned long long* steps, int K) { *steps += (unsigned long long)K; }
 
 // ------------------------------------------------------------ learner
+// Why a TD step produced no update (bits of a device word cleared at the
+// start of every step): a weight-image copy did not complete within its
+// bounded wait, or a sample's action index is outside the action table.
+// k_adam then writes NaN loss and gradient and leaves the parameters, the
+// Adam moments and the image untouched; the step count does not advance.
+constexpr unsigned kTdFailCopy = 1u;
+constexpr unsigned kTdFailAction = 2u;
 // Ring entry of sample i of optimiser step `tstep`: uniform over the
 // V = min(steps, slots - reserve) most recently completed slots, so that a
 // rollout running concurrently (which writes the next slots) is never read.
@@ -1312,7 +1320,7 @@ __device__ __forceinline__ void gather_tile(bf16* X, int ld1, const float* __res
 __global__ void __launch_bounds__(kThreads, 1)
     k_td_target(const uint8_t* __restrict__ img, const uint8_t* __restrict__ img_t, ImgLayout L, ReplayDev rp,
                 unsigned long long seed, const unsigned long long* __restrict__ step, int batch, float gamma,
-                float* __restrict__ y, int* __restrict__ idx) {
+                float* __restrict__ y, int* __restrict__ idx, unsigned* __restrict__ fail) {
   extern __shared__ __align__(16) uint8_t smem[];
   uint8_t* sw = smem;
   bf16* X = reinterpret_cast<bf16*>(smem + L.bytes);
@@ -1333,6 +1341,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   // online image (phase 0) while the tile is gathered; a copy that does not
   // complete makes the targets NaN
   bool ok = stage_image_bulk(sw, img, L.bytes, &bar_img, 0u, kTcTries);
+  uint32_t phase = 0u;  // the copy in flight
   gather_tile(X, L.ld1, rp.s2, rows, rp.obs_dim, warp, lane);
   __syncthreads();
   if (ok) mlp_tile(qw_at(sw, L), X, H1, H2, O, warp, lane);
@@ -1340,9 +1349,20 @@ __global__ void __launch_bounds__(kThreads, 1)
   fence_async_smem();  // this thread's reads of the online image before the bulk copy overwrites it
   __syncthreads();
   // the target image over it (phase 1)
-  if (ok) ok = stage_image_bulk(sw, img_t, L.bytes, &bar_img, 1u, kTcTries);
+  if (ok) {
+    phase = 1u;
+    ok = stage_image_bulk(sw, img_t, L.bytes, &bar_img, 1u, kTcTries);
+  }
   if (ok) mlp_tile(qw_at(sw, L), X, H1, H2, O, warp, lane);
-  if (lane == 0 && i < batch && !ok) y[i] = __int_as_float(0x7fc00000);
+  if (!ok) {
+    if (threadIdx.x == 0) {
+      atomicOr(fail, kTdFailCopy);
+      // the copy that timed out may still be writing shared memory: give it
+      // one more bounded wait before the CTA exits
+      mbar_wait(&bar_img, phase, kTcTries);
+    }
+    if (lane == 0 && i < batch) y[i] = __int_as_float(0x7fc00000);
+  }
   if (lane == 0 && i < batch && ok) {
     float qv[5];
     greedy_action(O + warp * kOutPad, qv, L.plain);
@@ -1360,7 +1380,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 // that the reduction order is fixed.
 __global__ void __launch_bounds__(kThreads, 1)
     k_td_grad(const uint8_t* __restrict__ img, ImgLayout L, ParamLayout P, ReplayDev rp,
-              const int* __restrict__ idx, const float* __restrict__ y, int batch, float* __restrict__ partial) {
+              const int* __restrict__ idx, const float* __restrict__ y, int batch, float* __restrict__ partial,
+              unsigned* __restrict__ fail) {
   extern __shared__ __align__(16) uint8_t smem[];
   uint8_t* sw = smem;
   bf16* S = reinterpret_cast<bf16*>(smem + L.bytes);
@@ -1379,8 +1400,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (threadIdx.x == 0) mbar_init(&bar_img, 1);
   __syncthreads();
   if (!stage_image_bulk(sw, img, L.bytes, &bar_img, 0u, kTcTries)) {
-    // the image copy did not complete: this CTA's loss term is NaN
-    if (threadIdx.x == 0) partial[(long long)blockIdx.x * partial_stride(P.total) + P.total] = __int_as_float(0x7fc00000);
+    // the image copy did not complete: no update this step (k_adam reads the
+    // flag); one more bounded wait for the copy before the CTA exits
+    if (threadIdx.x == 0) {
+      atomicOr(fail, kTdFailCopy);
+      mbar_wait(&bar_img, 0u, kTcTries);
+    }
     return;
   }
   gather_tile(S, L.ld1, rp.s, rows, rp.obs_dim, warp, lane);
@@ -1394,11 +1419,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int e = rows[warp];
     float gq = 0.0f, hl = 0.0f;
     if (e >= 0) {
-      const int a = rp.a[e];
-      const float d = qv[a] - y[i];
+      int a = rp.a[e];
+      float d;
+      if (a >= 5) {
+        // outside the action table: no loss term, and no update this step
+        atomicOr(fail, kTdFailAction);
+        a = 0;
+        d = __int_as_float(0x7fc00000);
+      } else {
+        d = qv[a] - y[i];
+      }
       const float ad = fabsf(d);
       hl = ad <= 1.0f ? 0.5f * d * d : ad - 0.5f;
-      gq = fminf(fmaxf(d, -1.0f), 1.0f) / (float)batch;
+      // a NaN target (a failed target copy) stays NaN through the clip
+      gq = (isnan(d) ? d : fminf(fmaxf(d, -1.0f), 1.0f)) / (float)batch;
       if (L.plain) {
         for (int k = 0; k < 5; ++k) DO[warp * kOutPad + k] = k == a ? gq : 0.0f;
         DO[warp * kOutPad + 5] = 0.0f;
@@ -1525,8 +1559,19 @@ __global__ void __launch_bounds__(kThreads, 1)
 __global__ void k_adam(float* __restrict__ th, float* __restrict__ m, float* __restrict__ v,
                        const float* __restrict__ partial, int nblk, ParamLayout P, ImgLayout L, uint8_t* __restrict__ img,
                        const unsigned long long* __restrict__ step, float lr, float b1, float b2, float eps,
-                       float* __restrict__ loss, float* __restrict__ grad_out, int batch) {
+                       float* __restrict__ loss, float* __restrict__ grad_out, int batch,
+                       const unsigned* __restrict__ fail) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (*fail) {
+    // no usable gradient this step: NaN out, parameters and moments unchanged
+    const float qnan = __int_as_float(0x7fc00000);
+    if (i == 0 && loss) *loss = qnan;
+    if (grad_out && i < P.total) {
+      const int j = L.plain ? paper_index(i, P, L.n_in) : i;
+      if (j >= 0) grad_out[j] = qnan;
+    }
+    return;
+  }
   if (i == 0 && loss) {
     float acc = 0.0f;
     for (int b = 0; b < nblk; ++b) acc += partial[(long long)b * partial_stride(P.total) + P.total];
@@ -1569,7 +1614,9 @@ __global__ void k_adam(float* __restrict__ th, float* __restrict__ m, float* __r
   }
 }
 
-__global__ void k_step_advance(unsigned long long* step) { *step += 1ull; }
+__global__ void k_step_advance(unsigned long long* step, const unsigned* __restrict__ fail) {
+  if (!*fail) *step += 1ull;
+}
 
 // Target network <- online network when the optimiser step count is a
 // multiple of `every` (checked on the device, so the call can be replayed
@@ -1628,6 +1675,7 @@ void free_qnet(sg_qnet* q) {
   cudaFree(q->img);
   cudaFree(q->img_t);
   cudaFree(q->step);
+  cudaFree(q->td_fail);
   cudaFree(q->partial);
   cudaFree(q->y);
   cudaFree(q->idx);
@@ -1661,6 +1709,7 @@ extern "C" int sg_qnet_create(int32_t n_in, int32_t arch, int32_t max_batch, uin
   alloc((void**)&q->img, (size_t)q->IL.bytes);
   alloc((void**)&q->img_t, (size_t)q->IL.bytes);
   alloc((void**)&q->step, 8);
+  alloc((void**)&q->td_fail, 4);
   alloc((void**)&q->partial, nblk * partial_stride(P) * 4);
   alloc((void**)&q->y, (size_t)q->max_batch * 4);
   alloc((void**)&q->idx, (size_t)q->max_batch * 4);
@@ -1675,6 +1724,7 @@ extern "C" int sg_qnet_create(int32_t n_in, int32_t arch, int32_t max_batch, uin
   if (e == cudaSuccess) e = cudaMemset(q->adam_m, 0, P * 4);
   if (e == cudaSuccess) e = cudaMemset(q->adam_v, 0, P * 4);
   if (e == cudaSuccess) e = cudaMemset(q->step, 0, 8);
+  if (e == cudaSuccess) e = cudaMemset(q->td_fail, 0, 4);
   if (e == cudaSuccess) e = cudaMemset(q->img, 0, (size_t)q->IL.bytes);
   if (e == cudaSuccess) e = cudaMemset(q->img_t, 0, (size_t)q->IL.bytes);
   if (e == cudaSuccess) {
@@ -2008,19 +2058,21 @@ extern "C" int sg_td_train_step(sg_qnet_t q, sg_replay_t rp, int32_t batch, floa
   if (!q || !rp || batch < 1 || batch > q->max_batch || rp->d.obs_dim != q->n_in) return SG_E_INVAL;
   if (!(gamma >= 0.0f && gamma <= 1.0f) || !(lr >= 0.0f)) return SG_E_INVAL;
   const int nblk = (batch + kTile - 1) / kTile;
+  SG_CUDA(cudaMemsetAsync(q->td_fail, 0, 4, stream));
   k_td_target<<<nblk, kThreads, fwd_smem(q->IL), stream>>>(q->img, q->img_t, q->IL, rp->d, seed, q->step, batch,
-                                                            gamma, q->y, q->idx);
+                                                            gamma, q->y, q->idx, q->td_fail);
   SG_CUDA(cudaGetLastError());
   k_td_grad<<<nblk, kThreads, grad_smem(q->IL), stream>>>(q->img, q->IL, q->PL, rp->d, q->idx, q->y, batch,
-                                                          q->partial);
+                                                          q->partial, q->td_fail);
   SG_CUDA(cudaGetLastError());
   const int P = q->PL.total;
   k_adam<<<(P + 255) / 256, 256, 0, stream>>>(q->master, q->adam_m, q->adam_v, q->partial, nblk, q->PL, q->IL, q->img,
-                                               q->step, lr, 0.9f, 0.999f, 1e-8f, loss_dev, grad_dev, batch);
+                                               q->step, lr, 0.9f, 0.999f, 1e-8f, loss_dev, grad_dev, batch,
+                                               q->td_fail);
   SG_CUDA(cudaGetLastError());
   if (int rc = refresh_tc_image(q, stream)) return rc;
   if (lr > 0.0f) {
-    k_step_advance<<<1, 1, 0, stream>>>(q->step);
+    k_step_advance<<<1, 1, 0, stream>>>(q->step, q->td_fail);
     SG_CUDA(cudaGetLastError());
     const int words = q->IL.bytes / 4;
     const int n = P > words ? P : words;
@@ -2054,7 +2106,8 @@ static_assert(kNaImgBytes + 16 < (1 << 20), "one weight image fits an mbarrier p
 constexpr int kNaMaxParams = kHid * kNaMaxIn + kHid + kHid * kHid + kHid + kOut * kHid + kOut;
 constexpr long long kNaOffY = 2ll * kNaImgSlot;
 constexpr long long kNaOffIdx = kNaOffY + kNaMaxBatch * 4;
-constexpr long long kNaOffPartial = (kNaOffIdx + kNaMaxBatch * 4 + 255) / 256 * 256;
+constexpr long long kNaOffFail = kNaOffIdx + kNaMaxBatch * 4;
+constexpr long long kNaOffPartial = (kNaOffFail + 4 + 255) / 256 * 256;
 constexpr long long kNaBytes = kNaOffPartial + (long long)kNaMaxBlk * partial_stride(kNaMaxParams) * 4;
 }  // namespace
 
@@ -2144,6 +2197,7 @@ extern "C" int sg_td_grad_noalloc(const float* params_dev, const float* target_p
   float* y = reinterpret_cast<float*>(base + kNaOffY);
   int* idx = reinterpret_cast<int*>(base + kNaOffIdx);
   float* partial = reinterpret_cast<float*>(base + kNaOffPartial);
+  unsigned* fail = reinterpret_cast<unsigned*>(base + kNaOffFail);
   ReplayDev b;
   std::memset(&b, 0, sizeof(b));
   b.s = const_cast<float*>(s_dev);
@@ -2160,12 +2214,14 @@ extern "C" int sg_td_grad_noalloc(const float* params_dev, const float* target_p
   k_build_image<<<(ne + 255) / 256, 256, 0, stream>>>(target_params_dev, img_t, IL, PL);
   SG_CUDA(cudaGetLastError());
   const int nblk = (batch + kTile - 1) / kTile;
+  SG_CUDA(cudaMemsetAsync(fail, 0, 4, stream));
   k_td_target_given<<<nblk, kThreads, fwd_smem(IL), stream>>>(img, img_t, IL, b, batch, gamma, y, idx);
   SG_CUDA(cudaGetLastError());
-  k_td_grad<<<nblk, kThreads, grad_smem(IL), stream>>>(img, IL, PL, b, idx, y, batch, partial);
+  k_td_grad<<<nblk, kThreads, grad_smem(IL), stream>>>(img, IL, PL, b, idx, y, batch, partial, fail);
   SG_CUDA(cudaGetLastError());
   k_adam<<<(PL.total + 255) / 256, 256, 0, stream>>>(nullptr, nullptr, nullptr, partial, nblk, PL, IL, nullptr,
-                                                      nullptr, 0.0f, 0.9f, 0.999f, 1e-8f, loss_dev, grad_dev, batch);
+                                                      nullptr, 0.0f, 0.9f, 0.999f, 1e-8f, loss_dev, grad_dev, batch,
+                                                      fail);
   SG_CUDA(cudaGetLastError());
   return SG_OK;
 }

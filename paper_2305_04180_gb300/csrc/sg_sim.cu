@@ -101,6 +101,46 @@ __global__ void k_clr_cols(const uint8_t* __restrict__ g, const PrepMap* __restr
   clr[d.clr_off + (long long)cy * d.clr_ld + cx] = (uint8_t)(best == 0 ? 0 : max(1, best - 1));
 }
 
+// Sector skip planes (see MapDesc in sg_device.cuh).  Block (x, y): 256
+// cells of the maps' concatenated cells, sector y.  The sector's offset list
+// (cell offsets o with their skip J(o) = max(1, ceil(D(o) - 0.01)), sorted
+// by the wedge distance D(o), every o with D(o) <= kSecRadius) is staged in
+// shared memory; a free cell takes the J of the first offset whose cell is
+// occupied or outside the map (the nearest obstacle in the widened sector),
+// kSecRadius when there is none, and at least its Chebyshev skip.
+__global__ void __launch_bounds__(256) k_sector_skip(const uint32_t* __restrict__ atlas, const uint8_t* __restrict__ clr,
+                                                     const MapDesc* __restrict__ maps,
+                                                     const long long* __restrict__ cell_prefix, int n_maps,
+                                                     long long total, const uint32_t* __restrict__ table,
+                                                     const int* __restrict__ tab_start, uint8_t* __restrict__ sec) {
+  extern __shared__ uint32_t offs[];
+  const int sector = blockIdx.y;
+  const int t0 = tab_start[sector], nt = tab_start[sector + 1] - t0;
+  for (int i = threadIdx.x; i < nt; i += blockDim.x) offs[i] = table[t0 + i];
+  __syncthreads();
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const int m = find_map(cell_prefix, n_maps, i);
+  const MapDesc d = maps[m];
+  const long long local = i - cell_prefix[m];
+  const int cx = (int)(local % d.w), cy = (int)(local / d.w);
+  const int own = clr[d.clr_off + (long long)cy * d.clr_ld + cx];
+  if (own == 0) return;  // occupied: the plane keeps its 0
+  const uint32_t* rows = atlas + d.word_off;
+  int J = kSecRadius;
+  for (int e = 0; e < nt; ++e) {
+    const uint32_t v = offs[e];
+    const int px = cx + (int)(int8_t)(v & 0xFFu), py = cy + (int)(int8_t)((v >> 8) & 0xFFu);
+    const bool blocked = (unsigned)px >= (unsigned)d.w || (unsigned)py >= (unsigned)d.h ||
+                         ((rows[(long long)py * d.row_words + (px >> 5)] >> (px & 31)) & 1u);
+    if (blocked) {
+      J = (int)((v >> 16) & 0xFFu);
+      break;
+    }
+  }
+  sec[d.sec_off + (long long)sector * d.sec_plane + (long long)cy * d.clr_ld + cx] = (uint8_t)max(J, own);
+}
+
 // Episode 0 of every env; one warp per env.
 template <bool kDyn>
 __global__ void __launch_bounds__(128) k_reset(const __grid_constant__ DevCfg c, SimPtrs p, float* __restrict__ obs) {
@@ -889,6 +929,10 @@ static int make_devcfg(const sg_sim_config* cfg, DevCfg* dc) {
   if (!(kmaxf >= 1.0f) || kmaxf > 4096.0f) return SG_E_INVAL;
   if (!finite_nonneg(cfg->fov) || !finite_nonneg(cfg->robot_radius) || !finite_nonneg(cfg->goal_radius))
     return SG_E_INVAL;
+  if (cfg->fov > 6.2831855f) return SG_E_INVAL;  // at most one turn
+  if (cfg->march_sectors < 0 || cfg->march_sectors > kMaxSectors ||
+      (cfg->march_sectors > 1 && (cfg->march_sectors & (cfg->march_sectors - 1))) || cfg->march_sectors == 2)
+    return SG_E_INVAL;
   if (!std::isfinite(cfg->near_dist) || !std::isfinite(cfg->start_offset) || !finite_nonneg(cfg->start_jitter))
     return SG_E_INVAL;
   const float pairs[][2] = {{cfg->dt_lo, cfg->dt_hi}, {cfg->k_lo, cfg->k_hi}, {cfg->cap_lo, cfg->cap_hi},
@@ -957,12 +1001,149 @@ static int make_devcfg(const sg_sim_config* cfg, DevCfg* dc) {
   return SG_OK;
 }
 
+// ---------------------------------------------------- sector skip tables
+// Wedge distance of a cell offset o for the direction sector [a0, a1]
+// (a1 - a0 < pi): the smallest |w| over the points w of the square
+// [ox - 1, ox + 1] x [oy - 1, oy + 1] (every difference q' - q of a point q'
+// of the offset cell and a point q of the origin cell) whose direction lies
+// in the sector; infinity when only w = 0 does (no forward motion within the
+// sector reaches the cell).  The square is clipped by the sector's two
+// bounding half-planes (Sutherland-Hodgman), then the distance from the
+// origin to the convex remainder is taken.
+static int clip_halfplane(const double (*in)[2], int n, double nx, double ny, double (*out)[2]) {
+  int m = 0;
+  for (int i = 0; i < n; ++i) {
+    const double* P = in[i];
+    const double* Q = in[(i + 1) % n];
+    const double dp = nx * P[0] + ny * P[1], dq = nx * Q[0] + ny * Q[1];
+    if (dp >= 0.0) {
+      out[m][0] = P[0];
+      out[m][1] = P[1];
+      ++m;
+    }
+    if ((dp >= 0.0) != (dq >= 0.0)) {
+      const double t = dp / (dp - dq);
+      out[m][0] = P[0] + t * (Q[0] - P[0]);
+      out[m][1] = P[1] + t * (Q[1] - P[1]);
+      ++m;
+    }
+  }
+  return m;
+}
+
+static double segment_to_origin(const double* A, const double* B) {
+  const double dx = B[0] - A[0], dy = B[1] - A[1];
+  const double L = dx * dx + dy * dy;
+  double t = L > 0.0 ? -(A[0] * dx + A[1] * dy) / L : 0.0;
+  t = t < 0.0 ? 0.0 : (t > 1.0 ? 1.0 : t);
+  const double px = A[0] + t * dx, py = A[1] + t * dy;
+  return std::sqrt(px * px + py * py);
+}
+
+double sg_wedge_distance(int ox, int oy, double a0, double a1) {
+  double sq[4][2] = {{ox - 1.0, oy - 1.0}, {ox + 1.0, oy - 1.0}, {ox + 1.0, oy + 1.0}, {ox - 1.0, oy + 1.0}};
+  double t1[16][2], t2[16][2];
+  // left of the ray at a0 and right of the ray at a1
+  int n = clip_halfplane(sq, 4, -std::sin(a0), std::cos(a0), t1);
+  if (n == 0) return HUGE_VAL;
+  n = clip_halfplane(t1, n, std::sin(a1), -std::cos(a1), t2);
+  if (n == 0) return HUGE_VAL;
+  double far = 0.0;
+  for (int i = 0; i < n; ++i) far = std::max(far, std::hypot(t2[i][0], t2[i][1]));
+  if (far < 1e-9) return HUGE_VAL;  // the apex alone
+  bool inside = true;  // the origin inside the (counter-clockwise) polygon
+  for (int i = 0; i < n && inside; ++i) {
+    const double* P = t2[i];
+    const double* Q = t2[(i + 1) % n];
+    if ((Q[0] - P[0]) * (-P[1]) - (Q[1] - P[1]) * (-P[0]) < -1e-12) inside = false;
+  }
+  if (inside) return 0.0;
+  double best = HUGE_VAL;
+  for (int i = 0; i < n; ++i) best = std::min(best, segment_to_origin(t2[i], t2[(i + 1) % n]));
+  return best;
+}
+
+// Offset lists of the n_sec sectors: entry = ox & 0xFF | (oy & 0xFF) << 8 |
+// J << 16 with J = max(1, ceil(D - 0.01)), sorted by D (then oy, ox), every
+// offset with D <= kSecRadius; start[s] .. start[s + 1] is sector s.
+constexpr double kSecWiden = 0.01;   // radians added on both sides of a sector
+constexpr double kSecMargin = 0.01;  // cells taken off the wedge distance
+
+void sg_sector_table(int n_sec, std::vector<uint32_t>& table, std::vector<int>& start) {
+  table.clear();
+  start.assign(1, 0);
+  const int R = kSecRadius + 2;
+  struct E {
+    double d;
+    int ox, oy;
+  };
+  std::vector<E> list;
+  for (int sct = 0; sct < n_sec; ++sct) {
+    const double a0 = -M_PI + sct * 2.0 * M_PI / n_sec - kSecWiden;
+    const double a1 = -M_PI + (sct + 1) * 2.0 * M_PI / n_sec + kSecWiden;
+    list.clear();
+    for (int oy = -R; oy <= R; ++oy)
+      for (int ox = -R; ox <= R; ++ox) {
+        if (ox == 0 && oy == 0) continue;  // the cell the sample is in (free)
+        const double d = sg_wedge_distance(ox, oy, a0, a1);
+        if (d <= (double)kSecRadius) list.push_back({d, ox, oy});
+      }
+    std::sort(list.begin(), list.end(), [](const E& a, const E& b) {
+      return a.d != b.d ? a.d < b.d : (a.oy != b.oy ? a.oy < b.oy : a.ox < b.ox);
+    });
+    for (const E& e : list) {
+      const int J = std::max(1, (int)std::ceil(e.d - kSecMargin));
+      table.push_back((uint32_t)(e.ox & 0xFF) | ((uint32_t)(e.oy & 0xFF) << 8) | ((uint32_t)J << 16));
+    }
+    start.push_back((int)table.size());
+  }
+}
+
+// Build the sector planes of every map (the skip maps and bit atlas exist).
+static cudaError_t build_sector_planes(sg_sim* s) {
+  std::vector<uint32_t> table;
+  std::vector<int> start;
+  sg_sector_table(s->dc.n_sec, table, start);
+  int max_list = 0;
+  for (int i = 0; i < s->dc.n_sec; ++i) max_list = std::max(max_list, start[i + 1] - start[i]);
+  std::vector<long long> prefix((size_t)s->n_maps + 1, 0);
+  for (int m = 0; m < s->n_maps; ++m)
+    prefix[m + 1] = prefix[m] + (long long)s->maps_host[m].w * s->maps_host[m].h;
+  uint32_t* tab_dev = nullptr;
+  int* start_dev = nullptr;
+  long long* prefix_dev = nullptr;
+  cudaError_t e = cudaMalloc((void**)&tab_dev, table.size() * 4);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&start_dev, start.size() * 4);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&prefix_dev, prefix.size() * 8);
+  if (e == cudaSuccess) e = cudaMemcpy(tab_dev, table.data(), table.size() * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(start_dev, start.data(), start.size() * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(prefix_dev, prefix.data(), prefix.size() * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(s->sec, 0, (size_t)s->sec_bytes);  // zero borders and occupied cells
+  if (e == cudaSuccess) {
+    const size_t smem = (size_t)max_list * 4;
+    if (smem > 48 * 1024) e = cudaFuncSetAttribute(k_sector_skip, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const long long total = prefix.back();
+    if (e == cudaSuccess) {
+      dim3 grid((unsigned)((total + 255) / 256), (unsigned)s->dc.n_sec);
+      k_sector_skip<<<grid, 256, smem>>>(s->atlas, s->clr, s->maps_dev, prefix_dev, s->n_maps, total, tab_dev,
+                                         start_dev, s->sec);
+      e = cudaGetLastError();
+    }
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(tab_dev);
+  cudaFree(start_dev);
+  cudaFree(prefix_dev);
+  return e;
+}
+
 SimPtrs sg_sim_ptrs(sg_sim* s) {
   SimPtrs p;
   p.f = s->fstate;
   p.u = s->ustate;
   p.atlas = s->atlas;
   p.clr = s->clr;
+  p.sec = s->sec;
   p.maps = s->maps_dev;
   p.env_map = s->env_map_dev;
   p.env_beams = s->env_beams_dev;
@@ -977,6 +1158,7 @@ static void free_sim(sg_sim* s) {
   if (!s) return;
   cudaFree(s->atlas);
   cudaFree(s->clr);
+  cudaFree(s->sec);
   cudaFree(s->maps_dev);
   cudaFree(s->env_map_dev);
   cudaFree(s->env_beams_dev);
@@ -1026,6 +1208,28 @@ extern "C" int sg_sim_create(const sg_sim_config* cfg, int32_t n_maps, const uin
     if (env_map[i] < 0 || env_map[i] >= n_maps) return SG_E_INVAL;
     if (env_beams && (env_beams[i] < 2 || env_beams[i] > cfg->n_beams)) return SG_E_INVAL;
   }
+  // sector skip planes: n_sec planes of the skip-map layout per map
+  int n_sec = dc.skip_ok ? cfg->march_sectors : 1;
+  if (n_sec == 0) {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
+    const double limit = std::min(16.0 * (double)(1ull << 30), 0.25 * (double)free_b);
+    n_sec = 1;
+    for (int cand : {16, 8, 4})
+      if ((double)cand * (double)clr_bytes <= limit) {
+        n_sec = cand;
+        break;
+      }
+  }
+  dc.n_sec = n_sec;
+  dc.sec_scale = (float)((double)n_sec / (2.0 * M_PI));
+  long long sec_bytes = 0;
+  for (int m = 0; m < n_maps; ++m) {
+    const long long plane = (long long)md[m].clr_ld * (map_h[m] + 2 * kClrBorder);
+    md[m].sec_plane = n_sec > 1 ? plane : 0;
+    md[m].sec_off = n_sec > 1 ? sec_bytes + (long long)kClrBorder * md[m].clr_ld + kClrBorder : 0;
+    if (n_sec > 1) sec_bytes += plane * n_sec;
+  }
   sg_sim* s = new (std::nothrow) sg_sim();
   if (!s) return SG_E_OOM;
   s->cfg = *cfg;
@@ -1034,6 +1238,7 @@ extern "C" int sg_sim_create(const sg_sim_config* cfg, int32_t n_maps, const uin
   s->maps_host = md;
   s->atlas_words = words;
   s->clr_bytes = clr_bytes;
+  s->sec_bytes = sec_bytes;
   cudaGetDevice(&s->device);
   cudaError_t e = cudaSuccess;
   auto alloc = [&](void** ptr, size_t bytes) {
@@ -1042,6 +1247,7 @@ extern "C" int sg_sim_create(const sg_sim_config* cfg, int32_t n_maps, const uin
   };
   alloc((void**)&s->atlas, (size_t)words * 4);
   alloc((void**)&s->clr, (size_t)clr_bytes);
+  if (sec_bytes > 0) alloc((void**)&s->sec, (size_t)sec_bytes);
   alloc((void**)&s->maps_dev, sizeof(MapDesc) * n_maps);
   alloc((void**)&s->env_map_dev, sizeof(int) * n);
   if (env_beams) alloc((void**)&s->env_beams_dev, sizeof(int) * n);
@@ -1121,6 +1327,7 @@ extern "C" int sg_sim_create(const sg_sim_config* cfg, int32_t n_maps, const uin
   cudaFree(mp_dev);
   cudaFree(prefix_dev);
   if (e == cudaSuccess) e = cudaMemcpy(s->maps_dev, md.data(), sizeof(MapDesc) * n_maps, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && sec_bytes > 0) e = build_sector_planes(s);
   if (e == cudaSuccess) e = cudaMemcpy(s->env_map_dev, env_map, sizeof(int) * n, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) {
     std::vector<int> order((size_t)n);
@@ -1159,6 +1366,7 @@ extern "C" int sg_sim_info_get(sg_sim_t sim, sg_sim_info* info) {
   info->atlas_words = sim->atlas_words;
   info->state_bytes = sg_state_bytes(sim);
   info->device = sim->device;
+  info->march_sectors = sim->dc.n_sec;
   return SG_OK;
 }
 
@@ -1417,6 +1625,35 @@ extern "C" int sg_sim_get_clearance(sg_sim_t sim, uint8_t* host, size_t* bytes, 
     for (int m = 0; m < sim->n_maps; ++m) {
       offs_host[m] = off;
       off += (int64_t)sim->maps_host[m].w * sim->maps_host[m].h;
+    }
+  }
+  return SG_OK;
+}
+
+extern "C" int sg_sim_get_sector_skip(sg_sim_t sim, uint8_t* host, size_t* bytes, int64_t* offs_host) {
+  if (!sim || !bytes) return SG_E_INVAL;
+  const int S = sim->dc.n_sec > 1 ? sim->dc.n_sec : 0;
+  size_t total = 0;
+  for (int m = 0; m < sim->n_maps; ++m) total += (size_t)S * sim->maps_host[m].w * sim->maps_host[m].h;
+  if (host && total > 0) {
+    if (*bytes < total) return SG_E_INVAL;
+    SG_CUDA(cudaDeviceSynchronize());
+    size_t off = 0;
+    for (int m = 0; m < sim->n_maps; ++m) {
+      const MapDesc& d = sim->maps_host[m];
+      for (int p = 0; p < S; ++p) {
+        SG_CUDA(cudaMemcpy2D(host + off, (size_t)d.w, sim->sec + d.sec_off + (long long)p * d.sec_plane,
+                             (size_t)d.clr_ld, (size_t)d.w, (size_t)d.h, cudaMemcpyDeviceToHost));
+        off += (size_t)d.w * d.h;
+      }
+    }
+  }
+  *bytes = total;
+  if (offs_host) {
+    int64_t off = 0;
+    for (int m = 0; m < sim->n_maps; ++m) {
+      offs_host[m] = off;
+      off += (int64_t)S * sim->maps_host[m].w * sim->maps_host[m].h;
     }
   }
   return SG_OK;

@@ -36,6 +36,8 @@ def make_config(params: dict, n_envs: int) -> _lib.sg_sim_config:
     c.n_dyn = int(params.get("n_dyn", 0))
     for k in ("dyn_radius", "dyn_speed_lo", "dyn_speed_hi", "dyn_keepout"):
         setattr(c, k, float(params.get(k, 0.0)))
+    # direction sectors of the march's skip planes (0: chosen by the library)
+    c.march_sectors = int(params.get("march_sectors", 0))
     return c
 
 
@@ -202,6 +204,17 @@ class Sim:
         check(self.L.sg_sim_get_clearance(self.handle, out.ctypes.data, C.byref(nbytes), offs.ctypes.data),
               "sg_sim_get_clearance")
         return out, offs
+
+    def sector_skip(self):
+        """(bytes, per-map offsets, sectors) of the march's sector skip planes
+        (empty when the simulator uses the Chebyshev skip map alone)."""
+        nbytes = C.c_size_t(0)
+        check(self.L.sg_sim_get_sector_skip(self.handle, None, C.byref(nbytes), None), "sg_sim_get_sector_skip")
+        out = np.zeros(nbytes.value, np.uint8)
+        offs = np.zeros(self.n_maps, np.int64)
+        check(self.L.sg_sim_get_sector_skip(self.handle, out.ctypes.data, C.byref(nbytes), offs.ctypes.data),
+              "sg_sim_get_sector_skip")
+        return out, offs, int(self.info.march_sectors)
 
     def status(self):
         v = C.c_uint32(0)

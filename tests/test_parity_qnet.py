@@ -78,6 +78,35 @@ def test_forward_against_oracle(n_in, M, arch):
     assert err_64 <= 5e-2
 
 
+@pytest.mark.parametrize("M,stride", [(65536, 1), (1 << 20, 61)])
+def test_forward_multi_tile_against_oracle(M, stride):
+    """The batched tcgen05 forward at sizes where every persistent CTA runs
+    many 128-row tiles (65,536 rows: about 3 per CTA; 2^20 rows: about 54),
+    so that the streamed W2 halves, the next tile's input conversion during
+    layer 2 and the barrier phases across tiles are all exercised.  Rows are
+    compared element by element with the oracle's bf16 recipe: all of them at
+    65,536, every 61st at 2^20 (17,190 rows spread over every tile)."""
+    n_in = 37
+    rng = np.random.default_rng(M)
+    q = _qnet(n_in)
+    th = _theta(4, n_in, scale=2.0)
+    q.set_params(th)
+    obs = rng.uniform(-1, 1, size=(M, n_in)).astype(np.float32)
+    got = q.forward(torch.from_numpy(obs).cuda()).cpu().numpy().astype(np.float64)
+    rows = np.arange(0, M, stride)
+    p = OQ.unflatten(th.astype(np.float64), n_in)
+    ref_bf = OQ.forward(p, obs[rows], bf16=True)
+    scale = np.abs(ref_bf).max()
+    err = np.abs(got[rows] - ref_bf) / scale
+    print(f"M={M}: max relative Q error vs bf16 recipe {err.max():.2e} over {rows.size} rows")
+    assert np.isfinite(got).all()
+    assert err.max() <= Q_REL_TOL
+    # a tile's rows do not leak into another's: permuting the batch permutes the output
+    perm = rng.permutation(M)
+    got_p = q.forward(torch.from_numpy(obs[perm]).cuda()).cpu().numpy().astype(np.float64)
+    assert np.array_equal(got_p, got[perm])
+
+
 def _margin_ok(q_ref, act, tol):
     """Greedy action equals the argmax, or the argmax is within tol of it."""
     best = q_ref.max(axis=1)
@@ -270,27 +299,35 @@ def test_full_learned_workload_sampled_against_oracle():
     tiny = np.ones((1, 1), np.uint8)
     o = OracleSim(w.params, [maps[m] if m in keep else tiny for m in range(len(maps))], w.env_map, w.env_beams,
                   prec="f32")
-    n_explore = 0
+    p = OQ.unflatten(_theta(12, g.obs_dim, scale=2.0).astype(np.float64), g.obs_dim)
+    n_explore = n_greedy = 0
     for i in sample:
-        o.reset_env(i, 0)
+        ob = o.reset_env(i, 0)
         for k in range(K):
             a = int(act[k, i])
             if o.L.orc_explore_uniform(C.byref(o.cfg), i, k) < w.eps[i]:
                 assert a == o.random_action(i, k), (i, k)
                 n_explore += 1
-            _, orew, odone, _ = o.step_one(i, a)
+            else:
+                # greedy: the oracle's argmax of its bf16-recipe Q of the
+                # observation the step starts from, up to near ties
+                qref = OQ.forward(p, np.asarray(ob, np.float32)[None], bf16=True)
+                tol = Q_REL_TOL * np.abs(qref).max()
+                assert _margin_ok(qref, np.array([a]), 2 * tol)[0], (i, k, qref, a)
+                n_greedy += 1
+            ob, orew, odone, _ = o.step_one(i, a)
             assert odone == done[k, i] and bits(np.float32(orew)) == bits(rew[k, i]), (i, k)
         assert np.array_equal(bits(o.f[:, i]), bits(f[:, i])), i
         assert np.array_equal(o.u[:, i], u[:2, i]), i
-    assert n_explore > 10
+    assert n_explore > 10 and n_greedy > 300
 
 
-def _fill_replay(n_envs=64, steps=40, seed_theta=7, arch="dueling"):
+def _fill_replay(n_envs=64, steps=40, seed_theta=7, arch="dueling", max_batch=256):
     from paper_2305_04180_gb300 import Replay, Sim
 
     w = workload("qnet4096", n_envs=n_envs)
     g = Sim(w.params, w.maps(), w.env_map)
-    q = _qnet(g.obs_dim, arch=arch)
+    q = _qnet(g.obs_dim, arch=arch, max_batch=max_batch)
     q.set_params(_theta(seed_theta, g.obs_dim, scale=2.0, arch=arch))
     rp = Replay(32, g.n, g.obs_dim)
     g.reset()
@@ -339,6 +376,162 @@ def test_td_loss_and_gradient_against_oracle(batch, arch):
         nb = np.linalg.norm(rflat[sl])
         if nb > 0:
             assert np.linalg.norm(gg[sl] - rflat[sl]) / nb <= 6e-2, name
+
+
+# Element-wise bound of the TD gradient against the oracle's bf16 recipe:
+# |g - g_ref| <= TD_ATOL * max|g_ref over the parameter block| + TD_RTOL * |g_ref|.
+# The two sides round the same quantities to bf16 (weights, activations, the
+# backpropagated dZ), but their float32 and float64 sums differ, so a value
+# close to a bf16 rounding boundary can land one bf16 step (2^-8 relative)
+# apart and carry that into the products it feeds; TD_ATOL bounds such
+# contributions relative to the block's scale, TD_RTOL the float32 sums.
+TD_RTOL = 1e-2
+TD_ATOL = 2e-3
+
+
+def _td_case(batch, arch, n_envs=64, steps=40):
+    g, q, rp = _fill_replay(arch=arch, n_envs=n_envs, steps=steps, max_batch=batch)
+    th_on = _theta(8, g.obs_dim, scale=2.0, arch=arch)
+    th_tg = _theta(9, g.obs_dim, scale=2.0, arch=arch)
+    q.set_params(th_on, "online")
+    q.set_params(th_tg, "target")
+    return g, q, rp, th_on, th_tg
+
+
+def _gpu_loss_grad(q, rp, batch, seed):
+    loss = torch.zeros(1, device="cuda")
+    grad = torch.zeros(q.n_params, device="cuda")
+    q.train_step(rp, batch, gamma=0.98, lr=0.0, seed=seed, loss=loss, grad=grad)
+    torch.cuda.synchronize()
+    return float(loss.item()), grad.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("batch,arch,n_envs", [(256, "dueling", 64), (4096, "dueling", 256), (256, "paper", 64),
+                                               (4096, "paper", 256)])
+def test_td_gradient_elementwise_against_oracle(batch, arch, n_envs):
+    """Every entry of the TD gradient (77,062 parameters of the dueling
+    network, 41,989 of the paper's) against the oracle's bf16 recipe, at the
+    learner batches of the 4,096-env workload (256) and of the 65,536-env
+    learned loop (4,096)."""
+    g, q, rp, th_on, th_tg = _td_case(batch, arch, n_envs=n_envs)
+    seed = 77
+    gl, gg = _gpu_loss_grad(q, rp, batch, seed)
+    _, bt = _oracle_batch(rp, seed, 0, batch)
+    pon = OQ.unflatten(th_on.astype(np.float64), g.obs_dim, arch)
+    ptg = OQ.unflatten(th_tg.astype(np.float64), g.obs_dim, arch)
+    ref_loss, ref_g = OQ.td_loss_grad(pon, ptg, bt, 0.98, bf16=True)
+    rflat = OQ.flatten(ref_g)
+    assert np.isfinite(gg).all()
+    assert abs(gl - ref_loss) <= 1e-4 * max(1e-6, abs(ref_loss)), (gl, ref_loss)
+    worst = 0.0
+    for name, sl in _blocks(g.obs_dim, arch):
+        r = rflat[sl]
+        e = np.abs(gg[sl] - r)
+        bound = TD_ATOL * np.abs(r).max() + TD_RTOL * np.abs(r)
+        ratio = (e / np.maximum(bound, 1e-30)).max()
+        worst = max(worst, ratio)
+        print(f"batch {batch} {arch} {name}: max |g - g_ref| {e.max():.3e} (block max |g_ref| "
+              f"{np.abs(r).max():.3e}), max error / bound {ratio:.3f}")
+        assert np.all(e <= bound), (name, int(np.argmax(e / np.maximum(bound, 1e-30))))
+    print(f"batch {batch} {arch}: loss {gl:.6f} vs {ref_loss:.6f}; worst error / bound {worst:.3f}")
+
+
+def test_td_gradient_finite_differences_at_batch_4096():
+    """Central finite differences of the GPU's own loss at batch 4,096 (lr = 0
+    evaluations by the learner).  gamma = 0 makes the TD target y = r a
+    constant, as the semi-gradient assumes (with gamma > 0 the online
+    network's argmax inside the double-DQN target flips under a perturbation
+    and the loss is not differentiable there).  Every perturbation moves the
+    bf16 weight image exactly: weights go to bf16 values, and the difference
+    of the two parameter vectors that were actually used enters the
+    directional derivative g . (theta+ - theta-).
+
+    * Head (W3, b3: the loss is smooth in them): 16 single entries, the
+      largest gradients of each block, within 1e-2 relative.
+    * Hidden layers (W1, b1, W2, b2): the activations are rounded to bf16, so
+      the loss is a fine staircase in these parameters; a random direction
+      over the whole block, moving every entry by 5% of its size, gives a
+      secant that is checked in sign and size (within 35%; the oracle's bf16
+      recipe shows up to 15% on such secants)."""
+    batch = 4096
+    g, q, rp, th_on, th_tg = _td_case(batch, "dueling", n_envs=256)
+    seed = 91
+    rng = np.random.default_rng(4)
+
+    def loss_grad(th):
+        q.set_params(th, "online")
+        q.set_params(th_tg, "target")
+        loss = torch.zeros(1, device="cuda")
+        grad = torch.zeros(q.n_params, device="cuda")
+        q.train_step(rp, batch, gamma=0.0, lr=0.0, seed=seed, loss=loss, grad=grad)
+        torch.cuda.synchronize()
+        return float(loss.item()), grad.cpu().numpy().astype(np.float64)
+
+    _, gg = loss_grad(th_on)
+    blocks = dict(_blocks(g.obs_dim))
+
+    def moved(sl, delta, is_w):
+        th = th_on.copy()
+        v = (th_on[sl].astype(np.float64) + delta).astype(np.float32)
+        th[sl] = OQ.bf16_round(v) if is_w else v
+        return th
+
+    worst = {}
+    for name in ("W3", "b3"):
+        sl = blocks[name]
+        for j in np.argsort(np.abs(gg[sl]))[::-1][:8]:
+            k = sl.start + int(j)
+            # W3: 16 bf16 steps of the weight; b3 (float32 in the image): 5%.
+            # The float32 loss itself carries ~1e-7 relative rounding, so the
+            # step must move it by far more than that.
+            h = 16.0 * 2.0 ** (np.floor(np.log2(abs(float(th_on[k])))) - 7) if name == "W3" \
+                else 5e-2 * abs(float(th_on[k])) + 1e-3
+            kp = moved(slice(k, k + 1), h, name == "W3")
+            km = moved(slice(k, k + 1), -h, name == "W3")
+            lp, lm = loss_grad(kp)[0], loss_grad(km)[0]
+            an = gg[k] * (float(kp[k]) - float(km[k]))
+            rel = abs((lp - lm) - an) / abs(an)
+            worst[name] = max(worst.get(name, 0.0), rel)
+            assert rel <= 1e-2, (name, k, lp - lm, an)
+    for name in ("W1", "b1", "W2", "b2"):
+        sl = blocks[name]
+        for trial in range(3):
+            d = rng.choice([-1.0, 1.0], size=sl.stop - sl.start) * np.abs(th_on[sl]) * 5e-2
+            kp = moved(sl, d, name.startswith("W"))
+            km = moved(sl, -d, name.startswith("W"))
+            lp, lm = loss_grad(kp)[0], loss_grad(km)[0]
+            an = float(gg @ (kp.astype(np.float64) - km.astype(np.float64)))
+            rel = abs((lp - lm) - an) / abs(an)
+            worst[name] = max(worst.get(name, 0.0), rel)
+            assert rel <= 0.35, (name, trial, lp - lm, an)
+    print("finite differences, worst relative difference per block: "
+          + ", ".join(f"{k} {v:.2e}" for k, v in worst.items()))
+
+
+def test_td_step_with_invalid_action_changes_nothing():
+    """A sampled transition whose action is outside the action table (written
+    into the ring on purpose) makes the whole step fail: NaN loss and
+    gradient, parameters, Adam moments and the step count unchanged."""
+    g, q, rp, th_on, _ = _td_case(256, "dueling")
+    s, s2, a, r, t = rp.read(0, rp.capacity)
+    a = a.copy()
+    a[::7] = 9
+    rp.write(0, s, s2, a, r, t, rp.steps_recorded())
+    m0, v0, st0 = q.optimizer_state()
+    loss = torch.zeros(1, device="cuda")
+    grad = torch.zeros(q.n_params, device="cuda")
+    q.train_step(rp, 256, gamma=0.98, lr=1e-3, seed=3, loss=loss, grad=grad)
+    torch.cuda.synchronize()
+    assert np.isnan(loss.item()) and torch.isnan(grad).all()
+    assert np.array_equal(q.get_params("online"), th_on)
+    m1, v1, st1 = q.optimizer_state()
+    assert st1 == st0 and np.array_equal(m1, m0) and np.array_equal(v1, v0)
+    # valid actions again: the next step updates
+    a[::7] = 0
+    rp.write(0, s, s2, a, r, t, rp.steps_recorded())
+    q.train_step(rp, 256, gamma=0.98, lr=1e-3, seed=3, loss=loss)
+    torch.cuda.synchronize()
+    assert np.isfinite(loss.item()) and q.optimizer_state()[2] == st0 + 1
 
 
 def _blocks(n_in, arch="dueling"):

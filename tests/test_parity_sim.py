@@ -328,6 +328,75 @@ def test_against_float64_oracle_tolerances():
     assert diff / tot <= 1e-4, (diff, tot)
 
 
+@pytest.mark.parametrize("sectors", [4, 16, 32])
+def test_sector_skip_planes_are_safe(sectors):
+    """Every value of the march's sector skip planes is a safe skip, checked
+    by brute force independently of how the library builds them: from points
+    spread over a free cell (its corners pulled in by 1e-3 and interior
+    points), along directions spread over the sector widened by 5 mrad, the
+    march samples 1 .. J-1 cells ahead all fall in free cells of the map.
+    Also J is at least the Chebyshev skip of the cell (so the planes never
+    slow the march down), and occupied cells hold 0."""
+    maps = [random_tiny_map(11, 37, 29, 0.15), make_map(5, 96), random_tiny_map(12, 64, 16, 0.05)]
+    g = _sim(dict(base_params(), march_sectors=sectors), maps, np.arange(len(maps), dtype=np.int32))
+    planes, offs, S = g.sector_skip()
+    assert S == sectors
+    clr, coffs = g.clearance()
+    frac = np.array([1e-3, 0.27, 0.5, 0.81, 1 - 1e-3])
+    qx, qy = (a.ravel() for a in np.meshgrid(frac, frac))
+    rng = np.random.default_rng(sectors)
+    longer = 0
+    for m, grid in enumerate(maps):
+        h, w = grid.shape
+        cheb = clr[coffs[m]:coffs[m] + w * h].reshape(h, w).astype(np.int64)
+        for sct in range(S):
+            J = planes[offs[m] + sct * w * h:offs[m] + (sct + 1) * w * h].reshape(h, w).astype(np.int64)
+            assert np.all((J == 0) == (grid != 0)), (m, sct)
+            assert np.all(J >= cheb), (m, sct)
+            longer += int((J > cheb).sum())
+            a0 = -np.pi + sct * 2 * np.pi / S - 5e-3
+            a1 = -np.pi + (sct + 1) * 2 * np.pi / S + 5e-3
+            ang = np.concatenate([[a0, a1], rng.uniform(a0, a1, size=5)])
+            # the 150 largest skips of the plane and 250 random cells with J > 1
+            ys, xs = np.nonzero(J > 1)
+            if ys.size == 0:
+                continue
+            pick = np.unique(np.concatenate([np.argsort(J[ys, xs])[-150:],
+                                             rng.choice(ys.size, size=min(250, ys.size), replace=False)]))
+            cy, cx, jj = ys[pick], xs[pick], J[ys[pick], xs[pick]]
+            j = np.arange(1, int(jj.max()), dtype=np.float64)
+            px = (cx[:, None] + qx[None, :])[:, :, None, None] + j * np.cos(ang)[None, None, :, None]
+            py = (cy[:, None] + qy[None, :])[:, :, None, None] + j * np.sin(ang)[None, None, :, None]
+            ix, iy = np.floor(px).astype(np.int64), np.floor(py).astype(np.int64)
+            live = np.broadcast_to((j[None, :] < jj[:, None])[:, None, None, :], ix.shape)
+            inside = (ix >= 0) & (iy >= 0) & (ix < w) & (iy < h)
+            assert inside[live].all(), (m, sct)
+            free = np.zeros_like(live)
+            free[inside] = grid[iy[inside], ix[inside]] == 0
+            assert free[live].all(), (m, sct)
+    assert longer > 0
+
+
+def test_march_sectors_leave_results_unchanged():
+    """The acceleration structure does not change the step: rollouts with the
+    Chebyshev skip map alone and with 4, 16 or 32 sector planes are
+    bit-identical (every one is also checked against the oracle elsewhere)."""
+    w = workload("dr1024", n_envs=96)
+    maps = w.maps()
+    out = []
+    for sectors in (1, 4, 16, 32):
+        g = _sim(dict(w.params, march_sectors=sectors), maps, w.env_map, w.env_beams)
+        assert g.info.march_sectors == sectors
+        g.reset()
+        K = 64
+        obs_seq = torch.empty((K, g.n, g.obs_dim), device="cuda")
+        rew = torch.empty((K, g.n), device="cuda")
+        g.rollout(K, obs_seq=obs_seq, rew_seq=rew)
+        out.append((obs_seq.cpu().numpy(), rew.cpu().numpy()))
+    for o in out[1:]:
+        assert np.array_equal(bits(o[0]), bits(out[0][0])) and np.array_equal(bits(o[1]), bits(out[0][1]))
+
+
 def test_clearance_matches_chessboard_distance_transform():
     """The march's skip map is the skip value of scipy's chessboard distance
     transform of the free cells (outside of the map counted as occupied,
