@@ -274,10 +274,26 @@ def run_ours(a):
     e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps)
     h2d = int(f0.nbytes + u0.nbytes)
     d2h = int(rew_h.numel() * 4 + done_h.numel())
+    # the same with every output read back: the observations of every step too
+    obs_h = torch.empty(tuple(obs_seq.shape), dtype=torch.float32, pin_memory=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    full_steps = 2
+    for _ in range(full_steps):
+        sim.set_state(f0, u0)
+        one_step()
+        rew_h.copy_(rew_seq, non_blocking=True)
+        done_h.copy_(done_seq, non_blocking=True)
+        obs_h.copy_(obs_seq, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_full_s = max_over_ranks((time.perf_counter() - t0) / full_steps)
+    d2h_full = d2h + int(obs_h.numel() * 4)
+    del obs_h
+    l2_read = measure_l2_read() if rank == 0 else None
 
     extras = None
     if not a.no_extras and rank == 0:
-        extras = run_extras(flush, ExtrasSel(a.extras.split(","), a.qtc_slots))
+        extras = run_extras(flush, ExtrasSel(a.extras.split(","), a.qtc_slots), l2_read)
     out = None
     if rank == 0:
         out = {
@@ -308,7 +324,11 @@ def run_ours(a):
                 "parallelism": "replicas" if world > 1 else "single GPU",
             },
             "e2e": {"value": job_throughput(n * K, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
+                    "d2h_bytes_per_step": d2h,
+                    "outputs_read": "rewards and done flags of every step (the observations stay on the device)",
+                    "full": {"value": job_throughput(n * K, world, e2e_full_s), "unit": UNIT,
+                             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h_full,
+                             "outputs_read": "every output: observations, rewards and done flags of every step"}},
             "gpu_launches": a.steps,
             "clocks": clk,
             "wall_s": wall,
@@ -317,6 +337,7 @@ def run_ours(a):
         }
         if extras is not None:
             out["extras"] = extras
+        out["l2_read"] = l2_read
     return out, pool, (w, n, K, ms_per_step, clk)
 
 
@@ -348,7 +369,7 @@ class ExtrasSel(set):
         self.qtc_slots = int(qtc_slots)
 
 
-def run_extras(flush, which):
+def run_extras(flush, which, l2_read=None):
     """Secondary measurements on the same GPU: the fused Q-net rollout
     against the network-free rollout on the 4,096-env workload, the learner
     step, the Q-value accuracy, and the single-step kernel at 65,536 envs."""
@@ -466,7 +487,19 @@ def _run_extras_tail(out, flush, which):
     soa_bytes = 52 + 1 + 148 + 4 + 1 + 52
     out["sim_step"] = {"n_envs": sim2.n, "us_per_launch": ms_s * 1e3, "value": sim2.n / (ms_s / 1e3),
                        "unit": UNIT, "soa_bytes_per_env_step": soa_bytes,
-                       "soa_gbs": sim2.n * soa_bytes / (ms_s / 1e3) / 1e9}
+                       "soa_gbs": sim2.n * soa_bytes / (ms_s / 1e3) / 1e9,
+                       "march_sectors": int(sim2.info.march_sectors)}
+    out["sim_step"]["streaming_view"] = streaming_view(sim2.n / (ms_s / 1e3), 4 * sim2.obs_dim + 5, l2_read)
+    rec = _recorded(sim2.n, 1, "k_step", "step")
+    if rec:
+        # what one launch really moves through L2 and issues (ncu record)
+        sv = out["sim_step"]["streaming_view"]
+        sv["ncu_l2_bytes_per_launch"] = int(rec["lts_bytes"])
+        sv["ncu_l2_gbs"] = int(rec["lts_bytes"]) / (ms_s / 1e3) / 1e9
+        if sv.get("l2_peak_gbs"):
+            sv["ncu_l2_frac"] = sv["ncu_l2_gbs"] / sv["l2_peak_gbs"]
+        out["sim_step"]["warp_inst_per_env_step"] = int(rec["inst_executed"]) / sim2.n
+        out["sim_step"]["lane_efficiency"] = float(rec["thread_inst_ratio"]) / 32.0
     del sim2, obs2
     if "uneven" in which:
         out["uneven_batching"] = run_uneven(flush)
@@ -657,11 +690,12 @@ def run_full_loop(flush):
 CPU_SAMPLE_STEPS = 16000
 
 
-def _recorded_traffic(n_envs, K, kernel, launch):
-    """DRAM bytes per launch of the timed kernel from the committed ncu
-    records (one line per kernel, workload and launch configuration), if one
-    was taken on this kernel, workload and launch and the kernel sources are
-    unchanged since (else None)."""
+def _recorded(n_envs, K, kernel, launch):
+    """The committed ncu record of the timed kernel (one line per kernel,
+    workload and launch configuration: DRAM and L2 bytes, warp instructions,
+    lane efficiency, duration of one launch), if one was taken on this
+    kernel, workload and launch and the kernel sources are unchanged since
+    (else None)."""
     import hashlib
 
     try:
@@ -675,7 +709,7 @@ def _recorded_traffic(n_envs, K, kernel, launch):
             rec = dict(tok.split("=", 1) for tok in line.split(" ") if "=" in tok)
             if (rec.get("source_sha1") == sha and rec.get("kernel") == kernel and rec.get("launch") == launch
                     and int(rec["n_envs"]) == n_envs and int(rec["steps_per_launch"]) == K):
-                return int(rec["dram_bytes_read"]) + int(rec["dram_bytes_write"])
+                return rec
         return None
     except Exception:
         return None
@@ -688,6 +722,65 @@ def _measured_peaks():
         return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]), "source": "measured"}
     except Exception:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+
+
+def measure_l2_read():
+    """L2 read bandwidth (GB/s): the library's read probe (16-byte loads cached
+    in L2 only, every SM) over buffers of 24 to 64 MiB, each read 20 times per
+    launch after a warm-up launch; CUDA events; the best size is the peak."""
+    import ctypes as C
+
+    import torch
+
+    from paper_2305_04180_gb300 import _lib
+
+    L = _lib.load()
+    buf = torch.randint(0, 2 ** 31 - 1, (64 << 18,), dtype=torch.int32, device="cuda")  # 64 MiB
+    sink = torch.zeros(4096, dtype=torch.int32, device="cuda")
+    st = torch.cuda.current_stream()
+    reps = 20
+    table = {}
+    for mib in (24, 32, 48, 64):
+        nbytes = mib << 20
+        args = (C.c_void_p(buf.data_ptr()), C.c_size_t(nbytes), reps, C.c_void_p(sink.data_ptr()), 4096,
+                C.c_void_p(st.cuda_stream))
+        _lib.check(L.sg_probe_read(*args), "sg_probe_read")
+        best = None
+        for _ in range(5):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            _lib.check(L.sg_probe_read(*args), "sg_probe_read")
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        table[f"{mib}MiB"] = nbytes * reps / (best / 1e3) / 1e9
+    del buf, sink
+    return {"peak_gbs": max(table.values()), "by_size_gbs": table,
+            "how": "sg_probe_read: 16-byte ld.global.cg loads over an L2-resident buffer by every SM, "
+                   "20 passes per launch, best of 5 launches per size"}
+
+
+# Algorithmic bytes of one env-step in the streaming view: the 201 x 201-cell
+# square around the 100-cell scan disc as bits (the map window the LiDAR can
+# touch) plus the SoA state, parameters and outputs.
+WINDOW_BYTES = 201 * 201 / 8.0
+SOA_BYTES = 65 + 185
+
+
+def streaming_view(env_steps_s, out_bytes, l2_read):
+    """The streaming view of a simulator kernel: algorithmic bytes per
+    env-step x env-steps/s against the measured HBM copy peak and the
+    measured L2 read peak."""
+    peaks = _measured_peaks()
+    per = WINDOW_BYTES + SOA_BYTES
+    gbs = env_steps_s * per / 1e9
+    l2 = (l2_read or {}).get("peak_gbs")
+    return {"algorithmic_bytes_per_env_step": round(per), "achieved_gbs": gbs,
+            "hbm_peak_gbs": peaks.get("hbm_gbs"), "hbm_frac": gbs / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
+            "l2_peak_gbs": l2, "l2_frac": gbs / l2 if l2 else None,
+            "output_bytes_per_env_step": out_bytes, "peak_source": peaks.get("source")}
 
 
 def roofline_alu(samples_per_env_step, n, K, ms_per_step, clk):
@@ -736,21 +829,35 @@ def main():
     kname = {"grid": "k_rollout_random"}.get(out["config"]["launch"]["kernel"],
                                               "k_rollout_random_" + out["config"]["launch"]["kernel"])
     out["roofline"]["kernel"] = kname
-    out["roofline"]["traffic"] = _recorded_traffic(n, K, kname, launch_label(out["config"]["launch"]))
+    rec = _recorded(n, K, kname, launch_label(out["config"]["launch"]))
+    out["roofline"]["traffic"] = (int(rec["dram_bytes_read"]) + int(rec["dram_bytes_write"])) if rec else None
     out["roofline"]["traffic_unit"] = "DRAM bytes per launch (ncu record in profiles/)"
-    # the streaming view: bytes a step must see if the map window and the SoA
-    # state were streamed from HBM every step (the rollout keeps them on chip)
-    peaks = _measured_peaks()
     env_steps_s = out["value"] / max(1, out["n_gpus"])
-    win = 201 * 201 / 8.0  # bits of the square around the 100-cell scan disc
-    soa = 65 + 185
+    mhz = (clk or {}).get("sm_mhz") or 2070.0
+    if rec and rec.get("inst_executed"):
+        # the hardware's view of the same launch: warp instructions issued per
+        # second against the issue rate of 152 SMs x 4 schedulers
+        ipe = int(rec["inst_executed"]) / (n * K)
+        peak_i = 152 * 4 * mhz * 1e6 / 1e9
+        out["roofline"]["issue"] = {"warp_inst_per_env_step": ipe, "achieved": ipe * env_steps_s / 1e9,
+                                    "peak": peak_i, "unit": "Gwarp-inst/s",
+                                    "frac": ipe * env_steps_s / 1e9 / peak_i,
+                                    "lane_efficiency": float(rec["thread_inst_ratio"]) / 32.0,
+                                    "basis": f"152 SM x 4 schedulers x {mhz:.0f} MHz; instruction count from the "
+                                             "ncu record in profiles/"}
+    # the streaming view: bytes a step must see if the map window and the SoA
+    # state were streamed every step (the rollout keeps them on chip)
     outb = 4 * (int(out["config"].get("obs_dim", 37))) + 4 + 1
-    out["l2_hbm"] = {"algorithmic_bytes_per_env_step": round(win + soa),
-                     "basis": "201x201-cell map window of the 100-cell scan + SoA state/params/outputs",
-                     "achieved_gbs": env_steps_s * (win + soa) / 1e9, "peak_gbs": peaks.get("hbm_gbs"),
-                     "frac": env_steps_s * (win + soa) / 1e9 / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
-                     "output_bytes_per_env_step": outb, "output_gbs": env_steps_s * outb / 1e9,
-                     "peak_source": peaks.get("source")}
+    out["l2_hbm"] = streaming_view(env_steps_s, outb, out.get("l2_read"))
+    out["l2_hbm"]["basis"] = "201x201-cell map window of the 100-cell scan + SoA state/params/outputs"
+    out["l2_hbm"]["output_gbs"] = env_steps_s * outb / 1e9
+    if rec and rec.get("lts_bytes"):
+        # the L2 traffic the launch really moves (ncu lts__t_bytes), per second
+        lts = int(rec["lts_bytes"])
+        out["l2_hbm"]["ncu_l2_bytes_per_launch"] = lts
+        out["l2_hbm"]["ncu_l2_gbs"] = lts / (ms_per_step / 1e3) / 1e9
+        if out["l2_hbm"].get("l2_peak_gbs"):
+            out["l2_hbm"]["ncu_l2_frac"] = out["l2_hbm"]["ncu_l2_gbs"] / out["l2_hbm"]["l2_peak_gbs"]
     print(json.dumps(out))
 
 

@@ -519,6 +519,25 @@ int sg_td_grad_noalloc(const float* params_dev, const float* target_params_dev, 
                        int32_t batch, float gamma, float* loss_dev, float* grad_dev, sg_stream_t stream);
 
 /* ---------------------------------------------------------------------- */
+/* Measurement                                                             */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * Read-bandwidth probe (not part of the paper's method: the measured
+ * denominator of the L2 roofline reported for the simulator kernels).
+ * `reps` passes of 16-byte loads cached in L2 only (ld.global.cg) over
+ * buf_dev[0, bytes), by a grid of every 512-thread CTA that fits the GPU at
+ * once (4 per SM); a buffer smaller than L2 is read from L2 after the first
+ * pass, so bytes x reps / time is the L2 read bandwidth.  Each CTA XORs
+ * what it read into sink_dev[its index] (so the loads cannot be dropped);
+ * sink_words must be >= the grid (4 x the SM count suffices).
+ * bytes: a multiple of 16, >= 16; buf_dev 16-byte aligned; reps >= 1; else
+ * SG_E_INVAL.  Caller-owned device memory.  Asynchronous on stream.
+ */
+int sg_probe_read(const void* buf_dev, size_t bytes, int32_t reps, uint32_t* sink_dev, int32_t sink_words,
+                  sg_stream_t stream);
+
+/* ---------------------------------------------------------------------- */
 /* CUDA graphs of rollouts and learner steps                                */
 /* ---------------------------------------------------------------------- */
 

@@ -101,6 +101,7 @@ SIGNATURES = {
     "sg_td_train_step": (C.c_int, [_vp, _vp, _i32, C.c_float, C.c_float, _i32, C.c_uint64, _vp, _vp, _vp]),
     "sg_vem_eps": (C.c_int, [_vp, C.c_float, C.c_float, C.c_double, C.c_double, C.c_double, _vp, _vp]),
     "sg_td_grad_noalloc": (C.c_int, [_vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _i32, C.c_float, _vp, _vp, _vp]),
+    "sg_probe_read": (C.c_int, [_vp, C.c_size_t, _i32, _vp, _i32, _vp]),
     "sg_graph_begin": (C.c_int, [_vp]),
     "sg_graph_end": (C.c_int, [_vp, _vp]),
     "sg_graph_launch": (C.c_int, [_vp, _vp]),

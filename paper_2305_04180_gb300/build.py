@@ -30,6 +30,7 @@ UNITS = {
     "sg_sim.cu": ["-fmad=false"],
     "sg_qnet.cu": ["-fmad=false"],
     "sg_graph.cu": [],
+    "sg_probe.cu": [],
 }
 
 

@@ -1,6 +1,6 @@
-"""Host logic of the benchmark (no GPU): the DRAM-traffic records are used
-only for the kernel source they were taken on, launch labels, the ALU
-roofline arithmetic and the extras selection."""
+"""Host logic of the benchmark (no GPU): the ncu records are used only for
+the kernel source they were taken on, launch labels, the ALU roofline and
+streaming-view arithmetic and the extras selection."""
 
 import hashlib
 import os
@@ -34,10 +34,11 @@ def test_traffic_records_are_used_only_on_their_kernel_source():
     assert recs
     sha = _source_sha()
     for r in recs:
-        got = bench._recorded_traffic(int(r["n_envs"]), int(r["steps_per_launch"]), r["kernel"], r["launch"])
+        got = bench._recorded(int(r["n_envs"]), int(r["steps_per_launch"]), r["kernel"], r["launch"])
         if r["source_sha1"] == sha:
-            assert got == int(r["dram_bytes_read"]) + int(r["dram_bytes_write"])
-            assert got >= 153 * int(r["n_envs"]) * int(r["steps_per_launch"])
+            assert got == r
+            traffic = int(r["dram_bytes_read"]) + int(r["dram_bytes_write"])
+            assert traffic >= 153 * int(r["n_envs"]) * int(r["steps_per_launch"])
         else:
             assert got is None
 
@@ -45,10 +46,10 @@ def test_traffic_records_are_used_only_on_their_kernel_source():
 def test_traffic_lookup_refuses_other_workloads_and_launches():
     r = _records()[0]
     n, K = int(r["n_envs"]), int(r["steps_per_launch"])
-    assert bench._recorded_traffic(n + 1, K, r["kernel"], r["launch"]) is None
-    assert bench._recorded_traffic(n, K + 1, r["kernel"], r["launch"]) is None
-    assert bench._recorded_traffic(n, K, "k_other", r["launch"]) is None
-    assert bench._recorded_traffic(n, K, r["kernel"], "pipe:1w:7obs:map") is None
+    assert bench._recorded(n + 1, K, r["kernel"], r["launch"]) is None
+    assert bench._recorded(n, K + 1, r["kernel"], r["launch"]) is None
+    assert bench._recorded(n, K, "k_other", r["launch"]) is None
+    assert bench._recorded(n, K, r["kernel"], "pipe:1w:7obs:map") is None
 
 
 def test_launch_labels():
@@ -72,6 +73,19 @@ def test_alu_roofline_arithmetic():
     # without the sample count (CPU leg skipped) there is no achieved value
     r = bench.roofline_alu(None, 1024, 10000, 10.0, None)
     assert r["achieved"] is None and r["frac"] is None and r["peak"] > 0
+
+
+def test_streaming_view_arithmetic():
+    """5,300 B per env-step (201^2/8 window bits + 250 B of SoA) at 1 G
+    env-steps/s is 5,300 GB/s, against the measured HBM peak and the given
+    L2 read peak."""
+    v = bench.streaming_view(1e9, 153, {"peak_gbs": 20000.0})
+    per = 201 * 201 / 8.0 + 250
+    assert v["algorithmic_bytes_per_env_step"] == round(per)
+    assert abs(v["achieved_gbs"] - per) < 1e-9
+    assert abs(v["l2_frac"] - per / 20000.0) < 1e-12
+    assert v["hbm_peak_gbs"] > 0 and abs(v["hbm_frac"] - per / v["hbm_peak_gbs"]) < 1e-12
+    assert bench.streaming_view(1e9, 153, None)["l2_frac"] is None
 
 
 def test_extras_selection_carries_the_ring_size():
