@@ -376,6 +376,7 @@ def run_extras(flush, which, l2_read=None):
     import numpy as np
     import torch
 
+    which.l2_read = l2_read
     from paper_2305_04180_gb300 import QNet, Replay, Sim
     from workloads import workload
 
@@ -489,7 +490,8 @@ def _run_extras_tail(out, flush, which):
                        "unit": UNIT, "soa_bytes_per_env_step": soa_bytes,
                        "soa_gbs": sim2.n * soa_bytes / (ms_s / 1e3) / 1e9,
                        "march_sectors": int(sim2.info.march_sectors)}
-    out["sim_step"]["streaming_view"] = streaming_view(sim2.n / (ms_s / 1e3), 4 * sim2.obs_dim + 5, l2_read)
+    out["sim_step"]["streaming_view"] = streaming_view(sim2.n / (ms_s / 1e3), 4 * sim2.obs_dim + 5,
+                                                       getattr(which, "l2_read", None))
     rec = _recorded(sim2.n, 1, "k_step", "step")
     if rec:
         # what one launch really moves through L2 and issues (ncu record)

@@ -117,9 +117,9 @@ typedef struct sg_sim_config {
    * samples a ray of that direction sector can skip from a cell (about 2x
    * fewer march iterations at 16 on the benchmark maps); they cost
    * march_sectors bytes per map cell and are built at creation.  0: 16 when
-   * the planes take at most 16 GiB and a quarter of the free device memory,
-   * else 8 or 4 under the same limit, else 1.  Ignored (1) when
-   * march_step > 1, where the march tests every sample.
+   * the 16 planes of all maps fit in the GPU's L2 cache (126 MB on GB300:
+   * 32 maps of 366 x 366 do), else 1.  Ignored (1) when march_step > 1,
+   * where the march tests every sample.
    */
   int32_t march_sectors;
 } sg_sim_config;

@@ -1211,15 +1211,13 @@ extern "C" int sg_sim_create(const sg_sim_config* cfg, int32_t n_maps, const uin
   // sector skip planes: n_sec planes of the skip-map layout per map
   int n_sec = dc.skip_ok ? cfg->march_sectors : 1;
   if (n_sec == 0) {
-    size_t free_b = 0, total_b = 0;
-    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
-    const double limit = std::min(16.0 * (double)(1ull << 30), 0.25 * (double)free_b);
-    n_sec = 1;
-    for (int cand : {16, 8, 4})
-      if ((double)cand * (double)clr_bytes <= limit) {
-        n_sec = cand;
-        break;
-      }
+    // 16 sectors while the planes fit in L2 (there they halve the march's
+    // iterations; streamed from DRAM they cost more than they save), else
+    // the Chebyshev skip map alone
+    int dev = 0, l2 = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess)
+      l2 = 0;
+    n_sec = 16.0 * (double)clr_bytes <= (double)l2 ? 16 : 1;
   }
   dc.n_sec = n_sec;
   dc.sec_scale = (float)((double)n_sec / (2.0 * M_PI));
