@@ -496,11 +496,11 @@ def _run_extras_tail(out, flush, which):
     if rec:
         # what one launch really moves through L2 and issues (ncu record)
         sv = out["sim_step"]["streaming_view"]
-        sv["ncu_l2_bytes_per_launch"] = int(rec["lts_bytes"])
-        sv["ncu_l2_gbs"] = int(rec["lts_bytes"]) / (ms_s / 1e3) / 1e9
+        sv["ncu_l2_bytes_per_launch"] = rec["lts_bytes_launch"]
+        sv["ncu_l2_gbs"] = rec["lts_bytes_launch"] / (ms_s / 1e3) / 1e9
         if sv.get("l2_peak_gbs"):
             sv["ncu_l2_frac"] = sv["ncu_l2_gbs"] / sv["l2_peak_gbs"]
-        out["sim_step"]["warp_inst_per_env_step"] = int(rec["inst_executed"]) / sim2.n
+        out["sim_step"]["warp_inst_per_env_step"] = rec["inst_executed_launch"] / sim2.n
         out["sim_step"]["lane_efficiency"] = float(rec["thread_inst_ratio"]) / 32.0
     del sim2, obs2
     if "uneven" in which:
@@ -695,9 +695,11 @@ CPU_SAMPLE_STEPS = 16000
 def _recorded(n_envs, K, kernel, launch):
     """The committed ncu record of the timed kernel (one line per kernel,
     workload and launch configuration: DRAM and L2 bytes, warp instructions,
-    lane efficiency, duration of one launch), if one was taken on this
-    kernel, workload and launch and the kernel sources are unchanged since
-    (else None)."""
+    lane efficiency), if one was taken on this kernel, workload (env count)
+    and launch and the kernel sources are unchanged since (else None).  A
+    record of a launch of another length is scaled to K steps by env-steps
+    (its byte and instruction counts grow in proportion); the returned dict
+    holds per-launch values for K steps and the record's own fields."""
     import hashlib
 
     try:
@@ -710,8 +712,15 @@ def _recorded(n_envs, K, kernel, launch):
                 continue
             rec = dict(tok.split("=", 1) for tok in line.split(" ") if "=" in tok)
             if (rec.get("source_sha1") == sha and rec.get("kernel") == kernel and rec.get("launch") == launch
-                    and int(rec["n_envs"]) == n_envs and int(rec["steps_per_launch"]) == K):
-                return rec
+                    and int(rec["n_envs"]) == n_envs):
+                f = K / int(rec["steps_per_launch"])
+                out = dict(rec)
+                out["scale"] = f
+                out["dram_bytes"] = round(f * (int(rec["dram_bytes_read"]) + int(rec["dram_bytes_write"])))
+                for k in ("lts_bytes", "inst_executed"):
+                    if k in rec:
+                        out[k + "_launch"] = round(f * int(rec[k]))
+                return out
         return None
     except Exception:
         return None
@@ -728,8 +737,9 @@ def _measured_peaks():
 
 def measure_l2_read():
     """L2 read bandwidth (GB/s): the library's read probe (16-byte loads cached
-    in L2 only, every SM) over buffers of 24 to 64 MiB, each read 20 times per
-    launch after a warm-up launch; CUDA events; the best size is the peak."""
+    in L2 only, every SM) over buffers of 24 to 64 MiB, each read 100 times
+    per launch after three warm-up launches; CUDA events; the best size is
+    the peak."""
     import ctypes as C
 
     import torch
@@ -740,13 +750,14 @@ def measure_l2_read():
     buf = torch.randint(0, 2 ** 31 - 1, (64 << 18,), dtype=torch.int32, device="cuda")  # 64 MiB
     sink = torch.zeros(4096, dtype=torch.int32, device="cuda")
     st = torch.cuda.current_stream()
-    reps = 20
+    reps = 100
     table = {}
     for mib in (24, 32, 48, 64):
         nbytes = mib << 20
         args = (C.c_void_p(buf.data_ptr()), C.c_size_t(nbytes), reps, C.c_void_p(sink.data_ptr()), 4096,
                 C.c_void_p(st.cuda_stream))
-        _lib.check(L.sg_probe_read(*args), "sg_probe_read")
+        for _ in range(3):
+            _lib.check(L.sg_probe_read(*args), "sg_probe_read")
         best = None
         for _ in range(5):
             e0 = torch.cuda.Event(enable_timing=True)
@@ -761,7 +772,7 @@ def measure_l2_read():
     del buf, sink
     return {"peak_gbs": max(table.values()), "by_size_gbs": table,
             "how": "sg_probe_read: 16-byte ld.global.cg loads over an L2-resident buffer by every SM, "
-                   "20 passes per launch, best of 5 launches per size"}
+                   "100 passes per launch, 3 warm-up launches, best of 5 launches per size"}
 
 
 # Algorithmic bytes of one env-step in the streaming view: the 201 x 201-cell
@@ -832,14 +843,17 @@ def main():
                                               "k_rollout_random_" + out["config"]["launch"]["kernel"])
     out["roofline"]["kernel"] = kname
     rec = _recorded(n, K, kname, launch_label(out["config"]["launch"]))
-    out["roofline"]["traffic"] = (int(rec["dram_bytes_read"]) + int(rec["dram_bytes_write"])) if rec else None
+    out["roofline"]["traffic"] = rec["dram_bytes"] if rec else None
     out["roofline"]["traffic_unit"] = "DRAM bytes per launch (ncu record in profiles/)"
+    if rec and rec["scale"] != 1.0:
+        out["roofline"]["traffic_note"] = (f"ncu record of a {rec['steps_per_launch']}-step launch scaled to "
+                                           f"{K} steps by env-steps")
     env_steps_s = out["value"] / max(1, out["n_gpus"])
     mhz = (clk or {}).get("sm_mhz") or 2070.0
     if rec and rec.get("inst_executed"):
         # the hardware's view of the same launch: warp instructions issued per
         # second against the issue rate of 152 SMs x 4 schedulers
-        ipe = int(rec["inst_executed"]) / (n * K)
+        ipe = rec["inst_executed_launch"] / (n * K)
         peak_i = 152 * 4 * mhz * 1e6 / 1e9
         out["roofline"]["issue"] = {"warp_inst_per_env_step": ipe, "achieved": ipe * env_steps_s / 1e9,
                                     "peak": peak_i, "unit": "Gwarp-inst/s",
@@ -855,7 +869,7 @@ def main():
     out["l2_hbm"]["output_gbs"] = env_steps_s * outb / 1e9
     if rec and rec.get("lts_bytes"):
         # the L2 traffic the launch really moves (ncu lts__t_bytes), per second
-        lts = int(rec["lts_bytes"])
+        lts = rec["lts_bytes_launch"]
         out["l2_hbm"]["ncu_l2_bytes_per_launch"] = lts
         out["l2_hbm"]["ncu_l2_gbs"] = lts / (ms_per_step / 1e3) / 1e9
         if out["l2_hbm"].get("l2_peak_gbs"):
