@@ -55,6 +55,8 @@ enum {
 /* Device status bits (sg_sim_status). */
 #define SG_DEV_BAD_ACTION 0x1u /* an action index >= n_actions was stepped */
 #define SG_DEV_TIMEOUT 0x2u    /* a bounded spin-wait gave up */
+#define SG_DEV_BOUNDS 0x4u     /* debug builds only: a computed map or ring index fell outside its
+                                  array; the access was skipped (see sg_sim_status) */
 
 /* Rollout action sources (sg_sim_rollout). */
 #define SG_POLICY_RANDOM 0 /* uniform over the action table, counter RNG */
@@ -330,7 +332,13 @@ int sg_sim_get_sector_skip(sg_sim_t sim, uint8_t* host, size_t* bytes, int64_t* 
 
 /*
  * Read (synchronously) and clear the device status word: SG_DEV_* bits.
- * Returns SG_E_DEVICE if any bit was set, SG_OK otherwise.
+ * Returns SG_E_DEVICE if any bit was set, SG_OK otherwise.  In the debug
+ * build (libsparrowgb_debug.so, compiled with SG_DEBUG_BOUNDS) every skip-map
+ * load of the ray march, every bit-row load of the collision test and every
+ * ring entry the learner samples is checked against its array first; an
+ * index outside it skips the access (the march then reports a hit there) and
+ * sets SG_DEV_BOUNDS, which this call also reports and clears (for every
+ * simulator and network of the process).  The regular build has no checks.
  */
 int sg_sim_status(sg_sim_t sim, uint32_t* device_status);
 

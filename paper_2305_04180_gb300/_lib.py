@@ -21,6 +21,7 @@ SG_E_DEVICE = -5
 SG_E_TIMEOUT = -6
 SG_DEV_BAD_ACTION = 0x1
 SG_DEV_TIMEOUT = 0x2
+SG_DEV_BOUNDS = 0x4
 SG_QNET_ARCHS = {"dueling": 0, "paper": 1}
 SG_POLICY_RANDOM = 0
 SG_POLICY_EPS_Q = 1
@@ -115,17 +116,23 @@ _LIB = None
 
 
 def load(build_if_missing: bool = True):
-    """Load the library (building it first if it is absent or stale)."""
+    """Load the library (building it first if it is absent or stale).  The
+    environment variable SG_LIB_VARIANT=debug selects the debug build
+    (bounds checks that report SG_DEV_BOUNDS, see sg_sim_status) for the
+    whole process."""
     global _LIB
     if _LIB is not None:
         return _LIB
     import torch  # noqa: F401  -- loads the CUDA runtime the library links against
 
-    path = _build.LIB
-    if build_if_missing and not _build.up_to_date():
-        _build.build()
+    variant = os.environ.get("SG_LIB_VARIANT", "")
+    if variant not in _build.VARIANTS:
+        raise ImportError(f"SG_LIB_VARIANT={variant!r}: expected one of {sorted(_build.VARIANTS)}")
+    path = _build.VARIANTS[variant][0]
+    if build_if_missing and not _build.up_to_date(variant):
+        _build.build(variant=variant)
     if not os.path.exists(path):
-        raise ImportError(f"libsparrowgb.so is not built ({path}); run paper_2305_04180_gb300.build.build()")
+        raise ImportError(f"{os.path.basename(path)} is not built ({path}); run paper_2305_04180_gb300.build.build()")
     L = C.CDLL(path)
     for name, (res, args) in SIGNATURES.items():
         fn = getattr(L, name)

@@ -21,6 +21,10 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libsparrowgb.so")
+# the debug variant: explicit bounds checks that latch SG_DEV_BOUNDS instead
+# of reading outside an array (see sg_sim_status in the header)
+DEBUG_LIB = os.path.join(BUILD, "debug", "libsparrowgb_debug.so")
+VARIANTS = {"": (LIB, []), "debug": (DEBUG_LIB, ["-DSG_DEBUG_BOUNDS"])}
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
@@ -52,24 +56,27 @@ def _deps():
     return out
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(variant: str = "") -> bool:
+    lib = VARIANTS[variant][0]
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra=None) -> str:
-    """Compile and link the library; returns its path."""
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra=None, variant: str = "") -> str:
+    """Compile and link the library (variant "" or "debug"); returns its path."""
+    lib, vflags = VARIANTS[variant]
+    if not force and up_to_date(variant):
+        return lib
+    out_dir = os.path.dirname(lib)
+    os.makedirs(out_dir, exist_ok=True)
     nvcc = _nvcc()
-    extra = list(extra or [])
+    extra = list(vflags) + list(extra or [])
 
     def compile_one(name):
         src = os.path.join(CSRC, name)
-        obj = os.path.join(BUILD, name.replace(".cu", ".o"))
+        obj = os.path.join(out_dir, name.replace(".cu", ".o"))
         cmd = [nvcc, *ARCH, *COMMON, *UNITS[name], *extra, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -80,16 +87,17 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
         objs = list(ex.map(compile_one, UNITS))
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib + f".{os.getpid()}.tmp"
     cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", *objs, "-o", tmp]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     import sys
     print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
-                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else None))
+                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else None,
+                variant="debug" if "--debug" in sys.argv else ""))

@@ -18,6 +18,20 @@
 namespace sg {
 
 constexpr unsigned kFull = 0xffffffffu;
+
+// Debug build (SG_DEBUG_BOUNDS): SG_IN_BOUNDS(cond) is cond, and a false
+// cond latches a per-translation-unit device flag that sg_sim_status reports
+// as SG_DEV_BOUNDS; the caller then skips the access.  Regular build: true.
+#ifdef SG_DEBUG_BOUNDS
+static __device__ unsigned g_debug_bounds;
+__device__ __forceinline__ bool sg_in_bounds(bool ok) {
+  if (!ok) atomicOr(&g_debug_bounds, 1u);
+  return ok;
+}
+#define SG_IN_BOUNDS(cond) sg_in_bounds(cond)
+#else
+#define SG_IN_BOUNDS(cond) true
+#endif
 constexpr uint32_t kStreamReset = 1;
 constexpr uint32_t kStreamNoise = 2;
 constexpr uint32_t kStreamAction = 3;
@@ -309,6 +323,10 @@ __device__ __forceinline__ int march(const uint8_t* __restrict__ clr, int W, int
       const float t = kUnitStep ? kf : kf * delta;
       const uint32_t bx = __float_as_uint(__fadd_rd(fmaf(t, ux, x), kMagic));
       const uint32_t by = __float_as_uint(__fadd_rd(fmaf(t, uy, y), kMagic));
+      // the sample cell (ix, iy) = (bx, by) - pattern(1.5 * 2^23), inside the border
+      if (!SG_IN_BOUNDS((int)(bx - kMagicBits) >= -kClrBorder && (int)(by - kMagicBits) >= -kClrBorder &&
+                        (int)(bx - kMagicBits) < W + kClrBorder && (int)(by - kMagicBits) < H + kClrBorder))
+        return k;
       const int s = __ldg(clr + (int)(by * (uint32_t)ld + bx + bias));
       if (s == 0) return k;
       k += s;
@@ -348,6 +366,7 @@ __device__ __forceinline__ bool collide_rows_warp(const DevCfg& c, const MapDesc
     for (int wd = cx0 >> 5; wd <= (cx1 >> 5); ++wd) {
       const int lo = max(cx0 - wd * 32, 0), hi = min(cx1 - wd * 32, 31);
       const uint32_t mask = (0xFFFFFFFFu >> (31 - hi)) & (0xFFFFFFFFu << lo);
+      if (!SG_IN_BOUNDS(cy >= 0 && cy < m.h && wd >= 0 && wd < m.row_words)) continue;
       uint32_t bits = __ldg(row + wd) & mask;
       while (bits) {
         const int b = __ffs(bits) - 1;

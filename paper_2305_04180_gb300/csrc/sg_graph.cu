@@ -25,12 +25,14 @@ struct sg_graph {
   } while (0)
 
 extern "C" int sg_graph_begin(sg_stream_t stream) {
+  SG_RANGE("sg_graph_begin");
   if (!stream) return SG_E_INVAL;  // the legacy default stream cannot be captured
   SG_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
   return SG_OK;
 }
 
 extern "C" int sg_graph_end(sg_stream_t stream, sg_graph_t* out) {
+  SG_RANGE("sg_graph_end");
   if (!stream || !out) return SG_E_INVAL;
   *out = nullptr;
   cudaGraph_t g = nullptr;
@@ -54,18 +56,21 @@ extern "C" int sg_graph_end(sg_stream_t stream, sg_graph_t* out) {
 }
 
 extern "C" int sg_graph_launch(sg_graph_t g, sg_stream_t stream) {
+  SG_RANGE("sg_graph_launch");
   if (!g) return SG_E_INVAL;
   SG_CUDA(cudaGraphLaunch(g->exec, stream));
   return SG_OK;
 }
 
 extern "C" int sg_graph_num_nodes(sg_graph_t g, int64_t* n) {
+  SG_RANGE("sg_graph_num_nodes");
   if (!g || !n) return SG_E_INVAL;
   *n = (int64_t)g->nodes;
   return SG_OK;
 }
 
 extern "C" int sg_graph_destroy(sg_graph_t g) {
+  SG_RANGE("sg_graph_destroy");
   if (!g) return SG_E_INVAL;
   cudaGraphExecDestroy(g->exec);
   cudaGraphDestroy(g->graph);

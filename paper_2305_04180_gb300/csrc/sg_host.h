@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <vector>
 
@@ -37,6 +38,16 @@ struct sg_sim {
   size_t pipe_sync_words = 0;
   unsigned* q_sync_dev = nullptr;  // time-sliced fused Q rollout: per-block segment flags, item counter, abort word
 };
+
+// An NVTX range over the body of a C entry point (named after it), so that
+// a timeline tool shows each library call; free when no tool is attached.
+struct SgRange {
+  explicit SgRange(const char* name) { nvtxRangePushA(name); }
+  ~SgRange() { nvtxRangePop(); }
+  SgRange(const SgRange&) = delete;
+  SgRange& operator=(const SgRange&) = delete;
+};
+#define SG_RANGE(name) SgRange sg_range_(name)
 
 sg::SimPtrs sg_sim_ptrs(sg_sim* s);
 long long sg_state_bytes(const sg_sim* s);

@@ -39,6 +39,7 @@ __global__ void __launch_bounds__(512) k_probe_read(const uint4* __restrict__ bu
 
 extern "C" int sg_probe_read(const void* buf_dev, size_t bytes, int32_t reps, uint32_t* sink_dev,
                              int32_t sink_words, sg_stream_t stream) {
+  SG_RANGE("sg_probe_read");
   if (!buf_dev || !sink_dev || bytes < 16 || (bytes & 15) || ((uintptr_t)buf_dev & 15) || reps < 1)
     return SG_E_INVAL;
   int dev = 0, sms = 0, per_sm = 0;

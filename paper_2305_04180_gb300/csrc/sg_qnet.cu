@@ -1302,7 +1302,8 @@ __device__ __forceinline__ long long sample_entry(unsigned long long seed, unsig
   const unsigned long long j = h % (V * (unsigned long long)rp.n_envs);
   const unsigned long long back = j / (unsigned long long)rp.n_envs;
   const unsigned long long slot = (st - 1ull - back) % (unsigned long long)rp.slots;
-  return (long long)(slot * (unsigned long long)rp.n_envs + j % (unsigned long long)rp.n_envs);
+  const long long e = (long long)(slot * (unsigned long long)rp.n_envs + j % (unsigned long long)rp.n_envs);
+  return SG_IN_BOUNDS(e >= 0 && e < (long long)rp.slots * rp.n_envs) ? e : -1;
 }
 
 // Gather 16 rows of a ring array into a BF16 tile (zero padded).
@@ -1684,7 +1685,18 @@ void free_qnet(sg_qnet* q) {
 }
 }  // namespace
 
+#ifdef SG_DEBUG_BOUNDS
+// This translation unit's debug bounds flag (read and cleared by sg_sim_status).
+int sg_take_debug_bounds_qnet(unsigned* v) {
+  unsigned z = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(v, g_debug_bounds, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_debug_bounds, &z, sizeof(unsigned));
+  return e == cudaSuccess ? SG_OK : sg_set_cuda_error(e, "debug bounds flag");
+}
+#endif
+
 extern "C" int sg_qnet_create(int32_t n_in, int32_t arch, int32_t max_batch, uint64_t seed, sg_qnet_t* out) {
+  SG_RANGE("sg_qnet_create");
   if (!out || n_in < 1 || n_in > 69 || max_batch < 1 || max_batch > (1 << 16)) return SG_E_INVAL;
   if (arch != SG_QNET_DUELING && arch != SG_QNET_PAPER) return SG_E_INVAL;
   *out = nullptr;
@@ -1759,6 +1771,7 @@ extern "C" int sg_qnet_create(int32_t n_in, int32_t arch, int32_t max_batch, uin
 }
 
 extern "C" int sg_qnet_destroy(sg_qnet_t q) {
+  SG_RANGE("sg_qnet_destroy");
   if (!q) return SG_E_INVAL;
   cudaDeviceSynchronize();
   free_qnet(q);
@@ -1795,12 +1808,14 @@ static int download(const sg_qnet* q, const float* dev, float* host) {
 }
 
 extern "C" int sg_qnet_num_params(sg_qnet_t q, int64_t* n) {
+  SG_RANGE("sg_qnet_num_params");
   if (!q || !n) return SG_E_INVAL;
   *n = compact_params(q);
   return SG_OK;
 }
 
 extern "C" int sg_qnet_set_params(sg_qnet_t q, const float* host, int64_t n, int32_t which) {
+  SG_RANGE("sg_qnet_set_params");
   if (!q || !host || n != compact_params(q) || which < 0 || which > 2) return SG_E_INVAL;
   SG_CUDA(cudaDeviceSynchronize());
   if (which == 0 || which == 2) {
@@ -1818,12 +1833,14 @@ extern "C" int sg_qnet_set_params(sg_qnet_t q, const float* host, int64_t n, int
 }
 
 extern "C" int sg_qnet_get_params(sg_qnet_t q, float* host, int64_t n, int32_t which) {
+  SG_RANGE("sg_qnet_get_params");
   if (!q || !host || n != compact_params(q) || which < 0 || which > 1) return SG_E_INVAL;
   SG_CUDA(cudaDeviceSynchronize());
   return download(q, which == 0 ? q->master : q->target, host);
 }
 
 extern "C" int sg_qnet_get_optimizer(sg_qnet_t q, float* m_host, float* v_host, int64_t n, uint64_t* steps) {
+  SG_RANGE("sg_qnet_get_optimizer");
   if (!q || n != compact_params(q)) return SG_E_INVAL;
   SG_CUDA(cudaDeviceSynchronize());
   int rc = SG_OK;
@@ -1835,12 +1852,14 @@ extern "C" int sg_qnet_get_optimizer(sg_qnet_t q, float* m_host, float* v_host, 
 }
 
 extern "C" int sg_qnet_set_rollout_rows(sg_qnet_t q, int32_t rows) {
+  SG_RANGE("sg_qnet_set_rollout_rows");
   if (!q || (rows != 0 && rows != 16 && rows != 32 && rows != 128)) return SG_E_INVAL;
   q->rollout_mt = rows / 16;
   return SG_OK;
 }
 
 extern "C" int sg_qnet_copy_params(sg_qnet_t dst, sg_qnet_t src, sg_stream_t stream) {
+  SG_RANGE("sg_qnet_copy_params");
   if (!dst || !src || dst->n_in != src->n_in || dst->arch != src->arch) return SG_E_INVAL;
   const size_t P = (size_t)src->PL.total;
   SG_CUDA(cudaMemcpyAsync(dst->master, src->master, P * 4, cudaMemcpyDeviceToDevice, stream));
@@ -1851,6 +1870,7 @@ extern "C" int sg_qnet_copy_params(sg_qnet_t dst, sg_qnet_t src, sg_stream_t str
 
 extern "C" int sg_qnet_set_optimizer(sg_qnet_t q, const float* m_host, const float* v_host, int64_t n,
                                      uint64_t steps) {
+  SG_RANGE("sg_qnet_set_optimizer");
   if (!q || !m_host || !v_host || n != compact_params(q)) return SG_E_INVAL;
   SG_CUDA(cudaDeviceSynchronize());
   int rc = upload(q, q->adam_m, m_host);
@@ -1862,6 +1882,7 @@ extern "C" int sg_qnet_set_optimizer(sg_qnet_t q, const float* m_host, const flo
 }
 
 extern "C" int sg_qnet_forward(sg_qnet_t q, const float* obs_dev, int32_t M, float* q_dev, sg_stream_t stream) {
+  SG_RANGE("sg_qnet_forward");
   if (!q || !obs_dev || !q_dev || M < 1) return SG_E_INVAL;
   // a persistent grid over the 128-row tiles
   const int ntiles = (M + kTcRows - 1) / kTcRows;
@@ -1873,6 +1894,7 @@ extern "C" int sg_qnet_forward(sg_qnet_t q, const float* obs_dev, int32_t M, flo
 
 extern "C" int sg_replay_create(int32_t slots_per_env, int32_t n_envs, int32_t obs_dim, int32_t reserve_slots,
                                 sg_replay_t* out) {
+  SG_RANGE("sg_replay_create");
   if (!out || slots_per_env < 1 || n_envs < 1 || obs_dim < 1) return SG_E_INVAL;
   if (reserve_slots < 0 || reserve_slots >= slots_per_env) return SG_E_INVAL;
   const long long cap = (long long)slots_per_env * n_envs;
@@ -1913,6 +1935,7 @@ extern "C" int sg_replay_create(int32_t slots_per_env, int32_t n_envs, int32_t o
 }
 
 extern "C" int sg_replay_destroy(sg_replay_t r) {
+  SG_RANGE("sg_replay_destroy");
   if (!r) return SG_E_INVAL;
   cudaDeviceSynchronize();
   cudaFree(r->d.s);
@@ -1927,6 +1950,7 @@ extern "C" int sg_replay_destroy(sg_replay_t r) {
 
 extern "C" int sg_replay_info(sg_replay_t r, int64_t* capacity, uint64_t* steps_recorded, void** s_dev, void** s2_dev,
                               void** a_dev, void** r_dev, void** term_dev) {
+  SG_RANGE("sg_replay_info");
   if (!r) return SG_E_INVAL;
   if (capacity) *capacity = r->cap;
   if (steps_recorded) {
@@ -1943,6 +1967,7 @@ extern "C" int sg_replay_info(sg_replay_t r, int64_t* capacity, uint64_t* steps_
 
 extern "C" int sg_replay_read(sg_replay_t r, int64_t first, int64_t count, float* s_host, float* s2_host,
                               uint8_t* a_host, float* r_host, uint8_t* term_host) {
+  SG_RANGE("sg_replay_read");
   if (!r || first < 0 || count < 0 || first + count > r->cap) return SG_E_INVAL;
   SG_CUDA(cudaDeviceSynchronize());
   const size_t od = (size_t)r->d.obs_dim;
@@ -1957,6 +1982,7 @@ extern "C" int sg_replay_read(sg_replay_t r, int64_t first, int64_t count, float
 extern "C" int sg_replay_write(sg_replay_t r, int64_t first, int64_t count, const float* s_host, const float* s2_host,
                                const uint8_t* a_host, const float* r_host, const uint8_t* term_host,
                                uint64_t steps_recorded) {
+  SG_RANGE("sg_replay_write");
   if (!r || first < 0 || count < 0 || first + count > r->cap) return SG_E_INVAL;
   if (count > 0 && (!s_host || !s2_host || !a_host || !r_host || !term_host)) return SG_E_INVAL;
   SG_CUDA(cudaDeviceSynchronize());
@@ -1989,6 +2015,7 @@ __global__ void k_vem_eps(const uint32_t* __restrict__ t_dev, int n, float e_min
 
 extern "C" int sg_vem_eps(sg_sim_t sim, float e_min, float e_max, double or_start, double or_final,
                           double decay_steps, float* eps_dev, sg_stream_t stream) {
+  SG_RANGE("sg_vem_eps");
   if (!sim || !eps_dev) return SG_E_INVAL;
   const int n = sim->dc.n_envs;
   if (!(or_final >= 2.0 && or_final <= n && or_start >= 2.0 && or_start <= n && decay_steps > 0.0 &&
@@ -2055,6 +2082,7 @@ int sg_rollout_eps_q(sg_sim* sim, int K, sg_qnet* q, const float* eps, sg_replay
 extern "C" int sg_td_train_step(sg_qnet_t q, sg_replay_t rp, int32_t batch, float gamma, float lr,
                                 int32_t target_every, uint64_t seed, float* loss_dev, float* grad_dev,
                                 sg_stream_t stream) {
+  SG_RANGE("sg_td_train_step");
   if (!q || !rp || batch < 1 || batch > q->max_batch || rp->d.obs_dim != q->n_in) return SG_E_INVAL;
   if (!(gamma >= 0.0f && gamma <= 1.0f) || !(lr >= 0.0f)) return SG_E_INVAL;
   const int nblk = (batch + kTile - 1) / kTile;
@@ -2180,6 +2208,7 @@ extern "C" int sg_td_grad_noalloc(const float* params_dev, const float* target_p
                                   const float* s_dev, const uint8_t* a_dev, const float* r_dev, const float* s2_dev,
                                   const uint8_t* term_dev, int32_t batch, float gamma, float* loss_dev,
                                   float* grad_dev, sg_stream_t stream) {
+  SG_RANGE("sg_td_grad_noalloc");
   if (!params_dev || !target_params_dev || !s_dev || !a_dev || !r_dev || !s2_dev || !term_dev || !grad_dev)
     return sg_set_error_text("sg_td_grad_noalloc: a required pointer is NULL", SG_E_INVAL);
   if (n_in < 1 || n_in > kNaMaxIn)

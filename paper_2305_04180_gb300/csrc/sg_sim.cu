@@ -1177,6 +1177,7 @@ static void free_sim(sg_sim* s) {
 extern "C" int sg_sim_create(const sg_sim_config* cfg, int32_t n_maps, const uint8_t* const* maps_host,
                              const int32_t* map_w, const int32_t* map_h, const int32_t* env_map,
                              const int32_t* env_beams, sg_sim_t* out) {
+  SG_RANGE("sg_sim_create");
   if (!cfg || !maps_host || !map_w || !map_h || !env_map || !out) return SG_E_INVAL;
   if (n_maps < 1) return SG_E_INVAL;
   *out = nullptr;
@@ -1348,6 +1349,7 @@ extern "C" int sg_sim_create(const sg_sim_config* cfg, int32_t n_maps, const uin
 }
 
 extern "C" int sg_sim_destroy(sg_sim_t sim) {
+  SG_RANGE("sg_sim_destroy");
   if (!sim) return SG_E_INVAL;
   cudaDeviceSynchronize();
   free_sim(sim);
@@ -1355,6 +1357,7 @@ extern "C" int sg_sim_destroy(sg_sim_t sim) {
 }
 
 extern "C" int sg_sim_info_get(sg_sim_t sim, sg_sim_info* info) {
+  SG_RANGE("sg_sim_info_get");
   if (!sim || !info) return SG_E_INVAL;
   std::memset(info, 0, sizeof(*info));
   info->n_envs = sim->dc.n_envs;
@@ -1371,6 +1374,7 @@ extern "C" int sg_sim_info_get(sg_sim_t sim, sg_sim_info* info) {
 long long sg_state_bytes(const sg_sim* s) { return (long long)s->dc.n_envs * (9 * 4 + 4 * 4 + 16 * s->dc.n_dyn); }
 
 extern "C" int sg_sim_reset(sg_sim_t sim, uint64_t seed, float* obs_dev, sg_stream_t stream) {
+  SG_RANGE("sg_sim_reset");
   if (!sim) return SG_E_INVAL;
   sim->dc.seed = seed;
   sim->cfg.seed = seed;
@@ -1384,6 +1388,7 @@ extern "C" int sg_sim_reset(sg_sim_t sim, uint64_t seed, float* obs_dev, sg_stre
 
 extern "C" int sg_sim_step(sg_sim_t sim, const uint8_t* act_dev, float* obs_dev, float* rew_dev,
                            uint8_t* done_dev, float* term_obs_dev, sg_stream_t stream) {
+  SG_RANGE("sg_sim_step");
   if (!sim || !act_dev || !obs_dev || !rew_dev || !done_dev) return SG_E_INVAL;
   if (((uintptr_t)obs_dev & 3) || ((uintptr_t)rew_dev & 3) || ((uintptr_t)term_obs_dev & 3)) return SG_E_ALIGN;
   constexpr int kPerBlock = kStepWarps * kStepEnvsPerWarp;
@@ -1401,6 +1406,7 @@ int sg_rollout_eps_q(sg_sim* sim, int K, sg_qnet* q, const float* eps, sg_replay
 extern "C" int sg_sim_rollout(sg_sim_t sim, int32_t K, int32_t policy, sg_qnet_t qnet, const float* eps_dev,
                               sg_replay_t replay, float* obs_dev, float* obs_seq_dev, uint8_t* act_seq_dev,
                               float* rew_seq_dev, uint8_t* done_seq_dev, sg_stream_t stream) {
+  SG_RANGE("sg_sim_rollout");
   if (!sim || K < 1 || K > (1 << 20)) return SG_E_INVAL;
   if (((uintptr_t)obs_dev & 3) || ((uintptr_t)obs_seq_dev & 3) || ((uintptr_t)rew_seq_dev & 3)) return SG_E_ALIGN;
   if (policy == SG_POLICY_RANDOM) {
@@ -1465,6 +1471,7 @@ extern "C" int sg_sim_rollout(sg_sim_t sim, int32_t K, int32_t policy, sg_qnet_t
 }
 
 extern "C" int sg_sim_set_launch(sg_sim_t sim, const sg_launch* cfg) {
+  SG_RANGE("sg_sim_set_launch");
   if (!sim || !cfg) return SG_E_INVAL;
   const sg_launch L = *cfg;
   auto pow2 = [](int v) { return v == 1 || v == 2 || v == 4 || v == 8 || v == 16; };
@@ -1549,12 +1556,14 @@ extern "C" int sg_sim_set_launch(sg_sim_t sim, const sg_launch* cfg) {
 }
 
 extern "C" int sg_sim_get_launch(sg_sim_t sim, sg_launch* cfg) {
+  SG_RANGE("sg_sim_get_launch");
   if (!sim || !cfg) return SG_E_INVAL;
   *cfg = sim->launch;
   return SG_OK;
 }
 
 extern "C" int sg_sim_get_state(sg_sim_t sim, void* host_buf, size_t* bytes) {
+  SG_RANGE("sg_sim_get_state");
   if (!sim || !bytes) return SG_E_INVAL;
   const size_t need = (size_t)sg_state_bytes(sim);
   if (!host_buf) {
@@ -1573,6 +1582,7 @@ extern "C" int sg_sim_get_state(sg_sim_t sim, void* host_buf, size_t* bytes) {
 }
 
 extern "C" int sg_sim_set_state(sg_sim_t sim, const void* host_buf, size_t bytes) {
+  SG_RANGE("sg_sim_set_state");
   if (!sim || !host_buf) return SG_E_INVAL;
   const size_t need = (size_t)sg_state_bytes(sim);
   if (bytes != need) return SG_E_INVAL;
@@ -1588,6 +1598,7 @@ extern "C" int sg_sim_set_state(sg_sim_t sim, const void* host_buf, size_t bytes
 
 extern "C" int sg_sim_get_atlas(sg_sim_t sim, uint32_t* atlas_host, size_t* words, int64_t* offs_host,
                                 int32_t* row_words_host) {
+  SG_RANGE("sg_sim_get_atlas");
   if (!sim) return SG_E_INVAL;
   if (atlas_host) {
     if (!words || *words < (size_t)sim->atlas_words) return SG_E_INVAL;
@@ -1603,6 +1614,7 @@ extern "C" int sg_sim_get_atlas(sg_sim_t sim, uint32_t* atlas_host, size_t* word
 }
 
 extern "C" int sg_sim_get_clearance(sg_sim_t sim, uint8_t* host, size_t* bytes, int64_t* offs_host) {
+  SG_RANGE("sg_sim_get_clearance");
   if (!sim || !bytes) return SG_E_INVAL;
   size_t total = 0;
   for (int m = 0; m < sim->n_maps; ++m) total += (size_t)sim->maps_host[m].w * sim->maps_host[m].h;
@@ -1629,6 +1641,7 @@ extern "C" int sg_sim_get_clearance(sg_sim_t sim, uint8_t* host, size_t* bytes, 
 }
 
 extern "C" int sg_sim_get_sector_skip(sg_sim_t sim, uint8_t* host, size_t* bytes, int64_t* offs_host) {
+  SG_RANGE("sg_sim_get_sector_skip");
   if (!sim || !bytes) return SG_E_INVAL;
   const int S = sim->dc.n_sec > 1 ? sim->dc.n_sec : 0;
   size_t total = 0;
@@ -1657,12 +1670,24 @@ extern "C" int sg_sim_get_sector_skip(sg_sim_t sim, uint8_t* host, size_t* bytes
   return SG_OK;
 }
 
+#ifdef SG_DEBUG_BOUNDS
+int sg_take_debug_bounds_qnet(unsigned* v);  // sg_qnet.cu
+#endif
+
 extern "C" int sg_sim_status(sg_sim_t sim, uint32_t* device_status) {
+  SG_RANGE("sg_sim_status");
   if (!sim || !device_status) return SG_E_INVAL;
   uint32_t v = 0;
   SG_CUDA(cudaDeviceSynchronize());
   SG_CUDA(cudaMemcpy(&v, sim->status_dev, 4, cudaMemcpyDeviceToHost));
   SG_CUDA(cudaMemset(sim->status_dev, 0, 4));
+#ifdef SG_DEBUG_BOUNDS
+  unsigned b = 0, bq = 0, z = 0;
+  SG_CUDA(cudaMemcpyFromSymbol(&b, g_debug_bounds, sizeof(unsigned)));
+  SG_CUDA(cudaMemcpyToSymbol(g_debug_bounds, &z, sizeof(unsigned)));
+  if (int rc = sg_take_debug_bounds_qnet(&bq)) return rc;
+  if (b | bq) v |= SG_DEV_BOUNDS;
+#endif
   *device_status = v;
   return v ? SG_E_DEVICE : SG_OK;
 }
