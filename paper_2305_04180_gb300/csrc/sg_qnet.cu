@@ -153,6 +153,9 @@ struct sg_qnet {
   int* idx = nullptr;        // [max_batch] sampled ring entries
   int rollout_mt = 0;        // m-tiles per CTA of the fused rollout (0 = choose by waves)
   uint8_t* img_tc = nullptr; // the online weights in the tensor cores' shared-memory layout (batched forward)
+  uint8_t* img_tc_t = nullptr; // the target weights in the same layout (tcgen05 learner)
+  float* q2 = nullptr;       // [2][max_batch][5] Q-values of the sampled next states (tcgen05 learner)
+  unsigned* td_sync = nullptr;  // [1 + max_batch / 128] job counter and per-tile counters (tcgen05 learner)
   int sms = 0;               // multiprocessors of the device (persistent grids)
 };
 
@@ -1624,12 +1627,647 @@ __global__ void k_step_advance(unsigned long long* step, const unsigned* __restr
 // from a CUDA graph).
 __global__ void k_target_sync(const unsigned long long* __restrict__ step, int every, const float* __restrict__ th,
                               float* __restrict__ tgt, const uint8_t* __restrict__ img, uint8_t* __restrict__ img_t,
-                              int P, int img_words) {
+                              int P, int img_words, const uint8_t* __restrict__ tc, uint8_t* __restrict__ tc_t,
+                              int tc_words) {
   if (every <= 0 || (*step % (unsigned long long)every) != 0ull) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < P) tgt[i] = th[i];
   if (i < img_words) reinterpret_cast<uint32_t*>(img_t)[i] = reinterpret_cast<const uint32_t*>(img)[i];
+  if (i < tc_words) reinterpret_cast<uint32_t*>(tc_t)[i] = reinterpret_cast<const uint32_t*>(tc)[i];
 }
+
+
+// ------------------------------------------------ tcgen05 learner (batch >= 128)
+// The TD step for large batches on the fifth-generation tensor cores, in
+// 128-sample tiles (one per CTA, 8 warps, the whole shared memory, 512
+// tensor-memory columns):
+//   k_td_target_tc: per (network, tile) job the forward of Q_online(s') or
+//     Q_target(s') (the fused rollout's layer order, weights streamed through
+//     two 32 KB buffers); the Q-values go to global memory.
+//   k_td_grad_tc: per tile y = r + gamma (1 - term) Q_target(s', argmax
+//     Q_online(s')), the forward on s keeping H1 and H2, dQ -> dO (dueling
+//     combine), dW3 / db3 / dH2 / dZ2 / db2 on the CUDA cores, then on the
+//     tensor cores dW2 = dZ2^T H1, dH1 = dZ2 W2^T (-> dZ1, db1) and
+//     dW1 = dZ1^T X; the tile's gradient goes to its own partial row, so the
+//     reduction (k_adam, in tile order) is fixed.
+// The weight-gradient and backpropagation products read their operands
+// transposed: a K-major tile [rows][cols] (core matrices of 8 rows x 16
+// bytes, LBO = rows x 16 between 8-column groups, SBO = 128 between 8-row
+// groups) is, for the transposed product, an MN-major operand whose core
+// matrices are the same 128 bytes (8 consecutive MN elements per 16-byte
+// row, 8 K rows): SBO = rows x 16 between 8-element MN groups, LBO = 128
+// between 8-row K groups, and the instruction descriptor's transpose bit of
+// that operand set.  The same BF16 recipe as the mma.sync learner (BF16
+// weights, activations and backpropagated dZ, FP32 sums; dW3, db and the
+// head on the CUDA cores in FP32).
+constexpr int kLtRows = 128;
+constexpr int kLtThreads = 256;
+// Below this batch the 16-sample mma.sync learner is faster (its CTAs spread
+// over more SMs); measured on one GB300: 58 vs 98 us per step at batch 256,
+// 120 vs 98 us at 4,096 with the two-kernel tcgen05 learner.
+constexpr int kLtMinBatch = 2048;
+constexpr uint32_t kLtBuf = 32u * 1024u;
+
+struct LtSmem {
+  uint32_t x, h1, h2, b0, b1, dout, bias, bytes;
+};
+__host__ __device__ inline LtSmem lt_smem(int k1) {
+  LtSmem t;
+  t.x = 0;
+  t.h1 = tc_up((uint32_t)(kLtRows * k1 * 2));
+  t.h2 = t.h1 + (uint32_t)(kLtRows * kHid * 2);
+  t.b0 = t.h2 + (uint32_t)(kLtRows * kHid * 2);
+  t.b1 = t.b0 + kLtBuf;
+  t.dout = t.b1 + kLtBuf;                          // dO [128][8] float
+  t.bias = t.dout + (uint32_t)(kLtRows * kOutPad * 4);  // b1, b2 [256] float, b3 [8], reduction scratch [4][256]
+  t.bytes = t.bias + (uint32_t)((2 * kHid + kOutPad + 4 * kHid) * 4);
+  return t;
+}
+
+// Instruction descriptor with the operands' major-ness: trans_a / trans_b = 1
+// reads A / B MN-major (bits 15 / 16).
+__host__ __device__ constexpr uint32_t idesc_bf16_f32_t(int M, int N, int trans_a, int trans_b) {
+  return idesc_bf16_f32(M, N) | ((uint32_t)trans_a << 15) | ((uint32_t)trans_b << 16);
+}
+
+// nks MMAs of K = 16: A at a0 + ks * ka, B at b0 + ks * kb (shared-memory
+// byte addresses), each with its own leading / stride byte offsets.
+__device__ __forceinline__ void lt_mma(uint32_t tacc, uint32_t a0, uint32_t lba, uint32_t sba, uint32_t ka,
+                                       uint32_t b0, uint32_t lbb, uint32_t sbb, uint32_t kb, uint32_t idesc, int nks,
+                                       bool accumulate) {
+  for (int ks = 0; ks < nks; ++ks)
+    tc_mma_bf16(tacc, smem_desc(a0 + (uint32_t)ks * ka, lba, sba), smem_desc(b0 + (uint32_t)ks * kb, lbb, sbb), idesc,
+                (accumulate || ks > 0) ? 1u : 0u);
+}
+
+// The two weight buffers of a CTA, run by thread 0: a copy into buffer b
+// waits (bounded) until the MMAs that read it are done.
+struct LtStream {
+  uint64_t* ld;
+  uint64_t* mm;
+  uint8_t* buf[2];
+  uint32_t pl[2], pm[2];
+  bool ld_out[2], mm_out[2];
+  bool ok;
+  __device__ __forceinline__ void load(int b, const void* src, uint32_t bytes) {
+    if (!ok) return;
+    if (mm_out[b]) {
+      ok = mbar_wait(&mm[b], pm[b], kTcTries);
+      pm[b] ^= 1u;
+      mm_out[b] = false;
+      if (!ok) return;
+    }
+    mbar_expect_tx(&ld[b], bytes);
+    bulk_g2s(buf[b], src, bytes, &ld[b]);
+    ld_out[b] = true;
+  }
+  __device__ __forceinline__ bool ready(int b) {
+    if (!ok) return false;
+    if (ld_out[b]) {
+      ok = mbar_wait(&ld[b], pl[b], kTcTries);
+      pl[b] ^= 1u;
+      ld_out[b] = false;
+    }
+    if (ok) tc_fence_after();
+    return ok;
+  }
+  __device__ __forceinline__ void done(int b) {
+    tc_commit(&mm[b]);
+    mm_out[b] = true;
+  }
+  __device__ __forceinline__ void drain() {
+    for (int b = 0; b < 2; ++b) {
+      if (mm_out[b]) mbar_wait(&mm[b], pm[b], kTcTries);
+      if (ld_out[b]) mbar_wait(&ld[b], pl[b], kTcTries);
+    }
+  }
+};
+
+// Rows of a tile: sample i's ring entry (or -1 past the batch) into X (BF16,
+// K-major, zero padded); the two threads of a row take alternate 8-column
+// groups.
+__device__ __forceinline__ void lt_load_x(uint8_t* xs, const float* __restrict__ src, const int* rows_sh, int n_in,
+                                          int k1, int tid) {
+  const int row = tid & (kLtRows - 1);
+  const int e = rows_sh[row];
+  for (int kg = tid >> 7; kg < k1 / 8; kg += 2) {
+    float v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int k = kg * 8 + j;
+      v[j] = (e >= 0 && k < n_in) ? __ldg(src + (long long)e * n_in + k) : 0.0f;
+    }
+    *reinterpret_cast<uint4*>(xs + kmajor_offset(row, kg * 8, kLtRows)) =
+        make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
+  }
+  fence_async_smem();
+}
+
+// A CTA-wide barrier that also orders the tensor-core work around it.
+__device__ __forceinline__ void lt_sync() {
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+}
+
+// Thread 0: the two W1 halves of timg into the two buffers (issued before the
+// tile's inputs are gathered, so that the copies overlap the gathers).
+__device__ __forceinline__ void lt_prefetch_w1(LtStream& S, const uint8_t* __restrict__ timg, const ImgLayout& L) {
+  const TcImg G = tc_img(L.k1);
+  const uint32_t w1h = 128u * (uint32_t)L.k1 * 2u;
+  S.load(0, timg + G.w1h, w1h);
+  S.load(1, timg + G.w1h + w1h, w1h);
+}
+
+// The forward of one tile (X in xs) through the network whose tensor-core
+// image is timg (W1 already on its way, lt_prefetch_w1), the hidden
+// activations left in h1s / h2s (BF16, K-major), the head's 16 columns in
+// tensor-memory columns [0, 16).  Thread 0 issues the MMAs and copies; every
+// thread runs the epilogues.  Returns false when a wait ran out (then
+// nothing after it was issued).
+__device__ __forceinline__ bool lt_forward(LtStream& S, uint64_t* bar_layer, uint32_t& player, uint32_t tacc,
+                                           const uint8_t* __restrict__ timg, const ImgLayout& L, uint8_t* xs,
+                                           uint8_t* h1s, uint8_t* h2s, const float* b1, const float* b2, int tid,
+                                           bool& layer_out) {
+  const TcImg G = tc_img(L.k1);
+  const int warp = tid >> 5, lane = tid & 31;
+  const uint32_t w2q = 64u * kHid * 2u;
+  const uint32_t sx = smem_u32(xs), sh1 = smem_u32(h1s), sh2 = smem_u32(h2s);
+  const uint32_t kA = kLtRows * 16u;  // K-group stride of a 128-row K-major tile
+  if (tid == 0) {
+    // layer 1 in two 128-unit halves (W1 halves in the two buffers)
+    for (int h = 0; h < 2; ++h)
+      if (S.ready(h)) {
+        lt_mma(tacc + 128u * h, sx, kA, 128, 2 * kA, smem_u32(S.buf[h]), 128u * 16u, 128, 2u * 128u * 16u,
+               idesc_bf16_f32(kLtRows, 128), L.k1 / 16, false);
+        S.done(h);
+      }
+    if (S.ok) tc_commit(bar_layer);
+    // the first two W2 quarters follow as soon as the buffers are free
+    S.load(0, timg + G.w2q, w2q);
+    S.load(1, timg + G.w2q + w2q, w2q);
+  }
+  layer_out = true;
+  bool ok = __syncthreads_and(mbar_wait(bar_layer, player, kTcTries));
+  player ^= 1u;
+  layer_out = !ok;
+  if (!ok) return false;
+  tc_fence_after();
+  tc_epilogue_hidden(tacc, b1, h1s, warp, lane);
+  fence_async_smem();
+  lt_sync();
+  if (tid == 0) {
+    // layer 2 in four 64-unit quarters (quarters 2 and 3 are copied in
+    // together once 0 and 1 are consumed)
+    for (int q = 0; q < 4; ++q) {
+      const int b = q & 1;
+      if (q == 2) {
+        S.load(0, timg + G.w2q + 2u * w2q, w2q);
+        S.load(1, timg + G.w2q + 3u * w2q, w2q);
+      }
+      if (S.ready(b)) {
+        lt_mma(tacc + 64u * q, sh1, kA, 128, 2 * kA, smem_u32(S.buf[b]), 64u * 16u, 128, 2u * 64u * 16u,
+               idesc_bf16_f32(kLtRows, 64), kHid / 16, false);
+        S.done(b);
+      }
+    }
+    if (S.ok) tc_commit(bar_layer);
+    S.load(0, timg + G.w3, 16u * kHid * 2u);  // the head's weights next
+  }
+  layer_out = true;
+  ok = __syncthreads_and(mbar_wait(bar_layer, player, kTcTries));
+  player ^= 1u;
+  layer_out = !ok;
+  if (!ok) return false;
+  tc_fence_after();
+  tc_epilogue_hidden(tacc, b2, h2s, warp, lane);
+  fence_async_smem();
+  lt_sync();
+  if (tid == 0) {
+    if (S.ready(0)) {
+      lt_mma(tacc, sh2, kA, 128, 2 * kA, smem_u32(S.buf[0]), 16u * 16u, 128, 2u * 16u * 16u,
+             idesc_bf16_f32(kLtRows, 16), kHid / 16, false);
+      S.done(0);
+      tc_commit(bar_layer);
+    }
+  }
+  layer_out = true;
+  ok = __syncthreads_and(mbar_wait(bar_layer, player, kTcTries));
+  player ^= 1u;
+  layer_out = !ok;
+  if (ok) tc_fence_after();
+  return ok;
+}
+
+// Sum of this lane's 32 values over the warp's 32 lanes, column by column:
+// afterwards lane l holds the sum of column l (fixed butterfly order).
+__device__ __forceinline__ float lt_colsum32(float (&v)[32], int lane) {
+#pragma unroll
+  for (int w = 16; w >= 1; w >>= 1) {
+    const bool upper = (lane & w) != 0;
+#pragma unroll
+    for (int i = 0; i < w; ++i) {
+      const float send = upper ? v[i] : v[i + w];
+      const float keep = upper ? v[i + w] : v[i];
+      v[i] = keep + __shfl_xor_sync(kFull, send, w);
+    }
+  }
+  return v[0];
+}
+
+// Bias vectors of a network's image into shared memory.
+__device__ __forceinline__ void lt_biases(const uint8_t* __restrict__ im, const ImgLayout& L, float* b1, float* b2,
+                                          float* b3, int tid) {
+  for (int i = tid; i < kHid; i += kLtThreads) {
+    b1[i] = __ldg(reinterpret_cast<const float*>(im + L.b1) + i);
+    b2[i] = __ldg(reinterpret_cast<const float*>(im + L.b2) + i);
+  }
+  if (tid < kOutPad) b3[tid] = __ldg(reinterpret_cast<const float*>(im + L.b3) + tid);
+  __syncthreads();
+}
+
+// The tensor-core work of one TD step in one kernel.  CTAs take jobs in start
+// order from a device counter: jobs [0, 2 ntiles) are the next-state
+// forwards (Q_online(s') of tile t, then Q_target(s') of tile t; Q-values to
+// q2[net][i][5], then the tile's counter in sync is raised), jobs
+// [2 ntiles, 4 ntiles) the tiles' loss and gradient in two halves per tile
+// (role 0: dW3, db3, db2, the loss, dW2; role 1: dH1, db1, dW1), each from its
+// own forward on s, into partial[tile].  A gradient job runs its forward
+// first and only then waits (bounded) for its tile's two next-state jobs:
+// those were taken earlier by CTAs that are running and never wait, so the
+// wait ends for any grid size.
+// sync: [0] the job counter, [1 + t] next-state jobs done for tile t; zero at
+// launch.
+__global__ void __launch_bounds__(kLtThreads, 1)
+    k_td_tc(const uint8_t* __restrict__ img, const uint8_t* __restrict__ img_t, const uint8_t* __restrict__ timg,
+            const uint8_t* __restrict__ timg_t, ImgLayout L, ParamLayout P, ReplayDev rp, unsigned long long seed,
+            const unsigned long long* __restrict__ step, int batch, float gamma, float* __restrict__ q2,
+            int* __restrict__ idx, unsigned* __restrict__ sync, float* __restrict__ partial,
+            unsigned* __restrict__ fail) {
+  extern __shared__ __align__(1024) uint8_t tsm[];
+  __shared__ uint64_t bar_ld[2], bar_mm[2], bar_layer;
+  __shared__ uint32_t tslot;
+  __shared__ int rows_sh[kLtRows];
+  __shared__ float y_sh[kLtRows];
+  __shared__ float hub_sh[kLtRows / 32];
+  __shared__ int job_sh, flag_sh;
+  const LtSmem T = lt_smem(L.k1);
+  const TcImg G = tc_img(L.k1);
+  uint8_t* xs = tsm + T.x;
+  uint8_t* h1s = tsm + T.h1;
+  uint8_t* h2s = tsm + T.h2;
+  float* dout = reinterpret_cast<float*>(tsm + T.dout);
+  float* b1 = reinterpret_cast<float*>(tsm + T.bias);
+  float* b2 = b1 + kHid;
+  float* b3 = b2 + kHid;
+  float* red = b3 + kOutPad;  // [4][256] column sums of the four lane quarters
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ntiles = (batch + kLtRows - 1) / kLtRows;
+  const uint32_t w2q = 64u * kHid * 2u;
+  const uint32_t kA = kLtRows * 16u;
+  const bf16* W3g = reinterpret_cast<const bf16*>(img + L.w3);
+  if (warp == 0) tmem_alloc(&tslot, 512);
+  if (tid == 0) {
+    mbar_init(&bar_ld[0], 1);
+    mbar_init(&bar_ld[1], 1);
+    mbar_init(&bar_mm[0], 1);
+    mbar_init(&bar_mm[1], 1);
+    mbar_init(&bar_layer, 1);
+  }
+  lt_sync();
+  const uint32_t tacc = tslot;
+  LtStream S;
+  S.ld = bar_ld;
+  S.mm = bar_mm;
+  S.buf[0] = tsm + T.b0;
+  S.buf[1] = tsm + T.b1;
+  S.pl[0] = S.pl[1] = S.pm[0] = S.pm[1] = 0u;
+  S.ld_out[0] = S.ld_out[1] = S.mm_out[0] = S.mm_out[1] = false;
+  S.ok = true;
+  uint32_t player = 0;
+  bool layer_out = false, ok = true;
+  const unsigned long long tstep = *step;
+  for (;;) {
+    if (tid == 0) job_sh = (int)atomicAdd(sync, 1u);
+    __syncthreads();
+    const int job = job_sh;
+    __syncthreads();  // every thread has the job before the next one is taken
+    if (job >= 4 * ntiles || !ok) break;
+    if (job < 2 * ntiles) {
+      const int net = job >= ntiles ? 1 : 0, tile = job - net * ntiles;
+      lt_biases(net ? img_t : img, L, b1, b2, b3, tid);
+      if (tid == 0) lt_prefetch_w1(S, net ? timg_t : timg, L);
+      if (tid < kLtRows) {
+        const int i = tile * kLtRows + tid;
+        const int e = i < batch ? (int)sample_entry(seed, tstep, i, rp) : -1;
+        rows_sh[tid] = e;
+        if (net == 0 && i < batch) idx[i] = e;
+      }
+      __syncthreads();
+      lt_load_x(xs, rp.s2, rows_sh, L.n_in, L.k1, tid);
+      lt_sync();
+      ok = lt_forward(S, &bar_layer, player, tacc, net ? timg_t : timg, L, xs, h1s, h2s, b1, b2, tid, layer_out);
+      if (warp < 4) {
+        const int i = tile * kLtRows + warp * 32 + lane;
+        float v[32];
+        if (ok) tmem_ld32(tacc + ((uint32_t)(warp * 32) << 16), v);
+        if (i < batch) {
+          float qv[5];
+          if (ok) {
+            float o[kOut];
+#pragma unroll
+            for (int j = 0; j < kOut; ++j) o[j] = v[j] + b3[j];
+            greedy_action(o, qv, L.plain);
+          } else {
+#pragma unroll
+            for (int a = 0; a < 5; ++a) qv[a] = __int_as_float(0x7fc00000);
+          }
+#pragma unroll
+          for (int a = 0; a < 5; ++a) q2[((long long)net * batch + i) * 5 + a] = qv[a];
+        }
+      }
+      // publish (also after a failure, whose Q-values are NaN): the values
+      // before the tile's counter (release)
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) atomicAdd(sync + 1 + tile, 1u);
+      lt_sync();
+      continue;
+    }
+    // gradient jobs: role 0 of a tile computes dW3, db3, db2, the loss and
+    // dW2; role 1 (on another CTA, from the same forward) dH1, db1 and dW1
+    const int role = job >= 3 * ntiles ? 1 : 0;
+    const int tile = job - (2 + role) * ntiles;
+    float* pg = partial + (long long)tile * partial_stride(P.total);
+    if (tid == 0) lt_prefetch_w1(S, timg, L);
+    lt_biases(img, L, b1, b2, b3, tid);
+    // the tile's samples (the same counter-RNG draws as the next-state jobs)
+    if (tid < kLtRows) {
+      const int i = tile * kLtRows + tid;
+      rows_sh[tid] = i < batch ? (int)sample_entry(seed, tstep, i, rp) : -1;
+    }
+    __syncthreads();
+    lt_load_x(xs, rp.s, rows_sh, L.n_in, L.k1, tid);
+    lt_sync();
+    ok = lt_forward(S, &bar_layer, player, tacc, timg, L, xs, h1s, h2s, b1, b2, tid, layer_out);
+    if (!ok) break;
+    // the tile's two next-state jobs (taken earlier by running CTAs, which
+    // never wait) publish their Q-values; bounded wait
+    if (tid == 0) {
+      unsigned it = 0;
+      while (qt_ld_acquire(sync + 1 + tile) < 2u && ++it < kQtWaitIters) __nanosleep(256);
+      flag_sh = it < kQtWaitIters ? 1 : 0;
+    }
+    __syncthreads();
+    if (!flag_sh) {
+      ok = false;
+      break;
+    }
+    // double-DQN targets y = r + gamma (1 - term) Q_target(s', argmax_a Q_online(s', a))
+    if (tid < kLtRows) {
+      const int i = tile * kLtRows + tid, e = rows_sh[tid];
+      float y = 0.0f;
+      if (e >= 0) {
+        const float* qo = q2 + (long long)i * 5;
+        const float* qt = q2 + ((long long)batch + i) * 5;
+        int astar = 0;
+        float best = __ldcg(qo);
+        for (int a = 1; a < 5; ++a) {
+          const float v = __ldcg(qo + a);
+          if (v > best) {
+            best = v;
+            astar = a;
+          }
+        }
+        const float nt = rp.term[e] ? 0.0f : 1.0f;
+        y = rp.r[e] + gamma * nt * __ldcg(qt + astar);
+        if (isnan(best)) y = best;  // a failed next-state job
+      }
+      y_sh[tid] = y;
+    }
+    __syncthreads();
+    // dL/dQ(s, a) = clip(Q(s, a) - y) / B, back through the head's combine
+    if (warp < 4) {
+      const int r = warp * 32 + lane, e = rows_sh[r];
+      float v[32];
+      tmem_ld32(tacc + ((uint32_t)(warp * 32) << 16), v);
+      float hl = 0.0f;
+      float* dO = dout + r * kOutPad;
+      for (int k = 0; k < kOutPad; ++k) dO[k] = 0.0f;
+      if (e >= 0) {
+        float o[kOut], qv[5];
+#pragma unroll
+        for (int j = 0; j < kOut; ++j) o[j] = v[j] + b3[j];
+        greedy_action(o, qv, L.plain);
+        int a = rp.a[e];
+        float d;
+        if (a >= 5) {
+          atomicOr(fail, kTdFailAction);
+          a = 0;
+          d = __int_as_float(0x7fc00000);
+        } else {
+          d = qv[a] - y_sh[r];
+        }
+        const float ad = fabsf(d);
+        hl = ad <= 1.0f ? 0.5f * d * d : ad - 0.5f;
+        const float gq = (isnan(d) ? d : fminf(fmaxf(d, -1.0f), 1.0f)) / (float)batch;
+        if (L.plain) {
+          for (int k = 0; k < 5; ++k) dO[k] = k == a ? gq : 0.0f;
+        } else {
+          dO[0] = gq;
+          for (int k = 0; k < 5; ++k) dO[1 + k] = (k == a ? gq : 0.0f) - gq / 5.0f;
+        }
+      }
+      // the tile's Huber sum: lanes in order, then warps in order
+      for (int off = 16; off > 0; off >>= 1) hl += __shfl_xor_sync(kFull, hl, off);
+      if (lane == 0) hub_sh[warp] = hl;
+    }
+    lt_sync();
+    // CUDA cores, thread per hidden unit n: dW3[o][n] = sum_s dO[s][o] H2[s][n],
+    // dZ2[s][n] = (H2 > 0) sum_o dO[s][o] W3[o][n] written over H2 (BF16),
+    // db2[n] = sum_s dZ2[s][n] (FP32)
+    {
+      const int n = tid;
+      float w3c[kOut];
+#pragma unroll
+      for (int o = 0; o < kOut; ++o) w3c[o] = __bfloat162float(W3g[o * kLdh + n]);
+      float acc3[kOut];
+#pragma unroll
+      for (int o = 0; o < kOut; ++o) acc3[o] = 0.0f;
+      float db2 = 0.0f;
+      // four rows at a time: their loads are independent of the stores
+      for (int r0 = 0; r0 < kLtRows; r0 += 4) {
+        bf16* hp[4];
+        float h[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          hp[u] = reinterpret_cast<bf16*>(h2s + kmajor_offset(r0 + u, n, kLtRows));
+          h[u] = __bfloat162float(*hp[u]);
+        }
+        bf16 z[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float* dO = dout + (r0 + u) * kOutPad;
+          float dh = 0.0f;
+#pragma unroll
+          for (int o = 0; o < kOut; ++o) {
+            acc3[o] += dO[o] * h[u];
+            dh += dO[o] * w3c[o];
+          }
+          const float dz = h[u] > 0.0f ? dh : 0.0f;
+          db2 += dz;
+          z[u] = __float2bfloat16_rn(dz);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) *hp[u] = z[u];
+      }
+      if (role == 0) {
+#pragma unroll
+        for (int o = 0; o < kOut; ++o) pg[P.w3 + o * kHid + n] = acc3[o];
+        pg[P.b2 + n] = db2;
+        if (n < kOut) {
+          float acc = 0.0f;
+          for (int r = 0; r < kLtRows; ++r) acc += dout[r * kOutPad + n];
+          pg[P.b3 + n] = acc;
+        }
+        if (n == 0) pg[P.total] = ((hub_sh[0] + hub_sh[1]) + hub_sh[2]) + hub_sh[3];
+      }
+    }
+    fence_async_smem();
+    lt_sync();
+    if (role == 0) {
+      // tensor cores: dW2 = dZ2^T H1 (M = out unit in two halves, N = in unit,
+      // K = sample; both operands transposed) into columns [0, 512); the W2
+      // quarters of dH1 stream in meanwhile
+      if (tid == 0) {
+        for (int h = 0; h < 2; ++h)
+          lt_mma(tacc + 256u * h, smem_u32(h2s) + 16u * (uint32_t)h * kA, 128, kA, 2u * 128u, smem_u32(h1s), 128, kA,
+                 2u * 128u, idesc_bf16_f32_t(kLtRows, kHid, 1, 1), kLtRows / 16, false);
+        tc_commit(&bar_layer);
+      }
+      layer_out = true;
+      ok = __syncthreads_and(mbar_wait(&bar_layer, player, kTcTries));
+      player ^= 1u;
+      layer_out = !ok;
+      if (!ok) break;
+      tc_fence_after();
+      {
+        // warp w: rows of lane quarter w % 4 (out unit 32 (w % 4) + lane of half
+        // w / 4), 32 columns at a time through a 32 x 32 float tile of buffer 1
+        // (rotated by the row: conflict-free both ways), then stored row by row
+        // with the warp's 32 lanes on 32 consecutive columns (coalesced)
+        const int quarter = warp & 3, h = warp >> 2, n0 = 128 * h + quarter * 32;
+        float* st = reinterpret_cast<float*>(S.buf[1]) + warp * 32 * 32;
+        for (int c = 0; c < kHid; c += 32) {
+          float v[32];
+          tmem_ld32(tacc + ((uint32_t)(quarter * 32) << 16) + 256u * h + (uint32_t)c, v);
+#pragma unroll
+          for (int k = 0; k < 32; ++k) st[lane * 32 + ((k + lane) & 31)] = v[k];
+          __syncwarp();
+#pragma unroll 8
+          for (int r = 0; r < 32; ++r) pg[P.w2 + (long long)(n0 + r) * kHid + c + lane] = st[r * 32 + ((lane + r) & 31)];
+          __syncwarp();
+        }
+      }
+      fence_async_smem();  // the staging reads before buffer 1 takes a bulk copy
+      lt_sync();
+      continue;
+    }  // role 0
+    // dH1 = dZ2 W2^T (A = dZ2 K-major over the out unit, B = W2 quarters
+    // transposed) into columns [0, 256)
+    if (tid == 0) {
+      for (int q = 0; q < 4; ++q) {
+        const int b = q & 1;
+        if (q < 2) S.load(b, timg + G.w2q + (uint32_t)q * w2q, w2q);
+        if (q == 2) {
+          S.load(0, timg + G.w2q + 2u * w2q, w2q);
+          S.load(1, timg + G.w2q + 3u * w2q, w2q);
+        }
+        if (S.ready(b)) {
+          lt_mma(tacc, smem_u32(h2s) + (uint32_t)(8 * q) * kA, kA, 128, 2u * kA, smem_u32(S.buf[b]), 128, 64u * 16u,
+                 2u * 128u, idesc_bf16_f32_t(kLtRows, kHid, 0, 1), 64 / 16, q > 0);
+          S.done(b);
+        }
+      }
+      if (S.ok) tc_commit(&bar_layer);
+    }
+    layer_out = true;
+    ok = __syncthreads_and(mbar_wait(&bar_layer, player, kTcTries));
+    player ^= 1u;
+    layer_out = !ok;
+    if (!ok) break;
+    tc_fence_after();
+    {
+      // dZ1 = (H1 > 0) dH1 written over H1 (BF16); db1 from the FP32 values
+      const int quarter = warp & 3, r = quarter * 32 + lane, c0 = (warp >> 2) * 128;
+      for (int c = c0; c < c0 + 128; c += 32) {
+        float v[32];
+        tmem_ld32(tacc + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c, v);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          uint4* hp = reinterpret_cast<uint4*>(h1s + kmajor_offset(r, c + 8 * g, kLtRows));
+          const uint4 hv = *hp;
+          const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
+          uint32_t w[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const bool m0 = (hw[j] & 0xFFFFu) != 0u && !(hw[j] & 0x8000u);
+            const bool m1 = (hw[j] >> 16) != 0u && !(hw[j] & 0x80000000u);
+            v[8 * g + 2 * j] = m0 ? v[8 * g + 2 * j] : 0.0f;
+            v[8 * g + 2 * j + 1] = m1 ? v[8 * g + 2 * j + 1] : 0.0f;
+            w[j] = pack_bf16x2(v[8 * g + 2 * j], v[8 * g + 2 * j + 1]);
+          }
+          *hp = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        const float s = lt_colsum32(v, lane);
+        red[quarter * kHid + c + lane] = s;
+      }
+    }
+    fence_async_smem();
+    lt_sync();
+    if (tid < kHid) pg[P.b1 + tid] = ((red[tid] + red[kHid + tid]) + red[2 * kHid + tid]) + red[3 * kHid + tid];
+    // dW1 = dZ1^T X (M = hidden unit in two halves, N = input feature,
+    // K = sample; both operands transposed) into columns [0, 2 k1)
+    if (tid == 0) {
+      for (int h = 0; h < 2; ++h)
+        lt_mma(tacc + (uint32_t)(h * L.k1), smem_u32(h1s) + 16u * (uint32_t)h * kA, 128, kA, 2u * 128u, smem_u32(xs),
+               128, kA, 2u * 128u, idesc_bf16_f32_t(kLtRows, L.k1, 1, 1), kLtRows / 16, false);
+      tc_commit(&bar_layer);
+    }
+    layer_out = true;
+    ok = __syncthreads_and(mbar_wait(&bar_layer, player, kTcTries));
+    player ^= 1u;
+    layer_out = !ok;
+    if (!ok) break;
+    tc_fence_after();
+    {
+      // dW1 rows (hidden unit j, n_in inputs) staged over the dead H1 / H2
+      // tiles with an odd row stride (conflict-free), then copied out: the
+      // block is contiguous in the partial row (coalesced)
+      const int quarter = warp & 3, h = warp >> 2, j = 128 * h + quarter * 32 + lane;
+      const int sn = L.n_in | 1;
+      float* st = reinterpret_cast<float*>(h1s);  // 256 x sn floats <= 70 KB of the 128 KB
+      for (int c = 0; c < L.k1; c += 32) {
+        float v[32];
+        tmem_ld32(tacc + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(h * L.k1 + c), v);
+#pragma unroll
+        for (int k = 0; k < 32; ++k)
+          if (c + k < L.n_in) st[j * sn + c + k] = v[k];
+      }
+      lt_sync();
+      for (int t = tid; t < kHid * L.n_in; t += kLtThreads) pg[P.w1 + t] = st[(t / L.n_in) * sn + t % L.n_in];
+    }
+    lt_sync();  // the tile's buffers and tensor memory are reused by the next tile
+  }
+  if (!ok && tid == 0) atomicOr(fail, kTdFailCopy);
+  if (tid == 0) {
+    S.drain();
+    if (layer_out) mbar_wait(&bar_layer, player, kTcTries);
+  }
+  lt_sync();
+  if (warp == 0) tmem_free(tacc, 512);
+}
+
 
 // ------------------------------------------------------------- host side
 
@@ -1664,7 +2302,11 @@ int rebuild_image(sg_qnet* q, const float* th, uint8_t* img, cudaStream_t st) {
   const int n = image_elems(q->IL);
   k_build_image<<<(n + 255) / 256, 256, 0, st>>>(th, img, q->IL, q->PL);
   SG_CUDA(cudaGetLastError());
-  return img == q->img ? refresh_tc_image(q, st) : SG_OK;
+  if (img == q->img) return refresh_tc_image(q, st);
+  // the target image's tensor-core copy (read by the tcgen05 learner)
+  k_tc_image<<<44, 256, 0, st>>>(q->img_t, q->IL, q->img_tc_t);
+  SG_CUDA(cudaGetLastError());
+  return SG_OK;
 }
 
 void free_qnet(sg_qnet* q) {
@@ -1681,6 +2323,9 @@ void free_qnet(sg_qnet* q) {
   cudaFree(q->y);
   cudaFree(q->idx);
   cudaFree(q->img_tc);
+  cudaFree(q->img_tc_t);
+  cudaFree(q->q2);
+  cudaFree(q->td_sync);
   delete q;
 }
 }  // namespace
@@ -1726,6 +2371,9 @@ extern "C" int sg_qnet_create(int32_t n_in, int32_t arch, int32_t max_batch, uin
   alloc((void**)&q->y, (size_t)q->max_batch * 4);
   alloc((void**)&q->idx, (size_t)q->max_batch * 4);
   alloc((void**)&q->img_tc, tc_img(q->IL.k1).bytes);
+  alloc((void**)&q->img_tc_t, tc_img(q->IL.k1).bytes);
+  alloc((void**)&q->q2, (size_t)2 * q->max_batch * 5 * 4);
+  alloc((void**)&q->td_sync, (size_t)(1 + (q->max_batch + kLtRows - 1) / kLtRows) * 4);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&q->sms, cudaDevAttrMultiProcessorCount, q->device);
   if (e != cudaSuccess) {
     free_qnet(q);
@@ -1746,6 +2394,8 @@ extern "C" int sg_qnet_create(int32_t n_in, int32_t arch, int32_t max_batch, uin
   if (e == cudaSuccess) rc = rebuild_image(q, q->master, q->img, 0);
   if (e == cudaSuccess && rc == SG_OK) e = cudaMemcpy(q->target, q->master, P * 4, cudaMemcpyDeviceToDevice);
   if (e == cudaSuccess && rc == SG_OK) e = cudaMemcpy(q->img_t, q->img, (size_t)q->IL.bytes, cudaMemcpyDeviceToDevice);
+  if (e == cudaSuccess && rc == SG_OK)
+    e = cudaMemcpy(q->img_tc_t, q->img_tc, tc_img(q->IL.k1).bytes, cudaMemcpyDeviceToDevice);
   if (e == cudaSuccess && rc == SG_OK) e = cudaDeviceSynchronize();
   if (e != cudaSuccess || rc != SG_OK) {
     free_qnet(q);
@@ -1762,7 +2412,8 @@ extern "C" int sg_qnet_create(int32_t n_in, int32_t arch, int32_t max_batch, uin
       (rc = set_smem_attr((const void*)k_rollout_q<1, true>, fwd_smem(widest))) ||
       (rc = set_smem_attr((const void*)k_rollout_q<2, true>, fwd_smem(widest, 32))) ||
       (rc = set_smem_attr((const void*)k_td_target, fwd_smem(widest))) ||
-      (rc = set_smem_attr((const void*)k_td_grad, grad_smem(widest)))) {
+      (rc = set_smem_attr((const void*)k_td_grad, grad_smem(widest))) ||
+      (rc = set_smem_attr((const void*)k_td_tc, kTcSmemLaunch))) {
     free_qnet(q);
     return rc;
   }
@@ -2085,14 +2736,27 @@ extern "C" int sg_td_train_step(sg_qnet_t q, sg_replay_t rp, int32_t batch, floa
   SG_RANGE("sg_td_train_step");
   if (!q || !rp || batch < 1 || batch > q->max_batch || rp->d.obs_dim != q->n_in) return SG_E_INVAL;
   if (!(gamma >= 0.0f && gamma <= 1.0f) || !(lr >= 0.0f)) return SG_E_INVAL;
-  const int nblk = (batch + kTile - 1) / kTile;
   SG_CUDA(cudaMemsetAsync(q->td_fail, 0, 4, stream));
-  k_td_target<<<nblk, kThreads, fwd_smem(q->IL), stream>>>(q->img, q->img_t, q->IL, rp->d, seed, q->step, batch,
-                                                            gamma, q->y, q->idx, q->td_fail);
-  SG_CUDA(cudaGetLastError());
-  k_td_grad<<<nblk, kThreads, grad_smem(q->IL), stream>>>(q->img, q->IL, q->PL, rp->d, q->idx, q->y, batch,
-                                                          q->partial, q->td_fail);
-  SG_CUDA(cudaGetLastError());
+  int nblk;
+  if (batch >= kLtMinBatch) {
+    // tcgen05 learner: 128-sample tiles, one partial gradient row per tile
+    const int ntiles = (batch + kLtRows - 1) / kLtRows;
+    nblk = ntiles;
+    SG_CUDA(cudaMemsetAsync(q->td_sync, 0, (size_t)(1 + ntiles) * 4, stream));
+    k_td_tc<<<std::min(4 * ntiles, q->sms), kLtThreads, kTcSmemLaunch, stream>>>(
+        q->img, q->img_t, q->img_tc, q->img_tc_t, q->IL, q->PL, rp->d, seed, q->step, batch, gamma, q->q2, q->idx,
+        q->td_sync, q->partial, q->td_fail);
+    SG_CUDA(cudaGetLastError());
+  } else {
+    // mma.sync learner: 16-sample tiles
+    nblk = (batch + kTile - 1) / kTile;
+    k_td_target<<<nblk, kThreads, fwd_smem(q->IL), stream>>>(q->img, q->img_t, q->IL, rp->d, seed, q->step, batch,
+                                                              gamma, q->y, q->idx, q->td_fail);
+    SG_CUDA(cudaGetLastError());
+    k_td_grad<<<nblk, kThreads, grad_smem(q->IL), stream>>>(q->img, q->IL, q->PL, rp->d, q->idx, q->y, batch,
+                                                            q->partial, q->td_fail);
+    SG_CUDA(cudaGetLastError());
+  }
   const int P = q->PL.total;
   k_adam<<<(P + 255) / 256, 256, 0, stream>>>(q->master, q->adam_m, q->adam_v, q->partial, nblk, q->PL, q->IL, q->img,
                                                q->step, lr, 0.9f, 0.999f, 1e-8f, loss_dev, grad_dev, batch,
@@ -2103,9 +2767,10 @@ extern "C" int sg_td_train_step(sg_qnet_t q, sg_replay_t rp, int32_t batch, floa
     k_step_advance<<<1, 1, 0, stream>>>(q->step, q->td_fail);
     SG_CUDA(cudaGetLastError());
     const int words = q->IL.bytes / 4;
-    const int n = P > words ? P : words;
+    const int tc_words = (int)(tc_img(q->IL.k1).bytes / 4);
+    const int n = std::max(P, std::max(words, tc_words));
     k_target_sync<<<(n + 255) / 256, 256, 0, stream>>>(q->step, target_every, q->master, q->target, q->img, q->img_t,
-                                                        P, words);
+                                                        P, words, q->img_tc, q->img_tc_t, tc_words);
     SG_CUDA(cudaGetLastError());
   }
   return SG_OK;

@@ -508,11 +508,13 @@ def test_td_gradient_finite_differences_at_batch_4096():
           + ", ".join(f"{k} {v:.2e}" for k, v in worst.items()))
 
 
-def test_td_step_with_invalid_action_changes_nothing():
+@pytest.mark.parametrize("batch", [256, 4096])
+def test_td_step_with_invalid_action_changes_nothing(batch):
     """A sampled transition whose action is outside the action table (written
     into the ring on purpose) makes the whole step fail: NaN loss and
-    gradient, parameters, Adam moments and the step count unchanged."""
-    g, q, rp, th_on, _ = _td_case(256, "dueling")
+    gradient, parameters, Adam moments and the step count unchanged (the
+    16-sample learner at 256, the tcgen05 learner at 4,096)."""
+    g, q, rp, th_on, _ = _td_case(batch, "dueling")
     s, s2, a, r, t = rp.read(0, rp.capacity)
     a = a.copy()
     a[::7] = 9
@@ -520,7 +522,7 @@ def test_td_step_with_invalid_action_changes_nothing():
     m0, v0, st0 = q.optimizer_state()
     loss = torch.zeros(1, device="cuda")
     grad = torch.zeros(q.n_params, device="cuda")
-    q.train_step(rp, 256, gamma=0.98, lr=1e-3, seed=3, loss=loss, grad=grad)
+    q.train_step(rp, batch, gamma=0.98, lr=1e-3, seed=3, loss=loss, grad=grad)
     torch.cuda.synchronize()
     assert np.isnan(loss.item()) and torch.isnan(grad).all()
     assert np.array_equal(q.get_params("online"), th_on)
@@ -529,7 +531,7 @@ def test_td_step_with_invalid_action_changes_nothing():
     # valid actions again: the next step updates
     a[::7] = 0
     rp.write(0, s, s2, a, r, t, rp.steps_recorded())
-    q.train_step(rp, 256, gamma=0.98, lr=1e-3, seed=3, loss=loss)
+    q.train_step(rp, batch, gamma=0.98, lr=1e-3, seed=3, loss=loss)
     torch.cuda.synchronize()
     assert np.isfinite(loss.item()) and q.optimizer_state()[2] == st0 + 1
 

@@ -6,8 +6,8 @@ fixed memory budget, another framework's allocator, contexts where cudaMalloc
 is not allowed): they pass parameters and a batch, and the library keeps its
 intermediates in a static device array.  Here its loss and gradient must equal
 those of sg_td_train_step (lr = 0) on the same transitions bit for bit (the
-same kernels in the same summation order), on two calls in a row (the shared
-scratch is reused); at the widest input (69) they must match the oracle's
+same kernels in the same summation order at these batches), on two calls in a
+row (the shared scratch is reused); at the widest input (69) they must match the oracle's
 bf16 recipe element by element; a batch with an action outside the table
 must give NaN; and oversized requests must be refused.
 """
@@ -83,6 +83,9 @@ def _theta(seed, n_in, scale):
 
 
 def test_noalloc_matches_regular_entry_point_twice():
+    """Two calls in a row, at batches 256 and 100: at batches up to 256 both
+    entry points run the same 16-sample kernels in the same summation order,
+    so loss and gradient are bit-equal."""
     g, q, rp = _setup()
     n_in = g.obs_dim
     for call, (batch, seed, s_on, s_tg) in enumerate(((256, 5, 21, 22), (100, 9, 23, 24))):
