@@ -387,7 +387,7 @@ def run_extras(flush, which, l2_read=None):
     w = workload("qnet4096")
     sim = Sim(wparams(w), w.maps(), w.env_map)
     sim.reset()
-    q = QNet(sim.obs_dim, w.extra["batch"], seed=1)
+    q = QNet(sim.obs_dim, 4096, seed=1)  # batches 256 (this workload) and 4,096 (the learned loop's)
     slots = w.extra["ring"] // sim.n
     rp = Replay(slots, sim.n, sim.obs_dim)
     eps = torch.from_numpy(w.eps).cuda()
@@ -452,7 +452,26 @@ def run_extras(flush, which, l2_read=None):
         ft()
     ms_t = _time_cuda(ft, 20, flush)
     out["td_train_step"] = {"batch": w.extra["batch"], "ms": ms_t, "samples_per_s": w.extra["batch"] / (ms_t / 1e3),
-                            "gpu_launches_per_call": 5, "loss": float(loss.item())}
+                            "gpu_launches_per_call": 5, "loss": float(loss.item()),
+                            "kernel": "k_td_target + k_td_grad (16-sample mma.sync tiles) + k_adam"}
+    # the learned loop's batch, 4,096: the tcgen05 learner (k_td_tc).  FLOPs
+    # per sample of the step's definition: three forwards (online and target
+    # on s', online on s) and the backward (dW1, dW2, dW3, dH1, dH2)
+    ft4 = lambda: q.train_step(rp, 4096, gamma=w.extra["gamma"], lr=w.extra["lr"],  # noqa: E731
+                               target_every=w.extra["target_every"], seed=3, loss=loss)
+    for _ in range(3):
+        ft4()
+    ms_t4 = _time_cuda(ft4, 20, flush)
+    n_in = sim.obs_dim
+    fwd = 2.0 * (n_in * 256 + 256 * 256 + 256 * 6)
+    bwd = 2.0 * (256 * n_in + 256 * 256 + 256 * 256 + 6 * 256 + 6 * 256)
+    flop = 4096 * (3 * fwd + bwd)
+    out["td_train_step_4096"] = {"batch": 4096, "ms": ms_t4, "samples_per_s": 4096 / (ms_t4 / 1e3),
+                                 "kernel": "k_td_tc (tcgen05, 128-sample tiles) + k_adam",
+                                 "roofline": {"bound": "tensor", "achieved": flop / (ms_t4 / 1e3) / 1e12,
+                                              "peak": peak_tf, "unit": "TFLOP/s",
+                                              "frac": flop / (ms_t4 / 1e3) / 1e12 / peak_tf,
+                                              "flop_per_step": flop}}
     del sim, q, rp
     return _run_extras_tail(out, flush, which)
 
