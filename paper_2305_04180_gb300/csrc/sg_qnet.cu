@@ -709,7 +709,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_qnet_forward_tc(const uint8_t
 template <int MT, bool kDyn>
 __global__ void __launch_bounds__(512 * MT, 1)
     k_rollout_q(const __grid_constant__ DevCfg c, SimPtrs p, const uint8_t* __restrict__ img, ImgLayout L, int K,
-                const float* __restrict__ eps, ReplayDev rp, int use_replay, const int* __restrict__ order,
+                const float* __restrict__ eps, ReplayDev rp, int use_replay, const int* __restrict__ order, int epc,
                 float* __restrict__ obs_out,
                 float* __restrict__ obs_seq, uint8_t* __restrict__ act_seq, float* __restrict__ rew_seq,
                 uint8_t* __restrict__ done_seq) {
@@ -729,9 +729,11 @@ __global__ void __launch_bounds__(512 * MT, 1)
   bf16* H1g = H1 + grp * 16 * kLdh;
   bf16* H2g = H2 + grp * 16 * kLdh;
   float* Og = O + grp * 16 * kOutPad;
-  // CTAs take envs grouped by map, so that one CTA's scans share cache lines
-  const int slot = blockIdx.x * kRows + warp;
-  const bool live = slot < c.n_envs;
+  // CTAs take envs grouped by map, so that one CTA's scans share cache lines;
+  // epc <= kRows envs per CTA (fewer than the tile when that spreads the
+  // envs over more SMs; the tile's other rows stay zero)
+  const int slot = blockIdx.x * epc + warp;
+  const bool live = warp < epc && slot < c.n_envs;
   const int env = live ? order[slot] : 0;
   const long long n = c.n_envs;
   EnvConst k;
@@ -2714,14 +2716,22 @@ int sg_rollout_eps_q(sg_sim* sim, int K, sg_qnet* q, const float* eps, sg_replay
     k_rollout_q_tc<<<grid, kQtThreads, qt_smem().bytes, stream>>>(
         sim->dc, sg_sim_ptrs(sim), q->img, q->img_tc, q->IL, K, eps, rd, rp ? 1 : 0, sim->map_order_dev, seg,
         seg > 0 ? sim->q_sync_dev : nullptr, obs, obs_seq, act_seq, rew_seq, done_seq);
-  } else if (mt == 2)
-    (dyn ? k_rollout_q<2, true> : k_rollout_q<2, false>)<<<(n + 31) / 32, 1024, fwd_smem(q->IL, 32), stream>>>(
-        sim->dc, sg_sim_ptrs(sim), q->img, q->IL, K, eps, rd, rp ? 1 : 0, sim->map_order_dev, obs, obs_seq, act_seq,
-        rew_seq, done_seq);
-  else
-    (dyn ? k_rollout_q<1, true> : k_rollout_q<1, false>)<<<(n + 15) / 16, 512, fwd_smem(q->IL), stream>>>(
-        sim->dc, sg_sim_ptrs(sim), q->img, q->IL, K, eps, rd, rp ? 1 : 0, sim->map_order_dev, obs, obs_seq, act_seq,
-        rew_seq, done_seq);
+  } else {
+    // envs per CTA: the full tile, or fewer (down to half of it) when the
+    // tiles would leave SMs idle (one CTA per SM: the staged image takes the
+    // shared memory); 4,096 envs: 152 CTAs of 27 instead of 128 of 32
+    const int rows = 16 * mt;
+    const int epc = (n + rows - 1) / rows < sms ? std::max(rows / 2, (n + sms - 1) / sms) : rows;
+    const int grid = (n + epc - 1) / epc;
+    if (mt == 2)
+      (dyn ? k_rollout_q<2, true> : k_rollout_q<2, false>)<<<grid, 1024, fwd_smem(q->IL, 32), stream>>>(
+          sim->dc, sg_sim_ptrs(sim), q->img, q->IL, K, eps, rd, rp ? 1 : 0, sim->map_order_dev, epc, obs, obs_seq,
+          act_seq, rew_seq, done_seq);
+    else
+      (dyn ? k_rollout_q<1, true> : k_rollout_q<1, false>)<<<grid, 512, fwd_smem(q->IL), stream>>>(
+          sim->dc, sg_sim_ptrs(sim), q->img, q->IL, K, eps, rd, rp ? 1 : 0, sim->map_order_dev, epc, obs, obs_seq,
+          act_seq, rew_seq, done_seq);
+  }
   SG_CUDA(cudaGetLastError());
   if (rp) {
     k_replay_advance<<<1, 1, 0, stream>>>(rp->d.steps, K);
