@@ -301,37 +301,55 @@ __device__ __forceinline__ Layout layout_of(const DevCfg& c, const MapDesc& m) {
 // the bounds-tested loop.  The same loop runs on a sector plane (see
 // MapDesc): its values are skips of the same meaning for the rays of its
 // sector, with the same zero border.
+// Conversions on the FP32 and integer pipes instead of the conversion unit:
+// for an integer or float v with |v| < 2^22, v + 1.5 * 2^23 lies in
+// [2^23, 2^24), where the floats are exactly the integers, so the bit pattern
+// of that sum minus the pattern of 1.5 * 2^23 is the integer.  (uint)k +
+// pattern, reinterpreted, minus 1.5 * 2^23 is (float)k; the sum rounded down
+// is floor(v).  Sample cells lie in [-2, 16386), the map offset iy * ld + ix
+// in int range, so it is taken modulo 2^32 from the two patterns (bias
+// folds in the two subtracted patterns).
+constexpr float kMarchMagic = 12582912.0f;
+constexpr uint32_t kMarchMagicBits = 0x4B400000u;
+
+// Whether a march from (x, y) takes the unbounded skipping loop.
+template <bool kUnitStep>
+__device__ __forceinline__ bool march_fast(int W, int H, float x, float y, int skip_ok) {
+  return (kUnitStep || skip_ok) && x >= 0.0f && y >= 0.0f && x < (float)W && y < (float)H;
+}
+
+// Skip value at sample k of the unbounded loop (0 = a hit there).
+template <bool kUnitStep>
+__device__ __forceinline__ int march_skip_at(const uint8_t* __restrict__ clr, int W, int H, int ld, uint32_t bias,
+                                             float x, float y, float ux, float uy, float delta, int k) {
+  const float kf = __uint_as_float((uint32_t)k + kMarchMagicBits) - kMarchMagic;
+  // with a unit step, (float)k * 1.0f is (float)k exactly
+  const float t = kUnitStep ? kf : kf * delta;
+  const uint32_t bx = __float_as_uint(__fadd_rd(fmaf(t, ux, x), kMarchMagic));
+  const uint32_t by = __float_as_uint(__fadd_rd(fmaf(t, uy, y), kMarchMagic));
+  // the sample cell (ix, iy) = (bx, by) - pattern(1.5 * 2^23), inside the border
+  if (!SG_IN_BOUNDS((int)(bx - kMarchMagicBits) >= -kClrBorder && (int)(by - kMarchMagicBits) >= -kClrBorder &&
+                    (int)(bx - kMarchMagicBits) < W + kClrBorder && (int)(by - kMarchMagicBits) < H + kClrBorder))
+    return 0;
+  return __ldg(clr + (int)(by * (uint32_t)ld + bx + bias));
+}
+__device__ __forceinline__ uint32_t march_bias(int ld) { return 0u - kMarchMagicBits * (uint32_t)(ld + 1); }
+
+// s1 >= 0: the caller checked march_fast and loaded sample 1's skip value
+// (march_skip_at, k = 1) ahead, so that its latency overlapped other work.
 template <bool kUnitStep>
 __device__ __forceinline__ int march(const uint8_t* __restrict__ clr, int W, int H, int ld, float x, float y,
-                                     float ux, float uy, float delta, int kmax, int skip_ok) {
+                                     float ux, float uy, float delta, int kmax, int skip_ok, int s1 = -1) {
   int k = 1;
-  if ((kUnitStep || skip_ok) && x >= 0.0f && y >= 0.0f && x < (float)W && y < (float)H) {
-    // Conversions on the FP32 and integer pipes instead of the conversion
-    // unit: for an integer or float v with |v| < 2^22, v + 1.5 * 2^23 lies in
-    // [2^23, 2^24), where the floats are exactly the integers, so the bit
-    // pattern of that sum minus the pattern of 1.5 * 2^23 is the integer.
-    // (uint)k + pattern, reinterpreted, minus 1.5 * 2^23 is (float)k; the
-    // sum rounded down is floor(v).  Sample cells lie in [-2, 16386), the
-    // map offset iy * ld + ix in int range, so it is taken modulo 2^32 from
-    // the two patterns (bias folds in the two subtracted patterns).
-    constexpr float kMagic = 12582912.0f;
-    constexpr uint32_t kMagicBits = 0x4B400000u;
-    const uint32_t bias = 0u - kMagicBits * (uint32_t)(ld + 1);
-    while (k <= kmax) {
-      const float kf = __uint_as_float((uint32_t)k + kMagicBits) - kMagic;
-      // with a unit step, (float)k * 1.0f is (float)k exactly
-      const float t = kUnitStep ? kf : kf * delta;
-      const uint32_t bx = __float_as_uint(__fadd_rd(fmaf(t, ux, x), kMagic));
-      const uint32_t by = __float_as_uint(__fadd_rd(fmaf(t, uy, y), kMagic));
-      // the sample cell (ix, iy) = (bx, by) - pattern(1.5 * 2^23), inside the border
-      if (!SG_IN_BOUNDS((int)(bx - kMagicBits) >= -kClrBorder && (int)(by - kMagicBits) >= -kClrBorder &&
-                        (int)(bx - kMagicBits) < W + kClrBorder && (int)(by - kMagicBits) < H + kClrBorder))
-        return k;
-      const int s = __ldg(clr + (int)(by * (uint32_t)ld + bx + bias));
+  if (s1 >= 0 || march_fast<kUnitStep>(W, H, x, y, skip_ok)) {
+    const uint32_t bias = march_bias(ld);
+    int s = s1 >= 0 ? s1 : march_skip_at<kUnitStep>(clr, W, H, ld, bias, x, y, ux, uy, delta, k);
+    for (;;) {
       if (s == 0) return k;
       k += s;
+      if (k > kmax) return kmax + 1;
+      s = march_skip_at<kUnitStep>(clr, W, H, ld, bias, x, y, ux, uy, delta, k);
     }
-    return kmax + 1;
   }
   while (k <= kmax) {
     const float t = kUnitStep ? (float)k : (float)k * delta;
@@ -634,21 +652,48 @@ __device__ __forceinline__ Noise noise_for(const EnvConst& k, float sigma, uint3
 // Normalised range of the beam at heading offset `off` from the pose (x, y,
 // phi), with noise sigma * nz; mn takes the minimum noise-free range.  With
 // kDyn the discs d are in the way too.
-template <bool kDyn = false>
-__device__ __forceinline__ float beam_at(const DevCfg& c, const EnvConst& k, float x, float y, float phi,
-                                         float sigma, float off, float nz, float& mn, const Discs* d = nullptr) {
+// A beam's direction, its skip values and, where the march takes the
+// unbounded loop, sample 1's skip value: issued before the noise draws of
+// the scan, so that the first (usually L1-missing) load's latency hides
+// behind them.
+struct BeamPre {
+  float ux, uy;
+  const uint8_t* skip;
+  int s1;  // -1: not loaded (the march starts as usual)
+};
+__device__ __forceinline__ BeamPre beam_pre(const DevCfg& c, const EnvConst& k, float x, float y, float phi,
+                                            float off) {
+  BeamPre b;
   const float beta = phi + off;
   float sn, cs;
   f_sincos(beta, sn, cs);
+  b.ux = -cs;
+  b.uy = -sn;
   // the skip values of this beam's sector: u = -(cos beta, sin beta) has
   // angle beta + pi, whose sector index is floor(beta n_sec / 2pi) mod n_sec
-  const uint8_t* skip =
-      c.n_sec > 1 ? k.sec + (long long)(__float2int_rd(beta * c.sec_scale) & (c.n_sec - 1)) * k.m.sec_plane : k.clr;
+  b.skip = c.n_sec > 1 ? k.sec + (long long)(__float2int_rd(beta * c.sec_scale) & (c.n_sec - 1)) * k.m.sec_plane
+                       : k.clr;
+  b.s1 = -1;
+  if (c.delta == 1.0f) {
+    if (march_fast<true>(k.m.w, k.m.h, x, y, 1))
+      b.s1 = march_skip_at<true>(b.skip, k.m.w, k.m.h, k.m.clr_ld, march_bias(k.m.clr_ld), x, y, b.ux, b.uy, c.delta, 1);
+  } else if (march_fast<false>(k.m.w, k.m.h, x, y, c.skip_ok)) {
+    b.s1 = march_skip_at<false>(b.skip, k.m.w, k.m.h, k.m.clr_ld, march_bias(k.m.clr_ld), x, y, b.ux, b.uy, c.delta, 1);
+  }
+  return b;
+}
+
+template <bool kDyn = false>
+__device__ __forceinline__ float beam_at(const DevCfg& c, const EnvConst& k, float x, float y, float phi,
+                                         float sigma, float off, float nz, float& mn, const Discs* d = nullptr,
+                                         const BeamPre* pre = nullptr) {
+  const BeamPre b = pre ? *pre : beam_pre(c, k, x, y, phi, off);
+  const float ux = b.ux, uy = b.uy;
   int h = c.delta == 1.0f
-              ? march<true>(skip, k.m.w, k.m.h, k.m.clr_ld, x, y, -cs, -sn, c.delta, c.kmax, 1)
-              : march<false>(skip, k.m.w, k.m.h, k.m.clr_ld, x, y, -cs, -sn, c.delta, c.kmax, c.skip_ok);
+              ? march<true>(b.skip, k.m.w, k.m.h, k.m.clr_ld, x, y, ux, uy, c.delta, c.kmax, 1, b.s1)
+              : march<false>(b.skip, k.m.w, k.m.h, k.m.clr_ld, x, y, ux, uy, c.delta, c.kmax, c.skip_ok, b.s1);
   if (kDyn)
-    h = c.delta == 1.0f ? discs_first<true>(c, *d, x, y, -cs, -sn, h) : discs_first<false>(c, *d, x, y, -cs, -sn, h);
+    h = c.delta == 1.0f ? discs_first<true>(c, *d, x, y, ux, uy, h) : discs_first<false>(c, *d, x, y, ux, uy, h);
   float r = fminf((float)h * c.delta, c.range_max);
   mn = fminf(mn, r);
   if (sigma > 0.0f) {
@@ -956,7 +1001,9 @@ static_assert(sizeof(StepScanRec) == 128, "step scan record is eight 16-byte wor
 
 // Scan of one pose by the warp for an env of map m with nb beams: this
 // lane's normalised ranges into b0 / b1; returns the minimum noise-free range.
-template <bool kDyn = false>
+// kPre: the first beam's first march load is issued before the noise draws
+// (beam_pre); the kernels with little register room leave it off.
+template <bool kDyn = false, bool kPre = false>
 __device__ __forceinline__ float scan_env(const DevCfg& c, const SimPtrs& p, const MapDesc& m, int nb, float stepb,
                                           float x, float y, float phi, float sigma, uint64_t nk, int lane,
                                           float& b0, float& b1, const Discs* d = nullptr) {
@@ -967,13 +1014,15 @@ __device__ __forceinline__ float scan_env(const DevCfg& c, const SimPtrs& p, con
   k.nb = nb;
   const float off0 = (float)lane * stepb - c.half_fov;
   const float off1 = (float)(lane + 32) * stepb - c.half_fov;
+  BeamPre p0;
+  if (kPre && lane < nb) p0 = beam_pre(c, k, x, y, phi, off0);
   float n0 = 0.0f, n1 = 0.0f;
   if (sigma > 0.0f) {
     n0 = box_muller(sm_at(nk, (uint64_t)lane));
     if (nb > 32) n1 = box_muller(sm_at(nk, (uint64_t)(lane + 32)));
   }
   float mn = c.range_max;
-  b0 = lane < nb ? beam_at<kDyn>(c, k, x, y, phi, sigma, off0, n0, mn, d) : 1.0f;
+  b0 = lane < nb ? beam_at<kDyn>(c, k, x, y, phi, sigma, off0, n0, mn, d, kPre ? &p0 : nullptr) : 1.0f;
   b1 = lane + 32 < nb ? beam_at<kDyn>(c, k, x, y, phi, sigma, off1, n1, mn, d) : 1.0f;
   return __uint_as_float(__reduce_min_sync(kFull, __float_as_uint(mn)));
 }

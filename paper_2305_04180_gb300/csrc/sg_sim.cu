@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(32 * kStepWarps, 4) k_step(const __grid_consta
     const uint32_t de = r.done;
     float b0, b1;
     const DiscRec* de_ = kDyn ? &drec[warp][e] : nullptr;
-    const float mn = scan_env<kDyn>(c, p, m, r.nb, r.stepb, r.ax, r.ay, r.aphi, r.asigma,
+    const float mn = scan_env<kDyn, true>(c, p, m, r.nb, r.stepb, r.ax, r.ay, r.aphi, r.asigma,
                                     ((uint64_t)r.anhi << 32) | r.anlo, lane, b0, b1, kDyn ? &de_->a : nullptr);
     float rw;
     if (de & 1u)
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(32 * kStepWarps, 4) k_step(const __grid_consta
       write_row(obs + (long long)ie * c.obs_dim, b0, b1, r.exa, c.B, lane);
     } else {
       if (term) write_row(term + (long long)ie * c.obs_dim, b0, b1, r.exa, c.B, lane);
-      scan_env<kDyn>(c, p, m, r.nb, r.stepb, r.bx, r.by, r.bphi, r.bsigma, ((uint64_t)r.bnhi << 32) | r.bnlo, lane,
+      scan_env<kDyn, true>(c, p, m, r.nb, r.stepb, r.bx, r.by, r.bphi, r.bsigma, ((uint64_t)r.bnhi << 32) | r.bnlo, lane,
                      b0, b1, kDyn ? &de_->b : nullptr);
       write_row(obs + (long long)ie * c.obs_dim, b0, b1, r.exb, c.B, lane);
     }
