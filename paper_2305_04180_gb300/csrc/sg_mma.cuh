@@ -81,5 +81,14 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<const uint32_t*>(&v);
 }
+// max(lo, 0) and max(hi, 0) rounded to BF16 (nearest even) in one
+// conversion: ReLU commutes with the monotone rounding, so this equals
+// pack_bf16x2(fmaxf(lo, 0), fmaxf(hi, 0)) up to the sign of a zero
+// (a NaN stays NaN).
+__device__ __forceinline__ uint32_t pack_bf16x2_relu(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;\n" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
 
 }  // namespace sg

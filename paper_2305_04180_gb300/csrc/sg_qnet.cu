@@ -392,47 +392,56 @@ __device__ __forceinline__ void obs_to_tile(bf16* row, const ObsRegs& o, int B, 
 
 // ------------------------------------------------ tcgen05 batched forward
 // Q[M][5] of obs[M][n_in] on the fifth-generation tensor cores, 128 rows per
-// tile.  A persistent CTA (one per SM) keeps W1 and W3 in shared memory and
-// streams the two 128-unit halves of W2 per tile; all weights arrive by bulk
-// asynchronous copies (TMA) from a copy of the online network in the
-// tensor cores' shared-memory layout (k_tc_image), completing on an
-// mbarrier.  Per tile: the threads convert the 128 input rows to BF16, one
-// thread issues the MMAs of a layer (tcgen05.mma, FP32 accumulators in 256
-// tensor-memory columns) and commits them to a second mbarrier, the eight
-// warps read the accumulators back (tcgen05.ld; warps w and w + 4 take the
-// rows of lane quarter w % 4 and half of the columns each) for the bias /
-// ReLU / BF16 epilogue that writes the next layer's A operand.  Shared memory:
-//   X 128 x k1 | W1 256 x k1 | H 128 x 256 (H1, then H2) | W2 half 128 x 256 | W3 16 x 256
+// tile.  A persistent CTA (one per SM) holds all weights in shared memory
+// (W1, W2, W3: one set of bulk asynchronous copies (TMA) from a copy of the
+// online network in the tensor cores' layout, k_tc_image) and the whole
+// 512-column tensor memory.  Per tile: the threads convert the 128 input
+// rows to BF16 (X, shared memory); one thread issues the MMAs of a layer
+// (tcgen05.mma, FP32 accumulators in tensor memory) and commits them to an
+// mbarrier; the eight warps read the accumulators back (tcgen05.ld; warps w
+// and w + 4 take the rows of lane quarter w % 4 and half of the columns
+// each), add the bias, apply ReLU, round to BF16 and store the pairs back
+// into the first half of the columns they read (tcgen05.st): the hidden
+// activations never leave tensor memory and are the A operand of the next
+// layer's MMAs.  Tensor-memory columns:
+//   [0, 256)   layer 1 accumulators; H1 in [0, 64) (units 0..127) and [128, 192) (128..255)
+//   [256, 512) layer 2 accumulators; H2 in [256, 320) and [384, 448); head accumulators at 320
+// The tensor cores run the next tile's layer 1 beside this tile's layer-2
+// epilogue, and this tile's head beside the next tile's layer-1 epilogue;
+// only layer 2 (N = 256) is waited for by all warps.
+// Shared memory: X 128 x k1 | W1 256 x k1 | W2 256 x 256 | W3 16 x 256,
 // in the canonical K-major layout of sg_tc.cuh.  Same BF16 recipe as the
 // mma.sync kernels (BF16 inputs, weights and hidden activations, FP32 sums);
 // only the summation order differs.
 constexpr int kTcRows = 128;
-constexpr int kTcThreads = 256;  // 8 warps: warps w and w + 4 share lane quarter w % 4 and split the columns
 constexpr uint32_t kTcTries = 1u << 24;  // bound of every mbarrier wait (polls)
 // The launch takes the whole shared memory of an SM (one CTA per SM either
 // way), so that every descriptor-addressed byte lies inside the allocation.
 constexpr uint32_t kTcSmemLaunch = 227u * 1024u - 4096u;
 
 struct TcSmem {
-  uint32_t x, w1, h, w2, w3, bytes;
+  uint32_t x, w1, w2, w3, bytes;
 };
 __host__ __device__ inline uint32_t tc_up(uint32_t v) { return (v + 1023u) & ~1023u; }
 __host__ __device__ inline TcSmem tc_smem(int k1) {
   TcSmem t;
   t.x = 0;
   t.w1 = tc_up(t.x + (uint32_t)(kTcRows * k1 * 2));
-  t.h = tc_up(t.w1 + (uint32_t)(kHid * k1 * 2));
-  t.w2 = tc_up(t.h + (uint32_t)(kTcRows * kHid * 2));
-  t.w3 = tc_up(t.w2 + (uint32_t)(128 * kHid * 2));
+  t.w2 = tc_up(t.w1 + (uint32_t)(kHid * k1 * 2));
+  t.w3 = tc_up(t.w2 + (uint32_t)(kHid * kHid * 2));
   t.bytes = tc_up(t.w3 + (uint32_t)(16 * kHid * 2));
   return t;
 }
+// k1 <= 80 (n_in <= 69): 197 KB, inside the launch's shared memory
+static_assert(kTcRows * 80 * 2 + 1024 + kHid * 80 * 2 + kHid * kHid * 2 + 16 * kHid * 2 + 1024 <= kTcSmemLaunch,
+              "tcgen05 forward: operands exceed the shared memory");
 // The weight copy in global memory: blocks identical to their shared-memory
 // images, so that each is one bulk copy.
 // For the fused rollout also W1 in two 128-row halves and W2 in four
-// 64-row quarters (each its own canonical operand).
+// 64-row quarters, and for the batched forward W2 as one 256-row operand
+// (each its own canonical operand).
 struct TcImg {
-  uint32_t w1, w2a, w2b, w3, w1h, w2q, bytes;
+  uint32_t w1, w2a, w2b, w3, w1h, w2q, w2f, bytes;
 };
 __host__ __device__ inline TcImg tc_img(int k1) {
   TcImg t;
@@ -442,7 +451,8 @@ __host__ __device__ inline TcImg tc_img(int k1) {
   t.w3 = t.w2b + 128u * kHid * 2u;
   t.w1h = t.w3 + 16u * kHid * 2u;
   t.w2q = t.w1h + (uint32_t)(kHid * k1 * 2);
-  t.bytes = t.w2q + (uint32_t)(kHid * kHid * 2);
+  t.w2f = t.w2q + (uint32_t)(kHid * kHid * 2);
+  t.bytes = t.w2f + (uint32_t)(kHid * kHid * 2);
   return t;
 }
 
@@ -466,9 +476,10 @@ __global__ void k_tc_image(const uint8_t* __restrict__ img, ImgLayout L, uint8_t
       const int j = c - n1, n = j % kHid, kg = j / kHid;
       v = __ldg(reinterpret_cast<const uint4*>(img + L.w2 + ((size_t)n * kLdh + kg * 8) * 2));
       dst = n < 128 ? T.w2a + kmajor_offset(n, kg * 8, 128) : T.w2b + kmajor_offset(n - 128, kg * 8, 128);
-      // and in its 64-row quarter
+      // in its 64-row quarter and in the 256-row operand
       *reinterpret_cast<uint4*>(out + T.w2q + (uint32_t)((n >> 6) * 64 * kHid * 2) +
                                 kmajor_offset(n & 63, kg * 8, 64)) = v;
+      *reinterpret_cast<uint4*>(out + T.w2f + kmajor_offset(n, kg * 8, kHid)) = v;
     } else {
       const int j = c - n1 - n2, n = j % 16, kg = j / 16;
       if (n < kOutPad) v = __ldg(reinterpret_cast<const uint4*>(img + L.w3 + ((size_t)n * kLdh + kg * 8) * 2));
@@ -500,203 +511,284 @@ __device__ __forceinline__ void tc_epilogue_hidden(uint32_t tacc, const float* b
   }
 }
 
-// Issue one layer: D[tacc] = A (128 rows) x B (Rb rows)^T over K, then
-// commit to the barrier (thread 0 only).
-__device__ __forceinline__ void tc_layer(uint32_t tacc, const uint8_t* a, const uint8_t* b, int Rb, int K,
-                                         uint64_t* bar) {
-  const uint32_t idesc = idesc_bf16_f32(kTcRows, Rb);
-  const uint32_t sa = smem_u32(a), sb = smem_u32(b);
-  const uint32_t la = kTcRows * 16, lb = (uint32_t)Rb * 16;
-  for (int ks = 0; ks < K / 16; ++ks)
-    tc_mma_bf16(tacc, smem_desc(sa + (uint32_t)ks * 2 * la, la, 128), smem_desc(sb + (uint32_t)ks * 2 * lb, lb, 128),
-                idesc, ks > 0 ? 1u : 0u);
-  tc_commit(bar);
+// Epilogue warps of the batched forward: four per lane quarter (warp w
+// takes lanes 32 (w % 4) .. and the kTfCols accumulator columns of group
+// w / 4).
+constexpr int kTfEpiWarps = 16;
+constexpr int kTfEpiThreads = kTfEpiWarps * 32;
+constexpr int kTfThreads = kTfEpiThreads + 32;  // + the MMA-issue warp
+constexpr int kTfCols = kHid / (kTfEpiWarps / 4);
+static_assert(kTfCols % 32 == 0, "each epilogue warp's columns hold whole 16-column chunks and head accumulators");
+
+// Hidden-layer epilogue in tensor memory: this thread's lane (row
+// 32 (warp % 4) + lane), accumulator columns [tacc + kTfCols g, + kTfCols) for
+// g = warp / 4, plus the bias, ReLU, rounded to BF16 pairs and stored over the
+// first half of those columns (units kTfCols g + 2 c, + 1 in column
+// tacc + kTfCols g + c).  The load of the next 16 columns is in flight while
+// a chunk is converted; a chunk's 8 output columns lie below every column
+// still to be read, and each load completes before the columns it frees are
+// written.  Returns once the stores have completed.
+__device__ __forceinline__ void tc_epilogue_tmem(uint32_t tacc, const float* bias, int warp) {
+  constexpr int kChunks = kTfCols / 16;
+  const uint32_t t = tacc + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((warp >> 2) * kTfCols);
+  const float4* b4 = reinterpret_cast<const float4*>(bias + (warp >> 2) * kTfCols);
+  uint32_t r[2][16];
+  tmem_ld16_nowait(t, r[0]);
+  tmem_ld_wait();
+#pragma unroll
+  for (int ch = 0; ch < kChunks; ++ch) {
+    if (ch + 1 < kChunks) tmem_ld16_nowait(t + (uint32_t)(16 * (ch + 1)), r[(ch + 1) & 1]);
+    const uint32_t(&v)[16] = r[ch & 1];
+    uint32_t w[8];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float4 bb = b4[4 * ch + j];
+      w[2 * j] = pack_bf16x2_relu(__uint_as_float(v[4 * j]) + bb.x, __uint_as_float(v[4 * j + 1]) + bb.y);
+      w[2 * j + 1] = pack_bf16x2_relu(__uint_as_float(v[4 * j + 2]) + bb.z, __uint_as_float(v[4 * j + 3]) + bb.w);
+    }
+    tmem_st8(t + (uint32_t)(8 * ch), w);
+    if (ch + 1 < kChunks) tmem_ld_wait();
+  }
+  tmem_st_wait();
+}
+// Tensor-memory column (relative to the layer's accumulators) of K step ks
+// of the packed activations, and of head accumulator q (four of 16 columns
+// in the halves the epilogue leaves free).
+__host__ __device__ constexpr uint32_t tf_a_col(int ks) {
+  return (uint32_t)((ks / (kTfCols / 16)) * kTfCols + (ks % (kTfCols / 16)) * 8);
+}
+__host__ __device__ constexpr uint32_t tf_head_col(int q) {
+  return (uint32_t)(kTfCols / 2 + (q / (kTfCols / 32)) * kTfCols + (q % (kTfCols / 32)) * 16);
 }
 
-// Input rows of a tile into the X operand (BF16, zero padded); the two
-// threads of a row take alternate 8-column groups.
-__device__ __forceinline__ void tc_load_x(uint8_t* xs, const float* __restrict__ obs, const ImgLayout& L, int M,
-                                          int tile, int tid) {
-  const int row = tid & (kTcRows - 1), grow = tile * kTcRows + row;
-  for (int kg = tid >> 7; kg < L.k1 / 8; kg += 2) {
-    float v[8];
+// One layer from a tensor-memory A operand (the packed activations of
+// tc_epilogue_tmem with accumulators at column a, K = 256):
+// D[d] = A x B^T for B in shared memory of Rb rows (K-major, canonical);
+// one thread.
+__device__ __forceinline__ void tc_layer_ta(uint32_t d, uint32_t a, uint32_t b_smem, int Rb) {
+  const uint32_t idesc = idesc_bf16_f32(kTcRows, Rb);
+  const uint32_t lb = (uint32_t)Rb * 16;
+#pragma unroll 1
+  for (int ks = 0; ks < kHid / 16; ++ks)
+    tc_mma_bf16_ta(d, a + tf_a_col(ks), smem_desc(b_smem + (uint32_t)ks * 2 * lb, lb, 128), idesc, ks > 0 ? 1u : 0u);
+}
+
+// Input rows of a tile into the X operand (BF16, zero padded) in two steps:
+// tc_fetch_x loads this thread's values (the kTfEpiThreads / 128 threads of
+// a row take interleaved 8-column groups, at most kTcMaxGroups each),
+// tc_store_x converts and stores them.
+constexpr int kTcXStride = kTfEpiThreads / kTcRows;
+constexpr int kTcMaxGroups = (80 / 8 + kTcXStride - 1) / kTcXStride;
+struct TcXRegs {
+  float v[kTcMaxGroups][8];
+};
+__device__ __forceinline__ void tc_fetch_x(TcXRegs& x, const float* __restrict__ obs, const ImgLayout& L, int M,
+                                           int tile, int tid) {
+  const int row = tid & (kTcRows - 1), grow = tile * kTcRows + row, ng = L.k1 / 8;
+  const float* src = obs + (long long)grow * L.n_in;
+#pragma unroll
+  for (int it = 0; it < kTcMaxGroups; ++it) {
+    const int kg = (tid >> 7) + kTcXStride * it;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const int k = kg * 8 + j;
-      v[j] = (grow < M && k < L.n_in) ? __ldg(obs + (long long)grow * L.n_in + k) : 0.0f;
+      x.v[it][j] = (kg < ng && grow < M && k < L.n_in) ? __ldg(src + k) : 0.0f;
     }
-    *reinterpret_cast<uint4*>(xs + kmajor_offset(row, kg * 8, kTcRows)) =
-        make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
+  }
+}
+__device__ __forceinline__ void tc_store_x(uint8_t* xs, const TcXRegs& x, const ImgLayout& L, int tid) {
+  const int row = tid & (kTcRows - 1), ng = L.k1 / 8;
+#pragma unroll
+  for (int it = 0; it < kTcMaxGroups; ++it) {
+    const int kg = (tid >> 7) + kTcXStride * it;
+    if (kg < ng)
+      *reinterpret_cast<uint4*>(xs + kmajor_offset(row, kg * 8, kTcRows)) =
+          make_uint4(pack_bf16x2(x.v[it][0], x.v[it][1]), pack_bf16x2(x.v[it][2], x.v[it][3]),
+                     pack_bf16x2(x.v[it][4], x.v[it][5]), pack_bf16x2(x.v[it][6], x.v[it][7]));
   }
   fence_async_smem();
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1) k_qnet_forward_tc(const uint8_t* __restrict__ img,
+// Warps 0..15 run the epilogues, convert the inputs and write Q; warp 16
+// (one lane) copies the weights and issues every MMA, so that the issue, which
+// waits while the tensor cores' queue is full, never holds up an epilogue.
+// The two sides meet on mbarriers, one phase per tile each: bar_x (X
+// stored), bar_h1 (H1 stored and the previous tile's head read), bar_h2 (H2
+// stored), and the MMA commits bar_l1, bar_l2, bar_hd (layer 1, layer 2,
+// head complete).  Order on the tensor cores per tile t: layer 2 (t) once H1
+// (t) is stored and the head of t - 1 is read; layer 1 (t + 1) once layer 2
+// (t) is complete and X (t + 1) is stored; the head (t) once H2 (t) is stored.
+__global__ void __launch_bounds__(kTfThreads, 1) k_qnet_forward_tc(const uint8_t* __restrict__ img,
                                                                 const uint8_t* __restrict__ timg, ImgLayout L,
                                                                 const float* __restrict__ obs, int M,
                                                                 float* __restrict__ qout) {
   extern __shared__ __align__(1024) uint8_t tsm[];
-  __shared__ uint64_t bar_mma, bar_ld;
+  __shared__ uint64_t bar_w, bar_l1, bar_l2, bar_hd, bar_x, bar_h1, bar_h2, bar_drain;
   __shared__ uint32_t tslot;
-  __shared__ float sb1[kHid], sb2[kHid], sb3[kOutPad];
+  __shared__ int s_fail;
+  __shared__ __align__(16) float sb1[kHid];
+  __shared__ __align__(16) float sb2[kHid];
+  __shared__ float sb3[kOutPad];
   const TcSmem T = tc_smem(L.k1);
   const TcImg G = tc_img(L.k1);
   uint8_t* xs = tsm + T.x;
-  uint8_t* w1s = tsm + T.w1;
-  uint8_t* hs = tsm + T.h;
-  uint8_t* w2s = tsm + T.w2;
-  uint8_t* w3s = tsm + T.w3;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int K1 = L.k1;
+  const int tid = threadIdx.x, warp = tid >> 5;
   const int ntiles = (M + kTcRows - 1) / kTcRows;
-  for (int i = tid; i < kHid; i += kTcThreads) {
+  // this CTA's tiles: blockIdx.x + i gridDim.x, i < my_tiles
+  const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  for (int i = tid; i < kHid; i += kTfThreads) {
     sb1[i] = __ldg(reinterpret_cast<const float*>(img + L.b1) + i);
     sb2[i] = __ldg(reinterpret_cast<const float*>(img + L.b2) + i);
   }
   if (tid < kOutPad) sb3[tid] = __ldg(reinterpret_cast<const float*>(img + L.b3) + tid);
-  const float* b1 = sb1;
-  const float* b2 = sb2;
-  const float* b3 = sb3;
-  if (warp == 0) tmem_alloc(&tslot, 256);
+  if (warp == 0) tmem_alloc(&tslot, 512);
   if (tid == 0) {
-    mbar_init(&bar_mma, 1);
-    mbar_init(&bar_ld, 1);
+    mbar_init(&bar_w, 1);
+    mbar_init(&bar_l1, 1);
+    mbar_init(&bar_l2, 1);
+    mbar_init(&bar_hd, 1);
+    mbar_init(&bar_drain, 1);
+    mbar_init(&bar_x, kTfEpiThreads);
+    mbar_init(&bar_h1, kTfEpiThreads);
+    mbar_init(&bar_h2, kTfEpiThreads);
+    s_fail = 0;
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tacc = tslot;
-  bool ld_out = (int)blockIdx.x < ntiles, mma_out = false;  // completions still to come
-  if (tid == 0 && ld_out) {
-    // resident W1 and W3, and the first tile's W2 half 0
-    mbar_expect_tx(&bar_ld, G.w2a + 128u * kHid * 2u + 16u * kHid * 2u);
-    bulk_g2s(w1s, timg + G.w1, G.w2a, &bar_ld);
-    bulk_g2s(w3s, timg + G.w3, 16u * kHid * 2u, &bar_ld);
-    bulk_g2s(w2s, timg + G.w2a, 128u * kHid * 2u, &bar_ld);
-  }
-  uint32_t pm = 0, pl = 0;  // phases of the two barriers
-  bool ok = true;
-  const int row = tid & (kTcRows - 1);  // this thread's row of the tile
-  // the first tile's inputs; later tiles' inputs are converted while the
-  // previous tile's first layer-2 MMAs run (X is free once layer 1 is done)
-  if ((int)blockIdx.x < ntiles) tc_load_x(xs, obs, L, M, blockIdx.x, tid);
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int grow = tile * kTcRows + row;
-    if (ok) {
-      tc_fence_before();
-      __syncthreads();
-      tc_fence_after();
-      // this tile's W2 half 0 (and on the first tile W1, W3) has arrived
-      ok = __syncthreads_and(mbar_wait(&bar_ld, pl, kTcTries));
+  const uint32_t tacc = tslot, tacc2 = tacc + 256u;
+  volatile int* fail = &s_fail;
+  if (warp == kTfEpiThreads / 32) {
+    if ((tid & 31) == 0 && my_tiles > 0) {
+      // ---- MMA issue
+      const uint32_t sx = smem_u32(xs), sw1 = smem_u32(tsm + T.w1), sw2 = smem_u32(tsm + T.w2),
+                     sw3 = smem_u32(tsm + T.w3);
+      auto issue_l1 = [&]() {
+        const uint32_t idesc = idesc_bf16_f32(kTcRows, kHid);
+        const uint32_t la = kTcRows * 16, lb = kHid * 16;
+        for (int ks = 0; ks < L.k1 / 16; ++ks)
+          tc_mma_bf16(tacc, smem_desc(sx + (uint32_t)ks * 2 * la, la, 128),
+                      smem_desc(sw1 + (uint32_t)ks * 2 * lb, lb, 128), idesc, ks > 0 ? 1u : 0u);
+        tc_commit(&bar_l1);
+      };
+      // the resident weights: W1, W2 (one 256-row operand), W3
+      mbar_expect_tx(&bar_w, G.w2a + kHid * kHid * 2u + 16u * kHid * 2u);
+      bulk_g2s(tsm + T.w1, timg + G.w1, G.w2a, &bar_w);
+      bulk_g2s(tsm + T.w2, timg + G.w2f, kHid * kHid * 2u, &bar_w);
+      bulk_g2s(tsm + T.w3, timg + G.w3, 16u * kHid * 2u, &bar_w);
+      bool ok = mbar_wait_or_fail(&bar_w, 0, kTcTries, fail) && mbar_wait_or_fail(&bar_x, 0, kTcTries, fail);
       if (ok) {
-        pl ^= 1u;
-        ld_out = false;
+        tc_fence_after();
+        issue_l1();
       }
-    }
-    if (ok) {
-      if (tid == 0) tc_layer(tacc, xs, w1s, kHid, K1, &bar_mma);
-      mma_out = true;
-      ok = __syncthreads_and(mbar_wait(&bar_mma, pm, kTcTries));
-      if (ok) {
-        pm ^= 1u;
-        mma_out = false;
-      }
-    }
-    if (ok) {
-      tc_fence_after();
-      tc_epilogue_hidden(tacc, b1, hs, warp, lane);
-      fence_async_smem();
-      tc_fence_before();
-      __syncthreads();
-      tc_fence_after();
-      // layer 2, units 0..127 into columns 0..127
-      if (tid == 0) tc_layer(tacc, hs, w2s, 128, kHid, &bar_mma);
-      mma_out = true;
-      if (tile + (int)gridDim.x < ntiles) tc_load_x(xs, obs, L, M, tile + gridDim.x, tid);
-      ok = __syncthreads_and(mbar_wait(&bar_mma, pm, kTcTries));
-      if (ok) {
-        pm ^= 1u;
-        mma_out = false;
-      }
-    }
-    if (ok) {
-      // half 0 is consumed: half 1 over it, units 128..255 into columns 128..255
-      if (tid == 0) {
-        mbar_expect_tx(&bar_ld, 128u * kHid * 2u);
-        bulk_g2s(w2s, timg + G.w2b, 128u * kHid * 2u, &bar_ld);
-      }
-      ld_out = true;
-      ok = __syncthreads_and(mbar_wait(&bar_ld, pl, kTcTries));
-      if (ok) {
-        pl ^= 1u;
-        ld_out = false;
-      }
-    }
-    if (ok) {
-      if (tid == 0) tc_layer(tacc + 128u, hs, w2s, 128, kHid, &bar_mma);
-      mma_out = true;
-      ok = __syncthreads_and(mbar_wait(&bar_mma, pm, kTcTries));
-      if (ok) {
-        pm ^= 1u;
-        mma_out = false;
-      }
-    }
-    if (ok) {
-      // the next tile's W2 half 0 streams in while this tile finishes
-      if (tile + (int)gridDim.x < ntiles) {
-        if (tid == 0) {
-          mbar_expect_tx(&bar_ld, 128u * kHid * 2u);
-          bulk_g2s(w2s, timg + G.w2a, 128u * kHid * 2u, &bar_ld);
+      for (int it = 0; ok && it < my_tiles; ++it) {
+        const uint32_t par = (uint32_t)it & 1u;
+        // layer 2 (t): D[256, 512) = H1 W2^T, N = 256
+        ok = mbar_wait_or_fail(&bar_h1, par, kTcTries, fail);
+        if (!ok) break;
+        tc_fence_after();
+        tc_layer_ta(tacc2, tacc, sw2, kHid);
+        tc_commit(&bar_l2);
+        // layer 1 (t + 1) over H1 (t), once layer 2 (t) has read it
+        if (it + 1 < my_tiles) {
+          ok = mbar_wait_or_fail(&bar_x, par ^ 1u, kTcTries, fail) && mbar_wait_or_fail(&bar_l2, par, kTcTries, fail);
+          if (!ok) break;
+          tc_fence_after();
+          issue_l1();
         }
-        ld_out = true;
+        // head (t): N = 16 (6 used) into four accumulators in layer-2
+        // columns the epilogue has read and left free, K step ks into
+        // accumulator ks % 4
+        ok = mbar_wait_or_fail(&bar_h2, par, kTcTries, fail);
+        if (!ok) break;
+        tc_fence_after();
+        {
+          const uint32_t idesc = idesc_bf16_f32(kTcRows, 16);
+#pragma unroll 1
+          for (int ks = 0; ks < kHid / 16; ++ks)
+            tc_mma_bf16_ta(tacc2 + tf_head_col(ks & 3), tacc2 + tf_a_col(ks),
+                           smem_desc(sw3 + (uint32_t)ks * 2 * 256, 256, 128), idesc, ks >= 4 ? 1u : 0u);
+        }
+        tc_commit(&bar_hd);
       }
-      tc_fence_after();
-      tc_epilogue_hidden(tacc, b2, hs, warp, lane);  // H2 over H1 (layer 2 is complete)
-      fence_async_smem();
+      // every MMA of this thread, and the weight copies, complete before the
+      // tensor memory is freed (bounded waits)
+      tc_commit(&bar_drain);
+      mbar_wait(&bar_drain, 0, kTcTries);
+      mbar_wait(&bar_w, 0, kTcTries);
+    }
+  } else {
+    // ---- epilogues, inputs, read-out (warps 0..7)
+    bool ok = true;
+    const int row = tid & (kTcRows - 1);
+    auto wait = [&](uint64_t* bar, uint32_t par) {
+      ok = __all_sync(0xffffffffu, ok && mbar_wait_or_fail(bar, par, kTcTries, fail));
+      if (ok) tc_fence_after();
+    };
+    // Q rows of local tile i from the four head accumulators (NaN where a
+    // wait ran out)
+    auto write_rows = [&](int i) {
+      uint32_t h[4][8];
+      if (ok && warp < 4) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tmem_ld8_nowait(tacc2 + tf_head_col(q) + ((uint32_t)(warp * 32) << 16), h[q]);
+        tmem_ld_wait();
+      }
+      const int grow = ((int)blockIdx.x + i * (int)gridDim.x) * kTcRows + row;
+      if (warp < 4 && grow < M) {
+        float qv[5];
+        if (ok) {
+          float o[kOut];
+#pragma unroll
+          for (int j = 0; j < kOut; ++j)
+            o[j] = ((__uint_as_float(h[0][j]) + __uint_as_float(h[1][j])) +
+                    (__uint_as_float(h[2][j]) + __uint_as_float(h[3][j]))) +
+                   sb3[j];
+          greedy_action(o, qv, L.plain);
+        } else {
+#pragma unroll
+          for (int a = 0; a < 5; ++a) qv[a] = __int_as_float(0x7fc00000);
+        }
+#pragma unroll
+        for (int a = 0; a < 5; ++a) qout[(long long)grow * 5 + a] = qv[a];
+      }
+    };
+    TcXRegs xr;
+    if (my_tiles > 0) {
+      tc_fetch_x(xr, obs, L, M, blockIdx.x, tid);
+      tc_store_x(xs, xr, L, tid);
+      mbar_arrive(&bar_x);
+    }
+    for (int it = 0; it < my_tiles; ++it) {
+      const uint32_t par = (uint32_t)it & 1u;
+      wait(&bar_l1, par);
+      if (ok) tc_epilogue_tmem(tacc, sb1, warp);  // H1 over the layer-1 accumulators
+      if (it > 0) {
+        wait(&bar_hd, par ^ 1u);
+        write_rows(it - 1);
+      }
       tc_fence_before();
-      __syncthreads();
-      tc_fence_after();
-      // head: 16 columns (6 used)
-      if (tid == 0) tc_layer(tacc, hs, w3s, 16, kHid, &bar_mma);
-      mma_out = true;
-      ok = __syncthreads_and(mbar_wait(&bar_mma, pm, kTcTries));
-      if (ok) {
-        pm ^= 1u;
-        mma_out = false;
+      mbar_arrive(&bar_h1);
+      // X is free (layer 1 of t is complete): the next tile's inputs while layer 2 runs
+      if (ok && it + 1 < my_tiles) {
+        tc_fetch_x(xr, obs, L, M, (int)blockIdx.x + (it + 1) * (int)gridDim.x, tid);
+        tc_store_x(xs, xr, L, tid);
+        mbar_arrive(&bar_x);
       }
+      wait(&bar_l2, par);
+      if (ok) tc_epilogue_tmem(tacc2, sb2, warp);  // H2 over the layer-2 accumulators
+      tc_fence_before();
+      mbar_arrive(&bar_h2);
     }
-    float v[32];
-    if (ok && warp < 4) {
-      tc_fence_after();
-      tmem_ld32(tacc + ((uint32_t)(warp * 32) << 16), v);
+    if (my_tiles > 0) {
+      wait(&bar_hd, (uint32_t)(my_tiles - 1) & 1u);
+      write_rows(my_tiles - 1);
     }
-    if (warp < 4 && grow < M) {
-      float qv[5];
-      if (ok) {
-        float o[kOut];
-#pragma unroll
-        for (int j = 0; j < kOut; ++j) o[j] = v[j] + b3[j];
-        greedy_action(o, qv, L.plain);
-      } else {
-        // a wait ran out: the row's values are marked invalid
-#pragma unroll
-        for (int a = 0; a < 5; ++a) qv[a] = __int_as_float(0x7fc00000);
-      }
-#pragma unroll
-      for (int a = 0; a < 5; ++a) qout[(long long)grow * 5 + a] = qv[a];
-    }
-    // the tensor memory and the X / H tiles are reused by the next tile
     tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
   }
-  // free the tensor memory once nothing is in flight (bounded waits)
-  if (mma_out) mbar_wait(&bar_mma, pm, kTcTries);
-  if (ld_out) mbar_wait(&bar_ld, pl, kTcTries);
-  tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 0) tmem_free(tacc, 256);
+  if (warp == 0) tmem_free(tacc, 512);
 }
 
 // VEM eps-greedy rollout with the network fused in: per step, the 16 envs of
@@ -2539,7 +2631,7 @@ extern "C" int sg_qnet_forward(sg_qnet_t q, const float* obs_dev, int32_t M, flo
   if (!q || !obs_dev || !q_dev || M < 1) return SG_E_INVAL;
   // a persistent grid over the 128-row tiles
   const int ntiles = (M + kTcRows - 1) / kTcRows;
-  k_qnet_forward_tc<<<std::min(ntiles, q->sms), kTcThreads, kTcSmemLaunch, stream>>>(q->img, q->img_tc, q->IL,
+  k_qnet_forward_tc<<<std::min(ntiles, q->sms), kTfThreads, kTcSmemLaunch, stream>>>(q->img, q->img_tc, q->IL,
                                                                                      obs_dev, M, q_dev);
   SG_CUDA(cudaGetLastError());
   return SG_OK;

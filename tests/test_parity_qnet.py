@@ -78,15 +78,17 @@ def test_forward_against_oracle(n_in, M, arch):
     assert err_64 <= 5e-2
 
 
-@pytest.mark.parametrize("M,stride", [(65536, 1), (1 << 20, 61)])
-def test_forward_multi_tile_against_oracle(M, stride):
+@pytest.mark.parametrize("M,stride,n_in", [(65536, 1, 37), (1 << 20, 61, 37), (65536 + 77, 1, 69)])
+def test_forward_multi_tile_against_oracle(M, stride, n_in):
     """The batched tcgen05 forward at sizes where every persistent CTA runs
     many 128-row tiles (65,536 rows: about 3 per CTA; 2^20 rows: about 54),
-    so that the streamed W2 halves, the next tile's input conversion during
-    layer 2 and the barrier phases across tiles are all exercised.  Rows are
-    compared element by element with the oracle's bf16 recipe: all of them at
-    65,536, every 61st at 2^20 (17,190 rows spread over every tile)."""
-    n_in = 37
+    so that the next tile's layer 1 running beside this tile's layer-2
+    epilogue and head, the next tile's input conversion during layer 2, the
+    activations kept in tensor memory and the barrier phases across tiles
+    are all exercised; at the widest input (69: five 16-column groups of
+    layer 1) with a ragged last tile of 77 rows.  Rows are compared element
+    by element with the oracle's bf16 recipe: all of them at 65,536, every
+    61st at 2^20 (17,190 rows spread over every tile)."""
     rng = np.random.default_rng(M)
     q = _qnet(n_in)
     th = _theta(4, n_in, scale=2.0)
