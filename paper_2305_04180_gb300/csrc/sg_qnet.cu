@@ -766,6 +766,9 @@ __global__ void __launch_bounds__(kTfThreads, 1) k_qnet_forward_tc(const uint8_t
       if (it > 0) {
         wait(&bar_hd, par ^ 1u);
         write_rows(it - 1);
+        // the read-out (warps 0..3) is on the critical path: the other
+        // warps' input loads start after it
+        asm volatile("bar.sync 1, %0;\n" ::"n"(kTfEpiThreads) : "memory");
       }
       tc_fence_before();
       mbar_arrive(&bar_h1);
