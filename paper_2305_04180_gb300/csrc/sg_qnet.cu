@@ -919,10 +919,11 @@ __global__ void __launch_bounds__(512 * MT, 1)
 // scans read: the input tile (at most 20 KB) and the step records (16 KB,
 // from byte 32 K) live inside the hidden-activation buffer, which holds H1
 // and H2 during the network only, and all of W1 (two 128-row halves) and W2
-// (four 64-row quarters) stream through two 32 KB buffers by bulk copies
+// (four 32 KB pieces: the K halves of its two 128-row halves) stream through
+// two 32 KB buffers by bulk copies
 // every step, each copy issued as soon as its buffer's previous MMAs are
-// done (both W1 halves during the env steps, two W2 quarters during the
-// layer-1 epilogue); W3 stays.
+// done (both W1 halves during the env steps, the first two W2 pieces during
+// the layer-1 epilogue); W3 stays.
 constexpr int kQtEnvs = 128;
 constexpr int kQtWarps = 32;
 constexpr int kQtThreads = kQtWarps * 32;
@@ -997,10 +998,11 @@ struct QtStream {
     bulk_g2s(buf[b], src, bytes, &ld[b]);
     ld_out[b] = true;
   }
-  // MMAs D[tacc] (+)= A x buffer b^T (Rb rows, K), then commits: the buffer's
-  // barrier, and the layer barrier when `last`
+  // MMAs D[tacc] (+)= A x buffer b^T (Rb rows, K; A from its K step ks0,
+  // onto D when acc), then commits: the buffer's barrier, and the layer
+  // barrier when `last`
   __device__ __forceinline__ void mma(int b, uint32_t tacc, const uint8_t* a, int Rb, int K, uint64_t* layer,
-                                      bool last) {
+                                      bool last, int ks0 = 0, bool acc = false) {
     if (!ok) return;
     if (ld_out[b]) {
       ok = mbar_wait(&ld[b], pl[b], kTcTries);
@@ -1013,8 +1015,8 @@ struct QtStream {
     const uint32_t sa = smem_u32(a), sb = smem_u32(buf[b]);
     const uint32_t la = kQtEnvs * 16, lb = (uint32_t)Rb * 16;
     for (int ks = 0; ks < K / 16; ++ks)
-      tc_mma_bf16(tacc, smem_desc(sa + (uint32_t)ks * 2 * la, la, 128),
-                  smem_desc(sb + (uint32_t)ks * 2 * lb, lb, 128), idesc, ks > 0 ? 1u : 0u);
+      tc_mma_bf16(tacc, smem_desc(sa + (uint32_t)(ks0 + ks) * 2 * la, la, 128),
+                  smem_desc(sb + (uint32_t)ks * 2 * lb, lb, 128), idesc, (acc || ks > 0) ? 1u : 0u);
     tc_commit(&mm[b]);
     mm_out[b] = true;
     if (last) tc_commit(layer);
@@ -1202,15 +1204,15 @@ __global__ void __launch_bounds__(kQtThreads, 1)
       __syncthreads();
       tc_fence_after();
       // layer 1: two 128-unit halves of W1 through the buffers (normally
-      // loaded during the previous env steps), then W2 quarters 0 and 1 into
-      // them as soon as each half's MMAs are done
+      // loaded during the previous env steps), then the two K-half pieces of
+      // W2's first 128 rows into them as soon as each half's MMAs are done
       if (tid == 0) {
         if (!S.ld_out[0]) S.load(0, timg + G.w1h, w1h_bytes);
         if (!S.ld_out[1]) S.load(1, timg + G.w1h + w1h_bytes, w1h_bytes);
         S.mma(0, tacc, hx, 128, L.k1, &bar_layer, false);
         S.mma(1, tacc + 128u, hx, 128, L.k1, &bar_layer, true);
-        S.load(0, timg + G.w2q, w2q_bytes);
-        S.load(1, timg + G.w2q + w2q_bytes, w2q_bytes);
+        S.load(0, timg + G.w2a, w2q_bytes);
+        S.load(1, timg + G.w2a + w2q_bytes, w2q_bytes);
         if (!S.ok) ok_sh = 0;
       }
       layer_out = true;
@@ -1225,15 +1227,17 @@ __global__ void __launch_bounds__(kQtThreads, 1)
       tc_fence_before();
       __syncthreads();
       tc_fence_after();
-      // layer 2: four 64-unit quarters of W2 through the buffers; quarters
-      // 2 and 3 are both in flight before either is needed
+      // layer 2: two 128-unit halves (N = 128: an MMA of M = 128 costs about
+      // as much at N = 64 as at 128), each from the two 32 KB K-half pieces
+      // of its rows through the buffers (piece c: K steps 8 c .. 8 c + 7);
+      // the second half's pieces are both in flight before either is needed
       if (tid == 0) {
-        S.mma(0, tacc, hx, 64, kHid, &bar_layer, false);
-        S.mma(1, tacc + 64u, hx, 64, kHid, &bar_layer, false);
-        S.load(0, timg + G.w2q + 2u * w2q_bytes, w2q_bytes);
-        S.load(1, timg + G.w2q + 3u * w2q_bytes, w2q_bytes);
-        S.mma(0, tacc + 128u, hx, 64, kHid, &bar_layer, false);
-        S.mma(1, tacc + 192u, hx, 64, kHid, &bar_layer, true);
+        S.mma(0, tacc, hx, 128, kHid / 2, &bar_layer, false, 0, false);
+        S.mma(1, tacc, hx, 128, kHid / 2, &bar_layer, false, 8, true);
+        S.load(0, timg + G.w2b, w2q_bytes);
+        S.load(1, timg + G.w2b + w2q_bytes, w2q_bytes);
+        S.mma(0, tacc + 128u, hx, 128, kHid / 2, &bar_layer, false, 0, false);
+        S.mma(1, tacc + 128u, hx, 128, kHid / 2, &bar_layer, true, 8, true);
         if (!S.ok) ok_sh = 0;
       }
       layer_out = true;
@@ -1900,9 +1904,10 @@ __device__ __forceinline__ bool lt_forward(LtStream& S, uint64_t* bar_layer, uin
         S.done(h);
       }
     if (S.ok) tc_commit(bar_layer);
-    // the first two W2 quarters follow as soon as the buffers are free
-    S.load(0, timg + G.w2q, w2q);
-    S.load(1, timg + G.w2q + w2q, w2q);
+    // W2 in 32 KB pieces: the two K halves of its first 128 rows follow as
+    // soon as the buffers are free
+    S.load(0, timg + G.w2a, w2q);
+    S.load(1, timg + G.w2a + w2q, w2q);
   }
   layer_out = true;
   bool ok = __syncthreads_and(mbar_wait(bar_layer, player, kTcTries));
@@ -1914,20 +1919,19 @@ __device__ __forceinline__ bool lt_forward(LtStream& S, uint64_t* bar_layer, uin
   fence_async_smem();
   lt_sync();
   if (tid == 0) {
-    // layer 2 in four 64-unit quarters (quarters 2 and 3 are copied in
-    // together once 0 and 1 are consumed)
-    for (int q = 0; q < 4; ++q) {
-      const int b = q & 1;
-      if (q == 2) {
-        S.load(0, timg + G.w2q + 2u * w2q, w2q);
-        S.load(1, timg + G.w2q + 3u * w2q, w2q);
+    // layer 2 in two 128-unit halves (N = 128: an MMA of M = 128 costs
+    // about as much at N = 64 as at 128), each from two 32 KB K-half pieces
+    // of its rows (piece c: K steps 8 c .. 8 c + 7, in buffer c); the second
+    // half's pieces are copied in as the first half's are consumed
+    for (int h = 0; h < 2; ++h)
+      for (int c = 0; c < 2; ++c) {
+        if (h == 1) S.load(c, timg + G.w2b + (uint32_t)c * w2q, w2q);
+        if (S.ready(c)) {
+          lt_mma(tacc + 128u * h, sh1 + (uint32_t)(16 * c) * kA, kA, 128, 2 * kA, smem_u32(S.buf[c]), 128u * 16u,
+                 128, 2u * 128u * 16u, idesc_bf16_f32(kLtRows, 128), kHid / 32, c > 0);
+          S.done(c);
+        }
       }
-      if (S.ready(b)) {
-        lt_mma(tacc + 64u * q, sh1, kA, 128, 2 * kA, smem_u32(S.buf[b]), 64u * 16u, 128, 2u * 64u * 16u,
-               idesc_bf16_f32(kLtRows, 64), kHid / 16, false);
-        S.done(b);
-      }
-    }
     if (S.ok) tc_commit(bar_layer);
     S.load(0, timg + G.w3, 16u * kHid * 2u);  // the head's weights next
   }
