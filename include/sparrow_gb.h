@@ -412,10 +412,12 @@ int sg_qnet_copy_params(sg_qnet_t dst, sg_qnet_t src, sg_stream_t stream);
 
 /*
  * Batched inference: q_dev[M][5] = Q(obs_dev[M][n_in]) with the online
- * network, on the fifth-generation tensor cores (tcgen05: 128 rows per CTA,
- * BF16 operands in shared memory, FP32 accumulators in tensor memory; the
- * same BF16 recipe as the fused rollout).  If a device-side wait runs out
- * (it should not), the rows of that CTA are NaN.
+ * network, on the fifth-generation tensor cores (tcgen05: persistent CTAs
+ * over 128-row tiles, BF16 weights and inputs in shared memory, FP32
+ * accumulators and the BF16 hidden activations in tensor memory; the same
+ * BF16 recipe as the fused rollout).  obs_dev and q_dev are device
+ * pointers, M >= 1; SG_E_INVAL for a null handle or pointer.  If a
+ * device-side wait runs out (it should not), the rows of that CTA are NaN.
  */
 int sg_qnet_forward(sg_qnet_t q, const float* obs_dev, int32_t M, float* q_dev, sg_stream_t stream);
 
