@@ -294,6 +294,16 @@ int sg_sim_get_launch(sg_sim_t sim, sg_launch* cfg);
  */
 int sg_sim_get_state(sg_sim_t sim, void* host_buf, size_t* bytes);
 int sg_sim_set_state(sg_sim_t sim, const void* host_buf, size_t bytes);
+/*
+ * sg_sim_set_state ordered on `stream` instead of synchronous: the upload
+ * (the same blob, bytes = info.state_bytes, else SG_E_INVAL) runs after the
+ * work enqueued on the stream before it, so a caller can queue the next
+ * rollout's start state behind the current one.  host_buf must stay valid
+ * and unchanged until the copy has run; page-locked memory makes the copy
+ * asynchronous (with pageable memory the call returns once the data is
+ * staged).
+ */
+int sg_sim_set_state_async(sg_sim_t sim, const void* host_buf, size_t bytes, sg_stream_t stream);
 
 /*
  * Copy the bit-packed map atlas to the host: for map m, row cy starts at

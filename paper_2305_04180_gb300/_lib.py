@@ -80,6 +80,7 @@ SIGNATURES = {
     "sg_sim_get_launch": (C.c_int, [_vp, _vp]),
     "sg_sim_get_state": (C.c_int, [_vp, _vp, _vp]),
     "sg_sim_set_state": (C.c_int, [_vp, _vp, C.c_size_t]),
+    "sg_sim_set_state_async": (C.c_int, [_vp, _vp, C.c_size_t, _vp]),
     "sg_sim_get_atlas": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "sg_sim_get_clearance": (C.c_int, [_vp, _vp, _vp, _vp]),
     "sg_sim_get_sector_skip": (C.c_int, [_vp, _vp, _vp, _vp]),

@@ -1596,6 +1596,21 @@ extern "C" int sg_sim_set_state(sg_sim_t sim, const void* host_buf, size_t bytes
   return SG_OK;
 }
 
+extern "C" int sg_sim_set_state_async(sg_sim_t sim, const void* host_buf, size_t bytes, sg_stream_t stream) {
+  SG_RANGE("sg_sim_set_state_async");
+  if (!sim || !host_buf) return SG_E_INVAL;
+  const size_t need = (size_t)sg_state_bytes(sim);
+  if (bytes != need) return SG_E_INVAL;
+  const size_t n = (size_t)sim->dc.n_envs;
+  const cudaStream_t st = (cudaStream_t)stream;
+  SG_CUDA(cudaMemcpyAsync(sim->fstate, host_buf, 9 * 4 * n, cudaMemcpyHostToDevice, st));
+  SG_CUDA(cudaMemcpyAsync(sim->ustate, (const char*)host_buf + 9 * 4 * n, 4 * 4 * n, cudaMemcpyHostToDevice, st));
+  if (sim->dc.n_dyn > 0)
+    SG_CUDA(cudaMemcpyAsync(sim->dyn, (const char*)host_buf + 13 * 4 * n, 16 * (size_t)sim->dc.n_dyn * n,
+                            cudaMemcpyHostToDevice, st));
+  return SG_OK;
+}
+
 extern "C" int sg_sim_get_atlas(sg_sim_t sim, uint32_t* atlas_host, size_t* words, int64_t* offs_host,
                                 int32_t* row_words_host) {
   SG_RANGE("sg_sim_get_atlas");

@@ -185,6 +185,23 @@ class Sim:
         buf = np.concatenate(parts)
         check(self.L.sg_sim_set_state(self.handle, buf.ctypes.data, buf.size), "sg_sim_set_state")
 
+    def state_blob(self, f, u, dyn=None, pin=True):
+        """The state blob of set_state as a (page-locked) uint8 host tensor,
+        for set_state_async."""
+        f = np.ascontiguousarray(f, np.float32).reshape(9, self.n)
+        u = np.ascontiguousarray(u, np.uint32).reshape(4, self.n)
+        parts = [f.ravel().view(np.uint8), u.ravel().view(np.uint8)]
+        if self.n_dyn:
+            parts.append(np.ascontiguousarray(dyn, np.float32).reshape(4 * self.n_dyn, self.n).ravel().view(np.uint8))
+        buf = torch.from_numpy(np.concatenate(parts))
+        return buf.pin_memory() if pin else buf
+
+    def set_state_async(self, blob, stream=None):
+        """sg_sim_set_state_async: upload a state blob (state_blob) ordered
+        on the stream; blob must stay alive until the copy has run."""
+        check(self.L.sg_sim_set_state_async(self.handle, C.c_void_p(blob.data_ptr()), int(blob.numel()),
+                                            _stream(stream)), "sg_sim_set_state_async")
+
     def atlas(self):
         words = C.c_size_t(0)
         check(self.L.sg_sim_get_atlas(self.handle, None, C.byref(words), None, None), "sg_sim_get_atlas")

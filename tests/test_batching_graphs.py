@@ -326,3 +326,47 @@ def test_checkpoint_resume_is_bit_identical():
     fb, ub = tb.sim.get_state()
     assert np.array_equal(bits(fa), bits(fb)) and np.array_equal(ua, ub)
     assert ta.updates == tb.updates and ta.replay.steps_recorded() == tb.replay.steps_recorded()
+
+
+def test_async_state_upload_matches_synchronous_and_is_stream_ordered():
+    """sg_sim_set_state_async restores exactly what sg_sim_set_state does,
+    and, queued on a stream behind a rollout, replaces the state only after
+    that rollout (the next rollout then repeats the first from the same
+    start state, bit for bit)."""
+    from paper_2305_04180_gb300 import Sim
+
+    params, maps, env_map, beams = _uneven(n=64, seed=5)
+    s = Sim(params, maps, env_map, beams)
+    s.reset()
+    _run(s, 7)
+    f0, u0 = s.get_state()
+    blob = s.state_blob(f0, u0)
+    ref = _run(s, 20)
+    f1, u1 = s.get_state()
+    # a synchronous restore and an asynchronous one give the same state
+    s.set_state(f0, u0)
+    fa, ua = s.get_state()
+    _run(s, 5)
+    s.set_state_async(blob)
+    torch.cuda.synchronize()
+    fb, ub = s.get_state()
+    assert np.array_equal(bits(fa), bits(fb)) and np.array_equal(ua, ub)
+    # on one stream: rollout, upload, rollout (no host synchronisation between)
+    st = torch.cuda.Stream()
+    n, K = s.n, 20
+    bufs = [dict(obs_seq=torch.empty((K, n, s.obs_dim), device="cuda"), rew=torch.empty((K, n), device="cuda"),
+                 done=torch.empty((K, n), dtype=torch.uint8, device="cuda")) for _ in range(2)]
+    s.set_state_async(blob, st)
+    for b in bufs:
+        if b is bufs[1]:
+            s.set_state_async(blob, st)
+        s.rollout(K, obs_seq=b["obs_seq"], rew_seq=b["rew"], done_seq=b["done"], stream=st)
+    torch.cuda.synchronize()
+    for b in bufs:
+        for k in ("obs_seq", "rew", "done"):
+            assert np.array_equal(b[k].cpu().numpy(), ref[k]), k
+    fc, uc = s.get_state()
+    assert np.array_equal(bits(fc), bits(f1)) and np.array_equal(uc, u1)
+    from paper_2305_04180_gb300 import _lib
+
+    assert s.L.sg_sim_set_state_async(s.handle, blob.data_ptr(), int(blob.numel()) - 4, None) == _lib.SG_E_INVAL
