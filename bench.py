@@ -709,27 +709,31 @@ def run_full_loop(flush):
         sim.rollout(32, policy="eps_q", qnet=tr.actor, eps=tr.eps, replay=tr.replay)
     torch.cuda.synchronize()
     td = 8
-    # the iteration with the learner's branch running beside the rollout, and
-    # with the learner after it (the rollout's resident grid holds every SM,
-    # so the branches mostly take turns); the faster is the value
+    # the iteration with the learner's branch beside the rollout on SMs of its
+    # own (the rollout's grid capped), beside it on every SM (the rollout's
+    # resident grid holds every SM, so the branches mostly take turns), and
+    # after it; the fastest is the value
+    variants = {"concurrent, learner on 8 SMs": (True, 8), "concurrent, learner on 16 SMs": (True, 16),
+                "concurrent": (True, 0), "after the rollout": (False, 0)}
     times, nodes = {}, {}
-    for conc in (True, False):
-        g = tr.capture_iteration(32, td, concurrent=conc)
+    for name, (conc, lsm) in variants.items():
+        g = tr.capture_iteration(32, td, concurrent=conc, learner_sms=lsm)
         for _ in range(2):
             g.launch(tr.s_actor)
         torch.cuda.synchronize()
         with torch.cuda.stream(tr.s_actor):
-            times[conc] = _time_cuda(lambda: [g.launch(tr.s_actor) for _ in range(4)], 3, flush)
-        nodes[conc] = g.num_nodes()
-    conc = min(times, key=times.get)
-    ms = times[conc]
+            times[name] = _time_cuda(lambda: [g.launch(tr.s_actor) for _ in range(4)], 3, flush)
+        nodes[name] = g.num_nodes()
+        del g
+    best = min(times, key=times.get)
+    ms = times[best]
     return {"workload": w.name, "n_envs": sim.n, "maps": sim.n_maps, "steps_timed": 128,
             "value": sim.n * 128 / (ms / 1e3), "unit": UNIT, "ms_per_128_steps": ms,
-            "learner_branch": "concurrent" if conc else "after the rollout",
-            "ms_per_128_steps_concurrent": times[True], "ms_per_128_steps_sequential": times[False],
+            "learner_branch": best, "ms_per_128_steps_by_variant": times,
+            "ms_per_128_steps_concurrent": times["concurrent"], "ms_per_128_steps_sequential": times["after the rollout"],
             "learner": {"batch": tr.batch, "td_steps_per_128_env_steps": 4 * td,
                         "td_steps_per_s": 4 * td / (ms / 1e3), "loss": float(tr.loss.item())},
-            "ring": f"{tr.replay.capacity} transitions (reserve 32 slots)", "graph_nodes": nodes[conc]}
+            "ring": f"{tr.replay.capacity} transitions (reserve 32 slots)", "graph_nodes": nodes[best]}
 
 
 # vectorized steps of the CPU-oracle sample (about 10 s on 16 cores at 1,024 envs)

@@ -414,6 +414,18 @@ int sg_qnet_set_optimizer(sg_qnet_t q, const float* m_host, const float* v_host,
 int sg_qnet_set_rollout_rows(sg_qnet_t q, int32_t rows);
 
 /*
+ * At most rollout_ctas CTAs (one per SM) for the tcgen05 fused rollout run
+ * with this network, and at most learner_ctas for its tcgen05 TD step (0 =
+ * every SM, the default; negative: SG_E_INVAL).  The ASL framework runs the
+ * actor and the learner in parallel (Sec. 3.1, Alg. 1 and 2): a rollout and
+ * a learning step launched on concurrent streams (or graph branches) with
+ * caps that add up to the SM count each keep SMs of their own instead of
+ * taking turns.  Results do not depend on the caps (the rollout's items and
+ * the learner's jobs are taken from device counters by whichever CTAs run).
+ */
+int sg_qnet_set_grid_limit(sg_qnet_t q, int32_t rollout_ctas, int32_t learner_ctas);
+
+/*
  * Model upload (Alg. 2 step 3 / Alg. 1 step 1: the actor takes the learner's
  * latest parameters every U optimisation steps): dst's online network takes
  * src's online parameters and BF16 copy, stream-ordered.  Same n_in.

@@ -93,6 +93,7 @@ SIGNATURES = {
     "sg_qnet_get_optimizer": (C.c_int, [_vp, _vp, _vp, C.c_int64, _vp]),
     "sg_qnet_set_optimizer": (C.c_int, [_vp, _vp, _vp, C.c_int64, C.c_uint64]),
     "sg_qnet_set_rollout_rows": (C.c_int, [_vp, _i32]),
+    "sg_qnet_set_grid_limit": (C.c_int, [_vp, _i32, _i32]),
     "sg_qnet_copy_params": (C.c_int, [_vp, _vp, _vp]),
     "sg_qnet_forward": (C.c_int, [_vp, _vp, _i32, _vp, _vp]),
     "sg_replay_create": (C.c_int, [_i32, _i32, _i32, _i32, _vp]),

@@ -152,6 +152,8 @@ struct sg_qnet {
   float* y = nullptr;        // [max_batch] TD targets
   int* idx = nullptr;        // [max_batch] sampled ring entries
   int rollout_mt = 0;        // m-tiles per CTA of the fused rollout (0 = choose by waves)
+  int lim_rollout = 0;       // CTA caps of the tcgen05 rollout / learner grids (0 = every SM)
+  int lim_learner = 0;
   uint8_t* img_tc = nullptr; // the online weights in the tensor cores' shared-memory layout (batched forward)
   uint8_t* img_tc_t = nullptr; // the target weights in the same layout (tcgen05 learner)
   float* q2 = nullptr;       // [2][max_batch][5] Q-values of the sampled next states (tcgen05 learner)
@@ -2610,6 +2612,14 @@ extern "C" int sg_qnet_set_rollout_rows(sg_qnet_t q, int32_t rows) {
   return SG_OK;
 }
 
+extern "C" int sg_qnet_set_grid_limit(sg_qnet_t q, int32_t rollout_ctas, int32_t learner_ctas) {
+  SG_RANGE("sg_qnet_set_grid_limit");
+  if (!q || rollout_ctas < 0 || learner_ctas < 0) return SG_E_INVAL;
+  q->lim_rollout = rollout_ctas;
+  q->lim_learner = learner_ctas;
+  return SG_OK;
+}
+
 extern "C" int sg_qnet_copy_params(sg_qnet_t dst, sg_qnet_t src, sg_stream_t stream) {
   SG_RANGE("sg_qnet_copy_params");
   if (!dst || !src || dst->n_in != src->n_in || dst->arch != src->arch) return SG_E_INVAL;
@@ -2805,11 +2815,13 @@ int sg_rollout_eps_q(sg_sim* sim, int K, sg_qnet* q, const float* eps, sg_replay
   if (tc) {
     // more than one wave of 128-env CTAs: slice the rollout into 4 segments
     // over a resident grid so that no SM idles in a part-empty last wave
+    // (the grid within the network's CTA cap, when one is set)
+    const int cap = q->lim_rollout > 0 ? std::min(q->lim_rollout, sms) : sms;
     const int nblk = (n + kQtEnvs - 1) / kQtEnvs;
-    const int seg = (nblk > sms && K >= 4) ? (K + 3) / 4 : 0;
+    const int seg = (nblk > cap && K >= 4) ? (K + 3) / 4 : 0;
     int grid = nblk;
     if (seg > 0) {
-      grid = std::min(nblk * ((K + seg - 1) / seg), sms);
+      grid = std::min(nblk * ((K + seg - 1) / seg), cap);
       SG_CUDA(cudaMemsetAsync(sim->q_sync_dev, 0, sizeof(unsigned) * (size_t)(nblk + 2), stream));
     }
     k_rollout_q_tc<<<grid, kQtThreads, qt_smem().bytes, stream>>>(
@@ -2852,7 +2864,8 @@ extern "C" int sg_td_train_step(sg_qnet_t q, sg_replay_t rp, int32_t batch, floa
     const int ntiles = (batch + kLtRows - 1) / kLtRows;
     nblk = ntiles;
     SG_CUDA(cudaMemsetAsync(q->td_sync, 0, (size_t)(1 + ntiles) * 4, stream));
-    k_td_tc<<<std::min(4 * ntiles, q->sms), kLtThreads, kTcSmemLaunch, stream>>>(
+    const int cap = q->lim_learner > 0 ? std::min(q->lim_learner, q->sms) : q->sms;
+    k_td_tc<<<std::min(4 * ntiles, cap), kLtThreads, kTcSmemLaunch, stream>>>(
         q->img, q->img_t, q->img_tc, q->img_tc_t, q->IL, q->PL, rp->d, seed, q->step, batch, gamma, q->q2, q->idx,
         q->td_sync, q->partial, q->td_fail);
     SG_CUDA(cudaGetLastError());

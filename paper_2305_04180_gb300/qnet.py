@@ -73,6 +73,12 @@ class QNet:
         128 on the tcgen05 kernel, or 0 = automatic)."""
         check(self.L.sg_qnet_set_rollout_rows(self.handle, int(rows)), "sg_qnet_set_rollout_rows")
 
+    def set_grid_limit(self, rollout: int = 0, learner: int = 0):
+        """CTA caps of the tcgen05 fused rollout and TD step run with this
+        network (0 = every SM): concurrent actor and learner keep SMs of
+        their own."""
+        check(self.L.sg_qnet_set_grid_limit(self.handle, int(rollout), int(learner)), "sg_qnet_set_grid_limit")
+
     def copy_from(self, src: "QNet", stream=None):
         """This network's online weights <- src's (model upload), stream-ordered."""
         check(self.L.sg_qnet_copy_params(self.handle, src.handle, _stream(stream)), "sg_qnet_copy_params")

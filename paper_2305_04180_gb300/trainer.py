@@ -181,18 +181,36 @@ class ColorTrainer:
         torch.cuda.synchronize()
         return self
 
-    def capture_iteration(self, rollout_k: int, td_steps: int, concurrent: bool = True):
+    def capture_iteration(self, rollout_k: int, td_steps: int, concurrent: bool = True, learner_sms: int = 0):
         """One actor-learner iteration as a CUDA graph: the actor's fused
         rollout of rollout_k steps and td_steps learner steps, then the model
         upload.  concurrent=True forks the two as branches of the graph that
         overlap on the GPU (the ring's reserve keeps the learner off the
         slots being written; which completed slots it samples then depends on
         timing); concurrent=False runs the learner after the rollout and is
-        deterministic.  Requires two_streams=True, rollout_k <= max_rollout_k."""
+        deterministic.  learner_sms > 0 (concurrent only): the learner's TD
+        steps run on at most that many CTAs and the rollout on the other SMs,
+        so the branches overlap instead of taking turns.  Requires
+        two_streams=True, rollout_k <= max_rollout_k."""
         assert self.two_streams and rollout_k <= self.max_rollout_k
         g = Graph()
         main = self.s_actor
         torch.cuda.synchronize()
+        split = concurrent and learner_sms > 0
+        if split:
+            sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+            assert 0 < learner_sms < sms
+            self.actor.set_grid_limit(rollout=sms - learner_sms)
+            self.learner.set_grid_limit(learner=learner_sms)
+        try:
+            self._capture_body(g, main, rollout_k, td_steps, concurrent)
+        finally:
+            if split:
+                self.actor.set_grid_limit()
+                self.learner.set_grid_limit()
+        return g
+
+    def _capture_body(self, g, main, rollout_k, td_steps, concurrent):
         with g.capture(main):
             if concurrent:
                 fork = torch.cuda.Event()
@@ -212,4 +230,3 @@ class ColorTrainer:
             join.record(self.s_learner)
             main.wait_event(join)
             self.actor.copy_from(self.learner, stream=main)
-        return g

@@ -109,6 +109,54 @@ def test_forward_multi_tile_against_oracle(M, stride, n_in):
     assert np.array_equal(got_p, got[perm])
 
 
+def test_grid_limits_do_not_change_results():
+    """sg_qnet_set_grid_limit caps the tcgen05 rollout's and learner's
+    grids (so that a concurrent actor and learner keep SMs of their own);
+    with caps of 30 rollout CTAs (40 blocks of 128 envs: a time-sliced
+    rollout over a resident grid instead of one CTA per block) and 8 learner
+    CTAs (16 jobs per CTA) the actions,
+    rewards, ring contents, final state, loss and gradient equal the
+    uncapped runs bit for bit."""
+    from paper_2305_04180_gb300 import Replay, Sim
+
+    w = workload("qnet4096", n_envs=5120)
+    maps = w.maps()
+    q = _qnet(w.params["n_beams"] + 5, max_batch=4096)
+    q.set_params(_theta(22, q.n_in, scale=3.0))
+    q.set_rollout_rows(128)
+    eps = torch.from_numpy(_eps_spread(5120)).cuda()
+    out = []
+    for caps in ((0, 0), (30, 8)):
+        q.set_grid_limit(rollout=caps[0], learner=caps[1])
+        s = Sim(w.params, maps, w.env_map)
+        rp = Replay(48, s.n, s.obs_dim)
+        s.reset()
+        K = 24
+        act = torch.empty((K, s.n), dtype=torch.uint8, device="cuda")
+        rew = torch.empty((K, s.n), device="cuda")
+        s.rollout(K, policy="eps_q", qnet=q, eps=eps, replay=rp, act_seq=act, rew_seq=rew)
+        loss = torch.zeros(1, device="cuda")
+        grad = torch.zeros(q.n_params, device="cuda")
+        q2 = _qnet(q.n_in, max_batch=4096)
+        q2.set_params(q.get_params())
+        q2.set_grid_limit(learner=caps[1])
+        q2.train_step(rp, 4096, gamma=0.98, lr=0.0, seed=7, loss=loss, grad=grad)
+        torch.cuda.synchronize()
+        assert s.status() == 0
+        out.append((act.cpu().numpy(), rew.cpu().numpy(), rp.read(0, K * s.n), s.get_state(),
+                    loss.cpu().numpy(), grad.cpu().numpy()))
+    q.set_grid_limit()
+    (a0, r0, ring0, st0, l0, g0), (a1, r1, ring1, st1, l1, g1) = out
+    assert np.array_equal(a0, a1) and np.array_equal(bits(r0), bits(r1))
+    for x, y in zip(ring0, ring1):
+        assert np.array_equal(x.view(np.uint8), y.view(np.uint8))
+    for x, y in zip(st0, st1):
+        assert np.array_equal(x.view(np.uint32), y.view(np.uint32))
+    assert np.isfinite(l0).all() and np.array_equal(bits(l0), bits(l1))
+    assert np.array_equal(bits(g0), bits(g1))
+    assert q.L.sg_qnet_set_grid_limit(q.handle, -1, 0) != 0
+
+
 def _margin_ok(q_ref, act, tol):
     """Greedy action equals the argmax, or the argmax is within tol of it."""
     best = q_ref.max(axis=1)
