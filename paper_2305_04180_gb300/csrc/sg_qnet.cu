@@ -2813,12 +2813,28 @@ int sg_rollout_eps_q(sg_sim* sim, int K, sg_qnet* q, const float* eps, sg_replay
   const bool tc = !dyn && (q->rollout_mt == 8 || (q->rollout_mt == 0 && n >= kQtEnvs * sms));
   const int mt = q->rollout_mt > 0 && q->rollout_mt <= 2 ? q->rollout_mt : (!dyn && waves32 < waves16 ? 2 : 1);
   if (tc) {
-    // more than one wave of 128-env CTAs: slice the rollout into 4 segments
-    // over a resident grid so that no SM idles in a part-empty last wave
-    // (the grid within the network's CTA cap, when one is set)
+    // more than one wave of 128-env CTAs: slice the rollout into 4 to 6
+    // segments over a resident grid so that no SM idles in a part-empty last
+    // wave (the grid within the network's CTA cap, when one is set): the
+    // count whose (block, segment) items fill the last round of the grid
+    // best (65,536 envs: 5 segments, 429.7 M env-steps/s against 425.8 M
+    // with 4, 427.0 M with 6, 413.5 M with 8)
     const int cap = q->lim_rollout > 0 ? std::min(q->lim_rollout, sms) : sms;
     const int nblk = (n + kQtEnvs - 1) / kQtEnvs;
-    const int seg = (nblk > cap && K >= 4) ? (K + 3) / 4 : 0;
+    int seg = 0;
+    if (nblk > cap && K >= 4) {
+      double best = 0.0;
+      for (int ns = 4; ns <= 6 && ns <= K; ++ns) {
+        const int sl = (K + ns - 1) / ns;
+        const long long items = (long long)nblk * ((K + sl - 1) / sl);
+        const long long rounds = (items + cap - 1) / cap;
+        const double fill = (double)items / ((double)rounds * cap);
+        if (fill > best + 1e-9) {
+          best = fill;
+          seg = sl;
+        }
+      }
+    }
     int grid = nblk;
     if (seg > 0) {
       grid = std::min(nblk * ((K + seg - 1) / seg), cap);
