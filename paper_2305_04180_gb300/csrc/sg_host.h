@@ -14,6 +14,7 @@ struct sg_sim {
   sg::DevCfg dc;
   int n_maps = 0;
   int device = 0;
+  int step_epw = 0;  // envs per warp of k_step (0 = not chosen yet)
   long long atlas_words = 0;
   long long clr_bytes = 0;
   std::vector<sg::MapDesc> maps_host;

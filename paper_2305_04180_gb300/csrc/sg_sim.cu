@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(128) k_reset(const __grid_constant__ DevCfg c,
   if (kDyn && lane < c.n_dyn) store_obst(p, lane, env, b);
 }
 
-// One vectorized step of every env (sg_sim_step).  A warp takes kStepEnvsPerWarp
+// One vectorized step of every env (sg_sim_step).  A warp takes kE
 // envs (consecutive in the env order grouped by map): its lanes 0.. run the
 // scalar part of the step for one env each (lane_step: state load, delay,
 // Eq. 5, Eq. 6, collision, arrival, truncation, AutoReset draws and the
@@ -171,9 +171,10 @@ __global__ void __launch_bounds__(128) k_reset(const __grid_constant__ DevCfg c,
 // post-motion state always (the observation, or the terminal observation and
 // the reward of a done env), the reset state of a done env.  No warp waits on
 // another.  Every value is the one-env-per-warp step's, in the same float32
-// expressions.  8 envs per warp measured fastest at 65,536 envs (4: 75 us,
-// 8: 72 us, 16: 75 us per launch; 4 or 16 warps per CTA instead of 8: 73 us).
-constexpr int kStepEnvsPerWarp = 8;
+// expressions.  kE envs per warp (6, 7 or 8; the host takes the count whose
+// grid fills its last wave of resident CTAs best: at 65,536 envs 7, 70.8 us
+// per launch, against 72.7 us with 8 and 77 us with 6; 4 per warp 75 us, 16
+// per warp 75 us; 4 or 16 warps per CTA instead of 8 slower).
 constexpr int kStepWarps = 8;
 
 // Disc centres of an env for its two scans (dynamic obstacles only).
@@ -181,18 +182,18 @@ struct DiscRec {
   Discs a, b;
 };
 
-template <bool kDyn>
+template <bool kDyn, int kE>
 __global__ void __launch_bounds__(32 * kStepWarps, 4) k_step(const __grid_constant__ DevCfg c, SimPtrs p,
                                                              const int* __restrict__ order,
                                                              const uint8_t* __restrict__ act,
                                                              float* __restrict__ obs, float* __restrict__ rew,
                                                              uint8_t* __restrict__ done, float* __restrict__ term) {
-  __shared__ StepScanRec rec[kStepWarps][kStepEnvsPerWarp];
-  __shared__ DiscRec drec[kDyn ? kStepWarps : 1][kDyn ? kStepEnvsPerWarp : 1];
+  __shared__ StepScanRec rec[kStepWarps][kE];
+  __shared__ DiscRec drec[kDyn ? kStepWarps : 1][kDyn ? kE : 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int base = (blockIdx.x * kStepWarps + warp) * kStepEnvsPerWarp;
+  const int base = (blockIdx.x * kStepWarps + warp) * kE;
   if (base >= c.n_envs) return;  // warp-uniform
-  const int nv = min(kStepEnvsPerWarp, c.n_envs - base);
+  const int nv = min(kE, c.n_envs - base);
   const bool live = lane < nv;
   const int i = live ? order[base + lane] : 0;
   Env s;
@@ -1391,9 +1392,32 @@ extern "C" int sg_sim_step(sg_sim_t sim, const uint8_t* act_dev, float* obs_dev,
   SG_RANGE("sg_sim_step");
   if (!sim || !act_dev || !obs_dev || !rew_dev || !done_dev) return SG_E_INVAL;
   if (((uintptr_t)obs_dev & 3) || ((uintptr_t)rew_dev & 3) || ((uintptr_t)term_obs_dev & 3)) return SG_E_ALIGN;
-  constexpr int kPerBlock = kStepWarps * kStepEnvsPerWarp;
-  auto kern = sim->dc.n_dyn > 0 ? k_step<true> : k_step<false>;
-  kern<<<(sim->dc.n_envs + kPerBlock - 1) / kPerBlock, 32 * kStepWarps, 0, stream>>>(
+  const bool dyn = sim->dc.n_dyn > 0;
+  auto kern_for = [dyn](int e) {
+    if (e == 6) return dyn ? k_step<true, 6> : k_step<false, 6>;
+    if (e == 7) return dyn ? k_step<true, 7> : k_step<false, 7>;
+    return dyn ? k_step<true, 8> : k_step<false, 8>;
+  };
+  const long long n = sim->dc.n_envs;
+  if (sim->step_epw == 0) {
+    // envs per warp: the count whose grid fills its last wave of resident
+    // CTAs best (chosen once per simulator)
+    int sms = 0;
+    SG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, sim->device));
+    double best = -1.0;
+    for (int e = 8; e >= 6; --e) {
+      int bps = 0;
+      SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern_for(e), 32 * kStepWarps, 0));
+      const long long ctas = (n + kStepWarps * e - 1) / (kStepWarps * e), res = (long long)sms * std::max(bps, 1);
+      const double fill = (double)ctas / (double)(((ctas + res - 1) / res) * res);
+      if (fill > best + 1e-9) {
+        best = fill;
+        sim->step_epw = e;
+      }
+    }
+  }
+  const int per = kStepWarps * sim->step_epw;
+  kern_for(sim->step_epw)<<<(unsigned)((n + per - 1) / per), 32 * kStepWarps, 0, stream>>>(
       sim->dc, sg_sim_ptrs(sim), sim->map_order_dev, act_dev, obs_dev, rew_dev, done_dev, term_obs_dev);
   SG_CUDA(cudaGetLastError());
   return SG_OK;
