@@ -713,8 +713,8 @@ def run_full_loop(flush):
     # own (the rollout's grid capped), beside it on every SM (the rollout's
     # resident grid holds every SM, so the branches mostly take turns), and
     # after it; the fastest is the value
-    variants = {"concurrent, learner on 8 SMs": (True, 8), "concurrent, learner on 16 SMs": (True, 16),
-                "concurrent": (True, 0), "after the rollout": (False, 0)}
+    variants = {f"concurrent, learner on {k} SMs": (True, k) for k in (6, 8, 10, 16)}
+    variants.update({"concurrent": (True, 0), "after the rollout": (False, 0)})
     times, nodes = {}, {}
     for name, (conc, lsm) in variants.items():
         g = tr.capture_iteration(32, td, concurrent=conc, learner_sms=lsm)
