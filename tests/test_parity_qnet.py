@@ -59,7 +59,8 @@ def test_params_roundtrip_and_count(arch, n_in, count):
 
 @pytest.mark.parametrize("n_in,M,arch", [(37, 1, "dueling"), (37, 53, "dueling"), (37, 4096, "dueling"),
                                          (69, 300, "dueling"), (21, 17, "dueling"), (32, 300, "paper"),
-                                         (32, 1, "paper"), (37, 77, "paper")])
+                                         (32, 1, "paper"), (37, 77, "paper"), (48, 300, "dueling"),
+                                         (64, 129, "dueling"), (65, 257, "dueling")])
 def test_forward_against_oracle(n_in, M, arch):
     rng = np.random.default_rng(n_in + M)
     q = _qnet(n_in, arch=arch)
@@ -484,6 +485,44 @@ def test_td_gradient_elementwise_against_oracle(batch, arch, n_envs):
               f"{np.abs(r).max():.3e}), max error / bound {ratio:.3f}")
         assert np.all(e <= bound), (name, int(np.argmax(e / np.maximum(bound, 1e-30))))
     print(f"batch {batch} {arch}: loss {gl:.6f} vs {ref_loss:.6f}; worst error / bound {worst:.3f}")
+
+
+@pytest.mark.parametrize("n_in", [69, 48])
+def test_td_gradient_widest_inputs_at_batch_4096(n_in):
+    """The tcgen05 learner at batch 4,096 with inputs of 69 (five 16-column
+    groups of layer 1, dW1 of N = 80) and 48 (no zero padding) on a
+    synthetic ring: loss and every gradient entry against the oracle's bf16
+    recipe at the bound of the other TD parity tests."""
+    from paper_2305_04180_gb300 import Replay
+
+    rng = np.random.default_rng(n_in)
+    n_envs, slots = 512, 16
+    rp = Replay(slots, n_envs, n_in)
+    cap = rp.capacity
+    s_ = rng.uniform(-1, 1, size=(cap, n_in)).astype(np.float32)
+    s2 = rng.uniform(-1, 1, size=(cap, n_in)).astype(np.float32)
+    a = rng.integers(0, 5, size=cap).astype(np.uint8)
+    r = rng.normal(size=cap).astype(np.float32)
+    t = (rng.uniform(size=cap) < 0.05).astype(np.uint8)
+    rp.write(0, s_, s2, a, r, t, steps_recorded=slots)
+    q = _qnet(n_in, max_batch=4096)
+    th_on, th_tg = _theta(10, n_in, scale=2.0), _theta(11, n_in, scale=2.0)
+    q.set_params(th_on, "online")
+    q.set_params(th_tg, "target")
+    batch, seed = 4096, 13
+    gl, gg = _gpu_loss_grad(q, rp, batch, seed)
+    _, bt = _oracle_batch(rp, seed, 0, batch)
+    pon = OQ.unflatten(th_on.astype(np.float64), n_in)
+    ptg = OQ.unflatten(th_tg.astype(np.float64), n_in)
+    ref_loss, ref_g = OQ.td_loss_grad(pon, ptg, bt, 0.98, bf16=True)
+    rflat = OQ.flatten(ref_g)
+    assert np.isfinite(gg).all()
+    assert abs(gl - ref_loss) <= 1e-4 * max(1e-6, abs(ref_loss)), (gl, ref_loss)
+    for name, sl in _blocks(n_in):
+        ref = rflat[sl]
+        e = np.abs(gg[sl] - ref)
+        bound = TD_ATOL * np.abs(ref).max() + TD_RTOL * np.abs(ref)
+        assert np.all(e <= bound), (name, int(np.argmax(e / np.maximum(bound, 1e-30))))
 
 
 def test_td_gradient_finite_differences_at_batch_4096():
